@@ -1,0 +1,433 @@
+"""Pins for the CPU oracle: each test checks the oracle against something
+other than itself (a dense matvec or LAPACK solve from numpy, a closed
+form, an invariant, brute force, or a hand-written layout).  CPU only."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_08230_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _csr(n, ncols, rp, ci, va):
+    return W.CSR(n, ncols, np.asarray(rp), np.asarray(ci), np.asarray(va, dtype=np.float64))
+
+
+# ----------------------------------------------------------------- SpMV
+
+@pytest.mark.parametrize("seed,n,ncols,dens,empty,full", [
+    (1, 1, 1, 1.0, 0, 0), (2, 7, 5, 0.4, 2, 1), (3, 33, 40, 0.2, 5, 1),
+    (4, 64, 64, 0.1, 10, 2), (5, 37, 3, 0.5, 0, 0), (6, 50, 1, 0.5, 3, 0)])
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (-0.5, 2.0), (2.5, -1.0)])
+def test_spmv_matches_dense_matvec(seed, n, ncols, dens, empty, full, alpha, beta):
+    m = W.random_csr(n, ncols, dens, seed, empty_rows=empty, full_rows=full)
+    rng = np.random.default_rng(seed + 100)
+    x = rng.standard_normal(ncols)
+    y0 = rng.standard_normal(n)
+    ref = alpha * (m.to_dense() @ x) + beta * y0
+    for comp in (True, False):
+        y = oracle.spmv(m, x, alpha, beta, y0, compensated=comp)
+        scale = abs(alpha) * (np.abs(m.to_dense()) @ np.abs(x)) + abs(beta) * np.abs(y0)
+        assert np.all(np.abs(y - ref) <= 1e-14 * scale + 1e-300)
+
+
+def test_spmv_beta_zero_does_not_read_y():
+    m = W.laplacian_2d(4)
+    y = np.full(m.n, np.nan)
+    out = oracle.spmv(m, np.ones(m.n), 1.0, 0.0, y)
+    assert np.all(np.isfinite(out))
+
+
+def _interior_neighbours_2d(N):
+    cnt = np.zeros((N, N), dtype=np.int64)  # [y, x]
+    cnt[:, 1:] += 1
+    cnt[:, :-1] += 1
+    cnt[1:, :] += 1
+    cnt[:-1, :] += 1
+    return cnt.reshape(-1)
+
+
+def test_spmv_integer_exact_5pt_ones():
+    """A*1 for the 5-point Dirichlet Laplacian is 4 - (number of grid
+    neighbours), exactly."""
+    N = 64
+    m = W.laplacian_2d(N)
+    y = oracle.spmv(m, np.ones(m.n))
+    expect = 4 - _interior_neighbours_2d(N)
+    assert np.array_equal(y, expect.astype(np.float64))
+
+
+def test_spmv_integer_exact_mod7():
+    """Integer matrix times integer vector is exact in FP64: compare with an
+    int64 brute-force product."""
+    m = W.laplacian_3d(9, 7, 5)
+    x = (np.arange(m.n) % 7).astype(np.int64)
+    rows = np.repeat(np.arange(m.n), m.row_lengths())
+    ref = np.zeros(m.n, dtype=np.int64)
+    np.add.at(ref, rows, m.values.astype(np.int64) * x[m.col_idx])
+    y = oracle.spmv(m, x.astype(np.float64), compensated=False)
+    assert np.array_equal(y, ref.astype(np.float64))
+
+
+def test_spmv_compensated_sum():
+    """Neumaier compensation recovers the exact row sum where the plain sum
+    cancels: 1e16 + 1 - 1e16 = 1."""
+    m = _csr(1, 3, [0, 3], [0, 1, 2], [1e16, 1.0, -1e16])
+    x = np.ones(3)
+    assert oracle.spmv(m, x, compensated=True)[0] == 1.0
+    assert oracle.spmv(m, x, compensated=False)[0] == 0.0
+
+
+@pytest.mark.parametrize("dims", [(50,), (17, 13), (9, 8, 7)])
+def test_laplacian_closed_form_eigenpairs(dims):
+    """Dirichlet Laplacian eigenpairs: lambda = sum_d 4 sin^2(k_d pi / (2 (N_d + 1))),
+    v = prod_d sin(i_d k_d pi / (N_d + 1))."""
+    m = {1: W.laplacian_1d, 2: W.laplacian_2d, 3: W.laplacian_3d}[len(dims)](*dims)
+    rng = np.random.default_rng(7)
+    grids = np.meshgrid(*[np.arange(1, N + 1) for N in dims], indexing="ij")
+    for _ in range(4):
+        ks = [int(rng.integers(1, N + 1)) for N in dims]
+        lam = sum(4.0 * math.sin(k * math.pi / (2 * (N + 1))) ** 2 for k, N in zip(ks, dims))
+        v = np.ones_like(grids[0], dtype=np.float64)
+        for g, k, N in zip(grids, ks, dims):
+            v = v * np.sin(g * k * math.pi / (N + 1))
+        # workloads index x fastest: flatten with axis 0 fastest
+        v = v.transpose(tuple(reversed(range(len(dims))))).reshape(-1)
+        Av = oracle.spmv(m, v)
+        assert np.linalg.norm(Av - lam * v) <= 1e-13 * np.linalg.norm(v) * max(1.0, lam)
+
+
+# ------------------------------------------------------------ COO -> CSR
+
+def _brute_coo_to_csr(n, row, col, val):
+    """Dictionary of (row, col) -> list of values in input order."""
+    d = {}
+    for r, c, v in zip(row.tolist(), col.tolist(), val.tolist()):
+        d.setdefault((r, c), []).append(v)
+    keys = sorted(d)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    cols, vals = [], []
+    for (r, c) in keys:
+        rp[r + 1] += 1
+        cols.append(c)
+        s = 0.0
+        first = True
+        for v in d[(r, c)]:
+            s = v if first else s + v
+            first = False
+        vals.append(s)
+    return np.cumsum(rp), np.array(cols, dtype=np.int64), np.array(vals)
+
+
+@pytest.mark.parametrize("seed,n,ncols,nnz", [(1, 10, 10, 40), (2, 100, 7, 500),
+                                              (3, 1, 1, 5), (4, 300, 300, 50)])
+def test_coo_to_csr_brute_force(seed, n, ncols, nnz):
+    r, c, v = W.random_coo(n, ncols, nnz, seed)
+    rp, ci, va = oracle.coo_to_csr(n, ncols, r, c, v)
+    brp, bci, bva = _brute_coo_to_csr(n, r, c, v)
+    assert np.array_equal(rp, brp) and np.array_equal(ci, bci)
+    assert np.array_equal(va, bva)
+
+
+def test_coo_duplicates_summed_in_input_order():
+    row = np.array([0, 0, 0, 1, 1, 1], dtype=np.int32)
+    col = np.array([1, 1, 1, 0, 0, 0], dtype=np.int32)
+    # row 0: ((1e16 + 1) - 1e16) = 0 ; row 1: ((1e16 - 1e16) + 1) = 1
+    val = np.array([1e16, 1.0, -1e16, 1e16, -1e16, 1.0])
+    rp, ci, va = oracle.coo_to_csr(2, 2, row, col, val)
+    assert rp.tolist() == [0, 1, 2] and ci.tolist() == [1, 0]
+    assert va.tolist() == [0.0, 1.0]
+
+
+def test_coo_duplicates_summed_in_float32_for_fp32():
+    row = np.zeros(3, dtype=np.int32)
+    col = np.zeros(3, dtype=np.int32)
+    val = np.array([1.0, 2.0 ** -24, 2.0 ** -24])
+    _, _, v32 = oracle.coo_to_csr(1, 1, row, col, val, sum_f32=True)
+    _, _, v64 = oracle.coo_to_csr(1, 1, row, col, val, sum_f32=False)
+    assert v32[0] == 1.0  # each float32 add rounds back to 1 (ties to even)
+    assert v64[0] == 1.0 + 2.0 ** -23
+
+
+def test_coo_keeps_explicit_zeros_and_empty_rows():
+    row = np.array([2, 0], dtype=np.int32)
+    col = np.array([1, 0], dtype=np.int32)
+    val = np.array([0.0, 5.0])
+    rp, ci, va = oracle.coo_to_csr(4, 2, row, col, val)
+    assert rp.tolist() == [0, 1, 1, 2, 2]
+    assert ci.tolist() == [0, 1] and va.tolist() == [5.0, 0.0]
+
+
+def test_coo_permutation_gives_same_csr():
+    m = W.power_law(2000, seed=3)
+    rows = np.repeat(np.arange(m.n), m.row_lengths()).astype(np.int32)
+    perm = np.random.default_rng(1).permutation(m.nnz)
+    rp, ci, va = oracle.coo_to_csr(m.n, m.ncols, rows[perm], m.col_idx[perm], m.values[perm])
+    assert np.array_equal(rp, m.row_ptr) and np.array_equal(ci, m.col_idx)
+    assert np.array_equal(va, m.values)
+
+
+def test_coo_rejects_out_of_range():
+    with pytest.raises(ValueError):
+        oracle.coo_to_csr(2, 2, np.array([0, 2]), np.array([0, 0]), np.ones(2))
+
+
+# --------------------------------------------------------- ELL / SELL-P
+
+def _golden_layout():
+    with open(os.path.join(GOLDEN, "layout_5x4.json")) as f:
+        g = json.load(f)
+    m = _csr(g["n"], g["ncols"], g["row_ptr"], g["col_idx"], g["values"])
+    return g, m
+
+
+def test_ell_golden_layout():
+    g, m = _golden_layout()
+    K, stride, ec, ev = oracle.csr_to_ell(m)
+    assert K == g["ell"]["K"] and stride == g["ell"]["stride"]
+    ec, ev = ec.reshape(K, stride), ev.reshape(K, stride)
+    assert ec[:, :m.n].tolist() == g["ell"]["col_first_n_per_k"]
+    assert ev[:, :m.n].tolist() == g["ell"]["val_first_n_per_k"]
+    assert np.all(ec[:, m.n:] == -1) and np.all(ev[:, m.n:] == 0.0)
+    assert not np.any(np.signbit(ev[ec < 0]))  # padding is +0.0
+
+
+def test_sellp_golden_layout():
+    g, m = _golden_layout()
+    sl, ss, sc, sv = oracle.csr_to_sellp(m, S=2, f=2)
+    gs = g["sellp_S2_f2"]
+    assert sl.tolist() == gs["slice_lengths"] and ss.tolist() == gs["slice_sets"]
+    assert sc.tolist() == gs["col"] and sv.tolist() == gs["val"]
+
+
+@pytest.mark.parametrize("S,f", [(32, 1), (8, 2), (16, 4), (64, 1), (1, 1)])
+def test_round_trips(S, f):
+    for m in (W.random_csr(70, 90, 0.1, 11, empty_rows=9, full_rows=1),
+              W.power_law(3000, seed=5), W.laplacian_2d(9, 5)):
+        sl, ss, sc, sv = oracle.csr_to_sellp(m, S, f)
+        assert np.all(sl % f == 0)
+        rp, ci, va = oracle.sellp_to_csr(m.n, S, sl, ss, sc, sv)
+        assert np.array_equal(rp, m.row_ptr) and np.array_equal(ci, m.col_idx)
+        assert np.array_equal(va, m.values)
+        K, st, ec, ev = oracle.csr_to_ell(m)
+        assert K == int(m.row_lengths().max())
+        rp, ci, va = oracle.ell_to_csr(m.n, K, st, ec, ev)
+        assert np.array_equal(rp, m.row_ptr) and np.array_equal(ci, m.col_idx)
+        assert np.array_equal(va, m.values)
+
+
+# --------------------------------------------------------------- Jacobi
+
+def test_jacobi_values_and_errors():
+    m = W.diffusion_3d(6)
+    d = oracle.jacobi(m)
+    assert np.allclose(d * np.diag(m.to_dense()), 1.0, rtol=0, atol=1e-15)
+    bad = _csr(2, 2, [0, 1, 2], [0, 1], [1.0, 0.0])
+    with pytest.raises(ZeroDivisionError):
+        oracle.jacobi(bad)
+    missing = _csr(2, 2, [0, 1, 2], [0, 0], [1.0, 3.0])
+    with pytest.raises(ZeroDivisionError):
+        oracle.jacobi(missing)
+
+
+# --------------------------------------------------------------- solvers
+
+def _spd_dense_csr(n, cond, seed):
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.geomspace(1.0, cond, n)
+    a = (q * ev) @ q.T
+    a = 0.5 * (a + a.T)
+    rp = np.arange(0, n * n + 1, n)
+    ci = np.tile(np.arange(n), n)
+    return _csr(n, n, rp, ci, a.reshape(-1)), a
+
+
+def _dense_csr(a):
+    n = a.shape[0]
+    rp = np.arange(0, n * n + 1, n)
+    ci = np.tile(np.arange(n), n)
+    return _csr(n, n, rp, ci, a.reshape(-1))
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_cg_matches_lapack(precond):
+    m = W.shifted_rectangle(11, 13, 0.3)
+    b = W.uniform_vector(m.n, 1)
+    x, info = oracle.solve(m, b, method=oracle.CG, precond=precond, tol=1e-12)
+    xs = np.linalg.solve(m.to_dense(), b)
+    assert info["status"] == oracle.OK
+    kappa = np.linalg.cond(m.to_dense())
+    assert np.linalg.norm(x - xs) <= kappa * 1e-12 * np.linalg.norm(xs) * 2
+    assert oracle.true_rel_residual(m, b, x) <= 1e-12
+
+
+@pytest.mark.parametrize("n,seed", [(5, 1), (12, 2), (16, 3)])
+def test_cg_exact_termination(n, seed):
+    """CG on an n x n SPD system terminates in n steps in exact arithmetic;
+    with kappa = 10 rounding costs at most two more."""
+    m, a = _spd_dense_csr(n, 10.0, seed)
+    b = np.random.default_rng(seed).standard_normal(n)
+    x, info = oracle.solve(m, b, method=oracle.CG, tol=1e-12, max_iters=n + 2)
+    assert info["status"] == oracle.OK and info["iters"] <= n + 2
+
+
+def test_cg_eigenvector_rhs_one_iteration():
+    N = 20
+    m = W.laplacian_1d(N)
+    i = np.arange(1, N + 1)
+    b = np.sin(i * 3 * math.pi / (N + 1))
+    x, info = oracle.solve(m, b, method=oracle.CG, tol=1e-12)
+    assert info["status"] == oracle.OK and info["iters"] == 1
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_cg_k_distinct_eigenvalues(k):
+    n = 40
+    vals = np.repeat(np.arange(1.0, k + 1.0), n // k + 1)[:n] * 1.7
+    m = _csr(n, n, np.arange(n + 1), np.arange(n), vals)
+    b = np.random.default_rng(k).standard_normal(n)
+    x, info = oracle.solve(m, b, method=oracle.CG, tol=1e-12)
+    assert info["status"] == oracle.OK and info["iters"] <= k + 1
+
+
+def test_jacobi_cg_diagonal_one_iteration():
+    n = 30
+    vals = np.linspace(0.5, 50.0, n)
+    m = _csr(n, n, np.arange(n + 1), np.arange(n), vals)
+    b = np.random.default_rng(2).standard_normal(n)
+    x, info = oracle.solve(m, b, method=oracle.CG, precond=1, tol=1e-13)
+    assert info["status"] == oracle.OK and info["iters"] == 1
+    assert np.allclose(x, b / vals, rtol=1e-15, atol=0)
+
+
+def test_cg_breakdown_on_negative_definite():
+    n = 5
+    m = _csr(n, n, np.arange(n + 1), np.arange(n), -np.ones(n))
+    _, info = oracle.solve(m, np.ones(n), method=oracle.CG)
+    assert info["status"] == oracle.BREAKDOWN
+
+
+@pytest.mark.parametrize("method", [oracle.CG, oracle.BICGSTAB, oracle.GMRES])
+def test_zero_rhs_returns_zero(method):
+    m = W.laplacian_2d(5)
+    x, info = oracle.solve(m, np.zeros(m.n), x0=np.ones(m.n), method=method)
+    assert info["status"] == oracle.OK and info["iters"] == 0 and np.all(x == 0)
+
+
+def test_cg_config1_iteration_bound_and_residuals():
+    """64x64 5-point Laplacian: kappa from the closed-form extreme
+    eigenvalues gives the CG A-norm bound 2((sqrt k - 1)/(sqrt k + 1))^it."""
+    N = 64
+    m = W.laplacian_2d(N)
+    b = W.uniform_vector(m.n, W.SEED_BASE + 1)
+    x, info, hist = oracle.solve(m, b, method=oracle.CG, tol=1e-10, max_iters=2000,
+                                 history=True)
+    lmin = 8 * math.sin(math.pi / (2 * (N + 1))) ** 2
+    lmax = 8 * math.sin(N * math.pi / (2 * (N + 1))) ** 2
+    kappa = lmax / lmin
+    q = (math.sqrt(kappa) - 1) / (math.sqrt(kappa) + 1)
+    bound = math.ceil(math.log(1e-10 / 2) / math.log(q))
+    assert info["status"] == oracle.OK
+    assert info["iters"] <= bound + 80
+    assert info["rel_res_true"] <= 1e-10
+    # recurrence residual tracks the recomputed true residual
+    assert abs(info["rel_res_true"] - info["rel_res_rec"]) <= 1e-12
+
+
+def test_residual_replacement_restart_reaches_tol():
+    """A tolerance near the rounding floor: the recurrence residual keeps
+    falling while the true one stalls; the replacement restart must still
+    return only with the true residual passing, or report non-convergence."""
+    m = W.diffusion_3d(8, sigma=2.0, seed=9)
+    b = W.uniform_vector(m.n, 9)
+    x, info = oracle.solve(m, b, method=oracle.CG, tol=1e-15, max_iters=3000)
+    if info["status"] == oracle.OK:
+        assert oracle.true_rel_residual(m, b, x) <= 1e-15 * 1.0001
+    else:
+        assert info["status"] == oracle.NOT_CONVERGED
+
+
+def _convdiff_1d(n, peclet):
+    """Upwind-free central 1D convection-diffusion: nonsymmetric tridiagonal."""
+    lo, di, up = -1.0 - peclet, 2.0, -1.0 + peclet
+    rp = [0]
+    ci, va = [], []
+    for i in range(n):
+        if i > 0:
+            ci.append(i - 1); va.append(lo)
+        ci.append(i); va.append(di)
+        if i < n - 1:
+            ci.append(i + 1); va.append(up)
+        rp.append(len(ci))
+    return _csr(n, n, rp, ci, va)
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_bicgstab_matches_lapack(precond):
+    m = _convdiff_1d(60, 0.4)
+    b = np.random.default_rng(4).standard_normal(m.n)
+    x, info = oracle.solve(m, b, method=oracle.BICGSTAB, precond=precond, tol=1e-12,
+                           max_iters=500)
+    xs = np.linalg.solve(m.to_dense(), b)
+    assert info["status"] == oracle.OK
+    kappa = np.linalg.cond(m.to_dense())
+    assert np.linalg.norm(x - xs) <= 2 * kappa * 1e-12 * np.linalg.norm(xs)
+    assert oracle.true_rel_residual(m, b, x) <= 1e-12
+
+
+@pytest.mark.parametrize("n,seed", [(10, 1), (25, 2), (30, 3)])
+def test_full_gmres_terminates_in_n_steps(n, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((n, n)) + n * 0.3 * np.eye(n)
+    m = _dense_csr(a)
+    b = rng.standard_normal(n)
+    x, info, hist = oracle.solve(m, b, method=oracle.GMRES, krylov_dim=n, tol=1e-11,
+                                 max_iters=n, history=True)
+    assert info["status"] == oracle.OK and info["iters"] <= n
+    h = hist[1:info["iters"] + 1]
+    assert np.all(np.diff(h) <= 1e-15 * np.abs(h[:-1]) + 1e-300)  # non-increasing
+    xs = np.linalg.solve(a, b)
+    assert np.linalg.norm(x - xs) <= np.linalg.cond(a) * 1e-10 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_restarted_gmres_matches_lapack(precond):
+    m = _convdiff_1d(80, 0.3)
+    b = np.random.default_rng(8).standard_normal(m.n)
+    x, info = oracle.solve(m, b, method=oracle.GMRES, precond=precond, krylov_dim=10,
+                           tol=1e-11, max_iters=5000)
+    assert info["status"] == oracle.OK and info["restarts"] >= 1
+    xs = np.linalg.solve(m.to_dense(), b)
+    assert np.linalg.norm(x - xs) <= 2 * np.linalg.cond(m.to_dense()) * 1e-11 * np.linalg.norm(xs)
+    assert oracle.true_rel_residual(m, b, x) <= 1e-11
+
+
+def test_gmres_givens_estimate_equals_true_residual_in_cycle():
+    """Inside a cycle, |g_{k+1}| equals ||b - A x_k|| in exact arithmetic;
+    with full GMRES on a well-conditioned system they agree to rounding."""
+    n = 20
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal((n, n)) + 2 * math.sqrt(n) * np.eye(n)
+    m = _dense_csr(a)
+    b = rng.standard_normal(n)
+    for steps in (3, 7, 12):
+        x, info = oracle.solve(m, b, method=oracle.GMRES, krylov_dim=n, tol=1e-30,
+                               max_iters=steps)
+        assert info["iters"] == steps
+        true = np.linalg.norm(b - a @ x) / np.linalg.norm(b)
+        assert abs(info["rel_res_rec"] - true) <= 1e-12
+
+
+def test_solvers_jacobi_on_diffusion_reach_tol():
+    m = W.diffusion_3d(10)
+    b = W.uniform_vector(m.n, 3)
+    for method in (oracle.CG, oracle.BICGSTAB, oracle.GMRES):
+        x, info = oracle.solve(m, b, method=method, precond=1, tol=1e-10, max_iters=5000)
+        assert info["status"] == oracle.OK, (method, info)
+        assert oracle.true_rel_residual(m, b, x) <= 1e-10
