@@ -1,0 +1,378 @@
+"""Benchmark: SpMV sweep over CSR / ELL / SELL-P, FP64 and FP32, on the 3D
+7-point Laplacian 256^3 and the Zipf(1.8) power-law matrix with 2^22 rows
+(the paper's SpMV benchmark x = A b with random b, Section 5.1, on
+synthetic stand-ins for its SuiteSparse set), plus CG solves/s on the 64x64
+5-point Laplacian to a 1e-10 relative residual.
+
+One step = one apply of every (matrix, format, dtype) item of the sweep.
+value = algorithmic bytes of all items / device time (GB/s); algorithmic
+bytes per item = nnz*(value+index bytes) + 4*(n+1) [CSR] + x and y once.
+Matrices (0.9-1.7 GB each) are larger than L2, so no flush is needed.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "SpMV GB/s & %HBM peak; CG solves/s at 1e-10 residual; serving p50/p99 latency"
+WORKLOAD = ("SpMV sweep {CSR, ELL, SELL-P(S=32)} x {FP64, FP32}: 3D 7-point Laplacian 256^3 "
+            "(n=16,777,216, nnz=117,047,296) and Zipf(1.8) power-law n=4,194,304 (mean 16, "
+            "max 4096; ELL skipped: ~206 GB padded); int32 indices; x ~ U[-1,1]")
+FALLBACK_HBM = 6800.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+def alg_bytes(m, sv, fmt):
+    """Algorithmic bytes of one SpMV: unpadded matrix, x and y once."""
+    b = m.nnz * (sv + 4) + m.n * sv + m.ncols * sv
+    if fmt == "csr":
+        b += 4 * (m.n + 1)
+    return int(b)
+
+
+def build_items(gk, W, dtypes=("f64", "f32")):
+    """Returns the sweep items (matrix handles + metadata)."""
+    items = []
+    lap = W.laplacian_3d(256)
+    pl = W.power_law(1 << 22, seed=W.SEED_BASE + 2)
+    for m, tag, fmts in ((lap, "lap3d_256", ("csr", "ell", "sellp")),
+                         (pl, "powerlaw_4M", ("csr", "sellp"))):
+        for dt in dtypes:
+            sv = 8 if dt == "f64" else 4
+            A = gk.Matrix.from_csr(m, dt)
+            for fmt in fmts:
+                H = A if fmt == "csr" else A.convert(fmt, None, 32, 1)
+                items.append({"name": f"{tag}/{fmt}/{dt}", "mat": H, "dtype": dt, "fmt": fmt,
+                              "n": m.n, "ncols": m.ncols, "nnz": m.nnz,
+                              "bytes": alg_bytes(m, sv, fmt),
+                              "kernel": H.desc["spmv_kernel"],
+                              "launches": H.desc["spmv_launches"]})
+    return items, lap, pl
+
+
+KERNEL_NAMES = {0: "k_csr_vector", 1: "k_csr_rowtile", 2: "k_csr_merge", 3: "k_ell", 4: "k_sellp"}
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        reasons = set()
+        for s in self.samples:
+            for i, nm in enumerate(names):
+                if s[3 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def kernel_src_hash():
+    h = hashlib.sha256()
+    for f in ("spmv.cuh", "prims.cuh", "gk_internal.cuh", "apply.cu"):
+        with open(os.path.join(ROOT, "paper_2510_08230_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel_name, item_name):
+    """DRAM bytes per launch from a committed ncu capture, if the kernel
+    sources are unchanged since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(item_name)
+    if not e or e.get("kernel") != kernel_name or e.get("src_hash") != kernel_src_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(lap, seconds=12.0):
+    """The oracle's row-parallel FP64 CSR SpMV on the host cores, on the
+    256^3 Laplacian, repeated for about `seconds`."""
+    import oracle
+    rp = np.ascontiguousarray(lap.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(lap.col_idx, dtype=np.int32)
+    va = np.ascontiguousarray(lap.values, dtype=np.float64)
+    x = np.random.default_rng(1).uniform(-1, 1, lap.n)
+    y = np.zeros(lap.n)
+    oracle.spmv_omp(lap, x, 0, y=y, arrays=(rp, ci, va))  # warm-up
+    reps, t0 = 0, time.perf_counter()
+    threads = 0
+    while True:
+        _, threads = oracle.spmv_omp(lap, x, 0, y=y, arrays=(rp, ci, va))
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or reps >= 200:
+            break
+    gbs = alg_bytes(lap, 8, "csr") * reps / el / 1e9
+    return {"value": round(gbs, 2), "unit": "GB/s", "cores": int(threads), "kind": "oracle",
+            "sample": f"{reps} x FP64 CSR SpMV of the 3D 7-point 256^3 Laplacian (row-parallel "
+                      f"OpenMP oracle, plain sum), {el:.1f} s"}
+
+
+def cg_solves_per_s(gk, W, torch, dev, reps=20):
+    m = W.laplacian_2d(64)
+    b = torch.from_numpy(W.uniform_vector(m.n, W.SEED_BASE + 1)).to(dev)
+    A = gk.Matrix.from_csr(m)
+    x = torch.zeros_like(b)
+    out = {}
+    for engine in (1, 2):
+        A.solve(b, x, method="cg", tol=1e-10, max_iters=5000, engine=engine)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        iters = 0
+        for _ in range(reps):
+            x.zero_()
+            info = A.solve(b, x, method="cg", tol=1e-10, max_iters=5000, engine=engine)
+            assert info["return"] == gk.GK_OK, info
+            iters = info["iters"]
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        out["multi_kernel" if engine == 1 else "single_block"] = {
+            "solves_per_s": round(reps / el, 1), "iters": iters,
+            "rel_res_true": info["rel_res_true"]}
+    A.close()
+    best = max(out.values(), key=lambda v: v["solves_per_s"])
+    return {"solves_per_s": best["solves_per_s"], "workload": "2D 5-point 64x64 FP64 CG to 1e-10, "
+            "b ~ U[-1,1] seed 2511, x0 = 0 (host wall clock per solve incl. launch)",
+            "engines": out}
+
+
+def run_reference(args):
+    """The oracle on the host cores, same metric and unit."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2510_08230_gb300 import workloads as W
+    import oracle
+    lap = W.laplacian_3d(256)
+    rp = np.ascontiguousarray(lap.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(lap.col_idx, dtype=np.int32)
+    va = np.ascontiguousarray(lap.values, dtype=np.float64)
+    x = np.random.default_rng(1).uniform(-1, 1, lap.n)
+    y = np.zeros(lap.n)
+    nb = alg_bytes(lap, 8, "csr")
+    for _ in range(args.warmup):
+        oracle.spmv_omp(lap, x, 0, y=y, arrays=(rp, ci, va))
+    t0 = time.perf_counter()
+    threads = 0
+    for _ in range(args.steps):
+        _, threads = oracle.spmv_omp(lap, x, 0, y=y, arrays=(rp, ci, va))
+    el = time.perf_counter() - t0
+    gbs = nb * args.steps / el / 1e9
+    sample = (f"each step = 1 FP64 CSR SpMV of the 3D 7-point 256^3 Laplacian by the oracle "
+              f"(row-parallel OpenMP, {threads} threads); FP32 / ELL / SELL-P / power-law items "
+              f"of the GPU sweep are not run by the oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(el * 1000 / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference_sample": sample},
+            "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gk", choices=["gk", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cg", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import __graft_entry__
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    __graft_entry__.build()
+    import paper_2510_08230_gb300 as gk
+    from paper_2510_08230_gb300 import workloads as W
+
+    items, lap, pl = build_items(gk, W)
+    rng = np.random.default_rng(W.SEED_BASE + 2)
+    for it in items:
+        vt = torch.float64 if it["dtype"] == "f64" else torch.float32
+        it["x"] = torch.from_numpy(rng.uniform(-1, 1, it["ncols"])).to(dev, vt)
+        it["y"] = torch.empty(it["n"], dtype=vt, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(events=None):
+        for k, it in enumerate(items):
+            if events is not None:
+                events[k][0].record(stream)
+            it["mat"].apply(it["x"], it["y"], stream)
+            if events is not None:
+                events[k][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in items] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(evs[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    per_item_ms = [statistics.mean(evs[s][k][0].elapsed_time(evs[s][k][1])
+                                   for s in range(args.steps)) for k in range(len(items))]
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    step_bytes = sum(it["bytes"] for it in items)
+    value = step_bytes * args.steps * world / (total_ms / 1000.0) / 1e9
+    peak, peak_kind = _peaks()
+    sweep = []
+    for it, ms in zip(items, per_item_ms):
+        gbs = it["bytes"] / (ms / 1000.0) / 1e9
+        sweep.append({"item": it["name"], "kernel": KERNEL_NAMES[it["kernel"]],
+                      "us": round(ms * 1000, 1), "GB_s": round(gbs, 1),
+                      "frac_of_measured_hbm": round(gbs / peak, 3),
+                      "frac_of_8TBs_nominal": round(gbs / 8000.0, 3)})
+    # dominant kernel: largest share of the step's device time
+    k_dom = max(range(len(items)), key=lambda k: per_item_ms[k])
+    dom = items[k_dom]
+    dom_gbs = dom["bytes"] / (per_item_ms[k_dom] / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(dom_gbs, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(dom_gbs / peak, 3),
+                "traffic": traffic_for(KERNEL_NAMES[dom["kernel"]], dom["name"]),
+                "kernel": KERNEL_NAMES[dom["kernel"]], "item": dom["name"],
+                "peak_source": f"{peak_kind} HBM copy bandwidth",
+                "algorithmic_bytes_per_launch": dom["bytes"]}
+    headline = next(s for s in sweep if s["item"] == "lap3d_256/csr/f64")
+
+    # e2e: same sweep through the C ABI with pinned HOST buffers (H2D of x,
+    # kernel, D2H of y inside the timed region, every step)
+    hx = [torch.from_numpy(it["x"].cpu().numpy()).pin_memory() for it in items]
+    hy = [torch.empty(it["n"], dtype=it["y"].dtype).pin_memory() for it in items]
+
+    def e2e_step():
+        for it, a, b in zip(items, hx, hy):
+            it["mat"].apply(a, b, stream)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(a.numel() * a.element_size() for a in hx)
+    d2h = sum(b.numel() * b.element_size() for b in hy)
+    e2e = {"value": round(step_bytes * args.steps * world / e2e_s / 1e9, 1), "unit": "GB/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "how": "gk_apply with pinned host x and y (library-staged copies), host wall clock"}
+
+    cg = None
+    if not args.no_cg and rank == 0:
+        cg = cg_solves_per_s(gk, W, torch, dev)
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0 and world == 1:
+        cpu = cpu_baseline(lap)
+    launches = sum(it["launches"] for it in items) * args.steps
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "spmv_lap3d_csr_f64": headline,
+            "sweep": sweep, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "cg": cg, "clocks": clk, "gpu_launches": launches}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

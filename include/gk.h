@@ -1,0 +1,235 @@
+/*
+ * gk.h - C ABI of the GB300 sparse operator library.
+ *
+ * The calls follow the paper's linear-operator model (Section 3.4,
+ * "Ginkgo's Linear Operator Abstraction"): a matrix is created once, then
+ * "applied" to a vector (an SpMV), and a solver is "applied" to a
+ * right-hand side b and an initial guess x, which it overwrites with the
+ * solution (Section 2.3 "pyGinkgo API", Listing 1).  Stopping follows the
+ * config solver's criteria (Listing 2): an iteration cap or a residual
+ * reduction relative to ||b||_2.
+ *
+ * General rules for every call:
+ *  - Return value: a gk_status.  No call aborts or throws; on an error the
+ *    outputs are left unspecified unless stated otherwise.
+ *  - Memory: a gk_matrix owns device copies of its arrays; the caller keeps
+ *    its own inputs.  Vector pointers are borrowed for the duration of the
+ *    call only.  Indices are int32, zero-based.
+ *  - Value types: GK_F64 uses double for values, vectors and scalars;
+ *    GK_F32 uses float; GK_BF16 stores matrix values as bfloat16 and uses
+ *    float vectors with float accumulation.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *    Device-pointer calls are stream-ordered and return without waiting,
+ *    unless documented otherwise.  Calls given host pointers copy through
+ *    library-owned device buffers and return after the result is back on
+ *    the host.
+ *  - One GPU: a matrix lives on the device that was current when it was
+ *    created; every later call on it must run with that device current.
+ *  - Thread safety: calls on different matrices may run concurrently from
+ *    different host threads; calls on the same matrix must be serialised
+ *    by the caller (the handle caches workspace and solver state).
+ */
+#ifndef GK_H
+#define GK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GK_VERSION 1
+
+typedef struct gk_matrix_s* gk_matrix;
+
+typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2 } gk_dtype;
+
+/* Storage formats.
+ * GK_CSR  : row_ptr[n+1], col_idx[nnz], values[nnz]; columns ascending
+ *           within a row is NOT required for SpMV.
+ * GK_ELL  : K = longest row, stride = n rounded up to 32; entry j of row i
+ *           at j*stride + i; padding col = -1, value = +0.0.
+ * GK_SELLP: slices of S consecutive rows; slice_lengths[s] = longest row
+ *           of slice s rounded up to a multiple of the stride factor f;
+ *           slice_sets = exclusive prefix sum of slice_lengths
+ *           (num_slices + 1 entries); entry j of row i = s*S + t at
+ *           (slice_sets[s] + j)*S + t; padding col = -1, value = +0.0,
+ *           including the virtual rows past n in the last slice.
+ * The paper names "other matrix formats" beside CSR and COO (Section 2)
+ * without defining them; these layouts are this library's definition. */
+typedef enum { GK_CSR = 0, GK_ELL = 1, GK_SELLP = 2 } gk_format;
+
+typedef enum { GK_CG = 0, GK_BICGSTAB = 1, GK_GMRES = 2 } gk_method;
+typedef enum { GK_PRECOND_NONE = 0, GK_PRECOND_JACOBI = 1 } gk_precond;
+typedef enum { GK_MEM_HOST = 0, GK_MEM_DEVICE = 1 } gk_memory;
+
+typedef enum {
+    GK_OK = 0,
+    GK_NOT_CONVERGED = 1,  /* iteration cap reached; x holds the last iterate */
+    GK_BREAKDOWN = 2,      /* CG: <p,Ap> <= 0; BiCGSTAB: rho, <rhat,v>, omega = 0;
+                              GMRES: zero Givens denominator */
+    GK_ERR_INVALID = -1,   /* bad argument or malformed matrix */
+    GK_ERR_OOM = -2,       /* device allocation failed */
+    GK_ERR_CUDA = -3,      /* a CUDA runtime call failed */
+    GK_ERR_TIMEOUT = -4,   /* a bounded device-side wait ran out */
+    GK_ERR_ZERO_DIAG = -5, /* Jacobi: missing or zero diagonal entry */
+    GK_ERR_NAN = -6,       /* NaN or Inf met in a residual norm */
+    GK_ERR_UNSUPPORTED = -7 /* combination not provided (e.g. wrong device) */
+} gk_status;
+
+/* Shape and layout of a matrix handle (all counts in entries). */
+typedef struct {
+    int32_t n;             /* rows */
+    int32_t ncols;         /* columns */
+    int64_t nnz;           /* stored nonzeros, padding excluded */
+    gk_format format;
+    gk_dtype dtype;
+    int32_t max_row;       /* longest row */
+    int32_t ell_width;     /* ELL: K */
+    int64_t ell_stride;    /* ELL: stride */
+    int32_t slice_size;    /* SELL-P: S */
+    int32_t stride_factor; /* SELL-P: f */
+    int32_t num_slices;    /* SELL-P: ceil(n / S) */
+    int64_t stored;        /* entries held in col/values incl. padding */
+    int64_t device_bytes;  /* bytes of the format arrays on the device */
+    int32_t spmv_kernel;   /* SpMV kernel apply uses: 0 CSR vector, 1 CSR row-tile,
+                              2 CSR merge-path, 3 ELL, 4 SELL-P */
+    int32_t spmv_launches; /* kernel launches per apply */
+} gk_matrix_desc;
+
+/* ---------------------------------------------------------------------
+ * Matrix creation and conversion
+ * ------------------------------------------------------------------- */
+
+/* Create a CSR matrix (the paper's default format: `format="Csr"` in
+ * Listing 1).  row_ptr has n+1 entries, col_idx and values nnz entries;
+ * `values` holds double (GK_F64), float (GK_F32) or uint16 bfloat16 bits
+ * (GK_BF16).  `mem` says whether the three arrays are host or device
+ * pointers; they are copied, the caller keeps ownership.  The copy is
+ * validated on the device: row_ptr[0] = 0, non-decreasing, row_ptr[n] =
+ * nnz, 0 <= col < ncols; otherwise GK_ERR_INVALID.  n = 0 and nnz = 0 are
+ * valid.  Synchronises `stream`. */
+gk_status gk_matrix_create_csr(int32_t n, int32_t ncols, int64_t nnz,
+                               const int32_t* row_ptr, const int32_t* col_idx,
+                               const void* values, gk_dtype dtype,
+                               gk_memory mem, void* stream, gk_matrix* out);
+
+/* Create a CSR matrix from COO triplets (COO is the paper's second
+ * benchmarked format, Section 5).  Entries may come in any order; they are
+ * ordered by (row, col) on the device, entries with equal (row, col) are
+ * summed in their input order (float arithmetic for GK_F32/GK_BF16 input,
+ * double for GK_F64), explicit zeros are kept.  Result is bit-for-bit the
+ * same for any thread schedule.  Index out of range: GK_ERR_INVALID.
+ * GK_BF16 values are summed as float and rounded to bfloat16 once.
+ * Synchronises `stream`. */
+gk_status gk_matrix_create_coo(int32_t n, int32_t ncols, int64_t nnz,
+                               const int32_t* row, const int32_t* col,
+                               const void* values, gk_dtype dtype,
+                               gk_memory mem, void* stream, gk_matrix* out);
+
+/* New handle holding A in format `fmt` with value type `dtype` (values
+ * rounded to nearest even when narrowing; no arithmetic otherwise).
+ * slice_size (S, 1..1024) and stride_factor (f >= 1) apply to GK_SELLP;
+ * pass 0 for the defaults S = 32, f = 1.  A is unchanged.  Converting to
+ * GK_CSR from any format is allowed.  Synchronises `stream`. */
+gk_status gk_matrix_convert(gk_matrix A, gk_format fmt, gk_dtype dtype,
+                            int32_t slice_size, int32_t stride_factor,
+                            void* stream, gk_matrix* out);
+
+gk_status gk_matrix_describe(gk_matrix A, gk_matrix_desc* out);
+
+/* Copy the format arrays to caller-owned HOST buffers (any pointer may be
+ * NULL to skip that array):
+ *   CSR  : idx_a = row_ptr[n+1], col = col_idx[nnz], values[nnz]
+ *   ELL  : col[K*stride], values[K*stride]              (idx_a, sets unused)
+ *   SELLP: idx_a = slice_lengths[num_slices], sets = slice_sets[num_slices+1],
+ *          col[stored], values[stored]
+ * values are in the matrix dtype (bfloat16 as uint16 bits).  Blocking. */
+gk_status gk_matrix_export(gk_matrix A, int32_t* idx_a, int64_t* sets,
+                           int32_t* col, void* values);
+
+/* Frees the handle and everything it owns (after a device synchronise). */
+gk_status gk_matrix_destroy(gk_matrix A);
+
+/* ---------------------------------------------------------------------
+ * Apply (SpMV)
+ * ------------------------------------------------------------------- */
+
+/* x = A b  (a matrix LinOp's apply, Section 3.4; the paper's SpMV
+ * benchmark computes x = A b, Section 5.1).  b has ncols entries, x has n.
+ * Both device pointers (stream-ordered, asynchronous) or both host
+ * pointers (staged, blocking).  b and x must not overlap. */
+gk_status gk_apply(gk_matrix A, const void* b, void* x, void* stream);
+
+/* x = alpha * A b + beta * x  (the advanced apply).  When beta == 0, x is
+ * not read, so NaN/Inf already in x does not propagate.  alpha and beta
+ * are rounded to the vector type. */
+gk_status gk_apply_adv(gk_matrix A, double alpha, const void* b, double beta,
+                       void* x, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Solve
+ * ------------------------------------------------------------------- */
+
+typedef struct {
+    gk_method method;
+    gk_precond precond;   /* Jacobi with block size 1 (Listing 2) */
+    double tol;           /* stop when ||b - A x||_2 <= tol * ||b||_2 */
+    int32_t max_iters;    /* CG/BiCGSTAB iterations; GMRES Arnoldi steps (all cycles) */
+    int32_t krylov_dim;   /* GMRES restart length m (0 = 30, the paper's value); <= 64 */
+    int32_t mixed;        /* 0: plain; 1: FP32 inner solves in FP64 iterative
+                             refinement; 2: BF16-stored FP32 inner solves */
+    double inner_tol;     /* refinement: inner reduction (0 = 1e-4) */
+    int32_t max_outer;    /* refinement: outer cap (0 = 50) */
+    int32_t engine;       /* 0 automatic, 1 multi-kernel (any n),
+                             2 single-block (n <= 16384) */
+} gk_solve_opts;
+
+typedef struct {
+    gk_status status;
+    int32_t iters;            /* iterations (refinement: inner, summed) */
+    int32_t restarts;         /* GMRES restarts; CG/BiCGSTAB residual replacements */
+    int32_t outer_iters;      /* refinement steps (0 without refinement) */
+    double rel_res_recurrence;/* last recurrence / Givens estimate over ||b|| */
+    double rel_res_true;      /* ||b - A x||_2 / ||b||_2 recomputed at exit */
+    float device_ms;          /* device time of the solve (CUDA events) */
+} gk_solve_info;
+
+/* Solve A x = b for square A (Listing 1: solver.apply(b, x) overwrites
+ * the initial guess).  CG (Hestenes-Stiefel), BiCGSTAB (van der Vorst,
+ * right-preconditioned) or GMRES(m) (right-preconditioned, Givens
+ * rotations, residual estimate checked after every Arnoldi step as in
+ * Section 5.2.1).  GK_OK is returned only when the recomputed true
+ * residual meets tol; when the recurrence residual passes but the true
+ * one does not, the residual is replaced by the true one and the method
+ * restarts from x.  b = 0 gives x = 0 and GK_OK after 0 iterations.
+ * b, x: device pointers of n entries (x in/out, the initial guess).
+ * info may be NULL.  Blocks until the solve is finished (one stream
+ * synchronise); everything is enqueued on `stream`. */
+gk_status gk_solve(gk_matrix A, const void* b, void* x,
+                   const gk_solve_opts* opts, gk_solve_info* info,
+                   void* stream);
+
+/* Solve `count` independent systems As[i] x_i = b_i in one launch, one
+ * thread block per system, whole iteration inside the kernel.  All
+ * matrices must be CSR, square, of the same dtype, with n <= 16384; CG
+ * and BiCGSTAB (GMRES: GK_ERR_UNSUPPORTED).  infos has count entries
+ * (may be NULL).  bs / xs: arrays of device pointers (host arrays of
+ * pointers).  Blocking. */
+gk_status gk_solve_batched(int32_t count, const gk_matrix* As,
+                           const void* const* bs, void* const* xs,
+                           const gk_solve_opts* opts, gk_solve_info* infos,
+                           void* stream);
+
+/* Static English text for a status code. */
+const char* gk_status_string(gk_status s);
+
+/* GK_VERSION of the built library. */
+int32_t gk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GK_H */

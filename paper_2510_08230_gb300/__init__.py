@@ -1,0 +1,380 @@
+"""GB300 sparse operators: SpMV (CSR, ELL, SELL-P), COO->CSR and
+CSR->ELL/SELL-P conversion, and CG / BiCGSTAB / GMRES(m) with a Jacobi
+preconditioner, behind the C ABI declared in include/gk.h.
+
+This module is a thin ctypes binding: the functions carry the C names and
+only marshal arguments (torch tensors or numpy arrays to raw pointers,
+enums to ints, structs to dicts).  Every step of the computation runs in
+libgk.so; there is no CPU fallback, and importing fails loudly when the
+library has not been built (``python -c "import __graft_entry__ as g;
+g.build()"``).
+
+Arrays may be CUDA torch tensors (device pointers) or host arrays (numpy or
+CPU torch tensors).  The ``Matrix`` class wraps a handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgk.so")
+
+GK_F64, GK_F32, GK_BF16 = 0, 1, 2
+GK_CSR, GK_ELL, GK_SELLP = 0, 1, 2
+GK_CG, GK_BICGSTAB, GK_GMRES = 0, 1, 2
+GK_PRECOND_NONE, GK_PRECOND_JACOBI = 0, 1
+GK_MEM_HOST, GK_MEM_DEVICE = 0, 1
+GK_OK, GK_NOT_CONVERGED, GK_BREAKDOWN = 0, 1, 2
+GK_ERR_INVALID, GK_ERR_OOM, GK_ERR_CUDA, GK_ERR_TIMEOUT = -1, -2, -3, -4
+GK_ERR_ZERO_DIAG, GK_ERR_NAN, GK_ERR_UNSUPPORTED = -5, -6, -7
+
+DTYPES = {"f64": GK_F64, "f32": GK_F32, "bf16": GK_BF16}
+FORMATS = {"csr": GK_CSR, "ell": GK_ELL, "sellp": GK_SELLP}
+METHODS = {"cg": GK_CG, "bicgstab": GK_BICGSTAB, "gmres": GK_GMRES}
+
+EXPORTED = [
+    "gk_matrix_create_csr", "gk_matrix_create_coo", "gk_matrix_convert",
+    "gk_matrix_describe", "gk_matrix_export", "gk_matrix_destroy", "gk_apply",
+    "gk_apply_adv", "gk_solve", "gk_solve_batched", "gk_status_string", "gk_version",
+]
+
+
+class GkError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {status} ({_status_text(status)})")
+
+
+class gk_matrix_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("ncols", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("format", ctypes.c_int), ("dtype", ctypes.c_int), ("max_row", ctypes.c_int32),
+                ("ell_width", ctypes.c_int32), ("ell_stride", ctypes.c_int64),
+                ("slice_size", ctypes.c_int32), ("stride_factor", ctypes.c_int32),
+                ("num_slices", ctypes.c_int32), ("stored", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("spmv_kernel", ctypes.c_int32),
+                ("spmv_launches", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class gk_solve_opts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("precond", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_iters", ctypes.c_int32), ("krylov_dim", ctypes.c_int32),
+                ("mixed", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("max_outer", ctypes.c_int32), ("engine", ctypes.c_int32)]
+
+
+class gk_solve_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("outer_iters", ctypes.c_int32), ("rel_res_recurrence", ctypes.c_double),
+                ("rel_res_true", ctypes.c_double), ("device_ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libgk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "paper_2510_08230_gb300._build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        pm = ctypes.POINTER(vp)
+        L.gk_matrix_create_csr.argtypes = [i32, i32, i64, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, pm]
+        L.gk_matrix_create_coo.argtypes = [i32, i32, i64, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, pm]
+        L.gk_matrix_convert.argtypes = [vp, ctypes.c_int, ctypes.c_int, i32, i32, vp, pm]
+        L.gk_matrix_describe.argtypes = [vp, ctypes.POINTER(gk_matrix_desc)]
+        L.gk_matrix_export.argtypes = [vp, vp, vp, vp, vp]
+        L.gk_matrix_destroy.argtypes = [vp]
+        L.gk_apply.argtypes = [vp, vp, vp, vp]
+        L.gk_apply_adv.argtypes = [vp, f64, vp, f64, vp, vp]
+        L.gk_solve.argtypes = [vp, vp, vp, ctypes.POINTER(gk_solve_opts),
+                               ctypes.POINTER(gk_solve_info), vp]
+        L.gk_solve_batched.argtypes = [i32, pm, pm, pm, ctypes.POINTER(gk_solve_opts),
+                                       ctypes.POINTER(gk_solve_info), vp]
+        L.gk_status_string.argtypes = [ctypes.c_int]
+        L.gk_status_string.restype = ctypes.c_char_p
+        L.gk_version.argtypes = []
+        L.gk_version.restype = i32
+        for name in EXPORTED:
+            f = getattr(L, name)
+            if name not in ("gk_status_string", "gk_version"):
+                f.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _status_text(s):
+    try:
+        return lib().gk_status_string(int(s)).decode()
+    except Exception:
+        return "?"
+
+
+# ------------------------------------------------------------------ marshalling
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor / numpy array (None stays None)."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if _is_torch(a):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _mem(a):
+    if _is_torch(a) and a.is_cuda:
+        return GK_MEM_DEVICE
+    return GK_MEM_HOST
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover
+        pass
+    return None
+
+
+def _check(st, what):
+    if st != GK_OK:
+        raise GkError(st, what)
+
+
+def _dt(dtype):
+    return DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+
+
+# ------------------------------------------------------------------ C names
+
+def gk_matrix_create_csr(n, ncols, nnz, row_ptr, col_idx, values, dtype, mem=None, stream=None):
+    h = ctypes.c_void_p()
+    mem = _mem(row_ptr) if mem is None else mem
+    st = lib().gk_matrix_create_csr(n, ncols, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(values),
+                                    _dt(dtype), mem, _stream(stream), ctypes.byref(h))
+    _check(st, "gk_matrix_create_csr")
+    return h.value
+
+
+def gk_matrix_create_coo(n, ncols, nnz, row, col, values, dtype, mem=None, stream=None):
+    h = ctypes.c_void_p()
+    mem = _mem(row) if mem is None else mem
+    st = lib().gk_matrix_create_coo(n, ncols, nnz, _ptr(row), _ptr(col), _ptr(values), _dt(dtype),
+                                    mem, _stream(stream), ctypes.byref(h))
+    _check(st, "gk_matrix_create_coo")
+    return h.value
+
+
+def gk_matrix_convert(A, fmt, dtype, slice_size=0, stride_factor=0, stream=None):
+    h = ctypes.c_void_p()
+    fmt = FORMATS[fmt] if isinstance(fmt, str) else fmt
+    st = lib().gk_matrix_convert(A, fmt, _dt(dtype), slice_size, stride_factor, _stream(stream),
+                                 ctypes.byref(h))
+    _check(st, "gk_matrix_convert")
+    return h.value
+
+
+def gk_matrix_describe(A):
+    d = gk_matrix_desc()
+    _check(lib().gk_matrix_describe(A, ctypes.byref(d)), "gk_matrix_describe")
+    return d.as_dict()
+
+
+def gk_matrix_export(A, idx_a=None, sets=None, col=None, values=None):
+    _check(lib().gk_matrix_export(A, _ptr(idx_a), _ptr(sets), _ptr(col), _ptr(values)),
+           "gk_matrix_export")
+
+
+def gk_matrix_destroy(A):
+    _check(lib().gk_matrix_destroy(A), "gk_matrix_destroy")
+
+
+def gk_apply(A, b, x, stream=None):
+    return lib().gk_apply(A, _ptr(b), _ptr(x), _stream(stream))
+
+
+def gk_apply_adv(A, alpha, b, beta, x, stream=None):
+    return lib().gk_apply_adv(A, float(alpha), _ptr(b), float(beta), _ptr(x), _stream(stream))
+
+
+def make_opts(method="cg", precond=None, tol=1e-10, max_iters=1000, krylov_dim=30, mixed=0,
+              inner_tol=0.0, max_outer=0, engine=0):
+    m = METHODS[method] if isinstance(method, str) else int(method)
+    if precond in (None, "none", 0, False):
+        p = GK_PRECOND_NONE
+    else:
+        p = GK_PRECOND_JACOBI
+    return gk_solve_opts(m, p, tol, max_iters, krylov_dim, mixed, inner_tol, max_outer, engine)
+
+
+def gk_solve(A, b, x, opts, stream=None):
+    info = gk_solve_info()
+    st = lib().gk_solve(A, _ptr(b), _ptr(x), ctypes.byref(opts), ctypes.byref(info),
+                        _stream(stream))
+    d = info.as_dict()
+    d["return"] = st
+    return d
+
+
+def gk_solve_batched(As, bs, xs, opts, stream=None):
+    n = len(As)
+    arrA = (ctypes.c_void_p * n)(*As)
+    arrB = (ctypes.c_void_p * n)(*[_ptr(b) for b in bs])
+    arrX = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    infos = (gk_solve_info * n)()
+    st = lib().gk_solve_batched(n, arrA, arrB, arrX, ctypes.byref(opts), infos, _stream(stream))
+    return st, [i.as_dict() for i in infos]
+
+
+def gk_status_string(s):
+    return lib().gk_status_string(int(s)).decode()
+
+
+def gk_version():
+    return lib().gk_version()
+
+
+# ------------------------------------------------------------------ convenience
+
+class Matrix:
+    """Owning wrapper of a gk_matrix handle."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.desc = gk_matrix_describe(handle)
+
+    @classmethod
+    def from_csr(cls, m, dtype="f64", device=None):
+        """From a workloads.CSR (host arrays) or any object with n, ncols,
+        row_ptr, col_idx, values.  Float64 values with an F32/BF16 dtype
+        are uploaded as F64 and rounded on the device (gk_matrix_convert)."""
+        if _dt(dtype) != GK_F64 and np.asarray(m.values).dtype == np.float64:
+            A = cls.from_csr(m, "f64", device)
+            B = A.convert("csr", dtype)
+            A.close()
+            return B
+        vals = host_values(m.values, dtype)
+        rp = np.ascontiguousarray(m.row_ptr, dtype=np.int32)
+        ci = np.ascontiguousarray(m.col_idx, dtype=np.int32)
+        if device is not None:
+            import torch
+            rp, ci, vals = (torch.from_numpy(a).to(device) for a in (rp, ci, vals))
+        return cls(gk_matrix_create_csr(m.n, m.ncols, int(m.col_idx.shape[0]), rp, ci, vals,
+                                        dtype))
+
+    @classmethod
+    def from_coo(cls, n, ncols, row, col, val, dtype="f64"):
+        row = np.ascontiguousarray(row, dtype=np.int32)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        vals = host_values(val, dtype)
+        return cls(gk_matrix_create_coo(n, ncols, row.shape[0], row, col, vals, dtype))
+
+    def convert(self, fmt, dtype=None, slice_size=0, stride_factor=0):
+        dt = self.desc["dtype"] if dtype is None else _dt(dtype)
+        return Matrix(gk_matrix_convert(self.handle, fmt, dt, slice_size, stride_factor))
+
+    @property
+    def n(self):
+        return self.desc["n"]
+
+    @property
+    def nnz(self):
+        return self.desc["nnz"]
+
+    def export(self):
+        """Host copies of the format arrays (dict)."""
+        d = self.desc
+        vdt = {GK_F64: np.float64, GK_F32: np.float32, GK_BF16: np.uint16}[d["dtype"]]
+        out = {}
+        if d["format"] == GK_CSR:
+            out["row_ptr"] = np.zeros(d["n"] + 1, np.int32)
+            out["col_idx"] = np.zeros(max(d["nnz"], 1), np.int32)
+            out["values"] = np.zeros(max(d["nnz"], 1), vdt)
+            gk_matrix_export(self.handle, out["row_ptr"], None, out["col_idx"], out["values"])
+            out["col_idx"] = out["col_idx"][:d["nnz"]]
+            out["values"] = out["values"][:d["nnz"]]
+        else:
+            st = d["stored"]
+            out["col"] = np.zeros(max(st, 1), np.int32)
+            out["values"] = np.zeros(max(st, 1), vdt)
+            sl = ss = None
+            if d["format"] == GK_SELLP:
+                sl = np.zeros(max(d["num_slices"], 1), np.int32)
+                ss = np.zeros(d["num_slices"] + 1, np.int64)
+            gk_matrix_export(self.handle, sl, ss, out["col"], out["values"])
+            out["col"] = out["col"][:st]
+            out["values"] = out["values"][:st]
+            if sl is not None:
+                out["slice_lengths"] = sl[:d["num_slices"]]
+                out["slice_sets"] = ss
+        return out
+
+    def apply(self, b, x, stream=None):
+        _check(gk_apply(self.handle, b, x, stream), "gk_apply")
+
+    def apply_adv(self, alpha, b, beta, x, stream=None):
+        _check(gk_apply_adv(self.handle, alpha, b, beta, x, stream), "gk_apply_adv")
+
+    def solve(self, b, x, stream=None, **kw):
+        return gk_solve(self.handle, b, x, make_opts(**kw), stream)
+
+    def close(self):
+        if self.handle:
+            gk_matrix_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bf16_bits(a):
+    """bfloat16 bit patterns of float32 values, rounded to nearest even
+    (used to pass BF16 data through the ABI; float64 data is converted on
+    the device with gk_matrix_convert instead)."""
+    f = np.ascontiguousarray(np.asarray(a), dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    rounded = (u + np.uint64(0x7FFF) + ((u >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)
+    out = rounded.astype(np.uint16)
+    out[np.isnan(f)] = np.uint16(0x7FC0)
+    return out
+
+
+def bf16_to_float(bits):
+    return (np.asarray(bits, dtype=np.uint16).astype(np.uint32) << np.uint32(16)).view(np.float32)
+
+
+def host_values(values, dtype):
+    """Values in the ABI layout of dtype (float32 input only for F32/BF16)."""
+    dt = _dt(dtype)
+    if dt == GK_F64:
+        return np.ascontiguousarray(values, dtype=np.float64)
+    v = np.asarray(values)
+    if v.dtype != np.float32:
+        raise TypeError("F32/BF16 matrices take float32 values; convert float64 "
+                        "matrices on the device with gk_matrix_convert")
+    if dt == GK_F32:
+        return np.ascontiguousarray(v)
+    return np.ascontiguousarray(bf16_bits(v))

@@ -1,0 +1,92 @@
+// apply.cu - gk_apply / gk_apply_adv: x = alpha A b + beta x on any format
+// (the LinOp apply of Section 3.4; the paper's SpMV benchmark, Section 5.1).
+#include "spmv.cuh"
+
+namespace gk {
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename V, typename T>
+static gk_status spmv_typed(gk_matrix A, double alpha, const void* b, double beta, void* x,
+                            cudaStream_t s) {
+    const int mode = (beta == 0.0) ? (alpha == 1.0 ? 0 : 1) : 2;
+    EpiStore<T> epi{static_cast<T*>(x), (T)alpha, (T)beta, mode};
+    if (A->n == 0) return GK_OK;
+    if (A->fmt == GK_CSR && A->plan.kind == 2) {
+        constexpr int E = sizeof(V) >= 8 ? 8 : 12;
+        const int64_t N = (int64_t)A->n + A->nnz;
+        const int64_t nb = (N + 256 * E - 1) / (256 * E);
+        GK_TRY(A->carry.ensure((size_t)nb * (sizeof(int32_t) + sizeof(T)) + 16));
+        int32_t* crow = static_cast<int32_t*>(A->carry.ptr);
+        T* cval = reinterpret_cast<T*>(static_cast<char*>(A->carry.ptr) +
+                                       (((size_t)nb * sizeof(int32_t) + 15) & ~(size_t)15));
+        k_csr_merge<E, V, T><<<(unsigned)nb, 256, 0, s>>>(A->n, A->nnz, A->row_ptr, A->col,
+                                                          (const V*)A->val, (const T*)b, epi, crow,
+                                                          cval);
+        const unsigned fg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, 4096));
+        k_csr_merge_fixup<T><<<fg, 256, 0, s>>>((int32_t)nb, crow, cval, static_cast<T*>(x),
+                                                (T)alpha, mode);
+        GK_CUDA(cudaGetLastError());
+        return GK_OK;
+    }
+    return launch_spmv_rows<V, T>(A, static_cast<const T*>(b), epi, s);
+}
+
+gk_status spmv_dispatch(gk_matrix A, double alpha, const void* b, double beta, void* x,
+                        cudaStream_t s) {
+    switch (A->dtype) {
+        case GK_F64: return spmv_typed<double, double>(A, alpha, b, beta, x, s);
+        case GK_F32: return spmv_typed<float, float>(A, alpha, b, beta, x, s);
+        case GK_BF16: return spmv_typed<__nv_bfloat16, float>(A, alpha, b, beta, x, s);
+    }
+    return GK_ERR_INVALID;
+}
+
+static gk_status apply_common(gk_matrix A, double alpha, const void* b, double beta, void* x,
+                              void* stream) {
+    if (!A || (!b && A->ncols > 0) || (!x && A->n > 0)) return GK_ERR_INVALID;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != A->device) return GK_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (A->n == 0) return GK_OK;
+    const bool db = A->ncols == 0 || is_device_ptr(b);
+    const bool dx = is_device_ptr(x);
+    if (db && dx) return spmv_dispatch(A, alpha, b, beta, x, s);
+    if (db != dx && A->ncols > 0) return GK_ERR_INVALID;  // mixed host/device vectors
+    // host vectors: stage through device buffers owned by the handle
+    std::lock_guard<std::mutex> lk(A->mu);
+    const size_t vb = vector_bytes(A->dtype);
+    GK_TRY(A->stage_in.ensure(vb * (size_t)std::max(A->ncols, 1)));
+    GK_TRY(A->stage_out.ensure(vb * (size_t)A->n));
+    if (A->ncols > 0)
+        GK_CUDA(cudaMemcpyAsync(A->stage_in.ptr, b, vb * (size_t)A->ncols, cudaMemcpyHostToDevice, s));
+    if (beta != 0.0)
+        GK_CUDA(cudaMemcpyAsync(A->stage_out.ptr, x, vb * (size_t)A->n, cudaMemcpyHostToDevice, s));
+    GK_TRY(spmv_dispatch(A, alpha, A->stage_in.ptr, beta, A->stage_out.ptr, s));
+    GK_CUDA(cudaMemcpyAsync(x, A->stage_out.ptr, vb * (size_t)A->n, cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    return GK_OK;
+}
+
+}  // namespace gk
+
+extern "C" {
+
+gk_status gk_apply(gk_matrix A, const void* b, void* x, void* stream) {
+    return gk::apply_common(A, 1.0, b, 0.0, x, stream);
+}
+
+gk_status gk_apply_adv(gk_matrix A, double alpha, const void* b, double beta, void* x,
+                       void* stream) {
+    return gk::apply_common(A, alpha, b, beta, x, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,557 @@
+// batched.cu - single-block engine: one thread block runs a whole CG or
+// BiCGSTAB solve (same algorithm, stopping rule and residual replacement
+// as the multi-kernel engine; Section 2.3 Listings 1-2 for the interface).
+//
+// Used for many small independent systems in one launch (gk_solve_batched)
+// and for small single systems (engine 2).  The vector that SpMV gathers
+// from (p for CG; phat, then shat for BiCGSTAB) is staged in shared memory;
+// the other vectors live in a per-system global workspace that stays in
+// L1/L2.  Blocks loop over systems (persistent grid), so the launch is one
+// kernel regardless of the number of systems.  Reductions are block-wide,
+// fixed order, so a system's result does not depend on the rest of the
+// batch or on the grid size.
+#include <cstring>
+#include <vector>
+
+#include "prims.cuh"
+
+namespace gk {
+
+
+struct SysDesc {
+    int32_t n, pad;
+    const int32_t* rp;
+    const int32_t* ci;
+    const void* va;
+    const void* b;
+    void* x;
+    void* work;  // workspace vectors, each `ld` elements
+    int64_t ld;
+};
+
+struct SysOut {
+    int32_t status, iters, restarts, pad;
+    double rec, tru;
+};
+
+struct BlockOpts {
+    double tol;
+    int32_t max_iters;
+    int32_t prec;
+};
+
+// Sum of NA values over the block, returned to every thread (fixed order).
+template <int NA>
+__device__ __forceinline__ void block_allsum(double (&v)[NA]) {
+    __shared__ double sh[NA][32];
+    __shared__ double tot[NA];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+        const double w = warp_sum(v[a]);
+        if (lane == 0) sh[a][warp] = w;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            const double w = warp_sum(lane < nw ? sh[a][lane] : 0.0);
+            if (lane == 0) tot[a] = w;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < NA; ++a) v[a] = tot[a];
+}
+
+template <typename V, typename T, typename G>
+__device__ __forceinline__ T row_dot(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                     const V* __restrict__ va, const G* __restrict__ g, int32_t i) {
+    T s = T(0);
+    const int32_t e = rp[i + 1];
+    for (int32_t k = rp[i]; k < e; ++k) s = fmadd(cvt<T>(va[k]), (T)g[ci[k]], s);
+    return s;
+}
+
+// Jacobi inverse diagonal of row i; 0 when missing or zero.
+template <typename V, typename T>
+__device__ __forceinline__ T row_dinv(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                      const V* __restrict__ va, int32_t i) {
+    T d = T(0);
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+        if (ci[k] == i) d += cvt<T>(va[k]);
+    return d == T(0) ? T(0) : T(1) / d;
+}
+
+// Prepares a system: Jacobi diagonal (in work slot 0), ||b||, true residual.
+// Returns false (and fills o) when the solve is already decided.
+template <typename V, typename T>
+__device__ bool block_setup(const SysDesc& d, const BlockOpts& opt, T* dinv, T* r, double& bn,
+                            double& thr, SysOut& o) {
+    const int32_t n = d.n;
+    const V* va = (const V*)d.va;
+    const T* b = (const T*)d.b;
+    T* x = (T*)d.x;
+    double acc[2] = {0.0, 0.0};
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const T bi = b[i];
+        acc[0] = fma((double)bi, (double)bi, acc[0]);
+        if (opt.prec) {
+            const T di = row_dinv<V, T>(d.rp, d.ci, va, i);
+            dinv[i] = di;
+            if (di == T(0)) acc[1] = 1.0;
+        }
+    }
+    block_allsum<2>(acc);
+    o.iters = 0;
+    o.restarts = 0;
+    o.rec = o.tru = 0.0;
+    if (acc[1] != 0.0) {
+        o.status = GK_ERR_ZERO_DIAG;
+        return false;
+    }
+    bn = sqrt(acc[0]);
+    thr = opt.tol * bn;
+    if (bn == 0.0) {
+        for (int32_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = T(0);
+        o.status = GK_OK;
+        return false;
+    }
+    if (!isfinite(bn)) {
+        o.status = GK_ERR_NAN;
+        return false;
+    }
+    double rr[1] = {0.0};
+    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const T ri = b[i] - row_dot<V, T>(d.rp, d.ci, va, x, i);
+        r[i] = ri;
+        rr[0] = fma((double)ri, (double)ri, rr[0]);
+    }
+    block_allsum<1>(rr);
+    const double rn = sqrt(rr[0]);
+    o.rec = o.tru = rn / bn;
+    if (!isfinite(rn)) {
+        o.status = GK_ERR_NAN;
+        return false;
+    }
+    if (rn <= thr) {
+        o.status = GK_OK;
+        return false;
+    }
+    o.status = GK_NOT_CONVERGED;
+    return true;
+}
+
+// r = b - A x in place; returns ||r||
+template <typename V, typename T>
+__device__ double block_true_resid(const SysDesc& d, T* r) {
+    const V* va = (const V*)d.va;
+    const T* b = (const T*)d.b;
+    const T* x = (const T*)d.x;
+    double tt[1] = {0.0};
+    for (int32_t i = threadIdx.x; i < d.n; i += blockDim.x) {
+        const T ri = b[i] - row_dot<V, T>(d.rp, d.ci, va, x, i);
+        r[i] = ri;
+        tt[0] = fma((double)ri, (double)ri, tt[0]);
+    }
+    block_allsum<1>(tt);
+    return sqrt(tt[0]);
+}
+
+// ---------------------------------------------------------------- CG
+// work slots: 0 dinv, 1 r, 2 q, 3 scratch (final residual)
+constexpr int BLOCK_MAX_THREADS = 512;
+
+template <typename V, typename T>
+__global__ void __launch_bounds__(BLOCK_MAX_THREADS) k_block_cg(const SysDesc* __restrict__ sys, SysOut* __restrict__ outs,
+                           int32_t count, BlockOpts opt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* ps = reinterpret_cast<T*>(smem_raw);
+    for (int32_t sidx = blockIdx.x; sidx < count; sidx += gridDim.x) {
+        const SysDesc d = sys[sidx];
+        const int32_t n = d.n;
+        const V* va = (const V*)d.va;
+        T* x = (T*)d.x;
+        T* dinv = (T*)d.work;
+        T* r = dinv + d.ld;
+        T* q = r + d.ld;
+        T* scratch = q + d.ld;
+        SysOut o;
+        double bn = 0.0, thr = 0.0;
+        if (block_setup<V, T>(d, opt, dinv, r, bn, thr, o)) {
+            double rho = 0.0;
+            auto init_dir = [&]() {
+                double rz[1] = {0.0};
+                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                    const T ri = r[i];
+                    const T zi = opt.prec ? dinv[i] * ri : ri;
+                    ps[i] = zi;
+                    rz[0] = fma((double)ri, (double)zi, rz[0]);
+                }
+                block_allsum<1>(rz);
+                rho = rz[0];
+            };
+            init_dir();
+            int32_t k = 0;
+            while (k < opt.max_iters) {
+                double pq[1] = {0.0};
+                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                    const T s = row_dot<V, T>(d.rp, d.ci, va, ps, i);
+                    q[i] = s;
+                    pq[0] = fma((double)ps[i], (double)s, pq[0]);
+                }
+                block_allsum<1>(pq);
+                if (!isfinite(pq[0])) { o.status = GK_ERR_NAN; break; }
+                if (pq[0] <= 0.0) { o.status = GK_BREAKDOWN; break; }
+                const double alpha = rho / pq[0];
+                const T ta = (T)alpha;
+                double a2[2] = {0.0, 0.0};
+                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                    x[i] = fmadd(ta, ps[i], x[i]);
+                    const T ri = fmadd(-ta, q[i], r[i]);
+                    r[i] = ri;
+                    const T zi = opt.prec ? dinv[i] * ri : ri;
+                    a2[0] = fma((double)ri, (double)zi, a2[0]);
+                    a2[1] = fma((double)ri, (double)ri, a2[1]);
+                }
+                block_allsum<2>(a2);
+                ++k;
+                const double rn = sqrt(a2[1]);
+                o.rec = rn / bn;
+                if (!isfinite(rn) || !isfinite(a2[0])) { o.status = GK_ERR_NAN; break; }
+                if (rn <= thr) {
+                    const double tn = block_true_resid<V, T>(d, r);
+                    if (tn <= thr) { o.status = GK_OK; break; }
+                    o.restarts += 1;  // residual replacement, restart from x
+                    init_dir();
+                    continue;
+                }
+                const double beta = a2[0] / rho;
+                rho = a2[0];
+                const T tb = (T)beta;
+                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                    const T zi = opt.prec ? dinv[i] * r[i] : r[i];
+                    ps[i] = fmadd(tb, ps[i], zi);
+                }
+                __syncthreads();
+            }
+            o.iters = k;
+            o.tru = block_true_resid<V, T>(d, scratch) / bn;
+        }
+        if (threadIdx.x == 0) outs[sidx] = o;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- BiCGSTAB
+// work slots: 0 dinv, 1 r, 2 rhat, 3 p, 4 phat, 5 v, 6 s, 7 shat, 8 t
+template <typename V, typename T>
+__global__ void __launch_bounds__(BLOCK_MAX_THREADS) k_block_bicgstab(const SysDesc* __restrict__ sys, SysOut* __restrict__ outs,
+                                 int32_t count, BlockOpts opt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* gs = reinterpret_cast<T*>(smem_raw);  // gathered vector
+    for (int32_t sidx = blockIdx.x; sidx < count; sidx += gridDim.x) {
+        const SysDesc d = sys[sidx];
+        const int32_t n = d.n;
+        const V* va = (const V*)d.va;
+        T* x = (T*)d.x;
+        T* dinv = (T*)d.work;
+        T *r = dinv + d.ld, *rh = r + d.ld, *p = rh + d.ld, *ph = p + d.ld, *v = ph + d.ld;
+        T *s = v + d.ld, *sh = s + d.ld, *t = sh + d.ld;
+        SysOut o;
+        double bn = 0.0, thr = 0.0;
+        if (block_setup<V, T>(d, opt, dinv, r, bn, thr, o)) {
+            double rho = 1.0, alpha = 1.0, omega = 1.0, rho_new = 0.0;
+            auto restart = [&]() {
+                double a[1] = {0.0};
+                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                    const T ri = r[i];
+                    rh[i] = ri;
+                    p[i] = T(0);
+                    v[i] = T(0);
+                    a[0] = fma((double)ri, (double)ri, a[0]);
+                }
+                block_allsum<1>(a);
+                rho = alpha = omega = 1.0;
+                rho_new = a[0];
+            };
+            restart();
+            int32_t k = 0;
+            while (k < opt.max_iters) {
+                if (!isfinite(rho_new)) { o.status = GK_ERR_NAN; break; }
+                if (rho_new == 0.0) { o.status = GK_BREAKDOWN; break; }
+                const T beta = (T)((rho_new / rho) * (alpha / omega));
+                const T tw = (T)omega;
+                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                    const T pi = fmadd(beta, fmadd(-tw, v[i], p[i]), r[i]);
+                    p[i] = pi;
+                    const T hi = opt.prec ? dinv[i] * pi : pi;
+                    ph[i] = hi;
+                    gs[i] = hi;
+                }
+                __syncthreads();
+                double rv[1] = {0.0};
+                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                    const T vi = row_dot<V, T>(d.rp, d.ci, va, gs, i);
+                    v[i] = vi;
+                    rv[0] = fma((double)rh[i], (double)vi, rv[0]);
+                }
+                block_allsum<1>(rv);
+                if (!isfinite(rv[0])) { o.status = GK_ERR_NAN; break; }
+                if (rv[0] == 0.0) { o.status = GK_BREAKDOWN; break; }
+                alpha = rho_new / rv[0];
+                const T ta = (T)alpha;
+                double ss[1] = {0.0};
+                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                    const T si = fmadd(-ta, v[i], r[i]);
+                    s[i] = si;
+                    ss[0] = fma((double)si, (double)si, ss[0]);
+                }
+                block_allsum<1>(ss);
+                ++k;
+                const double sn = sqrt(ss[0]);
+                if (!isfinite(sn)) { o.status = GK_ERR_NAN; break; }
+                if (sn <= thr) {  // half-step exit
+                    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = fmadd(ta, ph[i], x[i]);
+                    o.rec = sn / bn;
+                    __syncthreads();
+                    const double tn = block_true_resid<V, T>(d, r);
+                    if (tn <= thr) { o.status = GK_OK; break; }
+                    o.restarts += 1;
+                    restart();
+                    continue;
+                }
+                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                    const T hi = opt.prec ? dinv[i] * s[i] : s[i];
+                    sh[i] = hi;
+                    gs[i] = hi;
+                }
+                __syncthreads();
+                double a2[2] = {0.0, 0.0};
+                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                    const T ti = row_dot<V, T>(d.rp, d.ci, va, gs, i);
+                    t[i] = ti;
+                    a2[0] = fma((double)ti, (double)s[i], a2[0]);
+                    a2[1] = fma((double)ti, (double)ti, a2[1]);
+                }
+                block_allsum<2>(a2);
+                if (!isfinite(a2[0]) || !isfinite(a2[1])) { o.status = GK_ERR_NAN; break; }
+                if (a2[1] == 0.0) { o.status = GK_BREAKDOWN; break; }
+                omega = a2[0] / a2[1];
+                if (omega == 0.0) { o.status = GK_BREAKDOWN; break; }
+                const T to = (T)omega;
+                double a3[2] = {0.0, 0.0};
+                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                    x[i] = fmadd(to, sh[i], fmadd(ta, ph[i], x[i]));
+                    const T ri = fmadd(-to, t[i], s[i]);
+                    r[i] = ri;
+                    a3[0] = fma((double)rh[i], (double)ri, a3[0]);
+                    a3[1] = fma((double)ri, (double)ri, a3[1]);
+                }
+                block_allsum<2>(a3);
+                rho = rho_new;
+                rho_new = a3[0];
+                const double rn = sqrt(a3[1]);
+                o.rec = rn / bn;
+                if (!isfinite(rn)) { o.status = GK_ERR_NAN; break; }
+                if (rn <= thr) {
+                    const double tn = block_true_resid<V, T>(d, r);
+                    if (tn <= thr) { o.status = GK_OK; break; }
+                    o.restarts += 1;
+                    restart();
+                }
+            }
+            o.iters = k;
+            o.tru = block_true_resid<V, T>(d, t) / bn;
+        }
+        if (threadIdx.x == 0) outs[sidx] = o;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- host
+
+static int nslots(int method) { return method == GK_CG ? 4 : 9; }
+
+struct BatchBufs {
+    DevBuf desc, outs, work;
+    SysDesc* hdesc = nullptr;
+    SysOut* hout = nullptr;
+    size_t hcap = 0;
+    ~BatchBufs() {
+        if (hdesc) cudaFreeHost(hdesc);
+        if (hout) cudaFreeHost(hout);
+        desc.release();
+        outs.release();
+        work.release();
+    }
+};
+
+static std::mutex g_batch_mu;
+static BatchBufs* g_batch = nullptr;  // reused across calls (serialised by g_batch_mu)
+
+template <typename V, typename T>
+static gk_status launch_block(int method, const SysDesc* ddesc, SysOut* dout, int32_t count,
+                              const BlockOpts& bo, int nt, size_t smem, unsigned grid,
+                              cudaStream_t s) {
+    if (method == GK_CG) {
+        auto k = k_block_cg<V, T>;
+        GK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        k<<<grid, nt, smem, s>>>(ddesc, dout, count, bo);
+    } else {
+        auto k = k_block_bicgstab<V, T>;
+        GK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        k<<<grid, nt, smem, s>>>(ddesc, dout, count, bo);
+    }
+    GK_CUDA(cudaGetLastError());
+    return GK_OK;
+}
+
+// Runs count systems; infos may be null.  All matrices CSR, same dtype.
+static gk_status run_batch(int32_t count, const gk_matrix* As, const void* const* bs,
+                           void* const* xs, const gk_solve_opts* o, gk_solve_info* infos,
+                           cudaStream_t s, int nt, float* ms_out) {
+    const gk_dtype dt = As[0]->dtype;
+    const size_t vb = vector_bytes(dt);
+    int32_t nmax = 0;
+    size_t wbytes = 0;
+    const int ns = nslots(o->method);
+    for (int32_t i = 0; i < count; ++i) {
+        nmax = std::max(nmax, As[i]->n);
+        const size_t ld = (((size_t)As[i]->n * vb + 255) & ~(size_t)255) / vb;
+        wbytes += ld * vb * ns;
+    }
+    const size_t smem = std::max<size_t>((size_t)nmax * vb, 16);
+    if (smem > 200 * 1024) return GK_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    if (!g_batch) g_batch = new BatchBufs();
+    BatchBufs& B = *g_batch;
+    if (B.hcap < (size_t)count) {
+        if (B.hdesc) cudaFreeHost(B.hdesc);
+        if (B.hout) cudaFreeHost(B.hout);
+        B.hdesc = nullptr;
+        B.hout = nullptr;
+        GK_CUDA(cudaMallocHost(&B.hdesc, sizeof(SysDesc) * (size_t)count));
+        GK_CUDA(cudaMallocHost(&B.hout, sizeof(SysOut) * (size_t)count));
+        B.hcap = (size_t)count;
+    }
+    GK_TRY(B.desc.ensure(sizeof(SysDesc) * (size_t)count));
+    GK_TRY(B.outs.ensure(sizeof(SysOut) * (size_t)count));
+    GK_TRY(B.work.ensure(wbytes + 256));
+    char* w = (char*)B.work.ptr;
+    for (int32_t i = 0; i < count; ++i) {
+        gk_matrix A = As[i];
+        SysDesc& d = B.hdesc[i];
+        d.n = A->n;
+        d.pad = 0;
+        d.rp = A->row_ptr;
+        d.ci = A->col;
+        d.va = A->val;
+        d.b = bs[i];
+        d.x = xs[i];
+        d.work = w;
+        d.ld = (int64_t)((((size_t)A->n * vb + 255) & ~(size_t)255) / vb);
+        w += (size_t)d.ld * vb * ns;
+    }
+    GK_CUDA(cudaMemcpyAsync(B.desc.ptr, B.hdesc, sizeof(SysDesc) * (size_t)count,
+                            cudaMemcpyHostToDevice, s));
+    BlockOpts bo{o->tol, o->max_iters, o->precond == GK_PRECOND_JACOBI};
+    int occ = 1;
+    const int sms = num_sms();
+    cudaEvent_t e0, e1;
+    GK_CUDA(cudaEventCreate(&e0));
+    GK_CUDA(cudaEventCreate(&e1));
+    GK_CUDA(cudaEventRecord(e0, s));
+    gk_status st = GK_OK;
+    auto occ_of = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        int b = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, nt, smem) != cudaSuccess || b < 1) b = 1;
+        return b;
+    };
+    if (dt == GK_F64) {
+        occ = o->method == GK_CG ? occ_of(k_block_cg<double, double>) : occ_of(k_block_bicgstab<double, double>);
+    } else if (dt == GK_F32) {
+        occ = o->method == GK_CG ? occ_of(k_block_cg<float, float>) : occ_of(k_block_bicgstab<float, float>);
+    } else {
+        occ = o->method == GK_CG ? occ_of(k_block_cg<__nv_bfloat16, float>)
+                                 : occ_of(k_block_bicgstab<__nv_bfloat16, float>);
+    }
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(count, (int64_t)sms * occ));
+    const SysDesc* dd = (const SysDesc*)B.desc.ptr;
+    SysOut* dout = (SysOut*)B.outs.ptr;
+    if (dt == GK_F64) st = launch_block<double, double>(o->method, dd, dout, count, bo, nt, smem, grid, s);
+    else if (dt == GK_F32) st = launch_block<float, float>(o->method, dd, dout, count, bo, nt, smem, grid, s);
+    else st = launch_block<__nv_bfloat16, float>(o->method, dd, dout, count, bo, nt, smem, grid, s);
+    GK_CUDA(cudaEventRecord(e1, s));
+    if (st == GK_OK) {
+        GK_CUDA(cudaMemcpyAsync(B.hout, B.outs.ptr, sizeof(SysOut) * (size_t)count,
+                                cudaMemcpyDeviceToHost, s));
+        GK_CUDA(cudaStreamSynchronize(s));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms_out) *ms_out = ms;
+        if (infos)
+            for (int32_t i = 0; i < count; ++i) {
+                const SysOut& so = B.hout[i];
+                infos[i].status = (gk_status)so.status;
+                infos[i].iters = so.iters;
+                infos[i].restarts = so.restarts;
+                infos[i].outer_iters = 0;
+                infos[i].rel_res_recurrence = so.rec;
+                infos[i].rel_res_true = so.tru;
+                infos[i].device_ms = ms;
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+
+gk_status solve_small(gk_matrix A, const void* b, void* x, const gk_solve_opts* o, cudaStream_t s,
+                      SolveOut* out) {
+    if (A->fmt != GK_CSR || o->method == GK_GMRES) return GK_ERR_UNSUPPORTED;
+    gk_solve_info info;
+    std::memset(&info, 0, sizeof(info));
+    gk_matrix As[1] = {A};
+    const void* bs[1] = {b};
+    void* xs[1] = {x};
+    GK_TRY(run_batch(1, As, bs, xs, o, &info, s, BLOCK_MAX_THREADS, nullptr));
+    out->status = info.status;
+    out->iters = info.iters;
+    out->restarts = info.restarts;
+    out->rec = info.rel_res_recurrence;
+    out->tru = info.rel_res_true;
+    return GK_OK;
+}
+
+}  // namespace gk
+
+using namespace gk;
+
+extern "C" gk_status gk_solve_batched(int32_t count, const gk_matrix* As, const void* const* bs,
+                                      void* const* xs, const gk_solve_opts* o,
+                                      gk_solve_info* infos, void* stream) {
+    if (count < 0 || !o || (count > 0 && (!As || !bs || !xs))) return GK_ERR_INVALID;
+    if (count == 0) return GK_OK;
+    if (o->method == GK_GMRES) return GK_ERR_UNSUPPORTED;
+    if ((o->method != GK_CG && o->method != GK_BICGSTAB) || o->mixed ||
+        (o->precond != GK_PRECOND_NONE && o->precond != GK_PRECOND_JACOBI) || !(o->tol >= 0.0) ||
+        o->max_iters < 0)
+        return GK_ERR_INVALID;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    for (int32_t i = 0; i < count; ++i) {
+        const gk_matrix A = As[i];
+        if (!A || A->fmt != GK_CSR || A->n != A->ncols || A->dtype != As[0]->dtype ||
+            A->n > 16384 || (A->n > 0 && (!bs[i] || !xs[i])))
+            return GK_ERR_INVALID;
+        if (A->device != dev) return GK_ERR_UNSUPPORTED;
+    }
+    int nt = 256;
+    if (const char* e = getenv("GK_BATCH_THREADS")) nt = atoi(e);
+    if (nt != 128 && nt != 256 && nt != 512) nt = 256;
+    return run_batch(count, As, bs, xs, o, infos, (cudaStream_t)stream, nt, nullptr);
+}

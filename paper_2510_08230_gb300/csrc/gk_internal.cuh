@@ -1,0 +1,193 @@
+// gk_internal.cuh - internal types and helpers of the GB300 sparse library.
+//
+// Value types: F64 stores and computes in double; F32 in float; BF16 stores
+// matrix values as bfloat16 and computes in float (vectors are float).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <mutex>
+#include <string>
+
+#include "gk.h"
+
+namespace gk {
+
+// ------------------------------------------------------------------ types
+template <gk_dtype D> struct Types;
+template <> struct Types<GK_F64> { using V = double; using T = double; };
+template <> struct Types<GK_F32> { using V = float; using T = float; };
+template <> struct Types<GK_BF16> { using V = __nv_bfloat16; using T = float; };
+
+inline size_t value_bytes(gk_dtype d) { return d == GK_F64 ? 8 : d == GK_F32 ? 4 : 2; }
+inline size_t vector_bytes(gk_dtype d) { return d == GK_F64 ? 8 : 4; }
+inline bool valid_dtype(int d) { return d == GK_F64 || d == GK_F32 || d == GK_BF16; }
+
+__device__ __forceinline__ double to_t(double v, double) { return v; }
+__device__ __forceinline__ float to_t(float v, float) { return v; }
+__device__ __forceinline__ float to_t(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+
+// conversions between value types (round to nearest even when narrowing)
+template <typename O> struct Cvt;
+template <> struct Cvt<double> {
+    static __device__ __forceinline__ double f(double v) { return v; }
+    static __device__ __forceinline__ double f(float v) { return (double)v; }
+    static __device__ __forceinline__ double f(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+};
+template <> struct Cvt<float> {
+    static __device__ __forceinline__ float f(double v) { return __double2float_rn(v); }
+    static __device__ __forceinline__ float f(float v) { return v; }
+    static __device__ __forceinline__ float f(__nv_bfloat16 v) { return __bfloat162float(v); }
+};
+template <> struct Cvt<__nv_bfloat16> {
+    static __device__ __forceinline__ __nv_bfloat16 f(double v) { return __double2bfloat16(v); }
+    static __device__ __forceinline__ __nv_bfloat16 f(float v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ __nv_bfloat16 f(__nv_bfloat16 v) { return v; }
+};
+template <typename O, typename I>
+__device__ __forceinline__ O cvt(I v) { return Cvt<O>::f(v); }
+
+// accumulation type used when merging duplicate COO entries
+template <typename V> struct AccOf;
+template <> struct AccOf<double> { using type = double; };
+template <> struct AccOf<float> { using type = float; };
+template <> struct AccOf<__nv_bfloat16> { using type = float; };
+__device__ __forceinline__ double to_acc(double v) { return v; }
+__device__ __forceinline__ float to_acc(float v) { return v; }
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename O, typename A>
+__device__ __forceinline__ O from_acc(A v) { return Cvt<O>::f(v); }
+
+// fused multiply-add with one rounding
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// read-only, L1-cached load of a matrix value / index
+__device__ __forceinline__ double ldv(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ldv(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldv(const __nv_bfloat16* p) {
+    return __bfloat162float(__ldg(p));
+}
+
+// streaming loads for data touched once (do not keep in L1)
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const __nv_bfloat16* p) {
+    unsigned short u = __ldcs(reinterpret_cast<const unsigned short*>(p));
+    return __bfloat162float(__ushort_as_bfloat16(u));
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* where, cudaError_t e);
+const char* last_error();
+
+#define GK_CUDA(...)                                   \
+    do {                                               \
+        cudaError_t e_ = (__VA_ARGS__);                \
+        if (e_ != cudaSuccess) {                       \
+            ::gk::set_error(#__VA_ARGS__, e_);         \
+            return e_ == cudaErrorMemoryAllocation     \
+                       ? GK_ERR_OOM                    \
+                       : GK_ERR_CUDA;                  \
+        }                                              \
+    } while (0)
+
+#define GK_TRY(...)                                    \
+    do {                                               \
+        gk_status s_ = (__VA_ARGS__);                  \
+        if (s_ != GK_OK) return s_;                    \
+    } while (0)
+
+// Allocation padded by 64 bytes so that 16-byte vector loads rounded out
+// to alignment at either end of an array stay inside the allocation.
+cudaError_t dmalloc(void** p, size_t bytes);
+template <typename X>
+cudaError_t dmalloc_t(X** p, size_t count) {
+    return dmalloc(reinterpret_cast<void**>(p), count * sizeof(X));
+}
+void dfree(void* p);
+
+// Device buffer that only grows (workspace cache).
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    gk_status ensure(size_t want);
+    void release();
+};
+
+// ------------------------------------------------------------------ matrix
+// CSR row-tile plan: tile c covers rows [tile_row[c], tile_row[c+1]); its
+// nonzeros fit in `tile_cap` entries (launch plan of the row-tile kernel).
+struct CsrPlan {
+    int kind = 0;            // 0 vector (G lanes / row), 1 row-tile, 2 merge
+    int lanes = 1;           // vector kernel lanes per row
+    int32_t ntiles = 0;
+    int32_t chunk = 0;       // nnz per chunk used to cut tiles
+    int32_t tile_cap = 0;    // smem capacity in entries (>= chunk + max_row)
+    int32_t* tile_row = nullptr;  // ntiles + 1
+    // merge kernel
+    int32_t merge_tiles = 0;
+    int32_t merge_items = 0;      // nnz per merge tile
+    int32_t* merge_row = nullptr; // row containing the first nnz of each merge tile (+1)
+};
+
+struct SolverCache;  // solve.cu
+
+// result of one solve (either engine)
+struct SolveOut {
+    gk_status status = GK_OK;
+    int32_t iters = 0, restarts = 0;
+    double rec = 0.0, tru = 0.0;
+};
+
+}  // namespace gk
+
+struct gk_matrix_s {
+    int device = 0;
+    int32_t n = 0, ncols = 0;
+    int64_t nnz = 0;
+    gk_format fmt = GK_CSR;
+    gk_dtype dtype = GK_F64;
+    int32_t max_row = 0;
+    double mean_row = 0.0;
+    // CSR
+    int32_t* row_ptr = nullptr;
+    int32_t* col = nullptr;
+    void* val = nullptr;
+    // ELL
+    int32_t K = 0;
+    int64_t stride = 0;
+    // SELL-P
+    int32_t S = 0, f = 0, nslices = 0;
+    int32_t* slice_len = nullptr;
+    int64_t* slice_set = nullptr;
+    int64_t stored = 0;
+    // launch plan for CSR SpMV
+    gk::CsrPlan plan;
+    // derived data, built on first use
+    void* dinv = nullptr;         // Jacobi inverse diagonal (vector type)
+    int dinv_state = 0;           // 0 not built, 1 ok, -1 zero diagonal
+    gk_matrix_s* lowp[3] = {nullptr, nullptr, nullptr};  // same layout, other dtype
+    gk::SolverCache* solver = nullptr;
+    gk::DevBuf stage_in, stage_out;  // host-pointer apply staging
+    gk::DevBuf carry;                // merge-path block carries
+    cudaStream_t side = nullptr;     // library stream for graph capture
+    std::mutex mu;
+};
+
+namespace gk {
+gk_status build_csr_plan(gk_matrix A, cudaStream_t s);
+gk_status ensure_jacobi(gk_matrix A, cudaStream_t s);
+gk_status get_lowp(gk_matrix A, gk_dtype d, cudaStream_t s, gk_matrix* out);
+void free_solver_cache(gk_matrix A);
+gk_status spmv_dispatch(gk_matrix A, double alpha, const void* b, double beta,
+                        void* x, cudaStream_t s);
+int num_sms();
+}  // namespace gk

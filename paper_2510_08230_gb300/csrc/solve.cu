@@ -1,0 +1,1366 @@
+// solve.cu - Krylov solvers on the device: CG, BiCGSTAB and GMRES(m) with an
+// optional Jacobi preconditioner, and FP64 iterative refinement around
+// FP32 / BF16-stored inner solves.
+//
+// The solver LinOp overwrites the initial guess with the solution
+// (Section 2.3, Listing 1); stopping is an iteration cap OR
+// ||r|| <= tol * ||b|| with the right-hand-side norm as baseline
+// (Listing 2).  GMRES keeps the whole least-squares update on the GPU, uses
+// Givens rotations and checks the residual estimate after every Hessenberg
+// column (Section 5.2.1).
+//
+// Multi-kernel engine: each iteration is a fixed sequence of fused kernels
+// (SpMV + dot, axpys + dots + preconditioner, ...); all scalars (alpha,
+// beta, rho, Givens data) live in a device-side state block and are
+// produced by the last block of the kernel that finishes each reduction,
+// so no host round trip happens inside an iteration.  A chunk of
+// iterations is captured once into a CUDA graph and replayed; kernels
+// return immediately once the state says "halt".  The host looks at the
+// state only between chunks.
+#include <cstring>
+#include <vector>
+
+#include "spmv.cuh"
+
+namespace gk {
+
+constexpr int MAXM = 64;
+
+struct KState {
+    double thr;        // tol * ||b||
+    double bnorm;
+    double rho, alpha, beta, omega;
+    double rnorm;      // last recurrence residual (or Givens estimate)
+    double tnorm;      // last true residual norm
+    double snorm;
+    int32_t iter, max_iters;
+    int32_t halt;      // 0 run; 1 recurrence passed (host checks true residual); 2 stop
+    int32_t status;
+    int32_t half;      // BiCGSTAB: stopped at the half step
+    int32_t restarts;
+    // GMRES
+    int32_t k, m, cycle_end, v0_pending;
+    double beta0, inv_h;
+    double H[(MAXM + 1) * MAXM];
+    double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
+    double h1[MAXM + 1], h2[MAXM + 1];
+};
+
+__device__ __forceinline__ bool halted(const KState* st) {
+    return *reinterpret_cast<const volatile int32_t*>(&st->halt) != 0;
+}
+
+// ------------------------------------------------------------ grids
+
+static unsigned ew_grid(int64_t n) {
+    int64_t b = (n + 1023) / 1024;
+    int64_t cap = (int64_t)num_sms() * 8;
+    return (unsigned)std::max<int64_t>(1, std::min(b, cap));
+}
+
+// ------------------------------------------------------------ fins
+// (run by thread 0 of the last block with the grid totals)
+
+struct FinNorm {  // ||v|| -> field
+    KState* st;
+    int which;  // 0 bnorm, 1 tnorm
+    __device__ void operator()(double* t) const {
+        double v = sqrt(t[0]);
+        if (which == 0) st->bnorm = v;
+        else st->tnorm = v;
+    }
+};
+
+// ------------------------------------------------------------ epilogues
+
+// r_i = b_i - s ; acc += r_i^2  (true residual)
+template <typename T, class Fin>
+struct EpiResid {
+    T* __restrict__ r;
+    const T* __restrict__ b;
+    const int32_t* halt;
+    double* partials;
+    unsigned* ticket;
+    Fin fin;
+    static constexpr int NA = 1;
+    __device__ __forceinline__ bool skip() const {
+        return halt && *reinterpret_cast<const volatile int32_t*>(halt) != 0;
+    }
+    __device__ __forceinline__ void row(int64_t i, T s, double* acc) const {
+        T v = b[i] - s;
+        r[i] = v;
+        acc[0] = fma((double)v, (double)v, acc[0]);
+    }
+    __device__ __forceinline__ void finish(double* acc) const {
+        double a[1] = {acc[0]};
+        grid_reduce_finish<1>(a, partials, ticket, fin);
+    }
+};
+
+// y_i = s ; acc += w_i * s
+template <typename T, class Fin>
+struct EpiDot {
+    T* __restrict__ y;
+    const T* __restrict__ w;
+    const int32_t* halt;
+    double* partials;
+    unsigned* ticket;
+    Fin fin;
+    static constexpr int NA = 1;
+    __device__ __forceinline__ bool skip() const {
+        return halt && *reinterpret_cast<const volatile int32_t*>(halt) != 0;
+    }
+    __device__ __forceinline__ void row(int64_t i, T s, double* acc) const {
+        y[i] = s;
+        acc[0] = fma((double)w[i], (double)s, acc[0]);
+    }
+    __device__ __forceinline__ void finish(double* acc) const {
+        double a[1] = {acc[0]};
+        grid_reduce_finish<1>(a, partials, ticket, fin);
+    }
+};
+
+// y_i = s ; acc0 += s * u_i ; acc1 += s * s
+template <typename T, class Fin>
+struct EpiDot2 {
+    T* __restrict__ y;
+    const T* __restrict__ u;
+    const int32_t* halt;
+    double* partials;
+    unsigned* ticket;
+    Fin fin;
+    static constexpr int NA = 2;
+    __device__ __forceinline__ bool skip() const {
+        return halt && *reinterpret_cast<const volatile int32_t*>(halt) != 0;
+    }
+    __device__ __forceinline__ void row(int64_t i, T s, double* acc) const {
+        y[i] = s;
+        acc[0] = fma((double)s, (double)u[i], acc[0]);
+        acc[1] = fma((double)s, (double)s, acc[1]);
+    }
+    __device__ __forceinline__ void finish(double* acc) const {
+        double a[2] = {acc[0], acc[1]};
+        grid_reduce_finish<2>(a, partials, ticket, fin);
+    }
+};
+
+// plain store with a halt check (GMRES w = A z)
+template <typename T>
+struct EpiStoreHalt {
+    T* __restrict__ y;
+    const int32_t* halt;
+    static constexpr int NA = 0;
+    __device__ __forceinline__ bool skip() const {
+        return halt && *reinterpret_cast<const volatile int32_t*>(halt) != 0;
+    }
+    __device__ __forceinline__ void row(int64_t i, T s, double*) const { y[i] = s; }
+    __device__ __forceinline__ void finish(double*) const {}
+};
+
+// ------------------------------------------------------------ elementwise
+
+// per-thread partial sums in T, promoted to double for the grid reduction
+template <int NA, typename T, class Fin>
+__device__ __forceinline__ void finish_ew(T (&a)[NA], double* partials, unsigned* ticket,
+                                          const Fin& fin) {
+    double d[NA];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) d[k] = (double)a[k];
+    grid_reduce_finish<NA>(d, partials, ticket, fin);
+}
+
+#define GRID_LOOP(i, n)                                                             \
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); \
+         i += (int64_t)gridDim.x * blockDim.x)
+
+template <typename T, class Fin>
+__global__ void k_norm2(int32_t n, const T* __restrict__ v, double* partials, unsigned* ticket,
+                        Fin fin) {
+    T a[1] = {T(0)};
+    GRID_LOOP(i, n) a[0] = fmadd(v[i], v[i], a[0]);
+    finish_ew<1>(a, partials, ticket, fin);
+}
+
+template <typename T>
+__global__ void k_zero(int32_t n, T* __restrict__ v) {
+    GRID_LOOP(i, n) v[i] = T(0);
+}
+
+template <typename T>
+__global__ void k_copy(int32_t n, const T* __restrict__ a, T* __restrict__ b) {
+    GRID_LOOP(i, n) b[i] = a[i];
+}
+
+// Jacobi: dinv_i = 1 / a_ii (sum of stored diagonal entries); a missing or
+// zero diagonal sets *bad.
+template <typename V, typename T>
+__global__ void k_jacobi_gen(int32_t n, const int32_t* __restrict__ rp,
+                             const int32_t* __restrict__ ci, const V* __restrict__ va,
+                             T* __restrict__ dinv, int32_t* bad) {
+    GRID_LOOP(i, n) {
+        T d = T(0);
+        bool found = false;
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+            if (ci[k] == i) {
+                d += cvt<T>(va[k]);
+                found = true;
+            }
+        if (!found || d == T(0)) {
+            atomicOr(bad, 1);
+            dinv[i] = T(0);
+        } else {
+            dinv[i] = T(1) / d;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- CG
+// Hestenes-Stiefel with left preconditioner M = D (Jacobi) or I.
+
+struct CgAlphaFin {
+    KState* st;
+    __device__ void operator()(double* t) const {
+        const double pq = t[0];
+        if (!isfinite(pq)) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+        } else if (pq <= 0.0) {
+            st->status = GK_BREAKDOWN;
+            st->halt = 2;
+        } else {
+            st->alpha = st->rho / pq;
+        }
+    }
+};
+
+struct CgUpdFin {
+    KState* st;
+    int prec;
+    __device__ void operator()(double* t) const {
+        st->iter += 1;
+        const double rn = sqrt(t[1]);
+        st->rnorm = rn;
+        if (!isfinite(rn) || !isfinite(t[0])) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+            return;
+        }
+        if (rn <= st->thr) {
+            st->halt = 1;
+            return;
+        }
+        if (st->iter >= st->max_iters) {
+            st->status = GK_NOT_CONVERGED;
+            st->halt = 2;
+            return;
+        }
+        const double rz = prec ? t[0] : t[1];
+        st->beta = rz / st->rho;
+        st->rho = rz;
+    }
+};
+
+// x += alpha p ; r -= alpha q ; z = D^-1 r ; <r,z>, <r,r>
+template <typename T>
+__global__ void k_cg_update(int32_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
+                            const T* __restrict__ p, const T* __restrict__ q,
+                            const T* __restrict__ dinv, KState* st, double* partials,
+                            unsigned* ticket) {
+    if (halted(st)) return;
+    const T alpha = (T)st->alpha;
+    T a[2] = {T(0), T(0)};
+    GRID_LOOP(i, n) {
+        x[i] = fmadd(alpha, p[i], x[i]);
+        const T ri = fmadd(-alpha, q[i], r[i]);
+        r[i] = ri;
+        if (dinv) {
+            const T zi = dinv[i] * ri;
+            z[i] = zi;
+            a[0] = fmadd(ri, zi, a[0]);
+        }
+        a[1] = fmadd(ri, ri, a[1]);
+    }
+    finish_ew<2>(a, partials, ticket, CgUpdFin{st, dinv != nullptr});
+}
+
+// p = z + beta p
+template <typename T>
+__global__ void k_cg_p(int32_t n, T* __restrict__ p, const T* __restrict__ z, const KState* st) {
+    if (halted(st)) return;
+    const T beta = (T)st->beta;
+    GRID_LOOP(i, n) p[i] = fmadd(beta, p[i], z[i]);
+}
+
+struct CgInitFin {
+    KState* st;
+    __device__ void operator()(double* t) const { st->rho = t[0]; }
+};
+
+// z = D^-1 r ; p = z ; rho = <r, z>
+template <typename T>
+__global__ void k_cg_init(int32_t n, const T* __restrict__ r, T* __restrict__ z, T* __restrict__ p,
+                          const T* __restrict__ dinv, KState* st, double* partials,
+                          unsigned* ticket) {
+    T a[1] = {T(0)};
+    GRID_LOOP(i, n) {
+        const T ri = r[i];
+        const T zi = dinv ? dinv[i] * ri : ri;
+        if (dinv) z[i] = zi;
+        p[i] = zi;
+        a[0] = fmadd(ri, zi, a[0]);
+    }
+    finish_ew<1>(a, partials, ticket, CgInitFin{st});
+}
+
+// ---------------------------------------------------------------- BiCGSTAB
+// van der Vorst, right preconditioning (phat = M^-1 p, shat = M^-1 s).
+
+struct BiAlphaFin {
+    KState* st;
+    __device__ void operator()(double* t) const {
+        const double rv = t[0];
+        if (!isfinite(rv)) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+        } else if (rv == 0.0) {
+            st->status = GK_BREAKDOWN;
+            st->halt = 2;
+        } else {
+            st->alpha = st->rho / rv;  // rho holds rho' of this iteration
+        }
+    }
+};
+
+// beta = (rho'/rho_old)(alpha/omega) is prepared by the previous update's fin
+// p = r + beta (p - omega v) ; phat = M^-1 p
+template <typename T>
+__global__ void k_bi_p(int32_t n, T* __restrict__ p, T* __restrict__ ph, const T* __restrict__ r,
+                       const T* __restrict__ v, const T* __restrict__ dinv, const KState* st) {
+    if (halted(st)) return;
+    const T beta = (T)st->beta, omega = (T)st->omega;
+    GRID_LOOP(i, n) {
+        const T pi = fmadd(beta, fmadd(-omega, v[i], p[i]), r[i]);
+        p[i] = pi;
+        if (dinv) ph[i] = dinv[i] * pi;
+    }
+}
+
+struct BiSFin {
+    KState* st;
+    __device__ void operator()(double* t) const {
+        st->iter += 1;
+        const double sn = sqrt(t[0]);
+        st->snorm = sn;
+        if (!isfinite(sn)) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+        } else if (sn <= st->thr) {
+            st->half = 1;  // half-step exit: x += alpha phat in the next kernel
+            st->rnorm = sn;
+        }
+    }
+};
+
+// s = r - alpha v ; shat = M^-1 s ; ||s||^2
+template <typename T>
+__global__ void k_bi_s(int32_t n, T* __restrict__ s, T* __restrict__ sh, const T* __restrict__ r,
+                       const T* __restrict__ v, const T* __restrict__ dinv, KState* st,
+                       double* partials, unsigned* ticket) {
+    if (halted(st)) return;
+    const T alpha = (T)st->alpha;
+    T a[1] = {T(0)};
+    GRID_LOOP(i, n) {
+        const T si = fmadd(-alpha, v[i], r[i]);
+        s[i] = si;
+        if (dinv) sh[i] = dinv[i] * si;
+        a[0] = fmadd(si, si, a[0]);
+    }
+    finish_ew<1>(a, partials, ticket, BiSFin{st});
+}
+
+struct BiOmegaFin {
+    KState* st;
+    __device__ void operator()(double* t) const {
+        const double ts = t[0], tt = t[1];
+        if (!isfinite(ts) || !isfinite(tt)) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+        } else if (tt == 0.0) {
+            st->status = GK_BREAKDOWN;
+            st->halt = 2;
+        } else {
+            st->omega = ts / tt;
+            if (st->omega == 0.0) {
+                st->status = GK_BREAKDOWN;
+                st->halt = 2;
+            }
+        }
+    }
+};
+
+struct BiUpdFin {
+    KState* st;
+    __device__ void operator()(double* t) const {
+        if (st->half) {  // x was updated with alpha phat only
+            st->half = 0;
+            st->halt = 1;
+            return;
+        }
+        const double rho_new = t[0];
+        const double rn = sqrt(t[1]);
+        st->rnorm = rn;
+        if (!isfinite(rn) || !isfinite(rho_new)) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+            return;
+        }
+        if (rn <= st->thr) {
+            st->halt = 1;
+            return;
+        }
+        if (st->iter >= st->max_iters) {
+            st->status = GK_NOT_CONVERGED;
+            st->halt = 2;
+            return;
+        }
+        if (rho_new == 0.0) {
+            st->status = GK_BREAKDOWN;
+            st->halt = 2;
+            return;
+        }
+        st->beta = (rho_new / st->rho) * (st->alpha / st->omega);
+        st->rho = rho_new;
+    }
+};
+
+// full step: x += alpha phat + omega shat ; r = s - omega t ; <rhat, r>, <r, r>
+// half step (st->half): x += alpha phat only.
+template <typename T>
+__global__ void k_bi_update(int32_t n, T* __restrict__ x, T* __restrict__ r,
+                            const T* __restrict__ ph, const T* __restrict__ sh,
+                            const T* __restrict__ s, const T* __restrict__ t,
+                            const T* __restrict__ rh, KState* st, double* partials,
+                            unsigned* ticket) {
+    if (halted(st)) return;
+    const bool half = st->half != 0;
+    const T alpha = (T)st->alpha, omega = (T)st->omega;
+    T a[2] = {T(0), T(0)};
+    GRID_LOOP(i, n) {
+        if (half) {
+            x[i] = fmadd(alpha, ph[i], x[i]);
+        } else {
+            x[i] = fmadd(omega, sh[i], fmadd(alpha, ph[i], x[i]));
+            const T ri = fmadd(-omega, t[i], s[i]);
+            r[i] = ri;
+            a[0] = fmadd(rh[i], ri, a[0]);
+            a[1] = fmadd(ri, ri, a[1]);
+        }
+    }
+    finish_ew<2>(a, partials, ticket, BiUpdFin{st});
+}
+
+struct BiInitFin {
+    KState* st;
+    __device__ void operator()(double* t) const {
+        const double rho = t[0];
+        st->rho = rho;
+        st->alpha = 1.0;
+        st->omega = 1.0;
+        // first iteration: beta = (rho'/1)(1/1) with rho' = <rhat, r>
+        st->beta = 0.0;  // p = r exactly (p and v are zero)
+        if (rho == 0.0) {
+            st->status = GK_BREAKDOWN;
+            st->halt = 2;
+        }
+    }
+};
+
+// rhat = r ; p = v = 0 ; rho = <rhat, r>
+template <typename T>
+__global__ void k_bi_init(int32_t n, const T* __restrict__ r, T* __restrict__ rh, T* __restrict__ p,
+                          T* __restrict__ v, KState* st, double* partials, unsigned* ticket) {
+    T a[1] = {T(0)};
+    GRID_LOOP(i, n) {
+        const T ri = r[i];
+        rh[i] = ri;
+        p[i] = T(0);
+        v[i] = T(0);
+        a[0] = fmadd(ri, ri, a[0]);
+    }
+    finish_ew<1>(a, partials, ticket, BiInitFin{st});
+}
+
+// ---------------------------------------------------------------- GMRES
+// V: n x (m+1), column j at V + j*ldv.  CGS2 orthogonalisation:
+//   h1 = V^T w ; w -= V h1 ; h2 = V^T w ; w -= V h2 ; h = h1 + h2.
+
+constexpr int MD_ROWS = 2048;   // rows per block in the multi-dot kernels
+constexpr int MD_THREADS = 256;
+
+// Partial dot products of w with columns 0..k of V over a row chunk: one
+// warp per column (columns strided over warps), lanes over rows; w staged
+// in shared memory.  Writes partials[j * gridDim.x + blockIdx.x].
+template <typename T>
+__device__ void multidot_chunk(int32_t n, int64_t ldv, const T* __restrict__ V, const T* s_w,
+                               int64_t r0, int32_t rows, int32_t kk, double* partials) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j <= kk; j += nw) {
+        const T* col = V + (int64_t)j * ldv + r0;
+        T a = T(0);
+        for (int i = lane; i < rows; i += 32) a = fmadd(col[i], s_w[i], a);
+        double d = warp_sum((double)a);
+        if (lane == 0) partials[(size_t)j * gridDim.x + blockIdx.x] = d;
+    }
+}
+
+// Last block: h[j] = sum over blocks of partials[j][*] for j <= kk.
+__device__ bool multidot_finish(int32_t kk, double* partials, unsigned* ticket, double* h) {
+    __shared__ bool am_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        am_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j <= kk; j += nw) {
+        double s = 0.0;
+        for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(partials + (size_t)j * gridDim.x + b);
+        s = warp_sum(s);
+        if (lane == 0) h[j] = s;
+    }
+    __syncthreads();
+    return true;
+}
+
+// h1 = V^T w  (columns 0..k)
+template <typename T>
+__global__ void __launch_bounds__(MD_THREADS)
+k_gm_dot1(int32_t n, int64_t ldv, const T* __restrict__ V, const T* __restrict__ w, KState* st,
+          double* partials, unsigned* ticket) {
+    if (halted(st)) return;
+    __shared__ T s_w[MD_ROWS];
+    const int32_t kk = st->k;
+    const int64_t r0 = (int64_t)blockIdx.x * MD_ROWS;
+    const int32_t rows = (int32_t)(n - r0 < MD_ROWS ? n - r0 : MD_ROWS);
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) s_w[i] = w[r0 + i];
+    __syncthreads();
+    multidot_chunk(n, ldv, V, s_w, r0, rows, kk, partials);
+    if (multidot_finish(kk, partials, ticket, st->h1) && threadIdx.x == 0) *ticket = 0u;
+}
+
+// w -= V h1 ; h2 = V^T w
+template <typename T>
+__global__ void __launch_bounds__(MD_THREADS)
+k_gm_dot2(int32_t n, int64_t ldv, const T* __restrict__ V, T* __restrict__ w, KState* st,
+          double* partials, unsigned* ticket) {
+    if (halted(st)) return;
+    __shared__ T s_w[MD_ROWS];
+    __shared__ T s_h[MAXM + 1];
+    const int32_t kk = st->k;
+    for (int j = threadIdx.x; j <= kk; j += blockDim.x) s_h[j] = (T)st->h1[j];
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * MD_ROWS;
+    const int32_t rows = (int32_t)(n - r0 < MD_ROWS ? n - r0 : MD_ROWS);
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        T v = w[r0 + i];
+        for (int j = 0; j <= kk; ++j) v = fmadd(-s_h[j], V[(int64_t)j * ldv + r0 + i], v);
+        w[r0 + i] = v;
+        s_w[i] = v;
+    }
+    __syncthreads();
+    multidot_chunk(n, ldv, V, s_w, r0, rows, kk, partials);
+    if (multidot_finish(kk, partials, ticket, st->h2) && threadIdx.x == 0) *ticket = 0u;
+}
+
+// Givens step on column k, residual estimate, cycle decision and, at the
+// end of a cycle, the back substitution H y = g.
+struct GmGivensFin {
+    KState* st;
+    __device__ void operator()(double* t) const {
+        const int k = st->k, m = st->m;
+        double* H = st->H;
+        const double hk1 = sqrt(t[0]);
+        for (int j = 0; j <= k; ++j) H[j * m + k] = st->h1[j] + st->h2[j];
+        H[(k + 1) * m + k] = hk1;
+        for (int j = 0; j < k; ++j) {
+            const double a = H[j * m + k], b = H[(j + 1) * m + k];
+            H[j * m + k] = st->cs[j] * a + st->sn[j] * b;
+            H[(j + 1) * m + k] = -st->sn[j] * a + st->cs[j] * b;
+        }
+        const double a = H[k * m + k], b = H[(k + 1) * m + k];
+        const double d = hypot(a, b);
+        if (!isfinite(d)) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+            return;
+        }
+        if (d == 0.0) {
+            st->status = GK_BREAKDOWN;
+            st->halt = 2;
+            return;
+        }
+        st->v0_pending = 0;
+        st->cs[k] = a / d;
+        st->sn[k] = b / d;
+        H[k * m + k] = d;
+        H[(k + 1) * m + k] = 0.0;
+        st->g[k + 1] = -st->sn[k] * st->g[k];
+        st->g[k] = st->cs[k] * st->g[k];
+        st->iter += 1;
+        st->k = k + 1;
+        const double est = fabs(st->g[k + 1]);
+        st->rnorm = est;
+        if (!isfinite(est)) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+            return;
+        }
+        if (hk1 == 0.0 || est <= st->thr || k + 1 == m || st->iter >= st->max_iters) {
+            st->cycle_end = 1;
+            const int kk = k + 1;
+            for (int i = kk - 1; i >= 0; --i) {
+                double s = st->g[i];
+                for (int j = i + 1; j < kk; ++j) s -= H[i * m + j] * st->y[j];
+                st->y[i] = s / H[i * m + i];
+            }
+        } else {
+            st->cycle_end = 0;
+            st->inv_h = 1.0 / hk1;
+        }
+    }
+};
+
+// w -= V h2 ; ||w||^2 -> Givens fin
+template <typename T>
+__global__ void __launch_bounds__(MD_THREADS)
+k_gm_orth(int32_t n, int64_t ldv, const T* __restrict__ V, T* __restrict__ w, KState* st,
+          double* partials, unsigned* ticket) {
+    if (halted(st)) return;
+    __shared__ T s_h[MAXM + 1];
+    const int32_t kk = st->k;
+    for (int j = threadIdx.x; j <= kk; j += blockDim.x) s_h[j] = (T)st->h2[j];
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * MD_ROWS;
+    const int32_t rows = (int32_t)(n - r0 < MD_ROWS ? n - r0 : MD_ROWS);
+    T a[1] = {T(0)};
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        T v = w[r0 + i];
+        for (int j = 0; j <= kk; ++j) v = fmadd(-s_h[j], V[(int64_t)j * ldv + r0 + i], v);
+        w[r0 + i] = v;
+        a[0] = fmadd(v, v, a[0]);
+    }
+    finish_ew<1>(a, partials, ticket, GmGivensFin{st});
+}
+
+// not at the end of a cycle: v_{k} = w / h ; z = M^-1 v_k
+// at the end of a cycle:     x += M^-1 (V y)
+template <typename T>
+__global__ void k_gm_next(int32_t n, int64_t ldv, T* __restrict__ V, const T* __restrict__ w,
+                          T* __restrict__ z, T* __restrict__ x, const T* __restrict__ dinv,
+                          const KState* st) {
+    if (halted(st)) return;
+    const int32_t k = st->k;
+    if (!st->cycle_end) {
+        const T ih = (T)st->inv_h;
+        T* vk = V + (int64_t)k * ldv;
+        GRID_LOOP(i, n) {
+            const T v = w[i] * ih;
+            vk[i] = v;
+            z[i] = dinv ? dinv[i] * v : v;
+        }
+    } else {
+        __shared__ T s_y[MAXM];
+        for (int j = threadIdx.x; j < k; j += blockDim.x) s_y[j] = (T)st->y[j];
+        __syncthreads();
+        GRID_LOOP(i, n) {
+            T u = T(0);
+            for (int j = 0; j < k; ++j) u = fmadd(V[(int64_t)j * ldv + i], s_y[j], u);
+            x[i] = fmadd(dinv ? dinv[i] : T(1), u, x[i]);
+        }
+    }
+}
+
+// Cycle start (fin of the true residual r = b - A x): converged, out of
+// steps, or v_0 = r / beta0 and g = beta0 e_1.
+struct GmRestartFin {
+    KState* st;
+    __device__ void operator()(double* t) const {
+        const double b0 = sqrt(t[0]);
+        st->tnorm = b0;
+        st->beta0 = b0;
+        if (!isfinite(b0)) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+            return;
+        }
+        if (b0 <= st->thr) {
+            st->status = GK_OK;
+            st->halt = 2;
+            return;
+        }
+        if (st->iter >= st->max_iters) {
+            st->status = GK_NOT_CONVERGED;
+            st->halt = 2;
+            return;
+        }
+        if (st->cycle_end) st->restarts += 1;  // a cycle ended and a new one starts
+        for (int j = 0; j <= st->m; ++j) st->g[j] = 0.0;
+        st->g[0] = b0;
+        st->k = 0;
+        st->cycle_end = 0;
+        st->inv_h = 1.0 / b0;
+        st->v0_pending = 1;
+    }
+};
+
+// true residual at cycle end (skipped inside a cycle)
+template <typename T>
+struct EpiGmResid {
+    T* __restrict__ r;
+    const T* __restrict__ b;
+    const KState* st;
+    double* partials;
+    unsigned* ticket;
+    GmRestartFin fin;
+    static constexpr int NA = 1;
+    __device__ __forceinline__ bool skip() const {
+        return halted(st) || !*reinterpret_cast<const volatile int32_t*>(&st->cycle_end);
+    }
+    __device__ __forceinline__ void row(int64_t i, T s, double* acc) const {
+        const T v = b[i] - s;
+        r[i] = v;
+        acc[0] = fma((double)v, (double)v, acc[0]);
+    }
+    __device__ __forceinline__ void finish(double* acc) const {
+        double a[1] = {acc[0]};
+        grid_reduce_finish<1>(a, partials, ticket, fin);
+    }
+};
+
+// v_0 = r / beta0 ; z = M^-1 v_0 (after a restart decided to continue)
+template <typename T>
+__global__ void k_gm_v0(int32_t n, T* __restrict__ V, const T* __restrict__ r, T* __restrict__ z,
+                        const T* __restrict__ dinv, const KState* st) {
+    if (halted(st) || !st->v0_pending) return;
+    const T ib = (T)st->inv_h;
+    GRID_LOOP(i, n) {
+        const T v = r[i] * ib;
+        V[i] = v;
+        z[i] = dinv ? dinv[i] * v : v;
+    }
+}
+
+
+// Jacobi diagonal of ELL / SELL-P matrices (first stored entry with col == i)
+template <typename V, typename T>
+__global__ void k_jacobi_gen_padded(int32_t n, int fmt, int64_t stride, int32_t K, int32_t S,
+                                    const int32_t* __restrict__ slen,
+                                    const int64_t* __restrict__ sset,
+                                    const int32_t* __restrict__ pc, const V* __restrict__ pv,
+                                    T* __restrict__ dinv, int32_t* bad) {
+    GRID_LOOP(i, n) {
+        T d = T(0);
+        bool found = false;
+        if (fmt == GK_ELL) {
+            for (int32_t j = 0; j < K; ++j) {
+                const int64_t at = (int64_t)j * stride + i;
+                if (pc[at] == i) { d += cvt<T>(pv[at]); found = true; }
+            }
+        } else {
+            const int64_t sl = i / S, t = i - sl * S;
+            for (int32_t j = 0; j < slen[sl]; ++j) {
+                const int64_t at = (sset[sl] + j) * S + t;
+                if (pc[at] == i) { d += cvt<T>(pv[at]); found = true; }
+            }
+        }
+        if (!found || d == T(0)) {
+            atomicOr(bad, 1);
+            dinv[i] = T(0);
+        } else {
+            dinv[i] = T(1) / d;
+        }
+    }
+}
+
+// Setup fins: ||b|| -> thr; initial true residual
+struct FinBnorm {
+    KState* st;
+    double tol;
+    __device__ void operator()(double* t) const {
+        const double bn = sqrt(t[0]);
+        st->bnorm = bn;
+        st->thr = tol * bn;
+        if (!isfinite(bn)) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+        } else if (bn == 0.0) {
+            st->status = GK_OK;
+            st->halt = 2;
+        }
+    }
+};
+
+struct FinTrue {  // true residual norm; mode 0: initial check, 1: recheck
+    KState* st;
+    int mode;
+    __device__ void operator()(double* t) const {
+        const double tn = sqrt(t[0]);
+        st->tnorm = tn;
+        if (mode == 0) st->rnorm = tn;
+        if (!isfinite(tn)) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+        } else if (tn <= st->thr) {
+            st->status = GK_OK;
+            st->halt = 2;
+        }
+    }
+};
+
+// EpiTResid: true residual with a fin but no halt check
+template <typename T, class Fin>
+using EpiRes = EpiResid<T, Fin>;
+
+// BiCGSTAB t = A shat, skipped at a half-step exit
+template <typename T>
+struct EpiBiT {
+    T* __restrict__ y;
+    const T* __restrict__ u;
+    const KState* st;
+    double* partials;
+    unsigned* ticket;
+    BiOmegaFin fin;
+    static constexpr int NA = 2;
+    __device__ __forceinline__ bool skip() const {
+        return halted(st) || *reinterpret_cast<const volatile int32_t*>(&st->half) != 0;
+    }
+    __device__ __forceinline__ void row(int64_t i, T s, double* acc) const {
+        y[i] = s;
+        acc[0] = fma((double)s, (double)u[i], acc[0]);
+        acc[1] = fma((double)s, (double)s, acc[1]);
+    }
+    __device__ __forceinline__ void finish(double* acc) const {
+        double a[2] = {acc[0], acc[1]};
+        grid_reduce_finish<2>(a, partials, ticket, fin);
+    }
+};
+
+template <typename T>
+__global__ void k_cast_add(int32_t n, double* __restrict__ x, const T* __restrict__ d) {
+    GRID_LOOP(i, n) x[i] += (double)d[i];
+}
+template <typename T>
+__global__ void k_cast_to(int32_t n, const double* __restrict__ r, T* __restrict__ o) {
+    GRID_LOOP(i, n) o[i] = (T)r[i];
+}
+
+// ------------------------------------------------------------ host side
+
+constexpr size_t HDR = offsetof(KState, H);
+
+struct SolverCache {
+    DevBuf vecs, partials, ticket, state;
+    KState* hst = nullptr;  // pinned mirror of the state header
+    int32_t* hzero = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // key of the captured graph
+    const void* kb = nullptr;
+    void* kx = nullptr;
+    void* kv = nullptr;
+    int kmethod = -1, kprec = -1, km = -1, kchunk = 0;
+    ~SolverCache() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (hst) cudaFreeHost(hst);
+        if (hzero) cudaFreeHost(hzero);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        vecs.release();
+        partials.release();
+        ticket.release();
+        state.release();
+    }
+};
+
+void free_solver_cache(gk_matrix A) {
+    delete A->solver;
+    A->solver = nullptr;
+}
+
+static gk_status get_cache(gk_matrix A, SolverCache** out) {
+    if (!A->solver) {
+        SolverCache* C = new (std::nothrow) SolverCache();
+        if (!C) return GK_ERR_OOM;
+        A->solver = C;
+        GK_CUDA(cudaMallocHost(&C->hst, sizeof(KState)));
+        GK_CUDA(cudaMallocHost(&C->hzero, 64));
+        std::memset(C->hzero, 0, 64);
+        GK_TRY(C->ticket.ensure(256));
+        GK_CUDA(cudaMemset(C->ticket.ptr, 0, 256));
+        GK_TRY(C->state.ensure(sizeof(KState)));
+        GK_CUDA(cudaEventCreate(&C->ev0));
+        GK_CUDA(cudaEventCreate(&C->ev1));
+    }
+    *out = A->solver;
+    return GK_OK;
+}
+
+gk_status ensure_jacobi(gk_matrix A, cudaStream_t s) {
+    if (A->dinv_state == 1) return GK_OK;
+    if (A->dinv_state == -1) return GK_ERR_ZERO_DIAG;
+    const size_t vb = vector_bytes(A->dtype);
+    GK_CUDA(dmalloc(&A->dinv, vb * (size_t)std::max(A->n, 1)));
+    DevBuf bad;
+    GK_TRY(bad.ensure(16));
+    GK_CUDA(cudaMemsetAsync(bad.ptr, 0, 16, s));
+    const unsigned g = ew_grid(A->n);
+    auto go = [&](auto vt, auto tt) {
+        using V = decltype(vt);
+        using T = decltype(tt);
+        if (A->fmt == GK_CSR)
+            k_jacobi_gen<V, T><<<g, 256, 0, s>>>(A->n, A->row_ptr, A->col, (const V*)A->val,
+                                                 (T*)A->dinv, (int32_t*)bad.ptr);
+        else
+            k_jacobi_gen_padded<V, T><<<g, 256, 0, s>>>(A->n, A->fmt, A->stride, A->K, A->S,
+                                                        A->slice_len, A->slice_set, A->col,
+                                                        (const V*)A->val, (T*)A->dinv,
+                                                        (int32_t*)bad.ptr);
+    };
+    if (A->n > 0) {
+        if (A->dtype == GK_F64) go(double(), double());
+        else if (A->dtype == GK_F32) go(float(), float());
+        else go(__nv_bfloat16(), float());
+    }
+    GK_CUDA(cudaGetLastError());
+    int32_t h = 0;
+    GK_CUDA(cudaMemcpyAsync(&h, bad.ptr, 4, cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        A->dinv_state = -1;
+        return GK_ERR_ZERO_DIAG;
+    }
+    A->dinv_state = 1;
+    return GK_OK;
+}
+
+gk_status get_lowp(gk_matrix A, gk_dtype d, cudaStream_t s, gk_matrix* out) {
+    if (A->dtype == d) {
+        *out = A;
+        return GK_OK;
+    }
+    if (!A->lowp[d]) {
+        gk_matrix B = nullptr;
+        GK_TRY(gk_matrix_convert(A, A->fmt, d, A->S, A->f, s, &B));
+        A->lowp[d] = B;
+    }
+    *out = A->lowp[d];
+    return GK_OK;
+}
+
+static gk_status side_stream(gk_matrix A) {
+    if (!A->side) GK_CUDA(cudaStreamCreateWithFlags(&A->side, cudaStreamNonBlocking));
+    return GK_OK;
+}
+
+template <typename T>
+static T* vec_at(SolverCache* C, int64_t n, int idx) {
+    const size_t stride = ((size_t)n * sizeof(T) + 255) & ~(size_t)255;
+    return reinterpret_cast<T*>(static_cast<char*>(C->vecs.ptr) + stride * (size_t)idx);
+}
+
+template <typename T>
+static gk_status ensure_vecs(SolverCache* C, int64_t n, int count) {
+    const size_t stride = ((size_t)n * sizeof(T) + 255) & ~(size_t)255;
+    return C->vecs.ensure(stride * (size_t)count + 256);
+}
+
+static gk_status read_hdr(SolverCache* C, cudaStream_t s) {
+    GK_CUDA(cudaMemcpyAsync(C->hst, C->state.ptr, HDR, cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    return GK_OK;
+}
+
+static gk_status clear_halt(SolverCache* C, cudaStream_t s) {
+    KState* st = (KState*)C->state.ptr;
+    GK_CUDA(cudaMemcpyAsync(&st->halt, C->hzero, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    return GK_OK;
+}
+
+// Capture `chunk` iterations of `body` into C->exec (cached by key).
+template <class Body>
+static gk_status capture_chunk(gk_matrix A, SolverCache* C, int chunk, Body&& body) {
+    GK_TRY(side_stream(A));
+    if (C->exec) {
+        cudaGraphExecDestroy(C->exec);
+        C->exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    GK_CUDA(cudaStreamBeginCapture(A->side, cudaStreamCaptureModeThreadLocal));
+    gk_status st = GK_OK;
+    for (int c = 0; c < chunk && st == GK_OK; ++c) st = body(A->side);
+    cudaError_t e = cudaStreamEndCapture(A->side, &g);
+    if (st != GK_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    GK_CUDA(e);
+    e = cudaGraphInstantiate(&C->exec, g, 0);
+    cudaGraphDestroy(g);
+    GK_CUDA(e);
+    return GK_OK;
+}
+
+static int chunk_for(int64_t n) { return n < 200000 ? 32 : 8; }
+
+
+// Runs one Krylov solve on the multi-kernel engine.  b, x: device vectors
+// of type T.  Result status and counters in *out.
+template <typename V, typename T>
+static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, double tol,
+                          int32_t max_iters, int32_t m, cudaStream_t s, SolveOut* out) {
+    const int32_t n = A->n;
+    SolverCache* C = nullptr;
+    GK_TRY(get_cache(A, &C));
+    const T* dinv = nullptr;
+    if (prec) {
+        GK_TRY(ensure_jacobi(A, s));
+        dinv = (const T*)A->dinv;
+    }
+    const int nvec = method == GK_CG ? 5 : method == GK_BICGSTAB ? 9 : m + 4;
+    GK_TRY(ensure_vecs<T>(C, n, nvec));
+    const unsigned md_grid = (unsigned)std::max<int64_t>(1, ((int64_t)n + MD_ROWS - 1) / MD_ROWS);
+    const size_t pcount = (size_t)std::max<unsigned>(num_sms() * 8, md_grid) * (size_t)(MAXM + 2);
+    GK_TRY(C->partials.ensure(pcount * sizeof(double)));
+    double* part = (double*)C->partials.ptr;
+    unsigned* tk = (unsigned*)C->ticket.ptr;
+    KState* st = (KState*)C->state.ptr;
+    const int32_t* halt = &st->halt;
+    const unsigned eg = ew_grid(n);
+
+    // state header
+    KState* h = C->hst;
+    std::memset(h, 0, HDR);
+    h->max_iters = max_iters;
+    h->m = m;
+    GK_CUDA(cudaMemcpyAsync(st, h, HDR, cudaMemcpyHostToDevice, s));
+    k_norm2<T, FinBnorm><<<eg, 256, 0, s>>>(n, b, part, tk, FinBnorm{st, tol});
+    GK_CUDA(cudaGetLastError());
+
+    T *r = vec_at<T>(C, n, 0), *tmp = vec_at<T>(C, n, 1);
+    if (method == GK_GMRES) {
+        T* Vm = vec_at<T>(C, n, 3);
+        T *w = vec_at<T>(C, n, 1), *z = vec_at<T>(C, n, 2);
+        const int64_t ldv = (int64_t)(((size_t)n * sizeof(T) + 255) & ~(size_t)255) / sizeof(T);
+        // cycle start: r = b - A x, restart fin sets g, k; v0 = r / beta0
+        EpiResid<T, GmRestartFin> e0{r, b, halt, part, tk, GmRestartFin{st}};
+        GK_TRY((launch_spmv_rows<V, T>(A, x, e0, s)));
+        k_gm_v0<T><<<eg, 256, 0, s>>>(n, Vm, r, z, dinv, st);
+        GK_CUDA(cudaGetLastError());
+        const int chunk = chunk_for(n);
+        if (!C->exec || C->kb != b || C->kx != x || C->kmethod != method || C->kprec != (int)prec ||
+            C->km != m || C->kchunk != chunk || C->kv != (void*)C->vecs.ptr) {
+            GK_TRY(capture_chunk(A, C, chunk, [&](cudaStream_t cs) -> gk_status {
+                EpiStoreHalt<T> e1{w, halt};
+                GK_TRY((launch_spmv_rows<V, T>(A, z, e1, cs)));
+                k_gm_dot1<T><<<md_grid, MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st, part, tk);
+                k_gm_dot2<T><<<md_grid, MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st, part, tk);
+                k_gm_orth<T><<<md_grid, MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st, part, tk);
+                k_gm_next<T><<<eg, 256, 0, cs>>>(n, ldv, Vm, w, z, x, dinv, st);
+                EpiGmResid<T> e2{r, b, st, part, tk, GmRestartFin{st}};
+                GK_TRY((launch_spmv_rows<V, T>(A, x, e2, cs)));
+                k_gm_v0<T><<<eg, 256, 0, cs>>>(n, Vm, r, z, dinv, st);
+                GK_CUDA(cudaGetLastError());
+                return GK_OK;
+            }));
+            C->kb = b; C->kx = x; C->kmethod = method; C->kprec = prec; C->km = m;
+            C->kchunk = chunk; C->kv = C->vecs.ptr;
+        }
+        GK_TRY(read_hdr(C, s));
+        // every chunk advances the step counter unless halted: bound the loop
+        int64_t chunks_left = (int64_t)max_iters / chunk + 4;
+        while (!C->hst->halt) {
+            if (--chunks_left < 0) return GK_ERR_TIMEOUT;
+            GK_CUDA(cudaGraphLaunch(C->exec, s));
+            GK_TRY(read_hdr(C, s));
+        }
+    } else {
+        // initial true residual r = b - A x (stops at once when it passes)
+        EpiResid<T, FinTrue> e0{r, b, halt, part, tk, FinTrue{st, 0}};
+        GK_TRY((launch_spmv_rows<V, T>(A, x, e0, s)));
+        auto init = [&]() -> gk_status {
+            if (method == GK_CG)  // slots: 0 r, 1 tmp, 2 q, 3 p, 4 z
+                k_cg_init<T><<<eg, 256, 0, s>>>(n, r, vec_at<T>(C, n, 4), vec_at<T>(C, n, 3), dinv,
+                                                st, part, tk);
+            else
+                // slots: 0 r, 1 tmp, 2 rhat, 3 p, 4 phat, 5 s, 6 v, 7 shat, 8 t
+                k_bi_init<T><<<eg, 256, 0, s>>>(n, r, vec_at<T>(C, n, 2), vec_at<T>(C, n, 3),
+                                                vec_at<T>(C, n, 6), st, part, tk);
+            GK_CUDA(cudaGetLastError());
+            return GK_OK;
+        };
+        GK_TRY(init());
+        const int chunk = chunk_for(n);
+        if (!C->exec || C->kb != b || C->kx != x || C->kmethod != method || C->kprec != (int)prec ||
+            C->kchunk != chunk || C->kv != (void*)C->vecs.ptr) {
+            GK_TRY(capture_chunk(A, C, chunk, [&](cudaStream_t cs) -> gk_status {
+                if (method == GK_CG) {
+                    T *z = prec ? vec_at<T>(C, n, 4) : r, *p = vec_at<T>(C, n, 3),
+                      *q = vec_at<T>(C, n, 2);
+                    EpiDot<T, CgAlphaFin> e1{q, p, halt, part, tk, CgAlphaFin{st}};
+                    GK_TRY((launch_spmv_rows<V, T>(A, p, e1, cs)));
+                    k_cg_update<T><<<eg, 256, 0, cs>>>(n, x, r, z, p, q, dinv, st, part, tk);
+                    k_cg_p<T><<<eg, 256, 0, cs>>>(n, p, z, st);
+                } else {
+                    T *rh = vec_at<T>(C, n, 2), *p = vec_at<T>(C, n, 3), *ph = vec_at<T>(C, n, 4);
+                    T *v = vec_at<T>(C, n, 6), *sv = vec_at<T>(C, n, 5), *sh = vec_at<T>(C, n, 7);
+                    T* t = vec_at<T>(C, n, 8);
+                    const T* phs = prec ? ph : p;
+                    const T* shs = prec ? sh : sv;
+                    k_bi_p<T><<<eg, 256, 0, cs>>>(n, p, ph, r, v, dinv, st);
+                    EpiDot<T, BiAlphaFin> e1{v, rh, halt, part, tk, BiAlphaFin{st}};
+                    GK_TRY((launch_spmv_rows<V, T>(A, phs, e1, cs)));
+                    k_bi_s<T><<<eg, 256, 0, cs>>>(n, sv, sh, r, v, dinv, st, part, tk);
+                    EpiBiT<T> e2{t, sv, st, part, tk, BiOmegaFin{st}};
+                    GK_TRY((launch_spmv_rows<V, T>(A, shs, e2, cs)));
+                    k_bi_update<T><<<eg, 256, 0, cs>>>(n, x, r, phs, shs, sv, t, rh, st, part, tk);
+                }
+                GK_CUDA(cudaGetLastError());
+                return GK_OK;
+            }));
+            C->kb = b; C->kx = x; C->kmethod = method; C->kprec = prec; C->km = m;
+            C->kchunk = chunk; C->kv = C->vecs.ptr;
+        }
+        GK_TRY(read_hdr(C, s));
+        int64_t chunks_left = (int64_t)max_iters / chunk + 4;
+        int64_t checks_left = (int64_t)max_iters + 4;
+        for (;;) {
+            if (C->hst->halt == 2) break;
+            if (--chunks_left < 0 || checks_left < 0) return GK_ERR_TIMEOUT;
+            if (C->hst->halt == 1) {
+                // recurrence passed: check the true residual
+                ++chunks_left;
+                --checks_left;
+                GK_TRY(clear_halt(C, s));
+                EpiResid<T, FinTrue> et{tmp, b, halt, part, tk, FinTrue{st, 1}};
+                GK_TRY((launch_spmv_rows<V, T>(A, x, et, s)));
+                GK_TRY(read_hdr(C, s));
+                if (C->hst->halt == 2) break;
+                if (C->hst->iter >= max_iters) {
+                    out->status = GK_NOT_CONVERGED;
+                    break;
+                }
+                // residual replacement and restart from x
+                k_copy<T><<<eg, 256, 0, s>>>(n, tmp, r);
+                GK_TRY(init());
+                C->hst->restarts += 1;
+                GK_CUDA(cudaMemcpyAsync(&st->restarts, &C->hst->restarts, 4, cudaMemcpyHostToDevice, s));
+                GK_TRY(read_hdr(C, s));
+                continue;
+            }
+            GK_CUDA(cudaGraphLaunch(C->exec, s));
+            GK_TRY(read_hdr(C, s));
+        }
+    }
+    const KState* hs = C->hst;
+    if (out->status == GK_OK) out->status = (gk_status)hs->status;
+    if (hs->halt == 2 && hs->status == GK_OK) out->status = GK_OK;
+    out->iters = hs->iter;
+    out->restarts = hs->restarts;
+    out->rec = hs->bnorm > 0 ? hs->rnorm / hs->bnorm : 0.0;
+    // true residual at exit
+    if (hs->bnorm > 0) {
+        EpiResid<T, FinNorm> ef{tmp, b, nullptr, part, tk, FinNorm{st, 1}};
+        GK_TRY((launch_spmv_rows<V, T>(A, x, ef, s)));
+        GK_TRY(read_hdr(C, s));
+        out->tru = C->hst->tnorm / C->hst->bnorm;
+    } else {
+        k_zero<T><<<eg, 256, 0, s>>>(n, x);
+        GK_CUDA(cudaGetLastError());
+        out->status = GK_OK;
+        out->iters = 0;
+        out->tru = out->rec = 0.0;
+    }
+    return GK_OK;
+}
+
+}  // namespace gk
+
+// ---------------------------------------------------------------- entry points
+namespace gk {
+
+static gk_status check_opts(gk_matrix A, const gk_solve_opts* o) {
+    if (!o) return GK_ERR_INVALID;
+    if (o->method != GK_CG && o->method != GK_BICGSTAB && o->method != GK_GMRES) return GK_ERR_INVALID;
+    if (o->precond != GK_PRECOND_NONE && o->precond != GK_PRECOND_JACOBI) return GK_ERR_INVALID;
+    if (!(o->tol >= 0.0) || o->max_iters < 0) return GK_ERR_INVALID;
+    if (o->krylov_dim < 0 || o->krylov_dim > MAXM) return GK_ERR_INVALID;
+    if (o->mixed < 0 || o->mixed > 2) return GK_ERR_INVALID;
+    if (o->mixed && A->dtype != GK_F64) return GK_ERR_INVALID;
+    if (A->n != A->ncols) return GK_ERR_INVALID;
+    return GK_OK;
+}
+
+template <typename V, typename T>
+static gk_status solve_plain(gk_matrix A, const void* b, void* x, const gk_solve_opts* o,
+                             cudaStream_t s, SolveOut* out) {
+    const int m = o->method == GK_GMRES ? (o->krylov_dim ? o->krylov_dim : 30) : 0;
+    return solve_mk<V, T>(A, (const T*)b, (T*)x, o->method, o->precond == GK_PRECOND_JACOBI,
+                          o->tol, o->max_iters, m, s, out);
+}
+
+// FP64 iterative refinement: r = b - A x in FP64; inner solve of
+// A_low d = r (FP32 or BF16-stored values, FP32 vectors) to inner_tol;
+// x += d in FP64; until ||b - A x|| <= tol ||b||.
+static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solve_opts* o,
+                          cudaStream_t s, SolveOut* out, int32_t* outer) {
+    const int32_t n = A->n;
+    gk_matrix L = nullptr;
+    GK_TRY(get_lowp(A, o->mixed == 2 ? GK_BF16 : GK_F32, s, &L));
+    SolverCache* C = nullptr;
+    GK_TRY(get_cache(A, &C));
+    // FP64 workspace: r64 ; FP32: r32, d32 (in the low-precision handle's cache
+    // the inner solver keeps its own vectors)
+    const size_t s64 = ((size_t)n * 8 + 255) & ~(size_t)255;
+    const size_t s32 = ((size_t)n * 4 + 255) & ~(size_t)255;
+    GK_TRY(C->vecs.ensure(s64 + 2 * s32 + 256));
+    double* r64 = (double*)C->vecs.ptr;
+    float* r32 = (float*)((char*)C->vecs.ptr + s64);
+    float* d32 = (float*)((char*)C->vecs.ptr + s64 + s32);
+    const size_t pcount = (size_t)num_sms() * 8 * 4;
+    GK_TRY(C->partials.ensure(pcount * sizeof(double)));
+    double* part = (double*)C->partials.ptr;
+    unsigned* tk = (unsigned*)C->ticket.ptr;
+    KState* st = (KState*)C->state.ptr;
+    const unsigned eg = ew_grid(n);
+    KState* h = C->hst;
+    std::memset(h, 0, HDR);
+    GK_CUDA(cudaMemcpyAsync(st, h, HDR, cudaMemcpyHostToDevice, s));
+    k_norm2<double, FinBnorm><<<eg, 256, 0, s>>>(n, b, part, tk, FinBnorm{st, o->tol});
+    GK_TRY(read_hdr(C, s));
+    const double bnorm = C->hst->bnorm, thr = C->hst->thr;
+    if (!(bnorm > 0.0)) {
+        if (bnorm == 0.0) {
+            k_zero<double><<<eg, 256, 0, s>>>(n, x);
+            GK_CUDA(cudaGetLastError());
+            out->status = GK_OK;
+            return GK_OK;
+        }
+        out->status = GK_ERR_NAN;
+        return GK_OK;
+    }
+    const int max_outer = o->max_outer > 0 ? o->max_outer : 50;
+    const double inner_tol = o->inner_tol > 0 ? o->inner_tol : 1e-4;
+    const int m = o->method == GK_GMRES ? (o->krylov_dim ? o->krylov_dim : 30) : 0;
+    int32_t total_inner = 0, restarts = 0;
+    double tn = 0.0, last_rec = 0.0;
+    gk_status status = GK_NOT_CONVERGED;
+    int k = 0;
+    for (;; ++k) {
+        // r = b - A x in FP64 (and its norm)
+        std::memset(h, 0, HDR);
+        h->thr = thr;
+        h->bnorm = bnorm;
+        GK_CUDA(cudaMemcpyAsync(st, h, HDR, cudaMemcpyHostToDevice, s));
+        EpiResid<double, FinNorm> er{r64, b, nullptr, part, tk, FinNorm{st, 1}};
+        GK_TRY((launch_spmv_rows<double, double>(A, x, er, s)));
+        GK_TRY(read_hdr(C, s));
+        tn = C->hst->tnorm;
+        if (!std::isfinite(tn)) {
+            status = GK_ERR_NAN;
+            break;
+        }
+        if (tn <= thr) {
+            status = GK_OK;
+            break;
+        }
+        if (k >= max_outer || total_inner >= o->max_iters) break;
+        k_cast_to<float><<<eg, 256, 0, s>>>(n, r64, r32);
+        k_zero<float><<<eg, 256, 0, s>>>(n, d32);
+        GK_CUDA(cudaGetLastError());
+        SolveOut io;
+        const bool prec = o->precond == GK_PRECOND_JACOBI;
+        const int32_t left = o->max_iters - total_inner;
+        if (L->dtype == GK_F32)
+            GK_TRY((solve_mk<float, float>(L, r32, d32, o->method, prec, inner_tol, left, m, s, &io)));
+        else
+            GK_TRY((solve_mk<__nv_bfloat16, float>(L, r32, d32, o->method, prec, inner_tol, left, m, s, &io)));
+        total_inner += io.iters;
+        restarts += io.restarts;
+        last_rec = io.rec;
+        if (io.status == GK_BREAKDOWN || io.status == GK_ERR_NAN || io.status < GK_ERR_NAN) {
+            status = io.status;
+            break;
+        }
+        k_cast_add<float><<<eg, 256, 0, s>>>(n, x, d32);
+        GK_CUDA(cudaGetLastError());
+    }
+    out->status = status;
+    out->iters = total_inner;
+    out->restarts = restarts;
+    out->rec = last_rec;
+    out->tru = tn / bnorm;
+    *outer = k;
+    return GK_OK;
+}
+
+gk_status solve_small(gk_matrix A, const void* b, void* x, const gk_solve_opts* o, cudaStream_t s,
+                      SolveOut* out);
+
+}  // namespace gk
+
+using namespace gk;
+
+extern "C" gk_status gk_solve(gk_matrix A, const void* b, void* x, const gk_solve_opts* opts,
+                              gk_solve_info* info, void* stream) {
+    if (!A || !opts) return GK_ERR_INVALID;
+    if (A->n > 0 && (!b || !x)) return GK_ERR_INVALID;
+    GK_TRY(check_opts(A, opts));
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != A->device) return GK_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(A->mu);
+    SolveOut out;
+    int32_t outer = 0;
+    SolverCache* C = nullptr;
+    GK_TRY(get_cache(A, &C));
+    GK_CUDA(cudaEventRecord(C->ev0, s));
+    gk_status st = GK_OK;
+    if (A->n == 0) {
+        out.status = GK_OK;
+    } else if (opts->mixed) {
+        st = solve_ir(A, (const double*)b, (double*)x, opts, s, &out, &outer);
+    } else {
+        const bool small = opts->engine == 2;
+        if (small) {
+            st = solve_small(A, b, x, opts, s, &out);
+        } else if (A->dtype == GK_F64) {
+            st = solve_plain<double, double>(A, b, x, opts, s, &out);
+        } else if (A->dtype == GK_F32) {
+            st = solve_plain<float, float>(A, b, x, opts, s, &out);
+        } else {
+            st = solve_plain<__nv_bfloat16, float>(A, b, x, opts, s, &out);
+        }
+    }
+    GK_CUDA(cudaEventRecord(C->ev1, s));
+    GK_CUDA(cudaEventSynchronize(C->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, C->ev0, C->ev1);
+    if (st != GK_OK) {
+        if (info) info->status = st;
+        return st;
+    }
+    if (info) {
+        info->status = out.status;
+        info->iters = out.iters;
+        info->restarts = out.restarts;
+        info->outer_iters = outer;
+        info->rel_res_recurrence = out.rec;
+        info->rel_res_true = out.tru;
+        info->device_ms = ms;
+    }
+    return out.status;
+}

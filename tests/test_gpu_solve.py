@@ -1,0 +1,213 @@
+"""GPU Krylov solvers against the CPU oracle, through the C ABI.
+
+Solver parity (several iterates are correct, rounding differs): (i) the
+true relative residual ||b - A x|| / ||b||, recomputed by the oracle's FP64
+SpMV from the GPU's x, is <= tol; (ii) the iteration count is within
+max(3, 10 %) of the oracle's for CG and within max(one restart cycle,
+10 %) for GMRES.  ||x - x_oracle|| / ||x_oracle|| is reported, not gated."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2510_08230_gb300 as gk
+from paper_2510_08230_gb300 import workloads as W
+from gpu_util import ensure_built, torch_dev
+
+pytestmark = pytest.mark.gpu
+
+METHOD = {"cg": oracle.CG, "bicgstab": oracle.BICGSTAB, "gmres": oracle.GMRES}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def _convdiff_1d(n, peclet):
+    lo, di, up = -1.0 - peclet, 2.0, -1.0 + peclet
+    rp, ci, va = [0], [], []
+    for i in range(n):
+        if i > 0:
+            ci.append(i - 1); va.append(lo)
+        ci.append(i); va.append(di)
+        if i < n - 1:
+            ci.append(i + 1); va.append(up)
+        rp.append(len(ci))
+    return W.CSR(n, n, np.array(rp), np.array(ci), np.array(va))
+
+
+def _gpu_solve(m, b, method, precond, tol, max_iters=5000, fmt="csr", dtype="f64", x0=None,
+               engine=0, **kw):
+    import torch
+    dev = torch_dev()
+    A = gk.Matrix.from_csr(m, dtype if dtype != "mixed" else "f64")
+    if fmt != "csr":
+        B = A.convert(fmt)
+        A.close()
+        A = B
+    vt = torch.float64 if dtype in ("f64", "mixed") else torch.float32
+    bt = torch.from_numpy(np.asarray(b)).to(dev, vt)
+    xt = torch.zeros(m.n, dtype=vt, device=dev) if x0 is None else \
+        torch.from_numpy(np.asarray(x0)).to(dev, vt)
+    info = A.solve(bt, xt, method=method, precond=precond, tol=tol, max_iters=max_iters,
+                   engine=engine, **kw)
+    torch.cuda.synchronize()
+    x = xt.cpu().numpy().astype(np.float64)
+    A.close()
+    return x, info
+
+
+def _check(m, b, method, precond, tol, fmt="csr", krylov_dim=30, iters_gate=True, **kw):
+    x, info = _gpu_solve(m, b, method, 1 if precond else 0, tol, fmt=fmt,
+                         krylov_dim=krylov_dim, **kw)
+    assert info["return"] == gk.GK_OK, info
+    rel = oracle.true_rel_residual(m, b, x)
+    assert rel <= tol, (rel, info)
+    xo, io = oracle.solve(m, b, method=METHOD[method], precond=1 if precond else 0, tol=tol,
+                          max_iters=5000, krylov_dim=krylov_dim)
+    assert io["status"] == oracle.OK
+    if iters_gate:
+        if method == "gmres":
+            # one restart cycle, or 10 % when rounding differences between
+            # CGS2 (GPU) and MGS (oracle) compound over many cycles
+            assert abs(info["iters"] - io["iters"]) <= max(krylov_dim, 0.1 * io["iters"]), (info, io)
+        else:
+            assert abs(info["iters"] - io["iters"]) <= max(3, 0.1 * io["iters"]), (info, io)
+    assert abs(info["rel_res_true"] - rel) <= 1e-3 * max(rel, 1e-16) + 1e-15
+    return x, info, xo, io
+
+
+CASES = {
+    "lap2d_64": lambda: (W.laplacian_2d(64), W.uniform_vector(4096, W.SEED_BASE + 1)),
+    "diff3d_12": lambda: (W.diffusion_3d(12, seed=4), W.uniform_vector(12 ** 3, 5)),
+    "convdiff_300": lambda: (_convdiff_1d(300, 0.3), W.uniform_vector(300, 6)),
+    "banded_2000": lambda: (W.banded_spd(2000, 9, 2), W.uniform_vector(2000, 7)),
+}
+
+
+@pytest.mark.parametrize("case", ["lap2d_64", "diff3d_12", "banded_2000"])
+@pytest.mark.parametrize("precond", [False, True])
+def test_cg(case, precond):
+    m, b = CASES[case]()
+    _check(m, b, "cg", precond, 1e-10)
+
+
+@pytest.mark.parametrize("case", ["lap2d_64", "diff3d_12", "convdiff_300"])
+@pytest.mark.parametrize("precond", [False, True])
+def test_bicgstab(case, precond):
+    m, b = CASES[case]()
+    # BiCGSTAB's iteration count is sensitive to rounding: gate the residual only
+    _check(m, b, "bicgstab", precond, 1e-10, iters_gate=False)
+
+
+@pytest.mark.parametrize("case", ["lap2d_64", "diff3d_12", "convdiff_300"])
+@pytest.mark.parametrize("precond", [False, True])
+def test_gmres(case, precond):
+    m, b = CASES[case]()
+    _check(m, b, "gmres", precond, 1e-10)
+
+
+@pytest.mark.parametrize("fmt", ["ell", "sellp"])
+@pytest.mark.parametrize("method", ["cg", "bicgstab", "gmres"])
+def test_solvers_on_padded_formats(fmt, method):
+    m, b = CASES["diff3d_12"]()
+    _check(m, b, method, True, 1e-10, fmt=fmt, iters_gate=(method != "bicgstab"))
+
+
+def test_small_gmres_restart_length():
+    m, b = CASES["convdiff_300"]()
+    x, info, _, io = _check(m, b, "gmres", False, 1e-10, krylov_dim=8)
+    assert info["restarts"] >= 1
+
+
+def test_dense_solution_matches_lapack():
+    m = W.shifted_rectangle(9, 11, 0.5)
+    b = W.uniform_vector(m.n, 3)
+    xs = np.linalg.solve(m.to_dense(), b)
+    kappa = np.linalg.cond(m.to_dense())
+    for method in ("cg", "bicgstab", "gmres"):
+        x, info = _gpu_solve(m, b, method, 0, 1e-12)
+        assert info["return"] == gk.GK_OK
+        assert np.linalg.norm(x - xs) <= 2 * kappa * 1e-12 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("method", ["cg", "bicgstab", "gmres"])
+def test_zero_rhs(method):
+    m = W.laplacian_2d(10)
+    x, info = _gpu_solve(m, np.zeros(m.n), method, 0, 1e-10, x0=np.ones(m.n))
+    assert info["return"] == gk.GK_OK and info["iters"] == 0 and np.all(x == 0)
+
+
+def test_zero_diagonal_rejected():
+    m = W.CSR(3, 3, np.array([0, 1, 2, 3]), np.array([0, 1, 0]), np.array([1.0, 2.0, 3.0]))
+    _, info = _gpu_solve(m, np.ones(3), "cg", 1, 1e-10)
+    assert info["return"] == gk.GK_ERR_ZERO_DIAG
+
+
+def test_cg_breakdown_on_indefinite():
+    n = 6
+    m = W.CSR(n, n, np.arange(n + 1), np.arange(n), -np.ones(n))
+    _, info = _gpu_solve(m, np.ones(n), "cg", 0, 1e-10)
+    assert info["return"] == gk.GK_BREAKDOWN
+
+
+@pytest.mark.parametrize("method", ["cg", "bicgstab", "gmres"])
+def test_iteration_cap(method):
+    m, b = CASES["lap2d_64"]()
+    x, info = _gpu_solve(m, b, method, 0, 1e-12, max_iters=7)
+    assert info["return"] == gk.GK_NOT_CONVERGED and info["iters"] == 7
+    rel = oracle.true_rel_residual(m, b, x)
+    assert abs(rel - info["rel_res_true"]) <= 1e-6 * rel
+    # x holds the last iterate: same residual as the oracle after 7 steps
+    xo, io = oracle.solve(m, b, method=METHOD[method], tol=1e-12, max_iters=7)
+    assert abs(io["rel_res_true"] - rel) <= 1e-6 * rel
+
+
+def test_nonzero_initial_guess():
+    m, b = CASES["diff3d_12"]()
+    x0 = W.uniform_vector(m.n, 99)
+    x, info = _gpu_solve(m, b, "cg", 1, 1e-10, x0=x0)
+    assert info["return"] == gk.GK_OK and oracle.true_rel_residual(m, b, x) <= 1e-10
+
+
+def test_solve_deterministic():
+    m, b = CASES["diff3d_12"]()
+    x1, i1 = _gpu_solve(m, b, "cg", 1, 1e-10)
+    x2, i2 = _gpu_solve(m, b, "cg", 1, 1e-10)
+    assert np.array_equal(x1, x2) and i1["iters"] == i2["iters"]
+
+
+@pytest.mark.parametrize("method", ["cg", "bicgstab", "gmres"])
+def test_fp32_solve(method):
+    m, b = CASES["diff3d_12"]()
+    x, info = _gpu_solve(m, b, method, 1, 1e-5, dtype="f32")
+    assert info["return"] == gk.GK_OK
+    assert oracle.true_rel_residual(m, b, x) <= 2e-5  # FP32-rounded A differs from A
+
+
+@pytest.mark.parametrize("mixed", [1, 2])
+@pytest.mark.parametrize("method", ["cg", "gmres"])
+def test_mixed_precision_refinement(mixed, method):
+    """FP32 (or BF16-stored) inner solves inside FP64 refinement reach the
+    FP64 tolerance, and x agrees with the plain FP64 solve within kappa*tol."""
+    m, b = CASES["diff3d_12"]()
+    x, info = _gpu_solve(m, b, method, 1, 1e-10, dtype="mixed", mixed=mixed)
+    assert info["return"] == gk.GK_OK, info
+    assert info["outer_iters"] >= 1
+    assert oracle.true_rel_residual(m, b, x) <= 1e-10
+    xo, _ = oracle.solve(m, b, method=METHOD[method], precond=1, tol=1e-12, max_iters=5000)
+    kappa = np.linalg.cond(m.to_dense())
+    assert np.linalg.norm(x - xo) <= kappa * 2e-10 * np.linalg.norm(xo)
+
+
+def test_config3_full_size_jacobi_cg_and_refinement():
+    """128^3 log-normal diffusion: Jacobi-CG in FP64 and FP32-refined CG both
+    reach a true residual of 1e-10 (oracle SpMV on the GPU's x)."""
+    m = W.diffusion_3d(128)
+    b = W.uniform_vector(m.n, W.SEED_BASE + 3)
+    x, info = _gpu_solve(m, b, "cg", 1, 1e-10, max_iters=20000)
+    assert info["return"] == gk.GK_OK
+    assert oracle.true_rel_residual(m, b, x) <= 1e-10
+    x2, info2 = _gpu_solve(m, b, "cg", 1, 1e-10, max_iters=20000, dtype="mixed", mixed=1)
+    assert info2["return"] == gk.GK_OK
+    assert oracle.true_rel_residual(m, b, x2) <= 1e-10
