@@ -222,6 +222,45 @@ gk_status gk_solve_batched(int32_t count, const gk_matrix* As,
                            const gk_solve_opts* opts, gk_solve_info* infos,
                            void* stream);
 
+/* ---------------------------------------------------------------------
+ * SpMV without device allocation
+ * ------------------------------------------------------------------- */
+
+/* Largest n + nnz that gk_spmv_csr_f64_noalloc accepts. */
+#define GK_NOALLOC_MAX_ITEMS 134217728
+
+/* x = alpha * A b + beta * x for an FP64 CSR matrix given as raw DEVICE
+ * arrays (row_ptr[n+1], col_idx[nnz], values[nnz]; b has ncols entries,
+ * x has n), without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc - code
+ * whose device memory is owned by a framework's pool allocator that must
+ * not see foreign allocations, or code in a loop where an allocation,
+ * which can synchronise the device, is not allowed.
+ *
+ * It runs the merge-path kernels that gk_apply uses for skewed CSR
+ * matrices, with the per-block carry scratch held in a fixed file-scope
+ * device array of 768 KB that every GPU loading this library keeps until
+ * the process exits.  No cudaMalloc, cudaFree or allocating library call
+ * is made.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.
+ *
+ * All calls share the one scratch array: calls that overlap on the GPU
+ * (for example on two streams) race and give wrong results; serialise
+ * them.  Each call rewrites every scratch entry it reads, so nothing
+ * carries over from the previous call.
+ *
+ * Errors: GK_ERR_INVALID for negative sizes, null pointers, or
+ * n + nnz > GK_NOALLOC_MAX_ITEMS (the scratch holds the carries of at most
+ * GK_NOALLOC_MAX_ITEMS / 2048 blocks); GK_ERR_UNSUPPORTED on a device
+ * ordinal >= 64.  The arrays are not validated: they must form a valid
+ * CSR matrix (row_ptr non-decreasing from 0 to nnz, 0 <= col < ncols).
+ * beta == 0 does not read x.  Stream-ordered on `stream`, asynchronous. */
+gk_status gk_spmv_csr_f64_noalloc(int32_t n, int32_t ncols, int64_t nnz,
+                                  const int32_t* row_ptr, const int32_t* col_idx,
+                                  const double* values, double alpha, const double* b,
+                                  double beta, double* x, void* stream);
+
 /* Static English text for a status code. */
 const char* gk_status_string(gk_status s);
 

@@ -39,6 +39,7 @@ EXPORTED = [
     "gk_matrix_create_csr", "gk_matrix_create_coo", "gk_matrix_convert",
     "gk_matrix_describe", "gk_matrix_export", "gk_matrix_destroy", "gk_apply",
     "gk_apply_adv", "gk_solve", "gk_solve_batched", "gk_status_string", "gk_version",
+    "gk_spmv_csr_f64_noalloc",
 ]
 
 
@@ -102,6 +103,7 @@ def lib():
                                ctypes.POINTER(gk_solve_info), vp]
         L.gk_solve_batched.argtypes = [i32, pm, pm, pm, ctypes.POINTER(gk_solve_opts),
                                        ctypes.POINTER(gk_solve_info), vp]
+        L.gk_spmv_csr_f64_noalloc.argtypes = [i32, i32, i64, vp, vp, vp, f64, vp, f64, vp, vp]
         L.gk_status_string.argtypes = [ctypes.c_int]
         L.gk_status_string.restype = ctypes.c_char_p
         L.gk_version.argtypes = []
@@ -244,6 +246,15 @@ def gk_solve_batched(As, bs, xs, opts, stream=None):
     infos = (gk_solve_info * n)()
     st = lib().gk_solve_batched(n, arrA, arrB, arrX, ctypes.byref(opts), infos, _stream(stream))
     return st, [i.as_dict() for i in infos]
+
+
+def gk_spmv_csr_f64_noalloc(n, ncols, nnz, row_ptr, col_idx, values, alpha, b, beta, x,
+                            stream=None):
+    """x = alpha A b + beta x from raw device CSR arrays, with no device
+    allocation (scratch in a fixed device array; see include/gk.h)."""
+    return lib().gk_spmv_csr_f64_noalloc(n, ncols, nnz, _ptr(row_ptr), _ptr(col_idx),
+                                         _ptr(values), float(alpha), _ptr(b), float(beta),
+                                         _ptr(x), _stream(stream))
 
 
 def gk_status_string(s):
