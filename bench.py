@@ -4,10 +4,16 @@
 synthetic stand-ins for its SuiteSparse set), plus CG solves/s on the 64x64
 5-point Laplacian to a 1e-10 relative residual.
 
-One step = one apply of every (matrix, format, dtype) item of the sweep.
-value = algorithmic bytes of all items / device time (GB/s); algorithmic
-bytes per item = nnz*(value+index bytes) + 4*(n+1) [CSR] + x and y once.
+One step = one apply per (matrix, dtype) in the fastest of CSR / ELL /
+SELL-P for that matrix (picked by a short timing pass before the timed
+region, as the paper reports each library's best-performing format,
+Section 5).  value = algorithmic bytes of the step / device time (GB/s);
+algorithmic bytes per apply = nnz*(value+index bytes) + 4*(n+1) [CSR] +
+x and y once.  Every format is also timed and listed under "sweep".
 Matrices (0.9-1.7 GB each) are larger than L2, so no flush is needed.
+Extra keys: CG solves/s on the 64x64 Laplacian, time to 1e-10 on the 128^3
+diffusion problem for FP32-refined vs plain FP64 Jacobi-CG / GMRES(30),
+and 2048 batched systems in one launch vs a per-system loop.
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 """
@@ -29,9 +35,10 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "SpMV GB/s & %HBM peak; CG solves/s at 1e-10 residual; serving p50/p99 latency"
-WORKLOAD = ("SpMV sweep {CSR, ELL, SELL-P(S=32)} x {FP64, FP32}: 3D 7-point Laplacian 256^3 "
-            "(n=16,777,216, nnz=117,047,296) and Zipf(1.8) power-law n=4,194,304 (mean 16, "
-            "max 4096; ELL skipped: ~206 GB padded); int32 indices; x ~ U[-1,1]")
+WORKLOAD = ("SpMV, best of {CSR, ELL, SELL-P(S=32)} per matrix, {FP64, FP32}: 3D 7-point "
+            "Laplacian 256^3 (n=16,777,216, nnz=117,047,296) and Zipf(1.8) power-law "
+            "n=4,194,304 (mean 16, max 4096; ELL not built: ~206 GB padded); int32 indices; "
+            "x ~ U[-1,1]")
 FALLBACK_HBM = 6800.0
 
 
@@ -176,7 +183,7 @@ def cg_solves_per_s(gk, W, torch, dev, reps=20):
     A = gk.Matrix.from_csr(m)
     x = torch.zeros_like(b)
     out = {}
-    for engine in (1, 2):
+    for engine in (1, 2, 3):
         A.solve(b, x, method="cg", tol=1e-10, max_iters=5000, engine=engine)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -188,7 +195,7 @@ def cg_solves_per_s(gk, W, torch, dev, reps=20):
             iters = info["iters"]
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        out["multi_kernel" if engine == 1 else "single_block"] = {
+        out[{1: "multi_kernel", 2: "single_block", 3: "cluster"}[engine]] = {
             "solves_per_s": round(reps / el, 1), "iters": iters,
             "rel_res_true": info["rel_res_true"]}
     A.close()
@@ -196,6 +203,91 @@ def cg_solves_per_s(gk, W, torch, dev, reps=20):
     return {"solves_per_s": best["solves_per_s"], "workload": "2D 5-point 64x64 FP64 CG to 1e-10, "
             "b ~ U[-1,1] seed 2511, x0 = 0 (host wall clock per solve incl. launch)",
             "engines": out}
+
+
+def time_apply(it, stream, torch, reps=3):
+    """Mean device time (ms) of `reps` applies of one sweep item."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    it["mat"].apply(it["x"], it["y"], stream)
+    e0.record(stream)
+    for _ in range(reps):
+        it["mat"].apply(it["x"], it["y"], stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def ir_compare(gk, W, torch, dev):
+    """128^3 log-normal diffusion: wall time to a true 1e-10 residual,
+    FP32 inner solves in FP64 refinement vs plain FP64 (Jacobi-CG and
+    Jacobi-GMRES(30))."""
+    m = W.diffusion_3d(128)
+    b = torch.from_numpy(W.uniform_vector(m.n, W.SEED_BASE + 3)).to(dev)
+    A = gk.Matrix.from_csr(m)
+    out = {"workload": "128^3 7-point diffusion, exp(N(0,1)) cells, harmonic faces; "
+                       "b ~ U[-1,1] seed 2513; x0 = 0; tol 1e-10 (true residual)"}
+    for method in ("cg", "gmres"):
+        res = {}
+        for mixed in (0, 1, 2):
+            x = torch.zeros_like(b)
+            A.solve(b, x, method=method, precond="jacobi", tol=1e-10, max_iters=20000,
+                    mixed=mixed)  # warm-up (plans, low-precision copy, graphs)
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = A.solve(b, x, method=method, precond="jacobi", tol=1e-10, max_iters=20000,
+                           mixed=mixed)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            res[{0: "fp64", 1: "fp32_ir", 2: "bf16_ir"}[mixed]] = {
+                "ms": round(el * 1000, 2), "status": info["return"], "iters": info["iters"],
+                "outer": info["outer_iters"], "rel_res_true": info["rel_res_true"]}
+        res["speedup_fp32_ir"] = round(res["fp64"]["ms"] / res["fp32_ir"]["ms"], 3)
+        out[method] = res
+    A.close()
+    return out
+
+
+def batched_compare(gk, W, torch, dev, count=2048):
+    """2048 shifted-rectangle SPD systems (64-4096 rows): one persistent
+    launch vs a per-system gk_solve loop, CG to 1e-10, FP64 and FP32."""
+    mats, rhs = W.batched_rectangles(count, seed=W.SEED_BASE + 4)
+    out = {"workload": f"{count} 2D 5-point Laplacians on random rectangles + diagonal shift "
+                       "U[0,1], n 64..4096, CG (Jacobi) to 1e-10 (FP64) / 1e-5 (FP32)"}
+    for dt in ("f64", "f32"):
+        vt = torch.float64 if dt == "f64" else torch.float32
+        tol = 1e-10 if dt == "f64" else 1e-5
+        As = [gk.Matrix.from_csr(m, dt) for m in mats]
+        bs = [torch.from_numpy(b).to(dev, vt) for b in rhs]
+        xs = [torch.zeros(m.n, dtype=vt, device=dev) for m in mats]
+        opts = gk.make_opts(method="cg", precond="jacobi", tol=tol, max_iters=20000)
+        gk.gk_solve_batched([A.handle for A in As], bs, xs, opts)  # warm-up
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, infos = gk.gk_solve_batched([A.handle for A in As], bs, xs, opts)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        ok = sum(1 for i in infos if i["status"] == 0)
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loop_ok = 0
+        for A, b, x in zip(As, bs, xs):
+            info = A.solve(b, x, method="cg", precond="jacobi", tol=tol, max_iters=20000)
+            loop_ok += info["return"] == 0
+        torch.cuda.synchronize()
+        t_loop = time.perf_counter() - t0
+        out[dt] = {"batched_ms": round(t_batch * 1000, 2), "loop_ms": round(t_loop * 1000, 2),
+                   "speedup": round(t_loop / t_batch, 2),
+                   "solves_per_s_batched": round(count / t_batch, 1),
+                   "converged_batched": ok, "converged_loop": loop_ok}
+        for A in As:
+            A.close()
+    return out
 
 
 def run_reference(args):
@@ -244,6 +336,7 @@ def main():
     ap.add_argument("--impl", default="gk", choices=["gk", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--no-solvers", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -271,8 +364,17 @@ def main():
         it["y"] = torch.empty(it["n"], dtype=vt, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(events=None):
-        for k, it in enumerate(items):
+    # format choice: fastest format per (matrix, dtype), by a short timing pass
+    trial = {it["name"]: time_apply(it, stream, torch) for it in items}
+    best = {}
+    for it in items:
+        key = it["name"].rsplit("/", 2)[0] + "/" + it["dtype"]
+        if key not in best or trial[it["name"]] < trial[best[key]["name"]]:
+            best[key] = it
+    step_items = list(best.values())
+
+    def step(its, events=None):
+        for k, it in enumerate(its):
             if events is not None:
                 events[k][0].record(stream)
             it["mat"].apply(it["x"], it["y"], stream)
@@ -280,7 +382,7 @@ def main():
                 events[k][1].record(stream)
 
     for _ in range(args.warmup):
-        step()
+        step(step_items)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -288,54 +390,64 @@ def main():
     clocks.start()
     time.sleep(0.3)
     evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            for _ in items] for _ in range(args.steps)]
+            for _ in step_items] for _ in range(args.steps)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     t_start.record(stream)
-    for s in range(args.steps):
-        step(evs[s])
+    for s_ in range(args.steps):
+        step(step_items, evs[s_])
     t_end.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
-    per_item_ms = [statistics.mean(evs[s][k][0].elapsed_time(evs[s][k][1])
-                                   for s in range(args.steps)) for k in range(len(items))]
+    per_item_ms = [statistics.mean(evs[s_][k][0].elapsed_time(evs[s_][k][1])
+                                   for s_ in range(args.steps)) for k in range(len(step_items))]
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    step_bytes = sum(it["bytes"] for it in items)
+    step_bytes = sum(it["bytes"] for it in step_items)
     value = step_bytes * args.steps * world / (total_ms / 1000.0) / 1e9
     peak, peak_kind = _peaks()
+
+    # every format, for the record (not part of the timed step)
     sweep = []
-    for it, ms in zip(items, per_item_ms):
+    for it in items:
+        ms = time_apply(it, stream, torch, reps=max(3, args.steps))
         gbs = it["bytes"] / (ms / 1000.0) / 1e9
         sweep.append({"item": it["name"], "kernel": KERNEL_NAMES[it["kernel"]],
                       "us": round(ms * 1000, 1), "GB_s": round(gbs, 1),
                       "frac_of_measured_hbm": round(gbs / peak, 3),
-                      "frac_of_8TBs_nominal": round(gbs / 8000.0, 3)})
+                      "frac_of_8TBs_nominal": round(gbs / 8000.0, 3),
+                      "in_step": it in step_items})
     # dominant kernel: largest share of the step's device time
-    k_dom = max(range(len(items)), key=lambda k: per_item_ms[k])
-    dom = items[k_dom]
+    k_dom = max(range(len(step_items)), key=lambda k: per_item_ms[k])
+    dom = step_items[k_dom]
     dom_gbs = dom["bytes"] / (per_item_ms[k_dom] / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": round(dom_gbs, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(dom_gbs / peak, 3),
                 "traffic": traffic_for(KERNEL_NAMES[dom["kernel"]], dom["name"]),
                 "kernel": KERNEL_NAMES[dom["kernel"]], "item": dom["name"],
-                "peak_source": f"{peak_kind} HBM copy bandwidth",
-                "algorithmic_bytes_per_launch": dom["bytes"]}
-    headline = next(s for s in sweep if s["item"] == "lap3d_256/csr/f64")
+                "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": dom["bytes"],
+                "mean_launch_us": round(per_item_ms[k_dom] * 1000, 1),
+                "share_of_step": round(per_item_ms[k_dom] / sum(per_item_ms), 3)}
+    step_detail = [{"item": it["name"], "kernel": KERNEL_NAMES[it["kernel"]],
+                    "us": round(ms * 1000, 1), "GB_s": round(it["bytes"] / (ms / 1000.0) / 1e9, 1),
+                    "frac_of_measured_hbm": round(it["bytes"] / (ms / 1000.0) / 1e9 / peak, 3)}
+                   for it, ms in zip(step_items, per_item_ms)]
 
-    # e2e: same sweep through the C ABI with pinned HOST buffers (H2D of x,
-    # kernel, D2H of y inside the timed region, every step)
-    hx = [torch.from_numpy(it["x"].cpu().numpy()).pin_memory() for it in items]
-    hy = [torch.empty(it["n"], dtype=it["y"].dtype).pin_memory() for it in items]
+    # e2e: the same step through the C ABI with pinned HOST buffers (H2D of
+    # x, kernel, D2H of y inside the timed region, every step)
+    hx = [torch.from_numpy(it["x"].cpu().numpy()).pin_memory() for it in step_items]
+    hy = [torch.empty(it["n"], dtype=it["y"].dtype).pin_memory() for it in step_items]
 
     def e2e_step():
-        for it, a, b in zip(items, hx, hy):
+        for it, a, b in zip(step_items, hx, hy):
             it["mat"].apply(a, b, stream)
 
     e2e_step()
@@ -350,23 +462,30 @@ def main():
     e2e = {"value": round(step_bytes * args.steps * world / e2e_s / 1e9, 1), "unit": "GB/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "how": "gk_apply with pinned host x and y (library-staged copies), host wall clock"}
+    launches = sum(it["launches"] for it in step_items) * args.steps
+    for it in items:
+        it["mat"].close()
+    del items, step_items
+    torch.cuda.empty_cache()
 
-    cg = None
-    if not args.no_cg and rank == 0:
+    cg = ir = batched = None
+    if rank == 0 and not args.no_cg:
         cg = cg_solves_per_s(gk, W, torch, dev)
+    if rank == 0 and not args.no_solvers:
+        ir = ir_compare(gk, W, torch, dev)
+        batched = batched_compare(gk, W, torch, dev)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(lap)
-    launches = sum(it["launches"] for it in items) * args.steps
     line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-            "spmv_lap3d_csr_f64": headline,
-            "sweep": sweep, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "cg": cg, "clocks": clk, "gpu_launches": launches}
+            "step": step_detail, "sweep": sweep, "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": e2e, "cg": cg, "ir_128cubed": ir, "batched_2048": batched, "clocks": clk,
+            "gpu_launches": launches}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -96,6 +96,9 @@ typedef struct {
     int32_t spmv_kernel;   /* SpMV kernel apply uses: 0 CSR vector, 1 CSR row-tile,
                               2 CSR merge-path, 3 ELL, 4 SELL-P */
     int32_t spmv_launches; /* kernel launches per apply */
+    int32_t device_error;  /* 1 if a kernel on this matrix gave up a bounded
+                              device-side wait (its results are invalid) */
+    int32_t reserved;
 } gk_matrix_desc;
 
 /* ---------------------------------------------------------------------
@@ -137,6 +140,7 @@ gk_status gk_matrix_convert(gk_matrix A, gk_format fmt, gk_dtype dtype,
                             int32_t slice_size, int32_t stride_factor,
                             void* stream, gk_matrix* out);
 
+/* Shape and layout of A; blocking (reads the device error word). */
 gk_status gk_matrix_describe(gk_matrix A, gk_matrix_desc* out);
 
 /* Copy the format arrays to caller-owned HOST buffers (any pointer may be
@@ -182,8 +186,13 @@ typedef struct {
                              refinement; 2: BF16-stored FP32 inner solves */
     double inner_tol;     /* refinement: inner reduction (0 = 1e-4) */
     int32_t max_outer;    /* refinement: outer cap (0 = 50) */
-    int32_t engine;       /* 0 automatic, 1 multi-kernel (any n),
-                             2 single-block (n <= 16384) */
+    const double* batch_tols; /* gk_solve_batched only: per-system tolerances
+                             (host array of `count`), NULL = tol for all */
+    int32_t engine;       /* 0 automatic; 1 multi-kernel (any n, any format);
+                             2 single-block (CSR, CG/BiCGSTAB, n <= 16384);
+                             3 cluster of up to 16 blocks (CSR, CG, n <= 16384).
+                             Automatic picks 3 for CSR CG with n <= 16384 when a
+                             cluster can be scheduled, else 1. */
 } gk_solve_opts;
 
 typedef struct {

@@ -56,7 +56,8 @@ class gk_matrix_desc(ctypes.Structure):
                 ("slice_size", ctypes.c_int32), ("stride_factor", ctypes.c_int32),
                 ("num_slices", ctypes.c_int32), ("stored", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("spmv_kernel", ctypes.c_int32),
-                ("spmv_launches", ctypes.c_int32)]
+                ("spmv_launches", ctypes.c_int32), ("device_error", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -66,7 +67,8 @@ class gk_solve_opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("precond", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_iters", ctypes.c_int32), ("krylov_dim", ctypes.c_int32),
                 ("mixed", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("max_outer", ctypes.c_int32), ("engine", ctypes.c_int32)]
+                ("max_outer", ctypes.c_int32), ("batch_tols", ctypes.c_void_p),
+                ("engine", ctypes.c_int32)]
 
 
 class gk_solve_info(ctypes.Structure):
@@ -226,7 +228,8 @@ def make_opts(method="cg", precond=None, tol=1e-10, max_iters=1000, krylov_dim=3
         p = GK_PRECOND_NONE
     else:
         p = GK_PRECOND_JACOBI
-    return gk_solve_opts(m, p, tol, max_iters, krylov_dim, mixed, inner_tol, max_outer, engine)
+    return gk_solve_opts(m, p, tol, max_iters, krylov_dim, mixed, inner_tol, max_outer, None,
+                         engine)
 
 
 def gk_solve(A, b, x, opts, stream=None):
@@ -238,13 +241,21 @@ def gk_solve(A, b, x, opts, stream=None):
     return d
 
 
-def gk_solve_batched(As, bs, xs, opts, stream=None):
+def gk_solve_batched(As, bs, xs, opts, stream=None, tols=None):
+    """Solves len(As) systems in one launch; tols: optional per-system
+    tolerances (overrides opts.tol)."""
     n = len(As)
+    keep = None
+    if tols is not None:
+        keep = np.ascontiguousarray(tols, dtype=np.float64)
+        opts.batch_tols = keep.ctypes.data
     arrA = (ctypes.c_void_p * n)(*As)
     arrB = (ctypes.c_void_p * n)(*[_ptr(b) for b in bs])
     arrX = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
     infos = (gk_solve_info * n)()
     st = lib().gk_solve_batched(n, arrA, arrB, arrX, ctypes.byref(opts), infos, _stream(stream))
+    if keep is not None:
+        opts.batch_tols = None
     return st, [i.as_dict() for i in infos]
 
 

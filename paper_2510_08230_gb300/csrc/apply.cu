@@ -20,16 +20,22 @@ static gk_status spmv_typed(gk_matrix A, double alpha, const void* b, double bet
     EpiStore<T> epi{static_cast<T*>(x), (T)alpha, (T)beta, mode};
     if (A->n == 0) return GK_OK;
     if (A->fmt == GK_CSR && A->plan.kind == 2) {
-        constexpr int E = sizeof(V) >= 8 ? 8 : 12;
-        const int64_t N = (int64_t)A->n + A->nnz;
-        const int64_t nb = (N + 256 * E - 1) / (256 * E);
+        constexpr int E = MergeE<V>::value;
+        const int64_t nb = A->plan.merge_blocks;
         GK_TRY(A->carry.ensure((size_t)nb * (sizeof(int32_t) + sizeof(T)) + 16));
         int32_t* crow = static_cast<int32_t*>(A->carry.ptr);
         T* cval = reinterpret_cast<T*>(static_cast<char*>(A->carry.ptr) +
                                        (((size_t)nb * sizeof(int32_t) + 15) & ~(size_t)15));
-        k_csr_merge<E, V, T><<<(unsigned)nb, 256, 0, s>>>(A->n, A->nnz, A->row_ptr, A->col,
-                                                          (const V*)A->val, (const T*)b, epi, crow,
-                                                          cval);
+        constexpr size_t smem = merge_smem_bytes<E, V, T>();
+        static bool attr = false;
+        if (!attr) {
+            GK_CUDA(cudaFuncSetAttribute(k_csr_merge<E, V, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr = true;
+        }
+        k_csr_merge<E, V, T><<<(unsigned)nb, 256, smem, s>>>(A->n, A->nnz, A->row_ptr, A->col,
+                                                             (const V*)A->val, (const T*)b, epi,
+                                                             A->plan.block_row, crow, cval);
         const unsigned fg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, 4096));
         k_csr_merge_fixup<T><<<fg, 256, 0, s>>>((int32_t)nb, crow, cval, static_cast<T*>(x),
                                                 (T)alpha, mode);

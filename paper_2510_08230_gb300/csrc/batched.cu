@@ -27,6 +27,7 @@ struct SysDesc {
     void* x;
     void* work;  // workspace vectors, each `ld` elements
     int64_t ld;
+    double tol;  // this system's relative tolerance
 };
 
 struct SysOut {
@@ -43,26 +44,7 @@ struct BlockOpts {
 // Sum of NA values over the block, returned to every thread (fixed order).
 template <int NA>
 __device__ __forceinline__ void block_allsum(double (&v)[NA]) {
-    __shared__ double sh[NA][32];
-    __shared__ double tot[NA];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int a = 0; a < NA; ++a) {
-        const double w = warp_sum(v[a]);
-        if (lane == 0) sh[a][warp] = w;
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            const double w = warp_sum(lane < nw ? sh[a][lane] : 0.0);
-            if (lane == 0) tot[a] = w;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int a = 0; a < NA; ++a) v[a] = tot[a];
+    block_allsum_bcast<NA>(v);
 }
 
 template <typename V, typename T, typename G>
@@ -112,7 +94,7 @@ __device__ bool block_setup(const SysDesc& d, const BlockOpts& opt, T* dinv, T* 
         return false;
     }
     bn = sqrt(acc[0]);
-    thr = opt.tol * bn;
+    thr = d.tol * bn;
     if (bn == 0.0) {
         for (int32_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = T(0);
         o.status = GK_OK;
@@ -388,8 +370,26 @@ struct BatchBufs {
     }
 };
 
+// Buffers are pooled: a call takes a free set (or makes one) and returns it,
+// so batches launched from different host threads run concurrently.
 static std::mutex g_batch_mu;
-static BatchBufs* g_batch = nullptr;  // reused across calls (serialised by g_batch_mu)
+static std::vector<BatchBufs*> g_batch_pool;
+
+struct BatchLease {
+    BatchBufs* b = nullptr;
+    BatchLease() {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        if (!g_batch_pool.empty()) {
+            b = g_batch_pool.back();
+            g_batch_pool.pop_back();
+        }
+        if (!b) b = new BatchBufs();
+    }
+    ~BatchLease() {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        g_batch_pool.push_back(b);
+    }
+};
 
 template <typename V, typename T>
 static gk_status launch_block(int method, const SysDesc* ddesc, SysOut* dout, int32_t count,
@@ -424,9 +424,8 @@ static gk_status run_batch(int32_t count, const gk_matrix* As, const void* const
     }
     const size_t smem = std::max<size_t>((size_t)nmax * vb, 16);
     if (smem > 200 * 1024) return GK_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lk(g_batch_mu);
-    if (!g_batch) g_batch = new BatchBufs();
-    BatchBufs& B = *g_batch;
+    BatchLease lease;
+    BatchBufs& B = *lease.b;
     if (B.hcap < (size_t)count) {
         if (B.hdesc) cudaFreeHost(B.hdesc);
         if (B.hout) cudaFreeHost(B.hout);
@@ -452,6 +451,7 @@ static gk_status run_batch(int32_t count, const gk_matrix* As, const void* const
         d.x = xs[i];
         d.work = w;
         d.ld = (int64_t)((((size_t)A->n * vb + 255) & ~(size_t)255) / vb);
+        d.tol = o->batch_tols ? o->batch_tols[i] : o->tol;
         w += (size_t)d.ld * vb * ns;
     }
     GK_CUDA(cudaMemcpyAsync(B.desc.ptr, B.hdesc, sizeof(SysDesc) * (size_t)count,
@@ -541,6 +541,9 @@ extern "C" gk_status gk_solve_batched(int32_t count, const gk_matrix* As, const 
         (o->precond != GK_PRECOND_NONE && o->precond != GK_PRECOND_JACOBI) || !(o->tol >= 0.0) ||
         o->max_iters < 0)
         return GK_ERR_INVALID;
+    if (o->batch_tols)
+        for (int32_t i = 0; i < count; ++i)
+            if (!(o->batch_tols[i] >= 0.0)) return GK_ERR_INVALID;
     int dev = -1;
     cudaGetDevice(&dev);
     for (int32_t i = 0; i < count; ++i) {

@@ -1,0 +1,328 @@
+// cluster.cu - cluster engine: one thread-block cluster (up to 16 blocks,
+// one per SM) runs a whole CG solve of one small system.
+//
+// Same algorithm, stopping rule and residual replacement as the other CG
+// engines (Hestenes-Stiefel, optional Jacobi; stopping per Listing 2; true
+// residual confirms convergence).  Block r of the cluster owns rows
+// [r*rpb, (r+1)*rpb); each thread keeps up to RMAX of those rows' x, r, q
+// and inverse diagonal in registers.  The vector SpMV gathers from (p, or x
+// for the true residual) lives in the owners' shared memory and is read
+// across the cluster through distributed shared memory.  A reduction is a
+// fixed-order block sum, a cluster barrier, and every thread summing the C
+// block partials in rank order, so all blocks take identical decisions and
+// the result does not depend on timing.  Per CG iteration: three cluster
+// barriers and no kernel launches.
+#include <cooperative_groups.h>
+
+#include "prims.cuh"
+
+namespace cgx = cooperative_groups;
+
+namespace gk {
+
+constexpr int CL_THREADS = 256;
+constexpr int CL_RMAX = 4;
+constexpr int CL_MAX_BLOCKS = 16;
+
+struct ClusterArgs {
+    int32_t n;
+    int32_t rpb;  // rows per block
+    const int32_t* rp;
+    const int32_t* ci;
+    const void* va;
+    const void* b;
+    void* x;
+    double tol;
+    int32_t max_iters;
+    int32_t prec;
+    SolveOut* out;
+};
+
+// Sum of NA per-block partials over the cluster, identical in all threads:
+// block sum (warp 0), cluster barrier, then warp 0 loads the C block
+// partials (lane r reads block r) and adds them with a fixed shuffle tree;
+// every block evaluates the same tree over the same values.
+template <int NA>
+__device__ __forceinline__ void cluster_allsum(cgx::cluster_group& cl, double (&v)[NA],
+                                               double (*red)[4], int& tog) {
+    __shared__ double tot[4];
+    block_sum<NA>(v);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int a = 0; a < NA; ++a) red[tog][a] = v[a];
+    cl.sync();
+    if (threadIdx.x < 32) {
+        const unsigned C = cl.num_blocks();
+        const unsigned lane = threadIdx.x;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            double p = 0.0;
+            if (lane < C) {
+                double(*rr)[4] = cl.map_shared_rank(red, lane);
+                p = rr[tog][a];
+            }
+            p = warp_sum(p);
+            if (lane == 0) tot[a] = p;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < NA; ++a) v[a] = tot[a];
+    tog ^= 1;
+}
+
+template <typename V, typename T>
+__device__ __forceinline__ T cluster_row_dot(cgx::cluster_group& cl, const ClusterArgs& A,
+                                             const V* __restrict__ va, T* g_s, int32_t i,
+                                             unsigned my_rank) {
+    T s = T(0);
+    const int32_t e = A.rp[i + 1];
+    for (int32_t k = A.rp[i]; k < e; ++k) {
+        const int32_t c = A.ci[k];
+        const unsigned owner = (unsigned)(c / A.rpb);
+        const int32_t loc = c - (int32_t)owner * A.rpb;
+        const T gv = owner == my_rank ? g_s[loc] : cl.map_shared_rank(g_s, owner)[loc];
+        s = fmadd(cvt<T>(va[k]), gv, s);
+    }
+    return s;
+}
+
+template <typename V, typename T>
+__global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
+    cgx::cluster_group cl = cgx::this_cluster();
+    const unsigned rank = cl.block_rank();
+    __shared__ T g_s[CL_RMAX * CL_THREADS];  // owned part of the gathered vector
+    __shared__ double red[2][4];
+    int tog = 0;
+    const V* va = (const V*)A.va;
+    const T* b = (const T*)A.b;
+    T* xg = (T*)A.x;
+    const int32_t r0 = (int32_t)rank * A.rpb;
+    const int32_t nloc = max(0, min(A.rpb, A.n - r0));
+    T x[CL_RMAX], r[CL_RMAX], q[CL_RMAX], di[CL_RMAX];
+    double acc2[2] = {0.0, 0.0};
+    // x into shared memory (for the initial residual), b norm, Jacobi diagonal
+#pragma unroll
+    for (int k = 0; k < CL_RMAX; ++k) {
+        const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+        x[k] = r[k] = q[k] = T(0);
+        di[k] = T(1);
+        if (li < nloc) {
+            const int32_t i = r0 + li;
+            x[k] = xg[i];
+            g_s[li] = x[k];
+            const T bi = b[i];
+            acc2[0] = fma((double)bi, (double)bi, acc2[0]);
+            if (A.prec) {
+                T d = T(0);
+                for (int32_t kk = A.rp[i]; kk < A.rp[i + 1]; ++kk)
+                    if (A.ci[kk] == i) d += cvt<T>(va[kk]);
+                if (d == T(0)) acc2[1] = 1.0;
+                di[k] = d == T(0) ? T(0) : T(1) / d;
+            }
+        }
+    }
+    cluster_allsum<2>(cl, acc2, red, tog);  // includes the barrier that publishes g_s
+    SolveOut o;
+    o.status = GK_NOT_CONVERGED;
+    const double bn = sqrt(acc2[0]);
+    const double thr = A.tol * bn;
+    bool run = true;
+    if (acc2[1] != 0.0) {
+        o.status = GK_ERR_ZERO_DIAG;
+        run = false;
+    } else if (bn == 0.0) {
+#pragma unroll
+        for (int k = 0; k < CL_RMAX; ++k) {
+            const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+            if (li < nloc) xg[r0 + li] = T(0);
+        }
+        o.status = GK_OK;
+        run = false;
+    } else if (!isfinite(bn)) {
+        o.status = GK_ERR_NAN;
+        run = false;
+    }
+    // r = b - A x (gathering x)
+    auto true_resid = [&](double& nrm) {
+        double a[1] = {0.0};
+#pragma unroll
+        for (int k = 0; k < CL_RMAX; ++k) {
+            const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+            if (li < nloc) {
+                const int32_t i = r0 + li;
+                r[k] = b[i] - cluster_row_dot<V, T>(cl, A, va, g_s, i, rank);
+                a[0] = fma((double)r[k], (double)r[k], a[0]);
+            }
+        }
+        cluster_allsum<1>(cl, a, red, tog);
+        nrm = sqrt(a[0]);
+    };
+    // p = z = M^-1 r into shared memory; rho = <r, z>
+    auto init_dir = [&](double& rho) {
+        double a[1] = {0.0};
+        cl.sync();  // every block is done gathering from g_s
+#pragma unroll
+        for (int k = 0; k < CL_RMAX; ++k) {
+            const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+            if (li < nloc) {
+                const T z = A.prec ? di[k] * r[k] : r[k];
+                g_s[li] = z;
+                a[0] = fma((double)r[k], (double)z, a[0]);
+            }
+        }
+        cluster_allsum<1>(cl, a, red, tog);  // its barrier publishes p
+        rho = a[0];
+    };
+    int32_t it = 0;
+    double rho = 0.0;
+    if (run) {
+        double rn = 0.0;
+        true_resid(rn);
+        o.rec = o.tru = rn / bn;
+        if (!isfinite(rn)) {
+            o.status = GK_ERR_NAN;
+            run = false;
+        } else if (rn <= thr) {
+            o.status = GK_OK;
+            run = false;
+        }
+    }
+    if (run) init_dir(rho);
+    while (run && it < A.max_iters) {
+        double pq[1] = {0.0};
+#pragma unroll
+        for (int k = 0; k < CL_RMAX; ++k) {
+            const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+            if (li < nloc) {
+                q[k] = cluster_row_dot<V, T>(cl, A, va, g_s, r0 + li, rank);
+                pq[0] = fma((double)g_s[li], (double)q[k], pq[0]);
+            }
+        }
+        cluster_allsum<1>(cl, pq, red, tog);
+        if (!isfinite(pq[0])) { o.status = GK_ERR_NAN; break; }
+        if (pq[0] <= 0.0) { o.status = GK_BREAKDOWN; break; }
+        const T ta = (T)(rho / pq[0]);
+        double a2[2] = {0.0, 0.0};
+#pragma unroll
+        for (int k = 0; k < CL_RMAX; ++k) {
+            const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+            if (li < nloc) {
+                x[k] = fmadd(ta, g_s[li], x[k]);
+                r[k] = fmadd(-ta, q[k], r[k]);
+                const T z = A.prec ? di[k] * r[k] : r[k];
+                a2[0] = fma((double)r[k], (double)z, a2[0]);
+                a2[1] = fma((double)r[k], (double)r[k], a2[1]);
+            }
+        }
+        cluster_allsum<2>(cl, a2, red, tog);
+        ++it;
+        const double rn = sqrt(a2[1]);
+        o.rec = rn / bn;
+        if (!isfinite(rn) || !isfinite(a2[0])) { o.status = GK_ERR_NAN; break; }
+        if (rn <= thr) {
+            // publish x, recompute the true residual, replace r on failure
+#pragma unroll
+            for (int k = 0; k < CL_RMAX; ++k) {
+                const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+                if (li < nloc) g_s[li] = x[k];
+            }
+            cl.sync();
+            double tn = 0.0;
+            true_resid(tn);
+            if (tn <= thr) { o.status = GK_OK; break; }
+            o.restarts += 1;
+            init_dir(rho);
+            continue;
+        }
+        const T tb = (T)(a2[0] / rho);
+        rho = a2[0];
+#pragma unroll
+        for (int k = 0; k < CL_RMAX; ++k) {
+            const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+            if (li < nloc) {
+                const T z = A.prec ? di[k] * r[k] : r[k];
+                g_s[li] = fmadd(tb, g_s[li], z);
+            }
+        }
+        cl.sync();
+    }
+    o.iters = it;
+    // write x back and recompute the true residual for the report
+    if (o.status != GK_ERR_ZERO_DIAG && bn > 0.0) {
+        cl.sync();
+#pragma unroll
+        for (int k = 0; k < CL_RMAX; ++k) {
+            const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+            if (li < nloc) {
+                xg[r0 + li] = x[k];
+                g_s[li] = x[k];
+            }
+        }
+        cl.sync();
+        double tn = 0.0;
+        true_resid(tn);
+        o.tru = tn / bn;
+    }
+    cl.sync();  // no block leaves while others may read its shared memory
+    if (rank == 0 && threadIdx.x == 0) *A.out = o;
+}
+
+// Largest n the cluster engine takes.
+int32_t cluster_max_n() { return CL_MAX_BLOCKS * CL_RMAX * CL_THREADS; }
+
+// One CG solve on a cluster of C blocks.  Returns GK_ERR_UNSUPPORTED when
+// the system does not fit or the cluster cannot be scheduled.
+gk_status solve_cluster(gk_matrix A, const void* b, void* x, const gk_solve_opts* o,
+                        cudaStream_t s, SolveOut* out) {
+    if (A->fmt != GK_CSR || o->method != GK_CG || A->n > cluster_max_n()) return GK_ERR_UNSUPPORTED;
+    int C = 16;
+    if (const char* e = getenv("GK_CLUSTER_BLOCKS")) C = atoi(e);
+    C = std::max(1, std::min(C, CL_MAX_BLOCKS));
+    while (C > 1 && (A->n + C - 1) / C > CL_RMAX * CL_THREADS) ++C;
+    const int32_t rpb = (A->n + C - 1) / C;
+    if (rpb > CL_RMAX * CL_THREADS || C > CL_MAX_BLOCKS) return GK_ERR_UNSUPPORTED;
+    static thread_local DevBuf outbuf;
+    static thread_local SolveOut* hout = nullptr;
+    GK_TRY(outbuf.ensure(sizeof(SolveOut)));
+    if (!hout) GK_CUDA(cudaMallocHost(&hout, sizeof(SolveOut)));
+    ClusterArgs args{A->n, rpb, A->row_ptr, A->col, A->val, b, x, o->tol, o->max_iters,
+                     o->precond == GK_PRECOND_JACOBI, (SolveOut*)outbuf.ptr};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(CL_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    auto go = [&](auto kern) -> cudaError_t {
+        if (C > 8) {
+            cudaError_t a = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (a != cudaSuccess) return a;
+        }
+        int nclusters = 0;
+        cudaError_t q = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+        if (q != cudaSuccess) return q;
+        if (nclusters < 1) return cudaErrorLaunchOutOfResources;
+        return cudaLaunchKernelEx(&cfg, kern, args);
+    };
+    if (A->dtype == GK_F64) e = go(k_cluster_cg<double, double>);
+    else if (A->dtype == GK_F32) e = go(k_cluster_cg<float, float>);
+    else e = go(k_cluster_cg<__nv_bfloat16, float>);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return GK_ERR_UNSUPPORTED;
+    }
+    GK_CUDA(cudaMemcpyAsync(hout, outbuf.ptr, sizeof(SolveOut), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    *out = *hout;
+    return GK_OK;
+}
+
+}  // namespace gk

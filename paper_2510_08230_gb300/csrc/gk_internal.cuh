@@ -123,19 +123,21 @@ struct DevBuf {
 };
 
 // ------------------------------------------------------------------ matrix
-// CSR row-tile plan: tile c covers rows [tile_row[c], tile_row[c+1]); its
-// nonzeros fit in `tile_cap` entries (launch plan of the row-tile kernel).
+// CSR launch plan.  Row tiles: tile c covers the rows starting in nonzero
+// chunk c; tile_desc[c] = {first row, end row, aligned first nonzero,
+// staged entries}, staged entries <= tile_cap.  Merge path: block_row[b] =
+// first row of merge block b (n_blocks + 1 entries).
 struct CsrPlan {
     int kind = 0;            // 0 vector (G lanes / row), 1 row-tile, 2 merge
     int lanes = 1;           // vector kernel lanes per row
     int32_t ntiles = 0;
     int32_t chunk = 0;       // nnz per chunk used to cut tiles
-    int32_t tile_cap = 0;    // smem capacity in entries (>= chunk + max_row)
-    int32_t* tile_row = nullptr;  // ntiles + 1
-    // merge kernel
-    int32_t merge_tiles = 0;
-    int32_t merge_items = 0;      // nnz per merge tile
-    int32_t* merge_row = nullptr; // row containing the first nnz of each merge tile (+1)
+    int32_t tile_cap = 0;    // staged entries per tile (>= chunk + max_row + 14)
+    int32_t stages = 0;      // row-tile pipeline depth (0 = as many as fit, max 3)
+    int4* tile_desc = nullptr;
+    int32_t merge_blocks = 0;
+    int32_t* block_row = nullptr;
+    int32_t* err = nullptr;  // device word set by a kernel whose bounded wait ran out
 };
 
 struct SolverCache;  // solve.cu

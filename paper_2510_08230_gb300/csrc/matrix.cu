@@ -412,40 +412,47 @@ __global__ void k_padded_to_csr(int32_t n, int fmt, int64_t stride, int32_t K, i
     }
 }
 
-// Row-tile plan: tile c starts at the first row whose row_ptr >= c * chunk.
-__global__ void k_tile_rows(int32_t n, const int32_t* __restrict__ rp, int32_t chunk,
-                            int32_t ntiles, int32_t* __restrict__ tile_row) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= ntiles;
+__device__ __forceinline__ int32_t rows_before_nnz(int32_t n, const int32_t* __restrict__ rp,
+                                                   int64_t target) {
+    int32_t lo = 0, hi = n;  // first row r with row_ptr[r] >= target
+    while (lo < hi) {
+        const int32_t mid = lo + ((hi - lo) >> 1);
+        if ((int64_t)rp[mid] < target) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Row-tile plan: tile c holds the rows whose first nonzero lies in
+// [c * chunk, (c + 1) * chunk); its staged range is rounded out to 8 entries.
+__global__ void k_tile_desc(int32_t n, const int32_t* __restrict__ rp, int32_t chunk,
+                            int32_t ntiles, int4* __restrict__ desc) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ntiles;
          c += (int64_t)gridDim.x * blockDim.x) {
-        if (c == ntiles) {
-            tile_row[c] = n;
-            continue;
-        }
-        const int64_t target = c * (int64_t)chunk;
-        int32_t lo = 0, hi = n;  // lower_bound over rp[0..n)
-        while (lo < hi) {
-            int32_t mid = lo + ((hi - lo) >> 1);
-            if ((int64_t)rp[mid] < target) lo = mid + 1;
-            else hi = mid;
-        }
-        tile_row[c] = lo;
+        const int32_t r0 = rows_before_nnz(n, rp, c * (int64_t)chunk);
+        const int32_t r1 = (c + 1 == ntiles) ? n : rows_before_nnz(n, rp, (c + 1) * (int64_t)chunk);
+        const int32_t e0 = r0 < r1 ? rp[r0] : 0, e1 = r0 < r1 ? rp[r1] : 0;
+        const int32_t a0 = e0 & ~7;
+        const int32_t w = (e1 > e0) ? (((e1 + 7) & ~7) - a0) : 0;
+        desc[c] = make_int4(r0, r1, a0, w);
     }
 }
 
-// Merge plan: row that contains nonzero t * items (first row r with
-// row_ptr[r+1] > t * items), skipping empty rows.
-__global__ void k_merge_rows(int32_t n, const int32_t* __restrict__ rp, int32_t items,
-                             int32_t ntiles, int32_t* __restrict__ mrow) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= ntiles;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t target = t * (int64_t)items;
-        int32_t lo = 0, hi = n;  // first r with rp[r+1] > target
+// Merge plan: block b starts at path item b * items; its first row is the
+// number of rows whose end item lies before that point.
+__global__ void k_merge_rows(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
+                             int32_t items, int32_t nblocks, int32_t* __restrict__ mrow) {
+    const int64_t N = (int64_t)n + nnz;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b <= nblocks;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = min(b * (int64_t)items, N);
+        int32_t lo = 0, hi = n;
         while (lo < hi) {
-            int32_t mid = lo + ((hi - lo) >> 1);
-            if ((int64_t)rp[mid + 1] > target) hi = mid;
+            const int32_t mid = lo + ((hi - lo) >> 1);
+            if ((int64_t)rp[mid + 1] + mid + 1 > d) hi = mid;
             else lo = mid + 1;
         }
-        mrow[t] = lo;
+        mrow[b] = lo;
     }
 }
 
@@ -487,14 +494,16 @@ static void free_arrays(gk_matrix A) {
     dfree(A->val);
     dfree(A->slice_len);
     dfree(A->slice_set);
-    dfree(A->plan.tile_row);
-    dfree(A->plan.merge_row);
+    dfree(A->plan.tile_desc);
+    dfree(A->plan.block_row);
+    dfree(A->plan.err);
     dfree(A->dinv);
     A->row_ptr = A->col = nullptr;
     A->val = nullptr;
     A->slice_len = nullptr;
     A->slice_set = nullptr;
-    A->plan.tile_row = A->plan.merge_row = nullptr;
+    A->plan.tile_desc = nullptr;
+    A->plan.block_row = A->plan.err = nullptr;
     A->dinv = nullptr;
 }
 
@@ -510,39 +519,51 @@ static void destroy_handle(gk_matrix A) {
     delete A;
 }
 
-// CSR launch plan: row tiles when rows are short, merge tiles otherwise.
+// CSR launch plan: row tiles when rows are short, merge path otherwise.
 gk_status build_csr_plan(gk_matrix A, cudaStream_t s) {
     CsrPlan& P = A->plan;
-    dfree(P.tile_row);
-    dfree(P.merge_row);
+    dfree(P.tile_desc);
+    dfree(P.block_row);
+    dfree(P.err);
     P = CsrPlan();
+    GK_CUDA(dmalloc_t(&P.err, 4));
+    GK_CUDA(cudaMemsetAsync(P.err, 0, 4, s));
     if (A->fmt != GK_CSR || A->n == 0) return GK_OK;
     const double mean = A->mean_row;
     int lanes = 1;
     while (lanes < 32 && lanes < mean) lanes <<= 1;
     P.lanes = lanes;
-    // row-tile kernel: chunk ~ 256 rows of mean length, capacity chunk + max row
-    int32_t chunk = (int32_t)std::min<double>(4096.0, std::max<double>(512.0, 256.0 * std::ceil(std::max(mean, 1.0))));
+    // row tiles of ~rows_per_tile rows of mean length; staged capacity
+    // covers the chunk plus the longest row plus alignment slack
+    int rows_per_tile = 256;
+    if (const char* e = getenv("GK_TILE_ROWS")) rows_per_tile = std::max(32, atoi(e));
+    int32_t chunk = (int32_t)std::min<double>(
+        4096.0, std::max<double>(512.0, rows_per_tile * std::ceil(std::max(mean, 1.0))));
     chunk = (chunk + 7) & ~7;
     const int64_t cap = (int64_t)chunk + A->max_row + 16;
-    const char* force = getenv("GK_CSR_KERNEL");
-    int kind = (A->max_row <= 4 * chunk && A->max_row <= 1024) ? 1 : 2;
-    if (force) kind = atoi(force);
+    int kind = (A->max_row <= 1024) ? 1 : 2;
+    if (const char* force = getenv("GK_CSR_KERNEL")) kind = atoi(force);
+    // a single staged tile must fit in shared memory
+    if (kind == 1 && ((cap + 7) & ~7) * (int64_t)(4 + value_bytes(A->dtype)) > 200 * 1024) kind = 2;
     P.kind = kind;
+    if (const char* e = getenv("GK_ROWTILE_STAGES")) P.stages = std::max(1, std::min(3, atoi(e)));
     if (kind == 1) {
         P.chunk = chunk;
         P.tile_cap = (int32_t)((cap + 7) & ~7);
         P.ntiles = (int32_t)std::max<int64_t>(1, (A->nnz + chunk - 1) / chunk);
-        GK_CUDA(dmalloc_t(&P.tile_row, (size_t)P.ntiles + 1));
-        k_tile_rows<<<grid_for(P.ntiles + 1), 256, 0, s>>>(A->n, A->row_ptr, chunk, P.ntiles,
-                                                           P.tile_row);
+        GK_CUDA(dmalloc_t(&P.tile_desc, (size_t)P.ntiles));
+        k_tile_desc<<<grid_for(P.ntiles), 256, 0, s>>>(A->n, A->row_ptr, chunk, P.ntiles,
+                                                       P.tile_desc);
         GK_CUDA(cudaGetLastError());
     } else if (kind == 2) {
-        P.merge_items = 2048;
-        P.merge_tiles = (int32_t)std::max<int64_t>(1, (A->nnz + P.merge_items - 1) / P.merge_items);
-        GK_CUDA(dmalloc_t(&P.merge_row, (size_t)P.merge_tiles + 1));
-        k_merge_rows<<<grid_for(P.merge_tiles + 1), 256, 0, s>>>(A->n, A->row_ptr, P.merge_items,
-                                                                 P.merge_tiles, P.merge_row);
+        const int E = value_bytes(A->dtype) >= 8 ? 8 : 12;
+        const int64_t items = 256 * (int64_t)E;
+        const int64_t N = (int64_t)A->n + A->nnz;
+        P.merge_blocks = (int32_t)std::max<int64_t>(1, (N + items - 1) / items);
+        GK_CUDA(dmalloc_t(&P.block_row, (size_t)P.merge_blocks + 1));
+        k_merge_rows<<<grid_for(P.merge_blocks + 1), 256, 0, s>>>(A->n, A->nnz, A->row_ptr,
+                                                                  (int32_t)items, P.merge_blocks,
+                                                                  P.block_row);
         GK_CUDA(cudaGetLastError());
     }
     return GK_OK;
@@ -903,6 +924,10 @@ gk_status gk_matrix_describe(gk_matrix A, gk_matrix_desc* d) {
     d->stride_factor = A->f;
     d->num_slices = A->nslices;
     d->spmv_kernel = A->fmt == GK_CSR ? A->plan.kind : A->fmt == GK_ELL ? 3 : 4;
+    if (A->plan.err) {
+        int32_t e = 0;
+        if (cudaMemcpy(&e, A->plan.err, 4, cudaMemcpyDeviceToHost) == cudaSuccess) d->device_error = e;
+    }
     d->spmv_launches = (A->fmt == GK_CSR && A->plan.kind == 2) ? 2 : 1;
     const size_t vb = value_bytes(A->dtype);
     if (A->fmt == GK_CSR) {

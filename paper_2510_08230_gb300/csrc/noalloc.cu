@@ -36,6 +36,9 @@ static gk_status noalloc_scratch(void** out) {
     if (!g_noalloc_ptr[dev]) {
         void* p = nullptr;
         GK_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        GK_CUDA(cudaFuncSetAttribute(k_csr_merge<NA_ITEMS_PER_THREAD, double, double>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)merge_smem_bytes<NA_ITEMS_PER_THREAD, double, double>()));
         g_noalloc_ptr[dev] = p;
     }
     *out = g_noalloc_ptr[dev];
@@ -65,8 +68,9 @@ extern "C" gk_status gk_spmv_csr_f64_noalloc(int32_t n, int32_t ncols, int64_t n
     // scratch needs no clearing between calls
     int32_t* crow = static_cast<int32_t*>(scratch);
     double* cval = reinterpret_cast<double*>(static_cast<char*>(scratch) + NA_MAX_BLOCKS * 4);
-    k_csr_merge<E, double, double><<<(unsigned)nb, 256, 0, s>>>(n, nnz, row_ptr, col_idx, values,
-                                                                b, epi, crow, cval);
+    constexpr size_t smem = merge_smem_bytes<E, double, double>();
+    k_csr_merge<E, double, double><<<(unsigned)nb, 256, smem, s>>>(
+        n, nnz, row_ptr, col_idx, values, b, epi, nullptr, crow, cval);
     const unsigned fg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, 4096));
     k_csr_merge_fixup<double><<<fg, 256, 0, s>>>((int32_t)nb, crow, cval, x, alpha, mode);
     GK_CUDA(cudaGetLastError());

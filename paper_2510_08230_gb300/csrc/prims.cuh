@@ -114,26 +114,39 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Fixed-order sum of NA per-thread values over the block; result valid in
-// thread 0.  All threads must call.
+// Fixed-order sum of NA per-thread values over the block (blockDim <= 512);
+// the result is valid in every lane of warp 0.  All threads must call.
+// FP64 warp instructions are expensive on this part (~16 SM cycles each),
+// so threads only store their values and warp 0 adds them: blockDim/32
+// sequential adds per lane and a 5-level shuffle tree per value.
 template <int NA>
 __device__ __forceinline__ void block_sum(double (&v)[NA]) {
-    __shared__ double sh[NA > 0 ? NA : 1][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nw = (blockDim.x + 31) >> 5;
+    __shared__ double sh[NA > 0 ? NA : 1][512];
 #pragma unroll
-    for (int a = 0; a < NA; ++a) {
-        double w = warp_sum(v[a]);
-        if (lane == 0) sh[a][warp] = w;
-    }
+    for (int a = 0; a < NA; ++a) sh[a][threadIdx.x] = v[a];
     __syncthreads();
-    if (warp == 0) {
+    if (threadIdx.x < 32) {
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
-            double w = lane < nw ? sh[a][lane] : 0.0;
-            v[a] = warp_sum(w);
+            double s = 0.0;
+            for (unsigned i = threadIdx.x; i < blockDim.x; i += 32) s += sh[a][i];
+            v[a] = warp_sum(s);
         }
     }
+    __syncthreads();
+}
+
+// block_sum with the result broadcast to every thread of the block.
+template <int NA>
+__device__ __forceinline__ void block_allsum_bcast(double (&v)[NA]) {
+    __shared__ double tot[NA > 0 ? NA : 1];
+    block_sum<NA>(v);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int a = 0; a < NA; ++a) tot[a] = v[a];
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < NA; ++a) v[a] = tot[a];
     __syncthreads();
 }
 

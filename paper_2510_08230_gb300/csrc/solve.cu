@@ -95,6 +95,7 @@ struct EpiResid {
         double a[1] = {acc[0]};
         grid_reduce_finish<1>(a, partials, ticket, fin);
     }
+    __device__ __forceinline__ void timed_out() const {}
 };
 
 // y_i = s ; acc += w_i * s
@@ -118,6 +119,7 @@ struct EpiDot {
         double a[1] = {acc[0]};
         grid_reduce_finish<1>(a, partials, ticket, fin);
     }
+    __device__ __forceinline__ void timed_out() const {}
 };
 
 // y_i = s ; acc0 += s * u_i ; acc1 += s * s
@@ -142,6 +144,7 @@ struct EpiDot2 {
         double a[2] = {acc[0], acc[1]};
         grid_reduce_finish<2>(a, partials, ticket, fin);
     }
+    __device__ __forceinline__ void timed_out() const {}
 };
 
 // plain store with a halt check (GMRES w = A z)
@@ -155,6 +158,7 @@ struct EpiStoreHalt {
     }
     __device__ __forceinline__ void row(int64_t i, T s, double*) const { y[i] = s; }
     __device__ __forceinline__ void finish(double*) const {}
+    __device__ __forceinline__ void timed_out() const {}
 };
 
 // ------------------------------------------------------------ elementwise
@@ -738,6 +742,7 @@ struct EpiGmResid {
         double a[1] = {acc[0]};
         grid_reduce_finish<1>(a, partials, ticket, fin);
     }
+    __device__ __forceinline__ void timed_out() const {}
 };
 
 // v_0 = r / beta0 ; z = M^-1 v_0 (after a restart decided to continue)
@@ -846,6 +851,7 @@ struct EpiBiT {
         double a[2] = {acc[0], acc[1]};
         grid_reduce_finish<2>(a, partials, ticket, fin);
     }
+    __device__ __forceinline__ void timed_out() const {}
 };
 
 template <typename T>
@@ -1199,6 +1205,7 @@ static gk_status check_opts(gk_matrix A, const gk_solve_opts* o) {
     if (o->krylov_dim < 0 || o->krylov_dim > MAXM) return GK_ERR_INVALID;
     if (o->mixed < 0 || o->mixed > 2) return GK_ERR_INVALID;
     if (o->mixed && A->dtype != GK_F64) return GK_ERR_INVALID;
+    if (o->engine < 0 || o->engine > 3) return GK_ERR_INVALID;
     if (A->n != A->ncols) return GK_ERR_INVALID;
     return GK_OK;
 }
@@ -1308,6 +1315,9 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
 
 gk_status solve_small(gk_matrix A, const void* b, void* x, const gk_solve_opts* o, cudaStream_t s,
                       SolveOut* out);
+gk_status solve_cluster(gk_matrix A, const void* b, void* x, const gk_solve_opts* o,
+                        cudaStream_t s, SolveOut* out);
+int32_t cluster_max_n();
 
 }  // namespace gk
 
@@ -1334,9 +1344,16 @@ extern "C" gk_status gk_solve(gk_matrix A, const void* b, void* x, const gk_solv
     } else if (opts->mixed) {
         st = solve_ir(A, (const double*)b, (double*)x, opts, s, &out, &outer);
     } else {
-        const bool small = opts->engine == 2;
-        if (small) {
+        int engine = opts->engine;
+        if (engine == 0 && A->fmt == GK_CSR && opts->method == GK_CG && A->n <= cluster_max_n())
+            engine = 3;
+        if (engine == 3) {
+            st = solve_cluster(A, b, x, opts, s, &out);
+            if (st == GK_ERR_UNSUPPORTED && opts->engine == 0) engine = 1;  // cannot schedule
+        }
+        if (engine == 2) {
             st = solve_small(A, b, x, opts, s, &out);
+        } else if (engine == 3) {
         } else if (A->dtype == GK_F64) {
             st = solve_plain<double, double>(A, b, x, opts, s, &out);
         } else if (A->dtype == GK_F32) {

@@ -8,14 +8,18 @@
 // last act is epi.finish(acc), which reduces those partials across the grid
 // deterministically (fixed order, last block finishes).
 //
-// FP64 note for GB300: the FP64 pipe runs about 2 lane-FMAs per SM cycle,
+// FP64 note for GB300: the FP64 pipe retires about 2 lane-FMAs per SM cycle
+// (a warp instruction occupies it ~16 SM cycles whatever its active mask),
 // close to the rate at which HBM delivers FP64 nonzeros (12 B each).  The
-// kernels therefore spend exactly one FMA per stored nonzero and reduce a
-// row sum within one thread (row-tile, ELL, SELL-P) or with carries between
-// threads (merge-path); no FP64 shuffle trees on the per-row path.
+// kernels therefore spend one FMA per stored nonzero, keep warps converged
+// in the FMA loops, and reduce a row within one thread (row-tile, ELL,
+// SELL-P) or with carries between threads (merge-path); no FP64 shuffle
+// trees on the per-row path.  Loads that feed the FMAs are issued in
+// batches of 8 before the first FMA so that their latencies overlap.
 #pragma once
 
 #include "prims.cuh"
+#include "tma.cuh"
 
 namespace gk {
 
@@ -35,6 +39,7 @@ struct EpiStore {
         else y[i] = fmadd(beta, y[i], alpha * s);
     }
     __device__ __forceinline__ void finish(double*) const {}
+    __device__ __forceinline__ void timed_out() const {}
 };
 
 template <class Epi>
@@ -42,92 +47,208 @@ struct AccArr {
     double v[Epi::NA > 0 ? Epi::NA : 1];
 };
 
-// ------------------------------------------------------------ kernels
+constexpr int GATHER = 8;  // loads issued ahead of the FMAs that use them
 
-// CSR row-tile kernel.  Tile c = rows [tile_row[c], tile_row[c+1]) whose
-// nonzeros fit in `cap` entries.  The block copies the tile's col/val
-// range into shared memory with 16-byte streaming loads (range rounded out
-// to 8-entry alignment; allocations carry 64 bytes of slack), then one
-// thread per row accumulates its row sequentially from shared memory.
+// sum_{k in [ks, ke)} val[k] * x[col[k]] with values/columns in shared memory
+template <typename T, typename V>
+__device__ __forceinline__ T row_sum_staged(const int32_t* s_col, const V* s_val,
+                                            const T* __restrict__ x, int32_t ks, int32_t ke) {
+    T s = T(0);
+    for (int32_t k0 = ks; k0 < ke; k0 += GATHER) {
+        const int32_t m = min(GATHER, ke - k0);
+        T vv[GATHER], xv[GATHER];
+#pragma unroll
+        for (int u = 0; u < GATHER; ++u) {
+            if (u < m) {
+                vv[u] = cvt<T>(s_val[k0 + u]);
+                xv[u] = __ldg(x + s_col[k0 + u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < GATHER; ++u) {
+            if (u >= m) break;
+            s = fmadd(vv[u], xv[u], s);
+        }
+    }
+    return s;
+}
+
+// ------------------------------------------------------------ row-tile CSR
+
+// Tile descriptor: rows [x, y), staged nonzero range [z, z + w) with z a
+// multiple of 8 and w a multiple of 8 (16-byte aligned bulk copies).
+//
+// Persistent blocks take tiles c = blockIdx.x + k * gridDim.x.  Thread 0
+// keeps NST (1..3) tiles in flight: for each it issues two cp.async.bulk copies
+// (columns, values) into a shared-memory stage and arms the stage's
+// mbarrier with the byte count.  All threads wait on the barrier (bounded),
+// then one thread per row runs its row from shared memory; after a block
+// barrier the stage is refilled with the tile NST steps ahead.
 template <typename V, typename T, class Epi>
 __global__ void __launch_bounds__(256)
-k_csr_rowtile(int32_t ntiles, const int32_t* __restrict__ tile_row,
-              const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-              const V* __restrict__ va, const T* __restrict__ x, int32_t cap, Epi epi) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    int32_t* s_col = reinterpret_cast<int32_t*>(smem);
-    V* s_val = reinterpret_cast<V*>(smem + (size_t)cap * 4);
+k_csr_rowtile(int32_t ntiles, const int4* __restrict__ tdesc, const int32_t* __restrict__ rp,
+              const int32_t* __restrict__ ci, const V* __restrict__ va,
+              const T* __restrict__ x, int32_t cap, int NST, Epi epi, int32_t* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint32_t cbytes = (uint32_t)cap * 4u;
+    const uint32_t sbytes = (uint32_t)cap * (4u + (uint32_t)sizeof(V));
     if (epi.skip()) return;
     AccArr<Epi> acc{};
-    for (int32_t c = blockIdx.x; c < ntiles; c += gridDim.x) {
-        const int32_t r0 = __ldg(tile_row + c), r1 = __ldg(tile_row + c + 1);
-        if (r0 >= r1) continue;  // uniform over the block
-        const int32_t e0 = __ldg(rp + r0), e1 = __ldg(rp + r1);
-        const int32_t a0 = e0 & ~7;
-        const int32_t cnt = ((e1 + 7) & ~7) - a0;
-        {
-            const int4* gc = reinterpret_cast<const int4*>(ci + a0);
-            int4* sc = reinterpret_cast<int4*>(s_col);
-            for (int k = threadIdx.x; k < (cnt >> 2); k += blockDim.x) sc[k] = __ldcs(gc + k);
-            const int nv = (int)((cnt * sizeof(V)) >> 4);
-            const int4* gv = reinterpret_cast<const int4*>(va + a0);
-            int4* sv = reinterpret_cast<int4*>(s_val);
-            for (int k = threadIdx.x; k < nv; k += blockDim.x) sv[k] = __ldcs(gv + k);
+    const uint32_t bar0 = smem_addr(smem + (size_t)NST * sbytes);
+    const uint32_t buf0 = smem_addr(smem);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) mbar_init(bar0 + 8u * s, 1u);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int32_t stride = (int32_t)gridDim.x;
+    auto issue = [&](int32_t c, int s) {
+        const int4 d = __ldg(tdesc + c);
+        const uint32_t nc = (uint32_t)d.w * 4u, nv = (uint32_t)d.w * (uint32_t)sizeof(V);
+        const uint32_t bar = bar0 + 8u * s;
+        mbar_arrive_expect_tx(bar, nc + nv);
+        if (d.w > 0) {
+            bulk_g2s(buf0 + s * sbytes, ci + d.z, nc, bar);
+            bulk_g2s(buf0 + s * sbytes + cbytes, va + d.z, nv, bar);
+        }
+    };
+    if (threadIdx.x == 0)
+        for (int s = 0; s < NST; ++s) {
+            const int32_t c = (int32_t)blockIdx.x + s * stride;
+            if (c < ntiles) issue(c, s);
+        }
+    int it = 0;
+    bool timed_out = false;
+    for (int32_t c = blockIdx.x; c < ntiles; c += stride, ++it) {
+        const int s = it % NST;
+        const bool ok = mbar_wait_bounded(bar0 + 8u * s, (uint32_t)(it / NST) & 1u);
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        const int4 d = __ldg(tdesc + c);
+        const int32_t* s_col = reinterpret_cast<const int32_t*>(smem + (size_t)s * sbytes);
+        const V* s_val = reinterpret_cast<const V*>(smem + (size_t)s * sbytes + cbytes);
+        for (int32_t r = d.x + (int32_t)threadIdx.x; r < d.y; r += blockDim.x) {
+            const int32_t ks = __ldg(rp + r) - d.z, ke = __ldg(rp + r + 1) - d.z;
+            epi.row(r, row_sum_staged<T, V>(s_col, s_val, x, ks, ke), acc.v);
         }
         __syncthreads();
-        for (int32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-            const int32_t ks = __ldg(rp + r) - a0, ke = __ldg(rp + r + 1) - a0;
-            T s = T(0);
-            for (int32_t k = ks; k < ke; ++k)
-                s = fmadd(cvt<T>(s_val[k]), __ldg(x + s_col[k]), s);
-            epi.row(r, s, acc.v);
+        if (threadIdx.x == 0) {
+            const int32_t cn = c + NST * stride;
+            if (cn < ntiles) {
+                fence_proxy_async_smem();
+                issue(cn, s);
+            }
         }
-        __syncthreads();
+    }
+    if (timed_out) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+        epi.timed_out();
+        // let the copies already issued land before the block exits (bounded)
+        for (int k = 0; k < NST; ++k) {
+            const int32_t c = (int32_t)blockIdx.x + (it + k) * stride;
+            if (c >= ntiles) break;
+            mbar_wait_bounded(bar0 + 8u * ((it + k) % NST), (uint32_t)((it + k) / NST) & 1u);
+        }
     }
     epi.finish(acc.v);
 }
 
+// ------------------------------------------------------------ merge-path CSR
+
+// Shared-memory index with one pad slot per 8, so that threads walking
+// consecutive 8-entry segments hit different banks.
+__device__ __forceinline__ int mpad(int k) { return k + (k >> 3); }
+
+constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// Shared-memory layout of the merge kernel; every array starts on a
+// 16-byte boundary: values, gathered x, thread carries, row ends, thread rows.
+template <int E, typename V, typename T>
+struct MergeShape {
+    static constexpr int TI = 256 * E;            // path items per block
+    static constexpr int PADN = TI + TI / 8 + 8;  // padded entries
+    static constexpr size_t OFF_XV = align16((size_t)PADN * sizeof(V));
+    static constexpr size_t OFF_TC = align16(OFF_XV + (size_t)PADN * sizeof(T));
+    static constexpr size_t OFF_RE = align16(OFF_TC + 256 * sizeof(T));
+    static constexpr size_t OFF_TR = align16(OFF_RE + (size_t)(TI + 1) * 4);
+    static constexpr size_t BYTES = align16(OFF_TR + 256 * 4);
+};
+
+template <int E, typename V, typename T>
+constexpr size_t merge_smem_bytes() {
+    return MergeShape<E, V, T>::BYTES;
+}
+
 // CSR merge-path kernel (apply only).  The path of n row ends and nnz
 // nonzeros is cut into equal pieces of 256*E items per block and E items
-// per thread; each thread walks its piece sequentially (one FMA per
-// nonzero).  A row whose end lies in a thread's piece is finished there,
-// adding the carries of earlier threads of the block whose pieces ended
-// inside the same row.  The row open at the end of a block is handed to
-// k_csr_merge_fixup as (carry_row, carry_val).
+// per thread.  Phase 1: the block stages its row ends, values and the
+// gathered x values (all gathers independent, so many are in flight).
+// Phase 2: each thread walks its piece sequentially from shared memory (one
+// FMA per nonzero).  A row whose end lies in a thread's piece is finished
+// there, adding the carries of earlier threads of the block whose pieces
+// ended inside the same row.  The row open at the end of a block is handed
+// to k_csr_merge_fixup as (carry_row, carry_val).  block_row (n_blocks + 1
+// entries) gives each block's first row; when null the block finds it by
+// binary search.
 template <int E, typename V, typename T>
 __global__ void __launch_bounds__(256)
 k_csr_merge(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
             const int32_t* __restrict__ ci, const V* __restrict__ va,
-            const T* __restrict__ x, EpiStore<T> epi, int32_t* __restrict__ carry_row,
-            T* __restrict__ carry_val) {
-    constexpr int TI = 256 * E;
-    __shared__ int32_t s_rowend[TI + 1];
-    __shared__ int32_t s_col[TI];
-    __shared__ V s_val[TI];
-    __shared__ int32_t s_trow[256];
-    __shared__ T s_tcarry[256];
+            const T* __restrict__ x, EpiStore<T> epi, const int32_t* __restrict__ block_row,
+            int32_t* __restrict__ carry_row, T* __restrict__ carry_val) {
+    using Sh = MergeShape<E, V, T>;
+    constexpr int TI = Sh::TI;
+    extern __shared__ __align__(16) unsigned char smem[];
+    V* s_val = reinterpret_cast<V*>(smem);
+    T* s_xv = reinterpret_cast<T*>(smem + Sh::OFF_XV);
+    T* s_tcarry = reinterpret_cast<T*>(smem + Sh::OFF_TC);
+    int32_t* s_rowend = reinterpret_cast<int32_t*>(smem + Sh::OFF_RE);
+    int32_t* s_trow = reinterpret_cast<int32_t*>(smem + Sh::OFF_TR);
     __shared__ int32_t s_bounds[2];
     const int64_t N = (int64_t)n + nnz;
     const int64_t d0 = (int64_t)blockIdx.x * TI;
     const int64_t d1 = min(d0 + TI, N);
     if (threadIdx.x < 2) {
-        const int64_t d = threadIdx.x == 0 ? d0 : d1;
-        int32_t lo = 0, hi = n;  // rows whose end item lies before d
-        while (lo < hi) {
-            const int32_t mid = lo + ((hi - lo) >> 1);
-            if ((int64_t)__ldg(rp + mid + 1) + mid + 1 > d) hi = mid;
-            else lo = mid + 1;
+        if (block_row) {
+            s_bounds[threadIdx.x] = __ldg(block_row + blockIdx.x + threadIdx.x);
+        } else {
+            const int64_t d = threadIdx.x == 0 ? d0 : d1;
+            int32_t lo = 0, hi = n;  // rows whose end item lies before d
+            while (lo < hi) {
+                const int32_t mid = lo + ((hi - lo) >> 1);
+                if ((int64_t)__ldg(rp + mid + 1) + mid + 1 > d) hi = mid;
+                else lo = mid + 1;
+            }
+            s_bounds[threadIdx.x] = lo;
         }
-        s_bounds[threadIdx.x] = lo;
     }
     __syncthreads();
     const int32_t i0 = s_bounds[0], i1 = s_bounds[1];
     const int64_t j0 = d0 - i0, j1 = d1 - i1;
     const int32_t nloc = min(i1 - i0 + 1, n - i0);  // staged row ends
+    const int32_t cnt = (int32_t)(j1 - j0);
     for (int k = threadIdx.x; k < nloc; k += blockDim.x) s_rowend[k] = __ldg(rp + i0 + k + 1);
-    for (int k = threadIdx.x; k < (int)(j1 - j0); k += blockDim.x) {
-        s_col[k] = __ldcs(ci + j0 + k);
-        s_val[k] = va[j0 + k];
+    for (int k0 = threadIdx.x; k0 < cnt; k0 += 4 * blockDim.x) {
+        int32_t c[4];
+        V v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = k0 + u * (int)blockDim.x;
+            if (k < cnt) {
+                c[u] = __ldcs(ci + j0 + k);
+                v[u] = va[j0 + k];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = k0 + u * (int)blockDim.x;
+            if (k < cnt) {
+                s_val[mpad(k)] = v[u];
+                s_xv[mpad(k)] = __ldg(x + c[u]);
+            }
+        }
     }
     __syncthreads();
     // this thread's start on the path
@@ -147,7 +268,8 @@ k_csr_merge(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
     int64_t rend = (i < n) ? (int64_t)s_rowend[i - i0] : 0;
     for (int64_t d = dt; d < dend; ++d) {
         if (i < n && j < rend) {
-            acc = fmadd(cvt<T>(s_val[j - j0]), __ldg(x + s_col[j - j0]), acc);
+            const int k = mpad((int)(j - j0));
+            acc = fmadd(cvt<T>(s_val[k]), s_xv[k], acc);
             ++j;
         } else {
             if (head_row < 0) {
@@ -173,7 +295,7 @@ k_csr_merge(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
         // open row at the end of the block: sum the trailing carries
         int t = (int)blockDim.x - 1;
         while (t >= 0 && s_trow[t] < 0) --t;
-        int32_t r = t >= 0 ? s_trow[t] : -1;
+        const int32_t r = t >= 0 ? s_trow[t] : -1;
         T v = T(0);
         for (; t >= 0 && s_trow[t] == r; --t) v = s_tcarry[t] + v;
         carry_row[blockIdx.x] = (r >= 0 && r < n) ? r : -1;
@@ -196,6 +318,8 @@ __global__ void k_csr_merge_fixup(int32_t nblocks, const int32_t* __restrict__ c
         y[r] = mode == 0 ? y[r] + v : fmadd(alpha, v, y[r]);
     }
 }
+
+// ------------------------------------------------------------ vector CSR
 
 // CSR vector kernel: G lanes per row (warp = 32/G rows per step), lane
 // partial sums combined with shuffles.
@@ -224,7 +348,26 @@ k_csr_vector(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restric
     epi.finish(acc.v);
 }
 
-// ELL: one thread per row, column-major coalesced loads; padding skipped.
+// ------------------------------------------------------------ ELL / SELL-P
+
+// One row: `len` stored entries at base, base + step, ... (column-major
+// padded layouts).  Padding has col -1 and value 0 and adds nothing.
+template <typename T, typename V>
+__device__ __forceinline__ T row_sum_padded(const int32_t* __restrict__ pc,
+                                            const V* __restrict__ pv, const T* __restrict__ x,
+                                            int64_t base, int64_t step, int32_t len) {
+    T s = T(0);
+#pragma unroll 4
+    for (int32_t j = 0; j < len; ++j) {
+        const int64_t at = base + (int64_t)j * step;
+        const int32_t c = ld_stream(pc + at);
+        const T v = ld_stream(pv + at);
+        if (c >= 0) s = fmadd(v, __ldg(x + c), s);
+    }
+    return s;
+}
+
+// ELL: one thread per row, column-major coalesced loads.
 template <typename V, typename T, class Epi>
 __global__ void __launch_bounds__(256)
 k_ell(int32_t n, int64_t stride, int32_t K, const int32_t* __restrict__ ec,
@@ -232,42 +375,45 @@ k_ell(int32_t n, int64_t stride, int32_t K, const int32_t* __restrict__ ec,
     if (epi.skip()) return;
     AccArr<Epi> acc{};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        T s = T(0);
-        const int32_t* cp = ec + i;
-        const V* vp = ev + i;
-#pragma unroll 4
-        for (int32_t j = 0; j < K; ++j) {
-            const int32_t c = ld_stream(cp + (int64_t)j * stride);
-            const T v = ld_stream(vp + (int64_t)j * stride);
-            if (c >= 0) s = fmadd(v, __ldg(x + c), s);
-        }
-        epi.row(i, s, acc.v);
-    }
+         i += (int64_t)gridDim.x * blockDim.x)
+        epi.row(i, row_sum_padded<T, V>(ec, ev, x, i, stride, K), acc.v);
     epi.finish(acc.v);
 }
 
 // SELL-P: one thread per row; the rows of a slice read consecutive
-// addresses for every stored column position.
+// addresses for every stored column position.  The slice metadata of the
+// thread's next row is loaded before the current row is processed.
 template <typename V, typename T, class Epi>
 __global__ void __launch_bounds__(256)
 k_sellp(int32_t n, int32_t S, const int32_t* __restrict__ slen, const int64_t* __restrict__ sset,
         const int32_t* __restrict__ sc, const V* __restrict__ sv, const T* __restrict__ x, Epi epi) {
     if (epi.skip()) return;
     AccArr<Epi> acc{};
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t sl = i / S, t = i - sl * S;
-        const int32_t len = __ldg(slen + sl);
-        const int64_t base = __ldg(sset + sl) * S + t;
-        T s = T(0);
-#pragma unroll 4
-        for (int32_t j = 0; j < len; ++j) {
-            const int32_t c = ld_stream(sc + base + (int64_t)j * S);
-            const T v = ld_stream(sv + base + (int64_t)j * S);
-            if (c >= 0) s = fmadd(v, __ldg(x + c), s);
+    // row indices fit in 32 bits; S is a power of two in the common case
+    const int sh = (S & (S - 1)) == 0 ? __ffs(S) - 1 : -1;
+    auto slice_of = [&](uint32_t r) -> uint32_t { return sh >= 0 ? (r >> sh) : r / (uint32_t)S; };
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int32_t len = 0;
+    int64_t base = 0;
+    if (i < n) {
+        const uint32_t sl = slice_of((uint32_t)i);
+        len = __ldg(slen + sl);
+        base = __ldg(sset + sl) * S + ((int64_t)i - (int64_t)sl * S);
+    }
+    while (i < n) {
+        const int64_t in = i + G;
+        int32_t len_n = 0;
+        int64_t base_n = 0;
+        if (in < n) {
+            const uint32_t sl = slice_of((uint32_t)in);
+            len_n = __ldg(slen + sl);
+            base_n = __ldg(sset + sl) * S + (in - (int64_t)sl * S);
         }
-        epi.row(i, s, acc.v);
+        epi.row(i, row_sum_padded<T, V>(sc, sv, x, base, S, len), acc.v);
+        i = in;
+        len = len_n;
+        base = base_n;
     }
     epi.finish(acc.v);
 }
@@ -282,36 +428,47 @@ static int occupancy_blocks(K kernel, int threads, size_t smem) {
     return b;
 }
 
-// Grid of a kernel family for matrix A: deterministic for a given matrix
-// and device, so that the partial-sum layout of fused reductions is fixed.
-struct Launch {
-    unsigned grid = 1;
-    size_t smem = 0;
-};
+constexpr int ROWTILE_MAX_STAGES = 3;
+constexpr size_t ROWTILE_SMEM_BUDGET = 200 * 1024;
+
+// stages of the row-tile pipeline that fit the shared-memory budget
+inline int rowtile_stages(const gk_matrix A, size_t vbytes) {
+    const size_t stage = (size_t)A->plan.tile_cap * (4 + vbytes);
+    int nst = A->plan.stages > 0 ? A->plan.stages : ROWTILE_MAX_STAGES;
+    while (nst > 1 && (size_t)nst * stage + 8 * nst > ROWTILE_SMEM_BUDGET) --nst;
+    return nst;
+}
+
+inline size_t rowtile_smem(const gk_matrix A, size_t vbytes) {
+    const int nst = rowtile_stages(A, vbytes);
+    return (size_t)nst * (size_t)A->plan.tile_cap * (4 + vbytes) + 8 * (size_t)nst;
+}
 
 // Launches the row-complete SpMV of A (row-tile / vector CSR, ELL, SELL-P)
 // with epilogue epi.  For epilogues with NA > 0, the caller provides
-// partials (NA * max_grid doubles) and a zeroed ticket through epi.
+// partials (NA * num_sms() * 8 doubles) and a zeroed ticket through epi.
+// The grid depends only on the matrix and the device, so the partial-sum
+// layout of fused reductions is fixed.
 template <typename V, typename T, class Epi>
 gk_status launch_spmv_rows(gk_matrix A, const T* x, const Epi& epi, cudaStream_t s,
                            unsigned* grid_out = nullptr) {
     const int sms = num_sms();
     unsigned grid = 1;
     if (A->fmt == GK_CSR && A->plan.kind == 1) {
-        const size_t smem = (size_t)A->plan.tile_cap * (4 + sizeof(V));
+        const size_t smem = rowtile_smem(A, sizeof(V));
+        const int nst = rowtile_stages(A, sizeof(V));
         auto k = k_csr_rowtile<V, T, Epi>;
         static thread_local int occ_cache = 0;
         static thread_local size_t occ_smem = 0;
         if (occ_smem != smem || !occ_cache) {
-            if (smem > 48 * 1024)
-                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            occ_cache = occupancy_blocks(k, 256, smem);
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            occ_cache = std::min(occupancy_blocks(k, 256, smem), 8);
             occ_smem = smem;
         }
         grid = (unsigned)std::min<int64_t>(A->plan.ntiles, (int64_t)sms * occ_cache);
         if (grid < 1) grid = 1;
-        k<<<grid, 256, smem, s>>>(A->plan.ntiles, A->plan.tile_row, A->row_ptr, A->col,
-                                  (const V*)A->val, x, A->plan.tile_cap, epi);
+        k<<<grid, 256, smem, s>>>(A->plan.ntiles, A->plan.tile_desc, A->row_ptr, A->col,
+                                  (const V*)A->val, x, A->plan.tile_cap, nst, epi, A->plan.err);
     } else if (A->fmt == GK_CSR) {
         const int G = A->plan.lanes;
         const int64_t rows_per_block = 256 / G;
@@ -344,5 +501,11 @@ gk_status launch_spmv_rows(gk_matrix A, const T* x, const Epi& epi, cudaStream_t
 
 // Upper bound of the grid launch_spmv_rows uses for A (sizes partials).
 inline unsigned max_grid_rows(gk_matrix A) { return (unsigned)num_sms() * 8; }
+
+// merge-path items per thread for a value type
+template <typename V>
+struct MergeE {
+    static constexpr int value = sizeof(V) >= 8 ? 8 : 12;
+};
 
 }  // namespace gk

@@ -387,3 +387,40 @@ def random_coo(n: int, ncols: int, nnz: int, seed: int, dup_frac: float = 0.2,
     r, c = r[perm], c[perm]
     v = rng.standard_normal(r.size).astype(dtype)
     return r.astype(np.int32), c.astype(np.int32), v
+
+
+def serving_pool(count: int = 24, seed: int = SEED_BASE + 5, n_lo: float = 1e3,
+                 n_hi: float = 1e6, max_nnz: int = 20_000_000):
+    """Matrices for the serving mix: sizes log-uniform in [n_lo, n_hi], kind
+    uniform over {2D 5-point, 3D 7-point, banded SPD with half bandwidth
+    U{5..64}}.  A banded matrix whose nnz would exceed max_nnz gets fewer
+    rows (its bandwidth is kept)."""
+    rng = np.random.default_rng(seed)
+    mats = []
+    for _ in range(count):
+        n = int(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))
+        kind = int(rng.integers(0, 3))
+        if kind == 0:
+            side = max(2, int(round(n ** 0.5)))
+            mats.append(laplacian_2d(side))
+        elif kind == 1:
+            side = max(2, int(round(n ** (1.0 / 3.0))))
+            mats.append(laplacian_3d(side))
+        else:
+            w = int(rng.integers(5, 65))
+            n = max(2 * w + 2, min(n, max_nnz // (2 * w + 1)))
+            mats.append(banded_spd(n, w, int(rng.integers(0, 2 ** 31))))
+    return mats
+
+
+def serving_requests(pool, count: int, seed: int = SEED_BASE + 5):
+    """Request parameters: (matrix index, precision 'f64' | 'ir32' 50/50,
+    tol log-uniform in [1e-10, 1e-8], right-hand-side seed)."""
+    rng = np.random.default_rng(seed + 1)
+    out = []
+    for i in range(count):
+        out.append((int(rng.integers(0, len(pool))),
+                    "f64" if rng.random() < 0.5 else "ir32",
+                    float(10 ** rng.uniform(-10, -8)),
+                    int(rng.integers(0, 2 ** 31))))
+    return out

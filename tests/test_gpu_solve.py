@@ -87,9 +87,33 @@ CASES = {
 
 @pytest.mark.parametrize("case", ["lap2d_64", "diff3d_12", "banded_2000"])
 @pytest.mark.parametrize("precond", [False, True])
-def test_cg(case, precond):
+@pytest.mark.parametrize("engine", [1, 2, 3])
+def test_cg(case, precond, engine):
+    """CG on the multi-kernel (1), single-block (2) and cluster (3) engines."""
     m, b = CASES[case]()
-    _check(m, b, "cg", precond, 1e-10)
+    _check(m, b, "cg", precond, 1e-10, engine=engine)
+
+
+@pytest.mark.parametrize("n_side", [1, 3, 17, 128])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_cluster_engine_sizes(n_side, dtype):
+    """Cluster engine from one row up to its 16384-row limit (row slices
+    of 1..1024 rows per block)."""
+    m = W.shifted_rectangle(n_side, n_side, 0.05)
+    b = W.uniform_vector(m.n, 11)
+    tol = 1e-10 if dtype == "f64" else 1e-5
+    x, info = _gpu_solve(m, b, "cg", 1, tol, dtype=dtype, engine=3)
+    assert info["return"] == gk.GK_OK, info
+    assert oracle.true_rel_residual(m, b, x) <= (tol if dtype == "f64" else 3e-5)
+
+
+def test_cluster_engine_rejects_too_large():
+    m = W.laplacian_2d(129)  # 16641 rows > 16384
+    b = W.uniform_vector(m.n, 1)
+    _, info = _gpu_solve(m, b, "cg", 0, 1e-8, engine=3)
+    assert info["return"] == gk.GK_ERR_UNSUPPORTED
+    x, info = _gpu_solve(m, b, "cg", 0, 1e-8, engine=0)  # automatic: multi-kernel
+    assert info["return"] == gk.GK_OK
 
 
 @pytest.mark.parametrize("case", ["lap2d_64", "diff3d_12", "convdiff_300"])
