@@ -290,6 +290,76 @@ def batched_compare(gk, W, torch, dev, count=2048):
     return out
 
 
+def serving_bench(gk, W, torch, dev, n_req=240, factors=(0.5, 0.8, 0.95)):
+    """Config 5: Poisson arrivals of solve requests (2D/3D stencils and
+    banded SPD, n log-uniform 1e3..1e6, FP64 or FP32-refined 50/50, tol
+    log-uniform 1e-10..1e-8) under a 40 GB budget.  Saturation throughput is
+    measured with a burst of n_req requests; then n_req requests arrive at
+    0.5 / 0.8 / 0.95 x saturation.  Latency = submit -> x back on the host."""
+    import threading
+    from paper_2510_08230_gb300.serve import SolveRequest, SolveServer
+    pool = W.serving_pool(24)
+    rng = np.random.default_rng(W.SEED_BASE + 5)
+    params = W.serving_requests(pool, n_req * (len(factors) + 1))
+    rhs = {}
+
+    def make(rid):
+        mi, prec, tol, seed = params[rid]
+        key = (mi, seed % 4)
+        if key not in rhs:
+            rhs[key] = W.uniform_vector(pool[mi].n, seed % 4 + 17 * mi)
+        return SolveRequest(rid, mi, pool[mi], rhs[key], tol=tol, precision=prec)
+
+    reqs = [make(i) for i in range(len(params))]
+    srv = SolveServer(budget_bytes=40e9, workers=6)
+    # warm-up: every pool matrix once per precision (uploads, plans, graphs)
+    warm = []
+    for mi, m in enumerate(pool):
+        for prec in ("f64", "ir32"):
+            warm.append(srv.submit(SolveRequest(-1, mi, m, W.uniform_vector(m.n, 1), 1e-8, prec)))
+    for r in warm:
+        r.event.wait(600)
+    out = {"workload": "24-matrix pool (2D 5-pt / 3D 7-pt / banded SPD w 5..64, n log-uniform "
+                       "1e3..1e6), FP64 or FP32-refined 50/50, tol 1e-10..1e-8, Jacobi-CG, "
+                       f"40 GB budget, 6 worker streams, {n_req} requests per rate"}
+    burst = reqs[:n_req]
+    t0 = time.perf_counter()
+    for r in burst:
+        srv.submit(r)
+    for r in burst:
+        r.event.wait(600)
+    t1 = time.perf_counter()
+    sat = n_req / (t1 - t0)
+    out["saturation"] = SolveServer.summarize(burst, t0, t1)
+    for k, f in enumerate(factors):
+        batch = reqs[n_req * (k + 1):n_req * (k + 2)]
+        gaps = rng.exponential(1.0 / (f * sat), size=len(batch))
+        arrive = np.cumsum(gaps)
+
+        def feeder():
+            base = time.perf_counter()
+            for r, a in zip(batch, arrive):
+                dt = base + a - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                srv.submit(r)
+
+        t0 = time.perf_counter()
+        th = threading.Thread(target=feeder)
+        th.start()
+        th.join()
+        for r in batch:
+            r.event.wait(600)
+        t1 = time.perf_counter()
+        out[f"rate_{f}"] = dict(SolveServer.summarize(batch, t0, t1),
+                                offered_per_s=round(f * sat, 2))
+    srv.close()
+    out["p50_ms"] = out["rate_0.8"]["p50_ms"]
+    out["p99_ms"] = out["rate_0.8"]["p99_ms"]
+    out["solves_per_s"] = out["saturation"]["solves_per_s"]
+    return out
+
+
 def run_reference(args):
     """The oracle on the host cores, same metric and unit."""
     rank = int(os.environ.get("RANK", "0"))
@@ -337,6 +407,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-solvers", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -468,12 +539,14 @@ def main():
     del items, step_items
     torch.cuda.empty_cache()
 
-    cg = ir = batched = None
+    cg = ir = batched = serving = None
     if rank == 0 and not args.no_cg:
         cg = cg_solves_per_s(gk, W, torch, dev)
     if rank == 0 and not args.no_solvers:
         ir = ir_compare(gk, W, torch, dev)
         batched = batched_compare(gk, W, torch, dev)
+    if rank == 0 and not args.no_serving:
+        serving = serving_bench(gk, W, torch, dev)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(lap)
@@ -484,7 +557,8 @@ def main():
             "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "step": step_detail, "sweep": sweep, "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": e2e, "cg": cg, "ir_128cubed": ir, "batched_2048": batched, "clocks": clk,
+            "e2e": e2e, "cg": cg, "ir_128cubed": ir, "batched_2048": batched,
+            "serving": serving, "clocks": clk,
             "gpu_launches": launches}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -184,7 +184,9 @@ typedef struct {
     int32_t krylov_dim;   /* GMRES restart length m (0 = 30, the paper's value); <= 64 */
     int32_t mixed;        /* 0: plain; 1: FP32 inner solves in FP64 iterative
                              refinement; 2: BF16-stored FP32 inner solves */
-    double inner_tol;     /* refinement: inner reduction (0 = 1e-4) */
+    double inner_tol;     /* refinement: inner reduction (0 = 1e-5); an inner
+                             solve confirms its true residual but gives up
+                             after two residual replacements */
     int32_t max_outer;    /* refinement: outer cap (0 = 50) */
     const double* batch_tols; /* gk_solve_batched only: per-system tolerances
                              (host array of `count`), NULL = tol for all */
@@ -221,7 +223,13 @@ gk_status gk_solve(gk_matrix A, const void* b, void* x,
                    void* stream);
 
 /* Solve `count` independent systems As[i] x_i = b_i in one launch, one
- * thread block per system, whole iteration inside the kernel.  All
+ * thread block per system, whole iteration inside the kernel.  The block
+ * size (128/256/512 threads) is autotuned per batch shape on the first call
+ * for that shape (value type, method, preconditioner, log2 of the largest n
+ * and of the count): each candidate runs the batch capped at 30 iterations
+ * from the callers' initial guesses, which are restored afterwards; the
+ * choice is cached for the process.  GK_AUTOTUNE=0 disables tuning
+ * (256 threads), GK_BATCH_THREADS forces a size.  All
  * matrices must be CSR, square, of the same dtype, with n <= 16384; CG
  * and BiCGSTAB (GMRES: GK_ERR_UNSUPPORTED).  infos has count entries
  * (may be NULL).  bs / xs: arrays of device pointers (host arrays of

@@ -11,6 +11,7 @@
 // fixed order, so a system's result does not depend on the rest of the
 // batch or on the grid size.
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "prims.cuh"
@@ -41,10 +42,67 @@ struct BlockOpts {
     int32_t prec;
 };
 
-// Sum of NA values over the block, returned to every thread (fixed order).
+// Reductions use VL virtual lanes: row i adds into lane i mod VL, and the
+// VL lane partials are summed by warp 0 in a fixed order.  The rounding of
+// every dot product is therefore the same for 128, 256 or 512 threads per
+// block, so the block size (autotuned) never changes a system's result.
+constexpr int VL = 512;
+
 template <int NA>
-__device__ __forceinline__ void block_allsum(double (&v)[NA]) {
-    block_allsum_bcast<NA>(v);
+struct VAcc {
+    double v[NA][4];
+};
+
+template <int NA>
+__device__ __forceinline__ VAcc<NA> vacc() {
+    VAcc<NA> a;
+#pragma unroll
+    for (int k = 0; k < NA; ++k)
+#pragma unroll
+        for (int s = 0; s < 4; ++s) a.v[k][s] = 0.0;
+    return a;
+}
+
+// f(i, s) for every row i of this thread; s = (i mod VL) / blockDim.x
+template <class F>
+__device__ __forceinline__ void for_rows_vl(int32_t n, F&& f) {
+    const int ns = VL / (int)blockDim.x;
+    for (int32_t i0 = threadIdx.x; i0 < n; i0 += VL) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            if (s < ns) {
+                const int32_t i = i0 + s * (int32_t)blockDim.x;
+                if (i < n) f(i, s);
+            }
+        }
+    }
+}
+
+// Sum of the virtual-lane partials, returned to every thread.
+template <int NA>
+__device__ __forceinline__ void vl_allsum(const VAcc<NA>& acc, double (&out)[NA]) {
+    __shared__ double sh[NA][VL];
+    __shared__ double tot[NA];
+    const int ns = VL / (int)blockDim.x;
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+            if (s < ns) sh[a][threadIdx.x + s * blockDim.x] = acc.v[a][s];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            double t = 0.0;
+            for (int j = threadIdx.x; j < VL; j += 32) t += sh[a][j];
+            t = warp_sum(t);
+            if (threadIdx.x == 0) tot[a] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < NA; ++a) out[a] = tot[a];
+    __syncthreads();
 }
 
 template <typename V, typename T, typename G>
@@ -75,25 +133,26 @@ __device__ bool block_setup(const SysDesc& d, const BlockOpts& opt, T* dinv, T* 
     const V* va = (const V*)d.va;
     const T* b = (const T*)d.b;
     T* x = (T*)d.x;
-    double acc[2] = {0.0, 0.0};
-    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    VAcc<2> acc = vacc<2>();
+    for_rows_vl(n, [&](int32_t i, int s) {
         const T bi = b[i];
-        acc[0] = fma((double)bi, (double)bi, acc[0]);
+        acc.v[0][s] = fma((double)bi, (double)bi, acc.v[0][s]);
         if (opt.prec) {
             const T di = row_dinv<V, T>(d.rp, d.ci, va, i);
             dinv[i] = di;
-            if (di == T(0)) acc[1] = 1.0;
+            if (di == T(0)) acc.v[1][s] = 1.0;
         }
-    }
-    block_allsum<2>(acc);
+    });
+    double tot[2];
+    vl_allsum<2>(acc, tot);
     o.iters = 0;
     o.restarts = 0;
     o.rec = o.tru = 0.0;
-    if (acc[1] != 0.0) {
+    if (tot[1] != 0.0) {
         o.status = GK_ERR_ZERO_DIAG;
         return false;
     }
-    bn = sqrt(acc[0]);
+    bn = sqrt(tot[0]);
     thr = d.tol * bn;
     if (bn == 0.0) {
         for (int32_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = T(0);
@@ -104,14 +163,15 @@ __device__ bool block_setup(const SysDesc& d, const BlockOpts& opt, T* dinv, T* 
         o.status = GK_ERR_NAN;
         return false;
     }
-    double rr[1] = {0.0};
-    for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    VAcc<1> rr = vacc<1>();
+    for_rows_vl(n, [&](int32_t i, int s) {
         const T ri = b[i] - row_dot<V, T>(d.rp, d.ci, va, x, i);
         r[i] = ri;
-        rr[0] = fma((double)ri, (double)ri, rr[0]);
-    }
-    block_allsum<1>(rr);
-    const double rn = sqrt(rr[0]);
+        rr.v[0][s] = fma((double)ri, (double)ri, rr.v[0][s]);
+    });
+    double t1[1];
+    vl_allsum<1>(rr, t1);
+    const double rn = sqrt(t1[0]);
     o.rec = o.tru = rn / bn;
     if (!isfinite(rn)) {
         o.status = GK_ERR_NAN;
@@ -131,14 +191,15 @@ __device__ double block_true_resid(const SysDesc& d, T* r) {
     const V* va = (const V*)d.va;
     const T* b = (const T*)d.b;
     const T* x = (const T*)d.x;
-    double tt[1] = {0.0};
-    for (int32_t i = threadIdx.x; i < d.n; i += blockDim.x) {
+    VAcc<1> tt = vacc<1>();
+    for_rows_vl(d.n, [&](int32_t i, int s) {
         const T ri = b[i] - row_dot<V, T>(d.rp, d.ci, va, x, i);
         r[i] = ri;
-        tt[0] = fma((double)ri, (double)ri, tt[0]);
-    }
-    block_allsum<1>(tt);
-    return sqrt(tt[0]);
+        tt.v[0][s] = fma((double)ri, (double)ri, tt.v[0][s]);
+    });
+    double t[1];
+    vl_allsum<1>(tt, t);
+    return sqrt(t[0]);
 }
 
 // ---------------------------------------------------------------- CG
@@ -146,7 +207,7 @@ __device__ double block_true_resid(const SysDesc& d, T* r) {
 constexpr int BLOCK_MAX_THREADS = 512;
 
 template <typename V, typename T>
-__global__ void __launch_bounds__(BLOCK_MAX_THREADS) k_block_cg(const SysDesc* __restrict__ sys, SysOut* __restrict__ outs,
+__global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_cg(const SysDesc* __restrict__ sys, SysOut* __restrict__ outs,
                            int32_t count, BlockOpts opt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* ps = reinterpret_cast<T*>(smem_raw);
@@ -164,44 +225,47 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS) k_block_cg(const SysDesc* _
         if (block_setup<V, T>(d, opt, dinv, r, bn, thr, o)) {
             double rho = 0.0;
             auto init_dir = [&]() {
-                double rz[1] = {0.0};
-                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                VAcc<1> rz = vacc<1>();
+                for_rows_vl(n, [&](int32_t i, int s) {
                     const T ri = r[i];
                     const T zi = opt.prec ? dinv[i] * ri : ri;
                     ps[i] = zi;
-                    rz[0] = fma((double)ri, (double)zi, rz[0]);
-                }
-                block_allsum<1>(rz);
-                rho = rz[0];
+                    rz.v[0][s] = fma((double)ri, (double)zi, rz.v[0][s]);
+                });
+                double t[1];
+                vl_allsum<1>(rz, t);
+                rho = t[0];
             };
             init_dir();
             int32_t k = 0;
             while (k < opt.max_iters) {
-                double pq[1] = {0.0};
-                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
-                    const T s = row_dot<V, T>(d.rp, d.ci, va, ps, i);
-                    q[i] = s;
-                    pq[0] = fma((double)ps[i], (double)s, pq[0]);
-                }
-                block_allsum<1>(pq);
-                if (!isfinite(pq[0])) { o.status = GK_ERR_NAN; break; }
-                if (pq[0] <= 0.0) { o.status = GK_BREAKDOWN; break; }
-                const double alpha = rho / pq[0];
+                VAcc<1> pq = vacc<1>();
+                for_rows_vl(n, [&](int32_t i, int s) {
+                    const T sv = row_dot<V, T>(d.rp, d.ci, va, ps, i);
+                    q[i] = sv;
+                    pq.v[0][s] = fma((double)ps[i], (double)sv, pq.v[0][s]);
+                });
+                double tp[1];
+                vl_allsum<1>(pq, tp);
+                if (!isfinite(tp[0])) { o.status = GK_ERR_NAN; break; }
+                if (tp[0] <= 0.0) { o.status = GK_BREAKDOWN; break; }
+                const double alpha = rho / tp[0];
                 const T ta = (T)alpha;
-                double a2[2] = {0.0, 0.0};
-                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                VAcc<2> a2 = vacc<2>();
+                for_rows_vl(n, [&](int32_t i, int s) {
                     x[i] = fmadd(ta, ps[i], x[i]);
                     const T ri = fmadd(-ta, q[i], r[i]);
                     r[i] = ri;
                     const T zi = opt.prec ? dinv[i] * ri : ri;
-                    a2[0] = fma((double)ri, (double)zi, a2[0]);
-                    a2[1] = fma((double)ri, (double)ri, a2[1]);
-                }
-                block_allsum<2>(a2);
+                    a2.v[0][s] = fma((double)ri, (double)zi, a2.v[0][s]);
+                    a2.v[1][s] = fma((double)ri, (double)ri, a2.v[1][s]);
+                });
+                double t2[2];
+                vl_allsum<2>(a2, t2);
                 ++k;
-                const double rn = sqrt(a2[1]);
+                const double rn = sqrt(t2[1]);
                 o.rec = rn / bn;
-                if (!isfinite(rn) || !isfinite(a2[0])) { o.status = GK_ERR_NAN; break; }
+                if (!isfinite(rn) || !isfinite(t2[0])) { o.status = GK_ERR_NAN; break; }
                 if (rn <= thr) {
                     const double tn = block_true_resid<V, T>(d, r);
                     if (tn <= thr) { o.status = GK_OK; break; }
@@ -209,8 +273,8 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS) k_block_cg(const SysDesc* _
                     init_dir();
                     continue;
                 }
-                const double beta = a2[0] / rho;
-                rho = a2[0];
+                const double beta = t2[0] / rho;
+                rho = t2[0];
                 const T tb = (T)beta;
                 for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
                     const T zi = opt.prec ? dinv[i] * r[i] : r[i];
@@ -229,7 +293,7 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS) k_block_cg(const SysDesc* _
 // ---------------------------------------------------------------- BiCGSTAB
 // work slots: 0 dinv, 1 r, 2 rhat, 3 p, 4 phat, 5 v, 6 s, 7 shat, 8 t
 template <typename V, typename T>
-__global__ void __launch_bounds__(BLOCK_MAX_THREADS) k_block_bicgstab(const SysDesc* __restrict__ sys, SysOut* __restrict__ outs,
+__global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_bicgstab(const SysDesc* __restrict__ sys, SysOut* __restrict__ outs,
                                  int32_t count, BlockOpts opt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* gs = reinterpret_cast<T*>(smem_raw);  // gathered vector
@@ -240,23 +304,24 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS) k_block_bicgstab(const SysD
         T* x = (T*)d.x;
         T* dinv = (T*)d.work;
         T *r = dinv + d.ld, *rh = r + d.ld, *p = rh + d.ld, *ph = p + d.ld, *v = ph + d.ld;
-        T *s = v + d.ld, *sh = s + d.ld, *t = sh + d.ld;
+        T *sv = v + d.ld, *sh = sv + d.ld, *t = sh + d.ld;
         SysOut o;
         double bn = 0.0, thr = 0.0;
         if (block_setup<V, T>(d, opt, dinv, r, bn, thr, o)) {
             double rho = 1.0, alpha = 1.0, omega = 1.0, rho_new = 0.0;
             auto restart = [&]() {
-                double a[1] = {0.0};
-                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                VAcc<1> a = vacc<1>();
+                for_rows_vl(n, [&](int32_t i, int s) {
                     const T ri = r[i];
                     rh[i] = ri;
                     p[i] = T(0);
                     v[i] = T(0);
-                    a[0] = fma((double)ri, (double)ri, a[0]);
-                }
-                block_allsum<1>(a);
+                    a.v[0][s] = fma((double)ri, (double)ri, a.v[0][s]);
+                });
+                double tt[1];
+                vl_allsum<1>(a, tt);
                 rho = alpha = omega = 1.0;
-                rho_new = a[0];
+                rho_new = tt[0];
             };
             restart();
             int32_t k = 0;
@@ -273,26 +338,28 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS) k_block_bicgstab(const SysD
                     gs[i] = hi;
                 }
                 __syncthreads();
-                double rv[1] = {0.0};
-                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                VAcc<1> rv = vacc<1>();
+                for_rows_vl(n, [&](int32_t i, int s) {
                     const T vi = row_dot<V, T>(d.rp, d.ci, va, gs, i);
                     v[i] = vi;
-                    rv[0] = fma((double)rh[i], (double)vi, rv[0]);
-                }
-                block_allsum<1>(rv);
-                if (!isfinite(rv[0])) { o.status = GK_ERR_NAN; break; }
-                if (rv[0] == 0.0) { o.status = GK_BREAKDOWN; break; }
-                alpha = rho_new / rv[0];
+                    rv.v[0][s] = fma((double)rh[i], (double)vi, rv.v[0][s]);
+                });
+                double trv[1];
+                vl_allsum<1>(rv, trv);
+                if (!isfinite(trv[0])) { o.status = GK_ERR_NAN; break; }
+                if (trv[0] == 0.0) { o.status = GK_BREAKDOWN; break; }
+                alpha = rho_new / trv[0];
                 const T ta = (T)alpha;
-                double ss[1] = {0.0};
-                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                VAcc<1> ss = vacc<1>();
+                for_rows_vl(n, [&](int32_t i, int s) {
                     const T si = fmadd(-ta, v[i], r[i]);
-                    s[i] = si;
-                    ss[0] = fma((double)si, (double)si, ss[0]);
-                }
-                block_allsum<1>(ss);
+                    sv[i] = si;
+                    ss.v[0][s] = fma((double)si, (double)si, ss.v[0][s]);
+                });
+                double tss[1];
+                vl_allsum<1>(ss, tss);
                 ++k;
-                const double sn = sqrt(ss[0]);
+                const double sn = sqrt(tss[0]);
                 if (!isfinite(sn)) { o.status = GK_ERR_NAN; break; }
                 if (sn <= thr) {  // half-step exit
                     for (int32_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = fmadd(ta, ph[i], x[i]);
@@ -305,36 +372,38 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS) k_block_bicgstab(const SysD
                     continue;
                 }
                 for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
-                    const T hi = opt.prec ? dinv[i] * s[i] : s[i];
+                    const T hi = opt.prec ? dinv[i] * sv[i] : sv[i];
                     sh[i] = hi;
                     gs[i] = hi;
                 }
                 __syncthreads();
-                double a2[2] = {0.0, 0.0};
-                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                VAcc<2> a2 = vacc<2>();
+                for_rows_vl(n, [&](int32_t i, int s) {
                     const T ti = row_dot<V, T>(d.rp, d.ci, va, gs, i);
                     t[i] = ti;
-                    a2[0] = fma((double)ti, (double)s[i], a2[0]);
-                    a2[1] = fma((double)ti, (double)ti, a2[1]);
-                }
-                block_allsum<2>(a2);
-                if (!isfinite(a2[0]) || !isfinite(a2[1])) { o.status = GK_ERR_NAN; break; }
-                if (a2[1] == 0.0) { o.status = GK_BREAKDOWN; break; }
-                omega = a2[0] / a2[1];
+                    a2.v[0][s] = fma((double)ti, (double)sv[i], a2.v[0][s]);
+                    a2.v[1][s] = fma((double)ti, (double)ti, a2.v[1][s]);
+                });
+                double t2[2];
+                vl_allsum<2>(a2, t2);
+                if (!isfinite(t2[0]) || !isfinite(t2[1])) { o.status = GK_ERR_NAN; break; }
+                if (t2[1] == 0.0) { o.status = GK_BREAKDOWN; break; }
+                omega = t2[0] / t2[1];
                 if (omega == 0.0) { o.status = GK_BREAKDOWN; break; }
                 const T to = (T)omega;
-                double a3[2] = {0.0, 0.0};
-                for (int32_t i = threadIdx.x; i < n; i += blockDim.x) {
+                VAcc<2> a3 = vacc<2>();
+                for_rows_vl(n, [&](int32_t i, int s) {
                     x[i] = fmadd(to, sh[i], fmadd(ta, ph[i], x[i]));
-                    const T ri = fmadd(-to, t[i], s[i]);
+                    const T ri = fmadd(-to, t[i], sv[i]);
                     r[i] = ri;
-                    a3[0] = fma((double)rh[i], (double)ri, a3[0]);
-                    a3[1] = fma((double)ri, (double)ri, a3[1]);
-                }
-                block_allsum<2>(a3);
+                    a3.v[0][s] = fma((double)rh[i], (double)ri, a3.v[0][s]);
+                    a3.v[1][s] = fma((double)ri, (double)ri, a3.v[1][s]);
+                });
+                double t3[2];
+                vl_allsum<2>(a3, t3);
                 rho = rho_new;
-                rho_new = a3[0];
-                const double rn = sqrt(a3[1]);
+                rho_new = t3[0];
+                const double rn = sqrt(t3[1]);
                 o.rec = rn / bn;
                 if (!isfinite(rn)) { o.status = GK_ERR_NAN; break; }
                 if (rn <= thr) {
@@ -527,6 +596,64 @@ gk_status solve_small(gk_matrix A, const void* b, void* x, const gk_solve_opts* 
     return GK_OK;
 }
 
+// ------------------------------------------------------------ autotuner
+// Threads per block for a batch shape, picked by timing each candidate on
+// a capped run of the batch itself (the callers' initial guesses are saved
+// before and restored after the trials) and cached per key: value type,
+// method, preconditioner, log2 of the largest n and of the system count.
+static std::mutex g_tune_mu;
+static std::map<uint64_t, int> g_tune;
+
+static uint64_t tune_key(gk_dtype dt, const gk_solve_opts* o, int32_t nmax, int32_t count) {
+    auto lg = [](int64_t v) {
+        int b = 0;
+        while ((1ll << b) < v) ++b;
+        return (uint64_t)b;
+    };
+    return ((uint64_t)dt << 40) | ((uint64_t)o->method << 36) | ((uint64_t)o->precond << 32) |
+           (lg(nmax) << 16) | lg(count);
+}
+
+static gk_status autotune_threads(int32_t count, const gk_matrix* As, const void* const* bs,
+                                  void* const* xs, const gk_solve_opts* o, cudaStream_t s,
+                                  int* best) {
+    const size_t vb = vector_bytes(As[0]->dtype);
+    size_t total = 0;
+    for (int32_t i = 0; i < count; ++i) total += (size_t)As[i]->n * vb;
+    DevBuf save;
+    GK_TRY(save.ensure(total + 256));
+    auto copy_all = [&](bool to_save) -> gk_status {
+        size_t off = 0;
+        for (int32_t i = 0; i < count; ++i) {
+            const size_t b = (size_t)As[i]->n * vb;
+            char* sp = static_cast<char*>(save.ptr) + off;
+            if (b)
+                GK_CUDA(cudaMemcpyAsync(to_save ? (void*)sp : xs[i], to_save ? xs[i] : (void*)sp, b,
+                                        cudaMemcpyDeviceToDevice, s));
+            off += b;
+        }
+        return GK_OK;
+    };
+    GK_TRY(copy_all(true));
+    gk_solve_opts trial = *o;
+    trial.max_iters = std::min(o->max_iters, 30);
+    float best_ms = 1e30f;
+    *best = 256;
+    for (int nt : {128, 256, 512}) {
+        GK_TRY(copy_all(false));
+        float ms = 0.f;
+        GK_TRY(run_batch(count, As, bs, xs, &trial, nullptr, s, nt, &ms));
+        if (ms < best_ms) {
+            best_ms = ms;
+            *best = nt;
+        }
+    }
+    GK_TRY(copy_all(false));
+    GK_CUDA(cudaStreamSynchronize(s));
+    save.release();
+    return GK_OK;
+}
+
 }  // namespace gk
 
 using namespace gk;
@@ -553,8 +680,29 @@ extern "C" gk_status gk_solve_batched(int32_t count, const gk_matrix* As, const 
             return GK_ERR_INVALID;
         if (A->device != dev) return GK_ERR_UNSUPPORTED;
     }
-    int nt = 256;
+    cudaStream_t s = (cudaStream_t)stream;
+    int nt = 0;
     if (const char* e = getenv("GK_BATCH_THREADS")) nt = atoi(e);
-    if (nt != 128 && nt != 256 && nt != 512) nt = 256;
-    return run_batch(count, As, bs, xs, o, infos, (cudaStream_t)stream, nt, nullptr);
+    if (nt != 128 && nt != 256 && nt != 512) {
+        nt = 256;
+        const char* at = getenv("GK_AUTOTUNE");
+        if (!(at && at[0] == '0') && count >= 8) {
+            int32_t nmax = 0;
+            for (int32_t i = 0; i < count; ++i) nmax = std::max(nmax, As[i]->n);
+            const uint64_t key = tune_key(As[0]->dtype, o, nmax, count);
+            int found = 0;
+            {
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                auto it = g_tune.find(key);
+                if (it != g_tune.end()) found = it->second;
+            }
+            if (!found) {
+                GK_TRY(autotune_threads(count, As, bs, xs, o, s, &found));
+                std::lock_guard<std::mutex> lk(g_tune_mu);
+                g_tune[key] = found;
+            }
+            nt = found;
+        }
+    }
+    return run_batch(count, As, bs, xs, o, infos, s, nt, nullptr);
 }

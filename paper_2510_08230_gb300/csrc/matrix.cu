@@ -535,10 +535,13 @@ gk_status build_csr_plan(gk_matrix A, cudaStream_t s) {
     P.lanes = lanes;
     // row tiles of ~rows_per_tile rows of mean length; staged capacity
     // covers the chunk plus the longest row plus alignment slack
-    int rows_per_tile = 256;
+    // measured on GB300 (256^3 stencil): one staged tile per block with
+    // 512-row tiles beats deeper per-block pipelines, because more resident
+    // blocks hide the x-gather latency better than prefetching does
+    int rows_per_tile = 512;
     if (const char* e = getenv("GK_TILE_ROWS")) rows_per_tile = std::max(32, atoi(e));
     int32_t chunk = (int32_t)std::min<double>(
-        4096.0, std::max<double>(512.0, rows_per_tile * std::ceil(std::max(mean, 1.0))));
+        8192.0, std::max<double>(512.0, rows_per_tile * std::ceil(std::max(mean, 1.0))));
     chunk = (chunk + 7) & ~7;
     const int64_t cap = (int64_t)chunk + A->max_row + 16;
     int kind = (A->max_row <= 1024) ? 1 : 2;
@@ -546,6 +549,7 @@ gk_status build_csr_plan(gk_matrix A, cudaStream_t s) {
     // a single staged tile must fit in shared memory
     if (kind == 1 && ((cap + 7) & ~7) * (int64_t)(4 + value_bytes(A->dtype)) > 200 * 1024) kind = 2;
     P.kind = kind;
+    P.stages = 1;
     if (const char* e = getenv("GK_ROWTILE_STAGES")) P.stages = std::max(1, std::min(3, atoi(e)));
     if (kind == 1) {
         P.chunk = chunk;
@@ -556,7 +560,7 @@ gk_status build_csr_plan(gk_matrix A, cudaStream_t s) {
                                                        P.tile_desc);
         GK_CUDA(cudaGetLastError());
     } else if (kind == 2) {
-        const int E = value_bytes(A->dtype) >= 8 ? 8 : 12;
+        const int E = 8;  // merge-path items per thread (MergeE)
         const int64_t items = 256 * (int64_t)E;
         const int64_t N = (int64_t)A->n + A->nnz;
         P.merge_blocks = (int32_t)std::max<int64_t>(1, (N + items - 1) / items);

@@ -1024,9 +1024,14 @@ static int chunk_for(int64_t n) { return n < 200000 ? 32 : 8; }
 
 // Runs one Krylov solve on the multi-kernel engine.  b, x: device vectors
 // of type T.  Result status and counters in *out.
+// inner = true: a refinement inner solve.  It confirms a passed recurrence
+// residual with the true residual like any solve, but after two residual
+// replacements it stops anyway: the outer FP64 residual decides
+// convergence, and an FP32 solve can stall above a tight inner tolerance.
 template <typename V, typename T>
 static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, double tol,
-                          int32_t max_iters, int32_t m, cudaStream_t s, SolveOut* out) {
+                          int32_t max_iters, int32_t m, cudaStream_t s, SolveOut* out,
+                          bool inner = false) {
     const int32_t n = A->n;
     SolverCache* C = nullptr;
     GK_TRY(get_cache(A, &C));
@@ -1145,6 +1150,7 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
         for (;;) {
             if (C->hst->halt == 2) break;
             if (--chunks_left < 0 || checks_left < 0) return GK_ERR_TIMEOUT;
+            if (C->hst->halt == 1 && inner && C->hst->restarts >= 2) break;  // enough
             if (C->hst->halt == 1) {
                 // recurrence passed: check the true residual
                 ++chunks_left;
@@ -1173,6 +1179,14 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
     const KState* hs = C->hst;
     if (out->status == GK_OK) out->status = (gk_status)hs->status;
     if (hs->halt == 2 && hs->status == GK_OK) out->status = GK_OK;
+    if (inner && hs->halt == 1) {
+        out->status = GK_OK;
+        out->iters = hs->iter;
+        out->restarts = hs->restarts;
+        out->rec = hs->bnorm > 0 ? hs->rnorm / hs->bnorm : 0.0;
+        out->tru = out->rec;
+        return GK_OK;
+    }
     out->iters = hs->iter;
     out->restarts = hs->restarts;
     out->rec = hs->bnorm > 0 ? hs->rnorm / hs->bnorm : 0.0;
@@ -1259,7 +1273,7 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
         return GK_OK;
     }
     const int max_outer = o->max_outer > 0 ? o->max_outer : 50;
-    const double inner_tol = o->inner_tol > 0 ? o->inner_tol : 1e-4;
+    const double inner_tol = o->inner_tol > 0 ? o->inner_tol : 1e-5;  // see the header
     const int m = o->method == GK_GMRES ? (o->krylov_dim ? o->krylov_dim : 30) : 0;
     int32_t total_inner = 0, restarts = 0;
     double tn = 0.0, last_rec = 0.0;
@@ -1291,9 +1305,11 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
         const bool prec = o->precond == GK_PRECOND_JACOBI;
         const int32_t left = o->max_iters - total_inner;
         if (L->dtype == GK_F32)
-            GK_TRY((solve_mk<float, float>(L, r32, d32, o->method, prec, inner_tol, left, m, s, &io)));
+            GK_TRY((solve_mk<float, float>(L, r32, d32, o->method, prec, inner_tol, left, m, s, &io,
+                                           true)));
         else
-            GK_TRY((solve_mk<__nv_bfloat16, float>(L, r32, d32, o->method, prec, inner_tol, left, m, s, &io)));
+            GK_TRY((solve_mk<__nv_bfloat16, float>(L, r32, d32, o->method, prec, inner_tol, left, m,
+                                                   s, &io, true)));
         total_inner += io.iters;
         restarts += io.restarts;
         last_rec = io.rec;

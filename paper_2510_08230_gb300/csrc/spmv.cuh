@@ -73,6 +73,38 @@ __device__ __forceinline__ T row_sum_staged(const int32_t* s_col, const V* s_val
     return s;
 }
 
+// Two rows [ks0, ke0) and [ks1, ke1) of a staged tile at once: the loads
+// and gathers of both rows are issued before either FMA chain.
+template <typename T, typename V>
+__device__ __forceinline__ void row_pair_staged(const int32_t* s_col, const V* s_val,
+                                                const T* __restrict__ x, int32_t ks0, int32_t ke0,
+                                                int32_t ks1, int32_t ke1, T& s0, T& s1) {
+    constexpr int B = 4;
+    s0 = T(0);
+    s1 = T(0);
+    const int32_t l0 = ke0 - ks0, l1 = ke1 - ks1;
+    const int32_t lmax = max(l0, l1);
+    for (int32_t k0 = 0; k0 < lmax; k0 += B) {
+        T v0[B], x0[B], v1[B], x1[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            if (k0 + u < l0) {
+                v0[u] = cvt<T>(s_val[ks0 + k0 + u]);
+                x0[u] = __ldg(x + s_col[ks0 + k0 + u]);
+            }
+            if (k0 + u < l1) {
+                v1[u] = cvt<T>(s_val[ks1 + k0 + u]);
+                x1[u] = __ldg(x + s_col[ks1 + k0 + u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            if (k0 + u < l0) s0 = fmadd(v0[u], x0[u], s0);
+            if (k0 + u < l1) s1 = fmadd(v1[u], x1[u], s1);
+        }
+    }
+}
+
 // ------------------------------------------------------------ row-tile CSR
 
 // Tile descriptor: rows [x, y), staged nonzero range [z, z + w) with z a
@@ -129,9 +161,17 @@ k_csr_rowtile(int32_t ntiles, const int4* __restrict__ tdesc, const int32_t* __r
         const int4 d = __ldg(tdesc + c);
         const int32_t* s_col = reinterpret_cast<const int32_t*>(smem + (size_t)s * sbytes);
         const V* s_val = reinterpret_cast<const V*>(smem + (size_t)s * sbytes + cbytes);
-        for (int32_t r = d.x + (int32_t)threadIdx.x; r < d.y; r += blockDim.x) {
+        // two rows per thread per pass (r and r + blockDim), interleaved
+        for (int32_t r = d.x + (int32_t)threadIdx.x; r < d.y; r += 2 * (int32_t)blockDim.x) {
+            const int32_t r2 = r + (int32_t)blockDim.x;
+            const bool has2 = r2 < d.y;
             const int32_t ks = __ldg(rp + r) - d.z, ke = __ldg(rp + r + 1) - d.z;
-            epi.row(r, row_sum_staged<T, V>(s_col, s_val, x, ks, ke), acc.v);
+            const int32_t ks2 = has2 ? __ldg(rp + r2) - d.z : 0;
+            const int32_t ke2 = has2 ? __ldg(rp + r2 + 1) - d.z : 0;
+            T s0, s1;
+            row_pair_staged<T, V>(s_col, s_val, x, ks, ke, ks2, ke2, s0, s1);
+            epi.row(r, s0, acc.v);
+            if (has2) epi.row(r2, s1, acc.v);
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -164,16 +204,16 @@ __device__ __forceinline__ int mpad(int k) { return k + (k >> 3); }
 constexpr size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 // Shared-memory layout of the merge kernel; every array starts on a
-// 16-byte boundary: values, gathered x, thread carries, row ends, thread rows.
+// 16-byte boundary: values, gathered x, row ends, thread rows, carry scan.
 template <int E, typename V, typename T>
 struct MergeShape {
     static constexpr int TI = 256 * E;            // path items per block
     static constexpr int PADN = TI + TI / 8 + 8;  // padded entries
     static constexpr size_t OFF_XV = align16((size_t)PADN * sizeof(V));
-    static constexpr size_t OFF_TC = align16(OFF_XV + (size_t)PADN * sizeof(T));
-    static constexpr size_t OFF_RE = align16(OFF_TC + 256 * sizeof(T));
+    static constexpr size_t OFF_RE = align16(OFF_XV + (size_t)PADN * sizeof(T));
     static constexpr size_t OFF_TR = align16(OFF_RE + (size_t)(TI + 1) * 4);
-    static constexpr size_t BYTES = align16(OFF_TR + 256 * 4);
+    static constexpr size_t OFF_SC = align16(OFF_TR + 256 * 4);
+    static constexpr size_t BYTES = align16(OFF_SC + 256 * sizeof(T));
 };
 
 template <int E, typename V, typename T>
@@ -203,9 +243,9 @@ k_csr_merge(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
     extern __shared__ __align__(16) unsigned char smem[];
     V* s_val = reinterpret_cast<V*>(smem);
     T* s_xv = reinterpret_cast<T*>(smem + Sh::OFF_XV);
-    T* s_tcarry = reinterpret_cast<T*>(smem + Sh::OFF_TC);
     int32_t* s_rowend = reinterpret_cast<int32_t*>(smem + Sh::OFF_RE);
     int32_t* s_trow = reinterpret_cast<int32_t*>(smem + Sh::OFF_TR);
+    T* s_scan = reinterpret_cast<T*>(smem + Sh::OFF_SC);
     __shared__ int32_t s_bounds[2];
     const int64_t N = (int64_t)n + nnz;
     const int64_t d0 = (int64_t)blockIdx.x * TI;
@@ -230,11 +270,12 @@ k_csr_merge(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
     const int32_t nloc = min(i1 - i0 + 1, n - i0);  // staged row ends
     const int32_t cnt = (int32_t)(j1 - j0);
     for (int k = threadIdx.x; k < nloc; k += blockDim.x) s_rowend[k] = __ldg(rp + i0 + k + 1);
-    for (int k0 = threadIdx.x; k0 < cnt; k0 += 4 * blockDim.x) {
-        int32_t c[4];
-        V v[4];
+    for (int k0 = threadIdx.x; k0 < cnt; k0 += GATHER * blockDim.x) {
+        int32_t c[GATHER];
+        V v[GATHER];
+        T xv[GATHER];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < GATHER; ++u) {
             const int k = k0 + u * (int)blockDim.x;
             if (k < cnt) {
                 c[u] = __ldcs(ci + j0 + k);
@@ -242,11 +283,16 @@ k_csr_merge(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < GATHER; ++u) {
+            const int k = k0 + u * (int)blockDim.x;
+            if (k < cnt) xv[u] = __ldg(x + c[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < GATHER; ++u) {
             const int k = k0 + u * (int)blockDim.x;
             if (k < cnt) {
                 s_val[mpad(k)] = v[u];
-                s_xv[mpad(k)] = __ldg(x + c[u]);
+                s_xv[mpad(k)] = xv[u];
             }
         }
     }
@@ -283,23 +329,33 @@ k_csr_merge(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
             rend = (i < n && i - i0 < nloc) ? (int64_t)s_rowend[i - i0] : 0;
         }
     }
-    s_trow[threadIdx.x] = (dt < d1) ? i : -1;
-    s_tcarry[threadIdx.x] = acc;
+    // Carries: thread t ends its piece inside row s_trow[t] with partial sum
+    // acc.  A segmented inclusive scan over the threads (log steps, fixed
+    // order) gives S[t] = sum of the carries of the run of threads ending
+    // at t that share its row; rows are non-decreasing over valid threads.
+    const bool valid = dt < d1;
+    const int32_t myrow = valid ? i : INT32_MAX;
+    s_trow[threadIdx.x] = myrow;
+    T sc = acc;
+    s_scan[threadIdx.x] = sc;
     __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const bool take = (int)threadIdx.x >= o && s_trow[threadIdx.x - o] == myrow;
+        const T other = take ? s_scan[threadIdx.x - o] : T(0);
+        __syncthreads();
+        if (take) sc = other + sc;
+        s_scan[threadIdx.x] = sc;
+        __syncthreads();
+    }
     if (head_row >= 0) {
         T v = head_val;
-        for (int t = (int)threadIdx.x - 1; t >= 0 && s_trow[t] == head_row; --t) v = s_tcarry[t] + v;
+        if (threadIdx.x > 0 && s_trow[threadIdx.x - 1] == head_row) v = s_scan[threadIdx.x - 1] + v;
         epi.row(head_row, v, nullptr);
     }
-    if (threadIdx.x == blockDim.x - 1) {
-        // open row at the end of the block: sum the trailing carries
-        int t = (int)blockDim.x - 1;
-        while (t >= 0 && s_trow[t] < 0) --t;
-        const int32_t r = t >= 0 ? s_trow[t] : -1;
-        T v = T(0);
-        for (; t >= 0 && s_trow[t] == r; --t) v = s_tcarry[t] + v;
-        carry_row[blockIdx.x] = (r >= 0 && r < n) ? r : -1;
-        carry_val[blockIdx.x] = v;
+    // the row open at the end of the block: carried by the last valid thread
+    if (valid && (threadIdx.x == blockDim.x - 1 || s_trow[threadIdx.x + 1] == INT32_MAX)) {
+        carry_row[blockIdx.x] = (i < n) ? i : -1;
+        carry_val[blockIdx.x] = sc;
     }
 }
 
@@ -367,22 +423,68 @@ __device__ __forceinline__ T row_sum_padded(const int32_t* __restrict__ pc,
     return s;
 }
 
-// ELL: one thread per row, column-major coalesced loads.
+// Paired value type for two adjacent rows (16-byte loads for FP64).
+template <typename V> struct Pair2;
+template <> struct Pair2<double> { using type = double2; };
+template <> struct Pair2<float> { using type = float2; };
+template <> struct Pair2<__nv_bfloat16> { using type = __nv_bfloat162; };
+
+template <typename T, typename P>
+__device__ __forceinline__ void unpack2(const P& p, T& a, T& b) {
+    a = cvt<T>(p.x);
+    b = cvt<T>(p.y);
+}
+
+// Two adjacent rows i, i+1 (i even) stored column-major with `step`
+// between entries of a row: one 8-byte column load and one paired value
+// load per entry position serve both rows.
+template <typename T, typename V>
+__device__ __forceinline__ void row_pair_padded(const int32_t* __restrict__ pc,
+                                                const V* __restrict__ pv,
+                                                const T* __restrict__ x, int64_t base,
+                                                int64_t step, int32_t len, T& s0, T& s1) {
+    using P = typename Pair2<V>::type;
+    s0 = T(0);
+    s1 = T(0);
+#pragma unroll 4
+    for (int32_t j = 0; j < len; ++j) {
+        const int64_t at = base + (int64_t)j * step;
+        const int2 c = __ldcs(reinterpret_cast<const int2*>(pc + at));
+        const P pvv = *reinterpret_cast<const P*>(pv + at);
+        T v0, v1;
+        unpack2<T>(pvv, v0, v1);
+        const T x0 = c.x >= 0 ? __ldg(x + c.x) : T(0);
+        const T x1 = c.y >= 0 ? __ldg(x + c.y) : T(0);
+        s0 = fmadd(v0, x0, s0);
+        s1 = fmadd(v1, x1, s1);
+    }
+}
+
+// ELL: one thread per pair of adjacent rows (stride is a multiple of 32,
+// so pairs never straddle it), column-major coalesced paired loads.
 template <typename V, typename T, class Epi>
 __global__ void __launch_bounds__(256)
 k_ell(int32_t n, int64_t stride, int32_t K, const int32_t* __restrict__ ec,
       const V* __restrict__ ev, const T* __restrict__ x, Epi epi) {
     if (epi.skip()) return;
     AccArr<Epi> acc{};
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        epi.row(i, row_sum_padded<T, V>(ec, ev, x, i, stride, K), acc.v);
+    const int64_t npairs = ((int64_t)n + 1) / 2;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npairs;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = 2 * q;
+        T s0, s1;
+        row_pair_padded<T, V>(ec, ev, x, i, stride, K, s0, s1);
+        epi.row(i, s0, acc.v);
+        if (i + 1 < n) epi.row(i + 1, s1, acc.v);
+    }
     epi.finish(acc.v);
 }
 
 // SELL-P: one thread per row; the rows of a slice read consecutive
 // addresses for every stored column position.  The slice metadata of the
-// thread's next row is loaded before the current row is processed.
+// thread's next row is loaded before the current row is processed.  With
+// an even slice size, a thread takes two adjacent rows of one slice and
+// uses paired loads (k_sellp_pairs).
 template <typename V, typename T, class Epi>
 __global__ void __launch_bounds__(256)
 k_sellp(int32_t n, int32_t S, const int32_t* __restrict__ slen, const int64_t* __restrict__ sset,
@@ -412,6 +514,46 @@ k_sellp(int32_t n, int32_t S, const int32_t* __restrict__ slen, const int64_t* _
         }
         epi.row(i, row_sum_padded<T, V>(sc, sv, x, base, S, len), acc.v);
         i = in;
+        len = len_n;
+        base = base_n;
+    }
+    epi.finish(acc.v);
+}
+
+template <typename V, typename T, class Epi>
+__global__ void __launch_bounds__(256)
+k_sellp_pairs(int32_t n, int32_t S, const int32_t* __restrict__ slen,
+              const int64_t* __restrict__ sset, const int32_t* __restrict__ sc,
+              const V* __restrict__ sv, const T* __restrict__ x, Epi epi) {
+    if (epi.skip()) return;
+    AccArr<Epi> acc{};
+    const int sh = (S & (S - 1)) == 0 ? __ffs(S) - 1 : -1;
+    auto slice_of = [&](uint32_t r) -> uint32_t { return sh >= 0 ? (r >> sh) : r / (uint32_t)S; };
+    const int64_t npairs = ((int64_t)n + 1) / 2;
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int32_t len = 0;
+    int64_t base = 0;
+    if (q < npairs) {
+        const uint32_t r = (uint32_t)(2 * q), sl = slice_of(r);
+        len = __ldg(slen + sl);
+        base = __ldg(sset + sl) * S + ((int64_t)r - (int64_t)sl * S);
+    }
+    while (q < npairs) {
+        const int64_t qn = q + G;
+        int32_t len_n = 0;
+        int64_t base_n = 0;
+        if (qn < npairs) {
+            const uint32_t r = (uint32_t)(2 * qn), sl = slice_of(r);
+            len_n = __ldg(slen + sl);
+            base_n = __ldg(sset + sl) * S + ((int64_t)r - (int64_t)sl * S);
+        }
+        T s0, s1;
+        row_pair_padded<T, V>(sc, sv, x, base, S, len, s0, s1);
+        const int64_t i = 2 * q;
+        epi.row(i, s0, acc.v);
+        if (i + 1 < n) epi.row(i + 1, s1, acc.v);
+        q = qn;
         len = len_n;
         base = base_n;
     }
@@ -485,9 +627,14 @@ gk_status launch_spmv_rows(gk_matrix A, const T* x, const Epi& epi, cudaStream_t
             default: k_csr_vector<32, V, T, Epi><<<grid, 256, 0, s>>>(n, A->row_ptr, A->col, va, x, epi); break;
         }
     } else if (A->fmt == GK_ELL) {
-        int64_t need = (A->n + 255) / 256;
+        int64_t need = ((A->n + 1) / 2 + 255) / 256;
         grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 8));
         k_ell<V, T, Epi><<<grid, 256, 0, s>>>(A->n, A->stride, A->K, A->col, (const V*)A->val, x, epi);
+    } else if (A->S % 2 == 0) {
+        int64_t need = ((A->n + 1) / 2 + 255) / 256;
+        grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 8));
+        k_sellp_pairs<V, T, Epi><<<grid, 256, 0, s>>>(A->n, A->S, A->slice_len, A->slice_set,
+                                                      A->col, (const V*)A->val, x, epi);
     } else {
         int64_t need = (A->n + 255) / 256;
         grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 8));
@@ -505,7 +652,7 @@ inline unsigned max_grid_rows(gk_matrix A) { return (unsigned)num_sms() * 8; }
 // merge-path items per thread for a value type
 template <typename V>
 struct MergeE {
-    static constexpr int value = sizeof(V) >= 8 ? 8 : 12;
+    static constexpr int value = 8;
 };
 
 }  // namespace gk

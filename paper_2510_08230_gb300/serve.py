@@ -87,6 +87,7 @@ class SolveServer:
         self.jobs = collections.deque()
         self.running = True
         self.completed = []
+        self.error = None
         self.threads = [threading.Thread(target=self._worker, daemon=True) for _ in range(workers)]
         self.disp = threading.Thread(target=self._dispatch, daemon=True)
         for t in self.threads:
@@ -113,11 +114,14 @@ class SolveServer:
         self.cache.clear()
 
     # ----------------------------------------------------------- scheduler
-    def _evict(self, need):
-        """Evict unused cached matrices (LRU first) until `need` fits."""
+    def _evict(self, need, keep=None):
+        """Evict unused cached matrices (LRU first, never `keep`) until
+        `need` fits."""
         for key in list(self.cache.keys()):
             if self.used + need <= self.budget:
                 return
+            if key == keep:
+                continue
             mat, nb, users, _ = self.cache[key]
             if users == 0:
                 self.used -= nb
@@ -133,7 +137,7 @@ class SolveServer:
             entry = self.cache.get(req.key)
             mb = 0 if entry is not None else matrix_bytes(req.m, refined)
             if self.used + need + mb > self.budget:
-                self._evict(need + mb)
+                self._evict(need + mb, keep=req.key)
                 if self.used + need + mb > self.budget:
                     return  # head of line waits for memory
             self.queue.popleft()
@@ -156,6 +160,18 @@ class SolveServer:
             (self.pending_small if small else self.pending_single).append(req)
 
     def _dispatch(self):
+        try:
+            self._dispatch_loop()
+        except Exception as e:  # fail everything still waiting, loudly
+            with self.cv:
+                self.error = e
+                waiting = list(self.queue) + self.pending_small + list(self.pending_single)
+                for r in waiting:
+                    r.info = {"status": -3, "error": repr(e)}
+                    r.event.set()
+            raise
+
+    def _dispatch_loop(self):
         with self.cv:
             while self.running:
                 self._admit()
