@@ -98,7 +98,10 @@ typedef struct {
     int32_t spmv_launches; /* kernel launches per apply */
     int32_t device_error;  /* 1 if a kernel on this matrix gave up a bounded
                               device-side wait (its results are invalid) */
-    int32_t reserved;
+    int32_t solve_format;  /* layout the solvers' SpMV uses on this matrix: -1
+                              until the first gk_solve picks it (CSR matrices
+                              may solve on an ELL or SELL-P copy), else a
+                              gk_format */
 } gk_matrix_desc;
 
 /* ---------------------------------------------------------------------
@@ -217,7 +220,14 @@ typedef struct {
  * restarts from x.  b = 0 gives x = 0 and GK_OK after 0 iterations.
  * b, x: device pointers of n entries (x in/out, the initial guess).
  * info may be NULL.  Blocks until the solve is finished (one stream
- * synchronise); everything is enqueued on `stream`. */
+ * synchronise); everything is enqueued on `stream`.
+ * SpMV layout (multi-kernel engine and refinement on a CSR matrix): the first
+ * solve keeps an ELL copy of A when ELL stores at most 1.2 x nnz entries,
+ * else a SELL-P(32) copy under the same bound, else uses the CSR kernels; the
+ * copy lives with the handle (gk_matrix_desc.solve_format reports the pick).
+ * The rule reads only the sparsity pattern, so results are reproducible
+ * across handles.  Environment GK_SOLVE_FORMAT=csr|ell|sellp forces a layout,
+ * =timed picks the fastest of three timed SpMVs per admissible layout. */
 gk_status gk_solve(gk_matrix A, const void* b, void* x,
                    const gk_solve_opts* opts, gk_solve_info* info,
                    void* stream);

@@ -57,7 +57,7 @@ class gk_matrix_desc(ctypes.Structure):
                 ("num_slices", ctypes.c_int32), ("stored", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("spmv_kernel", ctypes.c_int32),
                 ("spmv_launches", ctypes.c_int32), ("device_error", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("solve_format", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -356,6 +356,11 @@ class Matrix:
 
     def apply_adv(self, alpha, b, beta, x, stream=None):
         _check(gk_apply_adv(self.handle, alpha, b, beta, x, stream), "gk_apply_adv")
+
+    def describe(self):
+        """Fresh gk_matrix_describe (solve_format is set by the first solve)."""
+        self.desc = gk_matrix_describe(self.handle)
+        return self.desc
 
     def solve(self, b, x, stream=None, **kw):
         return gk_solve(self.handle, b, x, make_opts(**kw), stream)

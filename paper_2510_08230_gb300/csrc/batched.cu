@@ -93,10 +93,15 @@ __device__ __forceinline__ void vl_allsum(const VAcc<NA>& acc, double (&out)[NA]
     if (threadIdx.x < 32) {
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
-            double t = 0.0;
-            for (int j = threadIdx.x; j < VL; j += 32) t += sh[a][j];
-            t = warp_sum(t);
-            if (threadIdx.x == 0) tot[a] = t;
+            double t[VL / 32];  // lane l: lanes l, l+32, ... as a pairwise tree
+#pragma unroll
+            for (int k = 0; k < VL / 32; ++k) t[k] = sh[a][threadIdx.x + 32 * k];
+#pragma unroll
+            for (int w = VL / 64; w > 0; w >>= 1)
+#pragma unroll
+                for (int k = 0; k < w; ++k) t[k] += t[k + w];
+            const double tt = warp_sum(t[0]);
+            if (threadIdx.x == 0) tot[a] = tt;
         }
     }
     __syncthreads();

@@ -177,6 +177,8 @@ struct gk_matrix_s {
     void* dinv = nullptr;         // Jacobi inverse diagonal (vector type)
     int dinv_state = 0;           // 0 not built, 1 ok, -1 zero diagonal
     gk_matrix_s* lowp[3] = {nullptr, nullptr, nullptr};  // same layout, other dtype
+    gk_matrix_s* solve_fmt = nullptr;  // SpMV layout picked for solves (null: not tuned)
+    int solve_fmt_tuned = 0;
     gk::SolverCache* solver = nullptr;
     gk::DevBuf stage_in, stage_out;  // host-pointer apply staging
     gk::DevBuf carry;                // merge-path block carries

@@ -510,6 +510,7 @@ static void free_arrays(gk_matrix A) {
 static void destroy_handle(gk_matrix A) {
     if (!A) return;
     for (int i = 0; i < 3; ++i) destroy_handle(A->lowp[i]);
+    if (A->solve_fmt != A) destroy_handle(A->solve_fmt);
     free_solver_cache(A);
     free_arrays(A);
     A->stage_in.release();
@@ -933,6 +934,9 @@ gk_status gk_matrix_describe(gk_matrix A, gk_matrix_desc* d) {
         if (cudaMemcpy(&e, A->plan.err, 4, cudaMemcpyDeviceToHost) == cudaSuccess) d->device_error = e;
     }
     d->spmv_launches = (A->fmt == GK_CSR && A->plan.kind == 2) ? 2 : 1;
+    d->solve_format = A->fmt != GK_CSR ? (int32_t)A->fmt
+                      : !A->solve_fmt_tuned ? -1
+                      : A->solve_fmt ? (int32_t)A->solve_fmt->fmt : (int32_t)GK_CSR;
     const size_t vb = value_bytes(A->dtype);
     if (A->fmt == GK_CSR) {
         d->stored = A->nnz;

@@ -126,11 +126,22 @@ __device__ __forceinline__ void block_sum(double (&v)[NA]) {
     for (int a = 0; a < NA; ++a) sh[a][threadIdx.x] = v[a];
     __syncthreads();
     if (threadIdx.x < 32) {
+        // lane l adds sh[l], sh[l+32], ... as a pairwise tree (short FP64
+        // dependency chains), then the lanes combine with shuffles
+        const int per = (int)((blockDim.x + 31) >> 5);  // values per lane, <= 16
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
-            double s = 0.0;
-            for (unsigned i = threadIdx.x; i < blockDim.x; i += 32) s += sh[a][i];
-            v[a] = warp_sum(s);
+            double t[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const unsigned idx = threadIdx.x + 32u * k;
+                t[k] = (k < per && idx < blockDim.x) ? sh[a][idx] : 0.0;
+            }
+#pragma unroll
+            for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+                for (int k = 0; k < w; ++k) t[k] += t[k + w];
+            v[a] = warp_sum(t[0]);
         }
     }
     __syncthreads();

@@ -41,6 +41,8 @@ struct KState {
     // GMRES
     int32_t k, m, cycle_end, v0_pending;
     double beta0, inv_h;
+    double stag;       // GMRES: stop when a cycle's residual > stag * the previous (0: off)
+    double prev_beta0;
     double H[(MAXM + 1) * MAXM];
     double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
     double h1[MAXM + 1], h2[MAXM + 1];
@@ -710,6 +712,12 @@ struct GmRestartFin {
             st->halt = 2;
             return;
         }
+        if (st->stag > 0.0 && st->prev_beta0 > 0.0 && b0 > st->stag * st->prev_beta0) {
+            st->status = GK_NOT_CONVERGED;  // stagnating inner solve: hand back
+            st->halt = 2;
+            return;
+        }
+        st->prev_beta0 = b0;
         if (st->cycle_end) st->restarts += 1;  // a cycle ended and a new one starts
         for (int j = 0; j <= st->m; ++j) st->g[j] = 0.0;
         st->g[0] = b0;
@@ -966,6 +974,80 @@ gk_status get_lowp(gk_matrix A, gk_dtype d, cudaStream_t s, gk_matrix* out) {
     return GK_OK;
 }
 
+// SpMV layout for solves on a CSR matrix (solver format selection).  The
+// padded layouts stream their column/value arrays with paired, fully
+// coalesced loads and no row-pointer indirection, so when padding costs
+// little they beat every CSR kernel.  Default rule, decided on the first
+// solve and kept: ELL when its stored entries are at most 1.2 x nnz, else
+// SELL-P(32) when its stored entries are at most 1.2 x nnz, else the CSR
+// itself.  The rule depends only on the sparsity pattern, so every handle of
+// a matrix solves with the same summation order (bit-identical results).
+// GK_SOLVE_FORMAT=csr|ell|sellp forces a layout; GK_SOLVE_FORMAT=timed times
+// three SpMVs of each admissible layout and keeps the fastest.  The copy holds
+// the same values bit for bit, so the choice changes the order of the row
+// sums, not the matrix.
+static gk_status solve_matrix(gk_matrix A, cudaStream_t s, gk_matrix* out) {
+    *out = A;
+    if (A->fmt != GK_CSR || A->n == 0) return GK_OK;
+    if (A->solve_fmt_tuned) {
+        *out = A->solve_fmt ? A->solve_fmt : A;
+        return GK_OK;
+    }
+    const char* env = getenv("GK_SOLVE_FORMAT");
+    const bool timed = env && !strcmp(env, "timed");
+    const bool force = env && !timed && strcmp(env, "auto") != 0;
+    const bool want_ell = !force || !strcmp(env, "ell");
+    const bool want_sellp = !force || !strcmp(env, "sellp");
+    auto padding_ok = [&](int64_t stored) { return force || stored <= A->nnz + A->nnz / 5; };
+    std::vector<gk_matrix> cand;
+    if (want_ell && padding_ok((int64_t)A->max_row * A->n)) {
+        gk_matrix E = nullptr;
+        GK_TRY(gk_matrix_convert(A, GK_ELL, A->dtype, 0, 0, s, &E));
+        cand.push_back(E);
+    }
+    if (want_sellp && (timed || cand.empty())) {
+        gk_matrix P = nullptr;
+        GK_TRY(gk_matrix_convert(A, GK_SELLP, A->dtype, 32, 1, s, &P));
+        if (padding_ok(P->stored)) cand.push_back(P);
+        else gk_matrix_destroy(P);
+    }
+    gk_matrix best = cand.empty() ? A : cand.front();
+    if (timed && !cand.empty()) {
+        const size_t vb = vector_bytes(A->dtype);
+        DevBuf xv, yv;
+        GK_TRY(xv.ensure(vb * (size_t)A->ncols));
+        GK_TRY(yv.ensure(vb * (size_t)A->n));
+        GK_CUDA(cudaMemsetAsync(xv.ptr, 0, vb * (size_t)A->ncols, s));
+        cudaEvent_t e0, e1;
+        GK_CUDA(cudaEventCreate(&e0));
+        GK_CUDA(cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        std::vector<gk_matrix> all = cand;
+        all.insert(all.begin(), A);
+        for (gk_matrix M : all) {
+            GK_TRY(spmv_dispatch(M, 1.0, xv.ptr, 0.0, yv.ptr, s));  // warm-up
+            GK_CUDA(cudaEventRecord(e0, s));
+            for (int r = 0; r < 3; ++r) GK_TRY(spmv_dispatch(M, 1.0, xv.ptr, 0.0, yv.ptr, s));
+            GK_CUDA(cudaEventRecord(e1, s));
+            GK_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = M;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    for (gk_matrix M : cand)
+        if (M != best) gk_matrix_destroy(M);
+    A->solve_fmt = best == A ? nullptr : best;
+    A->solve_fmt_tuned = 1;
+    *out = best;
+    return GK_OK;
+}
+
 static gk_status side_stream(gk_matrix A) {
     if (!A->side) GK_CUDA(cudaStreamCreateWithFlags(&A->side, cudaStreamNonBlocking));
     return GK_OK;
@@ -1056,6 +1138,7 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
     std::memset(h, 0, HDR);
     h->max_iters = max_iters;
     h->m = m;
+    h->stag = inner ? 0.95 : 0.0;
     GK_CUDA(cudaMemcpyAsync(st, h, HDR, cudaMemcpyHostToDevice, s));
     k_norm2<T, FinBnorm><<<eg, 256, 0, s>>>(n, b, part, tk, FinBnorm{st, tol});
     GK_CUDA(cudaGetLastError());
@@ -1228,7 +1311,9 @@ template <typename V, typename T>
 static gk_status solve_plain(gk_matrix A, const void* b, void* x, const gk_solve_opts* o,
                              cudaStream_t s, SolveOut* out) {
     const int m = o->method == GK_GMRES ? (o->krylov_dim ? o->krylov_dim : 30) : 0;
-    return solve_mk<V, T>(A, (const T*)b, (T*)x, o->method, o->precond == GK_PRECOND_JACOBI,
+    gk_matrix M = nullptr;
+    GK_TRY(solve_matrix(A, s, &M));
+    return solve_mk<V, T>(M, (const T*)b, (T*)x, o->method, o->precond == GK_PRECOND_JACOBI,
                           o->tol, o->max_iters, m, s, out);
 }
 
@@ -1240,6 +1325,9 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
     const int32_t n = A->n;
     gk_matrix L = nullptr;
     GK_TRY(get_lowp(A, o->mixed == 2 ? GK_BF16 : GK_F32, s, &L));
+    GK_TRY(solve_matrix(L, s, &L));  // layout of the inner SpMV
+    gk_matrix A64 = nullptr;
+    GK_TRY(solve_matrix(A, s, &A64));  // layout of the outer FP64 residual
     SolverCache* C = nullptr;
     GK_TRY(get_cache(A, &C));
     // FP64 workspace: r64 ; FP32: r32, d32 (in the low-precision handle's cache
@@ -1286,7 +1374,7 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
         h->bnorm = bnorm;
         GK_CUDA(cudaMemcpyAsync(st, h, HDR, cudaMemcpyHostToDevice, s));
         EpiResid<double, FinNorm> er{r64, b, nullptr, part, tk, FinNorm{st, 1}};
-        GK_TRY((launch_spmv_rows<double, double>(A, x, er, s)));
+        GK_TRY((launch_spmv_rows<double, double>(A64, x, er, s)));
         GK_TRY(read_hdr(C, s));
         tn = C->hst->tnorm;
         if (!std::isfinite(tn)) {

@@ -235,3 +235,73 @@ def test_config3_full_size_jacobi_cg_and_refinement():
     x2, info2 = _gpu_solve(m, b, "cg", 1, 1e-10, max_iters=20000, dtype="mixed", mixed=1)
     assert info2["return"] == gk.GK_OK
     assert oracle.true_rel_residual(m, b, x2) <= 1e-10
+
+
+def _with_long_row(m, row, width):
+    """m plus `width` symmetric entries 1e-3 between `row` and a contiguous
+    block of columns far from the band: ELL padding explodes, SELL-P pads
+    mostly the one slice holding `row` (the matrix stays SPD: the added
+    entries keep it diagonally dominant)."""
+    d = m.to_dense()
+    cols = np.arange(m.n // 2, m.n // 2 + width)
+    assert not np.any(d[row, cols])
+    d[row, cols] = d[cols, row] = 1e-3
+    return _dense_to_csr(d)
+
+
+def _dense_to_csr(d):
+    rp, ci, va = [0], [], []
+    for i in range(d.shape[0]):
+        nz = np.flatnonzero(d[i])
+        ci.extend(nz.tolist()); va.extend(d[i, nz].tolist())
+        rp.append(len(ci))
+    return W.CSR(d.shape[0], d.shape[1], np.array(rp), np.array(ci), np.array(va))
+
+
+def _solve_format(m, **kw):
+    import torch
+    dev = torch_dev()
+    A = gk.Matrix.from_csr(m, "f64")
+    assert A.describe()["solve_format"] == -1
+    b = torch.from_numpy(W.uniform_vector(m.n, 11)).to(dev)
+    x = torch.zeros(m.n, dtype=torch.float64, device=dev)
+    info = A.solve(b, x, method="cg", precond=1, tol=1e-10, max_iters=5000, engine=1, **kw)
+    fmt = A.describe()["solve_format"]
+    A.close()
+    return fmt, x.cpu().numpy(), info
+
+
+def test_solve_format_selection(monkeypatch):
+    """Solves on a CSR handle use ELL when its padding is <= 20 %, else
+    SELL-P(32) when its padding is <= 20 %, else the CSR kernels; the result
+    is bit-identical to solving on an explicit copy in that layout, and the
+    choice meets the tolerance like any other layout."""
+    monkeypatch.delenv("GK_SOLVE_FORMAT", raising=False)
+    m, b = CASES["lap2d_64"]()
+    fmt, x, info = _solve_format(m)
+    assert fmt == gk.GK_ELL and info["return"] == gk.GK_OK
+    xe, ie = _gpu_solve(m, W.uniform_vector(m.n, 11), "cg", 1, 1e-10, fmt="ell", engine=1)
+    assert np.array_equal(x, xe) and info["iters"] == ie["iters"]
+
+    m2 = _with_long_row(W.banded_spd(2000, 4, 3), 700, 64)
+    fmt2, x2, info2 = _solve_format(m2)
+    assert fmt2 == gk.GK_SELLP and info2["return"] == gk.GK_OK
+    assert oracle.true_rel_residual(m2, W.uniform_vector(m2.n, 11), x2) <= 1e-10 * 1.01
+
+    m3 = W.power_law(8192)
+    A3 = gk.Matrix.from_csr(m3, "f64")
+    import torch
+    dev = torch_dev()
+    b3 = torch.ones(m3.n, dtype=torch.float64, device=dev)
+    x3 = torch.zeros_like(b3)
+    A3.solve(b3, x3, method="gmres", precond=0, tol=1e-10, max_iters=3, engine=1)
+    assert A3.describe()["solve_format"] == gk.GK_CSR  # Zipf rows: padding too large
+    A3.close()
+
+    monkeypatch.setenv("GK_SOLVE_FORMAT", "csr")
+    fmt4, x4, info4 = _solve_format(m)
+    assert fmt4 == gk.GK_CSR and info4["return"] == gk.GK_OK
+    assert oracle.true_rel_residual(m, W.uniform_vector(m.n, 11), x4) <= 1e-10
+    monkeypatch.setenv("GK_SOLVE_FORMAT", "timed")
+    fmt5, x5, info5 = _solve_format(m)
+    assert fmt5 in (gk.GK_CSR, gk.GK_ELL) and info5["return"] == gk.GK_OK
