@@ -117,8 +117,10 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Fixed-order sum of NA per-thread values over the block (blockDim <= 512);
 // the result is valid in every lane of warp 0.  All threads must call.
 // FP64 warp instructions are expensive on this part (~16 SM cycles each),
-// so threads only store their values and warp 0 adds them: blockDim/32
-// sequential adds per lane and a 5-level shuffle tree per value.
+// so threads only store their values and warp 0 adds them: lane l sums
+// sh[l], sh[l+32], ... in two interleaved chains (even and odd slots),
+// then a 5-level shuffle tree combines the lanes.  Few registers stay live,
+// so the reduction does not lower the occupancy of the kernel calling it.
 template <int NA>
 __device__ __forceinline__ void block_sum(double (&v)[NA]) {
     __shared__ double sh[NA > 0 ? NA : 1][512];
@@ -126,22 +128,17 @@ __device__ __forceinline__ void block_sum(double (&v)[NA]) {
     for (int a = 0; a < NA; ++a) sh[a][threadIdx.x] = v[a];
     __syncthreads();
     if (threadIdx.x < 32) {
-        // lane l adds sh[l], sh[l+32], ... as a pairwise tree (short FP64
-        // dependency chains), then the lanes combine with shuffles
-        const int per = (int)((blockDim.x + 31) >> 5);  // values per lane, <= 16
+        const unsigned nb = blockDim.x;
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
-            double t[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const unsigned idx = threadIdx.x + 32u * k;
-                t[k] = (k < per && idx < blockDim.x) ? sh[a][idx] : 0.0;
+            double s0 = 0.0, s1 = 0.0;
+            unsigned idx = threadIdx.x;
+            for (; idx + 32u < nb; idx += 64u) {
+                s0 += sh[a][idx];
+                s1 += sh[a][idx + 32u];
             }
-#pragma unroll
-            for (int w = 8; w > 0; w >>= 1)
-#pragma unroll
-                for (int k = 0; k < w; ++k) t[k] += t[k + w];
-            v[a] = warp_sum(t[0]);
+            if (idx < nb) s0 += sh[a][idx];
+            v[a] = warp_sum(s0 + s1);
         }
     }
     __syncthreads();

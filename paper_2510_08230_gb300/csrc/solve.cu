@@ -18,6 +18,7 @@
 // return immediately once the state says "halt".  The host looks at the
 // state only between chunks.
 #include <cstring>
+#include <unordered_map>
 #include <vector>
 
 #include "spmv.cuh"
@@ -58,6 +59,31 @@ static unsigned ew_grid(int64_t n) {
     int64_t b = (n + 1023) / 1024;
     int64_t cap = (int64_t)num_sms() * 8;
     return (unsigned)std::max<int64_t>(1, std::min(b, cap));
+}
+
+// Grid of a grid-stride element-wise kernel (256 threads): at most one wave
+// of the blocks the kernel can keep resident (its register count decides:
+// 4 to 8 per SM), so no ragged second wave; at least ~4 elements a thread.
+template <typename K>
+static unsigned ewg(K kernel, int64_t n) {
+    static std::mutex mu;
+    static std::unordered_map<const void*, int> occ;
+    int b = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = occ.find((const void*)kernel);
+        if (it == occ.end()) {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 256, 0) != cudaSuccess ||
+                b < 1)
+                b = 1;
+            b = std::min(b, 8);
+            occ[(const void*)kernel] = b;
+        } else {
+            b = it->second;
+        }
+    }
+    const int64_t need = (n + 1023) / 1024;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * b));
 }
 
 // ------------------------------------------------------------ fins
@@ -175,25 +201,82 @@ __device__ __forceinline__ void finish_ew(T (&a)[NA], double* partials, unsigned
     grid_reduce_finish<NA>(d, partials, ticket, fin);
 }
 
+// Element-wise kernels run 256 threads per block (ewg sizes their grids).
+#define EW_BOUNDS __launch_bounds__(256)
+
 #define GRID_LOOP(i, n)                                                             \
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); \
          i += (int64_t)gridDim.x * blockDim.x)
 
+// 16-byte packs (2 doubles or 4 floats) for the streaming solver kernels.
+// A thread visits packs j = tid, tid + G, ...; pack j holds elements
+// [jN, jN + N).  When every pointer is 16-byte aligned a full pack moves as
+// one 16-byte access, else element by element; the elements a thread sees
+// and their order are the same either way, so no result depends on the
+// alignment of the caller's vectors.  Twice (FP64) or four times (FP32) the
+// bytes in flight per load instruction compared with scalar accesses.
+template <typename T>
+struct alignas(16) Pack {
+    static constexpr int N = 16 / (int)sizeof(T);
+    T v[N];
+};
+
+__device__ __forceinline__ bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+template <typename T>
+__device__ __forceinline__ Pack<T> pld(const T* __restrict__ p, int64_t j, int32_t n, bool vec) {
+    constexpr int N = Pack<T>::N;
+    const int64_t i0 = j * N;
+    Pack<T> r;
+    if (vec && i0 + N <= n) {
+        r = *reinterpret_cast<const Pack<T>*>(p + i0);
+    } else {
+#pragma unroll
+        for (int c = 0; c < N; ++c) r.v[c] = i0 + c < n ? p[i0 + c] : T(0);
+    }
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void pst(T* __restrict__ p, int64_t j, int32_t n, bool vec,
+                                    const Pack<T>& r) {
+    constexpr int N = Pack<T>::N;
+    const int64_t i0 = j * N;
+    if (vec && i0 + N <= n) {
+        *reinterpret_cast<Pack<T>*>(p + i0) = r;
+    } else {
+#pragma unroll
+        for (int c = 0; c < N; ++c)
+            if (i0 + c < n) p[i0 + c] = r.v[c];
+    }
+}
+
+#define PACK_LOOP(j, n, T)                                                                 \
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x,                       \
+                 j##_end = ((int64_t)(n) + Pack<T>::N - 1) / Pack<T>::N;                    \
+         j < j##_end; j += (int64_t)gridDim.x * blockDim.x)
+
 template <typename T, class Fin>
-__global__ void k_norm2(int32_t n, const T* __restrict__ v, double* partials, unsigned* ticket,
+__global__ void EW_BOUNDS k_norm2(int32_t n, const T* __restrict__ v, double* partials, unsigned* ticket,
                         Fin fin) {
+    constexpr int N = Pack<T>::N;
+    const bool vec = al16(v);
     T a[1] = {T(0)};
-    GRID_LOOP(i, n) a[0] = fmadd(v[i], v[i], a[0]);
+    PACK_LOOP(j, n, T) {
+        const Pack<T> V = pld(v, j, n, vec);
+#pragma unroll
+        for (int c = 0; c < N; ++c) a[0] = fmadd(V.v[c], V.v[c], a[0]);  // padding adds 0
+    }
     finish_ew<1>(a, partials, ticket, fin);
 }
 
 template <typename T>
-__global__ void k_zero(int32_t n, T* __restrict__ v) {
+__global__ void EW_BOUNDS k_zero(int32_t n, T* __restrict__ v) {
     GRID_LOOP(i, n) v[i] = T(0);
 }
 
 template <typename T>
-__global__ void k_copy(int32_t n, const T* __restrict__ a, T* __restrict__ b) {
+__global__ void EW_BOUNDS k_copy(int32_t n, const T* __restrict__ a, T* __restrict__ b) {
     GRID_LOOP(i, n) b[i] = a[i];
 }
 
@@ -268,33 +351,50 @@ struct CgUpdFin {
 
 // x += alpha p ; r -= alpha q ; z = D^-1 r ; <r,z>, <r,r>
 template <typename T>
-__global__ void k_cg_update(int32_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
+__global__ void EW_BOUNDS k_cg_update(int32_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
                             const T* __restrict__ p, const T* __restrict__ q,
                             const T* __restrict__ dinv, KState* st, double* partials,
                             unsigned* ticket) {
     if (halted(st)) return;
+    constexpr int N = Pack<T>::N;
     const T alpha = (T)st->alpha;
+    const bool vec = al16(x) && al16(r) && al16(z) && al16(p) && al16(q) && al16(dinv);
     T a[2] = {T(0), T(0)};
-    GRID_LOOP(i, n) {
-        x[i] = fmadd(alpha, p[i], x[i]);
-        const T ri = fmadd(-alpha, q[i], r[i]);
-        r[i] = ri;
-        if (dinv) {
-            const T zi = dinv[i] * ri;
-            z[i] = zi;
-            a[0] = fmadd(ri, zi, a[0]);
+    PACK_LOOP(j, n, T) {
+        const Pack<T> P = pld(p, j, n, vec), Q = pld(q, j, n, vec);
+        Pack<T> X = pld(x, j, n, vec), R = pld(r, j, n, vec);
+        Pack<T> Z = dinv ? pld(dinv, j, n, vec) : Pack<T>{};
+#pragma unroll
+        for (int c = 0; c < N; ++c) {  // padding lanes are 0 and add 0
+            X.v[c] = fmadd(alpha, P.v[c], X.v[c]);
+            R.v[c] = fmadd(-alpha, Q.v[c], R.v[c]);
+            if (dinv) {
+                Z.v[c] = Z.v[c] * R.v[c];
+                a[0] = fmadd(R.v[c], Z.v[c], a[0]);
+            }
+            a[1] = fmadd(R.v[c], R.v[c], a[1]);
         }
-        a[1] = fmadd(ri, ri, a[1]);
+        pst(x, j, n, vec, X);
+        pst(r, j, n, vec, R);
+        if (dinv) pst(z, j, n, vec, Z);
     }
     finish_ew<2>(a, partials, ticket, CgUpdFin{st, dinv != nullptr});
 }
 
 // p = z + beta p
 template <typename T>
-__global__ void k_cg_p(int32_t n, T* __restrict__ p, const T* __restrict__ z, const KState* st) {
+__global__ void EW_BOUNDS k_cg_p(int32_t n, T* __restrict__ p, const T* __restrict__ z, const KState* st) {
     if (halted(st)) return;
+    constexpr int N = Pack<T>::N;
     const T beta = (T)st->beta;
-    GRID_LOOP(i, n) p[i] = fmadd(beta, p[i], z[i]);
+    const bool vec = al16(p) && al16(z);
+    PACK_LOOP(j, n, T) {
+        Pack<T> P = pld(p, j, n, vec);
+        const Pack<T> Z = pld(z, j, n, vec);
+#pragma unroll
+        for (int c = 0; c < N; ++c) P.v[c] = fmadd(beta, P.v[c], Z.v[c]);
+        pst(p, j, n, vec, P);
+    }
 }
 
 struct CgInitFin {
@@ -304,7 +404,7 @@ struct CgInitFin {
 
 // z = D^-1 r ; p = z ; rho = <r, z>
 template <typename T>
-__global__ void k_cg_init(int32_t n, const T* __restrict__ r, T* __restrict__ z, T* __restrict__ p,
+__global__ void EW_BOUNDS k_cg_init(int32_t n, const T* __restrict__ r, T* __restrict__ z, T* __restrict__ p,
                           const T* __restrict__ dinv, KState* st, double* partials,
                           unsigned* ticket) {
     T a[1] = {T(0)};
@@ -340,14 +440,23 @@ struct BiAlphaFin {
 // beta = (rho'/rho_old)(alpha/omega) is prepared by the previous update's fin
 // p = r + beta (p - omega v) ; phat = M^-1 p
 template <typename T>
-__global__ void k_bi_p(int32_t n, T* __restrict__ p, T* __restrict__ ph, const T* __restrict__ r,
+__global__ void EW_BOUNDS k_bi_p(int32_t n, T* __restrict__ p, T* __restrict__ ph, const T* __restrict__ r,
                        const T* __restrict__ v, const T* __restrict__ dinv, const KState* st) {
     if (halted(st)) return;
+    constexpr int N = Pack<T>::N;
     const T beta = (T)st->beta, omega = (T)st->omega;
-    GRID_LOOP(i, n) {
-        const T pi = fmadd(beta, fmadd(-omega, v[i], p[i]), r[i]);
-        p[i] = pi;
-        if (dinv) ph[i] = dinv[i] * pi;
+    const bool vec = al16(p) && al16(ph) && al16(r) && al16(v) && al16(dinv);
+    PACK_LOOP(j, n, T) {
+        Pack<T> P = pld(p, j, n, vec);
+        const Pack<T> Vv = pld(v, j, n, vec), R = pld(r, j, n, vec);
+        Pack<T> D = dinv ? pld(dinv, j, n, vec) : Pack<T>{};
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            P.v[c] = fmadd(beta, fmadd(-omega, Vv.v[c], P.v[c]), R.v[c]);
+            D.v[c] = D.v[c] * P.v[c];
+        }
+        pst(p, j, n, vec, P);
+        if (dinv) pst(ph, j, n, vec, D);
     }
 }
 
@@ -369,17 +478,26 @@ struct BiSFin {
 
 // s = r - alpha v ; shat = M^-1 s ; ||s||^2
 template <typename T>
-__global__ void k_bi_s(int32_t n, T* __restrict__ s, T* __restrict__ sh, const T* __restrict__ r,
+__global__ void EW_BOUNDS k_bi_s(int32_t n, T* __restrict__ s, T* __restrict__ sh, const T* __restrict__ r,
                        const T* __restrict__ v, const T* __restrict__ dinv, KState* st,
                        double* partials, unsigned* ticket) {
     if (halted(st)) return;
+    constexpr int N = Pack<T>::N;
     const T alpha = (T)st->alpha;
+    const bool vec = al16(s) && al16(sh) && al16(r) && al16(v) && al16(dinv);
     T a[1] = {T(0)};
-    GRID_LOOP(i, n) {
-        const T si = fmadd(-alpha, v[i], r[i]);
-        s[i] = si;
-        if (dinv) sh[i] = dinv[i] * si;
-        a[0] = fmadd(si, si, a[0]);
+    PACK_LOOP(j, n, T) {
+        const Pack<T> Vv = pld(v, j, n, vec);
+        Pack<T> S = pld(r, j, n, vec);
+        Pack<T> D = dinv ? pld(dinv, j, n, vec) : Pack<T>{};
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            S.v[c] = fmadd(-alpha, Vv.v[c], S.v[c]);
+            D.v[c] = D.v[c] * S.v[c];
+            a[0] = fmadd(S.v[c], S.v[c], a[0]);
+        }
+        pst(s, j, n, vec, S);
+        if (dinv) pst(sh, j, n, vec, D);
     }
     finish_ew<1>(a, partials, ticket, BiSFin{st});
 }
@@ -442,24 +560,40 @@ struct BiUpdFin {
 // full step: x += alpha phat + omega shat ; r = s - omega t ; <rhat, r>, <r, r>
 // half step (st->half): x += alpha phat only.
 template <typename T>
-__global__ void k_bi_update(int32_t n, T* __restrict__ x, T* __restrict__ r,
+__global__ void EW_BOUNDS k_bi_update(int32_t n, T* __restrict__ x, T* __restrict__ r,
                             const T* __restrict__ ph, const T* __restrict__ sh,
                             const T* __restrict__ s, const T* __restrict__ t,
                             const T* __restrict__ rh, KState* st, double* partials,
                             unsigned* ticket) {
     if (halted(st)) return;
     const bool half = st->half != 0;
+    constexpr int N = Pack<T>::N;
     const T alpha = (T)st->alpha, omega = (T)st->omega;
+    const bool vec = al16(x) && al16(r) && al16(ph) && al16(sh) && al16(s) && al16(t) && al16(rh);
     T a[2] = {T(0), T(0)};
-    GRID_LOOP(i, n) {
-        if (half) {
-            x[i] = fmadd(alpha, ph[i], x[i]);
-        } else {
-            x[i] = fmadd(omega, sh[i], fmadd(alpha, ph[i], x[i]));
-            const T ri = fmadd(-omega, t[i], s[i]);
-            r[i] = ri;
-            a[0] = fmadd(rh[i], ri, a[0]);
-            a[1] = fmadd(ri, ri, a[1]);
+    if (half) {
+        PACK_LOOP(j, n, T) {
+            Pack<T> X = pld(x, j, n, vec);
+            const Pack<T> PH = pld(ph, j, n, vec);
+#pragma unroll
+            for (int c = 0; c < N; ++c) X.v[c] = fmadd(alpha, PH.v[c], X.v[c]);
+            pst(x, j, n, vec, X);
+        }
+    } else {
+        PACK_LOOP(j, n, T) {
+            Pack<T> X = pld(x, j, n, vec);
+            const Pack<T> PH = pld(ph, j, n, vec), SH = pld(sh, j, n, vec);
+            const Pack<T> Tt = pld(t, j, n, vec), RH = pld(rh, j, n, vec);
+            Pack<T> R = pld(s, j, n, vec);
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                X.v[c] = fmadd(omega, SH.v[c], fmadd(alpha, PH.v[c], X.v[c]));
+                R.v[c] = fmadd(-omega, Tt.v[c], R.v[c]);
+                a[0] = fmadd(RH.v[c], R.v[c], a[0]);
+                a[1] = fmadd(R.v[c], R.v[c], a[1]);
+            }
+            pst(x, j, n, vec, X);
+            pst(r, j, n, vec, R);
         }
     }
     finish_ew<2>(a, partials, ticket, BiUpdFin{st});
@@ -483,7 +617,7 @@ struct BiInitFin {
 
 // rhat = r ; p = v = 0 ; rho = <rhat, r>
 template <typename T>
-__global__ void k_bi_init(int32_t n, const T* __restrict__ r, T* __restrict__ rh, T* __restrict__ p,
+__global__ void EW_BOUNDS k_bi_init(int32_t n, const T* __restrict__ r, T* __restrict__ rh, T* __restrict__ p,
                           T* __restrict__ v, KState* st, double* partials, unsigned* ticket) {
     T a[1] = {T(0)};
     GRID_LOOP(i, n) {
@@ -664,27 +798,44 @@ k_gm_orth(int32_t n, int64_t ldv, const T* __restrict__ V, T* __restrict__ w, KS
 // not at the end of a cycle: v_{k} = w / h ; z = M^-1 v_k
 // at the end of a cycle:     x += M^-1 (V y)
 template <typename T>
-__global__ void k_gm_next(int32_t n, int64_t ldv, T* __restrict__ V, const T* __restrict__ w,
+__global__ void EW_BOUNDS k_gm_next(int32_t n, int64_t ldv, T* __restrict__ V, const T* __restrict__ w,
                           T* __restrict__ z, T* __restrict__ x, const T* __restrict__ dinv,
                           const KState* st) {
     if (halted(st)) return;
     const int32_t k = st->k;
+    constexpr int N = Pack<T>::N;
+    // ldv spans a multiple of 256 bytes, so every basis vector shares V's alignment
+    const bool vec = al16(V) && al16(w) && al16(z) && al16(x) && al16(dinv);
     if (!st->cycle_end) {
         const T ih = (T)st->inv_h;
         T* vk = V + (int64_t)k * ldv;
-        GRID_LOOP(i, n) {
-            const T v = w[i] * ih;
-            vk[i] = v;
-            z[i] = dinv ? dinv[i] * v : v;
+        PACK_LOOP(j, n, T) {
+            Pack<T> Vk = pld(w, j, n, vec);
+            Pack<T> Z = dinv ? pld(dinv, j, n, vec) : Pack<T>{};
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                Vk.v[c] = Vk.v[c] * ih;
+                Z.v[c] = dinv ? Z.v[c] * Vk.v[c] : Vk.v[c];
+            }
+            pst(vk, j, n, vec, Vk);
+            pst(z, j, n, vec, Z);
         }
     } else {
         __shared__ T s_y[MAXM];
         for (int j = threadIdx.x; j < k; j += blockDim.x) s_y[j] = (T)st->y[j];
         __syncthreads();
-        GRID_LOOP(i, n) {
-            T u = T(0);
-            for (int j = 0; j < k; ++j) u = fmadd(V[(int64_t)j * ldv + i], s_y[j], u);
-            x[i] = fmadd(dinv ? dinv[i] : T(1), u, x[i]);
+        PACK_LOOP(j, n, T) {
+            Pack<T> U{};
+            for (int l = 0; l < k; ++l) {
+                const Pack<T> Vl = pld(V + (int64_t)l * ldv, j, n, vec);
+#pragma unroll
+                for (int c = 0; c < N; ++c) U.v[c] = fmadd(Vl.v[c], s_y[l], U.v[c]);
+            }
+            Pack<T> X = pld(x, j, n, vec);
+            const Pack<T> D = dinv ? pld(dinv, j, n, vec) : Pack<T>{};
+#pragma unroll
+            for (int c = 0; c < N; ++c) X.v[c] = fmadd(dinv ? D.v[c] : T(1), U.v[c], X.v[c]);
+            pst(x, j, n, vec, X);
         }
     }
 }
@@ -755,14 +906,22 @@ struct EpiGmResid {
 
 // v_0 = r / beta0 ; z = M^-1 v_0 (after a restart decided to continue)
 template <typename T>
-__global__ void k_gm_v0(int32_t n, T* __restrict__ V, const T* __restrict__ r, T* __restrict__ z,
+__global__ void EW_BOUNDS k_gm_v0(int32_t n, T* __restrict__ V, const T* __restrict__ r, T* __restrict__ z,
                         const T* __restrict__ dinv, const KState* st) {
     if (halted(st) || !st->v0_pending) return;
+    constexpr int N = Pack<T>::N;
     const T ib = (T)st->inv_h;
-    GRID_LOOP(i, n) {
-        const T v = r[i] * ib;
-        V[i] = v;
-        z[i] = dinv ? dinv[i] * v : v;
+    const bool vec = al16(V) && al16(r) && al16(z) && al16(dinv);
+    PACK_LOOP(j, n, T) {
+        Pack<T> V0 = pld(r, j, n, vec);
+        Pack<T> Z = dinv ? pld(dinv, j, n, vec) : Pack<T>{};
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            V0.v[c] = V0.v[c] * ib;
+            Z.v[c] = dinv ? Z.v[c] * V0.v[c] : V0.v[c];
+        }
+        pst(V, j, n, vec, V0);
+        pst(z, j, n, vec, Z);
     }
 }
 
@@ -863,11 +1022,11 @@ struct EpiBiT {
 };
 
 template <typename T>
-__global__ void k_cast_add(int32_t n, double* __restrict__ x, const T* __restrict__ d) {
+__global__ void EW_BOUNDS k_cast_add(int32_t n, double* __restrict__ x, const T* __restrict__ d) {
     GRID_LOOP(i, n) x[i] += (double)d[i];
 }
 template <typename T>
-__global__ void k_cast_to(int32_t n, const double* __restrict__ r, T* __restrict__ o) {
+__global__ void EW_BOUNDS k_cast_to(int32_t n, const double* __restrict__ r, T* __restrict__ o) {
     GRID_LOOP(i, n) o[i] = (T)r[i];
 }
 
@@ -1131,7 +1290,6 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
     unsigned* tk = (unsigned*)C->ticket.ptr;
     KState* st = (KState*)C->state.ptr;
     const int32_t* halt = &st->halt;
-    const unsigned eg = ew_grid(n);
 
     // state header
     KState* h = C->hst;
@@ -1140,7 +1298,7 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
     h->m = m;
     h->stag = inner ? 0.95 : 0.0;
     GK_CUDA(cudaMemcpyAsync(st, h, HDR, cudaMemcpyHostToDevice, s));
-    k_norm2<T, FinBnorm><<<eg, 256, 0, s>>>(n, b, part, tk, FinBnorm{st, tol});
+    k_norm2<T, FinBnorm><<<ewg(k_norm2<T, FinBnorm>, n), 256, 0, s>>>(n, b, part, tk, FinBnorm{st, tol});
     GK_CUDA(cudaGetLastError());
 
     T *r = vec_at<T>(C, n, 0), *tmp = vec_at<T>(C, n, 1);
@@ -1151,7 +1309,7 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
         // cycle start: r = b - A x, restart fin sets g, k; v0 = r / beta0
         EpiResid<T, GmRestartFin> e0{r, b, halt, part, tk, GmRestartFin{st}};
         GK_TRY((launch_spmv_rows<V, T>(A, x, e0, s)));
-        k_gm_v0<T><<<eg, 256, 0, s>>>(n, Vm, r, z, dinv, st);
+        k_gm_v0<T><<<ewg(k_gm_v0<T>, n), 256, 0, s>>>(n, Vm, r, z, dinv, st);
         GK_CUDA(cudaGetLastError());
         const int chunk = chunk_for(n);
         if (!C->exec || C->kb != b || C->kx != x || C->kmethod != method || C->kprec != (int)prec ||
@@ -1162,10 +1320,10 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
                 k_gm_dot1<T><<<md_grid, MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st, part, tk);
                 k_gm_dot2<T><<<md_grid, MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st, part, tk);
                 k_gm_orth<T><<<md_grid, MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st, part, tk);
-                k_gm_next<T><<<eg, 256, 0, cs>>>(n, ldv, Vm, w, z, x, dinv, st);
+                k_gm_next<T><<<ewg(k_gm_next<T>, n), 256, 0, cs>>>(n, ldv, Vm, w, z, x, dinv, st);
                 EpiGmResid<T> e2{r, b, st, part, tk, GmRestartFin{st}};
                 GK_TRY((launch_spmv_rows<V, T>(A, x, e2, cs)));
-                k_gm_v0<T><<<eg, 256, 0, cs>>>(n, Vm, r, z, dinv, st);
+                k_gm_v0<T><<<ewg(k_gm_v0<T>, n), 256, 0, cs>>>(n, Vm, r, z, dinv, st);
                 GK_CUDA(cudaGetLastError());
                 return GK_OK;
             }));
@@ -1186,11 +1344,11 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
         GK_TRY((launch_spmv_rows<V, T>(A, x, e0, s)));
         auto init = [&]() -> gk_status {
             if (method == GK_CG)  // slots: 0 r, 1 tmp, 2 q, 3 p, 4 z
-                k_cg_init<T><<<eg, 256, 0, s>>>(n, r, vec_at<T>(C, n, 4), vec_at<T>(C, n, 3), dinv,
+                k_cg_init<T><<<ewg(k_cg_init<T>, n), 256, 0, s>>>(n, r, vec_at<T>(C, n, 4), vec_at<T>(C, n, 3), dinv,
                                                 st, part, tk);
             else
                 // slots: 0 r, 1 tmp, 2 rhat, 3 p, 4 phat, 5 s, 6 v, 7 shat, 8 t
-                k_bi_init<T><<<eg, 256, 0, s>>>(n, r, vec_at<T>(C, n, 2), vec_at<T>(C, n, 3),
+                k_bi_init<T><<<ewg(k_bi_init<T>, n), 256, 0, s>>>(n, r, vec_at<T>(C, n, 2), vec_at<T>(C, n, 3),
                                                 vec_at<T>(C, n, 6), st, part, tk);
             GK_CUDA(cudaGetLastError());
             return GK_OK;
@@ -1205,21 +1363,21 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
                       *q = vec_at<T>(C, n, 2);
                     EpiDot<T, CgAlphaFin> e1{q, p, halt, part, tk, CgAlphaFin{st}};
                     GK_TRY((launch_spmv_rows<V, T>(A, p, e1, cs)));
-                    k_cg_update<T><<<eg, 256, 0, cs>>>(n, x, r, z, p, q, dinv, st, part, tk);
-                    k_cg_p<T><<<eg, 256, 0, cs>>>(n, p, z, st);
+                    k_cg_update<T><<<ewg(k_cg_update<T>, n), 256, 0, cs>>>(n, x, r, z, p, q, dinv, st, part, tk);
+                    k_cg_p<T><<<ewg(k_cg_p<T>, n), 256, 0, cs>>>(n, p, z, st);
                 } else {
                     T *rh = vec_at<T>(C, n, 2), *p = vec_at<T>(C, n, 3), *ph = vec_at<T>(C, n, 4);
                     T *v = vec_at<T>(C, n, 6), *sv = vec_at<T>(C, n, 5), *sh = vec_at<T>(C, n, 7);
                     T* t = vec_at<T>(C, n, 8);
                     const T* phs = prec ? ph : p;
                     const T* shs = prec ? sh : sv;
-                    k_bi_p<T><<<eg, 256, 0, cs>>>(n, p, ph, r, v, dinv, st);
+                    k_bi_p<T><<<ewg(k_bi_p<T>, n), 256, 0, cs>>>(n, p, ph, r, v, dinv, st);
                     EpiDot<T, BiAlphaFin> e1{v, rh, halt, part, tk, BiAlphaFin{st}};
                     GK_TRY((launch_spmv_rows<V, T>(A, phs, e1, cs)));
-                    k_bi_s<T><<<eg, 256, 0, cs>>>(n, sv, sh, r, v, dinv, st, part, tk);
+                    k_bi_s<T><<<ewg(k_bi_s<T>, n), 256, 0, cs>>>(n, sv, sh, r, v, dinv, st, part, tk);
                     EpiBiT<T> e2{t, sv, st, part, tk, BiOmegaFin{st}};
                     GK_TRY((launch_spmv_rows<V, T>(A, shs, e2, cs)));
-                    k_bi_update<T><<<eg, 256, 0, cs>>>(n, x, r, phs, shs, sv, t, rh, st, part, tk);
+                    k_bi_update<T><<<ewg(k_bi_update<T>, n), 256, 0, cs>>>(n, x, r, phs, shs, sv, t, rh, st, part, tk);
                 }
                 GK_CUDA(cudaGetLastError());
                 return GK_OK;
@@ -1248,7 +1406,7 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
                     break;
                 }
                 // residual replacement and restart from x
-                k_copy<T><<<eg, 256, 0, s>>>(n, tmp, r);
+                k_copy<T><<<ewg(k_copy<T>, n), 256, 0, s>>>(n, tmp, r);
                 GK_TRY(init());
                 C->hst->restarts += 1;
                 GK_CUDA(cudaMemcpyAsync(&st->restarts, &C->hst->restarts, 4, cudaMemcpyHostToDevice, s));
@@ -1280,7 +1438,7 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
         GK_TRY(read_hdr(C, s));
         out->tru = C->hst->tnorm / C->hst->bnorm;
     } else {
-        k_zero<T><<<eg, 256, 0, s>>>(n, x);
+        k_zero<T><<<ewg(k_zero<T>, n), 256, 0, s>>>(n, x);
         GK_CUDA(cudaGetLastError());
         out->status = GK_OK;
         out->iters = 0;
@@ -1343,16 +1501,15 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
     double* part = (double*)C->partials.ptr;
     unsigned* tk = (unsigned*)C->ticket.ptr;
     KState* st = (KState*)C->state.ptr;
-    const unsigned eg = ew_grid(n);
     KState* h = C->hst;
     std::memset(h, 0, HDR);
     GK_CUDA(cudaMemcpyAsync(st, h, HDR, cudaMemcpyHostToDevice, s));
-    k_norm2<double, FinBnorm><<<eg, 256, 0, s>>>(n, b, part, tk, FinBnorm{st, o->tol});
+    k_norm2<double, FinBnorm><<<ewg(k_norm2<double, FinBnorm>, n), 256, 0, s>>>(n, b, part, tk, FinBnorm{st, o->tol});
     GK_TRY(read_hdr(C, s));
     const double bnorm = C->hst->bnorm, thr = C->hst->thr;
     if (!(bnorm > 0.0)) {
         if (bnorm == 0.0) {
-            k_zero<double><<<eg, 256, 0, s>>>(n, x);
+            k_zero<double><<<ewg(k_zero<double>, n), 256, 0, s>>>(n, x);
             GK_CUDA(cudaGetLastError());
             out->status = GK_OK;
             return GK_OK;
@@ -1386,8 +1543,8 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
             break;
         }
         if (k >= max_outer || total_inner >= o->max_iters) break;
-        k_cast_to<float><<<eg, 256, 0, s>>>(n, r64, r32);
-        k_zero<float><<<eg, 256, 0, s>>>(n, d32);
+        k_cast_to<float><<<ewg(k_cast_to<float>, n), 256, 0, s>>>(n, r64, r32);
+        k_zero<float><<<ewg(k_zero<float>, n), 256, 0, s>>>(n, d32);
         GK_CUDA(cudaGetLastError());
         SolveOut io;
         const bool prec = o->precond == GK_PRECOND_JACOBI;
@@ -1405,7 +1562,7 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
             status = io.status;
             break;
         }
-        k_cast_add<float><<<eg, 256, 0, s>>>(n, x, d32);
+        k_cast_add<float><<<ewg(k_cast_add<float>, n), 256, 0, s>>>(n, x, d32);
         GK_CUDA(cudaGetLastError());
     }
     out->status = status;

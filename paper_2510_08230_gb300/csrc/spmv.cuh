@@ -240,7 +240,7 @@ k_csr_merge(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
             int32_t* __restrict__ carry_row, T* __restrict__ carry_val) {
     using Sh = MergeShape<E, V, T>;
     constexpr int TI = Sh::TI;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     V* s_val = reinterpret_cast<V*>(smem);
     T* s_xv = reinterpret_cast<T*>(smem + Sh::OFF_XV);
     int32_t* s_rowend = reinterpret_cast<int32_t*>(smem + Sh::OFF_RE);
@@ -627,17 +627,24 @@ gk_status launch_spmv_rows(gk_matrix A, const T* x, const Epi& epi, cudaStream_t
             default: k_csr_vector<32, V, T, Epi><<<grid, 256, 0, s>>>(n, A->row_ptr, A->col, va, x, epi); break;
         }
     } else if (A->fmt == GK_ELL) {
+        // grid-stride kernels: one full wave of resident blocks, no ragged second wave
+        static thread_local int occ = 0;
+        if (!occ) occ = std::min(occupancy_blocks(k_ell<V, T, Epi>, 256, 0), 8);
         int64_t need = ((A->n + 1) / 2 + 255) / 256;
-        grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 8));
+        grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * occ));
         k_ell<V, T, Epi><<<grid, 256, 0, s>>>(A->n, A->stride, A->K, A->col, (const V*)A->val, x, epi);
     } else if (A->S % 2 == 0) {
+        static thread_local int occ = 0;
+        if (!occ) occ = std::min(occupancy_blocks(k_sellp_pairs<V, T, Epi>, 256, 0), 8);
         int64_t need = ((A->n + 1) / 2 + 255) / 256;
-        grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 8));
+        grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * occ));
         k_sellp_pairs<V, T, Epi><<<grid, 256, 0, s>>>(A->n, A->S, A->slice_len, A->slice_set,
                                                       A->col, (const V*)A->val, x, epi);
     } else {
+        static thread_local int occ = 0;
+        if (!occ) occ = std::min(occupancy_blocks(k_sellp<V, T, Epi>, 256, 0), 8);
         int64_t need = (A->n + 255) / 256;
-        grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * 8));
+        grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * occ));
         k_sellp<V, T, Epi><<<grid, 256, 0, s>>>(A->n, A->S, A->slice_len, A->slice_set, A->col,
                                                 (const V*)A->val, x, epi);
     }
