@@ -22,7 +22,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 ERR_INVALID, ERR_ZERO_DIAG, ERR_NAN = -1, -5, -6
-CG, BICGSTAB, GMRES = 0, 1, 2
+CG, BICGSTAB, GMRES, CGS = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -89,7 +89,7 @@ def _declare(L):
     L.or_sellp_to_csr.restype = i64
     L.or_jacobi_gen.argtypes = [i32, _i32p, _i32p, _f64p, _f64p]
     L.or_jacobi_gen.restype = ctypes.c_int
-    for name in ("or_cg", "or_bicgstab", "or_gmres"):
+    for name in ("or_cg", "or_bicgstab", "or_gmres", "or_cgs"):
         f = getattr(L, name)
         f.argtypes = [i32, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.POINTER(Opts),
                       ctypes.POINTER(Info), vp]
@@ -204,12 +204,13 @@ def jacobi(m):
 
 def solve(m, b, x0=None, method=CG, precond=0, tol=1e-10, max_iters=1000,
           krylov_dim=30, history=False):
-    """Runs CG / BiCGSTAB / GMRES(m).  Returns (x, info dict[, history])."""
+    """Runs CG / BiCGSTAB / GMRES(m) / CGS.  Returns (x, info dict[, history])."""
     x = np.zeros(m.n) if x0 is None else _f64(x0).copy()
     o = Opts(method, precond, tol, max_iters, krylov_dim)
     info = Info()
     hist = np.full(max_iters + 2, np.nan) if history else None
-    f = {CG: lib().or_cg, BICGSTAB: lib().or_bicgstab, GMRES: lib().or_gmres}[method]
+    f = {CG: lib().or_cg, BICGSTAB: lib().or_bicgstab, GMRES: lib().or_gmres,
+         CGS: lib().or_cgs}[method]
     if m.n == 0:
         x = np.zeros(0)
         info.status = OK

@@ -313,7 +313,7 @@ def test_cg_breakdown_on_negative_definite():
     assert info["status"] == oracle.BREAKDOWN
 
 
-@pytest.mark.parametrize("method", [oracle.CG, oracle.BICGSTAB, oracle.GMRES])
+@pytest.mark.parametrize("method", [oracle.CG, oracle.BICGSTAB, oracle.GMRES, oracle.CGS])
 def test_zero_rhs_returns_zero(method):
     m = W.laplacian_2d(5)
     x, info = oracle.solve(m, np.zeros(m.n), x0=np.ones(m.n), method=method)
@@ -427,7 +427,67 @@ def test_gmres_givens_estimate_equals_true_residual_in_cycle():
 def test_solvers_jacobi_on_diffusion_reach_tol():
     m = W.diffusion_3d(10)
     b = W.uniform_vector(m.n, 3)
-    for method in (oracle.CG, oracle.BICGSTAB, oracle.GMRES):
+    for method in (oracle.CG, oracle.BICGSTAB, oracle.GMRES, oracle.CGS):
         x, info = oracle.solve(m, b, method=method, precond=1, tol=1e-10, max_iters=5000)
         assert info["status"] == oracle.OK, (method, info)
         assert oracle.true_rel_residual(m, b, x) <= 1e-10
+
+
+# ---------------------------------------------------------------- CGS pins
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_cgs_matches_lapack(precond):
+    """CGS on the nonsymmetric 1D convection-diffusion system reaches the
+    dense LU solution within kappa * tol."""
+    m = _convdiff_1d(60, 0.4)
+    b = np.random.default_rng(6).standard_normal(m.n)
+    x, info = oracle.solve(m, b, method=oracle.CGS, precond=precond, tol=1e-12, max_iters=500)
+    xs = np.linalg.solve(m.to_dense(), b)
+    assert info["status"] == oracle.OK
+    kappa = np.linalg.cond(m.to_dense())
+    assert np.linalg.norm(x - xs) <= 2 * kappa * 1e-12 * np.linalg.norm(xs)
+    assert oracle.true_rel_residual(m, b, x) <= 1e-12
+
+
+@pytest.mark.parametrize("n,seed", [(8, 1), (12, 2)])
+def test_cgs_finite_termination(n, seed):
+    """CGS squares the BiCG residual polynomial; BiCG ends in at most n steps
+    in exact arithmetic, so a well-conditioned nonsymmetric n x n system
+    reaches 1e-11 in n (+2 for rounding) iterations."""
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((n, n)) * 0.2 + 3.0 * np.eye(n)
+    m = _dense_csr(a)
+    b = rng.standard_normal(n)
+    x, info = oracle.solve(m, b, method=oracle.CGS, tol=1e-11, max_iters=n + 2)
+    assert info["status"] == oracle.OK and info["iters"] <= n + 2
+    xs = np.linalg.solve(a, b)
+    assert np.linalg.norm(x - xs) <= np.linalg.cond(a) * 1e-10 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_cgs_residual_is_squared_cg_polynomial(k):
+    """For SPD A with shadow residual r_0, BiCG is CG, and the CGS residual
+    after k steps is P_k(A)^2 r_0 where P_k(A) r_0 is the CG residual.  On a
+    diagonal A the polynomial is read per eigenvalue: P_k(l_i) = r^CG_i / r0_i,
+    and r^CGS_i must equal P_k(l_i)^2 r0_i (a wrong alpha or beta breaks it)."""
+    n = 8
+    lam = np.linspace(1.0, 3.0, n)
+    m = _csr(n, n, np.arange(n + 1), np.arange(n), lam)
+    b = np.random.default_rng(10 + k).uniform(0.5, 1.5, n)
+    x_cg, i_cg = oracle.solve(m, b, method=oracle.CG, tol=1e-30, max_iters=k)
+    x_cgs, i_cgs = oracle.solve(m, b, method=oracle.CGS, tol=1e-30, max_iters=k)
+    assert i_cg["iters"] == k and i_cgs["iters"] == k
+    pk = (b - lam * x_cg) / b
+    r_cgs = b - lam * x_cgs
+    assert np.allclose(r_cgs, pk * pk * b, rtol=1e-9, atol=1e-12 * np.linalg.norm(b))
+
+
+def test_jacobi_cgs_diagonal_one_iteration():
+    n = 30
+    d = np.linspace(1.0, 50.0, n)
+    m = _csr(n, n, np.arange(n + 1), np.arange(n), d)
+    b = np.random.default_rng(3).standard_normal(n)
+    x, info = oracle.solve(m, b, method=oracle.CGS, precond=1, tol=1e-12)
+    assert info["status"] == oracle.OK and info["iters"] == 1
+    assert np.allclose(x, b / d, rtol=1e-15, atol=0)
