@@ -360,6 +360,57 @@ def serving_bench(gk, W, torch, dev, n_req=240, factors=(0.5, 0.8, 0.95)):
     return out
 
 
+def profile_case(name, dtype):
+    """One small case per kernel family for `ncu` captures: inputs larger
+    than L2 (129 MB) but a few hundred MB on the device, three launches of
+    the kernel after the matrix is built.
+      merge    CSR merge path, Zipf(1.8) power-law n=2^21 (~33M nnz)
+      rowtile  CSR row tiles, 3D 7-point Laplacian 128^3 (14.6M nnz)
+      ell      ELL of the same Laplacian
+      sellp    SELL-P(32) of the same Laplacian
+      cg, bicgstab, gmres
+               24 Jacobi-preconditioned iterations (GMRES(30): Arnoldi
+               steps) on the 128^3 diffusion problem (solver kernels: SpMV
+               epilogues, fused updates, multi-dots)"""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_08230_gb300 as gk
+    from paper_2510_08230_gb300 import workloads as W
+    dev = torch.device("cuda:0")
+    vt = torch.float64 if dtype == "f64" else torch.float32
+    if name in ("cg", "bicgstab", "gmres"):
+        m = W.diffusion_3d(128)
+        A = gk.Matrix.from_csr(m, dtype)
+        b = torch.from_numpy(W.uniform_vector(m.n, W.SEED_BASE + 3)).to(dev, vt)
+        x = torch.zeros_like(b)
+        info = A.solve(b, x, method=name, precond="jacobi", tol=0.0, max_iters=24)
+        torch.cuda.synchronize()
+        print("profile case", name, dtype, info["iters"], A.describe()["solve_format"])
+        A.close()
+        return 0
+    if name == "merge":
+        os.environ["GK_CSR_KERNEL"] = "2"
+        m = W.power_law(1 << 21, seed=W.SEED_BASE + 2)
+    else:
+        os.environ["GK_CSR_KERNEL"] = "1"
+        m = W.laplacian_3d(128)
+    A = gk.Matrix.from_csr(m, dtype)
+    if name in ("ell", "sellp"):
+        B = A.convert(name, None, 32, 1)
+        A.close()
+        A = B
+    x = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, m.ncols)).to(dev, vt)
+    y = torch.empty(m.n, dtype=vt, device=dev)
+    for _ in range(3):
+        A.apply(x, y)
+    torch.cuda.synchronize()
+    print("profile case", name, dtype, KERNEL_NAMES[A.desc["spmv_kernel"]], m.n, m.nnz,
+          alg_bytes(m, 8 if dtype == "f64" else 4, "csr" if name in ("merge", "rowtile") else name))
+    A.close()
+    return 0
+
+
 def run_reference(args):
     """The oracle on the host cores, same metric and unit."""
     rank = int(os.environ.get("RANK", "0"))
@@ -408,7 +459,13 @@ def main():
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-solvers", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--profile-case", choices=["merge", "rowtile", "ell", "sellp", "cg", "bicgstab",
+                                               "gmres"],
+                    help="run one small case for an ncu capture and exit")
+    ap.add_argument("--profile-dtype", default="f64", choices=["f64", "f32"])
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case(args.profile_case, args.profile_dtype)
     if args.impl == "reference":
         return run_reference(args)
 

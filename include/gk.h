@@ -60,7 +60,10 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2 } gk_dtype;
  * without defining them; these layouts are this library's definition. */
 typedef enum { GK_CSR = 0, GK_ELL = 1, GK_SELLP = 2 } gk_format;
 
-typedef enum { GK_CG = 0, GK_BICGSTAB = 1, GK_GMRES = 2 } gk_method;
+/* Krylov methods: CG (Hestenes-Stiefel), BiCGSTAB (van der Vorst), GMRES(m),
+ * and CGS (Sonneveld's conjugate gradient squared, the solver the paper
+ * benchmarks beside CG and GMRES in Section 5.2.1). */
+typedef enum { GK_CG = 0, GK_BICGSTAB = 1, GK_GMRES = 2, GK_CGS = 3 } gk_method;
 typedef enum { GK_PRECOND_NONE = 0, GK_PRECOND_JACOBI = 1 } gk_precond;
 typedef enum { GK_MEM_HOST = 0, GK_MEM_DEVICE = 1 } gk_memory;
 
@@ -68,6 +71,7 @@ typedef enum {
     GK_OK = 0,
     GK_NOT_CONVERGED = 1,  /* iteration cap reached; x holds the last iterate */
     GK_BREAKDOWN = 2,      /* CG: <p,Ap> <= 0; BiCGSTAB: rho, <rhat,v>, omega = 0;
+                              CGS: <rt,r> or <rt,A M^-1 p> = 0;
                               GMRES: zero Givens denominator */
     GK_ERR_INVALID = -1,   /* bad argument or malformed matrix */
     GK_ERR_OOM = -2,       /* device allocation failed */
@@ -212,7 +216,8 @@ typedef struct {
 
 /* Solve A x = b for square A (Listing 1: solver.apply(b, x) overwrites
  * the initial guess).  CG (Hestenes-Stiefel), BiCGSTAB (van der Vorst,
- * right-preconditioned) or GMRES(m) (right-preconditioned, Givens
+ * right-preconditioned), CGS (Sonneveld, M^-1 on the search directions,
+ * multi-kernel engine only) or GMRES(m) (right-preconditioned, Givens
  * rotations, residual estimate checked after every Arnoldi step as in
  * Section 5.2.1).  GK_OK is returned only when the recomputed true
  * residual meets tol; when the recurrence residual passes but the true

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libgk.so")
 
 GK_F64, GK_F32, GK_BF16 = 0, 1, 2
 GK_CSR, GK_ELL, GK_SELLP = 0, 1, 2
-GK_CG, GK_BICGSTAB, GK_GMRES = 0, 1, 2
+GK_CG, GK_BICGSTAB, GK_GMRES, GK_CGS = 0, 1, 2, 3
 GK_PRECOND_NONE, GK_PRECOND_JACOBI = 0, 1
 GK_MEM_HOST, GK_MEM_DEVICE = 0, 1
 GK_OK, GK_NOT_CONVERGED, GK_BREAKDOWN = 0, 1, 2
@@ -33,7 +33,7 @@ GK_ERR_ZERO_DIAG, GK_ERR_NAN, GK_ERR_UNSUPPORTED = -5, -6, -7
 
 DTYPES = {"f64": GK_F64, "f32": GK_F32, "bf16": GK_BF16}
 FORMATS = {"csr": GK_CSR, "ell": GK_ELL, "sellp": GK_SELLP}
-METHODS = {"cg": GK_CG, "bicgstab": GK_BICGSTAB, "gmres": GK_GMRES}
+METHODS = {"cg": GK_CG, "bicgstab": GK_BICGSTAB, "gmres": GK_GMRES, "cgs": GK_CGS}
 
 EXPORTED = [
     "gk_matrix_create_csr", "gk_matrix_create_coo", "gk_matrix_convert",

@@ -13,6 +13,36 @@ static bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// One merge-path instance (E path items per thread; block or warp units).
+template <int E, typename V, typename T>
+static gk_status launch_merge(gk_matrix A, const T* b, const EpiStore<T>& epi, int32_t* crow,
+                              T* cval, cudaStream_t s) {
+    if (A->plan.merge_warp) {
+        constexpr size_t smem = MergeWarpShape<E, V, T>::BYTES;
+        static bool attr = false;
+        if (!attr) {
+            GK_CUDA(cudaFuncSetAttribute(k_csr_merge_warp<E, V, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr = true;
+        }
+        const int64_t units = A->plan.merge_blocks;
+        k_csr_merge_warp<E, V, T><<<(unsigned)((units + 7) / 8), 256, smem, s>>>(
+            A->n, A->nnz, A->row_ptr, A->col, (const V*)A->val, b, epi, A->plan.block_row, units,
+            crow, cval);
+        return GK_OK;
+    }
+    constexpr size_t smem = merge_smem_bytes<E, V, T>();
+    static bool attr = false;
+    if (!attr) {
+        GK_CUDA(cudaFuncSetAttribute(k_csr_merge<E, V, T>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    k_csr_merge<E, V, T><<<(unsigned)A->plan.merge_blocks, 256, smem, s>>>(
+        A->n, A->nnz, A->row_ptr, A->col, (const V*)A->val, b, epi, A->plan.block_row, crow, cval);
+    return GK_OK;
+}
+
 template <typename V, typename T>
 static gk_status spmv_typed(gk_matrix A, double alpha, const void* b, double beta, void* x,
                             cudaStream_t s) {
@@ -20,22 +50,17 @@ static gk_status spmv_typed(gk_matrix A, double alpha, const void* b, double bet
     EpiStore<T> epi{static_cast<T*>(x), (T)alpha, (T)beta, mode};
     if (A->n == 0) return GK_OK;
     if (A->fmt == GK_CSR && A->plan.kind == 2) {
-        constexpr int E = MergeE<V>::value;
         const int64_t nb = A->plan.merge_blocks;
         GK_TRY(A->carry.ensure((size_t)nb * (sizeof(int32_t) + sizeof(T)) + 16));
         int32_t* crow = static_cast<int32_t*>(A->carry.ptr);
         T* cval = reinterpret_cast<T*>(static_cast<char*>(A->carry.ptr) +
                                        (((size_t)nb * sizeof(int32_t) + 15) & ~(size_t)15));
-        constexpr size_t smem = merge_smem_bytes<E, V, T>();
-        static bool attr = false;
-        if (!attr) {
-            GK_CUDA(cudaFuncSetAttribute(k_csr_merge<E, V, T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            attr = true;
+        const T* bt = static_cast<const T*>(b);
+        switch (A->plan.merge_e) {
+            case 4: GK_TRY((launch_merge<4, V, T>(A, bt, epi, crow, cval, s))); break;
+            case 6: GK_TRY((launch_merge<6, V, T>(A, bt, epi, crow, cval, s))); break;
+            default: GK_TRY((launch_merge<8, V, T>(A, bt, epi, crow, cval, s))); break;
         }
-        k_csr_merge<E, V, T><<<(unsigned)nb, 256, smem, s>>>(A->n, A->nnz, A->row_ptr, A->col,
-                                                             (const V*)A->val, (const T*)b, epi,
-                                                             A->plan.block_row, crow, cval);
         const unsigned fg = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, 4096));
         k_csr_merge_fixup<T><<<fg, 256, 0, s>>>((int32_t)nb, crow, cval, static_cast<T*>(x),
                                                 (T)alpha, mode);

@@ -561,8 +561,17 @@ gk_status build_csr_plan(gk_matrix A, cudaStream_t s) {
                                                        P.tile_desc);
         GK_CUDA(cudaGetLastError());
     } else if (kind == 2) {
-        const int E = 8;  // merge-path items per thread (MergeE)
-        const int64_t items = 256 * (int64_t)E;
+        // merge-path items per lane: 4 measured fastest on the Zipf power-law
+        // matrix in FP64 and FP32 (2, 3, 6, 8 were slower); GK_MERGE_E and
+        // GK_MERGE_UNIT=block (256*E items per block, a block-wide carry
+        // scan) select the other instances
+        int E = 4;
+        if (const char* e = getenv("GK_MERGE_E")) E = atoi(e);
+        if (E != 4 && E != 6 && E != 8) E = 4;
+        P.merge_warp = 1;
+        if (const char* w = getenv("GK_MERGE_UNIT")) P.merge_warp = strcmp(w, "block") != 0;
+        P.merge_e = E;
+        const int64_t items = (P.merge_warp ? 32 : 256) * (int64_t)E;
         const int64_t N = (int64_t)A->n + A->nnz;
         P.merge_blocks = (int32_t)std::max<int64_t>(1, (N + items - 1) / items);
         GK_CUDA(dmalloc_t(&P.block_row, (size_t)P.merge_blocks + 1));

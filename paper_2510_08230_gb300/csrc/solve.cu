@@ -38,6 +38,7 @@ struct KState {
     int32_t halt;      // 0 run; 1 recurrence passed (host checks true residual); 2 stop
     int32_t status;
     int32_t half;      // BiCGSTAB: stopped at the half step
+    int32_t fresh;     // CGS: the next step is the first after a (re)start
     int32_t restarts;
     // GMRES
     int32_t k, m, cycle_end, v0_pending;
@@ -111,16 +112,17 @@ struct EpiResid {
     unsigned* ticket;
     Fin fin;
     static constexpr int NA = 1;
+    using acc_t = T;  // per-thread partial sums in the vector type
     __device__ __forceinline__ bool skip() const {
         return halt && *reinterpret_cast<const volatile int32_t*>(halt) != 0;
     }
-    __device__ __forceinline__ void row(int64_t i, T s, double* acc) const {
+    __device__ __forceinline__ void row(int64_t i, T s, T* acc) const {
         T v = b[i] - s;
         r[i] = v;
-        acc[0] = fma((double)v, (double)v, acc[0]);
+        acc[0] = fmadd(v, v, acc[0]);
     }
-    __device__ __forceinline__ void finish(double* acc) const {
-        double a[1] = {acc[0]};
+    __device__ __forceinline__ void finish(T* acc) const {
+        double a[1] = {(double)acc[0]};
         grid_reduce_finish<1>(a, partials, ticket, fin);
     }
     __device__ __forceinline__ void timed_out() const {}
@@ -136,15 +138,16 @@ struct EpiDot {
     unsigned* ticket;
     Fin fin;
     static constexpr int NA = 1;
+    using acc_t = T;  // per-thread partial sums in the vector type
     __device__ __forceinline__ bool skip() const {
         return halt && *reinterpret_cast<const volatile int32_t*>(halt) != 0;
     }
-    __device__ __forceinline__ void row(int64_t i, T s, double* acc) const {
+    __device__ __forceinline__ void row(int64_t i, T s, T* acc) const {
         y[i] = s;
-        acc[0] = fma((double)w[i], (double)s, acc[0]);
+        acc[0] = fmadd(w[i], s, acc[0]);
     }
-    __device__ __forceinline__ void finish(double* acc) const {
-        double a[1] = {acc[0]};
+    __device__ __forceinline__ void finish(T* acc) const {
+        double a[1] = {(double)acc[0]};
         grid_reduce_finish<1>(a, partials, ticket, fin);
     }
     __device__ __forceinline__ void timed_out() const {}
@@ -160,16 +163,17 @@ struct EpiDot2 {
     unsigned* ticket;
     Fin fin;
     static constexpr int NA = 2;
+    using acc_t = T;
     __device__ __forceinline__ bool skip() const {
         return halt && *reinterpret_cast<const volatile int32_t*>(halt) != 0;
     }
-    __device__ __forceinline__ void row(int64_t i, T s, double* acc) const {
+    __device__ __forceinline__ void row(int64_t i, T s, T* acc) const {
         y[i] = s;
-        acc[0] = fma((double)s, (double)u[i], acc[0]);
-        acc[1] = fma((double)s, (double)s, acc[1]);
+        acc[0] = fmadd(s, u[i], acc[0]);
+        acc[1] = fmadd(s, s, acc[1]);
     }
-    __device__ __forceinline__ void finish(double* acc) const {
-        double a[2] = {acc[0], acc[1]};
+    __device__ __forceinline__ void finish(T* acc) const {
+        double a[2] = {(double)acc[0], (double)acc[1]};
         grid_reduce_finish<2>(a, partials, ticket, fin);
     }
     __device__ __forceinline__ void timed_out() const {}
@@ -181,11 +185,12 @@ struct EpiStoreHalt {
     T* __restrict__ y;
     const int32_t* halt;
     static constexpr int NA = 0;
+    using acc_t = T;
     __device__ __forceinline__ bool skip() const {
         return halt && *reinterpret_cast<const volatile int32_t*>(halt) != 0;
     }
-    __device__ __forceinline__ void row(int64_t i, T s, double*) const { y[i] = s; }
-    __device__ __forceinline__ void finish(double*) const {}
+    __device__ __forceinline__ void row(int64_t i, T s, T*) const { y[i] = s; }
+    __device__ __forceinline__ void finish(T*) const {}
     __device__ __forceinline__ void timed_out() const {}
 };
 
@@ -630,31 +635,273 @@ __global__ void EW_BOUNDS k_bi_init(int32_t n, const T* __restrict__ r, T* __res
     finish_ew<1>(a, partials, ticket, BiInitFin{st});
 }
 
-// ---------------------------------------------------------------- GMRES
-// V: n x (m+1), column j at V + j*ldv.  CGS2 orthogonalisation:
-//   h1 = V^T w ; w -= V h1 ; h2 = V^T w ; w -= V h2 ; h = h1 + h2.
+// ---------------------------------------------------------------- CGS
+// Sonneveld's conjugate gradient squared with M^-1 on the search
+// directions; shadow residual rt = r_0.  One iteration, four kernels:
+//   k_cgs_p : u = r + beta q ; p = u + beta (q + beta p) ; ph = M^-1 p
+//             (first step after a (re)start: u = p = r)
+//   SpMV    : vh = A ph ; <rt, vh> -> alpha = rho / <rt, vh>
+//   k_cgs_q : q = u - alpha vh ; uh = M^-1 (u + q) ; x += alpha uh
+//   SpMV    : r -= alpha A uh ; <rt, r>, ||r||^2 -> stopping test, beta, rho
 
-constexpr int MD_ROWS = 2048;   // rows per block in the multi-dot kernels
-constexpr int MD_THREADS = 256;
+// rt = r ; rho = <rt, r>
+struct CgsInitFin {
+    KState* st;
+    __device__ void operator()(double* t) const {
+        st->rho = t[0];
+        st->fresh = 1;
+        if (!isfinite(t[0])) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+        } else if (t[0] == 0.0) {
+            st->status = GK_BREAKDOWN;
+            st->halt = 2;
+        }
+    }
+};
 
-// Partial dot products of w with columns 0..k of V over a row chunk: one
-// warp per column (columns strided over warps), lanes over rows; w staged
-// in shared memory.  Writes partials[j * gridDim.x + blockIdx.x].
 template <typename T>
-__device__ void multidot_chunk(int32_t n, int64_t ldv, const T* __restrict__ V, const T* s_w,
-                               int64_t r0, int32_t rows, int32_t kk, double* partials) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = warp; j <= kk; j += nw) {
-        const T* col = V + (int64_t)j * ldv + r0;
-        T a = T(0);
-        for (int i = lane; i < rows; i += 32) a = fmadd(col[i], s_w[i], a);
-        double d = warp_sum((double)a);
-        if (lane == 0) partials[(size_t)j * gridDim.x + blockIdx.x] = d;
+__global__ void EW_BOUNDS k_cgs_init(int32_t n, const T* __restrict__ r, T* __restrict__ rt,
+                                     KState* st, double* partials, unsigned* ticket) {
+    constexpr int N = Pack<T>::N;
+    const bool vec = al16(r) && al16(rt);
+    T a[1] = {T(0)};
+    PACK_LOOP(j, n, T) {
+        const Pack<T> R = pld(r, j, n, vec);
+        pst(rt, j, n, vec, R);
+#pragma unroll
+        for (int c = 0; c < N; ++c) a[0] = fmadd(R.v[c], R.v[c], a[0]);  // padding adds 0
+    }
+    finish_ew<1>(a, partials, ticket, CgsInitFin{st});
+}
+
+template <typename T>
+__global__ void EW_BOUNDS k_cgs_p(int32_t n, T* __restrict__ u, T* __restrict__ p,
+                                  T* __restrict__ ph, const T* __restrict__ r,
+                                  const T* __restrict__ q, const T* __restrict__ dinv,
+                                  const KState* st) {
+    if (halted(st)) return;
+    constexpr int N = Pack<T>::N;
+    const bool first = st->fresh != 0;
+    const T beta = first ? T(0) : (T)st->beta;
+    const bool vec = al16(u) && al16(p) && al16(ph) && al16(r) && al16(q) && al16(dinv);
+    PACK_LOOP(j, n, T) {
+        Pack<T> U = pld(r, j, n, vec);
+        Pack<T> P{};
+        if (!first) {
+            const Pack<T> Q = pld(q, j, n, vec);
+            P = pld(p, j, n, vec);
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                U.v[c] = fmadd(beta, Q.v[c], U.v[c]);
+                P.v[c] = fmadd(beta, fmadd(beta, P.v[c], Q.v[c]), U.v[c]);
+            }
+        } else {
+            P = U;
+        }
+        pst(u, j, n, vec, U);
+        pst(p, j, n, vec, P);
+        if (dinv) {
+            Pack<T> D = pld(dinv, j, n, vec);
+#pragma unroll
+            for (int c = 0; c < N; ++c) D.v[c] = D.v[c] * P.v[c];
+            pst(ph, j, n, vec, D);
+        }
     }
 }
 
-// Last block: h[j] = sum over blocks of partials[j][*] for j <= kk.
-__device__ bool multidot_finish(int32_t kk, double* partials, unsigned* ticket, double* h) {
+// alpha = rho / <rt, vh>
+struct CgsAlphaFin {
+    KState* st;
+    __device__ void operator()(double* t) const {
+        const double sg = t[0];
+        st->fresh = 0;
+        if (!isfinite(sg)) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+        } else if (sg == 0.0) {
+            st->status = GK_BREAKDOWN;
+            st->halt = 2;
+        } else {
+            st->alpha = st->rho / sg;
+        }
+    }
+};
+
+template <typename T>
+__global__ void EW_BOUNDS k_cgs_q(int32_t n, T* __restrict__ q, T* __restrict__ uh,
+                                  T* __restrict__ x, const T* __restrict__ u,
+                                  const T* __restrict__ vh, const T* __restrict__ dinv,
+                                  const KState* st) {
+    if (halted(st)) return;
+    constexpr int N = Pack<T>::N;
+    const T alpha = (T)st->alpha;
+    const bool vec = al16(q) && al16(uh) && al16(x) && al16(u) && al16(vh) && al16(dinv);
+    PACK_LOOP(j, n, T) {
+        const Pack<T> U = pld(u, j, n, vec), VH = pld(vh, j, n, vec);
+        Pack<T> X = pld(x, j, n, vec);
+        Pack<T> Q, UH = dinv ? pld(dinv, j, n, vec) : Pack<T>{};
+#pragma unroll
+        for (int c = 0; c < N; ++c) {
+            Q.v[c] = fmadd(-alpha, VH.v[c], U.v[c]);
+            const T tc = U.v[c] + Q.v[c];
+            UH.v[c] = dinv ? UH.v[c] * tc : tc;
+            X.v[c] = fmadd(alpha, UH.v[c], X.v[c]);
+        }
+        pst(q, j, n, vec, Q);
+        pst(uh, j, n, vec, UH);
+        pst(x, j, n, vec, X);
+    }
+}
+
+// r -= alpha s (s = (A uh)_i) ; <rt, r>, <r, r>
+struct CgsRFin {
+    KState* st;
+    __device__ void operator()(double* t) const {
+        st->iter += 1;
+        const double rn = sqrt(t[1]);
+        st->rnorm = rn;
+        if (!isfinite(rn) || !isfinite(t[0])) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+            return;
+        }
+        if (rn <= st->thr) {
+            st->halt = 1;
+            return;
+        }
+        if (st->iter >= st->max_iters) {
+            st->status = GK_NOT_CONVERGED;
+            st->halt = 2;
+            return;
+        }
+        if (t[0] == 0.0) {
+            st->status = GK_BREAKDOWN;
+            st->halt = 2;
+            return;
+        }
+        st->beta = t[0] / st->rho;
+        st->rho = t[0];
+    }
+};
+
+template <typename T>
+struct EpiCgsR {
+    T* __restrict__ r;
+    const T* __restrict__ rt;
+    const KState* st;
+    double* partials;
+    unsigned* ticket;
+    static constexpr int NA = 2;
+    using acc_t = T;
+    __device__ __forceinline__ bool skip() const { return halted(st); }
+    __device__ __forceinline__ void row(int64_t i, T s, T* acc) const {
+        const T v = fmadd(-(T)st->alpha, s, r[i]);
+        r[i] = v;
+        acc[0] = fmadd(rt[i], v, acc[0]);
+        acc[1] = fmadd(v, v, acc[1]);
+    }
+    __device__ __forceinline__ void finish(T* acc) const {
+        double a[2] = {(double)acc[0], (double)acc[1]};
+        grid_reduce_finish<2>(a, partials, ticket, CgsRFin{const_cast<KState*>(st)});
+    }
+    __device__ __forceinline__ void timed_out() const {}
+};
+
+// ---------------------------------------------------------------- GMRES
+// V: n x (m+1), column j at V + j*ldv (ldv spans a multiple of 256 bytes).
+// CGS2 orthogonalisation, three passes over the basis per Arnoldi step:
+//   h1 = V^T w ;  w -= V h1, h2 = V^T w (one kernel: a block subtracts on its
+//   row chunk, then takes the dots from the chunk it just wrote) ;
+//   w -= V h2, ||w|| and the Givens step.
+// A pass over V is FP64-FMA-bound on this part (one FMA per 8 bytes), so the
+// kernels keep every lane busy and many independent loads in flight.
+
+constexpr int MD_ROWS = 2048;   // rows per block in the multi-dot kernels
+constexpr int MD_THREADS = 256;
+constexpr int MD_UNROLL = 4;    // independent pack loads per lane per step
+
+// Stages w's row chunk into shared memory, zero-padded to whole packs.
+template <typename T>
+__device__ __forceinline__ void stage_chunk(const T* __restrict__ w, int64_t r0, int32_t rows,
+                                            T* s_w) {
+    constexpr int N = Pack<T>::N;
+    const int32_t padded = (rows + N - 1) / N * N;
+    for (int i = threadIdx.x; i < padded; i += blockDim.x) s_w[i] = i < rows ? w[r0 + i] : T(0);
+}
+
+// Dot products of the staged chunk s_w with columns 0..kk of V, added to
+// the block's running column sums s_colsum.  Work items are (column, row
+// segment): with few columns a column is split into segments so that all 8
+// warps work; a warp's lanes step over 16-byte packs of the segment,
+// MD_UNROLL independent loads at a time.  Segment sums are added per column
+// in segment order.
+template <typename T>
+__device__ void multidot_chunk(int64_t ldv, const T* __restrict__ V, const T* s_w, int64_t r0,
+                               int32_t rows, int32_t kk, bool vec, double* s_colsum) {
+    constexpr int N = Pack<T>::N;
+    __shared__ double s_part[(MAXM + 1) * 8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int np = (rows + N - 1) / N;
+    const int ncol = kk + 1;
+    int S = 1;  // segments per column (power of two, ncol * S >= nw when possible)
+    while (S < 8 && ncol * S * 2 <= nw) S *= 2;
+    const int seg = (np + S - 1) / S;
+    for (int it = warp; it < ncol * S; it += nw) {
+        const int j = it / S, sgi = it - j * S;
+        const T* col = V + (int64_t)j * ldv + r0;
+        const int p0 = sgi * seg, p1 = min(np, p0 + seg);
+        T acc[MD_UNROLL][N];
+#pragma unroll
+        for (int u = 0; u < MD_UNROLL; ++u)
+#pragma unroll
+            for (int c = 0; c < N; ++c) acc[u][c] = T(0);
+        for (int pb = p0 + lane; pb < p1; pb += 32 * MD_UNROLL) {
+            Pack<T> cp[MD_UNROLL], wp[MD_UNROLL];
+#pragma unroll
+            for (int u = 0; u < MD_UNROLL; ++u) {
+                const int p = pb + 32 * u;
+                if (p < p1) {
+                    cp[u] = pld(col, p, rows, vec);
+                    wp[u] = *reinterpret_cast<const Pack<T>*>(s_w + p * N);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < N; ++c) cp[u].v[c] = wp[u].v[c] = T(0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < MD_UNROLL; ++u)
+#pragma unroll
+                for (int c = 0; c < N; ++c) acc[u][c] = fmadd(cp[u].v[c], wp[u].v[c], acc[u][c]);
+        }
+        T a = T(0);
+#pragma unroll
+        for (int u = 0; u < MD_UNROLL; ++u)
+#pragma unroll
+            for (int c = 0; c < N; ++c) a += acc[u][c];
+        const double d = warp_sum((double)a);
+        if (lane == 0) s_part[it] = d;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
+        double t = s_colsum[j];
+        for (int q = 0; q < S; ++q) t += s_part[j * S + q];
+        s_colsum[j] = t;
+    }
+    __syncthreads();
+}
+
+// Rows of this block: an equal share of whole 8-row groups, so that every
+// block of a one-wave grid does the same work; processed in chunks of at
+// most MD_ROWS rows.
+__device__ __forceinline__ void md_block_rows(int32_t n, int64_t& beg, int64_t& end) {
+    const int64_t R = (((int64_t)n + gridDim.x - 1) / gridDim.x + 7) / 8 * 8;
+    beg = min((int64_t)n, (int64_t)blockIdx.x * R);
+    end = min((int64_t)n, beg + R);
+}
+
+// Last block: h[j] = sum over blocks of partials[j][*] for j < ncol.
+__device__ bool multidot_finish(int32_t ncol, double* partials, unsigned* ticket, double* h) {
     __shared__ bool am_last;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -665,7 +912,7 @@ __device__ bool multidot_finish(int32_t kk, double* partials, unsigned* ticket, 
     if (!am_last) return false;
     __threadfence();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = warp; j <= kk; j += nw) {
+    for (int j = warp; j < ncol; j += nw) {
         double s = 0.0;
         for (unsigned b = lane; b < gridDim.x; b += 32) s += __ldcg(partials + (size_t)j * gridDim.x + b);
         s = warp_sum(s);
@@ -675,44 +922,103 @@ __device__ bool multidot_finish(int32_t kk, double* partials, unsigned* ticket, 
     return true;
 }
 
+// w -= V h on a row chunk (h negated in s_nh), thread per 16-byte pack of
+// rows, the chunk's packs of a thread (MD_ROWS / 256 / N of them) updated
+// together so their loads of each column are in flight at once.  Returns
+// the thread's sum of squares of the new w when want_norm.
+template <typename T>
+__device__ __forceinline__ T subtract_chunk(const T* __restrict__ V, int64_t ldv, T* __restrict__ wc,
+                                            int64_t r0, int32_t rows, int32_t kk, const T* s_nh,
+                                            bool vec, T* s_w) {
+    constexpr int N = Pack<T>::N;
+    constexpr int PP = MD_ROWS / MD_THREADS / N;  // packs per thread
+    const int np = (rows + N - 1) / N;
+    Pack<T> W[PP];
+#pragma unroll
+    for (int q = 0; q < PP; ++q) {
+        const int p = threadIdx.x + q * MD_THREADS;
+        if (p < np) W[q] = pld(wc, p, rows, vec);
+    }
+    for (int j = 0; j <= kk; ++j) {
+        const T* col = V + (int64_t)j * ldv + r0;
+        const T hj = s_nh[j];
+#pragma unroll
+        for (int q = 0; q < PP; ++q) {
+            const int p = threadIdx.x + q * MD_THREADS;
+            if (p < np) {
+                const Pack<T> Vj = pld(col, p, rows, vec);
+#pragma unroll
+                for (int c = 0; c < N; ++c) W[q].v[c] = fmadd(hj, Vj.v[c], W[q].v[c]);
+            }
+        }
+    }
+    T a = T(0);
+#pragma unroll
+    for (int q = 0; q < PP; ++q) {
+        const int p = threadIdx.x + q * MD_THREADS;
+        if (p < np) {
+            pst(wc, p, rows, vec, W[q]);
+            if (s_w) *reinterpret_cast<Pack<T>*>(s_w + p * N) = W[q];
+#pragma unroll
+            for (int c = 0; c < N; ++c) a = fmadd(W[q].v[c], W[q].v[c], a);  // padding adds 0
+        }
+    }
+    return a;
+}
+
 // h1 = V^T w  (columns 0..k)
 template <typename T>
-__global__ void __launch_bounds__(MD_THREADS)
+__global__ void __launch_bounds__(MD_THREADS, 4)
 k_gm_dot1(int32_t n, int64_t ldv, const T* __restrict__ V, const T* __restrict__ w, KState* st,
           double* partials, unsigned* ticket) {
     if (halted(st)) return;
-    __shared__ T s_w[MD_ROWS];
+    __shared__ __align__(16) T s_w[MD_ROWS];
+    __shared__ double s_colsum[MAXM + 1];
     const int32_t kk = st->k;
-    const int64_t r0 = (int64_t)blockIdx.x * MD_ROWS;
-    const int32_t rows = (int32_t)(n - r0 < MD_ROWS ? n - r0 : MD_ROWS);
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) s_w[i] = w[r0 + i];
+    for (int j = threadIdx.x; j <= kk; j += blockDim.x) s_colsum[j] = 0.0;
+    int64_t beg, end;
+    md_block_rows(n, beg, end);
+    for (int64_t r0 = beg; r0 < end; r0 += MD_ROWS) {
+        const int32_t rows = (int32_t)min((int64_t)MD_ROWS, end - r0);
+        __syncthreads();
+        stage_chunk(w, r0, rows, s_w);
+        __syncthreads();
+        multidot_chunk(ldv, V, s_w, r0, rows, kk, al16(V), s_colsum);
+    }
     __syncthreads();
-    multidot_chunk(n, ldv, V, s_w, r0, rows, kk, partials);
-    if (multidot_finish(kk, partials, ticket, st->h1) && threadIdx.x == 0) *ticket = 0u;
+    for (int j = threadIdx.x; j <= kk; j += blockDim.x)
+        partials[(size_t)j * gridDim.x + blockIdx.x] = s_colsum[j];
+    if (multidot_finish(kk + 1, partials, ticket, st->h1) && threadIdx.x == 0) *ticket = 0u;
 }
 
 // w -= V h1 ; h2 = V^T w
 template <typename T>
-__global__ void __launch_bounds__(MD_THREADS)
+__global__ void __launch_bounds__(MD_THREADS, 4)
 k_gm_dot2(int32_t n, int64_t ldv, const T* __restrict__ V, T* __restrict__ w, KState* st,
           double* partials, unsigned* ticket) {
     if (halted(st)) return;
-    __shared__ T s_w[MD_ROWS];
-    __shared__ T s_h[MAXM + 1];
+    __shared__ __align__(16) T s_w[MD_ROWS];  // the updated chunk (padding lanes stay 0)
+    __shared__ T s_nh[MAXM + 1];
+    __shared__ double s_colsum[MAXM + 1];
     const int32_t kk = st->k;
-    for (int j = threadIdx.x; j <= kk; j += blockDim.x) s_h[j] = (T)st->h1[j];
-    __syncthreads();
-    const int64_t r0 = (int64_t)blockIdx.x * MD_ROWS;
-    const int32_t rows = (int32_t)(n - r0 < MD_ROWS ? n - r0 : MD_ROWS);
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-        T v = w[r0 + i];
-        for (int j = 0; j <= kk; ++j) v = fmadd(-s_h[j], V[(int64_t)j * ldv + r0 + i], v);
-        w[r0 + i] = v;
-        s_w[i] = v;
+    for (int j = threadIdx.x; j <= kk; j += blockDim.x) {
+        s_nh[j] = -(T)st->h1[j];
+        s_colsum[j] = 0.0;
+    }
+    const bool vec = al16(V) && al16(w);
+    int64_t beg, end;
+    md_block_rows(n, beg, end);
+    for (int64_t r0 = beg; r0 < end; r0 += MD_ROWS) {
+        const int32_t rows = (int32_t)min((int64_t)MD_ROWS, end - r0);
+        __syncthreads();
+        subtract_chunk(V, ldv, w + r0, r0, rows, kk, s_nh, vec, s_w);
+        __syncthreads();
+        multidot_chunk(ldv, V, s_w, r0, rows, kk, vec, s_colsum);
     }
     __syncthreads();
-    multidot_chunk(n, ldv, V, s_w, r0, rows, kk, partials);
-    if (multidot_finish(kk, partials, ticket, st->h2) && threadIdx.x == 0) *ticket = 0u;
+    for (int j = threadIdx.x; j <= kk; j += blockDim.x)
+        partials[(size_t)j * gridDim.x + blockIdx.x] = s_colsum[j];
+    if (multidot_finish(kk + 1, partials, ticket, st->h2) && threadIdx.x == 0) *ticket = 0u;
 }
 
 // Givens step on column k, residual estimate, cycle decision and, at the
@@ -779,18 +1085,17 @@ __global__ void __launch_bounds__(MD_THREADS)
 k_gm_orth(int32_t n, int64_t ldv, const T* __restrict__ V, T* __restrict__ w, KState* st,
           double* partials, unsigned* ticket) {
     if (halted(st)) return;
-    __shared__ T s_h[MAXM + 1];
+    __shared__ T s_nh[MAXM + 1];
     const int32_t kk = st->k;
-    for (int j = threadIdx.x; j <= kk; j += blockDim.x) s_h[j] = (T)st->h2[j];
+    for (int j = threadIdx.x; j <= kk; j += blockDim.x) s_nh[j] = -(T)st->h2[j];
     __syncthreads();
-    const int64_t r0 = (int64_t)blockIdx.x * MD_ROWS;
-    const int32_t rows = (int32_t)(n - r0 < MD_ROWS ? n - r0 : MD_ROWS);
+    const bool vec = al16(V) && al16(w);
+    int64_t beg, end;
+    md_block_rows(n, beg, end);
     T a[1] = {T(0)};
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-        T v = w[r0 + i];
-        for (int j = 0; j <= kk; ++j) v = fmadd(-s_h[j], V[(int64_t)j * ldv + r0 + i], v);
-        w[r0 + i] = v;
-        a[0] = fmadd(v, v, a[0]);
+    for (int64_t r0 = beg; r0 < end; r0 += MD_ROWS) {
+        const int32_t rows = (int32_t)min((int64_t)MD_ROWS, end - r0);
+        a[0] += subtract_chunk(V, ldv, w + r0, r0, rows, kk, s_nh, vec, (T*)nullptr);
     }
     finish_ew<1>(a, partials, ticket, GmGivensFin{st});
 }
@@ -889,16 +1194,17 @@ struct EpiGmResid {
     unsigned* ticket;
     GmRestartFin fin;
     static constexpr int NA = 1;
+    using acc_t = T;  // per-thread partial sums in the vector type
     __device__ __forceinline__ bool skip() const {
         return halted(st) || !*reinterpret_cast<const volatile int32_t*>(&st->cycle_end);
     }
-    __device__ __forceinline__ void row(int64_t i, T s, double* acc) const {
+    __device__ __forceinline__ void row(int64_t i, T s, T* acc) const {
         const T v = b[i] - s;
         r[i] = v;
-        acc[0] = fma((double)v, (double)v, acc[0]);
+        acc[0] = fmadd(v, v, acc[0]);
     }
-    __device__ __forceinline__ void finish(double* acc) const {
-        double a[1] = {acc[0]};
+    __device__ __forceinline__ void finish(T* acc) const {
+        double a[1] = {(double)acc[0]};
         grid_reduce_finish<1>(a, partials, ticket, fin);
     }
     __device__ __forceinline__ void timed_out() const {}
@@ -1006,16 +1312,17 @@ struct EpiBiT {
     unsigned* ticket;
     BiOmegaFin fin;
     static constexpr int NA = 2;
+    using acc_t = T;
     __device__ __forceinline__ bool skip() const {
         return halted(st) || *reinterpret_cast<const volatile int32_t*>(&st->half) != 0;
     }
-    __device__ __forceinline__ void row(int64_t i, T s, double* acc) const {
+    __device__ __forceinline__ void row(int64_t i, T s, T* acc) const {
         y[i] = s;
-        acc[0] = fma((double)s, (double)u[i], acc[0]);
-        acc[1] = fma((double)s, (double)s, acc[1]);
+        acc[0] = fmadd(s, u[i], acc[0]);
+        acc[1] = fmadd(s, s, acc[1]);
     }
-    __device__ __forceinline__ void finish(double* acc) const {
-        double a[2] = {acc[0], acc[1]};
+    __device__ __forceinline__ void finish(T* acc) const {
+        double a[2] = {(double)acc[0], (double)acc[1]};
         grid_reduce_finish<2>(a, partials, ticket, fin);
     }
     __device__ __forceinline__ void timed_out() const {}
@@ -1281,9 +1588,17 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
         GK_TRY(ensure_jacobi(A, s));
         dinv = (const T*)A->dinv;
     }
-    const int nvec = method == GK_CG ? 5 : method == GK_BICGSTAB ? 9 : m + 4;
+    const int nvec = method == GK_CG ? 5 : (method == GK_BICGSTAB || method == GK_CGS) ? 9 : m + 4;
     GK_TRY(ensure_vecs<T>(C, n, nvec));
-    const unsigned md_grid = (unsigned)std::max<int64_t>(1, ((int64_t)n + MD_ROWS - 1) / MD_ROWS);
+    // multi-dot kernels: one wave of resident blocks sharing the rows equally
+    const int64_t md_need = std::max<int64_t>(1, ((int64_t)n + MD_ROWS - 1) / MD_ROWS);
+    auto md_grid_of = [&](auto kern) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, MD_THREADS, 0) != cudaSuccess || b < 1)
+            b = 1;
+        return (unsigned)std::min<int64_t>(md_need, (int64_t)num_sms() * std::min(b, 8));
+    };
+    const unsigned md_grid = (unsigned)std::min<int64_t>(md_need, (int64_t)num_sms() * 8);
     const size_t pcount = (size_t)std::max<unsigned>(num_sms() * 8, md_grid) * (size_t)(MAXM + 2);
     GK_TRY(C->partials.ensure(pcount * sizeof(double)));
     double* part = (double*)C->partials.ptr;
@@ -1317,9 +1632,12 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
             GK_TRY(capture_chunk(A, C, chunk, [&](cudaStream_t cs) -> gk_status {
                 EpiStoreHalt<T> e1{w, halt};
                 GK_TRY((launch_spmv_rows<V, T>(A, z, e1, cs)));
-                k_gm_dot1<T><<<md_grid, MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st, part, tk);
-                k_gm_dot2<T><<<md_grid, MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st, part, tk);
-                k_gm_orth<T><<<md_grid, MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st, part, tk);
+                k_gm_dot1<T><<<md_grid_of(k_gm_dot1<T>), MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st,
+                                                                               part, tk);
+                k_gm_dot2<T><<<md_grid_of(k_gm_dot2<T>), MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st,
+                                                                               part, tk);
+                k_gm_orth<T><<<md_grid_of(k_gm_orth<T>), MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st,
+                                                                               part, tk);
                 k_gm_next<T><<<ewg(k_gm_next<T>, n), 256, 0, cs>>>(n, ldv, Vm, w, z, x, dinv, st);
                 EpiGmResid<T> e2{r, b, st, part, tk, GmRestartFin{st}};
                 GK_TRY((launch_spmv_rows<V, T>(A, x, e2, cs)));
@@ -1346,6 +1664,10 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
             if (method == GK_CG)  // slots: 0 r, 1 tmp, 2 q, 3 p, 4 z
                 k_cg_init<T><<<ewg(k_cg_init<T>, n), 256, 0, s>>>(n, r, vec_at<T>(C, n, 4), vec_at<T>(C, n, 3), dinv,
                                                 st, part, tk);
+            else if (method == GK_CGS)
+                // slots: 0 r, 1 tmp, 2 rt, 3 u, 4 p, 5 q, 6 ph, 7 vh, 8 uh
+                k_cgs_init<T><<<ewg(k_cgs_init<T>, n), 256, 0, s>>>(n, r, vec_at<T>(C, n, 2), st,
+                                                                    part, tk);
             else
                 // slots: 0 r, 1 tmp, 2 rhat, 3 p, 4 phat, 5 s, 6 v, 7 shat, 8 t
                 k_bi_init<T><<<ewg(k_bi_init<T>, n), 256, 0, s>>>(n, r, vec_at<T>(C, n, 2), vec_at<T>(C, n, 3),
@@ -1365,6 +1687,17 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
                     GK_TRY((launch_spmv_rows<V, T>(A, p, e1, cs)));
                     k_cg_update<T><<<ewg(k_cg_update<T>, n), 256, 0, cs>>>(n, x, r, z, p, q, dinv, st, part, tk);
                     k_cg_p<T><<<ewg(k_cg_p<T>, n), 256, 0, cs>>>(n, p, z, st);
+                } else if (method == GK_CGS) {
+                    T *rt = vec_at<T>(C, n, 2), *u = vec_at<T>(C, n, 3), *p = vec_at<T>(C, n, 4);
+                    T *q = vec_at<T>(C, n, 5), *ph = vec_at<T>(C, n, 6), *vh = vec_at<T>(C, n, 7);
+                    T* uh = vec_at<T>(C, n, 8);
+                    const T* phs = prec ? ph : p;
+                    k_cgs_p<T><<<ewg(k_cgs_p<T>, n), 256, 0, cs>>>(n, u, p, ph, r, q, dinv, st);
+                    EpiDot<T, CgsAlphaFin> e1{vh, rt, halt, part, tk, CgsAlphaFin{st}};
+                    GK_TRY((launch_spmv_rows<V, T>(A, phs, e1, cs)));
+                    k_cgs_q<T><<<ewg(k_cgs_q<T>, n), 256, 0, cs>>>(n, q, uh, x, u, vh, dinv, st);
+                    EpiCgsR<T> e2{r, rt, st, part, tk};
+                    GK_TRY((launch_spmv_rows<V, T>(A, uh, e2, cs)));
                 } else {
                     T *rh = vec_at<T>(C, n, 2), *p = vec_at<T>(C, n, 3), *ph = vec_at<T>(C, n, 4);
                     T *v = vec_at<T>(C, n, 6), *sv = vec_at<T>(C, n, 5), *sh = vec_at<T>(C, n, 7);
@@ -1454,7 +1787,9 @@ namespace gk {
 
 static gk_status check_opts(gk_matrix A, const gk_solve_opts* o) {
     if (!o) return GK_ERR_INVALID;
-    if (o->method != GK_CG && o->method != GK_BICGSTAB && o->method != GK_GMRES) return GK_ERR_INVALID;
+    if (o->method != GK_CG && o->method != GK_BICGSTAB && o->method != GK_GMRES &&
+        o->method != GK_CGS)
+        return GK_ERR_INVALID;
     if (o->precond != GK_PRECOND_NONE && o->precond != GK_PRECOND_JACOBI) return GK_ERR_INVALID;
     if (!(o->tol >= 0.0) || o->max_iters < 0) return GK_ERR_INVALID;
     if (o->krylov_dim < 0 || o->krylov_dim > MAXM) return GK_ERR_INVALID;

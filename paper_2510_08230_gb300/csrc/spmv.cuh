@@ -6,7 +6,9 @@
 // s_i = sum_j a_ij b_j and passes (i, s_i) to an epilogue, which writes the
 // output and may accumulate per-thread partial dot products; the kernel's
 // last act is epi.finish(acc), which reduces those partials across the grid
-// deterministically (fixed order, last block finishes).
+// deterministically (fixed order, last block finishes).  A thread keeps its
+// partials in the vector type (FP32 in FP32 solves, so no FP64 instruction
+// sits on their per-row path) and the grid reduction adds them in FP64.
 //
 // FP64 note for GB300: the FP64 pipe retires about 2 lane-FMAs per SM cycle
 // (a warp instruction occupies it ~16 SM cycles whatever its active mask),
@@ -32,19 +34,20 @@ struct EpiStore {
     T alpha, beta;
     int mode;
     static constexpr int NA = 0;
+    using acc_t = T;
     __device__ __forceinline__ bool skip() const { return false; }
-    __device__ __forceinline__ void row(int64_t i, T s, double*) const {
+    __device__ __forceinline__ void row(int64_t i, T s, T*) const {
         if (mode == 0) y[i] = s;
         else if (mode == 1) y[i] = alpha * s;
         else y[i] = fmadd(beta, y[i], alpha * s);
     }
-    __device__ __forceinline__ void finish(double*) const {}
+    __device__ __forceinline__ void finish(T*) const {}
     __device__ __forceinline__ void timed_out() const {}
 };
 
 template <class Epi>
 struct AccArr {
-    double v[Epi::NA > 0 ? Epi::NA : 1];
+    typename Epi::acc_t v[Epi::NA > 0 ? Epi::NA : 1];
 };
 
 constexpr int GATHER = 8;  // loads issued ahead of the FMAs that use them
@@ -270,12 +273,13 @@ k_csr_merge(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
     const int32_t nloc = min(i1 - i0 + 1, n - i0);  // staged row ends
     const int32_t cnt = (int32_t)(j1 - j0);
     for (int k = threadIdx.x; k < nloc; k += blockDim.x) s_rowend[k] = __ldg(rp + i0 + k + 1);
-    for (int k0 = threadIdx.x; k0 < cnt; k0 += GATHER * blockDim.x) {
-        int32_t c[GATHER];
-        V v[GATHER];
-        T xv[GATHER];
+    constexpr int G = E < GATHER ? E : GATHER;  // loads in flight per thread
+    for (int k0 = threadIdx.x; k0 < cnt; k0 += G * blockDim.x) {
+        int32_t c[G];
+        V v[G];
+        T xv[G];
 #pragma unroll
-        for (int u = 0; u < GATHER; ++u) {
+        for (int u = 0; u < G; ++u) {
             const int k = k0 + u * (int)blockDim.x;
             if (k < cnt) {
                 c[u] = __ldcs(ci + j0 + k);
@@ -283,12 +287,12 @@ k_csr_merge(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
             }
         }
 #pragma unroll
-        for (int u = 0; u < GATHER; ++u) {
+        for (int u = 0; u < G; ++u) {
             const int k = k0 + u * (int)blockDim.x;
             if (k < cnt) xv[u] = __ldg(x + c[u]);
         }
 #pragma unroll
-        for (int u = 0; u < GATHER; ++u) {
+        for (int u = 0; u < G; ++u) {
             const int k = k0 + u * (int)blockDim.x;
             if (k < cnt) {
                 s_val[mpad(k)] = v[u];
@@ -356,6 +360,154 @@ k_csr_merge(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
     if (valid && (threadIdx.x == blockDim.x - 1 || s_trow[threadIdx.x + 1] == INT32_MAX)) {
         carry_row[blockIdx.x] = (i < n) ? i : -1;
         carry_val[blockIdx.x] = sc;
+    }
+}
+
+// Shared-memory layout of the warp-level merge kernel, per warp (8 warps a
+// block): values, gathered x, row ends; every array on a 16-byte boundary.
+template <int E, typename V, typename T>
+struct MergeWarpShape {
+    static constexpr int WI = 32 * E;             // path items per warp
+    static constexpr int PADN = WI + WI / 8 + 8;  // padded entries
+    static constexpr size_t OFF_XV = align16((size_t)PADN * sizeof(V));
+    static constexpr size_t OFF_RE = align16(OFF_XV + (size_t)PADN * sizeof(T));
+    static constexpr size_t WARP_BYTES = align16(OFF_RE + (size_t)(WI + 1) * 4);
+    static constexpr size_t BYTES = 8 * WARP_BYTES;
+};
+
+// CSR merge-path kernel at warp granularity (apply only).  The path of n
+// row ends and nnz nonzeros is cut into units of 32*E items, one unit per
+// warp and E items per lane; the 8 warps of a block share nothing but the
+// block's shared memory, so the kernel has no block barrier and a warp
+// never waits for another.  A warp stages its row ends, values and the
+// gathered x values (E independent gathers per lane in flight), each lane
+// walks its piece (one FMA per nonzero), and the carries of lanes whose
+// pieces end inside a row are combined with a 5-level segmented shuffle
+// scan (a level's add runs only in warps where some run is that long).  The
+// row open at the end of a unit goes to k_csr_merge_fixup as (carry_row,
+// carry_val).  unit_row (nunits + 1 entries) gives each unit's first row;
+// when null the warp finds it by binary search.
+template <int E, typename V, typename T>
+__global__ void __launch_bounds__(256)
+k_csr_merge_warp(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
+                 const int32_t* __restrict__ ci, const V* __restrict__ va,
+                 const T* __restrict__ x, EpiStore<T> epi, const int32_t* __restrict__ unit_row,
+                 int64_t nunits, int32_t* __restrict__ carry_row, T* __restrict__ carry_val) {
+    using Sh = MergeWarpShape<E, V, T>;
+    constexpr int WI = Sh::WI;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t u = (int64_t)blockIdx.x * 8 + warp;
+    if (u >= nunits) return;  // the whole warp; no block barrier follows
+    unsigned char* base = smem + (size_t)warp * Sh::WARP_BYTES;
+    V* s_val = reinterpret_cast<V*>(base);
+    T* s_xv = reinterpret_cast<T*>(base + Sh::OFF_XV);
+    int32_t* s_rowend = reinterpret_cast<int32_t*>(base + Sh::OFF_RE);
+    const int64_t N = (int64_t)n + nnz;
+    const int64_t d0 = u * WI;
+    const int64_t d1 = min(d0 + WI, N);
+    int32_t bnd = 0;
+    if (unit_row) {
+        if (lane < 2) bnd = __ldg(unit_row + u + lane);
+    } else if (lane < 2) {
+        const int64_t d = lane == 0 ? d0 : d1;
+        int32_t lo = 0, hi = n;  // rows whose end item lies before d
+        while (lo < hi) {
+            const int32_t mid = lo + ((hi - lo) >> 1);
+            if ((int64_t)__ldg(rp + mid + 1) + mid + 1 > d) hi = mid;
+            else lo = mid + 1;
+        }
+        bnd = lo;
+    }
+    const int32_t i0 = __shfl_sync(FULL, bnd, 0), i1 = __shfl_sync(FULL, bnd, 1);
+    const int64_t j0 = d0 - i0, j1 = d1 - i1;
+    const int32_t nloc = min(i1 - i0 + 1, n - i0);  // staged row ends
+    const int32_t cnt = (int32_t)(j1 - j0);
+    for (int k = lane; k < nloc; k += 32) s_rowend[k] = __ldg(rp + i0 + k + 1);
+    {
+        int32_t c[E];
+        V v[E];
+        T xv[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int k = lane + 32 * q;
+            if (k < cnt) {
+                c[q] = __ldcs(ci + j0 + k);
+                v[q] = va[j0 + k];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int k = lane + 32 * q;
+            if (k < cnt) xv[q] = __ldg(x + c[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int k = lane + 32 * q;
+            if (k < cnt) {
+                s_val[mpad(k)] = v[q];
+                s_xv[mpad(k)] = xv[q];
+            }
+        }
+    }
+    __syncwarp();
+    // this lane's start on the path
+    const int64_t dt = min(d0 + (int64_t)lane * E, d1);
+    int32_t lo = 0, hi = max(0, nloc);
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if ((int64_t)s_rowend[mid] + i0 + mid + 1 > dt) hi = mid;
+        else lo = mid + 1;
+    }
+    int32_t i = i0 + lo;
+    int64_t j = dt - i;
+    const int64_t dend = min(dt + E, d1);
+    T acc = T(0);
+    int32_t head_row = -1;
+    T head_val = T(0);
+    int64_t rend = (i < n) ? (int64_t)s_rowend[i - i0] : 0;
+    for (int64_t d = dt; d < dend; ++d) {
+        if (i < n && j < rend) {
+            const int k = mpad((int)(j - j0));
+            acc = fmadd(cvt<T>(s_val[k]), s_xv[k], acc);
+            ++j;
+        } else {
+            if (head_row < 0) {
+                head_row = i;
+                head_val = acc;
+            } else {
+                epi.row(i, acc, nullptr);
+            }
+            acc = T(0);
+            ++i;
+            rend = (i < n && i - i0 < nloc) ? (int64_t)s_rowend[i - i0] : 0;
+        }
+    }
+    // Carries: lane l ends its piece inside row myrow with partial sum acc;
+    // rows are non-decreasing over the valid lanes, so a segmented inclusive
+    // scan (fixed order) gives each lane the sum over its run of lanes.
+    const bool valid = dt < d1;
+    const int32_t myrow = valid ? i : INT32_MAX;
+    T sc = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t orow = __shfl_up_sync(FULL, myrow, o);
+        const T osc = __shfl_up_sync(FULL, sc, o);
+        if (lane >= o && orow == myrow) sc = osc + sc;
+    }
+    const int32_t prow = __shfl_up_sync(FULL, myrow, 1);
+    const T psc = __shfl_up_sync(FULL, sc, 1);
+    const int32_t nrow = __shfl_down_sync(FULL, myrow, 1);
+    if (head_row >= 0) {
+        T vv = head_val;
+        if (lane > 0 && prow == head_row) vv = psc + vv;
+        epi.row(head_row, vv, nullptr);
+    }
+    // the row open at the end of the unit: carried by the last valid lane
+    if (valid && (lane == 31 || nrow == INT32_MAX)) {
+        carry_row[u] = (i < n) ? i : -1;
+        carry_val[u] = sc;
     }
 }
 

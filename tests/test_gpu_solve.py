@@ -15,7 +15,7 @@ from gpu_util import ensure_built, torch_dev
 
 pytestmark = pytest.mark.gpu
 
-METHOD = {"cg": oracle.CG, "bicgstab": oracle.BICGSTAB, "gmres": oracle.GMRES}
+METHOD = {"cg": oracle.CG, "bicgstab": oracle.BICGSTAB, "gmres": oracle.GMRES, "cgs": oracle.CGS}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -124,6 +124,31 @@ def test_bicgstab(case, precond):
     _check(m, b, "bicgstab", precond, 1e-10, iters_gate=False)
 
 
+@pytest.mark.parametrize("case", ["lap2d_64", "diff3d_12", "convdiff_300", "banded_2000"])
+@pytest.mark.parametrize("precond", [False, True])
+def test_cgs(case, precond):
+    """CGS squares the BiCG residual polynomial, so rounding differences grow
+    faster than in CG: the residual is gated, the iteration count only
+    loosely (within 1.5x + 10 of the oracle's)."""
+    m, b = CASES[case]()
+    x, info, xo, io = _check(m, b, "cgs", precond, 1e-10, iters_gate=False)
+    assert info["iters"] <= 1.5 * io["iters"] + 10, (info, io)
+
+
+def test_cgs_rejected_by_single_block_and_batched_engines():
+    m, b = CASES["lap2d_64"]()
+    _, info = _gpu_solve(m, b, "cgs", 0, 1e-10, engine=2)
+    assert info["return"] == gk.GK_ERR_UNSUPPORTED
+    import torch
+    dev = torch_dev()
+    A = gk.Matrix.from_csr(m)
+    bt = torch.from_numpy(b).to(dev)
+    xt = torch.zeros_like(bt)
+    st, _ = gk.gk_solve_batched([A.handle], [bt], [xt], gk.make_opts(method="cgs", tol=1e-10))
+    assert st == gk.GK_ERR_UNSUPPORTED
+    A.close()
+
+
 @pytest.mark.parametrize("case", ["lap2d_64", "diff3d_12", "convdiff_300"])
 @pytest.mark.parametrize("precond", [False, True])
 def test_gmres(case, precond):
@@ -132,10 +157,10 @@ def test_gmres(case, precond):
 
 
 @pytest.mark.parametrize("fmt", ["ell", "sellp"])
-@pytest.mark.parametrize("method", ["cg", "bicgstab", "gmres"])
+@pytest.mark.parametrize("method", ["cg", "bicgstab", "gmres", "cgs"])
 def test_solvers_on_padded_formats(fmt, method):
     m, b = CASES["diff3d_12"]()
-    _check(m, b, method, True, 1e-10, fmt=fmt, iters_gate=(method != "bicgstab"))
+    _check(m, b, method, True, 1e-10, fmt=fmt, iters_gate=(method not in ("bicgstab", "cgs")))
 
 
 def test_small_gmres_restart_length():
@@ -155,7 +180,7 @@ def test_dense_solution_matches_lapack():
         assert np.linalg.norm(x - xs) <= 2 * kappa * 1e-12 * np.linalg.norm(xs)
 
 
-@pytest.mark.parametrize("method", ["cg", "bicgstab", "gmres"])
+@pytest.mark.parametrize("method", ["cg", "bicgstab", "gmres", "cgs"])
 def test_zero_rhs(method):
     m = W.laplacian_2d(10)
     x, info = _gpu_solve(m, np.zeros(m.n), method, 0, 1e-10, x0=np.ones(m.n))
@@ -175,7 +200,7 @@ def test_cg_breakdown_on_indefinite():
     assert info["return"] == gk.GK_BREAKDOWN
 
 
-@pytest.mark.parametrize("method", ["cg", "bicgstab", "gmres"])
+@pytest.mark.parametrize("method", ["cg", "bicgstab", "gmres", "cgs"])
 def test_iteration_cap(method):
     m, b = CASES["lap2d_64"]()
     x, info = _gpu_solve(m, b, method, 0, 1e-12, max_iters=7)
@@ -201,7 +226,7 @@ def test_solve_deterministic():
     assert np.array_equal(x1, x2) and i1["iters"] == i2["iters"]
 
 
-@pytest.mark.parametrize("method", ["cg", "bicgstab", "gmres"])
+@pytest.mark.parametrize("method", ["cg", "bicgstab", "gmres", "cgs"])
 def test_fp32_solve(method):
     m, b = CASES["diff3d_12"]()
     x, info = _gpu_solve(m, b, method, 1, 1e-5, dtype="f32")
@@ -210,7 +235,7 @@ def test_fp32_solve(method):
 
 
 @pytest.mark.parametrize("mixed", [1, 2])
-@pytest.mark.parametrize("method", ["cg", "gmres"])
+@pytest.mark.parametrize("method", ["cg", "gmres", "cgs"])
 def test_mixed_precision_refinement(mixed, method):
     """FP32 (or BF16-stored) inner solves inside FP64 refinement reach the
     FP64 tolerance, and x agrees with the plain FP64 solve within kappa*tol."""
