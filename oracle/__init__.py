@@ -73,6 +73,9 @@ def _declare(L):
     L.or_spmv_csr.restype = None
     L.or_spmv_csr_omp.argtypes = [i32, _i32p, _i32p, _f64p, _f64p, f64, f64, _f64p, ctypes.c_int]
     L.or_spmv_csr_omp.restype = ctypes.c_int
+    L.or_spmv_coo.argtypes = [i32, i32, i64, _i32p, _i32p, _f64p, _f64p, f64, f64, _f64p,
+                              ctypes.c_int]
+    L.or_spmv_coo.restype = ctypes.c_int
     L.or_coo_to_csr.argtypes = [i32, i32, i64, _i32p, _i32p, _f64p, ctypes.c_int, _i32p, _i32p, _f64p]
     L.or_coo_to_csr.restype = i64
     L.or_ell_width.argtypes = [i32, _i32p]
@@ -110,6 +113,18 @@ def spmv(m, x, alpha=1.0, beta=0.0, y=None, compensated=True):
     out = np.zeros(m.n) if y is None else _f64(y).copy()
     lib().or_spmv_csr(m.n, _i32(m.row_ptr), _i32(m.col_idx), _f64(m.values), _f64(x),
                       float(alpha), float(beta), out, 1 if compensated else 0)
+    return out
+
+
+def spmv_coo(n, ncols, row, col, val, x, alpha=1.0, beta=0.0, y=None, compensated=True):
+    """y = alpha * A x + beta * y with A given as COO triplets (visited in
+    storage order).  Returns a new array."""
+    out = np.zeros(n) if y is None else _f64(y).copy()
+    row, col = _i32(row), _i32(col)
+    st = lib().or_spmv_coo(n, ncols, row.shape[0], row, col, _f64(val), _f64(x), float(alpha),
+                           float(beta), out, 1 if compensated else 0)
+    if st != 0:
+        raise ValueError("COO index out of range")
     return out
 
 

@@ -88,6 +88,45 @@ void or_spmv_csr(int32_t n, const int32_t* rp, const int32_t* ci,
     }
 }
 
+/* COO SpMV straight from the definition: every row sum starts at zero,
+ * the triplets (row[k], col[k], val[k]) are visited in storage order and
+ * each adds val * x[col] to its row's sum (Neumaier-compensated, as in the
+ * CSR check mode, when compensated = 1); then y_i = alpha s_i + beta y_i
+ * for every row, including rows without entries (beta == 0: y not read).
+ * The paper benchmarks COO beside CSR (Section 5.1).  Returns -1 if a
+ * triplet lies outside the matrix, else 0. */
+int or_spmv_coo(int32_t n, int32_t ncols, int64_t nnz, const int32_t* row,
+                const int32_t* col, const double* val, const double* x, double alpha,
+                double beta, double* y, int compensated)
+{
+    double* s = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double* c = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    for (int64_t k = 0; k < nnz; ++k) {
+        if (row[k] < 0 || row[k] >= n || col[k] < 0 || col[k] >= ncols) {
+            free(s);
+            free(c);
+            return -1;
+        }
+        const int32_t i = row[k];
+        const double p = val[k] * x[col[k]];
+        if (compensated) {
+            const double t = s[i] + p;
+            if (fabs(s[i]) >= fabs(p)) c[i] += (s[i] - t) + p;
+            else c[i] += (p - t) + s[i];
+            s[i] = t;
+        } else {
+            s[i] += p;
+        }
+    }
+    for (int32_t i = 0; i < n; ++i) {
+        const double si = s[i] + c[i];
+        y[i] = (beta == 0.0) ? alpha * si : alpha * si + beta * y[i];
+    }
+    free(s);
+    free(c);
+    return 0;
+}
+
 /* Row-parallel version of the plain sum (bitwise identical to
  * or_spmv_csr with compensated = 0, since each row is summed by one
  * thread in the same order).  Returns the number of threads used. */

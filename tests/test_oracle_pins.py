@@ -491,3 +491,37 @@ def test_jacobi_cgs_diagonal_one_iteration():
     x, info = oracle.solve(m, b, method=oracle.CGS, precond=1, tol=1e-12)
     assert info["status"] == oracle.OK and info["iters"] == 1
     assert np.allclose(x, b / d, rtol=1e-15, atol=0)
+
+
+# ---------------------------------------------------------------- COO SpMV pins
+
+
+@pytest.mark.parametrize("seed,n,ncols,nnz", [(1, 1, 1, 1), (2, 17, 9, 40), (3, 64, 70, 300),
+                                               (4, 50, 50, 0)])
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (-0.5, 2.0)])
+def test_coo_spmv_matches_dense_matvec(seed, n, ncols, nnz, alpha, beta):
+    """Unsorted triplets with duplicates and empty rows: the COO SpMV equals
+    alpha * D x + beta * y for the densified D (duplicates add)."""
+    rng = np.random.default_rng(seed)
+    row = rng.integers(0, n, nnz)
+    col = rng.integers(0, ncols, nnz)
+    val = rng.standard_normal(nnz)
+    d = np.zeros((n, ncols))
+    np.add.at(d, (row, col), val)
+    x = rng.standard_normal(ncols)
+    y = rng.standard_normal(n)
+    got = oracle.spmv_coo(n, ncols, row, col, val, x, alpha, beta, y=y)
+    ref = alpha * (d @ x) + beta * y
+    scale = np.abs(alpha) * (np.abs(d) @ np.abs(x)) + np.abs(beta) * np.abs(y)
+    assert np.all(np.abs(got - ref) <= 1e-14 * scale + 1e-300)
+
+
+def test_coo_spmv_integer_exact_and_rejects_out_of_range():
+    m = W.laplacian_2d(12)
+    row = np.repeat(np.arange(m.n), np.diff(m.row_ptr))
+    x = (np.arange(m.n) % 7).astype(np.float64)
+    got = oracle.spmv_coo(m.n, m.n, row, m.col_idx, m.values, x, compensated=False)
+    ref = m.to_dense() @ x  # integers: exact in either order
+    assert np.array_equal(got, ref)
+    with pytest.raises(ValueError):
+        oracle.spmv_coo(3, 3, [0, 3], [0, 0], [1.0, 1.0], np.ones(3))
