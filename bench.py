@@ -5,15 +5,19 @@ synthetic stand-ins for its SuiteSparse set), plus CG solves/s on the 64x64
 5-point Laplacian to a 1e-10 relative residual.
 
 One step = one apply per (matrix, dtype) in the fastest of CSR / ELL /
-SELL-P for that matrix (picked by a short timing pass before the timed
-region, as the paper reports each library's best-performing format,
-Section 5).  value = algorithmic bytes of the step / device time (GB/s);
-algorithmic bytes per apply = nnz*(value+index bytes) + 4*(n+1) [CSR] +
-x and y once.  Every format is also timed and listed under "sweep".
+SELL-P / COO for that matrix (picked by a short timing pass before the
+timed region, as the paper reports each library's best-performing format,
+Section 5).  value = algorithmic bytes of the step / device time (GB/s),
+where every matrix counts its CSR algorithmic bytes = nnz*(value+index
+bytes) + 4*(n+1) + x and y once, whichever format ran.  Every format is also
+timed and listed under "sweep" with its own algorithmic bytes (ELL/SELL-P
+unpadded without the row pointer, COO with a row index per entry).
 Matrices (0.9-1.7 GB each) are larger than L2, so no flush is needed.
 Extra keys: CG solves/s on the 64x64 Laplacian, time to 1e-10 on the 128^3
-diffusion problem for FP32-refined vs plain FP64 Jacobi-CG / GMRES(30),
-and 2048 batched systems in one launch vs a per-system loop.
+diffusion problem for FP32-refined vs plain FP64 Jacobi-CG / GMRES(30) /
+CGS, the paper's fixed-1000-iteration time per iteration of CG, CGS and
+GMRES(30), 2048 batched systems in one launch vs a per-system loop, and
+serving latency.
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 """
@@ -35,7 +39,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "SpMV GB/s & %HBM peak; CG solves/s at 1e-10 residual; serving p50/p99 latency"
-WORKLOAD = ("SpMV, best of {CSR, ELL, SELL-P(S=32)} per matrix, {FP64, FP32}: 3D 7-point "
+WORKLOAD = ("SpMV, best of {CSR, ELL, SELL-P(S=32), COO} per matrix, {FP64, FP32}: 3D 7-point "
             "Laplacian 256^3 (n=16,777,216, nnz=117,047,296) and Zipf(1.8) power-law "
             "n=4,194,304 (mean 16, max 4096; ELL not built: ~206 GB padded); int32 indices; "
             "x ~ U[-1,1]")
@@ -56,6 +60,8 @@ def alg_bytes(m, sv, fmt):
     b = m.nnz * (sv + 4) + m.n * sv + m.ncols * sv
     if fmt == "csr":
         b += 4 * (m.n + 1)
+    if fmt == "coo":
+        b += 4 * m.nnz  # the row index of every entry
     return int(b)
 
 
@@ -64,8 +70,8 @@ def build_items(gk, W, dtypes=("f64", "f32")):
     items = []
     lap = W.laplacian_3d(256)
     pl = W.power_law(1 << 22, seed=W.SEED_BASE + 2)
-    for m, tag, fmts in ((lap, "lap3d_256", ("csr", "ell", "sellp")),
-                         (pl, "powerlaw_4M", ("csr", "sellp"))):
+    for m, tag, fmts in ((lap, "lap3d_256", ("csr", "ell", "sellp", "coo")),
+                         (pl, "powerlaw_4M", ("csr", "sellp", "coo"))):
         for dt in dtypes:
             sv = 8 if dt == "f64" else 4
             A = gk.Matrix.from_csr(m, dt)
@@ -74,12 +80,14 @@ def build_items(gk, W, dtypes=("f64", "f32")):
                 items.append({"name": f"{tag}/{fmt}/{dt}", "mat": H, "dtype": dt, "fmt": fmt,
                               "n": m.n, "ncols": m.ncols, "nnz": m.nnz,
                               "bytes": alg_bytes(m, sv, fmt),
+                              "csr_bytes": alg_bytes(m, sv, "csr"),
                               "kernel": H.desc["spmv_kernel"],
                               "launches": H.desc["spmv_launches"]})
     return items, lap, pl
 
 
-KERNEL_NAMES = {0: "k_csr_vector", 1: "k_csr_rowtile", 2: "k_csr_merge", 3: "k_ell", 4: "k_sellp"}
+KERNEL_NAMES = {0: "k_csr_vector", 1: "k_csr_rowtile", 2: "k_csr_merge_warp", 3: "k_ell",
+                4: "k_sellp", 5: "k_coo_warp"}
 
 
 class ClockSampler:
@@ -220,14 +228,14 @@ def time_apply(it, stream, torch, reps=3):
 
 def ir_compare(gk, W, torch, dev):
     """128^3 log-normal diffusion: wall time to a true 1e-10 residual,
-    FP32 inner solves in FP64 refinement vs plain FP64 (Jacobi-CG and
-    Jacobi-GMRES(30))."""
+    FP32 inner solves in FP64 refinement vs plain FP64 (Jacobi-CG,
+    Jacobi-GMRES(30) and Jacobi-CGS)."""
     m = W.diffusion_3d(128)
     b = torch.from_numpy(W.uniform_vector(m.n, W.SEED_BASE + 3)).to(dev)
     A = gk.Matrix.from_csr(m)
     out = {"workload": "128^3 7-point diffusion, exp(N(0,1)) cells, harmonic faces; "
                        "b ~ U[-1,1] seed 2513; x0 = 0; tol 1e-10 (true residual)"}
-    for method in ("cg", "gmres"):
+    for method in ("cg", "gmres", "cgs"):
         res = {}
         for mixed in (0, 1, 2):
             x = torch.zeros_like(b)
@@ -245,6 +253,31 @@ def ir_compare(gk, W, torch, dev):
                 "outer": info["outer_iters"], "rel_res_true": info["rel_res_true"]}
         res["speedup_fp32_ir"] = round(res["fp64"]["ms"] / res["fp32_ir"]["ms"], 3)
         out[method] = res
+    A.close()
+    return out
+
+
+def per_iteration_protocol(gk, W, torch, dev, iters=1000):
+    """The paper's solver protocol (Section 5.2.1): a fixed 1000 iterations
+    of CG, CGS and GMRES(30) without a preconditioner, reported as time per
+    iteration, here on the 128^3 diffusion matrix (FP64).  A method that
+    breaks down or reaches a residual of 1e-30 first is timed over the
+    iterations it ran."""
+    m = W.diffusion_3d(128)
+    b = torch.from_numpy(W.uniform_vector(m.n, W.SEED_BASE + 3)).to(dev)
+    A = gk.Matrix.from_csr(m)
+    out = {"workload": "128^3 diffusion FP64, no preconditioner, 1000 iterations (GMRES: "
+                       "Arnoldi steps, restart 30), x0 = 0; device time per iteration"}
+    for method in ("cg", "cgs", "gmres"):
+        x = torch.zeros_like(b)
+        A.solve(b, x, method=method, tol=1e-30, max_iters=20)  # warm-up (graphs)
+        x.zero_()
+        torch.cuda.synchronize()
+        info = A.solve(b, x, method=method, tol=1e-30, max_iters=iters, krylov_dim=30)
+        its = max(int(info["iters"]), 1)
+        out[method] = {"iters": int(info["iters"]), "status": info["return"],
+                       "us_per_iter": round(info["device_ms"] * 1000.0 / its, 2),
+                       "rel_res_true": info["rel_res_true"]}
     A.close()
     return out
 
@@ -365,6 +398,7 @@ def profile_case(name, dtype):
     than L2 (129 MB) but a few hundred MB on the device, three launches of
     the kernel after the matrix is built.
       merge    CSR merge path, Zipf(1.8) power-law n=2^21 (~33M nnz)
+      coo      COO of the same power-law matrix
       rowtile  CSR row tiles, 3D 7-point Laplacian 128^3 (14.6M nnz)
       ell      ELL of the same Laplacian
       sellp    SELL-P(32) of the same Laplacian
@@ -389,14 +423,14 @@ def profile_case(name, dtype):
         print("profile case", name, dtype, info["iters"], A.describe()["solve_format"])
         A.close()
         return 0
-    if name == "merge":
+    if name in ("merge", "coo"):
         os.environ["GK_CSR_KERNEL"] = "2"
         m = W.power_law(1 << 21, seed=W.SEED_BASE + 2)
     else:
         os.environ["GK_CSR_KERNEL"] = "1"
         m = W.laplacian_3d(128)
     A = gk.Matrix.from_csr(m, dtype)
-    if name in ("ell", "sellp"):
+    if name in ("ell", "sellp", "coo"):
         B = A.convert(name, None, 32, 1)
         A.close()
         A = B
@@ -459,8 +493,8 @@ def main():
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-solvers", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--profile-case", choices=["merge", "rowtile", "ell", "sellp", "cg", "bicgstab",
-                                               "gmres"],
+    ap.add_argument("--profile-case", choices=["merge", "coo", "rowtile", "ell", "sellp", "cg",
+                                               "bicgstab", "gmres"],
                     help="run one small case for an ncu capture and exit")
     ap.add_argument("--profile-dtype", default="f64", choices=["f64", "f32"])
     args = ap.parse_args()
@@ -539,7 +573,10 @@ def main():
         t = torch.tensor([total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    step_bytes = sum(it["bytes"] for it in step_items)
+    # the step counts every matrix at its CSR algorithmic bytes, whatever
+    # format ran, so a format that moves more (COO's row indices) or less
+    # (ELL's missing row pointer) does not change the yardstick
+    step_bytes = sum(it["csr_bytes"] for it in step_items)
     value = step_bytes * args.steps * world / (total_ms / 1000.0) / 1e9
     peak, peak_kind = _peaks()
 
@@ -598,11 +635,12 @@ def main():
     del items, step_items
     torch.cuda.empty_cache()
 
-    cg = ir = batched = serving = None
+    cg = ir = batched = serving = per_iter = None
     if rank == 0 and not args.no_cg:
         cg = cg_solves_per_s(gk, W, torch, dev)
     if rank == 0 and not args.no_solvers:
         ir = ir_compare(gk, W, torch, dev)
+        per_iter = per_iteration_protocol(gk, W, torch, dev)
         batched = batched_compare(gk, W, torch, dev)
     if rank == 0 and not args.no_serving:
         serving = serving_bench(gk, W, torch, dev)
@@ -616,7 +654,8 @@ def main():
             "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "step": step_detail, "sweep": sweep, "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": e2e, "cg": cg, "ir_128cubed": ir, "batched_2048": batched,
+            "e2e": e2e, "cg": cg, "ir_128cubed": ir, "per_iteration_1000": per_iter,
+            "batched_2048": batched,
             "serving": serving, "clocks": clk,
             "gpu_launches": launches}
     if rank == 0:

@@ -48,6 +48,9 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2 } gk_dtype;
 /* Storage formats.
  * GK_CSR  : row_ptr[n+1], col_idx[nnz], values[nnz]; columns ascending
  *           within a row is NOT required for SpMV.
+ * GK_COO  : row[nnz], col[nnz], values[nnz] in CSR order (sorted by row).
+ *           A COO handle also keeps the CSR row pointer it was converted
+ *           from: apply runs the COO kernel, the solvers use the CSR view.
  * GK_ELL  : K = longest row, stride = n rounded up to 32; entry j of row i
  *           at j*stride + i; padding col = -1, value = +0.0.
  * GK_SELLP: slices of S consecutive rows; slice_lengths[s] = longest row
@@ -58,7 +61,7 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2 } gk_dtype;
  *           including the virtual rows past n in the last slice.
  * The paper names "other matrix formats" beside CSR and COO (Section 2)
  * without defining them; these layouts are this library's definition. */
-typedef enum { GK_CSR = 0, GK_ELL = 1, GK_SELLP = 2 } gk_format;
+typedef enum { GK_CSR = 0, GK_ELL = 1, GK_SELLP = 2, GK_COO = 3 } gk_format;
 
 /* Krylov methods: CG (Hestenes-Stiefel), BiCGSTAB (van der Vorst), GMRES(m),
  * and CGS (Sonneveld's conjugate gradient squared, the solver the paper
@@ -98,7 +101,7 @@ typedef struct {
     int64_t stored;        /* entries held in col/values incl. padding */
     int64_t device_bytes;  /* bytes of the format arrays on the device */
     int32_t spmv_kernel;   /* SpMV kernel apply uses: 0 CSR vector, 1 CSR row-tile,
-                              2 CSR merge-path, 3 ELL, 4 SELL-P */
+                              2 CSR merge-path, 3 ELL, 4 SELL-P, 5 COO */
     int32_t spmv_launches; /* kernel launches per apply */
     int32_t device_error;  /* 1 if a kernel on this matrix gave up a bounded
                               device-side wait (its results are invalid) */
@@ -153,6 +156,7 @@ gk_status gk_matrix_describe(gk_matrix A, gk_matrix_desc* out);
 /* Copy the format arrays to caller-owned HOST buffers (any pointer may be
  * NULL to skip that array):
  *   CSR  : idx_a = row_ptr[n+1], col = col_idx[nnz], values[nnz]
+ *   COO  : idx_a = row[nnz], col[nnz], values[nnz]
  *   ELL  : col[K*stride], values[K*stride]              (idx_a, sets unused)
  *   SELLP: idx_a = slice_lengths[num_slices], sets = slice_sets[num_slices+1],
  *          col[stored], values[stored]

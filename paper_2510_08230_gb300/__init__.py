@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgk.so")
 
 GK_F64, GK_F32, GK_BF16 = 0, 1, 2
-GK_CSR, GK_ELL, GK_SELLP = 0, 1, 2
+GK_CSR, GK_ELL, GK_SELLP, GK_COO = 0, 1, 2, 3
 GK_CG, GK_BICGSTAB, GK_GMRES, GK_CGS = 0, 1, 2, 3
 GK_PRECOND_NONE, GK_PRECOND_JACOBI = 0, 1
 GK_MEM_HOST, GK_MEM_DEVICE = 0, 1
@@ -32,7 +32,7 @@ GK_ERR_INVALID, GK_ERR_OOM, GK_ERR_CUDA, GK_ERR_TIMEOUT = -1, -2, -3, -4
 GK_ERR_ZERO_DIAG, GK_ERR_NAN, GK_ERR_UNSUPPORTED = -5, -6, -7
 
 DTYPES = {"f64": GK_F64, "f32": GK_F32, "bf16": GK_BF16}
-FORMATS = {"csr": GK_CSR, "ell": GK_ELL, "sellp": GK_SELLP}
+FORMATS = {"csr": GK_CSR, "ell": GK_ELL, "sellp": GK_SELLP, "coo": GK_COO}
 METHODS = {"cg": GK_CG, "bicgstab": GK_BICGSTAB, "gmres": GK_GMRES, "cgs": GK_CGS}
 
 EXPORTED = [
@@ -328,7 +328,15 @@ class Matrix:
         d = self.desc
         vdt = {GK_F64: np.float64, GK_F32: np.float32, GK_BF16: np.uint16}[d["dtype"]]
         out = {}
-        if d["format"] == GK_CSR:
+        if d["format"] == GK_COO:
+            nz = max(d["nnz"], 1)
+            out["row"] = np.zeros(nz, np.int32)
+            out["col_idx"] = np.zeros(nz, np.int32)
+            out["values"] = np.zeros(nz, vdt)
+            gk_matrix_export(self.handle, out["row"], None, out["col_idx"], out["values"])
+            for k in ("row", "col_idx", "values"):
+                out[k] = out[k][:d["nnz"]]
+        elif d["format"] == GK_CSR:
             out["row_ptr"] = np.zeros(d["n"] + 1, np.int32)
             out["col_idx"] = np.zeros(max(d["nnz"], 1), np.int32)
             out["values"] = np.zeros(max(d["nnz"], 1), vdt)

@@ -49,6 +49,36 @@ static gk_status spmv_typed(gk_matrix A, double alpha, const void* b, double bet
     const int mode = (beta == 0.0) ? (alpha == 1.0 ? 0 : 1) : 2;
     EpiStore<T> epi{static_cast<T*>(x), (T)alpha, (T)beta, mode};
     if (A->n == 0) return GK_OK;
+    if (A->coo) {
+        const int E = A->coo_e;
+        const int64_t units = (A->nnz + 32 * E - 1) / (32 * E);
+        if (units > 0) {
+            GK_TRY(A->carry.ensure((size_t)units * (sizeof(int32_t) + sizeof(T)) + 16));
+            int32_t* crow = static_cast<int32_t*>(A->carry.ptr);
+            T* cval = reinterpret_cast<T*>(static_cast<char*>(A->carry.ptr) +
+                                           (((size_t)units * sizeof(int32_t) + 15) & ~(size_t)15));
+            const unsigned g = (unsigned)((units + 7) / 8);
+            if (E == 8)
+                k_coo_warp<8, V, T><<<g, 256, 0, s>>>(A->n, A->nnz, A->coo_row, A->col,
+                                                      (const V*)A->val, static_cast<const T*>(b),
+                                                      epi, units, crow, cval);
+            else
+                k_coo_warp<4, V, T><<<g, 256, 0, s>>>(A->n, A->nnz, A->coo_row, A->col,
+                                                      (const V*)A->val, static_cast<const T*>(b),
+                                                      epi, units, crow, cval);
+            const unsigned fg =
+                (unsigned)std::max<int64_t>(1, std::min<int64_t>((units + 255) / 256, 4096));
+            k_csr_merge_fixup<T><<<fg, 256, 0, s>>>((int32_t)units, crow, cval, static_cast<T*>(x),
+                                                    (T)alpha, mode);
+        }
+        if (A->n_empty) {
+            const unsigned eg = (unsigned)std::max<int64_t>(
+                1, std::min<int64_t>((A->n_empty + 255) / 256, (int64_t)num_sms() * 8));
+            k_coo_empty<T><<<eg, 256, 0, s>>>(A->n_empty, A->empty_rows, epi);
+        }
+        GK_CUDA(cudaGetLastError());
+        return GK_OK;
+    }
     if (A->fmt == GK_CSR && A->plan.kind == 2) {
         const int64_t nb = A->plan.merge_blocks;
         GK_TRY(A->carry.ensure((size_t)nb * (sizeof(int32_t) + sizeof(T)) + 16));

@@ -165,6 +165,12 @@ struct gk_matrix_s {
     int32_t* row_ptr = nullptr;
     int32_t* col = nullptr;
     void* val = nullptr;
+    // COO view (apply runs the COO kernel; fmt stays GK_CSR for everything else)
+    int coo = 0;
+    int32_t* coo_row = nullptr;     // row of every entry
+    int32_t* empty_rows = nullptr;  // rows without entries
+    int32_t n_empty = 0;
+    int coo_e = 4;                  // entries per lane of the COO kernel (4 or 8)
     // ELL
     int32_t K = 0;
     int64_t stride = 0;

@@ -498,6 +498,9 @@ static void free_arrays(gk_matrix A) {
     dfree(A->plan.block_row);
     dfree(A->plan.err);
     dfree(A->dinv);
+    dfree(A->coo_row);
+    dfree(A->empty_rows);
+    A->coo_row = A->empty_rows = nullptr;
     A->row_ptr = A->col = nullptr;
     A->val = nullptr;
     A->slice_len = nullptr;
@@ -518,6 +521,43 @@ static void destroy_handle(gk_matrix A) {
     A->carry.release();
     if (A->side) cudaStreamDestroy(A->side);
     delete A;
+}
+
+// COO view of a CSR handle: the row of every entry, and the list of rows
+// without entries (the COO kernel never visits them).
+__global__ void k_coo_rows(int32_t n, const int32_t* __restrict__ rp, int32_t* __restrict__ rows,
+                           int32_t* __restrict__ empty, unsigned int* __restrict__ n_empty) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = rp[i], b = rp[i + 1];
+        for (int32_t k = a; k < b; ++k) rows[k] = (int32_t)i;
+        if (a == b) empty[atomicAdd(n_empty, 1u)] = (int32_t)i;  // order of the list is free
+    }
+}
+
+static gk_status build_coo_view(gk_matrix A, cudaStream_t s) {
+    DevBuf cnt, tmp_empty;
+    GK_TRY(cnt.ensure(16));
+    GK_CUDA(cudaMemsetAsync(cnt.ptr, 0, 16, s));
+    GK_CUDA(dmalloc_t(&A->coo_row, (size_t)std::max<int64_t>(A->nnz, 1)));
+    GK_TRY(tmp_empty.ensure(4 * (size_t)std::max(A->n, 1)));
+    if (A->n > 0)
+        k_coo_rows<<<grid_for(A->n), 256, 0, s>>>(A->n, A->row_ptr, A->coo_row,
+                                                   (int32_t*)tmp_empty.ptr, (unsigned int*)cnt.ptr);
+    GK_CUDA(cudaGetLastError());
+    unsigned int ne = 0;
+    GK_CUDA(cudaMemcpyAsync(&ne, cnt.ptr, 4, cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    A->n_empty = (int32_t)ne;
+    if (ne) {
+        GK_CUDA(dmalloc_t(&A->empty_rows, (size_t)ne));
+        GK_CUDA(cudaMemcpyAsync(A->empty_rows, tmp_empty.ptr, 4 * (size_t)ne, cudaMemcpyDeviceToDevice, s));
+        GK_CUDA(cudaStreamSynchronize(s));
+    }
+    A->coo = 1;
+    A->coo_e = 4;
+    if (const char* e = getenv("GK_COO_E")) A->coo_e = atoi(e) == 8 ? 8 : 4;
+    return GK_OK;
 }
 
 // CSR launch plan: row tiles when rows are short, merge path otherwise.
@@ -800,8 +840,10 @@ gk_status gk_matrix_create_coo(int32_t n, int32_t ncols, int64_t nnz, const int3
 gk_status gk_matrix_convert(gk_matrix A, gk_format fmt, gk_dtype dtype, int32_t slice_size,
                             int32_t stride_factor, void* stream, gk_matrix* out) {
     if (!A || !out || !valid_dtype(dtype)) return GK_ERR_INVALID;
-    if (fmt != GK_CSR && fmt != GK_ELL && fmt != GK_SELLP) return GK_ERR_INVALID;
+    if (fmt != GK_CSR && fmt != GK_ELL && fmt != GK_SELLP && fmt != GK_COO) return GK_ERR_INVALID;
     *out = nullptr;
+    const bool to_coo = fmt == GK_COO;
+    if (to_coo) fmt = GK_CSR;  // the COO handle is a CSR handle plus the row of every entry
     cudaStream_t s = (cudaStream_t)stream;
     const int32_t S = slice_size ? slice_size : 32;
     const int32_t f = stride_factor ? stride_factor : 1;
@@ -917,6 +959,7 @@ gk_status gk_matrix_convert(gk_matrix A, gk_format fmt, gk_dtype dtype, int32_t 
     });
     if (st != GK_OK) return failB(st);
     if (fmt == GK_CSR && (st = build_csr_plan(B, s)) != GK_OK) return failB(st);
+    if (to_coo && (st = build_coo_view(B, s)) != GK_OK) return failB(st);
     if (cudaStreamSynchronize(s)) return failB(GK_ERR_CUDA);
     destroy_handle(tmpC);
     *out = B;
@@ -929,7 +972,7 @@ gk_status gk_matrix_describe(gk_matrix A, gk_matrix_desc* d) {
     d->n = A->n;
     d->ncols = A->ncols;
     d->nnz = A->nnz;
-    d->format = A->fmt;
+    d->format = A->coo ? GK_COO : A->fmt;
     d->dtype = A->dtype;
     d->max_row = A->max_row;
     d->ell_width = A->K;
@@ -937,12 +980,13 @@ gk_status gk_matrix_describe(gk_matrix A, gk_matrix_desc* d) {
     d->slice_size = A->S;
     d->stride_factor = A->f;
     d->num_slices = A->nslices;
-    d->spmv_kernel = A->fmt == GK_CSR ? A->plan.kind : A->fmt == GK_ELL ? 3 : 4;
+    d->spmv_kernel = A->coo ? 5 : A->fmt == GK_CSR ? A->plan.kind : A->fmt == GK_ELL ? 3 : 4;
     if (A->plan.err) {
         int32_t e = 0;
         if (cudaMemcpy(&e, A->plan.err, 4, cudaMemcpyDeviceToHost) == cudaSuccess) d->device_error = e;
     }
-    d->spmv_launches = (A->fmt == GK_CSR && A->plan.kind == 2) ? 2 : 1;
+    d->spmv_launches = A->coo ? (A->n_empty ? 3 : 2)
+                       : (A->fmt == GK_CSR && A->plan.kind == 2) ? 2 : 1;
     d->solve_format = A->fmt != GK_CSR ? (int32_t)A->fmt
                       : !A->solve_fmt_tuned ? -1
                       : A->solve_fmt ? (int32_t)A->solve_fmt->fmt : (int32_t)GK_CSR;
@@ -950,6 +994,7 @@ gk_status gk_matrix_describe(gk_matrix A, gk_matrix_desc* d) {
     if (A->fmt == GK_CSR) {
         d->stored = A->nnz;
         d->device_bytes = (int64_t)(4 * ((size_t)A->n + 1) + (4 + vb) * (size_t)A->nnz);
+        if (A->coo) d->device_bytes += (int64_t)(4 * (size_t)A->nnz + 4 * (size_t)A->n_empty);
     } else if (A->fmt == GK_ELL) {
         d->stored = A->stored;
         d->device_bytes = (int64_t)((4 + vb) * (size_t)A->stored);
@@ -965,7 +1010,11 @@ gk_status gk_matrix_export(gk_matrix A, int32_t* idx_a, int64_t* sets, int32_t* 
     if (!A) return GK_ERR_INVALID;
     GK_CUDA(cudaDeviceSynchronize());
     const size_t vb = value_bytes(A->dtype);
-    if (A->fmt == GK_CSR) {
+    if (A->coo) {
+        if (idx_a && A->nnz) GK_CUDA(cudaMemcpy(idx_a, A->coo_row, 4 * (size_t)A->nnz, cudaMemcpyDeviceToHost));
+        if (col && A->nnz) GK_CUDA(cudaMemcpy(col, A->col, 4 * (size_t)A->nnz, cudaMemcpyDeviceToHost));
+        if (values && A->nnz) GK_CUDA(cudaMemcpy(values, A->val, vb * (size_t)A->nnz, cudaMemcpyDeviceToHost));
+    } else if (A->fmt == GK_CSR) {
         if (idx_a) GK_CUDA(cudaMemcpy(idx_a, A->row_ptr, 4 * ((size_t)A->n + 1), cudaMemcpyDeviceToHost));
         if (col && A->nnz) GK_CUDA(cudaMemcpy(col, A->col, 4 * (size_t)A->nnz, cudaMemcpyDeviceToHost));
         if (values && A->nnz) GK_CUDA(cudaMemcpy(values, A->val, vb * (size_t)A->nnz, cudaMemcpyDeviceToHost));

@@ -45,6 +45,9 @@ struct KState {
     double beta0, inv_h;
     double stag;       // GMRES: stop when a cycle's residual > stag * the previous (0: off)
     double prev_beta0;
+    double best_rn;    // CG/BiCGSTAB/CGS inner solves: best residual so far ...
+    int32_t best_iter; // ... and its iteration
+    int32_t stall;     // stop after this many iterations without a 10 % gain (0: off)
     double H[(MAXM + 1) * MAXM];
     double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
     double h1[MAXM + 1], h2[MAXM + 1];
@@ -52,6 +55,20 @@ struct KState {
 
 __device__ __forceinline__ bool halted(const KState* st) {
     return *reinterpret_cast<const volatile int32_t*>(&st->halt) != 0;
+}
+
+// Inner solves of iterative refinement: a solve whose residual has not
+// dropped below 0.9x its best for `stall` iterations stops (CGS and
+// BiCGSTAB can stagnate or wander in FP32); the refinement step continues
+// from the iterate it reached.  Run by the last block's fin.
+__device__ __forceinline__ bool stalled(KState* st, double rn) {
+    if (st->stall <= 0) return false;
+    if (!(st->best_rn > 0.0) || rn < 0.9 * st->best_rn) {
+        st->best_rn = rn;
+        st->best_iter = st->iter;
+        return false;
+    }
+    return st->iter - st->best_iter >= st->stall;
 }
 
 // ------------------------------------------------------------ grids
@@ -343,7 +360,7 @@ struct CgUpdFin {
             st->halt = 1;
             return;
         }
-        if (st->iter >= st->max_iters) {
+        if (st->iter >= st->max_iters || stalled(st, rn)) {
             st->status = GK_NOT_CONVERGED;
             st->halt = 2;
             return;
@@ -547,7 +564,7 @@ struct BiUpdFin {
             st->halt = 1;
             return;
         }
-        if (st->iter >= st->max_iters) {
+        if (st->iter >= st->max_iters || stalled(st, rn)) {
             st->status = GK_NOT_CONVERGED;
             st->halt = 2;
             return;
@@ -770,7 +787,7 @@ struct CgsRFin {
             st->halt = 1;
             return;
         }
-        if (st->iter >= st->max_iters) {
+        if (st->iter >= st->max_iters || stalled(st, rn)) {
             st->status = GK_NOT_CONVERGED;
             st->halt = 2;
             return;
@@ -1612,6 +1629,7 @@ static gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, 
     h->max_iters = max_iters;
     h->m = m;
     h->stag = inner ? 0.95 : 0.0;
+    h->stall = inner ? 200 : 0;
     GK_CUDA(cudaMemcpyAsync(st, h, HDR, cudaMemcpyHostToDevice, s));
     k_norm2<T, FinBnorm><<<ewg(k_norm2<T, FinBnorm>, n), 256, 0, s>>>(n, b, part, tk, FinBnorm{st, tol});
     GK_CUDA(cudaGetLastError());

@@ -511,6 +511,119 @@ k_csr_merge_warp(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
     }
 }
 
+// COO SpMV (apply only): triplets sorted by (row, col).  The nonzeros are
+// cut into units of 32*COO_E per warp, COO_E consecutive triplets per lane,
+// read with 16-byte loads (no shared-memory staging: the row index comes
+// with every entry).  A lane sums each run of equal rows; a row ends where the next
+// triplet (in this lane, the next lane, the next unit, or none) has another
+// row.  The first row a lane ends may have begun in earlier lanes: it adds
+// their carries, combined with the 5-level segmented shuffle scan used by
+// the merge kernel; the run open at the end of a unit goes to
+// k_csr_merge_fixup.  Rows without entries are written by k_coo_empty.
+
+// E consecutive entries starting at k (k % E == 0): 16-byte loads when the
+// group is whole (the arrays start on 256-byte boundaries), else one by one.
+template <int E, typename V>
+__device__ __forceinline__ void load_group(const V* __restrict__ p, int64_t k, int64_t nnz,
+                                           bool full, V (&v)[E]) {
+    constexpr int PER = 16 / (int)sizeof(V) < E ? 16 / (int)sizeof(V) : E;  // per 16 B
+    struct alignas(PER * sizeof(V)) Q { V e[PER]; };
+    if (full) {
+#pragma unroll
+        for (int h = 0; h < E / PER; ++h) {
+            const Q q = *reinterpret_cast<const Q*>(p + k + h * PER);
+#pragma unroll
+            for (int c = 0; c < PER; ++c) v[h * PER + c] = q.e[c];
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < E; ++c) v[c] = k + c < nnz ? p[k + c] : V{};
+    }
+}
+
+template <int COO_E, typename V, typename T>
+__global__ void __launch_bounds__(256)
+k_coo_warp(int32_t n, int64_t nnz, const int32_t* __restrict__ rows,
+           const int32_t* __restrict__ ci, const V* __restrict__ va, const T* __restrict__ x,
+           EpiStore<T> epi, int64_t nunits, int32_t* __restrict__ carry_row,
+           T* __restrict__ carry_val) {
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int WI = 32 * COO_E;
+    const int lane = threadIdx.x & 31;
+    const int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (u >= nunits) return;  // the whole warp
+    const int64_t k0 = u * WI + (int64_t)lane * COO_E;
+    const bool full = k0 + COO_E <= nnz;
+    int32_t r[COO_E], c[COO_E];
+    V v[COO_E];
+    load_group<COO_E>(rows, k0, nnz, full, r);
+    load_group<COO_E>(ci, k0, nnz, full, c);
+    load_group<COO_E>(va, k0, nnz, full, v);
+    const int32_t rnext = k0 + COO_E < nnz ? __ldg(rows + k0 + COO_E) : INT32_MAX;
+    T xv[COO_E];
+#pragma unroll
+    for (int q = 0; q < COO_E; ++q) xv[q] = k0 + q < nnz ? __ldg(x + c[q]) : T(0);
+    T acc = T(0);
+    int32_t head_row = -1;
+    T head_val = T(0);
+    bool begun_here = false;  // the open run began after a row end in this lane
+    bool open = false;
+#pragma unroll
+    for (int q = 0; q < COO_E; ++q) {
+        if (k0 + q < nnz) {
+            acc = fmadd(cvt<T>(v[q]), xv[q], acc);
+            open = true;
+            const int32_t nr = (q + 1 < COO_E) ? (k0 + q + 1 < nnz ? r[q + 1] : INT32_MAX) : rnext;
+            if (nr != r[q]) {  // row r[q] ends here
+                if (!begun_here) {
+                    head_row = r[q];
+                    head_val = acc;
+                } else {
+                    epi.row(r[q], acc, nullptr);
+                }
+                acc = T(0);
+                begun_here = true;
+                open = false;
+            }
+        }
+    }
+    // the lane's open run (a row that continues in the next lane) is its carry
+    int32_t last = -1;
+#pragma unroll
+    for (int q = 0; q < COO_E; ++q)
+        if (k0 + q < nnz) last = r[q];
+    const int32_t myrow = open ? last : INT32_MAX;
+    T sc = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t orow = __shfl_up_sync(FULL, myrow, o);
+        const T osc = __shfl_up_sync(FULL, sc, o);
+        if (lane >= o && orow == myrow) sc = osc + sc;
+    }
+    const int32_t prow = __shfl_up_sync(FULL, myrow, 1);
+    const T psc = __shfl_up_sync(FULL, sc, 1);
+    if (head_row >= 0) {
+        T vv = head_val;
+        if (lane > 0 && prow == head_row) vv = psc + vv;
+        epi.row(head_row, vv, nullptr);
+    }
+    // the unit's open run: carried by its last lane holding entries
+    const bool has = k0 < nnz;
+    const bool next_has = __shfl_down_sync(FULL, has ? 1 : 0, 1) != 0;
+    if (has && (lane == 31 || !next_has)) {
+        carry_row[u] = myrow != INT32_MAX ? myrow : -1;
+        carry_val[u] = sc;
+    }
+}
+
+// Rows without entries: x_i = 0 (modes 0, 1) or beta x_i (mode 2).
+template <typename T>
+__global__ void k_coo_empty(int32_t count, const int32_t* __restrict__ idx, EpiStore<T> epi) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count;
+         k += (int64_t)gridDim.x * blockDim.x)
+        epi.row(idx[k], T(0), nullptr);
+}
+
 // Adds the block carries to the rows they belong to: the first block of
 // every run of blocks sharing a carry row sums the run in block order.
 template <typename T>

@@ -66,7 +66,8 @@ MATS = {
                                      np.zeros(0)),
 }
 VARIANTS = [("csr", 1, 0, 0), ("csr", 2, 0, 0), ("csr", 0, 0, 0), ("ell", None, 0, 0),
-            ("sellp", None, 32, 1), ("sellp", None, 8, 4), ("sellp", None, 64, 2)]
+            ("sellp", None, 32, 1), ("sellp", None, 8, 4), ("sellp", None, 64, 2),
+            ("coo", None, 0, 0)]
 
 
 @pytest.mark.parametrize("name", list(MATS))
@@ -126,10 +127,10 @@ def test_host_pointer_apply_matches_device():
     assert_rows_close(yh, ref, scale, 1e-13, "host apply_adv")
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2])
-def test_spmv_deterministic(kernel):
+@pytest.mark.parametrize("fmt,kernel", [("csr", 0), ("csr", 1), ("csr", 2), ("coo", None)])
+def test_spmv_deterministic(fmt, kernel):
     m = W.power_law(50000, max_len=4096, seed=9)
-    A = _make(m, "csr", "f64", kernel)
+    A = _make(m, fmt, "f64", kernel)
     x = W.uniform_vector(m.n, 1)
     y1 = _run(A, x, 1.0, 0.0, None, "f64")
     y2 = _run(A, x, 1.0, 0.0, None, "f64")
@@ -158,7 +159,7 @@ def _sampled_check(m, A, dtype, seed):
     assert np.all(np.isfinite(y))
 
 
-@pytest.mark.parametrize("fmt", ["csr", "ell", "sellp"])
+@pytest.mark.parametrize("fmt", ["csr", "ell", "sellp", "coo"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_full_size_stencil_sampled(lap256, fmt, dtype):
     A = _make(lap256, fmt, dtype)
@@ -166,9 +167,42 @@ def test_full_size_stencil_sampled(lap256, fmt, dtype):
     A.close()
 
 
-@pytest.mark.parametrize("fmt", ["csr", "sellp"])
+@pytest.mark.parametrize("fmt", ["csr", "sellp", "coo"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_full_size_powerlaw_sampled(powerlaw4m, fmt, dtype):
     A = _make(powerlaw4m, fmt, dtype)
     _sampled_check(powerlaw4m, A, dtype, 22)
+    A.close()
+
+
+@pytest.mark.parametrize("name", list(MATS))
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_coo_layout_and_oracle_coo_spmv(name, dtype):
+    """The COO handle holds the row of every entry in CSR order (bit-exact
+    against the expanded row pointer), and its apply matches the oracle's
+    COO SpMV (triplets visited in storage order)."""
+    from gpu_util import rounded_values, rounded_vector
+    m = MATS[name]()
+    A = _make(m, "coo", dtype)
+    assert A.desc["format"] == gk.GK_COO and A.desc["spmv_kernel"] == 5
+    e = A.export()
+    rows = np.repeat(np.arange(m.n, dtype=np.int32), np.diff(m.row_ptr))
+    assert np.array_equal(e["row"], rows) and np.array_equal(e["col_idx"], m.col_idx)
+    vals = rounded_values(m, dtype)
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-1, 1, m.ncols)
+    y0 = rng.uniform(-1, 1, m.n)
+    xv, y0v = rounded_vector(x, dtype), rounded_vector(y0, dtype)
+    for alpha, beta in ((1.0, 0.0), (-1.5, 0.5)):
+        y = _run(A, x, alpha, beta, y0 if beta else None, dtype)
+        ref = oracle.spmv_coo(m.n, m.ncols, rows, m.col_idx, vals, xv, alpha, beta,
+                              y=y0v if beta else None)
+        scale = abs(alpha) * oracle.spmv_coo(m.n, m.ncols, rows, m.col_idx, np.abs(vals),
+                                             np.abs(xv)) + abs(beta) * np.abs(y0v)
+        assert_rows_close(y, ref, scale, TOL[dtype], f"coo {name} {dtype} a={alpha} b={beta}")
+    # round trip: COO -> CSR gives the original arrays
+    B = A.convert("csr")
+    eb = B.export()
+    assert np.array_equal(eb["row_ptr"], m.row_ptr) and np.array_equal(eb["col_idx"], m.col_idx)
+    B.close()
     A.close()
