@@ -86,7 +86,7 @@ def build_items(gk, W, dtypes=("f64", "f32")):
     return items, lap, pl
 
 
-KERNEL_NAMES = {0: "k_csr_vector", 1: "k_csr_rowtile", 2: "k_csr_merge_warp", 3: "k_ell",
+KERNEL_NAMES = {0: "k_csr_vector", 1: "k_csr_rowtile", 2: "k_csr_merge_reg", 3: "k_ell",
                 4: "k_sellp", 5: "k_coo_warp"}
 
 

@@ -17,6 +17,14 @@ static bool is_device_ptr(const void* p) {
 template <int E, typename V, typename T>
 static gk_status launch_merge(gk_matrix A, const T* b, const EpiStore<T>& epi, int32_t* crow,
                               T* cval, cudaStream_t s) {
+    if (A->plan.merge_warp == 2) {
+        constexpr size_t smem = MergeRegShape<E>::BYTES;
+        const int64_t units = A->plan.merge_blocks;
+        k_csr_merge_reg<E, V, T><<<(unsigned)((units + 7) / 8), 256, smem, s>>>(
+            A->n, A->nnz, A->row_ptr, A->col, (const V*)A->val, b, epi, A->plan.block_row, units,
+            crow, cval);
+        return GK_OK;
+    }
     if (A->plan.merge_warp) {
         constexpr size_t smem = MergeWarpShape<E, V, T>::BYTES;
         static bool attr = false;

@@ -136,8 +136,10 @@ struct CsrPlan {
     int32_t stages = 0;      // row-tile pipeline depth (0 = as many as fit, max 3)
     int4* tile_desc = nullptr;
     int32_t merge_blocks = 0;
-    int32_t merge_e = 4;     // merge-path items per lane (4, 6 or 8)
-    int32_t merge_warp = 1;  // merge units: 1 one warp (32*E items), 0 one block (256*E)
+    int32_t merge_e = 8;     // merge-path items per lane (4, 6 or 8)
+    int32_t merge_warp = 2;  // merge units: 1 one warp (32*E items, operands staged in
+                             // shared memory), 2 one warp (operands in registers),
+                             // 0 one block (256*E items)
     int32_t* block_row = nullptr;
     int32_t* err = nullptr;  // device word set by a kernel whose bounded wait ran out
 };

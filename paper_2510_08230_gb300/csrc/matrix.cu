@@ -601,17 +601,19 @@ gk_status build_csr_plan(gk_matrix A, cudaStream_t s) {
                                                        P.tile_desc);
         GK_CUDA(cudaGetLastError());
     } else if (kind == 2) {
-        // merge-path items per lane: 4 measured fastest on the Zipf power-law
-        // matrix in FP64 and FP32 (2, 3, 6, 8 were slower); GK_MERGE_E and
-        // GK_MERGE_UNIT=block (256*E items per block, a block-wide carry
-        // scan) select the other instances
-        int E = 4;
+        // Merge-path units: 32*E items per warp.  Default: operands in
+        // registers (k_csr_merge_reg), E = 8 -- measured fastest on the 4M-row
+        // Zipf(1.8) matrix (FP64 424 us; E = 4, 6, 12, 16 and the kernel that
+        // stages operands in shared memory were slower).  GK_MERGE_E and
+        // GK_MERGE_UNIT (reg | warp | block) select the other instances.
+        int E = 8;
         if (const char* e = getenv("GK_MERGE_E")) E = atoi(e);
-        if (E != 4 && E != 6 && E != 8) E = 4;
-        P.merge_warp = 1;
-        if (const char* w = getenv("GK_MERGE_UNIT")) P.merge_warp = strcmp(w, "block") != 0;
+        if (E != 4 && E != 6 && E != 8) E = 8;
+        P.merge_warp = 2;
+        if (const char* w = getenv("GK_MERGE_UNIT"))
+            P.merge_warp = !strcmp(w, "block") ? 0 : !strcmp(w, "warp") ? 1 : 2;
         P.merge_e = E;
-        const int64_t items = (P.merge_warp ? 32 : 256) * (int64_t)E;
+        const int64_t items = (P.merge_warp ? 32 : 256) * (int64_t)E;  // path items per unit
         const int64_t N = (int64_t)A->n + A->nnz;
         P.merge_blocks = (int32_t)std::max<int64_t>(1, (N + items - 1) / items);
         GK_CUDA(dmalloc_t(&P.block_row, (size_t)P.merge_blocks + 1));

@@ -363,6 +363,129 @@ k_csr_merge(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
     }
 }
 
+// Merge path with register operands (apply only): the same 32*E-item warp
+// units and lane pieces as k_csr_merge_warp, but a lane loads the values and
+// columns of its (at most E, contiguous) nonzeros straight from global
+// memory and gathers their x into registers; only the unit's row ends are
+// staged in shared memory (for the lane's binary search and the row ends it
+// meets).  The walk visits the lane's nonzero slots k = 0..E-1 in order and
+// closes every row that ends before slot k first, so each nonzero costs one
+// FMA on registers indexed at compile time.
+template <int E>
+struct MergeRegShape {
+    static constexpr int WI = 32 * E;
+    static constexpr size_t WARP_BYTES = align16((size_t)(WI + 1) * 4);
+    static constexpr size_t BYTES = 8 * WARP_BYTES;
+};
+
+template <int E, typename V, typename T>
+__global__ void __launch_bounds__(256)
+k_csr_merge_reg(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
+                const int32_t* __restrict__ ci, const V* __restrict__ va,
+                const T* __restrict__ x, EpiStore<T> epi, const int32_t* __restrict__ unit_row,
+                int64_t nunits, int32_t* __restrict__ carry_row, T* __restrict__ carry_val) {
+    constexpr int WI = MergeRegShape<E>::WI;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t u = (int64_t)blockIdx.x * 8 + warp;
+    if (u >= nunits) return;  // the whole warp; no block barrier follows
+    int32_t* s_rowend = reinterpret_cast<int32_t*>(smem + (size_t)warp * MergeRegShape<E>::WARP_BYTES);
+    const int64_t N = (int64_t)n + nnz;
+    const int64_t d0 = u * WI;
+    const int64_t d1 = min(d0 + WI, N);
+    int32_t bnd = 0;
+    if (lane < 2) bnd = __ldg(unit_row + u + lane);
+    const int32_t i0 = __shfl_sync(FULL, bnd, 0), i1 = __shfl_sync(FULL, bnd, 1);
+    const int32_t nloc = min(i1 - i0 + 1, n - i0);  // staged row ends
+    for (int k = lane; k < nloc; k += 32) s_rowend[k] = __ldg(rp + i0 + k + 1);
+    __syncwarp();
+    // this lane's start on the path: row i, nonzero j
+    const int64_t dt = min(d0 + (int64_t)lane * E, d1);
+    const int64_t dend = min(dt + E, d1);
+    int32_t lo = 0, hi = max(0, nloc);
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if ((int64_t)s_rowend[mid] + i0 + mid + 1 > dt) hi = mid;
+        else lo = mid + 1;
+    }
+    int32_t i = i0 + lo;
+    const int64_t j0 = dt - i;
+    // the lane's end on the path: row iend, nonzero jend (its nonzeros are [j0, jend))
+    lo = 0;
+    hi = max(0, nloc);
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if ((int64_t)s_rowend[mid] + i0 + mid + 1 > dend) hi = mid;
+        else lo = mid + 1;
+    }
+    const int32_t iend = i0 + lo;
+    const int64_t jend = dend - iend;
+    const int cnt = (int)(jend - j0);  // nonzeros of this lane, 0..E
+    V v[E];
+    T xv[E];
+    {
+        int32_t c[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k)
+            if (k < cnt) {
+                c[k] = __ldcs(ci + j0 + k);
+                v[k] = va[j0 + k];
+            }
+#pragma unroll
+        for (int k = 0; k < E; ++k)
+            if (k < cnt) xv[k] = __ldg(x + c[k]);
+    }
+    T acc = T(0);
+    int32_t head_row = -1;
+    T head_val = T(0);
+    int64_t rend = (i < n) ? (int64_t)s_rowend[i - i0] : 0;
+    // close the rows that end at nonzero position p (before its slot)
+    auto close_until = [&](int64_t p) {
+        while (i < iend && rend <= p) {
+            if (head_row < 0) {
+                head_row = i;
+                head_val = acc;
+            } else {
+                epi.row(i, acc, nullptr);
+            }
+            acc = T(0);
+            ++i;
+            rend = (i < n && i - i0 < nloc) ? (int64_t)s_rowend[i - i0] : 0;
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        if (k < cnt) {
+            close_until(j0 + k);
+            acc = fmadd(cvt<T>(v[k]), xv[k], acc);
+        }
+    }
+    close_until(jend);  // row ends after the last nonzero of the piece
+    // carries: as in k_csr_merge_warp
+    const bool valid = dt < d1;
+    const int32_t myrow = valid ? i : INT32_MAX;
+    T sc = acc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t orow = __shfl_up_sync(FULL, myrow, o);
+        const T osc = __shfl_up_sync(FULL, sc, o);
+        if (lane >= o && orow == myrow) sc = osc + sc;
+    }
+    const int32_t prow = __shfl_up_sync(FULL, myrow, 1);
+    const T psc = __shfl_up_sync(FULL, sc, 1);
+    const int32_t nrow = __shfl_down_sync(FULL, myrow, 1);
+    if (head_row >= 0) {
+        T vv = head_val;
+        if (lane > 0 && prow == head_row) vv = psc + vv;
+        epi.row(head_row, vv, nullptr);
+    }
+    if (valid && (lane == 31 || nrow == INT32_MAX)) {
+        carry_row[u] = (i < n) ? i : -1;
+        carry_val[u] = sc;
+    }
+}
+
 // Shared-memory layout of the warp-level merge kernel, per warp (8 warps a
 // block): values, gathered x, row ends; every array on a 16-byte boundary.
 template <int E, typename V, typename T>
