@@ -282,6 +282,62 @@ def per_iteration_protocol(gk, W, torch, dev, iters=1000):
     return out
 
 
+def abi_overhead(gk, W, torch, dev):
+    """The paper's binding-overhead experiment (Section 5.3) for this
+    library's ctypes binding: SpMV time through the Python binding against
+    the native C driver (native/abi_overhead.c) on the same matrices, both
+    timed per call on a host clock with a device synchronisation after each
+    apply.  P_overhead = (P_native - P_python) / P_native * 100 with P in
+    GFLOP/s (2 flops per nonzero); T_overhead = T_python - T_native."""
+    import tempfile
+    from paper_2510_08230_gb300 import _build
+    exe = _build.build_native()
+    out = {"workload": "2D 5-point Laplacians N x N, FP64, CSR and COO, x on the device; "
+                       "per-call host clock after cudaDeviceSynchronize (paper Section 5.3)",
+           "rows": []}
+    for N in (16, 64, 256, 1024, 2048):
+        m = W.laplacian_2d(N)
+        reps = 2000 if m.nnz < 1e6 else 200
+        with tempfile.NamedTemporaryFile(suffix=".csr", delete=False) as f:
+            np.array([m.n, m.ncols], np.int32).tofile(f)
+            np.array([m.nnz], np.int64).tofile(f)
+            np.asarray(m.row_ptr, np.int32).tofile(f)
+            np.asarray(m.col_idx, np.int32).tofile(f)
+            np.asarray(m.values, np.float64).tofile(f)
+            path = f.name
+        try:
+            for fmt in ("csr", "coo"):
+                A = gk.Matrix.from_csr(m)
+                if fmt == "coo":
+                    B = A.convert("coo")
+                    A.close()
+                    A = B
+                x = torch.zeros(m.n, dtype=torch.float64, device=dev)
+                y = torch.empty_like(x)
+                for _ in range(10):
+                    A.apply(x, y)
+                    torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(reps):
+                    A.apply(x, y)
+                    torch.cuda.synchronize()
+                t_py = (time.perf_counter() - t0) / reps
+                A.close()
+                r = subprocess.run([exe, path, fmt, str(reps)], capture_output=True, text=True,
+                                   timeout=300)
+                t_nat = float(r.stdout.strip()) if r.returncode == 0 else float("nan")
+                flops = 2.0 * m.nnz
+                p_py, p_nat = flops / t_py / 1e9, flops / t_nat / 1e9
+                out["rows"].append({"N": N, "nnz": m.nnz, "format": fmt,
+                                    "t_python_us": round(t_py * 1e6, 2),
+                                    "t_native_us": round(t_nat * 1e6, 2),
+                                    "T_overhead_us": round((t_py - t_nat) * 1e6, 2),
+                                    "P_overhead_pct": round((p_nat - p_py) / p_nat * 100.0, 1)})
+        finally:
+            os.unlink(path)
+    return out
+
+
 def batched_compare(gk, W, torch, dev, count=2048):
     """2048 shifted-rectangle SPD systems (64-4096 rows): one persistent
     launch vs a per-system gk_solve loop, CG to 1e-10, FP64 and FP32."""
@@ -635,12 +691,13 @@ def main():
     del items, step_items
     torch.cuda.empty_cache()
 
-    cg = ir = batched = serving = per_iter = None
+    cg = ir = batched = serving = per_iter = abi = None
     if rank == 0 and not args.no_cg:
         cg = cg_solves_per_s(gk, W, torch, dev)
     if rank == 0 and not args.no_solvers:
         ir = ir_compare(gk, W, torch, dev)
         per_iter = per_iteration_protocol(gk, W, torch, dev)
+        abi = abi_overhead(gk, W, torch, dev)
         batched = batched_compare(gk, W, torch, dev)
     if rank == 0 and not args.no_serving:
         serving = serving_bench(gk, W, torch, dev)
@@ -655,6 +712,7 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "step": step_detail, "sweep": sweep, "roofline": roofline, "cpu_baseline": cpu,
             "e2e": e2e, "cg": cg, "ir_128cubed": ir, "per_iteration_1000": per_iter,
+            "abi_overhead": abi,
             "batched_2048": batched,
             "serving": serving, "clocks": clk,
             "gpu_launches": launches}

@@ -77,5 +77,34 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     return LIB
 
 
+NATIVE_SRC = os.path.join(HERE, "native", "abi_overhead.c")
+NATIVE_BIN = os.path.join(HERE, "native", "abi_overhead")
+
+
+def build_native(force: bool = False) -> str:
+    """The native driver of the binding-overhead experiment (host C code
+    linked against libgk.so and the CUDA runtime)."""
+    lib = build()
+    if not force and os.path.exists(NATIVE_BIN) and \
+            os.path.getmtime(NATIVE_BIN) >= max(os.path.getmtime(NATIVE_SRC), os.path.getmtime(lib)):
+        return NATIVE_BIN
+    cuda = os.path.dirname(os.path.dirname(_nvcc()))
+    libdirs = [d for d in (os.path.join(cuda, "lib64"), os.path.join(cuda, "lib"),
+                           os.path.join(cuda, "targets", "sbsa-linux", "lib"),
+                           os.path.join(cuda, "targets", "x86_64-linux", "lib")) if os.path.isdir(d)]
+    cmd = ["gcc", "-O2", "-std=c11", "-D_POSIX_C_SOURCE=199309L", "-I" + INCLUDE,
+           "-I" + os.path.join(cuda, "include"), NATIVE_SRC, "-o", NATIVE_BIN + ".tmp",
+           "-L" + HERE, "-lgk", "-Wl,-rpath," + HERE]
+    for d in libdirs:
+        cmd += ["-L" + d, "-Wl,-rpath," + d]
+    cmd += ["-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"gcc failed on {NATIVE_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(NATIVE_BIN + ".tmp", NATIVE_BIN)
+    return NATIVE_BIN
+
+
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
+    print(build_native(force=True))

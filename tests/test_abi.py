@@ -97,3 +97,16 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "gk_oracle" not in txt, f
+
+
+def test_native_overhead_driver_builds_and_checks_arguments():
+    """The native side of the binding-overhead measurement compiles against
+    include/gk.h and libgk.so, and rejects bad arguments before any CUDA
+    call (no GPU needed)."""
+    import subprocess
+    from paper_2510_08230_gb300 import _build
+    exe = _build.build_native()
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 1 and "usage" in r.stderr
+    r = subprocess.run([exe, "/nonexistent.csr", "csr", "5"], capture_output=True, text=True)
+    assert r.returncode == 1 and "cannot open" in r.stderr
