@@ -1,0 +1,7 @@
+// solve_f32.cu - the multi-kernel Krylov engine for float values (float vectors).
+#include "solve_engine.cuh"
+
+namespace gk {
+template gk_status solve_mk<float, float>(gk_matrix, const float*, float*, int, bool, double, int32_t,
+                                      int32_t, cudaStream_t, SolveOut*, bool);
+}  // namespace gk
