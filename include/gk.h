@@ -43,7 +43,10 @@ extern "C" {
 
 typedef struct gk_matrix_s* gk_matrix;
 
-typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2 } gk_dtype;
+/* Value types.  F64 and F32 store and compute in their type; BF16 and F16
+ * store matrix values as bfloat16 / IEEE half (F16: |a_ij| <= 65504, larger
+ * values become infinite) and compute in FP32 with FP32 vectors. */
+typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
 
 /* Storage formats.
  * GK_CSR  : row_ptr[n+1], col_idx[nnz], values[nnz]; columns ascending
@@ -194,7 +197,8 @@ typedef struct {
     int32_t max_iters;    /* CG/BiCGSTAB iterations; GMRES Arnoldi steps (all cycles) */
     int32_t krylov_dim;   /* GMRES restart length m (0 = 30, the paper's value); <= 64 */
     int32_t mixed;        /* 0: plain; 1: FP32 inner solves in FP64 iterative
-                             refinement; 2: BF16-stored FP32 inner solves */
+                             refinement; 2: BF16-stored FP32 inner solves;
+                             3: FP16-stored FP32 inner solves */
     double inner_tol;     /* refinement: inner reduction (0 = 1e-5); an inner
                              solve confirms its true residual but gives up
                              after two residual replacements */

@@ -22,7 +22,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgk.so")
 
-GK_F64, GK_F32, GK_BF16 = 0, 1, 2
+GK_F64, GK_F32, GK_BF16, GK_F16 = 0, 1, 2, 3
 GK_CSR, GK_ELL, GK_SELLP, GK_COO = 0, 1, 2, 3
 GK_CG, GK_BICGSTAB, GK_GMRES, GK_CGS = 0, 1, 2, 3
 GK_PRECOND_NONE, GK_PRECOND_JACOBI = 0, 1
@@ -31,7 +31,7 @@ GK_OK, GK_NOT_CONVERGED, GK_BREAKDOWN = 0, 1, 2
 GK_ERR_INVALID, GK_ERR_OOM, GK_ERR_CUDA, GK_ERR_TIMEOUT = -1, -2, -3, -4
 GK_ERR_ZERO_DIAG, GK_ERR_NAN, GK_ERR_UNSUPPORTED = -5, -6, -7
 
-DTYPES = {"f64": GK_F64, "f32": GK_F32, "bf16": GK_BF16}
+DTYPES = {"f64": GK_F64, "f32": GK_F32, "bf16": GK_BF16, "f16": GK_F16}
 FORMATS = {"csr": GK_CSR, "ell": GK_ELL, "sellp": GK_SELLP, "coo": GK_COO}
 METHODS = {"cg": GK_CG, "bicgstab": GK_BICGSTAB, "gmres": GK_GMRES, "cgs": GK_CGS}
 
@@ -326,7 +326,8 @@ class Matrix:
     def export(self):
         """Host copies of the format arrays (dict)."""
         d = self.desc
-        vdt = {GK_F64: np.float64, GK_F32: np.float32, GK_BF16: np.uint16}[d["dtype"]]
+        vdt = {GK_F64: np.float64, GK_F32: np.float32, GK_BF16: np.uint16,
+               GK_F16: np.float16}[d["dtype"]]
         out = {}
         if d["format"] == GK_COO:
             nz = max(d["nnz"], 1)
@@ -402,11 +403,17 @@ def bf16_to_float(bits):
 
 
 def host_values(values, dtype):
-    """Values in the ABI layout of dtype (float32 input only for F32/BF16)."""
+    """Values in the ABI layout of dtype (float32 input only for F32/BF16;
+    float16 values as they are for F16)."""
     dt = _dt(dtype)
     if dt == GK_F64:
         return np.ascontiguousarray(values, dtype=np.float64)
     v = np.asarray(values)
+    if dt == GK_F16:
+        if v.dtype != np.float16:
+            raise TypeError("F16 matrices take float16 values; convert float64 matrices on "
+                            "the device with gk_matrix_convert")
+        return np.ascontiguousarray(v)
     if v.dtype != np.float32:
         raise TypeError("F32/BF16 matrices take float32 values; convert float64 "
                         "matrices on the device with gk_matrix_convert")

@@ -114,6 +114,7 @@ gk_status spmv_dispatch(gk_matrix A, double alpha, const void* b, double beta, v
         case GK_F64: return spmv_typed<double, double>(A, alpha, b, beta, x, s);
         case GK_F32: return spmv_typed<float, float>(A, alpha, b, beta, x, s);
         case GK_BF16: return spmv_typed<__nv_bfloat16, float>(A, alpha, b, beta, x, s);
+        case GK_F16: return spmv_typed<__half, float>(A, alpha, b, beta, x, s);
     }
     return GK_ERR_INVALID;
 }

@@ -586,7 +586,8 @@ static gk_status run_batch(int32_t count, const gk_matrix* As, const void* const
 
 gk_status solve_small(gk_matrix A, const void* b, void* x, const gk_solve_opts* o, cudaStream_t s,
                       SolveOut* out) {
-    if (A->fmt != GK_CSR || o->method == GK_GMRES || o->method == GK_CGS) return GK_ERR_UNSUPPORTED;
+    if (A->fmt != GK_CSR || o->method == GK_GMRES || o->method == GK_CGS || A->dtype == GK_F16)
+        return GK_ERR_UNSUPPORTED;
     gk_solve_info info;
     std::memset(&info, 0, sizeof(info));
     gk_matrix As[1] = {A};
@@ -680,6 +681,7 @@ extern "C" gk_status gk_solve_batched(int32_t count, const gk_matrix* As, const 
     cudaGetDevice(&dev);
     for (int32_t i = 0; i < count; ++i) {
         const gk_matrix A = As[i];
+        if (A && A->dtype == GK_F16) return GK_ERR_UNSUPPORTED;  // multi-kernel engine only
         if (!A || A->fmt != GK_CSR || A->n != A->ncols || A->dtype != As[0]->dtype ||
             A->n > 16384 || (A->n > 0 && (!bs[i] || !xs[i])))
             return GK_ERR_INVALID;

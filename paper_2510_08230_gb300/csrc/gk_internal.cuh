@@ -1,11 +1,13 @@
 // gk_internal.cuh - internal types and helpers of the GB300 sparse library.
 //
-// Value types: F64 stores and computes in double; F32 in float; BF16 stores
-// matrix values as bfloat16 and computes in float (vectors are float).
+// Value types: F64 stores and computes in double; F32 in float; BF16 and F16
+// store matrix values as bfloat16 / IEEE half and compute in float (vectors
+// are float).
 #pragma once
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 #include <stdio.h>
 
@@ -24,14 +26,16 @@ template <gk_dtype D> struct Types;
 template <> struct Types<GK_F64> { using V = double; using T = double; };
 template <> struct Types<GK_F32> { using V = float; using T = float; };
 template <> struct Types<GK_BF16> { using V = __nv_bfloat16; using T = float; };
+template <> struct Types<GK_F16> { using V = __half; using T = float; };
 
 inline size_t value_bytes(gk_dtype d) { return d == GK_F64 ? 8 : d == GK_F32 ? 4 : 2; }
 inline size_t vector_bytes(gk_dtype d) { return d == GK_F64 ? 8 : 4; }
-inline bool valid_dtype(int d) { return d == GK_F64 || d == GK_F32 || d == GK_BF16; }
+inline bool valid_dtype(int d) { return d == GK_F64 || d == GK_F32 || d == GK_BF16 || d == GK_F16; }
 
 __device__ __forceinline__ double to_t(double v, double) { return v; }
 __device__ __forceinline__ float to_t(float v, float) { return v; }
 __device__ __forceinline__ float to_t(__nv_bfloat16 v, float) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_t(__half v, float) { return __half2float(v); }
 
 // conversions between value types (round to nearest even when narrowing)
 template <typename O> struct Cvt;
@@ -39,16 +43,30 @@ template <> struct Cvt<double> {
     static __device__ __forceinline__ double f(double v) { return v; }
     static __device__ __forceinline__ double f(float v) { return (double)v; }
     static __device__ __forceinline__ double f(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+    static __device__ __forceinline__ double f(__half v) { return (double)__half2float(v); }
 };
 template <> struct Cvt<float> {
     static __device__ __forceinline__ float f(double v) { return __double2float_rn(v); }
     static __device__ __forceinline__ float f(float v) { return v; }
     static __device__ __forceinline__ float f(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ float f(__half v) { return __half2float(v); }
 };
 template <> struct Cvt<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 f(double v) { return __double2bfloat16(v); }
     static __device__ __forceinline__ __nv_bfloat16 f(float v) { return __float2bfloat16_rn(v); }
     static __device__ __forceinline__ __nv_bfloat16 f(__nv_bfloat16 v) { return v; }
+    static __device__ __forceinline__ __nv_bfloat16 f(__half v) {
+        return __float2bfloat16_rn(__half2float(v));
+    }
+};
+// IEEE half: values beyond +-65504 round to +-inf (the caller's range)
+template <> struct Cvt<__half> {
+    static __device__ __forceinline__ __half f(double v) { return __double2half(v); }
+    static __device__ __forceinline__ __half f(float v) { return __float2half_rn(v); }
+    static __device__ __forceinline__ __half f(__half v) { return v; }
+    static __device__ __forceinline__ __half f(__nv_bfloat16 v) {
+        return __float2half_rn(__bfloat162float(v));
+    }
 };
 template <typename O, typename I>
 __device__ __forceinline__ O cvt(I v) { return Cvt<O>::f(v); }
@@ -58,9 +76,11 @@ template <typename V> struct AccOf;
 template <> struct AccOf<double> { using type = double; };
 template <> struct AccOf<float> { using type = float; };
 template <> struct AccOf<__nv_bfloat16> { using type = float; };
+template <> struct AccOf<__half> { using type = float; };
 __device__ __forceinline__ double to_acc(double v) { return v; }
 __device__ __forceinline__ float to_acc(float v) { return v; }
 __device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_acc(__half v) { return __half2float(v); }
 template <typename O, typename A>
 __device__ __forceinline__ O from_acc(A v) { return Cvt<O>::f(v); }
 
@@ -74,6 +94,7 @@ __device__ __forceinline__ float ldv(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ldv(const __nv_bfloat16* p) {
     return __bfloat162float(__ldg(p));
 }
+__device__ __forceinline__ float ldv(const __half* p) { return __half2float(__ldg(p)); }
 
 // streaming loads for data touched once (do not keep in L1)
 __device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
@@ -81,6 +102,10 @@ __device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_stream(const __nv_bfloat16* p) {
     unsigned short u = __ldcs(reinterpret_cast<const unsigned short*>(p));
     return __bfloat162float(__ushort_as_bfloat16(u));
+}
+__device__ __forceinline__ float ld_stream(const __half* p) {
+    unsigned short u = __ldcs(reinterpret_cast<const unsigned short*>(p));
+    return __half2float(__ushort_as_half(u));
 }
 __device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
 

@@ -472,6 +472,7 @@ static gk_status dispatch_dtype(gk_dtype d, F&& f) {
         case GK_F64: return f(Types<GK_F64>{});
         case GK_F32: return f(Types<GK_F32>{});
         case GK_BF16: return f(Types<GK_BF16>{});
+        case GK_F16: return f(Types<GK_F16>{});
     }
     return GK_ERR_INVALID;
 }

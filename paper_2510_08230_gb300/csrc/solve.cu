@@ -53,6 +53,7 @@ gk_status ensure_jacobi(gk_matrix A, cudaStream_t s) {
     if (A->n > 0) {
         if (A->dtype == GK_F64) go(double(), double());
         else if (A->dtype == GK_F32) go(float(), float());
+        else if (A->dtype == GK_F16) go(__half(), float());
         else go(__nv_bfloat16(), float());
     }
     GK_CUDA(cudaGetLastError());
@@ -185,7 +186,7 @@ static gk_status check_opts(gk_matrix A, const gk_solve_opts* o) {
     if (o->precond != GK_PRECOND_NONE && o->precond != GK_PRECOND_JACOBI) return GK_ERR_INVALID;
     if (!(o->tol >= 0.0) || o->max_iters < 0) return GK_ERR_INVALID;
     if (o->krylov_dim < 0 || o->krylov_dim > MAXM) return GK_ERR_INVALID;
-    if (o->mixed < 0 || o->mixed > 2) return GK_ERR_INVALID;
+    if (o->mixed < 0 || o->mixed > 3) return GK_ERR_INVALID;
     if (o->mixed && A->dtype != GK_F64) return GK_ERR_INVALID;
     if (o->engine < 0 || o->engine > 3) return GK_ERR_INVALID;
     if (A->n != A->ncols) return GK_ERR_INVALID;
@@ -203,13 +204,13 @@ static gk_status solve_plain(gk_matrix A, const void* b, void* x, const gk_solve
 }
 
 // FP64 iterative refinement: r = b - A x in FP64; inner solve of
-// A_low d = r (FP32 or BF16-stored values, FP32 vectors) to inner_tol;
+// A_low d = r (FP32, BF16- or FP16-stored values, FP32 vectors) to inner_tol;
 // x += d in FP64; until ||b - A x|| <= tol ||b||.
 static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solve_opts* o,
                           cudaStream_t s, SolveOut* out, int32_t* outer) {
     const int32_t n = A->n;
     gk_matrix L = nullptr;
-    GK_TRY(get_lowp(A, o->mixed == 2 ? GK_BF16 : GK_F32, s, &L));
+    GK_TRY(get_lowp(A, o->mixed == 2 ? GK_BF16 : o->mixed == 3 ? GK_F16 : GK_F32, s, &L));
     GK_TRY(solve_matrix(L, s, &L));  // layout of the inner SpMV
     gk_matrix A64 = nullptr;
     GK_TRY(solve_matrix(A, s, &A64));  // layout of the outer FP64 residual
@@ -279,6 +280,9 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
         if (L->dtype == GK_F32)
             GK_TRY((solve_mk<float, float>(L, r32, d32, o->method, prec, inner_tol, left, m, s, &io,
                                            true)));
+        else if (L->dtype == GK_F16)
+            GK_TRY((solve_mk<__half, float>(L, r32, d32, o->method, prec, inner_tol, left, m, s,
+                                            &io, true)));
         else
             GK_TRY((solve_mk<__nv_bfloat16, float>(L, r32, d32, o->method, prec, inner_tol, left, m,
                                                    s, &io, true)));
@@ -346,6 +350,8 @@ extern "C" gk_status gk_solve(gk_matrix A, const void* b, void* x, const gk_solv
             st = solve_plain<double, double>(A, b, x, opts, s, &out);
         } else if (A->dtype == GK_F32) {
             st = solve_plain<float, float>(A, b, x, opts, s, &out);
+        } else if (A->dtype == GK_F16) {
+            st = solve_plain<__half, float>(A, b, x, opts, s, &out);
         } else {
             st = solve_plain<__nv_bfloat16, float>(A, b, x, opts, s, &out);
         }

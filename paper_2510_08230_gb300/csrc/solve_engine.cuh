@@ -1,7 +1,8 @@
 // solve_engine.cuh - the multi-kernel Krylov engine: device state, the fused
 // solver kernels and epilogues, and solve_mk<V, T>, one solve of CG,
 // BiCGSTAB, CGS or GMRES(m).  solve_mk is instantiated once per value type
-// in its own translation unit (solve_f64.cu, solve_f32.cu, solve_bf16.cu) so
+// in its own translation unit (solve_f64.cu, solve_f32.cu, solve_bf16.cu,
+// solve_f16.cu) so
 // the types compile in parallel; solve.cu holds the host-side helpers and
 // the entry points.
 //
@@ -1662,5 +1663,8 @@ extern template gk_status solve_mk<float, float>(gk_matrix, const float*, float*
 extern template gk_status solve_mk<__nv_bfloat16, float>(gk_matrix, const float*, float*, int,
                                                          bool, double, int32_t, int32_t,
                                                          cudaStream_t, SolveOut*, bool);
+extern template gk_status solve_mk<__half, float>(gk_matrix, const float*, float*, int, bool,
+                                                  double, int32_t, int32_t, cudaStream_t,
+                                                  SolveOut*, bool);
 
 }  // namespace gk

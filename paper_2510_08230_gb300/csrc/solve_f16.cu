@@ -1,0 +1,7 @@
+// solve_f16.cu - the multi-kernel Krylov engine for IEEE half values (float vectors).
+#include "solve_engine.cuh"
+
+namespace gk {
+template gk_status solve_mk<__half, float>(gk_matrix, const float*, float*, int, bool, double,
+                                           int32_t, int32_t, cudaStream_t, SolveOut*, bool);
+}  // namespace gk

@@ -816,6 +816,7 @@ template <typename V> struct Pair2;
 template <> struct Pair2<double> { using type = double2; };
 template <> struct Pair2<float> { using type = float2; };
 template <> struct Pair2<__nv_bfloat16> { using type = __nv_bfloat162; };
+template <> struct Pair2<__half> { using type = __half2; };
 
 template <typename T, typename P>
 __device__ __forceinline__ void unpack2(const P& p, T& a, T& b) {

@@ -2,8 +2,8 @@
 arrays to the device, and the per-row SpMV tolerance against the oracle.
 
 Tolerance (per row i): |y_i - y_oracle_i| <= tol * (|alpha| sum_j |a_ij x_j|
-+ |beta| |y_i|), tol = 1e-13 for FP64 and 1e-5 for FP32 / BF16-stored
-values (the oracle then uses the FP32- or BF16-rounded A and x in FP64).
++ |beta| |y_i|), tol = 1e-13 for FP64 and 1e-5 for FP32 / BF16- / FP16-
+stored values (the oracle then uses the rounded A and FP32 x in FP64).
 It is scaled by the absolute row sum because stencil rows cancel to ~0.
 """
 import numpy as np
@@ -12,7 +12,7 @@ import oracle
 import paper_2510_08230_gb300 as gk
 from paper_2510_08230_gb300 import workloads as W
 
-TOL = {"f64": 1e-13, "f32": 1e-5, "bf16": 1e-5}
+TOL = {"f64": 1e-13, "f32": 1e-5, "bf16": 1e-5, "f16": 1e-5}
 
 
 def ensure_built():
@@ -48,6 +48,8 @@ def rounded_values(m, dtype):
         return v.astype(np.float64)
     if v.dtype == np.float64 and dtype == "bf16":
         return bf16_round_f64(v)
+    if dtype == "f16":  # IEEE half, one rounding to nearest even from the input type
+        return v.astype(np.float16).astype(np.float64)
     f = v.astype(np.float32)
     if dtype == "f32":
         return f.astype(np.float64)

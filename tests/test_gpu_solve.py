@@ -234,7 +234,7 @@ def test_fp32_solve(method):
     assert oracle.true_rel_residual(m, b, x) <= 2e-5  # FP32-rounded A differs from A
 
 
-@pytest.mark.parametrize("mixed", [1, 2])
+@pytest.mark.parametrize("mixed", [1, 2, 3])
 @pytest.mark.parametrize("method", ["cg", "gmres", "cgs"])
 def test_mixed_precision_refinement(mixed, method):
     """FP32 (or BF16-stored) inner solves inside FP64 refinement reach the
@@ -330,3 +330,19 @@ def test_solve_format_selection(monkeypatch):
     monkeypatch.setenv("GK_SOLVE_FORMAT", "timed")
     fmt5, x5, info5 = _solve_format(m)
     assert fmt5 in (gk.GK_CSR, gk.GK_ELL) and info5["return"] == gk.GK_OK
+
+
+@pytest.mark.parametrize("method", ["cg", "bicgstab", "gmres", "cgs"])
+def test_f16_stored_solve(method):
+    """A solve on FP16-stored values (FP32 vectors) reaches its tolerance on
+    the FP16-rounded system (residual recomputed by the oracle with the
+    rounded values); the single-block and cluster engines refuse FP16."""
+    m, b = CASES["diff3d_12"]()
+    x, info = _gpu_solve(m, b, method, 1, 1e-5, dtype="f16")
+    assert info["return"] == gk.GK_OK, info
+    m16 = W.CSR(m.n, m.ncols, m.row_ptr, m.col_idx,
+                np.asarray(m.values, np.float64).astype(np.float16).astype(np.float64))
+    assert oracle.true_rel_residual(m16, b, x) <= 2e-5
+    if method == "cg":
+        _, i2 = _gpu_solve(m, b, method, 1, 1e-5, dtype="f16", engine=2)
+        assert i2["return"] == gk.GK_ERR_UNSUPPORTED

@@ -72,7 +72,7 @@ VARIANTS = [("csr", 1, 0, 0), ("csr", 2, 0, 0), ("csr", 0, 0, 0), ("ell", None, 
 
 @pytest.mark.parametrize("name", list(MATS))
 @pytest.mark.parametrize("fmt,kernel,S,f", VARIANTS)
-@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16", "f16"])
 def test_spmv_matches_oracle(name, fmt, kernel, S, f, dtype):
     m = MATS[name]()
     if fmt == "ell" and m.nnz and m.row_lengths().max() * m.n > 50_000_000:
@@ -205,4 +205,23 @@ def test_coo_layout_and_oracle_coo_spmv(name, dtype):
     eb = B.export()
     assert np.array_equal(eb["row_ptr"], m.row_ptr) and np.array_equal(eb["col_idx"], m.col_idx)
     B.close()
+    A.close()
+
+
+@pytest.mark.parametrize("fmt", ["csr", "ell", "sellp", "coo"])
+def test_f16_values_round_once_to_nearest_even(fmt):
+    """FP64 values converted on the device to IEEE half are the correctly
+    rounded halves (numpy's float64 -> float16), bit for bit, in every
+    layout; the padding of ELL / SELL-P stays +0.0."""
+    m = W.power_law(3000, max_len=300, seed=4)
+    A = _make(m, fmt, "f16")
+    e = A.export()
+    want = np.asarray(m.values, np.float64).astype(np.float16)
+    got = e["values"]
+    if fmt in ("csr", "coo"):
+        assert np.array_equal(got.view(np.uint16), want.view(np.uint16))
+    else:
+        assert np.array_equal(np.sort(got[e["col"] >= 0].view(np.uint16)),
+                              np.sort(want.view(np.uint16)))
+        assert np.all(got[e["col"] < 0].view(np.uint16) == 0)
     A.close()
