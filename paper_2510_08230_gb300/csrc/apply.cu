@@ -66,14 +66,15 @@ static gk_status spmv_typed(gk_matrix A, double alpha, const void* b, double bet
             T* cval = reinterpret_cast<T*>(static_cast<char*>(A->carry.ptr) +
                                            (((size_t)units * sizeof(int32_t) + 15) & ~(size_t)15));
             const unsigned g = (unsigned)((units + 7) / 8);
-            if (E == 8)
-                k_coo_warp<8, V, T><<<g, 256, 0, s>>>(A->n, A->nnz, A->coo_row, A->col,
-                                                      (const V*)A->val, static_cast<const T*>(b),
-                                                      epi, units, crow, cval);
-            else
-                k_coo_warp<4, V, T><<<g, 256, 0, s>>>(A->n, A->nnz, A->coo_row, A->col,
-                                                      (const V*)A->val, static_cast<const T*>(b),
-                                                      epi, units, crow, cval);
+            const int32_t* rw = A->coo_row;
+            const V* vals = (const V*)A->val;
+            const T* bt = static_cast<const T*>(b);
+            switch (E) {
+                case 8: k_coo_warp<2, V, T><<<g, 256, 0, s>>>(A->n, A->nnz, rw, A->col, vals, bt, epi, units, crow, cval); break;
+                case 12: k_coo_warp<3, V, T><<<g, 256, 0, s>>>(A->n, A->nnz, rw, A->col, vals, bt, epi, units, crow, cval); break;
+                case 16: k_coo_warp<4, V, T><<<g, 256, 0, s>>>(A->n, A->nnz, rw, A->col, vals, bt, epi, units, crow, cval); break;
+                default: k_coo_warp<1, V, T><<<g, 256, 0, s>>>(A->n, A->nnz, rw, A->col, vals, bt, epi, units, crow, cval); break;
+            }
             const unsigned fg =
                 (unsigned)std::max<int64_t>(1, std::min<int64_t>((units + 255) / 256, 4096));
             k_csr_merge_fixup<T><<<fg, 256, 0, s>>>((int32_t)units, crow, cval, static_cast<T*>(x),

@@ -197,7 +197,7 @@ struct gk_matrix_s {
     int32_t* coo_row = nullptr;     // row of every entry
     int32_t* empty_rows = nullptr;  // rows without entries
     int32_t n_empty = 0;
-    int coo_e = 4;                  // entries per lane of the COO kernel (4 or 8)
+    int coo_e = 4;                  // entries per lane of the COO kernel (4, 8, 12 or 16)
     // ELL
     int32_t K = 0;
     int64_t stride = 0;

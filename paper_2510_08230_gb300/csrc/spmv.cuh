@@ -635,9 +635,9 @@ k_csr_merge_warp(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
 }
 
 // COO SpMV (apply only): triplets sorted by (row, col).  The nonzeros are
-// cut into units of 32*COO_E per warp, COO_E consecutive triplets per lane,
-// read with 16-byte loads (no shared-memory staging: the row index comes
-// with every entry).  A lane sums each run of equal rows; a row ends where the next
+// cut into units of 32*4H per warp, 4H consecutive triplets per lane, read
+// in groups of 4 with 16-byte loads (no shared-memory staging: the row index
+// comes with every entry).  A lane sums each run of equal rows; a row ends where the next
 // triplet (in this lane, the next lane, the next unit, or none) has another
 // row.  The first row a lane ends may have begun in earlier lanes: it adds
 // their carries, combined with the 5-level segmented shuffle scan used by
@@ -664,57 +664,64 @@ __device__ __forceinline__ void load_group(const V* __restrict__ p, int64_t k, i
     }
 }
 
-template <int COO_E, typename V, typename T>
+template <int H, typename V, typename T>
 __global__ void __launch_bounds__(256)
 k_coo_warp(int32_t n, int64_t nnz, const int32_t* __restrict__ rows,
            const int32_t* __restrict__ ci, const V* __restrict__ va, const T* __restrict__ x,
            EpiStore<T> epi, int64_t nunits, int32_t* __restrict__ carry_row,
            T* __restrict__ carry_val) {
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int WI = 32 * COO_E;
+    constexpr int G = 4;           // triplets per 16-byte group load
+    constexpr int EPL = G * H;     // triplets per lane
+    constexpr int WI = 32 * EPL;   // triplets per warp unit
     const int lane = threadIdx.x & 31;
     const int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (u >= nunits) return;  // the whole warp
-    const int64_t k0 = u * WI + (int64_t)lane * COO_E;
-    const bool full = k0 + COO_E <= nnz;
-    int32_t r[COO_E], c[COO_E];
-    V v[COO_E];
-    load_group<COO_E>(rows, k0, nnz, full, r);
-    load_group<COO_E>(ci, k0, nnz, full, c);
-    load_group<COO_E>(va, k0, nnz, full, v);
-    const int32_t rnext = k0 + COO_E < nnz ? __ldg(rows + k0 + COO_E) : INT32_MAX;
-    T xv[COO_E];
-#pragma unroll
-    for (int q = 0; q < COO_E; ++q) xv[q] = k0 + q < nnz ? __ldg(x + c[q]) : T(0);
+    const int64_t k0 = u * WI + (int64_t)lane * EPL;
     T acc = T(0);
     int32_t head_row = -1;
     T head_val = T(0);
     bool begun_here = false;  // the open run began after a row end in this lane
     bool open = false;
+    int32_t last = -1;
+    // groups of 4 triplets, one after the other (few registers live), the
+    // walk state carried across groups
+#pragma unroll 1
+    for (int g = 0; g < H; ++g) {
+        const int64_t kg = k0 + (int64_t)g * G;
+        if (kg >= nnz) break;
+        const bool full = kg + G <= nnz;
+        int32_t r[G], c[G];
+        V v[G];
+        load_group<G>(rows, kg, nnz, full, r);
+        load_group<G>(ci, kg, nnz, full, c);
+        load_group<G>(va, kg, nnz, full, v);
+        const int32_t rnext = kg + G < nnz ? __ldg(rows + kg + G) : INT32_MAX;
+        T xv[G];
 #pragma unroll
-    for (int q = 0; q < COO_E; ++q) {
-        if (k0 + q < nnz) {
-            acc = fmadd(cvt<T>(v[q]), xv[q], acc);
-            open = true;
-            const int32_t nr = (q + 1 < COO_E) ? (k0 + q + 1 < nnz ? r[q + 1] : INT32_MAX) : rnext;
-            if (nr != r[q]) {  // row r[q] ends here
-                if (!begun_here) {
-                    head_row = r[q];
-                    head_val = acc;
-                } else {
-                    epi.row(r[q], acc, nullptr);
+        for (int q = 0; q < G; ++q) xv[q] = kg + q < nnz ? __ldg(x + c[q]) : T(0);
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            if (kg + q < nnz) {
+                acc = fmadd(cvt<T>(v[q]), xv[q], acc);
+                open = true;
+                last = r[q];
+                const int32_t nr = (q + 1 < G) ? (kg + q + 1 < nnz ? r[q + 1] : INT32_MAX) : rnext;
+                if (nr != r[q]) {  // row r[q] ends here
+                    if (!begun_here) {
+                        head_row = r[q];
+                        head_val = acc;
+                    } else {
+                        epi.row(r[q], acc, nullptr);
+                    }
+                    acc = T(0);
+                    begun_here = true;
+                    open = false;
                 }
-                acc = T(0);
-                begun_here = true;
-                open = false;
             }
         }
     }
     // the lane's open run (a row that continues in the next lane) is its carry
-    int32_t last = -1;
-#pragma unroll
-    for (int q = 0; q < COO_E; ++q)
-        if (k0 + q < nnz) last = r[q];
     const int32_t myrow = open ? last : INT32_MAX;
     T sc = acc;
 #pragma unroll
