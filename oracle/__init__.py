@@ -55,7 +55,7 @@ _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 class Opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("max_iters", ctypes.c_int32),
-                ("krylov_dim", ctypes.c_int32)]
+                ("krylov_dim", ctypes.c_int32), ("block_size", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -92,6 +92,10 @@ def _declare(L):
     L.or_sellp_to_csr.restype = i64
     L.or_jacobi_gen.argtypes = [i32, _i32p, _i32p, _f64p, _f64p]
     L.or_jacobi_gen.restype = ctypes.c_int
+    L.or_block_jacobi_gen.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p]
+    L.or_block_jacobi_gen.restype = ctypes.c_int
+    L.or_block_jacobi_apply.argtypes = [i32, i32, _f64p, _f64p, _f64p]
+    L.or_block_jacobi_apply.restype = None
     for name in ("or_cg", "or_bicgstab", "or_gmres", "or_cgs"):
         f = getattr(L, name)
         f.argtypes = [i32, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.POINTER(Opts),
@@ -217,11 +221,30 @@ def jacobi(m):
     return d[:m.n]
 
 
+def block_jacobi(m, bs):
+    """Inverted diagonal blocks of bs rows, shape (nblocks, bs, bs); raises
+    ZeroDivisionError on a singular block."""
+    nb = (m.n + bs - 1) // bs
+    out = np.zeros(max(nb, 1) * bs * bs)
+    st = lib().or_block_jacobi_gen(m.n, _i32(m.row_ptr), _i32(m.col_idx), _f64(m.values), bs, out)
+    if st != OK:
+        raise ZeroDivisionError("singular diagonal block")
+    return out[:nb * bs * bs].reshape(nb, bs, bs)
+
+
+def block_jacobi_apply(n, bs, binv, r):
+    z = np.zeros(n)
+    lib().or_block_jacobi_apply(n, bs, _f64(binv).reshape(-1), _f64(r), z)
+    return z
+
+
 def solve(m, b, x0=None, method=CG, precond=0, tol=1e-10, max_iters=1000,
-          krylov_dim=30, history=False):
-    """Runs CG / BiCGSTAB / GMRES(m) / CGS.  Returns (x, info dict[, history])."""
+          krylov_dim=30, history=False, block_size=0):
+    """Runs CG / BiCGSTAB / GMRES(m) / CGS; precond 0 none, 1 Jacobi,
+    2 block-Jacobi with `block_size` rows per block.  Returns (x, info
+    dict[, history])."""
     x = np.zeros(m.n) if x0 is None else _f64(x0).copy()
-    o = Opts(method, precond, tol, max_iters, krylov_dim)
+    o = Opts(method, precond, tol, max_iters, krylov_dim, block_size)
     info = Info()
     hist = np.full(max_iters + 2, np.nan) if history else None
     f = {CG: lib().or_cg, BICGSTAB: lib().or_bicgstab, GMRES: lib().or_gmres,

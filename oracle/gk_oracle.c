@@ -353,16 +353,87 @@ int or_jacobi_gen(int32_t n, const int32_t* rp, const int32_t* ci,
     return OR_OK;
 }
 
+/* Block-Jacobi (the config solver's preconditioner with max_block_size > 1,
+ * Listing 2): the diagonal blocks of A over bs consecutive rows (the last
+ * block may be smaller), each inverted by Gauss-Jordan elimination with
+ * partial pivoting on the dense block.  binv holds block b's inverse at
+ * binv[b*bs*bs + i*bs + j] (unused slots of a short last block are 0).
+ * A block with no nonzero pivot left is singular: OR_ERR_ZERO_DIAG. */
+int or_block_jacobi_gen(int32_t n, const int32_t* rp, const int32_t* ci,
+                        const double* va, int32_t bs, double* binv)
+{
+    if (bs < 1) return OR_ERR_INVALID;
+    const int32_t nb = (n + bs - 1) / bs;
+    double* a = (double*)malloc(sizeof(double) * (size_t)bs * bs);
+    double* e = (double*)malloc(sizeof(double) * (size_t)bs * bs);
+    int status = OR_OK;
+    for (int32_t kb = 0; kb < nb && status == OR_OK; ++kb) {
+        const int32_t r0 = kb * bs;
+        const int32_t m = (n - r0 < bs) ? n - r0 : bs;
+        for (int32_t i = 0; i < m * m; ++i) { a[i] = 0.0; e[i] = 0.0; }
+        for (int32_t i = 0; i < m; ++i) {
+            e[i * m + i] = 1.0;
+            for (int32_t k = rp[r0 + i]; k < rp[r0 + i + 1]; ++k) {
+                const int32_t j = ci[k] - r0;
+                if (j >= 0 && j < m) a[i * m + j] += va[k];
+            }
+        }
+        for (int32_t c = 0; c < m; ++c) {
+            int32_t piv = c;
+            for (int32_t r = c + 1; r < m; ++r)
+                if (fabs(a[r * m + c]) > fabs(a[piv * m + c])) piv = r;
+            if (a[piv * m + c] == 0.0) { status = OR_ERR_ZERO_DIAG; break; }
+            if (piv != c)
+                for (int32_t j = 0; j < m; ++j) {
+                    double t = a[c * m + j]; a[c * m + j] = a[piv * m + j]; a[piv * m + j] = t;
+                    t = e[c * m + j]; e[c * m + j] = e[piv * m + j]; e[piv * m + j] = t;
+                }
+            const double d = a[c * m + c];
+            for (int32_t j = 0; j < m; ++j) { a[c * m + j] /= d; e[c * m + j] /= d; }
+            for (int32_t r = 0; r < m; ++r) {
+                if (r == c) continue;
+                const double f = a[r * m + c];
+                if (f == 0.0) continue;
+                for (int32_t j = 0; j < m; ++j) {
+                    a[r * m + j] -= f * a[c * m + j];
+                    e[r * m + j] -= f * e[c * m + j];
+                }
+            }
+        }
+        double* out = binv + (size_t)kb * bs * bs;
+        for (int32_t i = 0; i < bs * bs; ++i) out[i] = 0.0;
+        for (int32_t i = 0; i < m; ++i)
+            for (int32_t j = 0; j < m; ++j) out[i * bs + j] = e[i * m + j];
+    }
+    free(a);
+    free(e);
+    return status;
+}
+
+/* z = binv r block by block */
+void or_block_jacobi_apply(int32_t n, int32_t bs, const double* binv, const double* r, double* z)
+{
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t kb = i / bs, r0 = kb * bs, li = i - r0;
+        const int32_t m = (n - r0 < bs) ? n - r0 : bs;
+        const double* row = binv + (size_t)kb * bs * bs + (size_t)li * bs;
+        double s = 0.0;
+        for (int32_t j = 0; j < m; ++j) s += row[j] * r[r0 + j];
+        z[i] = s;
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* Solvers                                                             */
 /* ------------------------------------------------------------------ */
 
 typedef struct {
     int32_t method;     /* 0 CG, 1 BiCGSTAB, 2 GMRES, 3 CGS */
-    int32_t precond;    /* 0 none, 1 Jacobi */
+    int32_t precond;    /* 0 none, 1 Jacobi, 2 block-Jacobi */
     double tol;         /* relative to ||b||_2 ("rhs_norm" baseline) */
     int32_t max_iters;  /* CG: iterations; BiCGSTAB: iterations; GMRES: Arnoldi steps */
     int32_t krylov_dim; /* GMRES restart length m */
+    int32_t block_size; /* block-Jacobi (precond 2): rows per diagonal block */
 } or_opts;
 
 typedef struct {
@@ -393,9 +464,46 @@ static void resid(const or_mat* A, const double* b, const double* x, double* r)
 }
 
 /* z = M^{-1} r (identity without a preconditioner) */
-static void prec(int32_t n, const double* dinv, const double* r, double* z)
+/* Preconditioner M^{-1}: none (kind 0), Jacobi (1: data = 1/a_ii) or
+ * block-Jacobi (2: data = the inverted diagonal blocks of bs rows). */
+typedef struct {
+    int32_t kind;
+    int32_t bs;
+    double* data;
+} or_prec;
+
+static int prec_setup(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
+                      const or_opts* o, or_prec* P)
 {
-    for (int32_t i = 0; i < n; ++i) z[i] = dinv ? dinv[i] * r[i] : r[i];
+    P->kind = o->precond;
+    P->bs = o->block_size;
+    P->data = NULL;
+    if (P->kind == 1) {
+        P->data = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        if (or_jacobi_gen(n, rp, ci, va, P->data) != OR_OK) {
+            free(P->data);
+            return OR_ERR_ZERO_DIAG;
+        }
+    } else if (P->kind == 2) {
+        if (P->bs < 1) return OR_ERR_INVALID;
+        const int64_t nb = ((int64_t)n + P->bs - 1) / P->bs;
+        P->data = (double*)malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1) * P->bs * P->bs);
+        const int st = or_block_jacobi_gen(n, rp, ci, va, P->bs, P->data);
+        if (st != OR_OK) {
+            free(P->data);
+            return st;
+        }
+    }
+    return OR_OK;
+}
+
+static void prec(int32_t n, const or_prec* P, const double* r, double* z)
+{
+    if (P->kind == 2) {
+        or_block_jacobi_apply(n, P->bs, P->data, r, z);
+        return;
+    }
+    for (int32_t i = 0; i < n; ++i) z[i] = P->kind == 1 ? P->data[i] * r[i] : r[i];
 }
 
 /* rec_hist (optional, max_iters + 1 entries): relative recurrence residual
@@ -415,18 +523,15 @@ int or_cg(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
 {
     or_mat A = {n, rp, ci, va};
     memset(info, 0, sizeof(*info));
-    double* dinv = NULL;
-    if (o->precond == 1) {
-        dinv = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-        if (or_jacobi_gen(n, rp, ci, va, dinv) != OR_OK) {
-            free(dinv);
-            return info->status = OR_ERR_ZERO_DIAG;
-        }
+    or_prec P;
+    {
+        const int pst = prec_setup(n, rp, ci, va, o, &P);
+        if (pst != OR_OK) return info->status = pst;
     }
     double bnorm = nrm2(n, b);
     if (bnorm == 0.0) {
         for (int32_t i = 0; i < n; ++i) x[i] = 0.0;
-        free(dinv);
+        free(P.data);
         return info->status = OR_OK;
     }
     double thr = o->tol * bnorm;
@@ -439,7 +544,7 @@ int or_cg(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
     int status = OR_NOT_CONVERGED;
     if (!isfinite(rn)) status = OR_ERR_NAN;
     else if (rn <= thr) status = OR_OK;
-    prec(n, dinv, r, z);
+    prec(n, &P, r, z);
     memcpy(p, z, sz);
     double rho = dot(n, r, z);
     int32_t k = 0;
@@ -462,12 +567,12 @@ int or_cg(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
             if (tn <= thr) { status = OR_OK; break; }
             /* residual replacement: restart from the current x */
             info->restarts++;
-            prec(n, dinv, r, z);
+            prec(n, &P, r, z);
             memcpy(p, z, sz);
             rho = dot(n, r, z);
             continue;
         }
-        prec(n, dinv, r, z);
+        prec(n, &P, r, z);
         double rho_new = dot(n, r, z);
         double beta = rho_new / rho;
         rho = rho_new;
@@ -476,7 +581,7 @@ int or_cg(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
     info->iters = k;
     resid(&A, b, x, q);
     info->rel_res_true = nrm2(n, q) / bnorm;
-    free(r); free(z); free(p); free(q); free(dinv);
+    free(r); free(z); free(p); free(q); free(P.data);
     return info->status = status;
 }
 
@@ -497,18 +602,15 @@ int or_bicgstab(int32_t n, const int32_t* rp, const int32_t* ci,
 {
     or_mat A = {n, rp, ci, va};
     memset(info, 0, sizeof(*info));
-    double* dinv = NULL;
-    if (o->precond == 1) {
-        dinv = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-        if (or_jacobi_gen(n, rp, ci, va, dinv) != OR_OK) {
-            free(dinv);
-            return info->status = OR_ERR_ZERO_DIAG;
-        }
+    or_prec P;
+    {
+        const int pst = prec_setup(n, rp, ci, va, o, &P);
+        if (pst != OR_OK) return info->status = pst;
     }
     double bnorm = nrm2(n, b);
     if (bnorm == 0.0) {
         for (int32_t i = 0; i < n; ++i) x[i] = 0.0;
-        free(dinv);
+        free(P.data);
         return info->status = OR_OK;
     }
     double thr = o->tol * bnorm;
@@ -533,7 +635,7 @@ int or_bicgstab(int32_t n, const int32_t* rp, const int32_t* ci,
         if (rho_new == 0.0) { status = OR_BREAKDOWN; break; }
         double beta = (rho_new / rho) * (alpha / omega);
         for (int32_t i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
-        prec(n, dinv, p, ph);
+        prec(n, &P, p, ph);
         mv(&A, ph, v);
         double rv = dot(n, rh, v);
         if (rv == 0.0) { status = OR_BREAKDOWN; break; }
@@ -556,7 +658,7 @@ int or_bicgstab(int32_t n, const int32_t* rp, const int32_t* ci,
             memset(p, 0, sz);
             continue;
         }
-        prec(n, dinv, s, sh);
+        prec(n, &P, s, sh);
         mv(&A, sh, t);
         double tt = dot(n, t, t);
         double ts = dot(n, t, s);
@@ -585,7 +687,7 @@ int or_bicgstab(int32_t n, const int32_t* rp, const int32_t* ci,
     resid(&A, b, x, t);
     info->rel_res_true = nrm2(n, t) / bnorm;
     free(r); free(rh); free(p); free(ph); free(v); free(s); free(sh); free(t);
-    free(dinv);
+    free(P.data);
     return info->status = status;
 }
 
@@ -606,18 +708,15 @@ int or_cgs(int32_t n, const int32_t* rp, const int32_t* ci,
 {
     or_mat A = {n, rp, ci, va};
     memset(info, 0, sizeof(*info));
-    double* dinv = NULL;
-    if (o->precond == 1) {
-        dinv = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-        if (or_jacobi_gen(n, rp, ci, va, dinv) != OR_OK) {
-            free(dinv);
-            return info->status = OR_ERR_ZERO_DIAG;
-        }
+    or_prec P;
+    {
+        const int pst = prec_setup(n, rp, ci, va, o, &P);
+        if (pst != OR_OK) return info->status = pst;
     }
     double bnorm = nrm2(n, b);
     if (bnorm == 0.0) {
         for (int32_t i = 0; i < n; ++i) x[i] = 0.0;
-        free(dinv);
+        free(P.data);
         return info->status = OR_OK;
     }
     double thr = o->tol * bnorm;
@@ -649,7 +748,7 @@ int or_cgs(int32_t n, const int32_t* rp, const int32_t* ci,
             for (int32_t i = 0; i < n; ++i) u[i] = r[i] + beta * q[i];
             for (int32_t i = 0; i < n; ++i) p[i] = u[i] + beta * (q[i] + beta * p[i]);
         }
-        prec(n, dinv, p, ph);
+        prec(n, &P, p, ph);
         mv(&A, ph, vh);
         double sigma = dot(n, rt, vh);
         if (!isfinite(sigma)) { status = OR_ERR_NAN; break; }
@@ -657,7 +756,7 @@ int or_cgs(int32_t n, const int32_t* rp, const int32_t* ci,
         double alpha = rho / sigma;
         for (int32_t i = 0; i < n; ++i) q[i] = u[i] - alpha * vh[i];
         for (int32_t i = 0; i < n; ++i) t[i] = u[i] + q[i];
-        prec(n, dinv, t, uh);
+        prec(n, &P, t, uh);
         for (int32_t i = 0; i < n; ++i) x[i] += alpha * uh[i];
         mv(&A, uh, t);
         for (int32_t i = 0; i < n; ++i) r[i] -= alpha * t[i];
@@ -680,7 +779,7 @@ int or_cgs(int32_t n, const int32_t* rp, const int32_t* ci,
     resid(&A, b, x, t);
     info->rel_res_true = nrm2(n, t) / bnorm;
     free(r); free(rt); free(u); free(p); free(q); free(ph); free(vh); free(t); free(uh);
-    free(dinv);
+    free(P.data);
     return info->status = status;
 }
 
@@ -705,18 +804,15 @@ int or_gmres(int32_t n, const int32_t* rp, const int32_t* ci,
     or_mat A = {n, rp, ci, va};
     memset(info, 0, sizeof(*info));
     int32_t m = o->krylov_dim > 0 ? o->krylov_dim : 30;
-    double* dinv = NULL;
-    if (o->precond == 1) {
-        dinv = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-        if (or_jacobi_gen(n, rp, ci, va, dinv) != OR_OK) {
-            free(dinv);
-            return info->status = OR_ERR_ZERO_DIAG;
-        }
+    or_prec P;
+    {
+        const int pst = prec_setup(n, rp, ci, va, o, &P);
+        if (pst != OR_OK) return info->status = pst;
     }
     double bnorm = nrm2(n, b);
     if (bnorm == 0.0) {
         for (int32_t i = 0; i < n; ++i) x[i] = 0.0;
-        free(dinv);
+        free(P.data);
         return info->status = OR_OK;
     }
     double thr = o->tol * bnorm;
@@ -748,7 +844,7 @@ int or_gmres(int32_t n, const int32_t* rp, const int32_t* ci,
         g[0] = beta0;
         int32_t k = 0;
         while (k < m && total < o->max_iters) {
-            prec(n, dinv, V + (size_t)k * n, z);
+            prec(n, &P, V + (size_t)k * n, z);
             mv(&A, z, w);
             for (int32_t j = 0; j <= k; ++j) {
                 double h = dot(n, w, V + (size_t)j * n);
@@ -791,8 +887,10 @@ int or_gmres(int32_t n, const int32_t* rp, const int32_t* ci,
         for (int32_t i = 0; i < n; ++i) {
             double u = 0.0;
             for (int32_t j = 0; j < k; ++j) u += V[(size_t)j * n + i] * y[j];
-            x[i] += dinv ? dinv[i] * u : u;
+            w[i] = u;
         }
+        prec(n, &P, w, z);
+        for (int32_t i = 0; i < n; ++i) x[i] += z[i];
     }
     info->iters = total;
     if (status != OR_OK) {
@@ -800,6 +898,6 @@ int or_gmres(int32_t n, const int32_t* rp, const int32_t* ci,
         info->rel_res_true = nrm2(n, r) / bnorm;
     }
     free(V); free(w); free(z); free(r); free(H); free(cs); free(sn); free(g); free(y);
-    free(dinv);
+    free(P.data);
     return info->status = status;
 }

@@ -525,3 +525,77 @@ def test_coo_spmv_integer_exact_and_rejects_out_of_range():
     assert np.array_equal(got, ref)
     with pytest.raises(ValueError):
         oracle.spmv_coo(3, 3, [0, 3], [0, 0], [1.0, 1.0], np.ones(3))
+
+
+# ---------------------------------------------------------------- block-Jacobi pins
+
+
+@pytest.mark.parametrize("n,bs", [(40, 4), (37, 8), (5, 8), (64, 1)])
+def test_block_jacobi_blocks_are_numpy_inverses(n, bs):
+    """Each stored block is the inverse (numpy LAPACK) of A's dense diagonal
+    block over bs rows, the short last block included."""
+    m = W.banded_spd(n, 5, 7)
+    binv = oracle.block_jacobi(m, bs)
+    d = m.to_dense()
+    for kb in range(binv.shape[0]):
+        r0 = kb * bs
+        k = min(bs, n - r0)
+        want = np.linalg.inv(d[r0:r0 + k, r0:r0 + k])
+        assert np.allclose(binv[kb, :k, :k], want, rtol=1e-12, atol=1e-14)
+        assert np.all(binv[kb, k:, :] == 0) and np.all(binv[kb, :, k:] == 0)
+    r = np.random.default_rng(n).standard_normal(n)
+    z = oracle.block_jacobi_apply(n, bs, binv, r)
+    zz = np.concatenate([binv[kb, :min(bs, n - kb * bs), :min(bs, n - kb * bs)] @
+                         r[kb * bs:kb * bs + min(bs, n - kb * bs)] for kb in range(binv.shape[0])])
+    assert np.allclose(z, zz, rtol=1e-14, atol=1e-15)
+
+
+def test_block_jacobi_pivots_and_rejects_singular_blocks():
+    # a block with a zero diagonal needs a row exchange: [[0, 2], [3, 0]]
+    m = _csr(2, 2, [0, 1, 2], [1, 0], [2.0, 3.0])
+    binv = oracle.block_jacobi(m, 2)
+    assert np.allclose(binv[0], np.linalg.inv(np.array([[0.0, 2.0], [3.0, 0.0]])), rtol=0, atol=1e-15)
+    with pytest.raises(ZeroDivisionError):  # the same matrix has zero diagonals for Jacobi
+        oracle.jacobi(m)
+    sing = _csr(2, 2, [0, 2, 4], [0, 1, 0, 1], [1.0, 2.0, 2.0, 4.0])
+    with pytest.raises(ZeroDivisionError):
+        oracle.block_jacobi(sing, 2)
+    x, info = oracle.solve(sing, np.ones(2), precond=2, block_size=2)
+    assert info["status"] == oracle.ERR_ZERO_DIAG
+
+
+def test_block_size_one_is_jacobi():
+    m = W.diffusion_3d(6)
+    b = W.uniform_vector(m.n, 2)
+    assert np.array_equal(oracle.block_jacobi(m, 1).reshape(-1), oracle.jacobi(m))
+    for method in (oracle.CG, oracle.GMRES):
+        x1, i1 = oracle.solve(m, b, method=method, precond=1, tol=1e-10, max_iters=2000)
+        x2, i2 = oracle.solve(m, b, method=method, precond=2, block_size=1, tol=1e-10,
+                              max_iters=2000)
+        assert np.array_equal(x1, x2) and i1["iters"] == i2["iters"]
+
+
+def test_block_jacobi_exact_on_block_diagonal_matrix():
+    """When A is block diagonal with blocks of bs rows, block-Jacobi is A^-1:
+    preconditioned CG, BiCGSTAB, CGS and GMRES converge in one step."""
+    rng = np.random.default_rng(9)
+    bs, nb = 4, 6
+    d = np.zeros((bs * nb, bs * nb))
+    for k in range(nb):
+        q = rng.standard_normal((bs, bs))
+        d[k * bs:(k + 1) * bs, k * bs:(k + 1) * bs] = q @ q.T + bs * np.eye(bs)
+    m = _dense_csr(d)
+    b = rng.standard_normal(bs * nb)
+    for method in (oracle.CG, oracle.BICGSTAB, oracle.CGS, oracle.GMRES):
+        x, info = oracle.solve(m, b, method=method, precond=2, block_size=bs, tol=1e-12)
+        assert info["status"] == oracle.OK and info["iters"] == 1, (method, info)
+        assert np.allclose(x, np.linalg.solve(d, b), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("method", [oracle.CG, oracle.BICGSTAB, oracle.CGS, oracle.GMRES])
+def test_block_jacobi_solvers_reach_tol(method):
+    m = W.diffusion_3d(10)
+    b = W.uniform_vector(m.n, 3)
+    x, info = oracle.solve(m, b, method=method, precond=2, block_size=8, tol=1e-10, max_iters=5000)
+    assert info["status"] == oracle.OK, info
+    assert oracle.true_rel_residual(m, b, x) <= 1e-10
