@@ -70,7 +70,11 @@ typedef enum { GK_CSR = 0, GK_ELL = 1, GK_SELLP = 2, GK_COO = 3 } gk_format;
  * and CGS (Sonneveld's conjugate gradient squared, the solver the paper
  * benchmarks beside CG and GMRES in Section 5.2.1). */
 typedef enum { GK_CG = 0, GK_BICGSTAB = 1, GK_GMRES = 2, GK_CGS = 3 } gk_method;
-typedef enum { GK_PRECOND_NONE = 0, GK_PRECOND_JACOBI = 1 } gk_precond;
+/* Preconditioners (the config solver's Jacobi, Listing 2): point Jacobi
+ * (max_block_size 1) and block-Jacobi over diagonal blocks of block_size
+ * consecutive rows (max_block_size > 1; each block inverted by Gauss-Jordan
+ * with partial pivoting, a singular block is GK_ERR_ZERO_DIAG). */
+typedef enum { GK_PRECOND_NONE = 0, GK_PRECOND_JACOBI = 1, GK_PRECOND_BLOCK_JACOBI = 2 } gk_precond;
 typedef enum { GK_MEM_HOST = 0, GK_MEM_DEVICE = 1 } gk_memory;
 
 typedef enum {
@@ -192,7 +196,7 @@ gk_status gk_apply_adv(gk_matrix A, double alpha, const void* b, double beta,
 
 typedef struct {
     gk_method method;
-    gk_precond precond;   /* Jacobi with block size 1 (Listing 2) */
+    gk_precond precond;   /* none, Jacobi, or block-Jacobi (block_size below) */
     double tol;           /* stop when ||b - A x||_2 <= tol * ||b||_2 */
     int32_t max_iters;    /* CG/BiCGSTAB iterations; GMRES Arnoldi steps (all cycles) */
     int32_t krylov_dim;   /* GMRES restart length m (0 = 30, the paper's value); <= 64 */
@@ -209,7 +213,9 @@ typedef struct {
                              2 single-block (CSR, CG/BiCGSTAB, n <= 16384);
                              3 cluster of up to 16 blocks (CSR, CG, n <= 16384).
                              Automatic picks 3 for CSR CG with n <= 16384 when a
-                             cluster can be scheduled, else 1. */
+                             cluster can be scheduled, else 1.  Block-Jacobi and
+                             CGS run on engine 1 only. */
+    int32_t block_size;   /* block-Jacobi rows per diagonal block, 1..32 */
 } gk_solve_opts;
 
 typedef struct {

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libgk.so")
 GK_F64, GK_F32, GK_BF16, GK_F16 = 0, 1, 2, 3
 GK_CSR, GK_ELL, GK_SELLP, GK_COO = 0, 1, 2, 3
 GK_CG, GK_BICGSTAB, GK_GMRES, GK_CGS = 0, 1, 2, 3
-GK_PRECOND_NONE, GK_PRECOND_JACOBI = 0, 1
+GK_PRECOND_NONE, GK_PRECOND_JACOBI, GK_PRECOND_BLOCK_JACOBI = 0, 1, 2
 GK_MEM_HOST, GK_MEM_DEVICE = 0, 1
 GK_OK, GK_NOT_CONVERGED, GK_BREAKDOWN = 0, 1, 2
 GK_ERR_INVALID, GK_ERR_OOM, GK_ERR_CUDA, GK_ERR_TIMEOUT = -1, -2, -3, -4
@@ -68,7 +68,7 @@ class gk_solve_opts(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("krylov_dim", ctypes.c_int32),
                 ("mixed", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int32), ("batch_tols", ctypes.c_void_p),
-                ("engine", ctypes.c_int32)]
+                ("engine", ctypes.c_int32), ("block_size", ctypes.c_int32)]
 
 
 class gk_solve_info(ctypes.Structure):
@@ -222,14 +222,18 @@ def gk_apply_adv(A, alpha, b, beta, x, stream=None):
 
 
 def make_opts(method="cg", precond=None, tol=1e-10, max_iters=1000, krylov_dim=30, mixed=0,
-              inner_tol=0.0, max_outer=0, engine=0):
+              inner_tol=0.0, max_outer=0, engine=0, block_size=0):
+    """precond: None / "none" / 0, "jacobi" / 1 / True, or "block_jacobi" / 2
+    (with block_size rows per diagonal block)."""
     m = METHODS[method] if isinstance(method, str) else int(method)
     if precond in (None, "none", 0, False):
         p = GK_PRECOND_NONE
+    elif precond in ("block_jacobi", 2):
+        p = GK_PRECOND_BLOCK_JACOBI
     else:
         p = GK_PRECOND_JACOBI
     return gk_solve_opts(m, p, tol, max_iters, krylov_dim, mixed, inner_tol, max_outer, None,
-                         engine)
+                         engine, block_size)
 
 
 def gk_solve(A, b, x, opts, stream=None):

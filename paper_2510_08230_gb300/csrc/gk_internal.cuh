@@ -211,6 +211,8 @@ struct gk_matrix_s {
     // derived data, built on first use
     void* dinv = nullptr;         // Jacobi inverse diagonal (vector type)
     int dinv_state = 0;           // 0 not built, 1 ok, -1 zero diagonal
+    void* binv = nullptr;         // block-Jacobi inverses (vector type, column-major blocks)
+    int32_t binv_bs = 0;          // their block size (0 none, -bs singular)
     gk_matrix_s* lowp[3] = {nullptr, nullptr, nullptr};  // same layout, other dtype
     gk_matrix_s* solve_fmt = nullptr;  // SpMV layout picked for solves (null: not tuned)
     int solve_fmt_tuned = 0;

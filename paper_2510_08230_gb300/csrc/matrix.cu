@@ -499,6 +499,9 @@ static void free_arrays(gk_matrix A) {
     dfree(A->plan.block_row);
     dfree(A->plan.err);
     dfree(A->dinv);
+    dfree(A->binv);
+    A->binv = nullptr;
+    A->binv_bs = 0;
     dfree(A->coo_row);
     dfree(A->empty_rows);
     A->coo_row = A->empty_rows = nullptr;

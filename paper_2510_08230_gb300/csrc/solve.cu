@@ -68,6 +68,55 @@ gk_status ensure_jacobi(gk_matrix A, cudaStream_t s) {
     return GK_OK;
 }
 
+// Block-Jacobi inverses of A's diagonal blocks of bs rows (k_bj_gen), built
+// once per (matrix, block size) from the CSR arrays (a padded matrix goes
+// through a temporary CSR copy), stored in the vector type.
+gk_status ensure_block_jacobi(gk_matrix A, int32_t bs, cudaStream_t s) {
+    if (A->binv_bs == bs && A->binv) return GK_OK;
+    if (A->binv_bs == -bs) return GK_ERR_ZERO_DIAG;  // known singular
+    dfree(A->binv);
+    A->binv = nullptr;
+    A->binv_bs = 0;
+    gk_matrix C = A, tmp = nullptr;
+    if (A->fmt != GK_CSR) {
+        GK_TRY(gk_matrix_convert(A, GK_CSR, A->dtype, 0, 0, s, &tmp));
+        C = tmp;
+    }
+    const int64_t nb = ((int64_t)A->n + bs - 1) / bs;
+    const size_t vb = vector_bytes(A->dtype);
+    DevBuf bad;
+    gk_status st = GK_OK;
+    if (dmalloc(&A->binv, vb * (size_t)std::max<int64_t>(nb, 1) * bs * bs) != cudaSuccess) st = GK_ERR_OOM;
+    if (st == GK_OK) st = bad.ensure(16);
+    if (st == GK_OK && cudaMemsetAsync(bad.ptr, 0, 16, s) != cudaSuccess) st = GK_ERR_CUDA;
+    if (st == GK_OK && nb > 0) {
+        auto go = [&](auto vt, auto tt) {
+            using V = decltype(vt);
+            using T = decltype(tt);
+            k_bj_gen<V, T><<<(unsigned)nb, 32, 0, s>>>(C->n, bs, C->row_ptr, C->col,
+                                                       (const V*)C->val, (T*)A->binv,
+                                                       (int32_t*)bad.ptr);
+        };
+        if (A->dtype == GK_F64) go(double(), double());
+        else if (A->dtype == GK_F32) go(float(), float());
+        else if (A->dtype == GK_F16) go(__half(), float());
+        else go(__nv_bfloat16(), float());
+        if (cudaGetLastError() != cudaSuccess) st = GK_ERR_CUDA;
+    }
+    int32_t h = 0;
+    if (st == GK_OK && (cudaMemcpyAsync(&h, bad.ptr, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                        cudaStreamSynchronize(s) != cudaSuccess))
+        st = GK_ERR_CUDA;
+    if (tmp) gk_matrix_destroy(tmp);
+    if (st != GK_OK) return st;
+    if (h) {
+        A->binv_bs = -bs;
+        return GK_ERR_ZERO_DIAG;
+    }
+    A->binv_bs = bs;
+    return GK_OK;
+}
+
 gk_status get_lowp(gk_matrix A, gk_dtype d, cudaStream_t s, gk_matrix* out) {
     if (A->dtype == d) {
         *out = A;
@@ -183,7 +232,11 @@ static gk_status check_opts(gk_matrix A, const gk_solve_opts* o) {
     if (o->method != GK_CG && o->method != GK_BICGSTAB && o->method != GK_GMRES &&
         o->method != GK_CGS)
         return GK_ERR_INVALID;
-    if (o->precond != GK_PRECOND_NONE && o->precond != GK_PRECOND_JACOBI) return GK_ERR_INVALID;
+    if (o->precond != GK_PRECOND_NONE && o->precond != GK_PRECOND_JACOBI &&
+        o->precond != GK_PRECOND_BLOCK_JACOBI)
+        return GK_ERR_INVALID;
+    if (o->precond == GK_PRECOND_BLOCK_JACOBI && (o->block_size < 1 || o->block_size > BJ_MAX))
+        return GK_ERR_INVALID;
     if (!(o->tol >= 0.0) || o->max_iters < 0) return GK_ERR_INVALID;
     if (o->krylov_dim < 0 || o->krylov_dim > MAXM) return GK_ERR_INVALID;
     if (o->mixed < 0 || o->mixed > 3) return GK_ERR_INVALID;
@@ -199,7 +252,7 @@ static gk_status solve_plain(gk_matrix A, const void* b, void* x, const gk_solve
     const int m = o->method == GK_GMRES ? (o->krylov_dim ? o->krylov_dim : 30) : 0;
     gk_matrix M = nullptr;
     GK_TRY(solve_matrix(A, s, &M));
-    return solve_mk<V, T>(M, (const T*)b, (T*)x, o->method, o->precond == GK_PRECOND_JACOBI,
+    return solve_mk<V, T>(M, (const T*)b, (T*)x, o->method, (int)o->precond, o->block_size,
                           o->tol, o->max_iters, m, s, out, false);
 }
 
@@ -275,17 +328,18 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
         k_zero<float><<<ewg(k_zero<float>, n), 256, 0, s>>>(n, d32);
         GK_CUDA(cudaGetLastError());
         SolveOut io;
-        const bool prec = o->precond == GK_PRECOND_JACOBI;
+        const int pk = (int)o->precond;
+        const int32_t bsz = o->block_size;
         const int32_t left = o->max_iters - total_inner;
         if (L->dtype == GK_F32)
-            GK_TRY((solve_mk<float, float>(L, r32, d32, o->method, prec, inner_tol, left, m, s, &io,
-                                           true)));
+            GK_TRY((solve_mk<float, float>(L, r32, d32, o->method, pk, bsz, inner_tol, left, m, s,
+                                           &io, true)));
         else if (L->dtype == GK_F16)
-            GK_TRY((solve_mk<__half, float>(L, r32, d32, o->method, prec, inner_tol, left, m, s,
+            GK_TRY((solve_mk<__half, float>(L, r32, d32, o->method, pk, bsz, inner_tol, left, m, s,
                                             &io, true)));
         else
-            GK_TRY((solve_mk<__nv_bfloat16, float>(L, r32, d32, o->method, prec, inner_tol, left, m,
-                                                   s, &io, true)));
+            GK_TRY((solve_mk<__nv_bfloat16, float>(L, r32, d32, o->method, pk, bsz, inner_tol, left,
+                                                   m, s, &io, true)));
         total_inner += io.iters;
         restarts += io.restarts;
         last_rec = io.rec;

@@ -375,7 +375,23 @@ struct CgUpdFin {
             st->halt = 2;
             return;
         }
+        if (prec == 2) return;  // block-Jacobi: k_bj_apply's fin takes <r, z>
         const double rz = prec ? t[0] : t[1];
+        st->beta = rz / st->rho;
+        st->rho = rz;
+    }
+};
+
+// block-Jacobi CG: beta from <r, z> with z = B r (k_bj_apply)
+struct CgBetaFin {
+    KState* st;
+    __device__ void operator()(double* t) const {
+        const double rz = t[0];
+        if (!isfinite(rz)) {
+            st->status = GK_ERR_NAN;
+            st->halt = 2;
+            return;
+        }
         st->beta = rz / st->rho;
         st->rho = rz;
     }
@@ -386,7 +402,7 @@ template <typename T>
 __global__ void EW_BOUNDS k_cg_update(int32_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
                             const T* __restrict__ p, const T* __restrict__ q,
                             const T* __restrict__ dinv, KState* st, double* partials,
-                            unsigned* ticket) {
+                            unsigned* ticket, int pkind) {
     if (halted(st)) return;
     constexpr int N = Pack<T>::N;
     const T alpha = (T)st->alpha;
@@ -410,7 +426,7 @@ __global__ void EW_BOUNDS k_cg_update(int32_t n, T* __restrict__ x, T* __restric
         pst(r, j, n, vec, R);
         if (dinv) pst(z, j, n, vec, Z);
     }
-    finish_ew<2>(a, partials, ticket, CgUpdFin{st, dinv != nullptr});
+    finish_ew<2>(a, partials, ticket, CgUpdFin{st, pkind});
 }
 
 // p = z + beta p
@@ -759,13 +775,24 @@ template <typename T>
 __global__ void EW_BOUNDS k_cgs_q(int32_t n, T* __restrict__ q, T* __restrict__ uh,
                                   T* __restrict__ x, const T* __restrict__ u,
                                   const T* __restrict__ vh, const T* __restrict__ dinv,
-                                  const KState* st) {
+                                  const KState* st, T* __restrict__ tout) {
     if (halted(st)) return;
     constexpr int N = Pack<T>::N;
     const T alpha = (T)st->alpha;
     const bool vec = al16(q) && al16(uh) && al16(x) && al16(u) && al16(vh) && al16(dinv);
     PACK_LOOP(j, n, T) {
         const Pack<T> U = pld(u, j, n, vec), VH = pld(vh, j, n, vec);
+        if (tout) {  // block-Jacobi: t = u + q here, uh = B t and x += alpha uh in k_bj_apply
+            Pack<T> Q, Tt;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                Q.v[c] = fmadd(-alpha, VH.v[c], U.v[c]);
+                Tt.v[c] = U.v[c] + Q.v[c];
+            }
+            pst(q, j, n, vec, Q);
+            pst(tout, j, n, vec && al16(tout), Tt);
+            continue;
+        }
         Pack<T> X = pld(x, j, n, vec);
         Pack<T> Q, UH = dinv ? pld(dinv, j, n, vec) : Pack<T>{};
 #pragma unroll
@@ -1132,7 +1159,7 @@ k_gm_orth(int32_t n, int64_t ldv, const T* __restrict__ V, T* __restrict__ w, KS
 template <typename T>
 __global__ void EW_BOUNDS k_gm_next(int32_t n, int64_t ldv, T* __restrict__ V, const T* __restrict__ w,
                           T* __restrict__ z, T* __restrict__ x, const T* __restrict__ dinv,
-                          const KState* st) {
+                          const KState* st, T* __restrict__ ubuf) {
     if (halted(st)) return;
     const int32_t k = st->k;
     constexpr int N = Pack<T>::N;
@@ -1162,6 +1189,10 @@ __global__ void EW_BOUNDS k_gm_next(int32_t n, int64_t ldv, T* __restrict__ V, c
                 const Pack<T> Vl = pld(V + (int64_t)l * ldv, j, n, vec);
 #pragma unroll
                 for (int c = 0; c < N; ++c) U.v[c] = fmadd(Vl.v[c], s_y[l], U.v[c]);
+            }
+            if (ubuf) {  // block-Jacobi: k_bj_gm adds B (V y) to x
+                pst(ubuf, j, n, vec && al16(ubuf), U);
+                continue;
             }
             Pack<T> X = pld(x, j, n, vec);
             const Pack<T> D = dinv ? pld(dinv, j, n, vec) : Pack<T>{};
@@ -1364,6 +1395,160 @@ __global__ void EW_BOUNDS k_cast_to(int32_t n, const double* __restrict__ r, T* 
     GRID_LOOP(i, n) o[i] = (T)r[i];
 }
 
+// ---------------------------------------------------------------- block-Jacobi
+// Diagonal blocks of bs consecutive rows (the last may be shorter), inverted
+// once per matrix (k_bj_gen) and applied as z = B r (k_bj_apply, k_bj_gm).
+// The inverses are stored per block column-major in the vector type T:
+// entry (i, j) of block kb at binvT[kb*bs*bs + j*bs + i], so that the rows
+// of a block read consecutive addresses for each j.
+
+constexpr int BJ_MAX = 32;  // largest block size
+
+// One warp per block: gather A's block from CSR (lane i sums row i's
+// entries in CSR order), Gauss-Jordan on [A | I] in double with partial
+// pivoting (largest |a|, the first on ties), lanes over the columns.  A block
+// with no nonzero pivot left sets *bad (singular: the zero-diagonal error).
+template <typename V, typename T>
+__global__ void __launch_bounds__(32)
+k_bj_gen(int32_t n, int32_t bs, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+         const V* __restrict__ va, T* __restrict__ binvT, int32_t* bad) {
+    __shared__ double aug[BJ_MAX][2 * BJ_MAX + 1];
+    const int lane = threadIdx.x;
+    const int64_t kb = blockIdx.x;
+    const int32_t r0 = (int32_t)(kb * bs);
+    const int m = min(bs, n - r0);
+    for (int i = 0; i < m; ++i)
+        for (int c = lane; c < 2 * m; c += 32) aug[i][c] = (c - m == i) ? 1.0 : 0.0;
+    __syncwarp();
+    if (lane < m) {
+        const int i = lane;
+        for (int32_t k = rp[r0 + i]; k < rp[r0 + i + 1]; ++k) {
+            const int32_t j = ci[k] - r0;
+            if (j >= 0 && j < m) aug[i][j] += cvt<double>(va[k]);
+        }
+    }
+    __syncwarp();
+    for (int c = 0; c < m; ++c) {
+        // pivot: largest |a_rc| over r >= c, the smallest r on ties
+        double best = -1.0;
+        int piv = c;
+        if (lane >= c && lane < m) {
+            best = fabs(aug[lane][c]);
+            piv = lane;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_down_sync(0xffffffffu, best, o);
+            const int op = __shfl_down_sync(0xffffffffu, piv, o);
+            if (ob > best || (ob == best && op < piv)) {
+                best = ob;
+                piv = op;
+            }
+        }
+        piv = __shfl_sync(0xffffffffu, piv, 0);
+        if (aug[piv][c] == 0.0) {
+            if (lane == 0) atomicExch(bad, 1);
+            return;
+        }
+        if (piv != c)
+            for (int col = lane; col < 2 * m; col += 32) {
+                const double t = aug[c][col];
+                aug[c][col] = aug[piv][col];
+                aug[piv][col] = t;
+            }
+        __syncwarp();
+        const double d = aug[c][c];
+        __syncwarp();
+        for (int col = lane; col < 2 * m; col += 32) aug[c][col] = aug[c][col] / d;
+        __syncwarp();
+        for (int r = 0; r < m; ++r) {
+            if (r == c) continue;
+            const double f = aug[r][c];
+            __syncwarp();
+            if (f != 0.0)
+                for (int col = lane; col < 2 * m; col += 32)
+                    aug[r][col] = aug[r][col] - f * aug[c][col];
+            __syncwarp();
+        }
+    }
+    T* out = binvT + (size_t)kb * bs * bs;
+    for (int e = lane; e < bs * bs; e += 32) {
+        const int j = e / bs, i = e - j * bs;
+        out[e] = (i < m && j < m) ? cvt<T>(aug[i][m + j]) : T(0);
+    }
+}
+
+// z_i = sum_j B[i][j] r[r0 + j] per row, handed to an epilogue (store,
+// store + dot with a fin, store + x update); exits at once when halted.
+template <typename T, class Epi>
+__global__ void EW_BOUNDS k_bj_apply(int32_t n, int32_t bs, const T* __restrict__ binvT,
+                                     const T* __restrict__ r, Epi epi) {
+    if (epi.skip()) return;
+    typename Epi::acc_t acc[Epi::NA > 0 ? Epi::NA : 1] = {};
+    GRID_LOOP(i, n) {
+        const int32_t kb = (int32_t)(i / bs), li = (int32_t)(i - (int64_t)kb * bs);
+        const int64_t r0 = (int64_t)kb * bs;
+        const int m = (int)min((int64_t)bs, (int64_t)n - r0);
+        const T* col = binvT + (size_t)kb * bs * bs + li;
+        T s = T(0);
+        for (int j = 0; j < m; ++j) s = fmadd(col[(size_t)j * bs], r[r0 + j], s);
+        epi.row(i, s, acc);
+    }
+    epi.finish(acc);
+}
+
+// y_i = s ; x_i += alpha s  (CGS: uh = B (u + q), x += alpha uh)
+template <typename T>
+struct EpiBjX {
+    T* __restrict__ y;
+    T* __restrict__ x;
+    const KState* st;
+    static constexpr int NA = 0;
+    using acc_t = T;
+    __device__ __forceinline__ bool skip() const { return halted(st); }
+    __device__ __forceinline__ void row(int64_t i, T s, T*) const {
+        y[i] = s;
+        x[i] = fmadd((T)st->alpha, s, x[i]);
+    }
+    __device__ __forceinline__ void finish(T*) const {}
+    __device__ __forceinline__ void timed_out() const {}
+};
+
+// GMRES v_0 step: z = B v_0, only when a restart decided to continue
+template <typename T>
+struct EpiBjV0 {
+    T* __restrict__ y;
+    const KState* st;
+    static constexpr int NA = 0;
+    using acc_t = T;
+    __device__ __forceinline__ bool skip() const { return halted(st) || !st->v0_pending; }
+    __device__ __forceinline__ void row(int64_t i, T s, T*) const { y[i] = s; }
+    __device__ __forceinline__ void finish(T*) const {}
+    __device__ __forceinline__ void timed_out() const {}
+};
+
+// GMRES after k_gm_next: inside a cycle z = B v_k; at the end of a cycle
+// x += B (V y) (V y left in ubuf by k_gm_next).
+template <typename T>
+__global__ void EW_BOUNDS k_bj_gm(int32_t n, int32_t bs, const T* __restrict__ binvT,
+                                  const T* __restrict__ V, int64_t ldv,
+                                  const T* __restrict__ ubuf, T* __restrict__ z,
+                                  T* __restrict__ x, const KState* st) {
+    if (halted(st)) return;
+    const bool ce = st->cycle_end != 0;
+    const T* src = ce ? ubuf : V + (int64_t)st->k * ldv;
+    GRID_LOOP(i, n) {
+        const int32_t kb = (int32_t)(i / bs), li = (int32_t)(i - (int64_t)kb * bs);
+        const int64_t r0 = (int64_t)kb * bs;
+        const int m = (int)min((int64_t)bs, (int64_t)n - r0);
+        const T* col = binvT + (size_t)kb * bs * bs + li;
+        T s = T(0);
+        for (int j = 0; j < m; ++j) s = fmadd(col[(size_t)j * bs], src[r0 + j], s);
+        if (ce) x[i] += s;
+        else z[i] = s;
+    }
+}
+
 // ------------------------------------------------------------ host side
 
 constexpr size_t HDR = offsetof(KState, H);
@@ -1397,6 +1582,7 @@ gk_status get_cache(gk_matrix A, SolverCache** out);
 gk_status side_stream(gk_matrix A);
 gk_status read_hdr(SolverCache* C, cudaStream_t s);
 gk_status clear_halt(SolverCache* C, cudaStream_t s);
+gk_status ensure_block_jacobi(gk_matrix A, int32_t bs, cudaStream_t s);
 
 template <typename T>
 static T* vec_at(SolverCache* C, int64_t n, int idx) {
@@ -1444,18 +1630,27 @@ inline int chunk_for(int64_t n) { return n < 200000 ? 32 : 8; }
 // replacements it stops anyway: the outer FP64 residual decides
 // convergence, and an FP32 solve can stall above a tight inner tolerance.
 template <typename V, typename T>
-gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, double tol,
-                          int32_t max_iters, int32_t m, cudaStream_t s, SolveOut* out,
-                          bool inner) {
+gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t bs, double tol,
+                   int32_t max_iters, int32_t m, cudaStream_t s, SolveOut* out, bool inner) {
     const int32_t n = A->n;
     SolverCache* C = nullptr;
     GK_TRY(get_cache(A, &C));
+    // preconditioner: pkind 0 none, 1 Jacobi (fused into the update kernels
+    // as dinv), 2 block-Jacobi of bs rows (separate k_bj_* kernels; the
+    // update kernels then run unpreconditioned into the vectors B is
+    // applied to)
+    const bool prec = pkind != 0;
+    const bool block = pkind == 2;
     const T* dinv = nullptr;
-    if (prec) {
+    const T* binv = nullptr;
+    if (pkind == 1) {
         GK_TRY(ensure_jacobi(A, s));
         dinv = (const T*)A->dinv;
+    } else if (block) {
+        GK_TRY(ensure_block_jacobi(A, bs, s));
+        binv = (const T*)A->binv;
     }
-    const int nvec = method == GK_CG ? 5 : (method == GK_BICGSTAB || method == GK_CGS) ? 9 : m + 4;
+    const int nvec = method == GK_CG ? 5 : (method == GK_BICGSTAB || method == GK_CGS) ? 10 : m + 5;
     GK_TRY(ensure_vecs<T>(C, n, nvec));
     // multi-dot kernels: one wave of resident blocks sharing the rows equally
     const int64_t md_need = std::max<int64_t>(1, ((int64_t)n + MD_ROWS - 1) / MD_ROWS);
@@ -1492,10 +1687,15 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, double 
         // cycle start: r = b - A x, restart fin sets g, k; v0 = r / beta0
         EpiResid<T, GmRestartFin> e0{r, b, halt, part, tk, GmRestartFin{st}};
         GK_TRY((launch_spmv_rows<V, T>(A, x, e0, s)));
+        T* ubuf = vec_at<T>(C, n, m + 4);  // V y at a cycle end (block-Jacobi only)
         k_gm_v0<T><<<ewg(k_gm_v0<T>, n), 256, 0, s>>>(n, Vm, r, z, dinv, st);
+        if (block)
+            k_bj_apply<T, EpiBjV0<T>><<<ewg(k_bj_apply<T, EpiBjV0<T>>, n), 256, 0, s>>>(
+                n, bs, binv, Vm, EpiBjV0<T>{z, st});
         GK_CUDA(cudaGetLastError());
         const int chunk = chunk_for(n);
-        if (!C->exec || C->kb != b || C->kx != x || C->kmethod != method || C->kprec != (int)prec ||
+        const int pkey = pkind * 64 + (block ? bs : 0);
+        if (!C->exec || C->kb != b || C->kx != x || C->kmethod != method || C->kprec != pkey ||
             C->km != m || C->kchunk != chunk || C->kv != (void*)C->vecs.ptr) {
             GK_TRY(capture_chunk(A, C, chunk, [&](cudaStream_t cs) -> gk_status {
                 EpiStoreHalt<T> e1{w, halt};
@@ -1506,14 +1706,21 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, double 
                                                                                part, tk);
                 k_gm_orth<T><<<md_grid_of(k_gm_orth<T>), MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st,
                                                                                part, tk);
-                k_gm_next<T><<<ewg(k_gm_next<T>, n), 256, 0, cs>>>(n, ldv, Vm, w, z, x, dinv, st);
+                k_gm_next<T><<<ewg(k_gm_next<T>, n), 256, 0, cs>>>(n, ldv, Vm, w, z, x, dinv, st,
+                                                                   block ? ubuf : nullptr);
+                if (block)
+                    k_bj_gm<T><<<ewg(k_bj_gm<T>, n), 256, 0, cs>>>(n, bs, binv, Vm, ldv, ubuf, z,
+                                                                   x, st);
                 EpiGmResid<T> e2{r, b, st, part, tk, GmRestartFin{st}};
                 GK_TRY((launch_spmv_rows<V, T>(A, x, e2, cs)));
                 k_gm_v0<T><<<ewg(k_gm_v0<T>, n), 256, 0, cs>>>(n, Vm, r, z, dinv, st);
+                if (block)
+                    k_bj_apply<T, EpiBjV0<T>><<<ewg(k_bj_apply<T, EpiBjV0<T>>, n), 256, 0, cs>>>(
+                        n, bs, binv, Vm, EpiBjV0<T>{z, st});
                 GK_CUDA(cudaGetLastError());
                 return GK_OK;
             }));
-            C->kb = b; C->kx = x; C->kmethod = method; C->kprec = prec; C->km = m;
+            C->kb = b; C->kx = x; C->kmethod = method; C->kprec = pkey; C->km = m;
             C->kchunk = chunk; C->kv = C->vecs.ptr;
         }
         GK_TRY(read_hdr(C, s));
@@ -1529,7 +1736,13 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, double 
         EpiResid<T, FinTrue> e0{r, b, halt, part, tk, FinTrue{st, 0}};
         GK_TRY((launch_spmv_rows<V, T>(A, x, e0, s)));
         auto init = [&]() -> gk_status {
-            if (method == GK_CG)  // slots: 0 r, 1 tmp, 2 q, 3 p, 4 z
+            if (method == GK_CG && block) {  // z = B r, rho = <r, z> ; p = z
+                T *zb = vec_at<T>(C, n, 4), *pb = vec_at<T>(C, n, 3);
+                using E0 = EpiDot<T, CgInitFin>;
+                k_bj_apply<T, E0><<<ewg(k_bj_apply<T, E0>, n), 256, 0, s>>>(
+                    n, bs, binv, r, E0{zb, r, nullptr, part, tk, CgInitFin{st}});
+                k_copy<T><<<ewg(k_copy<T>, n), 256, 0, s>>>(n, zb, pb);
+            } else if (method == GK_CG)  // slots: 0 r, 1 tmp, 2 q, 3 p, 4 z
                 k_cg_init<T><<<ewg(k_cg_init<T>, n), 256, 0, s>>>(n, r, vec_at<T>(C, n, 4), vec_at<T>(C, n, 3), dinv,
                                                 st, part, tk);
             else if (method == GK_CGS)
@@ -1545,7 +1758,8 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, double 
         };
         GK_TRY(init());
         const int chunk = chunk_for(n);
-        if (!C->exec || C->kb != b || C->kx != x || C->kmethod != method || C->kprec != (int)prec ||
+        const int pkey = pkind * 64 + (block ? bs : 0);
+        if (!C->exec || C->kb != b || C->kx != x || C->kmethod != method || C->kprec != pkey ||
             C->kchunk != chunk || C->kv != (void*)C->vecs.ptr) {
             GK_TRY(capture_chunk(A, C, chunk, [&](cudaStream_t cs) -> gk_status {
                 if (method == GK_CG) {
@@ -1553,17 +1767,29 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, double 
                       *q = vec_at<T>(C, n, 2);
                     EpiDot<T, CgAlphaFin> e1{q, p, halt, part, tk, CgAlphaFin{st}};
                     GK_TRY((launch_spmv_rows<V, T>(A, p, e1, cs)));
-                    k_cg_update<T><<<ewg(k_cg_update<T>, n), 256, 0, cs>>>(n, x, r, z, p, q, dinv, st, part, tk);
+                    k_cg_update<T><<<ewg(k_cg_update<T>, n), 256, 0, cs>>>(n, x, r, z, p, q, dinv, st, part, tk, pkind);
+                    if (block) {  // z = B r ; beta = <r, z> / rho
+                        using E1 = EpiDot<T, CgBetaFin>;
+                        k_bj_apply<T, E1><<<ewg(k_bj_apply<T, E1>, n), 256, 0, cs>>>(
+                            n, bs, binv, r, E1{z, r, halt, part, tk, CgBetaFin{st}});
+                    }
                     k_cg_p<T><<<ewg(k_cg_p<T>, n), 256, 0, cs>>>(n, p, z, st);
                 } else if (method == GK_CGS) {
                     T *rt = vec_at<T>(C, n, 2), *u = vec_at<T>(C, n, 3), *p = vec_at<T>(C, n, 4);
                     T *q = vec_at<T>(C, n, 5), *ph = vec_at<T>(C, n, 6), *vh = vec_at<T>(C, n, 7);
-                    T* uh = vec_at<T>(C, n, 8);
+                    T *uh = vec_at<T>(C, n, 8), *tb = vec_at<T>(C, n, 9);
                     const T* phs = prec ? ph : p;
                     k_cgs_p<T><<<ewg(k_cgs_p<T>, n), 256, 0, cs>>>(n, u, p, ph, r, q, dinv, st);
+                    if (block)
+                        k_bj_apply<T, EpiStoreHalt<T>><<<ewg(k_bj_apply<T, EpiStoreHalt<T>>, n), 256, 0, cs>>>(
+                            n, bs, binv, p, EpiStoreHalt<T>{ph, halt});
                     EpiDot<T, CgsAlphaFin> e1{vh, rt, halt, part, tk, CgsAlphaFin{st}};
                     GK_TRY((launch_spmv_rows<V, T>(A, phs, e1, cs)));
-                    k_cgs_q<T><<<ewg(k_cgs_q<T>, n), 256, 0, cs>>>(n, q, uh, x, u, vh, dinv, st);
+                    k_cgs_q<T><<<ewg(k_cgs_q<T>, n), 256, 0, cs>>>(n, q, uh, x, u, vh, dinv, st,
+                                                                   block ? tb : nullptr);
+                    if (block)
+                        k_bj_apply<T, EpiBjX<T>><<<ewg(k_bj_apply<T, EpiBjX<T>>, n), 256, 0, cs>>>(
+                            n, bs, binv, tb, EpiBjX<T>{uh, x, st});
                     EpiCgsR<T> e2{r, rt, st, part, tk};
                     GK_TRY((launch_spmv_rows<V, T>(A, uh, e2, cs)));
                 } else {
@@ -1573,9 +1799,15 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, double 
                     const T* phs = prec ? ph : p;
                     const T* shs = prec ? sh : sv;
                     k_bi_p<T><<<ewg(k_bi_p<T>, n), 256, 0, cs>>>(n, p, ph, r, v, dinv, st);
+                    if (block)
+                        k_bj_apply<T, EpiStoreHalt<T>><<<ewg(k_bj_apply<T, EpiStoreHalt<T>>, n), 256, 0, cs>>>(
+                            n, bs, binv, p, EpiStoreHalt<T>{ph, halt});
                     EpiDot<T, BiAlphaFin> e1{v, rh, halt, part, tk, BiAlphaFin{st}};
                     GK_TRY((launch_spmv_rows<V, T>(A, phs, e1, cs)));
                     k_bi_s<T><<<ewg(k_bi_s<T>, n), 256, 0, cs>>>(n, sv, sh, r, v, dinv, st, part, tk);
+                    if (block)
+                        k_bj_apply<T, EpiStoreHalt<T>><<<ewg(k_bj_apply<T, EpiStoreHalt<T>>, n), 256, 0, cs>>>(
+                            n, bs, binv, sv, EpiStoreHalt<T>{sh, halt});
                     EpiBiT<T> e2{t, sv, st, part, tk, BiOmegaFin{st}};
                     GK_TRY((launch_spmv_rows<V, T>(A, shs, e2, cs)));
                     k_bi_update<T><<<ewg(k_bi_update<T>, n), 256, 0, cs>>>(n, x, r, phs, shs, sv, t, rh, st, part, tk);
@@ -1583,7 +1815,7 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, double 
                 GK_CUDA(cudaGetLastError());
                 return GK_OK;
             }));
-            C->kb = b; C->kx = x; C->kmethod = method; C->kprec = prec; C->km = m;
+            C->kb = b; C->kx = x; C->kmethod = method; C->kprec = pkey; C->km = m;
             C->kchunk = chunk; C->kv = C->vecs.ptr;
         }
         GK_TRY(read_hdr(C, s));
@@ -1651,19 +1883,19 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, double 
 
 // one solve on the multi-kernel engine (instantiated per value type)
 template <typename V, typename T>
-gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, bool prec, double tol,
+gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t bs, double tol,
                    int32_t max_iters, int32_t m, cudaStream_t s, SolveOut* out, bool inner);
 
-extern template gk_status solve_mk<double, double>(gk_matrix, const double*, double*, int, bool,
+extern template gk_status solve_mk<double, double>(gk_matrix, const double*, double*, int, int, int32_t,
                                                    double, int32_t, int32_t, cudaStream_t,
                                                    SolveOut*, bool);
-extern template gk_status solve_mk<float, float>(gk_matrix, const float*, float*, int, bool,
+extern template gk_status solve_mk<float, float>(gk_matrix, const float*, float*, int, int, int32_t,
                                                  double, int32_t, int32_t, cudaStream_t, SolveOut*,
                                                  bool);
 extern template gk_status solve_mk<__nv_bfloat16, float>(gk_matrix, const float*, float*, int,
-                                                         bool, double, int32_t, int32_t,
+                                                         int, int32_t, double, int32_t, int32_t,
                                                          cudaStream_t, SolveOut*, bool);
-extern template gk_status solve_mk<__half, float>(gk_matrix, const float*, float*, int, bool,
+extern template gk_status solve_mk<__half, float>(gk_matrix, const float*, float*, int, int, int32_t,
                                                   double, int32_t, int32_t, cudaStream_t,
                                                   SolveOut*, bool);
 

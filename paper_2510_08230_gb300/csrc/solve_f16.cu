@@ -2,6 +2,6 @@
 #include "solve_engine.cuh"
 
 namespace gk {
-template gk_status solve_mk<__half, float>(gk_matrix, const float*, float*, int, bool, double,
+template gk_status solve_mk<__half, float>(gk_matrix, const float*, float*, int, int, int32_t, double,
                                            int32_t, int32_t, cudaStream_t, SolveOut*, bool);
 }  // namespace gk

@@ -2,6 +2,6 @@
 #include "solve_engine.cuh"
 
 namespace gk {
-template gk_status solve_mk<double, double>(gk_matrix, const double*, double*, int, bool, double, int32_t,
+template gk_status solve_mk<double, double>(gk_matrix, const double*, double*, int, int, int32_t, double, int32_t,
                                       int32_t, cudaStream_t, SolveOut*, bool);
 }  // namespace gk

@@ -52,11 +52,13 @@ class SolveRequest:
 
 def matrix_bytes(m, refined):
     """Device bytes that stay with a cached matrix: FP64 CSR arrays, the
-    solver workspace its handle keeps (up to 10 FP64 vectors), and, once a
-    refined solve used it, the FP32 copy with its own FP32 workspace."""
-    b = 4 * (m.n + 1) + 12 * m.nnz + 10 * 8 * m.n
+    padded copy the solvers may keep for their SpMV (ELL or SELL-P, at most
+    1.2 x nnz entries), the solver workspace its handle keeps (up to 10 FP64
+    vectors), and, once a refined solve used it, the FP32 copy with its own
+    padded copy and FP32 workspace."""
+    b = 4 * (m.n + 1) + 12 * m.nnz + int(1.2 * 12 * m.nnz) + 10 * 8 * m.n
     if refined:
-        b += 4 * (m.n + 1) + 8 * m.nnz + 10 * 4 * m.n
+        b += 4 * (m.n + 1) + 8 * m.nnz + int(1.2 * 8 * m.nnz) + 10 * 4 * m.n
     return b
 
 
@@ -135,25 +137,27 @@ class SolveServer:
             refined = req.precision == "ir32"
             need = request_bytes(req, self.small_n)
             entry = self.cache.get(req.key)
-            mb = 0 if entry is not None else matrix_bytes(req.m, refined)
+            if entry is None:
+                mb = matrix_bytes(req.m, refined)
+            elif refined and not entry[3]:  # a cached matrix gains its FP32 copy
+                mb = matrix_bytes(req.m, True) - matrix_bytes(req.m, False)
+            else:
+                mb = 0
             if self.used + need + mb > self.budget:
                 self._evict(need + mb, keep=req.key)
                 if self.used + need + mb > self.budget:
                     return  # head of line waits for memory
             self.queue.popleft()
             req.need = need
-            self.used += need
+            self.used += need + mb
             if entry is None:
                 self.cache[req.key] = [None, mb, 1, refined]
-                self.used += mb
             else:
                 entry[2] += 1
                 self.cache.move_to_end(req.key)
-                if refined and not entry[3]:
-                    extra = matrix_bytes(req.m, True) - matrix_bytes(req.m, False)
-                    entry[1] += extra
+                if mb:
+                    entry[1] += mb
                     entry[3] = True
-                    self.used += extra
             small = req.m.n <= self.small_n and req.precision == "f64" and \
                 req.method in ("cg", "bicgstab")
             req.batched = small

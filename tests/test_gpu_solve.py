@@ -346,3 +346,67 @@ def test_f16_stored_solve(method):
     if method == "cg":
         _, i2 = _gpu_solve(m, b, method, 1, 1e-5, dtype="f16", engine=2)
         assert i2["return"] == gk.GK_ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------- block-Jacobi
+
+
+def _block_diag_csr(bs, nb, seed):
+    rng = np.random.default_rng(seed)
+    d = np.zeros((bs * nb, bs * nb))
+    for k in range(nb):
+        q = rng.standard_normal((bs, bs))
+        d[k * bs:(k + 1) * bs, k * bs:(k + 1) * bs] = q @ q.T + bs * np.eye(bs)
+    n = bs * nb
+    return W.CSR(n, n, np.arange(0, n * n + 1, n), np.tile(np.arange(n), n), d.reshape(-1)), d
+
+
+@pytest.mark.parametrize("method", ["cg", "bicgstab", "cgs", "gmres"])
+@pytest.mark.parametrize("case,bs", [("diff3d_12", 8), ("convdiff_300", 5), ("banded_2000", 32)])
+def test_block_jacobi_solvers(method, case, bs):
+    """Block-Jacobi (diagonal blocks of bs rows) against the oracle: the true
+    residual meets tol and the iteration count is close to the oracle's."""
+    m, b = CASES[case]()
+    if method == "cg" and case == "convdiff_300":
+        pytest.skip("CG needs an SPD matrix")
+    x, info = _gpu_solve(m, b, method, "block_jacobi", 1e-10, block_size=bs, engine=0)
+    assert info["return"] == gk.GK_OK, info
+    assert oracle.true_rel_residual(m, b, x) <= 1e-10
+    xo, io = oracle.solve(m, b, method=METHOD[method], precond=2, block_size=bs, tol=1e-10,
+                          max_iters=5000)
+    assert io["status"] == oracle.OK
+    assert info["iters"] <= max(io["iters"] + 30, 1.5 * io["iters"]), (info, io)
+
+
+def test_block_jacobi_exact_on_block_diagonal_and_size_one_is_jacobi():
+    m, d = _block_diag_csr(4, 50, 3)
+    b = np.random.default_rng(4).standard_normal(m.n)
+    for method in ("cg", "bicgstab", "cgs", "gmres"):
+        x, info = _gpu_solve(m, b, method, "block_jacobi", 1e-12, block_size=4)
+        assert info["return"] == gk.GK_OK and info["iters"] == 1, (method, info)
+        assert np.allclose(x, np.linalg.solve(d, b), rtol=1e-11, atol=1e-12)
+    mc, bc = CASES["diff3d_12"]()
+    _, i1 = _gpu_solve(mc, bc, "cg", 1, 1e-10, engine=1)
+    _, i2 = _gpu_solve(mc, bc, "cg", "block_jacobi", 1e-10, block_size=1)
+    assert abs(i1["iters"] - i2["iters"]) <= 1, (i1, i2)
+
+
+def test_block_jacobi_padded_formats_refinement_and_errors():
+    m, b = CASES["diff3d_12"]()
+    for fmt in ("ell", "sellp"):
+        x, info = _gpu_solve(m, b, "cg", "block_jacobi", 1e-10, block_size=6, fmt=fmt)
+        assert info["return"] == gk.GK_OK and oracle.true_rel_residual(m, b, x) <= 1e-10
+    x, info = _gpu_solve(m, b, "cg", "block_jacobi", 1e-10, block_size=12, dtype="mixed", mixed=1)
+    assert info["return"] == gk.GK_OK and oracle.true_rel_residual(m, b, x) <= 1e-10
+    for engine in (2, 3):
+        _, info = _gpu_solve(m, b, "cg", "block_jacobi", 1e-10, block_size=4, engine=engine)
+        assert info["return"] == gk.GK_ERR_UNSUPPORTED
+    _, info = _gpu_solve(m, b, "cg", "block_jacobi", 1e-10, block_size=33)
+    assert info["return"] == gk.GK_ERR_INVALID
+    sing = W.CSR(2, 2, np.array([0, 2, 4]), np.array([0, 1, 0, 1]), np.array([1.0, 2.0, 2.0, 4.0]))
+    _, info = _gpu_solve(sing, np.ones(2), "gmres", "block_jacobi", 1e-10, block_size=2)
+    assert info["return"] == gk.GK_ERR_ZERO_DIAG
+    # a zero diagonal inside a non-singular block is fine for block-Jacobi
+    piv = W.CSR(2, 2, np.array([0, 1, 2]), np.array([1, 0]), np.array([2.0, 3.0]))
+    x, info = _gpu_solve(piv, np.array([4.0, 9.0]), "gmres", "block_jacobi", 1e-12, block_size=2)
+    assert info["return"] == gk.GK_OK and np.allclose(x, [3.0, 2.0])
