@@ -282,6 +282,37 @@ def per_iteration_protocol(gk, W, torch, dev, iters=1000):
     return out
 
 
+def precond_compare(gk, W, torch, dev):
+    """CG and GMRES(30) to a true 1e-10 on the 128^3 diffusion matrix (FP64)
+    without a preconditioner, with Jacobi, and with block-Jacobi of 4, 8 and
+    16 rows: iterations and wall time (host clock around the solve).  GMRES
+    is capped at 5000 steps (status 1 if it had not converged)."""
+    m = W.diffusion_3d(128)
+    b = torch.from_numpy(W.uniform_vector(m.n, W.SEED_BASE + 3)).to(dev)
+    A = gk.Matrix.from_csr(m)
+    out = {"workload": "128^3 diffusion FP64, tol 1e-10, x0 = 0"}
+    for method in ("cg", "gmres"):
+        res = {}
+        for label, kw in (("none", dict(precond=None)), ("jacobi", dict(precond="jacobi")),
+                          ("block4", dict(precond="block_jacobi", block_size=4)),
+                          ("block8", dict(precond="block_jacobi", block_size=8)),
+                          ("block16", dict(precond="block_jacobi", block_size=16))):
+            x = torch.zeros_like(b)
+            A.solve(b, x, method=method, tol=1e-10, max_iters=20, **kw)  # warm-up (setup)
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cap = 20000 if method == "cg" else 5000  # GMRES without M: bounded
+            info = A.solve(b, x, method=method, tol=1e-10, max_iters=cap, **kw)
+            torch.cuda.synchronize()
+            res[label] = {"ms": round((time.perf_counter() - t0) * 1000, 2),
+                          "iters": info["iters"], "status": info["return"],
+                          "rel_res_true": info["rel_res_true"]}
+        out[method] = res
+    A.close()
+    return out
+
+
 def abi_overhead(gk, W, torch, dev):
     """The paper's binding-overhead experiment (Section 5.3) for this
     library's ctypes binding: SpMV time through the Python binding against
@@ -691,13 +722,14 @@ def main():
     del items, step_items
     torch.cuda.empty_cache()
 
-    cg = ir = batched = serving = per_iter = abi = None
+    cg = ir = batched = serving = per_iter = abi = pre = None
     if rank == 0 and not args.no_cg:
         cg = cg_solves_per_s(gk, W, torch, dev)
     if rank == 0 and not args.no_solvers:
         ir = ir_compare(gk, W, torch, dev)
         per_iter = per_iteration_protocol(gk, W, torch, dev)
         abi = abi_overhead(gk, W, torch, dev)
+        pre = precond_compare(gk, W, torch, dev)
         batched = batched_compare(gk, W, torch, dev)
     if rank == 0 and not args.no_serving:
         serving = serving_bench(gk, W, torch, dev)
@@ -712,7 +744,7 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "step": step_detail, "sweep": sweep, "roofline": roofline, "cpu_baseline": cpu,
             "e2e": e2e, "cg": cg, "ir_128cubed": ir, "per_iteration_1000": per_iter,
-            "abi_overhead": abi,
+            "abi_overhead": abi, "preconditioners": pre,
             "batched_2048": batched,
             "serving": serving, "clocks": clk,
             "gpu_launches": launches}
