@@ -856,17 +856,61 @@ __device__ __forceinline__ void row_pair_padded(const int32_t* __restrict__ pc,
     }
 }
 
+// Two pairs of adjacent rows (a0, a0+1) and (b0, b0+1), their loads issued
+// together: twice the bytes in flight of row_pair_padded.
+template <typename T, typename V>
+__device__ __forceinline__ void row_quad_padded(const int32_t* __restrict__ pc,
+                                                const V* __restrict__ pv,
+                                                const T* __restrict__ x, int64_t a0, int64_t b0,
+                                                int64_t step, int32_t len, T (&s)[4]) {
+    using P = typename Pair2<V>::type;
+    s[0] = s[1] = s[2] = s[3] = T(0);
+#pragma unroll 2
+    for (int32_t j = 0; j < len; ++j) {
+        const int64_t ja = a0 + (int64_t)j * step, jb = b0 + (int64_t)j * step;
+        const int2 ca = __ldcs(reinterpret_cast<const int2*>(pc + ja));
+        const int2 cb = __ldcs(reinterpret_cast<const int2*>(pc + jb));
+        const P pa = *reinterpret_cast<const P*>(pv + ja);
+        const P pb = *reinterpret_cast<const P*>(pv + jb);
+        T v0, v1, v2, v3;
+        unpack2<T>(pa, v0, v1);
+        unpack2<T>(pb, v2, v3);
+        const T x0 = ca.x >= 0 ? __ldg(x + ca.x) : T(0);
+        const T x1 = ca.y >= 0 ? __ldg(x + ca.y) : T(0);
+        const T x2 = cb.x >= 0 ? __ldg(x + cb.x) : T(0);
+        const T x3 = cb.y >= 0 ? __ldg(x + cb.y) : T(0);
+        s[0] = fmadd(v0, x0, s[0]);
+        s[1] = fmadd(v1, x1, s[1]);
+        s[2] = fmadd(v2, x2, s[2]);
+        s[3] = fmadd(v3, x3, s[3]);
+    }
+}
+
 // ELL: one thread per pair of adjacent rows (stride is a multiple of 32,
-// so pairs never straddle it), column-major coalesced paired loads.
-template <typename V, typename T, class Epi>
+// so pairs never straddle it), column-major coalesced paired loads.  With
+// QUAD a thread takes pairs q and q + G (G = grid threads) together while
+// both exist: more loads in flight when a thread has few pairs to do.
+template <typename V, typename T, class Epi, bool QUAD = false>
 __global__ void __launch_bounds__(256)
 k_ell(int32_t n, int64_t stride, int32_t K, const int32_t* __restrict__ ec,
       const V* __restrict__ ev, const T* __restrict__ x, Epi epi) {
     if (epi.skip()) return;
     AccArr<Epi> acc{};
     const int64_t npairs = ((int64_t)n + 1) / 2;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npairs;
-         q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (QUAD) {
+        for (; q + G < npairs; q += 2 * G) {
+            const int64_t i = 2 * q, k = 2 * (q + G);
+            T sq[4];
+            row_quad_padded<T, V>(ec, ev, x, i, k, stride, K, sq);
+            epi.row(i, sq[0], acc.v);
+            epi.row(i + 1, sq[1], acc.v);
+            epi.row(k, sq[2], acc.v);
+            if (k + 1 < n) epi.row(k + 1, sq[3], acc.v);
+        }
+    }
+    for (; q < npairs; q += G) {
         const int64_t i = 2 * q;
         T s0, s1;
         row_pair_padded<T, V>(ec, ev, x, i, stride, K, s0, s1);
@@ -1024,11 +1068,25 @@ gk_status launch_spmv_rows(gk_matrix A, const T* x, const Epi& epi, cudaStream_t
         }
     } else if (A->fmt == GK_ELL) {
         // grid-stride kernels: one full wave of resident blocks, no ragged second wave
-        static thread_local int occ = 0;
-        if (!occ) occ = std::min(occupancy_blocks(k_ell<V, T, Epi>, 256, 0), 8);
-        int64_t need = ((A->n + 1) / 2 + 255) / 256;
-        grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * occ));
-        k_ell<V, T, Epi><<<grid, 256, 0, s>>>(A->n, A->stride, A->K, A->col, (const V*)A->val, x, epi);
+        static const int quad = [] {
+            const char* e = getenv("GK_ELL_QUAD");
+            return e ? atoi(e) : 1;
+        }();
+        if (quad) {
+            static thread_local int occ = 0;
+            if (!occ) occ = std::min(occupancy_blocks(k_ell<V, T, Epi, true>, 256, 0), 8);
+            int64_t need = ((A->n + 1) / 2 + 255) / 256;
+            grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * occ));
+            k_ell<V, T, Epi, true><<<grid, 256, 0, s>>>(A->n, A->stride, A->K, A->col,
+                                                        (const V*)A->val, x, epi);
+        } else {
+            static thread_local int occ = 0;
+            if (!occ) occ = std::min(occupancy_blocks(k_ell<V, T, Epi>, 256, 0), 8);
+            int64_t need = ((A->n + 1) / 2 + 255) / 256;
+            grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * occ));
+            k_ell<V, T, Epi><<<grid, 256, 0, s>>>(A->n, A->stride, A->K, A->col, (const V*)A->val,
+                                                  x, epi);
+        }
     } else if (A->S % 2 == 0) {
         static thread_local int occ = 0;
         if (!occ) occ = std::min(occupancy_blocks(k_sellp_pairs<V, T, Epi>, 256, 0), 8);
