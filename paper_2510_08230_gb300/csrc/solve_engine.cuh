@@ -399,6 +399,33 @@ struct CgBetaFin {
 
 // x += alpha p ; r -= alpha q ; z = D^-1 r ; <r,z>, <r,r>
 template <typename T>
+__device__ __forceinline__ void cg_update_pack(int64_t j, int32_t n, bool vec, T alpha, T* x, T* r,
+                                               T* z, const T* p, const T* q, const T* dinv,
+                                               T (&a)[2]) {
+    constexpr int N = Pack<T>::N;
+    const Pack<T> P = pld(p, j, n, vec), Q = pld(q, j, n, vec);
+    Pack<T> X = pld(x, j, n, vec), R = pld(r, j, n, vec);
+    Pack<T> Z = dinv ? pld(dinv, j, n, vec) : Pack<T>{};
+#pragma unroll
+    for (int c = 0; c < N; ++c) {  // padding lanes are 0 and add 0
+        X.v[c] = fmadd(alpha, P.v[c], X.v[c]);
+        R.v[c] = fmadd(-alpha, Q.v[c], R.v[c]);
+        if (dinv) {
+            Z.v[c] = Z.v[c] * R.v[c];
+            a[0] = fmadd(R.v[c], Z.v[c], a[0]);
+        }
+        a[1] = fmadd(R.v[c], R.v[c], a[1]);
+    }
+    pst(x, j, n, vec, X);
+    pst(r, j, n, vec, R);
+    if (dinv) pst(z, j, n, vec, Z);
+}
+
+// A thread visits packs j, j + G, j + 2G, ... in that order.  FP32 takes
+// two of them per step (16-byte accesses only, while both are whole and
+// every pointer is aligned) so that twice the bytes are in flight; the
+// order of the additions is the same as one pack per step.
+template <typename T>
 __global__ void EW_BOUNDS k_cg_update(int32_t n, T* __restrict__ x, T* __restrict__ r, T* __restrict__ z,
                             const T* __restrict__ p, const T* __restrict__ q,
                             const T* __restrict__ dinv, KState* st, double* partials,
@@ -408,35 +435,87 @@ __global__ void EW_BOUNDS k_cg_update(int32_t n, T* __restrict__ x, T* __restric
     const T alpha = (T)st->alpha;
     const bool vec = al16(x) && al16(r) && al16(z) && al16(p) && al16(q) && al16(dinv);
     T a[2] = {T(0), T(0)};
-    PACK_LOOP(j, n, T) {
-        const Pack<T> P = pld(p, j, n, vec), Q = pld(q, j, n, vec);
-        Pack<T> X = pld(x, j, n, vec), R = pld(r, j, n, vec);
-        Pack<T> Z = dinv ? pld(dinv, j, n, vec) : Pack<T>{};
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    const int64_t np = ((int64_t)n + N - 1) / N;
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if constexpr (sizeof(T) == 4) {
+        if (vec) {
+            const int64_t whole = (int64_t)n / N;  // packs with N elements
+            using P4 = Pack<T>;
+            for (; j + G < whole; j += 2 * G) {
+                const int64_t j1 = j + G;
+                const P4 P0 = reinterpret_cast<const P4*>(p)[j], P1 = reinterpret_cast<const P4*>(p)[j1];
+                const P4 Q0 = reinterpret_cast<const P4*>(q)[j], Q1 = reinterpret_cast<const P4*>(q)[j1];
+                P4 X0 = reinterpret_cast<P4*>(x)[j], X1 = reinterpret_cast<P4*>(x)[j1];
+                P4 R0 = reinterpret_cast<P4*>(r)[j], R1 = reinterpret_cast<P4*>(r)[j1];
+                P4 Z0{}, Z1{};
+                if (dinv) {
+                    Z0 = reinterpret_cast<const P4*>(dinv)[j];
+                    Z1 = reinterpret_cast<const P4*>(dinv)[j1];
+                }
 #pragma unroll
-        for (int c = 0; c < N; ++c) {  // padding lanes are 0 and add 0
-            X.v[c] = fmadd(alpha, P.v[c], X.v[c]);
-            R.v[c] = fmadd(-alpha, Q.v[c], R.v[c]);
-            if (dinv) {
-                Z.v[c] = Z.v[c] * R.v[c];
-                a[0] = fmadd(R.v[c], Z.v[c], a[0]);
+                for (int c = 0; c < N; ++c) {
+                    X0.v[c] = fmadd(alpha, P0.v[c], X0.v[c]);
+                    R0.v[c] = fmadd(-alpha, Q0.v[c], R0.v[c]);
+                    if (dinv) {
+                        Z0.v[c] = Z0.v[c] * R0.v[c];
+                        a[0] = fmadd(R0.v[c], Z0.v[c], a[0]);
+                    }
+                    a[1] = fmadd(R0.v[c], R0.v[c], a[1]);
+                }
+#pragma unroll
+                for (int c = 0; c < N; ++c) {
+                    X1.v[c] = fmadd(alpha, P1.v[c], X1.v[c]);
+                    R1.v[c] = fmadd(-alpha, Q1.v[c], R1.v[c]);
+                    if (dinv) {
+                        Z1.v[c] = Z1.v[c] * R1.v[c];
+                        a[0] = fmadd(R1.v[c], Z1.v[c], a[0]);
+                    }
+                    a[1] = fmadd(R1.v[c], R1.v[c], a[1]);
+                }
+                reinterpret_cast<P4*>(x)[j] = X0;
+                reinterpret_cast<P4*>(x)[j1] = X1;
+                reinterpret_cast<P4*>(r)[j] = R0;
+                reinterpret_cast<P4*>(r)[j1] = R1;
+                if (dinv) {
+                    reinterpret_cast<P4*>(z)[j] = Z0;
+                    reinterpret_cast<P4*>(z)[j1] = Z1;
+                }
             }
-            a[1] = fmadd(R.v[c], R.v[c], a[1]);
         }
-        pst(x, j, n, vec, X);
-        pst(r, j, n, vec, R);
-        if (dinv) pst(z, j, n, vec, Z);
     }
+    for (; j < np; j += G) cg_update_pack(j, n, vec, alpha, x, r, z, p, q, dinv, a);
     finish_ew<2>(a, partials, ticket, CgUpdFin{st, pkind});
 }
 
-// p = z + beta p
+// p = z + beta p (FP32: two packs per step, as in k_cg_update)
 template <typename T>
 __global__ void EW_BOUNDS k_cg_p(int32_t n, T* __restrict__ p, const T* __restrict__ z, const KState* st) {
     if (halted(st)) return;
     constexpr int N = Pack<T>::N;
     const T beta = (T)st->beta;
     const bool vec = al16(p) && al16(z);
-    PACK_LOOP(j, n, T) {
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    const int64_t np = ((int64_t)n + N - 1) / N;
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if constexpr (sizeof(T) == 4) {
+        if (vec) {
+            const int64_t whole = (int64_t)n / N;
+            using P4 = Pack<T>;
+            for (; j + G < whole; j += 2 * G) {
+                P4 P0 = reinterpret_cast<P4*>(p)[j], P1 = reinterpret_cast<P4*>(p)[j + G];
+                const P4 Z0 = reinterpret_cast<const P4*>(z)[j], Z1 = reinterpret_cast<const P4*>(z)[j + G];
+#pragma unroll
+                for (int c = 0; c < N; ++c) {
+                    P0.v[c] = fmadd(beta, P0.v[c], Z0.v[c]);
+                    P1.v[c] = fmadd(beta, P1.v[c], Z1.v[c]);
+                }
+                reinterpret_cast<P4*>(p)[j] = P0;
+                reinterpret_cast<P4*>(p)[j + G] = P1;
+            }
+        }
+    }
+    for (; j < np; j += G) {
         Pack<T> P = pld(p, j, n, vec);
         const Pack<T> Z = pld(z, j, n, vec);
 #pragma unroll

@@ -697,9 +697,11 @@ k_coo_warp(int32_t n, int64_t nnz, const int32_t* __restrict__ rows,
         load_group<G>(ci, kg, nnz, full, c);
         load_group<G>(va, kg, nnz, full, v);
         const int32_t rnext = kg + G < nnz ? __ldg(rows + kg + G) : INT32_MAX;
+        // x gathers at uniformly random columns reuse nothing in L1: read
+        // them through L2 only (.cg), leaving L1 to the streamed triplets
         T xv[G];
 #pragma unroll
-        for (int q = 0; q < G; ++q) xv[q] = kg + q < nnz ? __ldg(x + c[q]) : T(0);
+        for (int q = 0; q < G; ++q) xv[q] = kg + q < nnz ? __ldcg(x + c[q]) : T(0);
 #pragma unroll
         for (int q = 0; q < G; ++q) {
             if (kg + q < nnz) {
