@@ -1,13 +1,13 @@
 """Benchmark: SpMV sweep over CSR / ELL / SELL-P, FP64 and FP32, on the 3D
 7-point Laplacian 256^3 and the Zipf(1.8) power-law matrix with 2^22 rows
-(the paper's SpMV benchmark x = A b with random b, Section 5.1, on
+(the paper's SpMV benchmark x = A b with random b, Section 6.1, on
 synthetic stand-ins for its SuiteSparse set), plus CG solves/s on the 64x64
 5-point Laplacian to a 1e-10 relative residual.
 
 One step = one apply per (matrix, dtype) in the fastest of CSR / ELL /
 SELL-P / COO for that matrix (picked by a short timing pass before the
 timed region, as the paper reports each library's best-performing format,
-Section 5).  value = algorithmic bytes of the step / device time (GB/s),
+Section 6).  value = algorithmic bytes of the step / device time (GB/s),
 where every matrix counts its CSR algorithmic bytes = nnz*(value+index
 bytes) + 4*(n+1) + x and y once, whichever format ran.  Every format is also
 timed and listed under "sweep" with its own algorithmic bytes (ELL/SELL-P
@@ -258,7 +258,7 @@ def ir_compare(gk, W, torch, dev):
 
 
 def per_iteration_protocol(gk, W, torch, dev, iters=1000):
-    """The paper's solver protocol (Section 5.2.1): a fixed 1000 iterations
+    """The paper's solver protocol (Section 6.2.1): a fixed 1000 iterations
     of CG, CGS and GMRES(30) without a preconditioner, reported as time per
     iteration, here on the 128^3 diffusion matrix (FP64).  A method that
     breaks down or reaches a residual of 1e-30 first is timed over the
@@ -314,7 +314,7 @@ def precond_compare(gk, W, torch, dev):
 
 
 def abi_overhead(gk, W, torch, dev):
-    """The paper's binding-overhead experiment (Section 5.3) for this
+    """The paper's binding-overhead experiment (Section 6.3) for this
     library's ctypes binding: SpMV time through the Python binding against
     the native C driver (native/abi_overhead.c) on the same matrices, both
     timed per call on a host clock with a device synchronisation after each
@@ -324,7 +324,7 @@ def abi_overhead(gk, W, torch, dev):
     from paper_2510_08230_gb300 import _build
     exe = _build.build_native()
     out = {"workload": "2D 5-point Laplacians N x N, FP64, CSR and COO, x on the device; "
-                       "per-call host clock after cudaDeviceSynchronize (paper Section 5.3)",
+                       "per-call host clock after cudaDeviceSynchronize (paper Section 6.3)",
            "rows": []}
     for N in (16, 64, 256, 1024, 2048):
         m = W.laplacian_2d(N)

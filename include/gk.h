@@ -1,11 +1,11 @@
 /*
  * gk.h - C ABI of the GB300 sparse operator library.
  *
- * The calls follow the paper's linear-operator model (Section 3.4,
+ * The calls follow the paper's linear-operator model (Section 4.2,
  * "Ginkgo's Linear Operator Abstraction"): a matrix is created once, then
  * "applied" to a vector (an SpMV), and a solver is "applied" to a
  * right-hand side b and an initial guess x, which it overwrites with the
- * solution (Section 2.3 "pyGinkgo API", Listing 1).  Stopping follows the
+ * solution (Section 3.5 "pyGinkgo API", Listing 1).  Stopping follows the
  * config solver's criteria (Listing 2): an iteration cap or a residual
  * reduction relative to ||b||_2.
  *
@@ -62,13 +62,13 @@ typedef enum { GK_F64 = 0, GK_F32 = 1, GK_BF16 = 2, GK_F16 = 3 } gk_dtype;
  *           (num_slices + 1 entries); entry j of row i = s*S + t at
  *           (slice_sets[s] + j)*S + t; padding col = -1, value = +0.0,
  *           including the virtual rows past n in the last slice.
- * The paper names "other matrix formats" beside CSR and COO (Section 2)
+ * The paper plans formats beyond CSR and COO (Section 3.1)
  * without defining them; these layouts are this library's definition. */
 typedef enum { GK_CSR = 0, GK_ELL = 1, GK_SELLP = 2, GK_COO = 3 } gk_format;
 
 /* Krylov methods: CG (Hestenes-Stiefel), BiCGSTAB (van der Vorst), GMRES(m),
  * and CGS (Sonneveld's conjugate gradient squared, the solver the paper
- * benchmarks beside CG and GMRES in Section 5.2.1). */
+ * benchmarks beside CG and GMRES in Section 6.2.1). */
 typedef enum { GK_CG = 0, GK_BICGSTAB = 1, GK_GMRES = 2, GK_CGS = 3 } gk_method;
 /* Preconditioners (the config solver's Jacobi, Listing 2): point Jacobi
  * (max_block_size 1) and block-Jacobi over diagonal blocks of block_size
@@ -136,7 +136,7 @@ gk_status gk_matrix_create_csr(int32_t n, int32_t ncols, int64_t nnz,
                                gk_memory mem, void* stream, gk_matrix* out);
 
 /* Create a CSR matrix from COO triplets (COO is the paper's second
- * benchmarked format, Section 5).  Entries may come in any order; they are
+ * benchmarked format, Section 6).  Entries may come in any order; they are
  * ordered by (row, col) on the device, entries with equal (row, col) are
  * summed in their input order (float arithmetic for GK_F32/GK_BF16 input,
  * double for GK_F64), explicit zeros are kept.  Result is bit-for-bit the
@@ -178,8 +178,8 @@ gk_status gk_matrix_destroy(gk_matrix A);
  * Apply (SpMV)
  * ------------------------------------------------------------------- */
 
-/* x = A b  (a matrix LinOp's apply, Section 3.4; the paper's SpMV
- * benchmark computes x = A b, Section 5.1).  b has ncols entries, x has n.
+/* x = A b  (a matrix LinOp's apply, Section 4.2; the paper's SpMV
+ * benchmark computes x = A b, Section 6.1).  b has ncols entries, x has n.
  * Both device pointers (stream-ordered, asynchronous) or both host
  * pointers (staged, blocking).  b and x must not overlap. */
 gk_status gk_apply(gk_matrix A, const void* b, void* x, void* stream);
@@ -233,7 +233,7 @@ typedef struct {
  * right-preconditioned), CGS (Sonneveld, M^-1 on the search directions,
  * multi-kernel engine only) or GMRES(m) (right-preconditioned, Givens
  * rotations, residual estimate checked after every Arnoldi step as in
- * Section 5.2.1).  GK_OK is returned only when the recomputed true
+ * Section 6.2.1).  GK_OK is returned only when the recomputed true
  * residual meets tol; when the recurrence residual passes but the true
  * one does not, the residual is replaced by the true one and the method
  * restarts from x.  b = 0 gives x = 0 and GK_OK after 0 iterations.

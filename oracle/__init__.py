@@ -96,6 +96,10 @@ def _declare(L):
     L.or_block_jacobi_gen.restype = ctypes.c_int
     L.or_block_jacobi_apply.argtypes = [i32, i32, _f64p, _f64p, _f64p]
     L.or_block_jacobi_apply.restype = None
+    L.or_ilu0.argtypes = [i32, _i32p, _i32p, _f64p, _f64p]
+    L.or_ilu0.restype = ctypes.c_int
+    L.or_ilu0_apply.argtypes = [i32, _i32p, _i32p, _f64p, _f64p, _f64p]
+    L.or_ilu0_apply.restype = None
     for name in ("or_cg", "or_bicgstab", "or_gmres", "or_cgs"):
         f = getattr(L, name)
         f.argtypes = [i32, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.POINTER(Opts),
@@ -238,10 +242,32 @@ def block_jacobi_apply(n, bs, binv, r):
     return z
 
 
+def ilu0(m):
+    """ILU(0) factors in A's CSR pattern (L strictly lower with unit
+    diagonal implied, U on and above the diagonal).  Raises ValueError for
+    rows whose columns are not strictly ascending and ZeroDivisionError for
+    a missing diagonal or a zero pivot."""
+    lu = np.zeros(max(int(m.nnz), 1))
+    st = lib().or_ilu0(m.n, _i32(m.row_ptr), _i32(m.col_idx), _f64(m.values), lu)
+    if st == ERR_INVALID:
+        raise ValueError("ILU(0) needs strictly ascending columns in every row")
+    if st != OK:
+        raise ZeroDivisionError("missing diagonal or zero pivot")
+    return lu[:m.nnz]
+
+
+def ilu0_apply(m, lu, r):
+    """z = U^-1 L^-1 r with the factors of ilu0(m)."""
+    z = np.zeros(max(m.n, 1))
+    lib().or_ilu0_apply(m.n, _i32(m.row_ptr), _i32(m.col_idx),
+                        _f64(lu) if np.asarray(lu).size else np.zeros(1), _f64(r), z)
+    return z[:m.n]
+
+
 def solve(m, b, x0=None, method=CG, precond=0, tol=1e-10, max_iters=1000,
           krylov_dim=30, history=False, block_size=0):
     """Runs CG / BiCGSTAB / GMRES(m) / CGS; precond 0 none, 1 Jacobi,
-    2 block-Jacobi with `block_size` rows per block.  Returns (x, info
+    2 block-Jacobi with `block_size` rows per block, 3 ILU(0).  Returns (x, info
     dict[, history])."""
     x = np.zeros(m.n) if x0 is None else _f64(x0).copy()
     o = Opts(method, precond, tol, max_iters, krylov_dim, block_size)

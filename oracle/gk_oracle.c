@@ -7,20 +7,20 @@
  * helper with the CUDA library.
  *
  * What it follows:
- *  - The linear-operator model of the paper (Section 3.4 "Ginkgo's Linear
+ *  - The linear-operator model of the paper (Section 4.2 "Ginkgo's Linear
  *    Operator Abstraction"): a matrix applied to b gives A b; a solver
  *    applied to (b, x) overwrites the initial guess x with the solution
- *    (Section 2.3 "pyGinkgo API", Listing 1).
- *  - Stopping criteria of the config solver (Section 2.3, Listing 2): an
+ *    (Section 3.5 "pyGinkgo API", Listing 1).
+ *  - Stopping criteria of the config solver (Section 3.5, Listing 2): an
  *    iteration cap OR a residual-norm reduction relative to the right-hand
  *    side norm ("baseline": "rhs_norm").
  *  - GMRES with Givens rotations and a residual check after every
- *    Hessenberg update (Section 5.2.1, the GMRES discussion).
+ *    Hessenberg update (Section 6.2.1, the GMRES discussion).
  *  - CG (Hestenes-Stiefel), BiCGSTAB (van der Vorst 1992) and GMRES(m)
  *    (Saad-Schultz 1986) in their textbook forms; the paper prints no
  *    pseudo-code for them.
  *  - CSR / ELL / SELL-P layouts: the paper names "other matrix formats"
- *    (Section 2) without defining them; the layouts below are this
+ *    (Section 3.1) without defining them; the layouts below are this
  *    library's stated readings (column-major padded slices, col = -1 and
  *    value = +0.0 for padding).
  *
@@ -58,7 +58,7 @@ static double dot(int32_t n, const double* u, const double* v)
 static double nrm2(int32_t n, const double* u) { return sqrt(dot(n, u, u)); }
 
 /* ------------------------------------------------------------------ */
-/* SpMV  y = alpha * A x + beta * y  (Section 3.4: a matrix LinOp's     */
+/* SpMV  y = alpha * A x + beta * y  (Section 4.2: a matrix LinOp's     */
 /* apply is an SpMV; the advanced form adds alpha and beta)            */
 /* ------------------------------------------------------------------ */
 
@@ -93,7 +93,7 @@ void or_spmv_csr(int32_t n, const int32_t* rp, const int32_t* ci,
  * each adds val * x[col] to its row's sum (Neumaier-compensated, as in the
  * CSR check mode, when compensated = 1); then y_i = alpha s_i + beta y_i
  * for every row, including rows without entries (beta == 0: y not read).
- * The paper benchmarks COO beside CSR (Section 5.1).  Returns -1 if a
+ * The paper benchmarks COO beside CSR (Section 6.1).  Returns -1 if a
  * triplet lies outside the matrix, else 0. */
 int or_spmv_coo(int32_t n, int32_t ncols, int64_t nnz, const int32_t* row,
                 const int32_t* col, const double* val, const double* x, double alpha,
@@ -156,8 +156,8 @@ int or_spmv_csr_omp(int32_t n, const int32_t* rp, const int32_t* ci,
 }
 
 /* ------------------------------------------------------------------ */
-/* COO -> CSR (COO and CSR are the paper's benchmarked formats,        */
-/* Section 5 "Benchmarks were conducted for both CSR and COO")         */
+/* COO -> CSR (COO and CSR are the two formats the paper benchmarks,  */
+/* Section 6.1)                                                        */
 /* ------------------------------------------------------------------ */
 
 typedef struct {
@@ -234,7 +234,7 @@ int64_t or_coo_to_csr(int32_t n, int32_t ncols, int64_t nnz,
 
 /* ------------------------------------------------------------------ */
 /* CSR -> ELL and CSR -> SELL-P (layouts are this library's reading:   */
-/* the paper only mentions "other matrix formats" in Section 2)        */
+/* the paper plans further formats without defining them, Section 3.1)*/
 /* ------------------------------------------------------------------ */
 
 /* ELL width K = longest row. */
@@ -423,13 +423,83 @@ void or_block_jacobi_apply(int32_t n, int32_t bs, const double* binv, const doub
     }
 }
 
+/* ILU(0), the incomplete LU factorisation without fill-in behind the
+ * paper's Ilu preconditioner (Listing 1; Section 5 names ILU and IC among
+ * the preconditioners pyGinkgo binds).  It follows the textbook IKJ form (Saad,
+ * "Iterative Methods for Sparse Linear Systems", 2nd ed., Section 10.3.2,
+ * the ILU(0) algorithm): for each row i in order, for each stored k < i in
+ * ascending order, a_ik /= a_kk and then a_ij -= a_ik * a_kj for every
+ * stored j > k of row k that is also stored in row i.  Entries outside the
+ * pattern are dropped.  lu[] (nnz) receives L's strictly lower part (unit
+ * diagonal implied) and U (diagonal and above) in A's CSR order.
+ * Rows need their columns strictly ascending (no duplicates): otherwise
+ * OR_ERR_INVALID.  A row without a stored diagonal, or a zero pivot u_ii,
+ * is OR_ERR_ZERO_DIAG. */
+static int32_t diag_pos(const int32_t* rp, const int32_t* ci, int32_t i)
+{
+    for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
+        if (ci[p] == i) return p;
+    return -1;
+}
+
+int or_ilu0(int32_t n, const int32_t* rp, const int32_t* ci, const double* va, double* lu)
+{
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t p = rp[i] + 1; p < rp[i + 1]; ++p)
+            if (ci[p] <= ci[p - 1]) return OR_ERR_INVALID;
+        if (diag_pos(rp, ci, i) < 0) return OR_ERR_ZERO_DIAG;
+    }
+    for (int64_t p = 0; p < (int64_t)rp[n]; ++p) lu[p] = va[p];
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t p = rp[i]; p < rp[i + 1] && ci[p] < i; ++p) {
+            const int32_t k = ci[p];
+            const int32_t dk = diag_pos(rp, ci, k);
+            lu[p] = lu[p] / lu[dk];
+            for (int32_t q = dk + 1; q < rp[k + 1]; ++q) {
+                const int32_t j = ci[q];
+                for (int32_t t = p + 1; t < rp[i + 1]; ++t)
+                    if (ci[t] == j) {
+                        lu[t] = lu[t] - lu[p] * lu[q];
+                        break;
+                    }
+            }
+        }
+        if (lu[diag_pos(rp, ci, i)] == 0.0) return OR_ERR_ZERO_DIAG;
+    }
+    return OR_OK;
+}
+
+/* z = U^{-1} L^{-1} r with the factors of or_ilu0.  Forward substitution
+ * in ascending row order, y_i = r_i - sum_{j<i} l_ij y_j with the terms
+ * subtracted in ascending column order; back substitution in descending
+ * row order, z_i = (y_i - sum_{j>i} u_ij z_j) / u_ii with the terms
+ * subtracted in descending column order (each unknown is used in the order
+ * the substitution produced it). */
+void or_ilu0_apply(int32_t n, const int32_t* rp, const int32_t* ci, const double* lu,
+                   const double* r, double* z)
+{
+    double* y = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int32_t i = 0; i < n; ++i) {
+        double s = r[i];
+        for (int32_t p = rp[i]; p < rp[i + 1] && ci[p] < i; ++p) s = s - lu[p] * y[ci[p]];
+        y[i] = s;
+    }
+    for (int32_t i = n - 1; i >= 0; --i) {
+        const int32_t d = diag_pos(rp, ci, i);
+        double s = y[i];
+        for (int32_t p = rp[i + 1] - 1; p > d; --p) s = s - lu[p] * z[ci[p]];
+        z[i] = s / lu[d];
+    }
+    free(y);
+}
+
 /* ------------------------------------------------------------------ */
 /* Solvers                                                             */
 /* ------------------------------------------------------------------ */
 
 typedef struct {
     int32_t method;     /* 0 CG, 1 BiCGSTAB, 2 GMRES, 3 CGS */
-    int32_t precond;    /* 0 none, 1 Jacobi, 2 block-Jacobi */
+    int32_t precond;    /* 0 none, 1 Jacobi, 2 block-Jacobi, 3 ILU(0) */
     double tol;         /* relative to ||b||_2 ("rhs_norm" baseline) */
     int32_t max_iters;  /* CG: iterations; BiCGSTAB: iterations; GMRES: Arnoldi steps */
     int32_t krylov_dim; /* GMRES restart length m */
@@ -464,12 +534,16 @@ static void resid(const or_mat* A, const double* b, const double* x, double* r)
 }
 
 /* z = M^{-1} r (identity without a preconditioner) */
-/* Preconditioner M^{-1}: none (kind 0), Jacobi (1: data = 1/a_ii) or
- * block-Jacobi (2: data = the inverted diagonal blocks of bs rows). */
+/* Preconditioner M^{-1}: none (kind 0), Jacobi (1: data = 1/a_ii),
+ * block-Jacobi (2: data = the inverted diagonal blocks of bs rows) or
+ * ILU(0) (3: data = the factors of or_ilu0 in A's pattern). */
 typedef struct {
     int32_t kind;
     int32_t bs;
     double* data;
+    int32_t n;          /* ILU(0): the pattern the factors live in */
+    const int32_t* rp;
+    const int32_t* ci;
 } or_prec;
 
 static int prec_setup(int32_t n, const int32_t* rp, const int32_t* ci, const double* va,
@@ -478,6 +552,18 @@ static int prec_setup(int32_t n, const int32_t* rp, const int32_t* ci, const dou
     P->kind = o->precond;
     P->bs = o->block_size;
     P->data = NULL;
+    P->n = n;
+    P->rp = rp;
+    P->ci = ci;
+    if (P->kind == 3) {
+        P->data = (double*)malloc(sizeof(double) * (size_t)(rp[n] > 0 ? rp[n] : 1));
+        const int st = or_ilu0(n, rp, ci, va, P->data);
+        if (st != OR_OK) {
+            free(P->data);
+            return st;
+        }
+        return OR_OK;
+    }
     if (P->kind == 1) {
         P->data = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
         if (or_jacobi_gen(n, rp, ci, va, P->data) != OR_OK) {
@@ -501,6 +587,10 @@ static void prec(int32_t n, const or_prec* P, const double* r, double* z)
 {
     if (P->kind == 2) {
         or_block_jacobi_apply(n, P->bs, P->data, r, z);
+        return;
+    }
+    if (P->kind == 3) {
+        or_ilu0_apply(n, P->rp, P->ci, P->data, r, z);
         return;
     }
     for (int32_t i = 0; i < n; ++i) z[i] = P->kind == 1 ? P->data[i] * r[i] : r[i];
@@ -693,7 +783,7 @@ int or_bicgstab(int32_t n, const int32_t* rp, const int32_t* ci,
 
 /* CGS (conjugate gradient squared, Sonneveld 1989), preconditioned form
  * with M^{-1} applied to the search directions: the paper benchmarks it
- * against CuPy's CGS (Section 5.2.1).  With shadow residual rt = r_0:
+ * against CuPy's CGS (Section 6.2.1).  With shadow residual rt = r_0:
  *   rho = <rt, r>  (0: breakdown)
  *   first step after a (re)start: u = r, p = u
  *   else: beta = rho / rho_old; u = r + beta q; p = u + beta (q + beta p)
@@ -786,7 +876,7 @@ int or_cgs(int32_t n, const int32_t* rp, const int32_t* ci,
 /* GMRES(m), right-preconditioned (A M^{-1} u = b, x = M^{-1} u), modified
  * Gram-Schmidt Arnoldi, Givens rotations on the Hessenberg matrix with the
  * residual estimate |g_{k+1}| checked after every column (the GMRES
- * discussion in Section 5.2.1).  One cycle:
+ * discussion in Section 6.2.1).  One cycle:
  *   r = b - A x; beta0 = ||r||; v_1 = r / beta0; g = beta0 e_1
  *   for k = 1..m: w = A M^{-1} v_k; MGS against v_1..v_k -> h_{1..k,k};
  *     h_{k+1,k} = ||w||; apply the k-1 earlier rotations to column k;

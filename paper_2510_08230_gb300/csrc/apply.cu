@@ -1,5 +1,5 @@
 // apply.cu - gk_apply / gk_apply_adv: x = alpha A b + beta x on any format
-// (the LinOp apply of Section 3.4; the paper's SpMV benchmark, Section 5.1).
+// (the LinOp apply of Section 4.2; the paper's SpMV benchmark, Section 6.1).
 #include "spmv.cuh"
 
 namespace gk {

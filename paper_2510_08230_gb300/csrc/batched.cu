@@ -1,6 +1,6 @@
 // batched.cu - single-block engine: one thread block runs a whole CG or
 // BiCGSTAB solve (same algorithm, stopping rule and residual replacement
-// as the multi-kernel engine; Section 2.3 Listings 1-2 for the interface).
+// as the multi-kernel engine; Section 3.5 Listings 1-2 for the interface).
 //
 // Used for many small independent systems in one launch (gk_solve_batched)
 // and for small single systems (engine 2).  The vector that SpMV gathers

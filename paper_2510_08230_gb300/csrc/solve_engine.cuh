@@ -11,11 +11,11 @@
 // FP32 / BF16-stored inner solves.
 //
 // The solver LinOp overwrites the initial guess with the solution
-// (Section 2.3, Listing 1); stopping is an iteration cap OR
+// (Section 3.5, Listing 1); stopping is an iteration cap OR
 // ||r|| <= tol * ||b|| with the right-hand-side norm as baseline
 // (Listing 2).  GMRES keeps the whole least-squares update on the GPU, uses
 // Givens rotations and checks the residual estimate after every Hessenberg
-// column (Section 5.2.1).
+// column (Section 6.2.1).
 //
 // Multi-kernel engine: each iteration is a fixed sequence of fused kernels
 // (SpMV + dot, axpys + dots + preconditioner, ...); all scalars (alpha,

@@ -1,7 +1,7 @@
 // spmv.cuh - SpMV kernels (CSR row-tile, CSR merge-path, CSR vector, ELL,
 // SELL-P) with fused epilogues.
 //
-// A matrix LinOp's apply is an SpMV (Section 3.4); the advanced form adds
+// A matrix LinOp's apply is an SpMV (Section 4.2); the advanced form adds
 // alpha and beta.  Every kernel produces, for each row i, the sum
 // s_i = sum_j a_ij b_j and passes (i, s_i) to an epilogue, which writes the
 // output and may accumulate per-thread partial dot products; the kernel's

@@ -1,7 +1,7 @@
 /* abi_overhead.c - native driver for the binding-overhead experiment.
  *
  * The paper measures what its Python binding costs against calling the
- * library from native code (Section 5.3): P_overhead, the relative loss of
+ * library from native code (Section 6.3): P_overhead, the relative loss of
  * SpMV performance, and T_overhead, the extra time per SpMV.  This driver is
  * the native side: it loads a CSR matrix from a file, builds the handle
  * (optionally its COO form), and times `reps` calls of gk_apply on device

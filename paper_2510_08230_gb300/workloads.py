@@ -7,7 +7,7 @@ generator writes down a sparsity pattern and its values directly, in CSR
 form with int32 indices and ascending columns inside each row.
 
 The workloads stand in for the SuiteSparse matrices of the paper's
-evaluation (Section 5, "Performance Results and Analysis"), which are not
+evaluation (Section 6, "Performance Results and Analysis"), which are not
 available here.  Generators:
 
 * ``laplacian_1d/2d/3d`` - Dirichlet finite-difference Laplacians
