@@ -293,6 +293,20 @@ def diffusion_3d(N: int = 128, sigma: float = 1.0,
     return _assemble(n, n, cols, vals, valid, f"diffusion3d_{N}")
 
 
+def convection_diffusion_2d(nx: int, c: float = 1.0) -> CSR:
+    """Nonsymmetric 5-point operator on an nx-by-nx grid (x fastest):
+    diffusion (4 / -1) plus first-order upwind convection in +x of
+    strength c >= 0, i.e. diagonal 4 + c and west neighbour -1 - c.
+    Dirichlet boundary; weakly diagonally dominant."""
+    m = _stencil((nx, nx), f"convdiff2d_{nx}_c{c:g}")
+    rows = np.repeat(np.arange(m.n), m.row_lengths())
+    v = m.values.copy()
+    v[m.col_idx == rows] += c
+    v[m.col_idx == rows - 1] -= c
+    m.values = v
+    return m
+
+
 def shifted_rectangle(a: int, b: int, shift: float) -> CSR:
     """2D 5-point Laplacian on an a-by-b grid plus shift on the diagonal."""
     m = _stencil((a, b), f"rect_{a}x{b}")

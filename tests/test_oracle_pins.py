@@ -599,3 +599,160 @@ def test_block_jacobi_solvers_reach_tol(method):
     x, info = oracle.solve(m, b, method=method, precond=2, block_size=8, tol=1e-10, max_iters=5000)
     assert info["status"] == oracle.OK, info
     assert oracle.true_rel_residual(m, b, x) <= 1e-10
+
+
+# ----------------------------------------------------------------- ILU(0)
+
+def _split_lu(m, lu):
+    """Dense unit-lower L and upper U from factors stored in m's pattern."""
+    n = m.n
+    L = np.eye(n)
+    U = np.zeros((n, n))
+    rows = np.repeat(np.arange(n), m.row_lengths())
+    for r, c, v in zip(rows, m.col_idx, lu):
+        if c < r:
+            L[r, c] = v
+        else:
+            U[r, c] = v
+    return L, U
+
+
+def _pattern(m):
+    rows = np.repeat(np.arange(m.n), m.row_lengths())
+    P = np.zeros((m.n, m.ncols), dtype=bool)
+    P[rows, m.col_idx] = True
+    return P
+
+
+def test_ilu0_1d_laplacian_closed_form():
+    # tridiag(-1, 2, -1): no fill, so ILU(0) is the exact LU with
+    # u_ii = (i + 2) / (i + 1), l_i,i-1 = -i / (i + 1), u_i,i+1 = -1
+    n = 40
+    m = W.laplacian_1d(n)
+    L, U = _split_lu(m, oracle.ilu0(m))
+    i = np.arange(n)
+    assert np.allclose(np.diag(U), (i + 2) / (i + 1), rtol=1e-15, atol=0)
+    assert np.allclose(np.diag(L, -1), -i[1:] / (i[1:] + 1), rtol=1e-15, atol=0)
+    assert np.all(np.diag(U, 1) == -1.0)
+
+
+def test_ilu0_tridiagonal_nonsymmetric_is_exact_solve():
+    rng = np.random.default_rng(7)
+    n = 30
+    lo, up = rng.uniform(-1, 0, n - 1), rng.uniform(-2, 1, n - 1)
+    d = 4.0 + rng.uniform(0, 1, n)
+    D = np.diag(d) + np.diag(lo, -1) + np.diag(up, 1)
+    rp, ci, va = [0], [], []
+    for r in range(n):
+        for c in range(max(r - 1, 0), min(r + 2, n)):
+            ci.append(c)
+            va.append(D[r, c])
+        rp.append(len(ci))
+    m = _csr(n, n, rp, ci, va)
+    lu = oracle.ilu0(m)
+    L, U = _split_lu(m, lu)
+    assert np.allclose(L @ U, D, rtol=0, atol=1e-14)
+    r = rng.uniform(-1, 1, n)
+    assert np.allclose(oracle.ilu0_apply(m, lu, r), np.linalg.solve(D, r), rtol=1e-12, atol=1e-13)
+
+
+def test_ilu0_full_pattern_matches_lapack_lu():
+    # every entry stored: ILU(0) drops nothing and is Doolittle LU; columns
+    # dominated by the diagonal, so LAPACK's partial pivoting swaps no rows
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(11)
+    n = 12
+    D = rng.uniform(-1, 1, (n, n))
+    D[np.arange(n), np.arange(n)] = np.abs(D).sum(axis=0) + 1.0
+    rp = np.arange(0, n * n + 1, n)
+    ci = np.tile(np.arange(n), n)
+    m = _csr(n, n, rp, ci, D.reshape(-1))
+    L, U = _split_lu(m, oracle.ilu0(m))
+    P, Ls, Us = scipy_linalg.lu(D)
+    assert np.array_equal(P, np.eye(n))
+    assert np.allclose(L, Ls, rtol=0, atol=1e-14)
+    assert np.allclose(U, Us, rtol=1e-14, atol=1e-13)
+
+
+@pytest.mark.parametrize("dims", [(7, 6), (5, 4, 3)])
+def test_ilu0_stencil_recurrence(dims):
+    # 5-/7-point Laplacian, natural order, every side >= 3: no two lower
+    # neighbours of a row share a stored entry, so ILU(0) reduces to
+    # l_ik = -1 / u_kk, u_ij = -1 above the diagonal and
+    # u_ii = a_ii - sum over lower neighbours k of 1 / u_kk
+    m = W.laplacian_2d(*dims) if len(dims) == 2 else W.laplacian_3d(*dims)
+    lu = oracle.ilu0(m)
+    u = np.zeros(m.n)
+    for i in range(m.n):
+        row = slice(m.row_ptr[i], m.row_ptr[i + 1])
+        cols, f = m.col_idx[row], lu[row]
+        lower = cols < i
+        assert np.allclose(f[lower], -1.0 / u[cols[lower]], rtol=1e-15, atol=0)
+        assert np.all(f[cols > i] == -1.0)
+        expect = 2.0 * len(dims) - np.sum(1.0 / u[cols[lower]])
+        u[i] = f[cols == i][0]
+        assert u[i] == pytest.approx(expect, rel=1e-15)
+
+
+@pytest.mark.parametrize("make", [lambda: W.laplacian_2d(8, 7),
+                                  lambda: W.convection_diffusion_2d(9, 2.0),
+                                  lambda: W.diffusion_3d(5)])
+def test_ilu0_reproduces_a_on_its_pattern(make):
+    # the defining property: (L U)_ij = a_ij for every stored (i, j); fill
+    # outside the pattern is dropped, so L U differs from A somewhere else
+    m = make()
+    L, U = _split_lu(m, oracle.ilu0(m))
+    A = m.to_dense()
+    P = _pattern(m)
+    LU = L @ U
+    assert np.allclose(LU[P], A[P], rtol=0, atol=1e-13 * np.abs(A).max())
+    assert np.abs(LU[~P]).max() > 1e-3
+
+
+def test_ilu0_apply_is_the_two_triangular_solves():
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    m = W.convection_diffusion_2d(11, 1.5)
+    lu = oracle.ilu0(m)
+    L, U = _split_lu(m, lu)
+    r = W.uniform_vector(m.n, 5)
+    y = scipy_linalg.solve_triangular(L, r, lower=True, unit_diagonal=True)
+    z = scipy_linalg.solve_triangular(U, y, lower=False)
+    got = oracle.ilu0_apply(m, lu, r)
+    assert np.allclose(got, z, rtol=1e-13, atol=1e-14)
+    assert np.allclose(L @ (U @ got), r, rtol=0, atol=1e-12)
+
+
+def test_ilu0_errors():
+    # missing diagonal
+    with pytest.raises(ZeroDivisionError):
+        oracle.ilu0(_csr(2, 2, [0, 1, 2], [1, 0], [1.0, 1.0]))
+    # the elimination creates a zero pivot: [[1, 1], [1, 1]]
+    with pytest.raises(ZeroDivisionError):
+        oracle.ilu0(_csr(2, 2, [0, 2, 4], [0, 1, 0, 1], [1.0, 1.0, 1.0, 1.0]))
+    # columns not ascending within a row
+    with pytest.raises(ValueError):
+        oracle.ilu0(_csr(2, 2, [0, 2, 3], [1, 0, 1], [1.0, 2.0, 3.0]))
+    # duplicates are rejected too
+    with pytest.raises(ValueError):
+        oracle.ilu0(_csr(1, 1, [0, 2], [0, 0], [1.0, 2.0]))
+
+
+def test_ilu_cg_beats_jacobi_cg_on_laplacian():
+    m = W.laplacian_2d(32)
+    b = W.uniform_vector(m.n, 2)
+    x1, i1 = oracle.solve(m, b, method=oracle.CG, precond=1, tol=1e-10)
+    x3, i3 = oracle.solve(m, b, method=oracle.CG, precond=3, tol=1e-10)
+    assert i1["status"] == oracle.OK and i3["status"] == oracle.OK
+    assert oracle.true_rel_residual(m, b, x3) <= 1e-10
+    assert i3["iters"] < 0.7 * i1["iters"], (i1["iters"], i3["iters"])
+
+
+@pytest.mark.parametrize("method", [oracle.BICGSTAB, oracle.CGS, oracle.GMRES])
+def test_ilu_solvers_on_convection_diffusion(method):
+    m = W.convection_diffusion_2d(24, 3.0)
+    b = W.uniform_vector(m.n, 4)
+    x0, i0 = oracle.solve(m, b, method=method, precond=1, tol=1e-10, max_iters=4000)
+    x, info = oracle.solve(m, b, method=method, precond=3, tol=1e-10, max_iters=4000)
+    assert info["status"] == oracle.OK, info
+    assert oracle.true_rel_residual(m, b, x) <= 1e-10
+    assert info["iters"] < i0["iters"], (i0["iters"], info["iters"])
