@@ -472,9 +472,11 @@ int or_ilu0(int32_t n, const int32_t* rp, const int32_t* ci, const double* va, d
 /* z = U^{-1} L^{-1} r with the factors of or_ilu0.  Forward substitution
  * in ascending row order, y_i = r_i - sum_{j<i} l_ij y_j with the terms
  * subtracted in ascending column order; back substitution in descending
- * row order, z_i = (y_i - sum_{j>i} u_ij z_j) / u_ii with the terms
+ * row order, z_i = (y_i - sum_{j>i} u_ij z_j) * (1 / u_ii) with the terms
  * subtracted in descending column order (each unknown is used in the order
- * the substitution produced it). */
+ * the substitution produced it).  The paper does not fix the arithmetic of
+ * the substitution; this reading scales by the pivot's reciprocal, rounded
+ * once, as a preconditioner that stores inverted pivots does. */
 void or_ilu0_apply(int32_t n, const int32_t* rp, const int32_t* ci, const double* lu,
                    const double* r, double* z)
 {
@@ -488,7 +490,8 @@ void or_ilu0_apply(int32_t n, const int32_t* rp, const int32_t* ci, const double
         const int32_t d = diag_pos(rp, ci, i);
         double s = y[i];
         for (int32_t p = rp[i + 1] - 1; p > d; --p) s = s - lu[p] * z[ci[p]];
-        z[i] = s / lu[d];
+        const double rd = 1.0 / lu[d];
+        z[i] = s * rd;
     }
     free(y);
 }
