@@ -70,11 +70,25 @@ typedef enum { GK_CSR = 0, GK_ELL = 1, GK_SELLP = 2, GK_COO = 3 } gk_format;
  * and CGS (Sonneveld's conjugate gradient squared, the solver the paper
  * benchmarks beside CG and GMRES in Section 6.2.1). */
 typedef enum { GK_CG = 0, GK_BICGSTAB = 1, GK_GMRES = 2, GK_CGS = 3 } gk_method;
-/* Preconditioners (the config solver's Jacobi, Listing 2): point Jacobi
+/* Preconditioners: the config solver's Jacobi (Listing 2) as point Jacobi
  * (max_block_size 1) and block-Jacobi over diagonal blocks of block_size
  * consecutive rows (max_block_size > 1; each block inverted by Gauss-Jordan
- * with partial pivoting, a singular block is GK_ERR_ZERO_DIAG). */
-typedef enum { GK_PRECOND_NONE = 0, GK_PRECOND_JACOBI = 1, GK_PRECOND_BLOCK_JACOBI = 2 } gk_precond;
+ * with partial pivoting, a singular block is GK_ERR_ZERO_DIAG), and
+ * ILU(0), the Ilu preconditioner of Listing 1: incomplete LU without
+ * fill-in (A's pattern; the IKJ form, products and differences rounded
+ * separately) applied as z = U^-1 (L^-1 r) by exact forward and backward
+ * substitution.  ILU(0) needs every row's columns strictly ascending (what
+ * gk_matrix_create_coo and the conversions produce; otherwise
+ * GK_ERR_INVALID) and a stored diagonal with nonzero pivots (otherwise
+ * GK_ERR_ZERO_DIAG).  For a symmetric matrix its U equals D L^T in exact
+ * arithmetic, so it is also the IC(0) preconditioner L D L^T and suits CG.
+ * The factors are built on first use and kept with the handle. */
+typedef enum {
+    GK_PRECOND_NONE = 0,
+    GK_PRECOND_JACOBI = 1,
+    GK_PRECOND_BLOCK_JACOBI = 2,
+    GK_PRECOND_ILU = 3
+} gk_precond;
 typedef enum { GK_MEM_HOST = 0, GK_MEM_DEVICE = 1 } gk_memory;
 
 typedef enum {
@@ -196,7 +210,7 @@ gk_status gk_apply_adv(gk_matrix A, double alpha, const void* b, double beta,
 
 typedef struct {
     gk_method method;
-    gk_precond precond;   /* none, Jacobi, or block-Jacobi (block_size below) */
+    gk_precond precond;   /* none, Jacobi, block-Jacobi (block_size below) or ILU(0) */
     double tol;           /* stop when ||b - A x||_2 <= tol * ||b||_2 */
     int32_t max_iters;    /* CG/BiCGSTAB iterations; GMRES Arnoldi steps (all cycles) */
     int32_t krylov_dim;   /* GMRES restart length m (0 = 30, the paper's value); <= 64 */
@@ -213,8 +227,8 @@ typedef struct {
                              2 single-block (CSR, CG/BiCGSTAB, n <= 16384);
                              3 cluster of up to 16 blocks (CSR, CG, n <= 16384).
                              Automatic picks 3 for CSR CG with n <= 16384 when a
-                             cluster can be scheduled, else 1.  Block-Jacobi and
-                             CGS run on engine 1 only. */
+                             cluster can be scheduled, else 1.  Block-Jacobi,
+                             ILU(0) and CGS run on engine 1 only. */
     int32_t block_size;   /* block-Jacobi rows per diagonal block, 1..32 */
 } gk_solve_opts;
 
@@ -267,6 +281,31 @@ gk_status gk_solve_batched(int32_t count, const gk_matrix* As,
                            const void* const* bs, void* const* xs,
                            const gk_solve_opts* opts, gk_solve_info* infos,
                            void* stream);
+
+/* ---------------------------------------------------------------------
+ * Preconditioner as an operator
+ * ------------------------------------------------------------------- */
+
+/* z = M^-1 r for the preconditioner `kind` of the square matrix A (a
+ * preconditioner is a LinOp whose apply transforms a vector, Section 4.2):
+ * GK_PRECOND_NONE copies, JACOBI scales by 1 / a_ii, BLOCK_JACOBI applies
+ * the inverted diagonal blocks of block_size (1..32) rows, ILU solves
+ * L y = r then U z = y.  r and z: distinct device vectors of n entries in
+ * the vector type (double for GK_F64, float otherwise).  The
+ * preconditioner is built on first use and cached with A (errors as for
+ * gk_solve).  Stream-ordered on `stream`; kinds NONE to BLOCK_JACOBI
+ * return without waiting, ILU waits for the result and returns
+ * GK_ERR_TIMEOUT if a substitution's bounded wait ran out (z is then
+ * wrong).  The substitutions run sync-free: each warp solves 32
+ * consecutive rows and waits, bounded, for the chunks its rows depend on. */
+gk_status gk_precond_apply(gk_matrix A, gk_precond kind, int32_t block_size,
+                           const void* r, void* z, void* stream);
+
+/* The ILU(0) factors of A, built on first use, copied to the host array
+ * lu (nnz entries in the vector type) in A's CSR order (for a padded
+ * format, the order of its CSR conversion): entries left of the diagonal
+ * hold L (unit diagonal implied), the rest U.  Blocking. */
+gk_status gk_ilu_factors(gk_matrix A, void* lu, void* stream);
 
 /* ---------------------------------------------------------------------
  * SpMV without device allocation

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libgk.so")
 GK_F64, GK_F32, GK_BF16, GK_F16 = 0, 1, 2, 3
 GK_CSR, GK_ELL, GK_SELLP, GK_COO = 0, 1, 2, 3
 GK_CG, GK_BICGSTAB, GK_GMRES, GK_CGS = 0, 1, 2, 3
-GK_PRECOND_NONE, GK_PRECOND_JACOBI, GK_PRECOND_BLOCK_JACOBI = 0, 1, 2
+GK_PRECOND_NONE, GK_PRECOND_JACOBI, GK_PRECOND_BLOCK_JACOBI, GK_PRECOND_ILU = 0, 1, 2, 3
 GK_MEM_HOST, GK_MEM_DEVICE = 0, 1
 GK_OK, GK_NOT_CONVERGED, GK_BREAKDOWN = 0, 1, 2
 GK_ERR_INVALID, GK_ERR_OOM, GK_ERR_CUDA, GK_ERR_TIMEOUT = -1, -2, -3, -4
@@ -39,8 +39,10 @@ EXPORTED = [
     "gk_matrix_create_csr", "gk_matrix_create_coo", "gk_matrix_convert",
     "gk_matrix_describe", "gk_matrix_export", "gk_matrix_destroy", "gk_apply",
     "gk_apply_adv", "gk_solve", "gk_solve_batched", "gk_status_string", "gk_version",
-    "gk_spmv_csr_f64_noalloc",
+    "gk_spmv_csr_f64_noalloc", "gk_precond_apply", "gk_ilu_factors",
 ]
+PRECONDS = {"none": GK_PRECOND_NONE, "jacobi": GK_PRECOND_JACOBI,
+            "block_jacobi": GK_PRECOND_BLOCK_JACOBI, "ilu": GK_PRECOND_ILU}
 
 
 class GkError(RuntimeError):
@@ -106,6 +108,8 @@ def lib():
         L.gk_solve_batched.argtypes = [i32, pm, pm, pm, ctypes.POINTER(gk_solve_opts),
                                        ctypes.POINTER(gk_solve_info), vp]
         L.gk_spmv_csr_f64_noalloc.argtypes = [i32, i32, i64, vp, vp, vp, f64, vp, f64, vp, vp]
+        L.gk_precond_apply.argtypes = [vp, ctypes.c_int, i32, vp, vp, vp]
+        L.gk_ilu_factors.argtypes = [vp, vp, vp]
         L.gk_status_string.argtypes = [ctypes.c_int]
         L.gk_status_string.restype = ctypes.c_char_p
         L.gk_version.argtypes = []
@@ -223,17 +227,27 @@ def gk_apply_adv(A, alpha, b, beta, x, stream=None):
 
 def make_opts(method="cg", precond=None, tol=1e-10, max_iters=1000, krylov_dim=30, mixed=0,
               inner_tol=0.0, max_outer=0, engine=0, block_size=0):
-    """precond: None / "none" / 0, "jacobi" / 1 / True, or "block_jacobi" / 2
-    (with block_size rows per diagonal block)."""
+    """precond: None / "none" / 0, "jacobi" / 1 / True, "block_jacobi" / 2
+    (with block_size rows per diagonal block) or "ilu" / 3 (ILU(0))."""
     m = METHODS[method] if isinstance(method, str) else int(method)
-    if precond in (None, "none", 0, False):
-        p = GK_PRECOND_NONE
-    elif precond in ("block_jacobi", 2):
-        p = GK_PRECOND_BLOCK_JACOBI
-    else:
-        p = GK_PRECOND_JACOBI
+    p = _precond(precond)
     return gk_solve_opts(m, p, tol, max_iters, krylov_dim, mixed, inner_tol, max_outer, None,
                          engine, block_size)
+
+
+def _precond(precond):
+    if precond in (None, "none", 0, False):
+        return GK_PRECOND_NONE
+    if isinstance(precond, str):
+        return PRECONDS[precond]
+    if precond is True:
+        return GK_PRECOND_JACOBI
+    return int(precond)
+
+
+def gk_precond_apply(A, kind, block_size, r, z, stream=None):
+    return lib().gk_precond_apply(A, _precond(kind), int(block_size), _ptr(r), _ptr(z),
+                                  _stream(stream))
 
 
 def gk_solve(A, b, x, opts, stream=None):
@@ -369,6 +383,21 @@ class Matrix:
 
     def apply_adv(self, alpha, b, beta, x, stream=None):
         _check(gk_apply_adv(self.handle, alpha, b, beta, x, stream), "gk_apply_adv")
+
+    def precond_apply(self, r, z, kind="ilu", block_size=0, stream=None):
+        """z = M^-1 r for the preconditioner `kind` (device vectors)."""
+        _check(gk_precond_apply(self.handle, kind, block_size, r, z, stream), "gk_precond_apply")
+
+    def ilu_factors(self):
+        """ILU(0) factors in the CSR order of the matrix (host array of the
+        vector type): L left of the diagonal (unit diagonal implied), U on
+        and right of it."""
+        d = self.desc
+        vdt = np.float64 if d["dtype"] == GK_F64 else np.float32
+        out = np.zeros(max(d["nnz"], 1), vdt)
+        _check(lib().gk_ilu_factors(self.handle, out.ctypes.data_as(ctypes.c_void_p), None),
+               "gk_ilu_factors")
+        return out[:d["nnz"]]
 
     def describe(self):
         """Fresh gk_matrix_describe (solve_format is set by the first solve)."""

@@ -587,7 +587,7 @@ static gk_status run_batch(int32_t count, const gk_matrix* As, const void* const
 gk_status solve_small(gk_matrix A, const void* b, void* x, const gk_solve_opts* o, cudaStream_t s,
                       SolveOut* out) {
     if (A->fmt != GK_CSR || o->method == GK_GMRES || o->method == GK_CGS || A->dtype == GK_F16 ||
-        o->precond == GK_PRECOND_BLOCK_JACOBI)
+        o->precond >= GK_PRECOND_BLOCK_JACOBI)
         return GK_ERR_UNSUPPORTED;
     gk_solve_info info;
     std::memset(&info, 0, sizeof(info));
@@ -670,7 +670,7 @@ extern "C" gk_status gk_solve_batched(int32_t count, const gk_matrix* As, const 
                                       gk_solve_info* infos, void* stream) {
     if (count < 0 || !o || (count > 0 && (!As || !bs || !xs))) return GK_ERR_INVALID;
     if (count == 0) return GK_OK;
-    if (o->method == GK_GMRES || o->method == GK_CGS || o->precond == GK_PRECOND_BLOCK_JACOBI)
+    if (o->method == GK_GMRES || o->method == GK_CGS || o->precond >= GK_PRECOND_BLOCK_JACOBI)
         return GK_ERR_UNSUPPORTED;
     if ((o->method != GK_CG && o->method != GK_BICGSTAB) || o->mixed ||
         (o->precond != GK_PRECOND_NONE && o->precond != GK_PRECOND_JACOBI) || !(o->tol >= 0.0) ||

@@ -276,7 +276,7 @@ int32_t cluster_max_n() { return CL_MAX_BLOCKS * CL_RMAX * CL_THREADS; }
 gk_status solve_cluster(gk_matrix A, const void* b, void* x, const gk_solve_opts* o,
                         cudaStream_t s, SolveOut* out) {
     if (A->fmt != GK_CSR || o->method != GK_CG || A->n > cluster_max_n() || A->dtype == GK_F16 ||
-        o->precond == GK_PRECOND_BLOCK_JACOBI)
+        o->precond >= GK_PRECOND_BLOCK_JACOBI)
         return GK_ERR_UNSUPPORTED;
     int C = 16;
     if (const char* e = getenv("GK_CLUSTER_BLOCKS")) C = atoi(e);

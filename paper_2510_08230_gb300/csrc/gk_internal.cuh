@@ -213,6 +213,17 @@ struct gk_matrix_s {
     int dinv_state = 0;           // 0 not built, 1 ok, -1 zero diagonal
     void* binv = nullptr;         // block-Jacobi inverses (vector type, column-major blocks)
     int32_t binv_bs = 0;          // their block size (0 none, -bs singular)
+    // ILU(0) factors in the vector type, built on first use
+    int ilu_state = 0;            // 0 not built, 1 built, < 0 the gk_status of a failed build
+    int32_t* ilu_rp = nullptr;    // CSR pattern of the factors (row_ptr, col)
+    int32_t* ilu_ci = nullptr;
+    int32_t* ilu_dpos = nullptr;  // position of each row's diagonal
+    void* ilu_lu = nullptr;       // factor values in CSR order
+    void* ilu_rdiag = nullptr;    // 1 / u_ii in the vector type
+    int32_t* ilu_ord = nullptr;   // chunks of 32 rows in claim (level) order: L, then U
+    int32_t ilu_warps[2] = {0, 0};  // warps per substitution launch (L, U)
+    void* ilu_sync = nullptr;     // substitution claim counters, epochs and chunk flags
+    gk::DevBuf ilu_w;             // scratch of gk_precond_apply
     gk_matrix_s* lowp[3] = {nullptr, nullptr, nullptr};  // same layout, other dtype
     gk_matrix_s* solve_fmt = nullptr;  // SpMV layout picked for solves (null: not tuned)
     int solve_fmt_tuned = 0;

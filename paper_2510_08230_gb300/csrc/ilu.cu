@@ -1,0 +1,488 @@
+// ilu.cu - ILU(0) factorisation on the device and the preconditioner
+// entry points (gk_precond_apply, gk_ilu_factors).
+//
+// Setup, once per matrix:
+//  1. k_ilu_prep: strictly ascending columns, diagonal positions.
+//  2. k_chunk_levels (L and U): the level of every 32-row chunk in the
+//     dependency graph of each substitution; a counting sort by level
+//     (k_level_hist, k_level_scan, k_level_scatter) gives the claim order
+//     of the substitution kernels and the widest level (their grid cap).
+//  3. k_ilu_factor: the factorisation (the IKJ form of ILU(0): for every
+//     row i, for every stored k < i in ascending order, l_ik = a_ik / u_kk,
+//     then a_ij -= l_ik u_kj for every stored j > k of row k that row i
+//     also stores) runs sync-free: one warp per row, rows claimed chunk by
+//     chunk in the L claim order and in ascending order inside a chunk (a
+//     topological order), so a row only waits (bounded) on rows claimed
+//     before it.  Row i waits for row
+// k to be final before it reads u_kk and row k's upper part; the lanes then
+// update row i's entries for row k's columns in parallel (each entry is hit
+// at most once per k, and the k steps run in ascending order), so every
+// entry sees exactly the oracle's sequence of roundings.  Products and
+// differences are rounded separately, no fused multiply-add.
+//
+// The factors are computed in double from the stored values and rounded
+// once to the vector type (double for GK_F64, float otherwise).
+#include "ilu.cuh"
+#include "solve_engine.cuh"
+
+namespace gk {
+
+// strictly ascending columns, diagonal position, values widened to double
+template <typename V>
+__global__ void k_ilu_prep(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                           const V* __restrict__ va, double* __restrict__ fac,
+                           int32_t* __restrict__ dpos, unsigned* bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t d = -1;
+        const int32_t b = rp[i], e = rp[i + 1];
+        for (int32_t k = b; k < e; ++k) {
+            const int32_t c = ci[k];
+            if (k > b && c <= ci[k - 1]) atomicOr(bad, 1u);
+            if (c == (int32_t)i) d = k;
+            fac[k] = cvt<double>(va[k]);
+        }
+        if (d < 0) atomicOr(bad, 2u);
+        dpos[i] = d;
+    }
+}
+
+// Spin until *p != 0 (bounded as wait_flag); returns the value, 0 after a
+// time-out.
+__device__ __forceinline__ unsigned wait_nonzero(const unsigned* p, unsigned* err) {
+    unsigned v = ld_acquire_u32(p);
+    if (v) return v;
+    const long long t0 = clock64();
+    unsigned ns = 32;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+        v = ld_relaxed_u32(p);
+        if (v) return ld_acquire_u32(p);
+        if (ld_relaxed_u32(err) != 0u) return 0u;
+        if (clock64() - t0 > ILU_WAIT_CYCLES) {
+            atomicExch(err, 1u);
+            return 0u;
+        }
+    }
+}
+
+// lev[c] = 1 + the highest level among the chunks chunk c depends on (L:
+// columns left of the chunk; U: right of it); chunks claimed in solve order.
+// misc[0] claim counter, misc[1] wait ran out.
+template <bool UP>
+__global__ void __launch_bounds__(256)
+k_chunk_levels(int32_t n, int32_t nch, const int32_t* __restrict__ rp,
+               const int32_t* __restrict__ ci, const int32_t* __restrict__ dpos, unsigned* lev,
+               unsigned* misc) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int c = 0;
+        if (lane == 0) c = (int)atomicAdd(&misc[0], 1u);
+        c = __shfl_sync(FULL, c, 0);
+        if (c >= nch) break;
+        const int32_t cc = UP ? nch - 1 - c : c;
+        const int32_t c0 = cc * TRSV_CHUNK, c1 = min(c0 + TRSV_CHUNK, n);
+        const int32_t i = c0 + lane;
+        unsigned mx = 0;
+        if (i < n) {
+            const int32_t d = dpos[i];
+            int32_t last = -1;
+            if (!UP) {
+                for (int32_t k = rp[i]; k < d; ++k) {
+                    const int32_t j = ci[k];
+                    if (j >= c0) break;
+                    const int32_t cj = j / TRSV_CHUNK;
+                    if (cj != last) {
+                        mx = max(mx, wait_nonzero(lev + cj, &misc[1]));
+                        last = cj;
+                    }
+                }
+            } else {
+                for (int32_t k = rp[i + 1] - 1; k > d; --k) {
+                    const int32_t j = ci[k];
+                    if (j < c1) break;
+                    const int32_t cj = j / TRSV_CHUNK;
+                    if (cj != last) {
+                        mx = max(mx, wait_nonzero(lev + cj, &misc[1]));
+                        last = cj;
+                    }
+                }
+            }
+        }
+        mx = __reduce_max_sync(FULL, mx);
+        if (lane == 0) st_release_u32(lev + cc, mx + 1);
+    }
+}
+
+// cnt[l] = chunks on level l (levels 1..nch)
+__global__ void k_level_hist(int32_t nch, const unsigned* __restrict__ lev, unsigned* cnt) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nch;
+         c += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[lev[c]], 1u);
+}
+
+// In place exclusive scan of cnt[0, len) by one block of 1024 threads;
+// *maxw = the largest count.
+__global__ void __launch_bounds__(1024) k_level_scan(int32_t len, unsigned* cnt, unsigned* maxw) {
+    __shared__ unsigned wsum[32];
+    __shared__ unsigned carry;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) carry = 0;
+    unsigned mx = 0;
+    __syncthreads();
+    for (int32_t base = 0; base < len; base += 1024) {
+        const int32_t k = base + tid;
+        const unsigned v = k < len ? cnt[k] : 0u;
+        mx = max(mx, v);
+        unsigned incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned w = wsum[lane], wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += t;
+            }
+            wsum[lane] = wi - w;  // exclusive warp offsets
+        }
+        __syncthreads();
+        const unsigned excl = carry + wsum[wid] + incl - v;
+        if (k < len) cnt[k] = excl;
+        __syncthreads();
+        if (tid == 1023) carry = excl + v;
+        __syncthreads();
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if (lane == 0) atomicMax(maxw, mx);
+}
+
+// ord[start[lev[c]]++] = c (order inside a level is immaterial: no chunk
+// depends on another of its level)
+__global__ void k_level_scatter(int32_t nch, const unsigned* __restrict__ lev, unsigned* cursor,
+                                int32_t* __restrict__ ord) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nch;
+         c += (int64_t)gridDim.x * blockDim.x)
+        ord[atomicAdd(&cursor[lev[c]], 1u)] = (int32_t)c;
+}
+
+// misc[0] claim counter, misc[1] wait ran out, misc[2] zero pivot
+__global__ void __launch_bounds__(256)
+k_ilu_factor(int32_t n, int32_t nch, const int32_t* __restrict__ rp,
+             const int32_t* __restrict__ ci, const int32_t* __restrict__ dpos,
+             const int32_t* __restrict__ ord, double* fac, unsigned* done, unsigned* misc) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t nclaim = (int64_t)nch * TRSV_CHUNK;
+    for (;;) {
+        int64_t c = 0;
+        if (lane == 0) c = (int64_t)atomicAdd(&misc[0], 1u);
+        c = __shfl_sync(FULL, c, 0);
+        if (c >= nclaim) break;
+        const int32_t i = ord[c / TRSV_CHUNK] * TRSV_CHUNK + (int32_t)(c % TRSV_CHUNK);
+        if (i >= n) continue;  // past the last row of the last chunk
+        const int32_t p1 = rp[i + 1], d = dpos[i];
+        int ok = 1;
+        for (int32_t pk = rp[i]; pk < d; ++pk) {
+            const int32_t k = ci[pk];
+            if (lane == 0 && ok) ok = wait_flag(done + k, 1u, &misc[1]) ? 1 : 0;
+            ok = __shfl_sync(FULL, ok, 0);
+            __syncwarp();  // row k's values, released by its warp, are read after the acquire
+            const int32_t dk = dpos[k], ek = rp[k + 1];
+            const double l = __ddiv_rn(__ldcg(fac + pk), __ldcg(fac + dk));
+            for (int32_t q = dk + 1 + lane; q < ek; q += 32) {
+                const int32_t j = ci[q];
+                int32_t lo = pk + 1, hi = p1;  // j in row i's columns after k
+                while (lo < hi) {
+                    const int32_t mid = (lo + hi) >> 1;
+                    if (ci[mid] < j) lo = mid + 1;
+                    else hi = mid;
+                }
+                if (lo < p1 && ci[lo] == j)
+                    fac[lo] = __dsub_rn(__ldcg(fac + lo), __dmul_rn(l, __ldcg(fac + q)));
+            }
+            if (lane == 0) fac[pk] = l;
+            __threadfence_block();
+            __syncwarp();
+        }
+        if (lane == 0 && __ldcg(fac + d) == 0.0) atomicOr(&misc[2], 1u);
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_u32(done + i, 1u);
+    }
+}
+
+// factors rounded to the vector type; the pivots' reciprocals 1 / u_ii
+// computed in double and rounded once
+template <typename T>
+__global__ void k_ilu_store(int32_t n, int64_t nnz, const double* __restrict__ fac,
+                            const int32_t* __restrict__ dpos, T* __restrict__ lu,
+                            T* __restrict__ rdiag) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x)
+        lu[k] = cvt<T>(fac[k]);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        rdiag[i] = cvt<T>(__ddiv_rn(1.0, fac[dpos[i]]));
+}
+
+static size_t ilu_sync_bytes(int32_t nch) {
+    return 2 * sizeof(TrsvSync) + 2 * (size_t)std::max(nch, 1) * sizeof(unsigned);
+}
+
+static void ilu_release(gk_matrix A) {
+    dfree(A->ilu_rp);
+    dfree(A->ilu_ci);
+    dfree(A->ilu_dpos);
+    dfree(A->ilu_lu);
+    dfree(A->ilu_sync);
+    dfree(A->ilu_ord);
+    dfree(A->ilu_rdiag);
+    A->ilu_rp = A->ilu_ci = A->ilu_dpos = A->ilu_ord = nullptr;
+    A->ilu_lu = A->ilu_sync = A->ilu_rdiag = nullptr;
+}
+
+// Grid of `kernel` (256 threads) when each of `items` needs one warp, at
+// most the resident blocks.
+template <typename K>
+static unsigned resident_grid(K kernel, int64_t items) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 256, 0) != cudaSuccess || b < 1)
+        b = 1;
+    const int64_t need = (items + 7) / 8;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * b));
+}
+
+// Levels of the L (up = false) or U chunk graph, the claim order sorted by
+// level into ord[0, nch), and the widest level in *maxw (host).
+static gk_status chunk_order(gk_matrix A, int32_t n, int32_t nch, bool up, int32_t* ord,
+                             unsigned* maxw, cudaStream_t s) {
+    DevBuf lev, cnt, misc;
+    GK_TRY(lev.ensure(sizeof(unsigned) * (size_t)nch));
+    GK_TRY(cnt.ensure(sizeof(unsigned) * ((size_t)nch + 2)));
+    GK_TRY(misc.ensure(64));
+    GK_CUDA(cudaMemsetAsync(lev.ptr, 0, sizeof(unsigned) * (size_t)nch, s));
+    GK_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(unsigned) * ((size_t)nch + 2), s));
+    GK_CUDA(cudaMemsetAsync(misc.ptr, 0, 64, s));
+    unsigned* mp = (unsigned*)misc.ptr;
+    if (up)
+        k_chunk_levels<true><<<resident_grid(k_chunk_levels<true>, nch), 256, 0, s>>>(
+            n, nch, A->ilu_rp, A->ilu_ci, A->ilu_dpos, (unsigned*)lev.ptr, mp);
+    else
+        k_chunk_levels<false><<<resident_grid(k_chunk_levels<false>, nch), 256, 0, s>>>(
+            n, nch, A->ilu_rp, A->ilu_ci, A->ilu_dpos, (unsigned*)lev.ptr, mp);
+    const unsigned g = ew_grid(nch);
+    k_level_hist<<<g, 256, 0, s>>>(nch, (const unsigned*)lev.ptr, (unsigned*)cnt.ptr);
+    k_level_scan<<<1, 1024, 0, s>>>(nch + 2, (unsigned*)cnt.ptr, mp + 2);
+    k_level_scatter<<<g, 256, 0, s>>>(nch, (const unsigned*)lev.ptr, (unsigned*)cnt.ptr, ord);
+    GK_CUDA(cudaGetLastError());
+    unsigned h[4] = {0, 0, 0, 0};
+    GK_CUDA(cudaMemcpyAsync(h, mp, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    if (h[1]) return GK_ERR_TIMEOUT;
+    *maxw = h[2];
+    return GK_OK;
+}
+
+static gk_status ilu_build(gk_matrix A, gk_matrix C, cudaStream_t s) {
+    const int32_t n = C->n;
+    const int64_t nnz = C->nnz;
+    const int32_t nch = (n + TRSV_CHUNK - 1) / TRSV_CHUNK;
+    const size_t vb = vector_bytes(A->dtype);
+    GK_CUDA(dmalloc_t(&A->ilu_rp, (size_t)n + 1));
+    GK_CUDA(dmalloc_t(&A->ilu_ci, (size_t)std::max<int64_t>(nnz, 1)));
+    GK_CUDA(dmalloc_t(&A->ilu_dpos, (size_t)std::max(n, 1)));
+    GK_CUDA(dmalloc(&A->ilu_lu, vb * (size_t)std::max<int64_t>(nnz, 1)));
+    GK_CUDA(dmalloc(&A->ilu_rdiag, vb * (size_t)std::max(n, 1)));
+    GK_CUDA(dmalloc(&A->ilu_sync, ilu_sync_bytes(nch)));
+    GK_CUDA(dmalloc_t(&A->ilu_ord, 2 * (size_t)std::max(nch, 1)));
+    GK_CUDA(cudaMemcpyAsync(A->ilu_rp, C->row_ptr, sizeof(int32_t) * ((size_t)n + 1),
+                            cudaMemcpyDeviceToDevice, s));
+    if (nnz > 0)
+        GK_CUDA(cudaMemcpyAsync(A->ilu_ci, C->col, sizeof(int32_t) * (size_t)nnz,
+                                cudaMemcpyDeviceToDevice, s));
+    // claim counters 0, epochs 1, chunk flags 0
+    GK_CUDA(cudaMemsetAsync(A->ilu_sync, 0, ilu_sync_bytes(nch), s));
+    static const TrsvSync init[2] = {{0u, 0u, 1u, 0u}, {0u, 0u, 1u, 0u}};
+    GK_CUDA(cudaMemcpyAsync(A->ilu_sync, init, sizeof(init), cudaMemcpyHostToDevice, s));
+
+    DevBuf fac, done, misc;
+    GK_TRY(fac.ensure(sizeof(double) * (size_t)std::max<int64_t>(nnz, 1)));
+    GK_TRY(done.ensure(sizeof(unsigned) * (size_t)std::max(n, 1)));
+    GK_TRY(misc.ensure(64));
+    GK_CUDA(cudaMemsetAsync(done.ptr, 0, sizeof(unsigned) * (size_t)std::max(n, 1), s));
+    GK_CUDA(cudaMemsetAsync(misc.ptr, 0, 64, s));
+    unsigned* mp = (unsigned*)misc.ptr;
+    unsigned h[4] = {0, 0, 0, 0};
+    if (n > 0) {
+        const unsigned g = ew_grid(n);
+        auto prep = [&](auto vt) {
+            using V = decltype(vt);
+            k_ilu_prep<V><<<g, 256, 0, s>>>(n, A->ilu_rp, A->ilu_ci, (const V*)C->val,
+                                           (double*)fac.ptr, A->ilu_dpos, mp + 3);
+        };
+        if (C->dtype == GK_F64) prep(double());
+        else if (C->dtype == GK_F32) prep(float());
+        else if (C->dtype == GK_F16) prep(__half());
+        else prep(__nv_bfloat16());
+        GK_CUDA(cudaGetLastError());
+        GK_CUDA(cudaMemcpyAsync(h, mp, sizeof(h), cudaMemcpyDeviceToHost, s));
+        GK_CUDA(cudaStreamSynchronize(s));
+        if (h[3] & 1u) return GK_ERR_INVALID;
+        if (h[3] & 2u) return GK_ERR_ZERO_DIAG;
+        // claim orders and grid caps of the two substitutions (a few
+        // times the widest level of chunks, at least 64 warps)
+        unsigned wl = 0, wu = 0;
+        GK_TRY(chunk_order(A, n, nch, false, A->ilu_ord, &wl, s));
+        GK_TRY(chunk_order(A, n, nch, true, A->ilu_ord + nch, &wu, s));
+        A->ilu_warps[0] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, 2 * (int64_t)wl), nch);
+        A->ilu_warps[1] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, 2 * (int64_t)wu), nch);
+        k_ilu_factor<<<resident_grid(k_ilu_factor, std::min<int64_t>(n, 64 * (int64_t)wl + 256)),
+                       256, 0, s>>>(n, nch, A->ilu_rp, A->ilu_ci, A->ilu_dpos, A->ilu_ord,
+                                    (double*)fac.ptr, (unsigned*)done.ptr, mp);
+        GK_CUDA(cudaGetLastError());
+        GK_CUDA(cudaMemcpyAsync(h, mp, sizeof(h), cudaMemcpyDeviceToHost, s));
+        GK_CUDA(cudaStreamSynchronize(s));
+        if (h[1]) return GK_ERR_TIMEOUT;
+        if (h[2]) return GK_ERR_ZERO_DIAG;
+        if (A->dtype == GK_F64)
+            k_ilu_store<double><<<ew_grid(nnz), 256, 0, s>>>(n, nnz, (const double*)fac.ptr,
+                                                             A->ilu_dpos, (double*)A->ilu_lu,
+                                                             (double*)A->ilu_rdiag);
+        else
+            k_ilu_store<float><<<ew_grid(nnz), 256, 0, s>>>(n, nnz, (const double*)fac.ptr,
+                                                            A->ilu_dpos, (float*)A->ilu_lu,
+                                                            (float*)A->ilu_rdiag);
+        GK_CUDA(cudaGetLastError());
+    }
+    GK_CUDA(cudaStreamSynchronize(s));
+    return GK_OK;
+}
+
+gk_status ensure_ilu(gk_matrix A, cudaStream_t s) {
+    if (A->ilu_state == 1) return GK_OK;
+    if (A->ilu_state < 0) return (gk_status)A->ilu_state;
+    if (A->n != A->ncols) return GK_ERR_INVALID;
+    gk_matrix C = A, tmp = nullptr;
+    if (A->fmt != GK_CSR) {
+        GK_TRY(gk_matrix_convert(A, GK_CSR, A->dtype, 0, 0, s, &tmp));
+        C = tmp;
+    }
+    const gk_status st = ilu_build(A, C, s);
+    if (tmp) gk_matrix_destroy(tmp);
+    if (st != GK_OK) {
+        cudaStreamSynchronize(s);
+        ilu_release(A);
+        // a malformed or singular pattern stays so; other failures may be retried
+        if (st == GK_ERR_INVALID || st == GK_ERR_ZERO_DIAG) A->ilu_state = (int)st;
+        return st;
+    }
+    A->ilu_state = 1;
+    return GK_OK;
+}
+
+template <typename T>
+IluDev<T> ilu_view(gk_matrix A) {
+    IluDev<T> f;
+    f.n = A->n;
+    f.nch = (A->n + TRSV_CHUNK - 1) / TRSV_CHUNK;
+    f.rp = A->ilu_rp;
+    f.ci = A->ilu_ci;
+    f.dpos = A->ilu_dpos;
+    f.lu = (const T*)A->ilu_lu;
+    f.rdiag = (const T*)A->ilu_rdiag;
+    f.ord = A->ilu_ord;
+    f.warps[0] = A->ilu_warps[0];
+    f.warps[1] = A->ilu_warps[1];
+    f.sy = (TrsvSync*)A->ilu_sync;
+    f.flags = (unsigned*)((char*)A->ilu_sync + 2 * sizeof(TrsvSync));
+    return f;
+}
+template IluDev<double> ilu_view<double>(gk_matrix);
+template IluDev<float> ilu_view<float>(gk_matrix);
+
+template <typename T>
+__global__ void EW_BOUNDS k_scale_by(int32_t n, const T* __restrict__ d, const T* __restrict__ r,
+                                     T* __restrict__ z) {
+    GRID_LOOP(i, n) z[i] = d[i] * r[i];
+}
+
+template <typename T>
+static gk_status precond_apply_t(gk_matrix A, int kind, int32_t bs, const T* r, T* z,
+                                 cudaStream_t s) {
+    const int32_t n = A->n;
+    if (kind == GK_PRECOND_NONE) {
+        if (n > 0 && z != r)
+            GK_CUDA(cudaMemcpyAsync(z, r, sizeof(T) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        return GK_OK;
+    }
+    if (kind == GK_PRECOND_JACOBI) {
+        GK_TRY(ensure_jacobi(A, s));
+        if (n > 0) k_scale_by<T><<<ewg(k_scale_by<T>, n), 256, 0, s>>>(n, (const T*)A->dinv, r, z);
+        GK_CUDA(cudaGetLastError());
+        return GK_OK;
+    }
+    if (kind == GK_PRECOND_BLOCK_JACOBI) {
+        GK_TRY(ensure_block_jacobi(A, bs, s));
+        if (n > 0)
+            k_bj_apply<T, EpiStoreHalt<T>><<<ewg(k_bj_apply<T, EpiStoreHalt<T>>, n), 256, 0, s>>>(
+                n, bs, (const T*)A->binv, r, EpiStoreHalt<T>{z, nullptr});
+        GK_CUDA(cudaGetLastError());
+        return GK_OK;
+    }
+    GK_TRY(ensure_ilu(A, s));
+    if (n == 0) return GK_OK;
+    GK_TRY(A->ilu_w.ensure(sizeof(T) * (size_t)n));
+    const IluDev<T> f = ilu_view<T>(A);
+    GK_TRY(ilu_clear_err(f, s));
+    GK_TRY(ilu_apply<T>(f, IluSrc<T>{r}, (T*)A->ilu_w.ptr, IluOutStore<T>{z}, IluSkipNever{},
+                        IluNoErr{}, s));
+    TrsvSync h[2];
+    GK_CUDA(cudaMemcpyAsync(h, f.sy, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    if (h[0].err | h[1].err) return GK_ERR_TIMEOUT;
+    return GK_OK;
+}
+
+}  // namespace gk
+
+using namespace gk;
+
+extern "C" gk_status gk_precond_apply(gk_matrix A, gk_precond kind, int32_t block_size,
+                                      const void* r, void* z, void* stream) {
+    if (!A || (!r && A->n > 0) || (!z && A->n > 0)) return GK_ERR_INVALID;
+    if (A->n != A->ncols) return GK_ERR_INVALID;
+    if (kind < GK_PRECOND_NONE || kind > GK_PRECOND_ILU) return GK_ERR_INVALID;
+    if (kind == GK_PRECOND_BLOCK_JACOBI && (block_size < 1 || block_size > BJ_MAX))
+        return GK_ERR_INVALID;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != A->device) return GK_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(A->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (A->dtype == GK_F64)
+        return precond_apply_t<double>(A, (int)kind, block_size, (const double*)r, (double*)z, s);
+    return precond_apply_t<float>(A, (int)kind, block_size, (const float*)r, (float*)z, s);
+}
+
+extern "C" gk_status gk_ilu_factors(gk_matrix A, void* lu, void* stream) {
+    if (!A || (!lu && A->nnz > 0)) return GK_ERR_INVALID;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != A->device) return GK_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(A->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    GK_TRY(ensure_ilu(A, s));
+    if (A->nnz > 0)
+        GK_CUDA(cudaMemcpyAsync(lu, A->ilu_lu, vector_bytes(A->dtype) * (size_t)A->nnz,
+                                cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    return GK_OK;
+}

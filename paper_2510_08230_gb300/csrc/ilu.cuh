@@ -1,0 +1,312 @@
+// ilu.cuh - ILU(0) preconditioner: device factors and the two triangular
+// substitutions z = U^-1 (L^-1 r) that apply it.
+//
+// ILU(0) keeps A's sparsity pattern (the paper's first usage example pairs
+// GMRES(30) with an Ilu preconditioner, Listing 1; Section 5 lists ILU and
+// IC among the bound preconditioners).  The factors live in one value
+// array lu[] in the CSR order of A (unit-lower L strictly below the
+// diagonal, U on and above it), beside private copies of row_ptr / col and
+// the position of every row's diagonal.
+//
+// Substitution is a dependency problem: row i of L^-1 r needs every y_j
+// with l_ij != 0.  The kernel is sync-free (no level sets, one launch per
+// triangle):
+//  - Rows are cut into chunks of 32 consecutive rows; one warp solves one
+//    chunk, one lane per row.  Warps claim chunks from an atomic counter in
+//    a topological order of the chunk dependency graph (by level: a
+//    chunk's level is one more than the highest level it depends on,
+//    computed once per matrix), so a chunk only ever waits on chunks
+//    claimed before it by running warps: no deadlock.  Claiming by level
+//    also keeps warps from spinning on chunks far ahead of the wavefront,
+//    and the grid is capped at a few times the widest level.
+//  - A lane first subtracts its row's terms outside the chunk, in the
+//    order the substitution produced them (L: ascending columns; U:
+//    descending), waiting per source chunk on that chunk's "done" flag.
+//  - The terms inside the chunk are resolved by a 32-step warp loop: at step
+//    t lane t's value is final and is broadcast with a shuffle; lanes whose
+//    row uses column c0 + t subtract it.  Together with the first phase this
+//    subtracts every term in exactly the sequential order, so the result
+//    is bit-identical to plain forward / backward substitution.
+//  - A finished chunk stores its values, fences, and publishes its flag
+//    with a release store of the launch's epoch number.  Flags are never
+//    cleared: a launch waits for "flag == its epoch", and the last warp to
+//    leave the kernel advances the epoch and resets the claim counter for
+//    the next launch.  Values written by other warps are read through L2.
+//  - Every wait is bounded (about two seconds of SM clock); a wait that
+//    runs out records an error flag and the kernel finishes with wrong
+//    values instead of hanging.  The solver engine turns the flag into
+//    GK_ERR_TIMEOUT.
+// Products and differences are rounded separately (no fused multiply-add)
+// and U's pivots are applied as stored reciprocals (1 / u_ii rounded once,
+// a multiplication instead of a division on the in-chunk chain), so that
+// FP64 results equal the plain substitution with those reciprocals bit
+// for bit.
+#pragma once
+
+#include "gk_internal.cuh"
+
+namespace gk {
+
+constexpr int TRSV_CHUNK = 32;                      // rows per warp
+constexpr long long ILU_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+
+// Per-direction synchronisation words (index 0: L, 1: U).
+struct TrsvSync {
+    unsigned ctr;     // next chunk to claim in solve order
+    unsigned exited;  // warps that left the current launch
+    unsigned epoch;   // number of the current launch (starts at 1)
+    unsigned err;     // a bounded wait ran out (sticky)
+};
+
+// Device view of one ILU(0) factorisation with values of type T.
+template <typename T>
+struct IluDev {
+    int32_t n = 0, nch = 0;
+    const int32_t* rp = nullptr;    // row_ptr[n + 1]
+    const int32_t* ci = nullptr;    // col[nnz], strictly ascending per row
+    const int32_t* dpos = nullptr;  // position of a_ii in row i
+    const T* lu = nullptr;          // factors in CSR order
+    const T* rdiag = nullptr;       // 1 / u_ii, rounded once
+    const int32_t* ord = nullptr;   // [2 * nch]: chunks in claim order, L then U
+    TrsvSync* sy = nullptr;         // [2]
+    unsigned* flags = nullptr;      // [2 * nch]
+    int32_t warps[2] = {0, 0};      // host: warps per substitution launch
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Spin until *flag == want (acquire), at most ILU_WAIT_CYCLES; on time-out
+// set *err and return false.  Once any wait of the launch has run out
+// (*err set), later waits give up at once, so a failed launch ends within
+// about one time-out.
+// Polls are acquire loads with a growing pause (32 to 256 ns).
+__device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned want, unsigned* err) {
+    if (ld_acquire_u32(flag) == want) return true;
+    const long long t0 = clock64();
+    unsigned ns = 32;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+        if (ld_acquire_u32(flag) == want) return true;
+        if (ld_relaxed_u32(err) != 0u) return false;
+        if (clock64() - t0 > ILU_WAIT_CYCLES) {
+            atomicExch(err, 1u);
+            return false;
+        }
+    }
+}
+
+// a - l * y with the product rounded before the subtraction
+__device__ __forceinline__ double sub_mul(double a, double l, double y) {
+    return __dsub_rn(a, __dmul_rn(l, y));
+}
+__device__ __forceinline__ float sub_mul(float a, float l, float y) {
+    return __fsub_rn(a, __fmul_rn(l, y));
+}
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+// ---------------------------------------------------------- sources
+
+template <typename T>
+struct IluSrc {  // a plain vector
+    const T* p;
+    __device__ __forceinline__ const T* ptr() const { return p; }
+};
+
+// ---------------------------------------------------------- skips
+
+struct IluSkipNever {
+    __device__ __forceinline__ bool skip() const { return false; }
+};
+
+// ---------------------------------------------------------- outputs
+// dst(): where the unknowns of this substitution are stored (and read back
+// by later chunks); extra(i, v): what else row i does with its value.
+
+template <typename T>
+struct IluOutStore {
+    T* y;
+    __device__ __forceinline__ T* dst() const { return y; }
+    __device__ __forceinline__ void extra(int64_t, T) const {}
+};
+
+// One substitution (UP = false: unit-lower L, ascending; UP = true: U with
+// its diagonal, descending).  The last warp of the U launch hands the
+// error flags of both directions to on_err (the engine turns a wait that
+// ran out into GK_ERR_TIMEOUT and a halt).
+template <typename T, bool UP, class Src, class Out, class Skip, class Err>
+__global__ void __launch_bounds__(256)
+k_ilu_trsv(IluDev<T> f, Src src, Out out, Skip sk, Err on_err) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    TrsvSync* sy = f.sy + (UP ? 1 : 0);
+    unsigned* flags = f.flags + (UP ? f.nch : 0);
+    const unsigned total = gridDim.x * (blockDim.x >> 5);
+    unsigned epoch = 0;
+    if (lane == 0) epoch = ld_acquire_u32(&sy->epoch);
+    epoch = __shfl_sync(FULL, epoch, 0);
+    if (!sk.skip()) {
+        const T* in = src.ptr();
+        T* dst = out.dst();
+        for (;;) {
+            int c = 0;
+            if (lane == 0) c = (int)atomicAdd(&sy->ctr, 1u);
+            c = __shfl_sync(FULL, c, 0);
+            if (c >= f.nch) break;
+            const int cc = f.ord[(UP ? f.nch : 0) + c];
+            const int32_t c0 = cc * TRSV_CHUNK;
+            const int32_t c1 = min(c0 + TRSV_CHUNK, f.n);
+            const int32_t i = c0 + lane;
+            const bool has = i < f.n;
+            T acc = T(0);
+            int32_t pin = 0, pend = 0;  // in-chunk entries [pin, pend)
+            if (has) {
+                acc = in[i];
+                const int32_t d = f.dpos[i];
+                int32_t waited = -1;
+                bool ok = true;
+                if (!UP) {
+                    int32_t k = f.rp[i];
+                    for (; k < d; ++k) {
+                        const int32_t j = f.ci[k];
+                        if (j >= c0) break;
+                        const int32_t cj = j / TRSV_CHUNK;
+                        if (cj != waited && ok) {
+                            ok = wait_flag(flags + cj, epoch, &sy->err);
+                            waited = cj;
+                        }
+                        acc = sub_mul(acc, f.lu[k], __ldcg(dst + j));
+                    }
+                    pin = k;
+                    pend = d;
+                } else {
+                    int32_t k = f.rp[i + 1] - 1;
+                    for (; k > d; --k) {
+                        const int32_t j = f.ci[k];
+                        if (j < c1) break;
+                        const int32_t cj = j / TRSV_CHUNK;
+                        if (cj != waited && ok) {
+                            ok = wait_flag(flags + cj, epoch, &sy->err);
+                            waited = cj;
+                        }
+                        acc = sub_mul(acc, f.lu[k], __ldcg(dst + j));
+                    }
+                    pin = d + 1;
+                    pend = k + 1;
+                }
+            }
+            const int m = c1 - c0;
+            T mine = T(0);
+            if (!UP) {
+                // lane t's value is final at step t; later lanes subtract it
+                int32_t col = pin < pend ? f.ci[pin] : INT32_MAX;
+                T lv = pin < pend ? f.lu[pin] : T(0);
+                for (int t = 0; t < m; ++t) {
+                    const T yt = __shfl_sync(FULL, acc, t);
+                    if (lane == t) mine = yt;
+                    if (col == c0 + t) {  // only lanes > t hold column c0 + t
+                        acc = sub_mul(acc, lv, yt);
+                        ++pin;
+                        col = pin < pend ? f.ci[pin] : INT32_MAX;
+                        lv = pin < pend ? f.lu[pin] : T(0);
+                    }
+                }
+            } else {
+                const T rd = has ? f.rdiag[i] : T(1);
+                int32_t col = pend > pin ? f.ci[pend - 1] : -1;
+                T uv = pend > pin ? f.lu[pend - 1] : T(0);
+                for (int t = m - 1; t >= 0; --t) {
+                    T v = T(0);
+                    if (lane == t) v = mul_rn(acc, rd);
+                    const T zt = __shfl_sync(FULL, v, t);
+                    if (lane == t) mine = zt;
+                    if (col == c0 + t) {  // only lanes < t hold column c0 + t
+                        acc = sub_mul(acc, uv, zt);
+                        --pend;
+                        col = pend > pin ? f.ci[pend - 1] : -1;
+                        uv = pend > pin ? f.lu[pend - 1] : T(0);
+                    }
+                }
+            }
+            if (has) {
+                dst[i] = mine;
+                out.extra(i, mine);
+            }
+            __syncwarp();  // the lanes' stores are ordered before lane 0's release
+            if (lane == 0) st_release_u32(flags + cc, epoch);
+        }
+    }
+    // every warp leaves exactly once; the last one prepares the next launch
+    __syncwarp();
+    if (lane == 0) {
+        const unsigned e = atomicAdd(&sy->exited, 1u);
+        if (e == total - 1) {
+            if (UP) on_err(ld_acquire_u32(&f.sy[0].err) | ld_acquire_u32(&f.sy[1].err));
+            sy->ctr = 0;
+            sy->exited = 0;
+            __threadfence();
+            st_release_u32(&sy->epoch, epoch + 1);
+        }
+    }
+}
+
+struct IluNoErr {
+    __device__ __forceinline__ void operator()(unsigned) const {}
+};
+
+// Blocks of 256 threads for a substitution: `warps` warps (a few times the
+// widest level), at most the resident ones.
+template <typename K>
+static unsigned ilu_grid(K kernel, int32_t warps) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 256, 0) != cudaSuccess || b < 1)
+        b = 1;
+    const int64_t need = ((int64_t)warps + 7) / 8;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * b));
+}
+
+// z = U^-1 L^-1 src: L into w, then U from w with the caller's output.
+template <typename T, class Src, class Out, class Skip, class Err>
+static gk_status ilu_apply(const IluDev<T>& f, Src src, T* w, Out out, Skip sk, Err on_err,
+                           cudaStream_t s) {
+    if (f.n == 0) return GK_OK;
+    auto kl = k_ilu_trsv<T, false, Src, IluOutStore<T>, Skip, IluNoErr>;
+    auto ku = k_ilu_trsv<T, true, IluSrc<T>, Out, Skip, Err>;
+    kl<<<ilu_grid(kl, f.warps[0]), 256, 0, s>>>(f, src, IluOutStore<T>{w}, sk, IluNoErr{});
+    ku<<<ilu_grid(ku, f.warps[1]), 256, 0, s>>>(f, IluSrc<T>{w}, out, sk, on_err);
+    GK_CUDA(cudaGetLastError());
+    return GK_OK;
+}
+
+// Clears the sticky wait-ran-out flags of both directions (before a solve
+// or an apply, so that only this run's waits are reported).
+template <typename T>
+static gk_status ilu_clear_err(const IluDev<T>& f, cudaStream_t s) {
+    GK_CUDA(cudaMemsetAsync(&f.sy[0].err, 0, sizeof(unsigned), s));
+    GK_CUDA(cudaMemsetAsync(&f.sy[1].err, 0, sizeof(unsigned), s));
+    return GK_OK;
+}
+
+// host side (ilu.cu): build the factors of A in the vector type on first
+// use (GK_ERR_INVALID: columns not strictly ascending; GK_ERR_ZERO_DIAG:
+// missing diagonal or zero pivot), and the device view of them.
+gk_status ensure_ilu(gk_matrix A, cudaStream_t s);
+template <typename T>
+IluDev<T> ilu_view(gk_matrix A);
+
+}  // namespace gk

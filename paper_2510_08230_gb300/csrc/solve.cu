@@ -233,7 +233,7 @@ static gk_status check_opts(gk_matrix A, const gk_solve_opts* o) {
         o->method != GK_CGS)
         return GK_ERR_INVALID;
     if (o->precond != GK_PRECOND_NONE && o->precond != GK_PRECOND_JACOBI &&
-        o->precond != GK_PRECOND_BLOCK_JACOBI)
+        o->precond != GK_PRECOND_BLOCK_JACOBI && o->precond != GK_PRECOND_ILU)
         return GK_ERR_INVALID;
     if (o->precond == GK_PRECOND_BLOCK_JACOBI && (o->block_size < 1 || o->block_size > BJ_MAX))
         return GK_ERR_INVALID;

@@ -31,6 +31,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "ilu.cuh"
 #include "spmv.cuh"
 
 namespace gk {
@@ -375,14 +376,14 @@ struct CgUpdFin {
             st->halt = 2;
             return;
         }
-        if (prec == 2) return;  // block-Jacobi: k_bj_apply's fin takes <r, z>
+        if (prec >= 2) return;  // block-Jacobi / ILU: the fin after z = M^-1 r takes <r, z>
         const double rz = prec ? t[0] : t[1];
         st->beta = rz / st->rho;
         st->rho = rz;
     }
 };
 
-// block-Jacobi CG: beta from <r, z> with z = B r (k_bj_apply)
+// block-Jacobi / ILU CG: beta from <r, z> with z = M^-1 r (k_bj_apply, k_dot_fin)
 struct CgBetaFin {
     KState* st;
     __device__ void operator()(double* t) const {
@@ -1628,6 +1629,87 @@ __global__ void EW_BOUNDS k_bj_gm(int32_t n, int32_t bs, const T* __restrict__ b
     }
 }
 
+// ---------------------------------------------------------------- ILU(0)
+// The engine applies ILU(0) where it applies block-Jacobi (the substitution
+// kernels of ilu.cuh), with these sources, skips and outputs.
+
+// GMRES after k_gm_next: V y (ubuf) at a cycle end, else the new v_k
+template <typename T>
+struct IluSrcGm {
+    const T* V;
+    int64_t ldv;
+    const T* ubuf;
+    const KState* st;
+    __device__ __forceinline__ const T* ptr() const {
+        return st->cycle_end ? ubuf : V + (int64_t)st->k * ldv;
+    }
+};
+
+struct IluSkipHalt {
+    const KState* st;
+    __device__ __forceinline__ bool skip() const { return halted(st); }
+};
+
+// GMRES v_0 step: only when a restart decided to continue
+struct IluSkipV0 {
+    const KState* st;
+    __device__ __forceinline__ bool skip() const { return halted(st) || !st->v0_pending; }
+};
+
+// y = s ; x += alpha s  (CGS: uh = M^-1 (u + q), x += alpha uh)
+template <typename T>
+struct IluOutX {
+    T* y;
+    T* x;
+    const KState* st;
+    __device__ __forceinline__ T* dst() const { return y; }
+    __device__ __forceinline__ void extra(int64_t i, T v) const {
+        x[i] = fmadd((T)st->alpha, v, x[i]);
+    }
+};
+
+// GMRES: inside a cycle z = M^-1 v_k; at a cycle end x += M^-1 (V y), the
+// substitution's unknowns kept in a scratch vector
+template <typename T>
+struct IluOutGm {
+    T* z;
+    T* scratch;
+    T* x;
+    const KState* st;
+    __device__ __forceinline__ T* dst() const { return st->cycle_end ? scratch : z; }
+    __device__ __forceinline__ void extra(int64_t i, T v) const {
+        if (st->cycle_end) x[i] += v;
+    }
+};
+
+// a substitution wait that ran out stops the solve with GK_ERR_TIMEOUT
+struct IluErrSt {
+    KState* st;
+    __device__ __forceinline__ void operator()(unsigned e) const {
+        if (e) {
+            st->status = GK_ERR_TIMEOUT;
+            st->halt = 2;
+        }
+    }
+};
+
+// <a, b> handed to a fin (CG with ILU: rho = <r, z> after z = M^-1 r)
+template <typename T, class Fin>
+__global__ void EW_BOUNDS k_dot_fin(int32_t n, const T* __restrict__ a, const T* __restrict__ b,
+                                    const int32_t* halt, double* partials, unsigned* ticket,
+                                    Fin fin) {
+    if (halt && *reinterpret_cast<const volatile int32_t*>(halt) != 0) return;
+    constexpr int N = Pack<T>::N;
+    const bool vec = al16(a) && al16(b);
+    T acc[1] = {T(0)};
+    PACK_LOOP(j, n, T) {
+        const Pack<T> A_ = pld(a, j, n, vec), B_ = pld(b, j, n, vec);
+#pragma unroll
+        for (int c = 0; c < N; ++c) acc[0] = fmadd(A_.v[c], B_.v[c], acc[0]);
+    }
+    finish_ew<1>(acc, partials, ticket, fin);
+}
+
 // ------------------------------------------------------------ host side
 
 constexpr size_t HDR = offsetof(KState, H);
@@ -1717,20 +1799,32 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
     // preconditioner: pkind 0 none, 1 Jacobi (fused into the update kernels
     // as dinv), 2 block-Jacobi of bs rows (separate k_bj_* kernels; the
     // update kernels then run unpreconditioned into the vectors B is
-    // applied to)
+    // applied to), 3 ILU(0) (the two substitution kernels where
+    // block-Jacobi runs k_bj_*)
     const bool prec = pkind != 0;
     const bool block = pkind == 2;
+    const bool ilu = pkind == 3;
+    const bool sep = block || ilu;  // preconditioner applied by its own kernels
     const T* dinv = nullptr;
     const T* binv = nullptr;
+    IluDev<T> ild;
     if (pkind == 1) {
         GK_TRY(ensure_jacobi(A, s));
         dinv = (const T*)A->dinv;
     } else if (block) {
         GK_TRY(ensure_block_jacobi(A, bs, s));
         binv = (const T*)A->binv;
+    } else if (ilu) {
+        GK_TRY(ensure_ilu(A, s));
+        ild = ilu_view<T>(A);
+        GK_TRY(ilu_clear_err(ild, s));
     }
-    const int nvec = method == GK_CG ? 5 : (method == GK_BICGSTAB || method == GK_CGS) ? 10 : m + 5;
+    const int nvec0 = method == GK_CG ? 5 : (method == GK_BICGSTAB || method == GK_CGS) ? 10 : m + 5;
+    // ILU: two more vectors, the L substitution's output and GMRES's scratch
+    const int nvec = nvec0 + (ilu ? 2 : 0);
     GK_TRY(ensure_vecs<T>(C, n, nvec));
+    T* ilu_w = ilu ? vec_at<T>(C, n, nvec0) : nullptr;
+    T* ilu_s = ilu ? vec_at<T>(C, n, nvec0 + 1) : nullptr;
     // multi-dot kernels: one wave of resident blocks sharing the rows equally
     const int64_t md_need = std::max<int64_t>(1, ((int64_t)n + MD_ROWS - 1) / MD_ROWS);
     auto md_grid_of = [&](auto kern) {
@@ -1766,11 +1860,14 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
         // cycle start: r = b - A x, restart fin sets g, k; v0 = r / beta0
         EpiResid<T, GmRestartFin> e0{r, b, halt, part, tk, GmRestartFin{st}};
         GK_TRY((launch_spmv_rows<V, T>(A, x, e0, s)));
-        T* ubuf = vec_at<T>(C, n, m + 4);  // V y at a cycle end (block-Jacobi only)
+        T* ubuf = vec_at<T>(C, n, m + 4);  // V y at a cycle end (block-Jacobi / ILU only)
         k_gm_v0<T><<<ewg(k_gm_v0<T>, n), 256, 0, s>>>(n, Vm, r, z, dinv, st);
         if (block)
             k_bj_apply<T, EpiBjV0<T>><<<ewg(k_bj_apply<T, EpiBjV0<T>>, n), 256, 0, s>>>(
                 n, bs, binv, Vm, EpiBjV0<T>{z, st});
+        if (ilu)
+            GK_TRY(ilu_apply<T>(ild, IluSrc<T>{Vm}, ilu_w, IluOutStore<T>{z}, IluSkipV0{st},
+                                IluErrSt{st}, s));
         GK_CUDA(cudaGetLastError());
         const int chunk = chunk_for(n);
         const int pkey = pkind * 64 + (block ? bs : 0);
@@ -1786,16 +1883,23 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
                 k_gm_orth<T><<<md_grid_of(k_gm_orth<T>), MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st,
                                                                                part, tk);
                 k_gm_next<T><<<ewg(k_gm_next<T>, n), 256, 0, cs>>>(n, ldv, Vm, w, z, x, dinv, st,
-                                                                   block ? ubuf : nullptr);
+                                                                   sep ? ubuf : nullptr);
                 if (block)
                     k_bj_gm<T><<<ewg(k_bj_gm<T>, n), 256, 0, cs>>>(n, bs, binv, Vm, ldv, ubuf, z,
                                                                    x, st);
+                if (ilu)
+                    GK_TRY(ilu_apply<T>(ild, IluSrcGm<T>{Vm, ldv, ubuf, st}, ilu_w,
+                                        IluOutGm<T>{z, ilu_s, x, st}, IluSkipHalt{st},
+                                        IluErrSt{st}, cs));
                 EpiGmResid<T> e2{r, b, st, part, tk, GmRestartFin{st}};
                 GK_TRY((launch_spmv_rows<V, T>(A, x, e2, cs)));
                 k_gm_v0<T><<<ewg(k_gm_v0<T>, n), 256, 0, cs>>>(n, Vm, r, z, dinv, st);
                 if (block)
                     k_bj_apply<T, EpiBjV0<T>><<<ewg(k_bj_apply<T, EpiBjV0<T>>, n), 256, 0, cs>>>(
                         n, bs, binv, Vm, EpiBjV0<T>{z, st});
+                if (ilu)
+                    GK_TRY(ilu_apply<T>(ild, IluSrc<T>{Vm}, ilu_w, IluOutStore<T>{z},
+                                        IluSkipV0{st}, IluErrSt{st}, cs));
                 GK_CUDA(cudaGetLastError());
                 return GK_OK;
             }));
@@ -1820,6 +1924,13 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
                 using E0 = EpiDot<T, CgInitFin>;
                 k_bj_apply<T, E0><<<ewg(k_bj_apply<T, E0>, n), 256, 0, s>>>(
                     n, bs, binv, r, E0{zb, r, nullptr, part, tk, CgInitFin{st}});
+                k_copy<T><<<ewg(k_copy<T>, n), 256, 0, s>>>(n, zb, pb);
+            } else if (method == GK_CG && ilu) {  // z = M^-1 r, rho = <r, z> ; p = z
+                T *zb = vec_at<T>(C, n, 4), *pb = vec_at<T>(C, n, 3);
+                GK_TRY(ilu_apply<T>(ild, IluSrc<T>{r}, ilu_w, IluOutStore<T>{zb}, IluSkipNever{},
+                                    IluErrSt{st}, s));
+                k_dot_fin<T, CgInitFin><<<ewg(k_dot_fin<T, CgInitFin>, n), 256, 0, s>>>(
+                    n, r, zb, nullptr, part, tk, CgInitFin{st});
                 k_copy<T><<<ewg(k_copy<T>, n), 256, 0, s>>>(n, zb, pb);
             } else if (method == GK_CG)  // slots: 0 r, 1 tmp, 2 q, 3 p, 4 z
                 k_cg_init<T><<<ewg(k_cg_init<T>, n), 256, 0, s>>>(n, r, vec_at<T>(C, n, 4), vec_at<T>(C, n, 3), dinv,
@@ -1852,6 +1963,12 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
                         k_bj_apply<T, E1><<<ewg(k_bj_apply<T, E1>, n), 256, 0, cs>>>(
                             n, bs, binv, r, E1{z, r, halt, part, tk, CgBetaFin{st}});
                     }
+                    if (ilu) {  // z = M^-1 r ; beta = <r, z> / rho
+                        GK_TRY(ilu_apply<T>(ild, IluSrc<T>{r}, ilu_w, IluOutStore<T>{z},
+                                            IluSkipHalt{st}, IluErrSt{st}, cs));
+                        k_dot_fin<T, CgBetaFin><<<ewg(k_dot_fin<T, CgBetaFin>, n), 256, 0, cs>>>(
+                            n, r, z, halt, part, tk, CgBetaFin{st});
+                    }
                     k_cg_p<T><<<ewg(k_cg_p<T>, n), 256, 0, cs>>>(n, p, z, st);
                 } else if (method == GK_CGS) {
                     T *rt = vec_at<T>(C, n, 2), *u = vec_at<T>(C, n, 3), *p = vec_at<T>(C, n, 4);
@@ -1862,13 +1979,19 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
                     if (block)
                         k_bj_apply<T, EpiStoreHalt<T>><<<ewg(k_bj_apply<T, EpiStoreHalt<T>>, n), 256, 0, cs>>>(
                             n, bs, binv, p, EpiStoreHalt<T>{ph, halt});
+                    if (ilu)
+                        GK_TRY(ilu_apply<T>(ild, IluSrc<T>{p}, ilu_w, IluOutStore<T>{ph},
+                                            IluSkipHalt{st}, IluErrSt{st}, cs));
                     EpiDot<T, CgsAlphaFin> e1{vh, rt, halt, part, tk, CgsAlphaFin{st}};
                     GK_TRY((launch_spmv_rows<V, T>(A, phs, e1, cs)));
                     k_cgs_q<T><<<ewg(k_cgs_q<T>, n), 256, 0, cs>>>(n, q, uh, x, u, vh, dinv, st,
-                                                                   block ? tb : nullptr);
+                                                                   sep ? tb : nullptr);
                     if (block)
                         k_bj_apply<T, EpiBjX<T>><<<ewg(k_bj_apply<T, EpiBjX<T>>, n), 256, 0, cs>>>(
                             n, bs, binv, tb, EpiBjX<T>{uh, x, st});
+                    if (ilu)
+                        GK_TRY(ilu_apply<T>(ild, IluSrc<T>{tb}, ilu_w, IluOutX<T>{uh, x, st},
+                                            IluSkipHalt{st}, IluErrSt{st}, cs));
                     EpiCgsR<T> e2{r, rt, st, part, tk};
                     GK_TRY((launch_spmv_rows<V, T>(A, uh, e2, cs)));
                 } else {
@@ -1881,12 +2004,18 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
                     if (block)
                         k_bj_apply<T, EpiStoreHalt<T>><<<ewg(k_bj_apply<T, EpiStoreHalt<T>>, n), 256, 0, cs>>>(
                             n, bs, binv, p, EpiStoreHalt<T>{ph, halt});
+                    if (ilu)
+                        GK_TRY(ilu_apply<T>(ild, IluSrc<T>{p}, ilu_w, IluOutStore<T>{ph},
+                                            IluSkipHalt{st}, IluErrSt{st}, cs));
                     EpiDot<T, BiAlphaFin> e1{v, rh, halt, part, tk, BiAlphaFin{st}};
                     GK_TRY((launch_spmv_rows<V, T>(A, phs, e1, cs)));
                     k_bi_s<T><<<ewg(k_bi_s<T>, n), 256, 0, cs>>>(n, sv, sh, r, v, dinv, st, part, tk);
                     if (block)
                         k_bj_apply<T, EpiStoreHalt<T>><<<ewg(k_bj_apply<T, EpiStoreHalt<T>>, n), 256, 0, cs>>>(
                             n, bs, binv, sv, EpiStoreHalt<T>{sh, halt});
+                    if (ilu)
+                        GK_TRY(ilu_apply<T>(ild, IluSrc<T>{sv}, ilu_w, IluOutStore<T>{sh},
+                                            IluSkipHalt{st}, IluErrSt{st}, cs));
                     EpiBiT<T> e2{t, sv, st, part, tk, BiOmegaFin{st}};
                     GK_TRY((launch_spmv_rows<V, T>(A, shs, e2, cs)));
                     k_bi_update<T><<<ewg(k_bi_update<T>, n), 256, 0, cs>>>(n, x, r, phs, shs, sv, t, rh, st, part, tk);
