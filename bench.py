@@ -284,9 +284,11 @@ def per_iteration_protocol(gk, W, torch, dev, iters=1000):
 
 def precond_compare(gk, W, torch, dev):
     """CG and GMRES(30) to a true 1e-10 on the 128^3 diffusion matrix (FP64)
-    without a preconditioner, with Jacobi, and with block-Jacobi of 4, 8 and
-    16 rows: iterations and wall time (host clock around the solve).  GMRES
-    is capped at 5000 steps (status 1 if it had not converged)."""
+    without a preconditioner, with Jacobi, with block-Jacobi of 4, 8 and 16
+    rows, and with ILU(0): iterations and wall time (host clock around the
+    solve; the preconditioner is built by a warm-up solve first).  GMRES is
+    capped at 5000 steps (status 1 if it had not converged).  Also the time
+    of one ILU(0) application (both substitutions) in FP64 and FP32."""
     m = W.diffusion_3d(128)
     b = torch.from_numpy(W.uniform_vector(m.n, W.SEED_BASE + 3)).to(dev)
     A = gk.Matrix.from_csr(m)
@@ -296,7 +298,8 @@ def precond_compare(gk, W, torch, dev):
         for label, kw in (("none", dict(precond=None)), ("jacobi", dict(precond="jacobi")),
                           ("block4", dict(precond="block_jacobi", block_size=4)),
                           ("block8", dict(precond="block_jacobi", block_size=8)),
-                          ("block16", dict(precond="block_jacobi", block_size=16))):
+                          ("block16", dict(precond="block_jacobi", block_size=16)),
+                          ("ilu0", dict(precond="ilu"))):
             x = torch.zeros_like(b)
             A.solve(b, x, method=method, tol=1e-10, max_iters=20, **kw)  # warm-up (setup)
             x.zero_()
@@ -310,6 +313,21 @@ def precond_compare(gk, W, torch, dev):
                           "rel_res_true": info["rel_res_true"]}
         out[method] = res
     A.close()
+    apply_us = {}
+    for dt in ("f64", "f32"):
+        vt = torch.float64 if dt == "f64" else torch.float32
+        B = gk.Matrix.from_csr(m, dt)
+        r = b.to(vt)
+        z = torch.empty_like(r)
+        B.precond_apply(r, z, "ilu")  # builds the factors
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(10):
+            B.precond_apply(r, z, "ilu")
+        torch.cuda.synchronize()
+        apply_us[dt] = round((time.perf_counter() - t0) / 10 * 1e6, 1)
+        B.close()
+    out["ilu0_apply_us"] = apply_us
     return out
 
 
@@ -492,7 +510,9 @@ def profile_case(name, dtype):
       cg, bicgstab, gmres
                24 Jacobi-preconditioned iterations (GMRES(30): Arnoldi
                steps) on the 128^3 diffusion problem (solver kernels: SpMV
-               epilogues, fused updates, multi-dots)"""
+               epilogues, fused updates, multi-dots)
+      ilu      ILU(0) of the 2D 5-point Laplacian 512^2 and three
+               applications (the substitution kernels k_ilu_trsv)"""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -500,6 +520,17 @@ def profile_case(name, dtype):
     from paper_2510_08230_gb300 import workloads as W
     dev = torch.device("cuda:0")
     vt = torch.float64 if dtype == "f64" else torch.float32
+    if name == "ilu":
+        m = W.laplacian_2d(512)
+        A = gk.Matrix.from_csr(m, dtype)
+        r = torch.from_numpy(W.uniform_vector(m.n, W.SEED_BASE + 3)).to(dev, vt)
+        z = torch.empty_like(r)
+        for _ in range(3):
+            A.precond_apply(r, z, "ilu")
+        torch.cuda.synchronize()
+        print("profile case ilu", dtype, m.n, m.nnz)
+        A.close()
+        return 0
     if name in ("cg", "bicgstab", "gmres"):
         m = W.diffusion_3d(128)
         A = gk.Matrix.from_csr(m, dtype)
@@ -581,7 +612,7 @@ def main():
     ap.add_argument("--no-solvers", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--profile-case", choices=["merge", "coo", "rowtile", "ell", "sellp", "cg",
-                                               "bicgstab", "gmres"],
+                                               "bicgstab", "gmres", "ilu"],
                     help="run one small case for an ncu capture and exit")
     ap.add_argument("--profile-dtype", default="f64", choices=["f64", "f32"])
     args = ap.parse_args()

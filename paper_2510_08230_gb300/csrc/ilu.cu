@@ -233,9 +233,7 @@ __global__ void k_ilu_store(int32_t n, int64_t nnz, const double* __restrict__ f
         rdiag[i] = cvt<T>(__ddiv_rn(1.0, fac[dpos[i]]));
 }
 
-static size_t ilu_sync_bytes(int32_t nch) {
-    return 2 * sizeof(TrsvSync) + 2 * (size_t)std::max(nch, 1) * sizeof(unsigned);
-}
+static size_t ilu_sync_bytes() { return 2 * sizeof(TrsvSync); }
 
 static void ilu_release(gk_matrix A) {
     dfree(A->ilu_rp);
@@ -301,17 +299,15 @@ static gk_status ilu_build(gk_matrix A, gk_matrix C, cudaStream_t s) {
     GK_CUDA(dmalloc_t(&A->ilu_dpos, (size_t)std::max(n, 1)));
     GK_CUDA(dmalloc(&A->ilu_lu, vb * (size_t)std::max<int64_t>(nnz, 1)));
     GK_CUDA(dmalloc(&A->ilu_rdiag, vb * (size_t)std::max(n, 1)));
-    GK_CUDA(dmalloc(&A->ilu_sync, ilu_sync_bytes(nch)));
+    GK_CUDA(dmalloc(&A->ilu_sync, ilu_sync_bytes()));
     GK_CUDA(dmalloc_t(&A->ilu_ord, 2 * (size_t)std::max(nch, 1)));
     GK_CUDA(cudaMemcpyAsync(A->ilu_rp, C->row_ptr, sizeof(int32_t) * ((size_t)n + 1),
                             cudaMemcpyDeviceToDevice, s));
     if (nnz > 0)
         GK_CUDA(cudaMemcpyAsync(A->ilu_ci, C->col, sizeof(int32_t) * (size_t)nnz,
                                 cudaMemcpyDeviceToDevice, s));
-    // claim counters 0, epochs 1, chunk flags 0
-    GK_CUDA(cudaMemsetAsync(A->ilu_sync, 0, ilu_sync_bytes(nch), s));
-    static const TrsvSync init[2] = {{0u, 0u, 1u, 0u}, {0u, 0u, 1u, 0u}};
-    GK_CUDA(cudaMemcpyAsync(A->ilu_sync, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    // claim counters, exit counters and error flags start at 0
+    GK_CUDA(cudaMemsetAsync(A->ilu_sync, 0, ilu_sync_bytes(), s));
 
     DevBuf fac, done, misc;
     GK_TRY(fac.ensure(sizeof(double) * (size_t)std::max<int64_t>(nnz, 1)));
@@ -342,8 +338,10 @@ static gk_status ilu_build(gk_matrix A, gk_matrix C, cudaStream_t s) {
         unsigned wl = 0, wu = 0;
         GK_TRY(chunk_order(A, n, nch, false, A->ilu_ord, &wl, s));
         GK_TRY(chunk_order(A, n, nch, true, A->ilu_ord + nch, &wu, s));
-        A->ilu_warps[0] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, 2 * (int64_t)wl), nch);
-        A->ilu_warps[1] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, 2 * (int64_t)wu), nch);
+        int64_t mult = 2;
+        if (const char* e = getenv("GK_ILU_WARPS")) mult = std::max(1, atoi(e));
+        A->ilu_warps[0] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, mult * (int64_t)wl), nch);
+        A->ilu_warps[1] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, mult * (int64_t)wu), nch);
         k_ilu_factor<<<resident_grid(k_ilu_factor, std::min<int64_t>(n, 64 * (int64_t)wl + 256)),
                        256, 0, s>>>(n, nch, A->ilu_rp, A->ilu_ci, A->ilu_dpos, A->ilu_ord,
                                     (double*)fac.ptr, (unsigned*)done.ptr, mp);
@@ -402,7 +400,7 @@ IluDev<T> ilu_view(gk_matrix A) {
     f.warps[0] = A->ilu_warps[0];
     f.warps[1] = A->ilu_warps[1];
     f.sy = (TrsvSync*)A->ilu_sync;
-    f.flags = (unsigned*)((char*)A->ilu_sync + 2 * sizeof(TrsvSync));
+    if (const char* e = getenv("GK_ILU_PAUSE")) f.pause_max = (unsigned)std::max(32, atoi(e));
     return f;
 }
 template IluDev<double> ilu_view<double>(gk_matrix);
@@ -460,6 +458,7 @@ extern "C" gk_status gk_precond_apply(gk_matrix A, gk_precond kind, int32_t bloc
     if (!A || (!r && A->n > 0) || (!z && A->n > 0)) return GK_ERR_INVALID;
     if (A->n != A->ncols) return GK_ERR_INVALID;
     if (kind < GK_PRECOND_NONE || kind > GK_PRECOND_ILU) return GK_ERR_INVALID;
+    if (kind == GK_PRECOND_ILU && A->n > 0 && r == z) return GK_ERR_INVALID;
     if (kind == GK_PRECOND_BLOCK_JACOBI && (block_size < 1 || block_size > BJ_MAX))
         return GK_ERR_INVALID;
     int dev = -1;

@@ -5,12 +5,12 @@
 // GMRES(30) with an Ilu preconditioner, Listing 1; Section 5 lists ILU and
 // IC among the bound preconditioners).  The factors live in one value
 // array lu[] in the CSR order of A (unit-lower L strictly below the
-// diagonal, U on and above it), beside private copies of row_ptr / col and
-// the position of every row's diagonal.
+// diagonal, U on and above it), beside private copies of row_ptr / col,
+// the position of every row's diagonal and the pivots' reciprocals.
 //
 // Substitution is a dependency problem: row i of L^-1 r needs every y_j
-// with l_ij != 0.  The kernel is sync-free (no level sets, one launch per
-// triangle):
+// with l_ij != 0.  The kernel is sync-free (no level-by-level launches, one
+// launch per triangle):
 //  - Rows are cut into chunks of 32 consecutive rows; one warp solves one
 //    chunk, one lane per row.  Warps claim chunks from an atomic counter in
 //    a topological order of the chunk dependency graph (by level: a
@@ -19,23 +19,25 @@
 //    claimed before it by running warps: no deadlock.  Claiming by level
 //    also keeps warps from spinning on chunks far ahead of the wavefront,
 //    and the grid is capped at a few times the widest level.
+//  - The values are their own ready signal: before a launch every slot of
+//    the output holds a signalling-NaN sentinel (k_ilu_mark), which no
+//    arithmetic produces; a lane polls the slot of each value it needs
+//    (relaxed loads at GPU scope, a few issued together) until it holds a
+//    number.  Inputs are multiplied by 1 on load, which turns any
+//    signalling NaN into a quiet one and leaves every other value as it is,
+//    so a copied input cannot look like the sentinel either.
 //  - A lane first subtracts its row's terms outside the chunk, in the
 //    order the substitution produced them (L: ascending columns; U:
-//    descending), waiting per source chunk on that chunk's "done" flag.
-//  - The terms inside the chunk are resolved by a 32-step warp loop: at step
-//    t lane t's value is final and is broadcast with a shuffle; lanes whose
-//    row uses column c0 + t subtract it.  Together with the first phase this
-//    subtracts every term in exactly the sequential order, so the result
-//    is bit-identical to plain forward / backward substitution.
-//  - A finished chunk stores its values, fences, and publishes its flag
-//    with a release store of the launch's epoch number.  Flags are never
-//    cleared: a launch waits for "flag == its epoch", and the last warp to
-//    leave the kernel advances the epoch and resets the claim counter for
-//    the next launch.  Values written by other warps are read through L2.
+//    descending).  The terms inside the chunk are resolved by a 32-step
+//    warp loop: at step t lane t's value is final and is broadcast with a
+//    shuffle; lanes whose row uses column c0 + t subtract it.  Together this
+//    subtracts every term in exactly the sequential order.
+//  - The last warp to leave the kernel resets the claim counter for the
+//    next launch.
 //  - Every wait is bounded (about two seconds of SM clock); a wait that
-//    runs out records an error flag and the kernel finishes with wrong
-//    values instead of hanging.  The solver engine turns the flag into
-//    GK_ERR_TIMEOUT.
+//    runs out records an error flag, later waits of the launch give up at
+//    once, and the kernel finishes with wrong values instead of hanging.
+//    The solver engine turns the flag into GK_ERR_TIMEOUT.
 // Products and differences are rounded separately (no fused multiply-add)
 // and U's pivots are applied as stored reciprocals (1 / u_ii rounded once,
 // a multiplication instead of a division on the in-chunk chain), so that
@@ -50,12 +52,12 @@ namespace gk {
 constexpr int TRSV_CHUNK = 32;                      // rows per warp
 constexpr long long ILU_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
-// Per-direction synchronisation words (index 0: L, 1: U).
+// Per-direction words (index 0: L, 1: U).
 struct TrsvSync {
-    unsigned ctr;     // next chunk to claim in solve order
+    unsigned ctr;     // next chunk to claim
     unsigned exited;  // warps that left the current launch
-    unsigned epoch;   // number of the current launch (starts at 1)
-    unsigned err;     // a bounded wait ran out (sticky)
+    unsigned err;     // a bounded wait ran out (sticky until cleared)
+    unsigned pad;
 };
 
 // Device view of one ILU(0) factorisation with values of type T.
@@ -69,7 +71,7 @@ struct IluDev {
     const T* rdiag = nullptr;       // 1 / u_ii, rounded once
     const int32_t* ord = nullptr;   // [2 * nch]: chunks in claim order, L then U
     TrsvSync* sy = nullptr;         // [2]
-    unsigned* flags = nullptr;      // [2 * nch]
+    unsigned pause_max = 64;        // longest pause between polls (ns)
     int32_t warps[2] = {0, 0};      // host: warps per substitution launch
 };
 
@@ -89,11 +91,41 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Sentinel of a not-yet-solved slot: a signalling NaN with a fixed payload.
+template <typename T> struct Sentinel;
+template <> struct Sentinel<double> {
+    static constexpr unsigned long long bits = 0x7FF0DEADBEEF1B1BULL;
+    __device__ static double value() { return __longlong_as_double((long long)bits); }
+    __device__ static bool is(double v) {
+        return (unsigned long long)__double_as_longlong(v) == bits;
+    }
+};
+template <> struct Sentinel<float> {
+    static constexpr unsigned bits = 0x7F801B1BU;
+    __device__ static float value() { return __uint_as_float(bits); }
+    __device__ static bool is(float v) { return __float_as_uint(v) == bits; }
+};
+
+__device__ __forceinline__ double ld_relaxed_v(const double* p) {
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ float ld_relaxed_v(const float* p) {
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_v(double* p, double v) {
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_v(float* p, float v) {
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
 // Spin until *flag == want (acquire), at most ILU_WAIT_CYCLES; on time-out
 // set *err and return false.  Once any wait of the launch has run out
-// (*err set), later waits give up at once, so a failed launch ends within
-// about one time-out.
-// Polls are acquire loads with a growing pause (32 to 256 ns).
+// (*err set), later waits give up at once.  Polls pause 32 to 256 ns.
 __device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned want, unsigned* err) {
     if (ld_acquire_u32(flag) == want) return true;
     const long long t0 = clock64();
@@ -106,6 +138,26 @@ __device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned want, u
         if (clock64() - t0 > ILU_WAIT_CYCLES) {
             atomicExch(err, 1u);
             return false;
+        }
+    }
+}
+
+// The value of slot p once it is no longer the sentinel (v: a first load
+// already issued); bounded like wait_flag, pauses 32 to pause_max ns.
+template <typename T>
+__device__ __forceinline__ T wait_value(const T* p, T v, unsigned* err, unsigned pause_max) {
+    if (!Sentinel<T>::is(v)) return v;
+    const long long t0 = clock64();
+    unsigned ns = 32;
+    for (;;) {
+        __nanosleep(ns);
+        if (ns < pause_max) ns <<= 1;
+        v = ld_relaxed_v(p);
+        if (!Sentinel<T>::is(v)) return v;
+        if (ld_relaxed_u32(err) != 0u) return v;
+        if (clock64() - t0 > ILU_WAIT_CYCLES) {
+            atomicExch(err, 1u);
+            return v;
         }
     }
 }
@@ -145,21 +197,32 @@ struct IluOutStore {
     __device__ __forceinline__ void extra(int64_t, T) const {}
 };
 
+// Marks every slot of both substitutions' outputs as unsolved.
+template <typename T, class Out, class Skip>
+__global__ void __launch_bounds__(256)
+k_ilu_mark(int32_t n, T* __restrict__ w, Out out, Skip sk) {
+    if (sk.skip()) return;
+    T* d = out.dst();
+    const T s = Sentinel<T>::value();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        w[i] = s;
+        d[i] = s;
+    }
+}
+
 // One substitution (UP = false: unit-lower L, ascending; UP = true: U with
-// its diagonal, descending).  The last warp of the U launch hands the
-// error flags of both directions to on_err (the engine turns a wait that
-// ran out into GK_ERR_TIMEOUT and a halt).
+// its reciprocal pivots, descending).  The last warp of the U launch hands
+// the error flags of both directions to on_err (the engine turns a wait
+// that ran out into GK_ERR_TIMEOUT and a halt).
 template <typename T, bool UP, class Src, class Out, class Skip, class Err>
 __global__ void __launch_bounds__(256)
 k_ilu_trsv(IluDev<T> f, Src src, Out out, Skip sk, Err on_err) {
     constexpr unsigned FULL = 0xffffffffu;
+    constexpr int G = 4;  // out-of-chunk values loaded together
     const int lane = threadIdx.x & 31;
     TrsvSync* sy = f.sy + (UP ? 1 : 0);
-    unsigned* flags = f.flags + (UP ? f.nch : 0);
     const unsigned total = gridDim.x * (blockDim.x >> 5);
-    unsigned epoch = 0;
-    if (lane == 0) epoch = ld_acquire_u32(&sy->epoch);
-    epoch = __shfl_sync(FULL, epoch, 0);
     if (!sk.skip()) {
         const T* in = src.ptr();
         T* dst = out.dst();
@@ -176,36 +239,45 @@ k_ilu_trsv(IluDev<T> f, Src src, Out out, Skip sk, Err on_err) {
             T acc = T(0);
             int32_t pin = 0, pend = 0;  // in-chunk entries [pin, pend)
             if (has) {
-                acc = in[i];
+                acc = mul_rn(in[i], T(1));  // quiets a signalling NaN, else exact
                 const int32_t d = f.dpos[i];
-                int32_t waited = -1;
-                bool ok = true;
-                if (!UP) {
-                    int32_t k = f.rp[i];
-                    for (; k < d; ++k) {
-                        const int32_t j = f.ci[k];
-                        if (j >= c0) break;
-                        const int32_t cj = j / TRSV_CHUNK;
-                        if (cj != waited && ok) {
-                            ok = wait_flag(flags + cj, epoch, &sy->err);
-                            waited = cj;
+                // terms outside the chunk, G at a time, in substitution order
+                // (L: ascending from the row start; U: descending from its end)
+                int32_t k = UP ? f.rp[i + 1] - 1 : f.rp[i];
+                for (;;) {
+                    int32_t jj[G];
+                    T vv[G], lv[G];
+                    int g = 0;
+#pragma unroll
+                    for (int u = 0; u < G; ++u) {
+                        jj[u] = -1;
+                        const int32_t ku = UP ? k - u : k + u;
+                        if (g == u && (UP ? ku > d : ku < d)) {
+                            const int32_t j = f.ci[ku];
+                            if (UP ? j >= c1 : j < c0) {
+                                jj[u] = j;
+                                ++g;
+                            }
                         }
-                        acc = sub_mul(acc, f.lu[k], __ldcg(dst + j));
                     }
+#pragma unroll
+                    for (int u = 0; u < G; ++u)
+                        if (jj[u] >= 0) {
+                            vv[u] = ld_relaxed_v(dst + jj[u]);
+                            lv[u] = f.lu[UP ? k - u : k + u];
+                        }
+#pragma unroll
+                    for (int u = 0; u < G; ++u)
+                        if (jj[u] >= 0)
+                            acc = sub_mul(acc, lv[u],
+                                          wait_value(dst + jj[u], vv[u], &sy->err, f.pause_max));
+                    k = UP ? k - g : k + g;
+                    if (g < G) break;
+                }
+                if (!UP) {
                     pin = k;
                     pend = d;
                 } else {
-                    int32_t k = f.rp[i + 1] - 1;
-                    for (; k > d; --k) {
-                        const int32_t j = f.ci[k];
-                        if (j < c1) break;
-                        const int32_t cj = j / TRSV_CHUNK;
-                        if (cj != waited && ok) {
-                            ok = wait_flag(flags + cj, epoch, &sy->err);
-                            waited = cj;
-                        }
-                        acc = sub_mul(acc, f.lu[k], __ldcg(dst + j));
-                    }
                     pin = d + 1;
                     pend = k + 1;
                 }
@@ -244,11 +316,9 @@ k_ilu_trsv(IluDev<T> f, Src src, Out out, Skip sk, Err on_err) {
                 }
             }
             if (has) {
-                dst[i] = mine;
+                st_relaxed_v(dst + i, mine);
                 out.extra(i, mine);
             }
-            __syncwarp();  // the lanes' stores are ordered before lane 0's release
-            if (lane == 0) st_release_u32(flags + cc, epoch);
         }
     }
     // every warp leaves exactly once; the last one prepares the next launch
@@ -260,7 +330,6 @@ k_ilu_trsv(IluDev<T> f, Src src, Out out, Skip sk, Err on_err) {
             sy->ctr = 0;
             sy->exited = 0;
             __threadfence();
-            st_release_u32(&sy->epoch, epoch + 1);
         }
     }
 }
@@ -280,13 +349,18 @@ static unsigned ilu_grid(K kernel, int32_t warps) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * b));
 }
 
-// z = U^-1 L^-1 src: L into w, then U from w with the caller's output.
+// z = U^-1 L^-1 src: mark both outputs unsolved, L into w, then U from w
+// with the caller's output.
 template <typename T, class Src, class Out, class Skip, class Err>
 static gk_status ilu_apply(const IluDev<T>& f, Src src, T* w, Out out, Skip sk, Err on_err,
                            cudaStream_t s) {
     if (f.n == 0) return GK_OK;
+    auto km = k_ilu_mark<T, Out, Skip>;
     auto kl = k_ilu_trsv<T, false, Src, IluOutStore<T>, Skip, IluNoErr>;
     auto ku = k_ilu_trsv<T, true, IluSrc<T>, Out, Skip, Err>;
+    const unsigned mg = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(((int64_t)f.n + 1023) / 1024, (int64_t)num_sms() * 8));
+    km<<<mg, 256, 0, s>>>(f.n, w, out, sk);
     kl<<<ilu_grid(kl, f.warps[0]), 256, 0, s>>>(f, src, IluOutStore<T>{w}, sk, IluNoErr{});
     ku<<<ilu_grid(ku, f.warps[1]), 256, 0, s>>>(f, IluSrc<T>{w}, out, sk, on_err);
     GK_CUDA(cudaGetLastError());

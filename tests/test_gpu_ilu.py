@@ -276,3 +276,30 @@ def test_full_size_diffusion_128_factors_and_apply_bit_exact():
     want = oracle.ilu0_apply(m, lu, r)
     assert np.array_equal(zt.cpu().numpy().view(np.uint64), want.view(np.uint64))
     A.close()
+
+
+def test_input_holding_the_unsolved_marker_is_a_plain_nan():
+    """The substitutions mark unsolved slots with one signalling-NaN bit
+    pattern; an input entry with exactly that pattern must come out as an
+    ordinary NaN (propagating to the rows that depend on it), not stall."""
+    import torch
+    dev = torch_dev()
+    m = W.laplacian_2d(40, 9)
+    A = gk.Matrix.from_csr(m, "f64")
+    r = W.uniform_vector(m.n, 12)
+    r.view(np.uint64)[[0, 77]] = np.uint64(0x7FF0DEADBEEF1B1B)
+    rt = torch.from_numpy(r).to(dev)
+    zt = torch.empty_like(rt)
+    A.precond_apply(rt, zt, "ilu")
+    torch.cuda.synchronize()
+    z = zt.cpu().numpy()
+    assert np.isnan(z).any()
+    assert not np.any(z.view(np.uint64) == np.uint64(0x7FF0DEADBEEF1B1B))
+    # a clean input afterwards is exact again
+    r2 = W.uniform_vector(m.n, 13)
+    rt2 = torch.from_numpy(r2).to(dev)
+    A.precond_apply(rt2, zt, "ilu")
+    torch.cuda.synchronize()
+    want = oracle.ilu0_apply(m, oracle.ilu0(m), r2)
+    assert np.array_equal(zt.cpu().numpy().view(np.uint64), want.view(np.uint64))
+    A.close()
