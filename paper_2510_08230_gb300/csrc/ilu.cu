@@ -3,7 +3,7 @@
 //
 // Setup, once per matrix:
 //  1. k_ilu_prep: strictly ascending columns, diagonal positions.
-//  2. k_chunk_levels (L and U): the level of every 32-row chunk in the
+//  2. k_chunk_levels (L and U): the level of every chunk of rows in the
 //     dependency graph of each substitution; a counting sort by level
 //     (k_level_hist, k_level_scan, k_level_scatter) gives the claim order
 //     of the substitution kernels and the widest level (their grid cap).
@@ -13,7 +13,9 @@
 //     also stores) runs sync-free: one warp per row, rows claimed chunk by
 //     chunk in the L claim order and in ascending order inside a chunk (a
 //     topological order), so a row only waits (bounded) on rows claimed
-//     before it.  Row i waits for row
+//     before it.
+//  4. k_ilu_store: factors rounded to the vector type, 1 / u_ii.
+//  5. tune_chunks: the substitutions' chunk size (32 or 8 rows), timed.  Row i waits for row
 // k to be final before it reads u_kk and row k's upper part; the lanes then
 // update row i's entries for row k's columns in parallel (each entry is hit
 // at most once per k, and the k steps run in ascending order), so every
@@ -67,12 +69,13 @@ __device__ __forceinline__ unsigned wait_nonzero(const unsigned* p, unsigned* er
     }
 }
 
-// lev[c] = 1 + the highest level among the chunks chunk c depends on (L:
-// columns left of the chunk; U: right of it); chunks claimed in solve order.
-// misc[0] claim counter, misc[1] wait ran out.
+// lev[c] = 1 + the highest level among the chunks (of cs rows) chunk c
+// depends on (L: columns left of the chunk; U: right of it); chunks claimed
+// in solve order.  misc[0] claim counter, misc[1] wait ran out, misc[3] the
+// highest level.
 template <bool UP>
 __global__ void __launch_bounds__(256)
-k_chunk_levels(int32_t n, int32_t nch, const int32_t* __restrict__ rp,
+k_chunk_levels(int32_t n, int32_t nch, int32_t cs, const int32_t* __restrict__ rp,
                const int32_t* __restrict__ ci, const int32_t* __restrict__ dpos, unsigned* lev,
                unsigned* misc) {
     constexpr unsigned FULL = 0xffffffffu;
@@ -83,17 +86,17 @@ k_chunk_levels(int32_t n, int32_t nch, const int32_t* __restrict__ rp,
         c = __shfl_sync(FULL, c, 0);
         if (c >= nch) break;
         const int32_t cc = UP ? nch - 1 - c : c;
-        const int32_t c0 = cc * TRSV_CHUNK, c1 = min(c0 + TRSV_CHUNK, n);
+        const int32_t c0 = cc * cs, c1 = min(c0 + cs, n);
         const int32_t i = c0 + lane;
         unsigned mx = 0;
-        if (i < n) {
+        if (lane < cs && i < n) {
             const int32_t d = dpos[i];
             int32_t last = -1;
             if (!UP) {
                 for (int32_t k = rp[i]; k < d; ++k) {
                     const int32_t j = ci[k];
                     if (j >= c0) break;
-                    const int32_t cj = j / TRSV_CHUNK;
+                    const int32_t cj = j / cs;
                     if (cj != last) {
                         mx = max(mx, wait_nonzero(lev + cj, &misc[1]));
                         last = cj;
@@ -103,7 +106,7 @@ k_chunk_levels(int32_t n, int32_t nch, const int32_t* __restrict__ rp,
                 for (int32_t k = rp[i + 1] - 1; k > d; --k) {
                     const int32_t j = ci[k];
                     if (j < c1) break;
-                    const int32_t cj = j / TRSV_CHUNK;
+                    const int32_t cj = j / cs;
                     if (cj != last) {
                         mx = max(mx, wait_nonzero(lev + cj, &misc[1]));
                         last = cj;
@@ -112,7 +115,10 @@ k_chunk_levels(int32_t n, int32_t nch, const int32_t* __restrict__ rp,
             }
         }
         mx = __reduce_max_sync(FULL, mx);
-        if (lane == 0) st_release_u32(lev + cc, mx + 1);
+        if (lane == 0) {
+            st_release_u32(lev + cc, mx + 1);
+            atomicMax(&misc[3], mx + 1);
+        }
     }
 }
 
@@ -175,18 +181,18 @@ __global__ void k_level_scatter(int32_t nch, const unsigned* __restrict__ lev, u
 
 // misc[0] claim counter, misc[1] wait ran out, misc[2] zero pivot
 __global__ void __launch_bounds__(256)
-k_ilu_factor(int32_t n, int32_t nch, const int32_t* __restrict__ rp,
+k_ilu_factor(int32_t n, int32_t nch, int32_t cs, const int32_t* __restrict__ rp,
              const int32_t* __restrict__ ci, const int32_t* __restrict__ dpos,
              const int32_t* __restrict__ ord, double* fac, unsigned* done, unsigned* misc) {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int64_t nclaim = (int64_t)nch * TRSV_CHUNK;
+    const int64_t nclaim = (int64_t)nch * cs;
     for (;;) {
         int64_t c = 0;
         if (lane == 0) c = (int64_t)atomicAdd(&misc[0], 1u);
         c = __shfl_sync(FULL, c, 0);
         if (c >= nclaim) break;
-        const int32_t i = ord[c / TRSV_CHUNK] * TRSV_CHUNK + (int32_t)(c % TRSV_CHUNK);
+        const int32_t i = ord[c / cs] * cs + (int32_t)(c % cs);
         if (i >= n) continue;  // past the last row of the last chunk
         const int32_t p1 = rp[i + 1], d = dpos[i];
         int ok = 1;
@@ -260,8 +266,9 @@ static unsigned resident_grid(K kernel, int64_t items) {
 
 // Levels of the L (up = false) or U chunk graph, the claim order sorted by
 // level into ord[0, nch), and the widest level in *maxw (host).
-static gk_status chunk_order(gk_matrix A, int32_t n, int32_t nch, bool up, int32_t* ord,
-                             unsigned* maxw, cudaStream_t s) {
+static gk_status chunk_order(gk_matrix A, int32_t n, int32_t cs, bool up, int32_t* ord,
+                             unsigned* maxw, unsigned* nlev, cudaStream_t s) {
+    const int32_t nch = (n + cs - 1) / cs;
     DevBuf lev, cnt, misc;
     GK_TRY(lev.ensure(sizeof(unsigned) * (size_t)nch));
     GK_TRY(cnt.ensure(sizeof(unsigned) * ((size_t)nch + 2)));
@@ -272,27 +279,127 @@ static gk_status chunk_order(gk_matrix A, int32_t n, int32_t nch, bool up, int32
     unsigned* mp = (unsigned*)misc.ptr;
     if (up)
         k_chunk_levels<true><<<resident_grid(k_chunk_levels<true>, nch), 256, 0, s>>>(
-            n, nch, A->ilu_rp, A->ilu_ci, A->ilu_dpos, (unsigned*)lev.ptr, mp);
+            n, nch, cs, A->ilu_rp, A->ilu_ci, A->ilu_dpos, (unsigned*)lev.ptr, mp);
     else
         k_chunk_levels<false><<<resident_grid(k_chunk_levels<false>, nch), 256, 0, s>>>(
-            n, nch, A->ilu_rp, A->ilu_ci, A->ilu_dpos, (unsigned*)lev.ptr, mp);
+            n, nch, cs, A->ilu_rp, A->ilu_ci, A->ilu_dpos, (unsigned*)lev.ptr, mp);
     const unsigned g = ew_grid(nch);
     k_level_hist<<<g, 256, 0, s>>>(nch, (const unsigned*)lev.ptr, (unsigned*)cnt.ptr);
     k_level_scan<<<1, 1024, 0, s>>>(nch + 2, (unsigned*)cnt.ptr, mp + 2);
-    k_level_scatter<<<g, 256, 0, s>>>(nch, (const unsigned*)lev.ptr, (unsigned*)cnt.ptr, ord);
+    if (ord)
+        k_level_scatter<<<g, 256, 0, s>>>(nch, (const unsigned*)lev.ptr, (unsigned*)cnt.ptr, ord);
     GK_CUDA(cudaGetLastError());
     unsigned h[4] = {0, 0, 0, 0};
     GK_CUDA(cudaMemcpyAsync(h, mp, sizeof(h), cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaStreamSynchronize(s));
     if (h[1]) return GK_ERR_TIMEOUT;
     *maxw = h[2];
+    *nlev = h[3];
+    return GK_OK;
+}
+
+template <typename T>
+IluDev<T> ilu_view(gk_matrix A) {
+    IluDev<T> f;
+    f.n = A->n;
+    f.cs = A->ilu_cs;
+    f.nch = (A->n + f.cs - 1) / f.cs;
+    f.rp = A->ilu_rp;
+    f.ci = A->ilu_ci;
+    f.dpos = A->ilu_dpos;
+    f.lu = (const T*)A->ilu_lu;
+    f.rdiag = (const T*)A->ilu_rdiag;
+    f.ord = A->ilu_ord;
+    f.warps[0] = A->ilu_warps[0];
+    f.warps[1] = A->ilu_warps[1];
+    f.sy = (TrsvSync*)A->ilu_sync;
+    if (const char* e = getenv("GK_ILU_PAUSE")) f.pause_max = (unsigned)std::max(32, atoi(e));
+    return f;
+}
+template IluDev<double> ilu_view<double>(gk_matrix);
+template IluDev<float> ilu_view<float>(gk_matrix);
+
+// Rows per substitution chunk, timed per matrix: 32-row chunks need fewest
+// dependency levels, 8-row chunks the shortest chain inside a chunk; which
+// wins depends on the pattern (on the 2D 5-point Laplacian 1024^2 8 rows
+// take 10.4 ms against 17.5, on the 128^3 diffusion matrix 32 rows take
+// 3.35 ms against 3.58).  Each candidate gets its claim orders, grid caps and
+// one timed application (after a warm-up one) of z = M^-1 d with d = 1/u_ii;
+// the fastest is kept.  GK_ILU_CHUNK (8, 16 or 32) forces a size.  Results
+// never depend on the choice, only the time does.
+template <typename T>
+static gk_status tune_chunks(gk_matrix A, int32_t n, cudaStream_t s) {
+    int forced = 0;
+    if (const char* e = getenv("GK_ILU_CHUNK")) {
+        const int v = atoi(e);
+        if (v == 8 || v == 16 || v == 32) forced = v;
+    }
+    int64_t mult = 2;
+    if (const char* e = getenv("GK_ILU_WARPS")) mult = std::max(1, atoi(e));
+    const int cands[2] = {forced ? forced : 32, 8};
+    const int ncand = forced ? 1 : 2;
+    DevBuf ordb[2], tmp;
+    int32_t warps[2][2] = {{0, 0}, {0, 0}};
+    GK_TRY(tmp.ensure(2 * sizeof(T) * (size_t)n));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    GK_CUDA(cudaEventCreate(&e0));
+    GK_CUDA(cudaEventCreate(&e1));
+    gk_status st = GK_OK;
+    float best = 0.f;
+    int pick = 0;
+    for (int k = 0; k < ncand && st == GK_OK; ++k) {
+        const int32_t cs = cands[k], nch = (n + cs - 1) / cs;
+        unsigned wl = 0, wu = 0, ll = 0, lu_ = 0;
+        st = ordb[k].ensure(2 * sizeof(int32_t) * (size_t)nch);
+        if (st == GK_OK) st = chunk_order(A, n, cs, false, (int32_t*)ordb[k].ptr, &wl, &ll, s);
+        if (st == GK_OK)
+            st = chunk_order(A, n, cs, true, (int32_t*)ordb[k].ptr + nch, &wu, &lu_, s);
+        if (st != GK_OK) break;
+        warps[k][0] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, mult * (int64_t)wl), nch);
+        warps[k][1] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, mult * (int64_t)wu), nch);
+        if (ncand == 1) break;
+        IluDev<T> f = ilu_view<T>(A);
+        f.cs = cs;
+        f.nch = nch;
+        f.ord = (const int32_t*)ordb[k].ptr;
+        f.warps[0] = warps[k][0];
+        f.warps[1] = warps[k][1];
+        T* w = (T*)tmp.ptr;
+        const IluSrc<T> src{(const T*)A->ilu_rdiag};
+        float ms = 0.f;
+        st = ilu_apply<T>(f, src, w, IluOutStore<T>{w + n}, IluSkipNever{}, IluNoErr{}, s);
+        if (st == GK_OK && cudaEventRecord(e0, s) != cudaSuccess) st = GK_ERR_CUDA;
+        if (st == GK_OK)
+            st = ilu_apply<T>(f, src, w, IluOutStore<T>{w + n}, IluSkipNever{}, IluNoErr{}, s);
+        if (st == GK_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                            cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            st = GK_ERR_CUDA;
+        if (st == GK_OK && (k == 0 || ms < best)) {
+            best = ms;
+            pick = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != GK_OK) return st;
+    TrsvSync h[2];
+    GK_CUDA(cudaMemcpyAsync(h, A->ilu_sync, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    if (h[0].err | h[1].err) return GK_ERR_TIMEOUT;
+    const int32_t cs = cands[pick], nch = (n + cs - 1) / cs;
+    GK_CUDA(cudaMemcpyAsync(A->ilu_ord, ordb[pick].ptr, 2 * sizeof(int32_t) * (size_t)nch,
+                            cudaMemcpyDeviceToDevice, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    A->ilu_cs = cs;
+    A->ilu_warps[0] = warps[pick][0];
+    A->ilu_warps[1] = warps[pick][1];
     return GK_OK;
 }
 
 static gk_status ilu_build(gk_matrix A, gk_matrix C, cudaStream_t s) {
     const int32_t n = C->n;
     const int64_t nnz = C->nnz;
-    const int32_t nch = (n + TRSV_CHUNK - 1) / TRSV_CHUNK;
     const size_t vb = vector_bytes(A->dtype);
     GK_CUDA(dmalloc_t(&A->ilu_rp, (size_t)n + 1));
     GK_CUDA(dmalloc_t(&A->ilu_ci, (size_t)std::max<int64_t>(nnz, 1)));
@@ -300,7 +407,8 @@ static gk_status ilu_build(gk_matrix A, gk_matrix C, cudaStream_t s) {
     GK_CUDA(dmalloc(&A->ilu_lu, vb * (size_t)std::max<int64_t>(nnz, 1)));
     GK_CUDA(dmalloc(&A->ilu_rdiag, vb * (size_t)std::max(n, 1)));
     GK_CUDA(dmalloc(&A->ilu_sync, ilu_sync_bytes()));
-    GK_CUDA(dmalloc_t(&A->ilu_ord, 2 * (size_t)std::max(nch, 1)));
+    // claim orders for chunks of 8 rows at most (the smallest chunk size)
+    GK_CUDA(dmalloc_t(&A->ilu_ord, 2 * (size_t)std::max((n + 7) / 8, 1)));
     GK_CUDA(cudaMemcpyAsync(A->ilu_rp, C->row_ptr, sizeof(int32_t) * ((size_t)n + 1),
                             cudaMemcpyDeviceToDevice, s));
     if (nnz > 0)
@@ -333,17 +441,14 @@ static gk_status ilu_build(gk_matrix A, gk_matrix C, cudaStream_t s) {
         GK_CUDA(cudaStreamSynchronize(s));
         if (h[3] & 1u) return GK_ERR_INVALID;
         if (h[3] & 2u) return GK_ERR_ZERO_DIAG;
-        // claim orders and grid caps of the two substitutions (a few
-        // times the widest level of chunks, at least 64 warps)
-        unsigned wl = 0, wu = 0;
-        GK_TRY(chunk_order(A, n, nch, false, A->ilu_ord, &wl, s));
-        GK_TRY(chunk_order(A, n, nch, true, A->ilu_ord + nch, &wu, s));
-        int64_t mult = 2;
-        if (const char* e = getenv("GK_ILU_WARPS")) mult = std::max(1, atoi(e));
-        A->ilu_warps[0] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, mult * (int64_t)wl), nch);
-        A->ilu_warps[1] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, mult * (int64_t)wu), nch);
-        k_ilu_factor<<<resident_grid(k_ilu_factor, std::min<int64_t>(n, 64 * (int64_t)wl + 256)),
-                       256, 0, s>>>(n, nch, A->ilu_rp, A->ilu_ci, A->ilu_dpos, A->ilu_ord,
+        // the factorisation claims rows chunk by chunk in the L level order
+        // of 32-row chunks
+        const int32_t cs = 32, nch = (n + cs - 1) / cs;
+        unsigned wl = 0, ll = 0;
+        GK_TRY(chunk_order(A, n, cs, false, A->ilu_ord, &wl, &ll, s));
+        k_ilu_factor<<<resident_grid(k_ilu_factor,
+                                     std::min<int64_t>(n, 2 * (int64_t)cs * wl + 256)),
+                       256, 0, s>>>(n, nch, cs, A->ilu_rp, A->ilu_ci, A->ilu_dpos, A->ilu_ord,
                                     (double*)fac.ptr, (unsigned*)done.ptr, mp);
         GK_CUDA(cudaGetLastError());
         GK_CUDA(cudaMemcpyAsync(h, mp, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -359,6 +464,7 @@ static gk_status ilu_build(gk_matrix A, gk_matrix C, cudaStream_t s) {
                                                             A->ilu_dpos, (float*)A->ilu_lu,
                                                             (float*)A->ilu_rdiag);
         GK_CUDA(cudaGetLastError());
+        GK_TRY(A->dtype == GK_F64 ? tune_chunks<double>(A, n, s) : tune_chunks<float>(A, n, s));
     }
     GK_CUDA(cudaStreamSynchronize(s));
     return GK_OK;
@@ -386,25 +492,6 @@ gk_status ensure_ilu(gk_matrix A, cudaStream_t s) {
     return GK_OK;
 }
 
-template <typename T>
-IluDev<T> ilu_view(gk_matrix A) {
-    IluDev<T> f;
-    f.n = A->n;
-    f.nch = (A->n + TRSV_CHUNK - 1) / TRSV_CHUNK;
-    f.rp = A->ilu_rp;
-    f.ci = A->ilu_ci;
-    f.dpos = A->ilu_dpos;
-    f.lu = (const T*)A->ilu_lu;
-    f.rdiag = (const T*)A->ilu_rdiag;
-    f.ord = A->ilu_ord;
-    f.warps[0] = A->ilu_warps[0];
-    f.warps[1] = A->ilu_warps[1];
-    f.sy = (TrsvSync*)A->ilu_sync;
-    if (const char* e = getenv("GK_ILU_PAUSE")) f.pause_max = (unsigned)std::max(32, atoi(e));
-    return f;
-}
-template IluDev<double> ilu_view<double>(gk_matrix);
-template IluDev<float> ilu_view<float>(gk_matrix);
 
 template <typename T>
 __global__ void EW_BOUNDS k_scale_by(int32_t n, const T* __restrict__ d, const T* __restrict__ r,

@@ -11,8 +11,11 @@
 // Substitution is a dependency problem: row i of L^-1 r needs every y_j
 // with l_ij != 0.  The kernel is sync-free (no level-by-level launches, one
 // launch per triangle):
-//  - Rows are cut into chunks of 32 consecutive rows; one warp solves one
-//    chunk, one lane per row.  Warps claim chunks from an atomic counter in
+//  - Rows are cut into chunks of cs consecutive rows (cs = 32 or 8, timed
+//    per matrix at setup: shorter chunks shorten the serial chain inside a
+//    chunk, longer ones cut the number of dependency levels when rows
+//    depend on their neighbours); one warp solves one chunk, one lane per
+//    row.  Warps claim chunks from an atomic counter in
 //    a topological order of the chunk dependency graph (by level: a
 //    chunk's level is one more than the highest level it depends on,
 //    computed once per matrix), so a chunk only ever waits on chunks
@@ -29,7 +32,7 @@
 //  - A lane first subtracts its row's terms outside the chunk, in the
 //    order the substitution produced them (L: ascending columns; U:
 //    descending).  The terms inside the chunk are resolved by a 32-step
-//    warp loop: at step t lane t's value is final and is broadcast with a
+//    warp loop (cs steps): at step t lane t's value is final and is broadcast with a
 //    shuffle; lanes whose row uses column c0 + t subtract it.  Together this
 //    subtracts every term in exactly the sequential order.
 //  - The last warp to leave the kernel resets the claim counter for the
@@ -49,7 +52,7 @@
 
 namespace gk {
 
-constexpr int TRSV_CHUNK = 32;                      // rows per warp
+constexpr int TRSV_CHUNK_MAX = 32;                  // rows per warp at most
 constexpr long long ILU_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
 // Per-direction words (index 0: L, 1: U).
@@ -64,6 +67,7 @@ struct TrsvSync {
 template <typename T>
 struct IluDev {
     int32_t n = 0, nch = 0;
+    int32_t cs = 32;                // rows per chunk (8, 16 or 32)
     const int32_t* rp = nullptr;    // row_ptr[n + 1]
     const int32_t* ci = nullptr;    // col[nnz], strictly ascending per row
     const int32_t* dpos = nullptr;  // position of a_ii in row i
@@ -232,10 +236,10 @@ k_ilu_trsv(IluDev<T> f, Src src, Out out, Skip sk, Err on_err) {
             c = __shfl_sync(FULL, c, 0);
             if (c >= f.nch) break;
             const int cc = f.ord[(UP ? f.nch : 0) + c];
-            const int32_t c0 = cc * TRSV_CHUNK;
-            const int32_t c1 = min(c0 + TRSV_CHUNK, f.n);
+            const int32_t c0 = cc * f.cs;
+            const int32_t c1 = min(c0 + f.cs, f.n);
             const int32_t i = c0 + lane;
-            const bool has = i < f.n;
+            const bool has = lane < f.cs && i < f.n;
             T acc = T(0);
             int32_t pin = 0, pend = 0;  // in-chunk entries [pin, pend)
             if (has) {
