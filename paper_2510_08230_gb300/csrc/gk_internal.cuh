@@ -223,6 +223,8 @@ struct gk_matrix_s {
     int32_t* ilu_ord = nullptr;   // chunks of 32 rows in claim (level) order: L, then U
     int32_t ilu_warps[2] = {0, 0};  // warps per substitution launch (L, U)
     int32_t ilu_cs = 32;            // rows per substitution chunk
+    int32_t ilu_cpw = 1;            // substitution chunks per warp
+    int32_t ilu_nord[2] = {0, 0};   // claim-order lengths (L at ilu_ord, U after it)
     void* ilu_sync = nullptr;     // substitution claim counters, epochs and chunk flags
     gk::DevBuf ilu_w;             // scratch of gk_precond_apply
     gk_matrix_s* lowp[3] = {nullptr, nullptr, nullptr};  // same layout, other dtype

@@ -129,9 +129,11 @@ __global__ void k_level_hist(int32_t nch, const unsigned* __restrict__ lev, unsi
         atomicAdd(&cnt[lev[c]], 1u);
 }
 
-// In place exclusive scan of cnt[0, len) by one block of 1024 threads;
-// *maxw = the largest count.
-__global__ void __launch_bounds__(1024) k_level_scan(int32_t len, unsigned* cnt, unsigned* maxw) {
+// In place exclusive scan of cnt[0, len), each count first rounded up to a
+// multiple of pad, by one block of 1024 threads; *maxw = the largest
+// (rounded) count, *total = the sum.
+__global__ void __launch_bounds__(1024)
+k_level_scan(int32_t len, int32_t pad, unsigned* cnt, unsigned* maxw, unsigned* total) {
     __shared__ unsigned wsum[32];
     __shared__ unsigned carry;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(1024) k_level_scan(int32_t len, unsigned* cnt,
     __syncthreads();
     for (int32_t base = 0; base < len; base += 1024) {
         const int32_t k = base + tid;
-        const unsigned v = k < len ? cnt[k] : 0u;
+        const unsigned v = k < len ? (cnt[k] + pad - 1) / pad * pad : 0u;
         mx = max(mx, v);
         unsigned incl = v;
 #pragma unroll
@@ -168,10 +170,11 @@ __global__ void __launch_bounds__(1024) k_level_scan(int32_t len, unsigned* cnt,
     }
     mx = __reduce_max_sync(0xffffffffu, mx);
     if (lane == 0) atomicMax(maxw, mx);
+    if (tid == 0) *total = carry;
 }
 
 // ord[start[lev[c]]++] = c (order inside a level is immaterial: no chunk
-// depends on another of its level)
+// depends on another of its level; the padding slots keep -1)
 __global__ void k_level_scatter(int32_t nch, const unsigned* __restrict__ lev, unsigned* cursor,
                                 int32_t* __restrict__ ord) {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nch;
@@ -266,8 +269,13 @@ static unsigned resident_grid(K kernel, int64_t items) {
 
 // Levels of the L (up = false) or U chunk graph, the claim order sorted by
 // level into ord[0, nch), and the widest level in *maxw (host).
-static gk_status chunk_order(gk_matrix A, int32_t n, int32_t cs, bool up, int32_t* ord,
-                             unsigned* maxw, unsigned* nlev, cudaStream_t s) {
+// Levels of the L (up = false) or U graph of cs-row chunks, the claim order
+// sorted by level into ord (each level's run padded to a multiple of pad with
+// -1; at most pad * nch entries), its length (*nord), the widest padded
+// level (*maxw) and the number of levels (*nlev).
+static gk_status chunk_order(gk_matrix A, int32_t n, int32_t cs, int32_t pad, bool up,
+                             int32_t* ord, unsigned* maxw, unsigned* nlev, unsigned* nord,
+                             cudaStream_t s) {
     const int32_t nch = (n + cs - 1) / cs;
     DevBuf lev, cnt, misc;
     GK_TRY(lev.ensure(sizeof(unsigned) * (size_t)nch));
@@ -285,16 +293,19 @@ static gk_status chunk_order(gk_matrix A, int32_t n, int32_t cs, bool up, int32_
             n, nch, cs, A->ilu_rp, A->ilu_ci, A->ilu_dpos, (unsigned*)lev.ptr, mp);
     const unsigned g = ew_grid(nch);
     k_level_hist<<<g, 256, 0, s>>>(nch, (const unsigned*)lev.ptr, (unsigned*)cnt.ptr);
-    k_level_scan<<<1, 1024, 0, s>>>(nch + 2, (unsigned*)cnt.ptr, mp + 2);
-    if (ord)
+    k_level_scan<<<1, 1024, 0, s>>>(nch + 2, pad, (unsigned*)cnt.ptr, mp + 2, mp + 4);
+    if (ord) {
+        GK_CUDA(cudaMemsetAsync(ord, 0xFF, sizeof(int32_t) * (size_t)pad * nch, s));
         k_level_scatter<<<g, 256, 0, s>>>(nch, (const unsigned*)lev.ptr, (unsigned*)cnt.ptr, ord);
+    }
     GK_CUDA(cudaGetLastError());
-    unsigned h[4] = {0, 0, 0, 0};
+    unsigned h[5] = {0, 0, 0, 0, 0};
     GK_CUDA(cudaMemcpyAsync(h, mp, sizeof(h), cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaStreamSynchronize(s));
     if (h[1]) return GK_ERR_TIMEOUT;
     *maxw = h[2];
     *nlev = h[3];
+    *nord = h[4];
     return GK_OK;
 }
 
@@ -303,13 +314,17 @@ IluDev<T> ilu_view(gk_matrix A) {
     IluDev<T> f;
     f.n = A->n;
     f.cs = A->ilu_cs;
+    f.cpw = A->ilu_cpw;
     f.nch = (A->n + f.cs - 1) / f.cs;
     f.rp = A->ilu_rp;
     f.ci = A->ilu_ci;
     f.dpos = A->ilu_dpos;
     f.lu = (const T*)A->ilu_lu;
     f.rdiag = (const T*)A->ilu_rdiag;
-    f.ord = A->ilu_ord;
+    f.ord_l = A->ilu_ord;
+    f.ord_u = A->ilu_ord + A->ilu_nord[0];
+    f.nord[0] = A->ilu_nord[0];
+    f.nord[1] = A->ilu_nord[1];
     f.warps[0] = A->ilu_warps[0];
     f.warps[1] = A->ilu_warps[1];
     f.sy = (TrsvSync*)A->ilu_sync;
@@ -319,14 +334,17 @@ IluDev<T> ilu_view(gk_matrix A) {
 template IluDev<double> ilu_view<double>(gk_matrix);
 template IluDev<float> ilu_view<float>(gk_matrix);
 
-// Rows per substitution chunk, timed per matrix: 32-row chunks need fewest
-// dependency levels, 8-row chunks the shortest chain inside a chunk; which
-// wins depends on the pattern (on the 2D 5-point Laplacian 1024^2 8 rows
-// take 10.4 ms against 17.5, on the 128^3 diffusion matrix 32 rows take
-// 3.35 ms against 3.58).  Each candidate gets its claim orders, grid caps and
-// one timed application (after a warm-up one) of z = M^-1 d with d = 1/u_ii;
-// the fastest is kept.  GK_ILU_CHUNK (8, 16 or 32) forces a size.  Results
-// never depend on the choice, only the time does.
+// Rows per substitution chunk and chunks per warp, timed per matrix:
+// 32-row chunks need the fewest dependency levels, 8-row chunks the
+// shortest chain inside a chunk; four 8-row chunks to a warp need 4x fewer
+// warps but move in step.  Which wins depends on the pattern (measured on
+// GB300, FP64: the 128^3 diffusion matrix 3.05 ms with 32 rows, 3.26 with
+// four 8-row chunks a warp; the 2D 5-point Laplacian 1024^2 17.4 ms, 10.4
+// with one 8-row chunk a warp, 12.5 with four).  Each candidate gets its
+// claim orders, grid caps and one timed application (after a warm-up one)
+// of z = M^-1 d with d = 1/u_ii; the fastest is kept.  GK_ILU_CHUNK (8, 16
+// or 32, one chunk a warp) forces a size.  Results never depend on the
+// choice, only the time does.
 template <typename T>
 static gk_status tune_chunks(gk_matrix A, int32_t n, cudaStream_t s) {
     int forced = 0;
@@ -336,10 +354,10 @@ static gk_status tune_chunks(gk_matrix A, int32_t n, cudaStream_t s) {
     }
     int64_t mult = 2;
     if (const char* e = getenv("GK_ILU_WARPS")) mult = std::max(1, atoi(e));
-    const int cands[2] = {forced ? forced : 32, 8};
-    const int ncand = forced ? 1 : 2;
-    DevBuf ordb[2], tmp;
-    int32_t warps[2][2] = {{0, 0}, {0, 0}};
+    const int all_cs[3] = {32, 8, 8}, all_cpw[3] = {1, 1, 4};
+    const int ncand = forced ? 1 : 3;
+    DevBuf ordb[3], tmp;
+    int32_t warps[3][2] = {}, nord[3][2] = {};
     GK_TRY(tmp.ensure(2 * sizeof(T) * (size_t)n));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     GK_CUDA(cudaEventCreate(&e0));
@@ -348,20 +366,29 @@ static gk_status tune_chunks(gk_matrix A, int32_t n, cudaStream_t s) {
     float best = 0.f;
     int pick = 0;
     for (int k = 0; k < ncand && st == GK_OK; ++k) {
-        const int32_t cs = cands[k], nch = (n + cs - 1) / cs;
-        unsigned wl = 0, wu = 0, ll = 0, lu_ = 0;
-        st = ordb[k].ensure(2 * sizeof(int32_t) * (size_t)nch);
-        if (st == GK_OK) st = chunk_order(A, n, cs, false, (int32_t*)ordb[k].ptr, &wl, &ll, s);
-        if (st == GK_OK)
-            st = chunk_order(A, n, cs, true, (int32_t*)ordb[k].ptr + nch, &wu, &lu_, s);
+        const int32_t cs = forced ? forced : all_cs[k], cpw = forced ? 1 : all_cpw[k];
+        const int32_t nch = (n + cs - 1) / cs;
+        const size_t cap = (size_t)cpw * nch;  // claim-order entries at most, per direction
+        unsigned wl = 0, wu = 0, ll = 0, lu_ = 0, nl = 0, nu = 0;
+        st = ordb[k].ensure(2 * sizeof(int32_t) * cap);
+        int32_t* ob = (int32_t*)ordb[k].ptr;
+        if (st == GK_OK) st = chunk_order(A, n, cs, cpw, false, ob, &wl, &ll, &nl, s);
+        if (st == GK_OK) st = chunk_order(A, n, cs, cpw, true, ob + nl, &wu, &lu_, &nu, s);
         if (st != GK_OK) break;
-        warps[k][0] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, mult * (int64_t)wl), nch);
-        warps[k][1] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, mult * (int64_t)wu), nch);
+        nord[k][0] = (int32_t)nl;
+        nord[k][1] = (int32_t)nu;
+        // warps: a few times the widest level, in warps of cpw chunks
+        warps[k][0] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, mult * (int64_t)wl / cpw), nl / cpw);
+        warps[k][1] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, mult * (int64_t)wu / cpw), nu / cpw);
         if (ncand == 1) break;
         IluDev<T> f = ilu_view<T>(A);
         f.cs = cs;
+        f.cpw = cpw;
         f.nch = nch;
-        f.ord = (const int32_t*)ordb[k].ptr;
+        f.ord_l = ob;
+        f.ord_u = ob + nl;
+        f.nord[0] = nord[k][0];
+        f.nord[1] = nord[k][1];
         f.warps[0] = warps[k][0];
         f.warps[1] = warps[k][1];
         T* w = (T*)tmp.ptr;
@@ -387,13 +414,17 @@ static gk_status tune_chunks(gk_matrix A, int32_t n, cudaStream_t s) {
     GK_CUDA(cudaMemcpyAsync(h, A->ilu_sync, sizeof(h), cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaStreamSynchronize(s));
     if (h[0].err | h[1].err) return GK_ERR_TIMEOUT;
-    const int32_t cs = cands[pick], nch = (n + cs - 1) / cs;
-    GK_CUDA(cudaMemcpyAsync(A->ilu_ord, ordb[pick].ptr, 2 * sizeof(int32_t) * (size_t)nch,
+    const int32_t cs = forced ? forced : all_cs[pick], cpw = forced ? 1 : all_cpw[pick];
+    GK_CUDA(cudaMemcpyAsync(A->ilu_ord, ordb[pick].ptr,
+                            sizeof(int32_t) * ((size_t)nord[pick][0] + nord[pick][1]),
                             cudaMemcpyDeviceToDevice, s));
     GK_CUDA(cudaStreamSynchronize(s));
     A->ilu_cs = cs;
-    A->ilu_warps[0] = warps[pick][0];
-    A->ilu_warps[1] = warps[pick][1];
+    A->ilu_cpw = cpw;
+    A->ilu_nord[0] = nord[pick][0];
+    A->ilu_nord[1] = nord[pick][1];
+    A->ilu_warps[0] = std::max(1, warps[pick][0]);
+    A->ilu_warps[1] = std::max(1, warps[pick][1]);
     return GK_OK;
 }
 
@@ -407,8 +438,8 @@ static gk_status ilu_build(gk_matrix A, gk_matrix C, cudaStream_t s) {
     GK_CUDA(dmalloc(&A->ilu_lu, vb * (size_t)std::max<int64_t>(nnz, 1)));
     GK_CUDA(dmalloc(&A->ilu_rdiag, vb * (size_t)std::max(n, 1)));
     GK_CUDA(dmalloc(&A->ilu_sync, ilu_sync_bytes()));
-    // claim orders for chunks of 8 rows at most (the smallest chunk size)
-    GK_CUDA(dmalloc_t(&A->ilu_ord, 2 * (size_t)std::max((n + 7) / 8, 1)));
+    // claim orders: at most 4 entries per 8-row chunk and direction
+    GK_CUDA(dmalloc_t(&A->ilu_ord, 2 * 4 * (size_t)std::max((n + 7) / 8, 1)));
     GK_CUDA(cudaMemcpyAsync(A->ilu_rp, C->row_ptr, sizeof(int32_t) * ((size_t)n + 1),
                             cudaMemcpyDeviceToDevice, s));
     if (nnz > 0)
@@ -444,8 +475,8 @@ static gk_status ilu_build(gk_matrix A, gk_matrix C, cudaStream_t s) {
         // the factorisation claims rows chunk by chunk in the L level order
         // of 32-row chunks
         const int32_t cs = 32, nch = (n + cs - 1) / cs;
-        unsigned wl = 0, ll = 0;
-        GK_TRY(chunk_order(A, n, cs, false, A->ilu_ord, &wl, &ll, s));
+        unsigned wl = 0, ll = 0, nl = 0;
+        GK_TRY(chunk_order(A, n, cs, 1, false, A->ilu_ord, &wl, &ll, &nl, s));
         k_ilu_factor<<<resident_grid(k_ilu_factor,
                                      std::min<int64_t>(n, 2 * (int64_t)cs * wl + 256)),
                        256, 0, s>>>(n, nch, cs, A->ilu_rp, A->ilu_ci, A->ilu_dpos, A->ilu_ord,

@@ -11,11 +11,15 @@
 // Substitution is a dependency problem: row i of L^-1 r needs every y_j
 // with l_ij != 0.  The kernel is sync-free (no level-by-level launches, one
 // launch per triangle):
-//  - Rows are cut into chunks of cs consecutive rows (cs = 32 or 8, timed
-//    per matrix at setup: shorter chunks shorten the serial chain inside a
-//    chunk, longer ones cut the number of dependency levels when rows
-//    depend on their neighbours); one warp solves one chunk, one lane per
-//    row.  Warps claim chunks from an atomic counter in
+//  - Rows are cut into chunks of cs consecutive rows (cs = 32, 16 or 8,
+//    timed per matrix at setup: shorter chunks shorten the serial chain
+//    inside a chunk, longer ones cut the number of dependency levels when
+//    rows depend on their neighbours); a warp solves cpw chunks at once
+//    (cpw = 1, or 32 / cs to fill the warp, also timed), a group of cs lanes
+//    per chunk and one lane per row.  A warp always takes chunks of one
+//    level (each level's run in the claim order is padded to a multiple of
+//    cpw with empty entries), so the chunks sharing a warp never depend on
+//    one another.  Warps claim chunks from an atomic counter in
 //    a topological order of the chunk dependency graph (by level: a
 //    chunk's level is one more than the highest level it depends on,
 //    computed once per matrix), so a chunk only ever waits on chunks
@@ -32,7 +36,8 @@
 //  - A lane first subtracts its row's terms outside the chunk, in the
 //    order the substitution produced them (L: ascending columns; U:
 //    descending).  The terms inside the chunk are resolved by a 32-step
-//    warp loop (cs steps): at step t lane t's value is final and is broadcast with a
+//    warp loop (cs steps, every group in step): at step t the group's lane
+//    t's value is final and is broadcast with a
 //    shuffle; lanes whose row uses column c0 + t subtract it.  Together this
 //    subtracts every term in exactly the sequential order.
 //  - The last warp to leave the kernel resets the claim counter for the
@@ -68,12 +73,15 @@ template <typename T>
 struct IluDev {
     int32_t n = 0, nch = 0;
     int32_t cs = 32;                // rows per chunk (8, 16 or 32)
+    int32_t cpw = 1;                // chunks per warp (1 .. 32 / cs)
     const int32_t* rp = nullptr;    // row_ptr[n + 1]
     const int32_t* ci = nullptr;    // col[nnz], strictly ascending per row
     const int32_t* dpos = nullptr;  // position of a_ii in row i
     const T* lu = nullptr;          // factors in CSR order
     const T* rdiag = nullptr;       // 1 / u_ii, rounded once
-    const int32_t* ord = nullptr;   // [2 * nch]: chunks in claim order, L then U
+    const int32_t* ord_l = nullptr;  // chunks in claim order (-1: empty), L
+    const int32_t* ord_u = nullptr;  // and U; nord entries each, multiples of 32 / cs
+    int32_t nord[2] = {0, 0};
     TrsvSync* sy = nullptr;         // [2]
     unsigned pause_max = 64;        // longest pause between polls (ns)
     int32_t warps[2] = {0, 0};      // host: warps per substitution launch
@@ -225,21 +233,25 @@ k_ilu_trsv(IluDev<T> f, Src src, Out out, Skip sk, Err on_err) {
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int G = 4;  // out-of-chunk values loaded together
     const int lane = threadIdx.x & 31;
+    const int cs = f.cs, cpw = f.cpw;
+    const int grp = lane / cs, gl = lane - grp * cs;  // chunk slot, row in the chunk
     TrsvSync* sy = f.sy + (UP ? 1 : 0);
+    const int32_t* ord = UP ? f.ord_u : f.ord_l;
+    const int nord = f.nord[UP ? 1 : 0];
     const unsigned total = gridDim.x * (blockDim.x >> 5);
     if (!sk.skip()) {
         const T* in = src.ptr();
         T* dst = out.dst();
         for (;;) {
             int c = 0;
-            if (lane == 0) c = (int)atomicAdd(&sy->ctr, 1u);
+            if (lane == 0) c = (int)atomicAdd(&sy->ctr, (unsigned)cpw);
             c = __shfl_sync(FULL, c, 0);
-            if (c >= f.nch) break;
-            const int cc = f.ord[(UP ? f.nch : 0) + c];
-            const int32_t c0 = cc * f.cs;
-            const int32_t c1 = min(c0 + f.cs, f.n);
-            const int32_t i = c0 + lane;
-            const bool has = lane < f.cs && i < f.n;
+            if (c >= nord) break;
+            const int cc = grp < cpw ? ord[c + grp] : -1;  // -1: no chunk for this group
+            const int32_t c0 = cc * cs;
+            const int32_t c1 = cc >= 0 ? min(c0 + cs, f.n) : c0;
+            const int32_t i = c0 + gl;
+            const bool has = cc >= 0 && i < f.n;
             T acc = T(0);
             int32_t pin = 0, pend = 0;  // in-chunk entries [pin, pend)
             if (has) {
@@ -286,15 +298,15 @@ k_ilu_trsv(IluDev<T> f, Src src, Out out, Skip sk, Err on_err) {
                     pend = k + 1;
                 }
             }
-            const int m = c1 - c0;
+            const int base = grp * cs;  // the group's first lane
             T mine = T(0);
             if (!UP) {
                 // lane t's value is final at step t; later lanes subtract it
                 int32_t col = pin < pend ? f.ci[pin] : INT32_MAX;
                 T lv = pin < pend ? f.lu[pin] : T(0);
-                for (int t = 0; t < m; ++t) {
-                    const T yt = __shfl_sync(FULL, acc, t);
-                    if (lane == t) mine = yt;
+                for (int t = 0; t < cs; ++t) {
+                    const T yt = __shfl_sync(FULL, acc, base + t);
+                    if (gl == t) mine = yt;
                     if (col == c0 + t) {  // only lanes > t hold column c0 + t
                         acc = sub_mul(acc, lv, yt);
                         ++pin;
@@ -304,17 +316,17 @@ k_ilu_trsv(IluDev<T> f, Src src, Out out, Skip sk, Err on_err) {
                 }
             } else {
                 const T rd = has ? f.rdiag[i] : T(1);
-                int32_t col = pend > pin ? f.ci[pend - 1] : -1;
+                int32_t col = pend > pin ? f.ci[pend - 1] : INT32_MIN;
                 T uv = pend > pin ? f.lu[pend - 1] : T(0);
-                for (int t = m - 1; t >= 0; --t) {
+                for (int t = cs - 1; t >= 0; --t) {
                     T v = T(0);
-                    if (lane == t) v = mul_rn(acc, rd);
-                    const T zt = __shfl_sync(FULL, v, t);
-                    if (lane == t) mine = zt;
+                    if (gl == t) v = mul_rn(acc, rd);
+                    const T zt = __shfl_sync(FULL, v, base + t);
+                    if (gl == t) mine = zt;
                     if (col == c0 + t) {  // only lanes < t hold column c0 + t
                         acc = sub_mul(acc, uv, zt);
                         --pend;
-                        col = pend > pin ? f.ci[pend - 1] : -1;
+                        col = pend > pin ? f.ci[pend - 1] : INT32_MIN;
                         uv = pend > pin ? f.lu[pend - 1] : T(0);
                     }
                 }
