@@ -11,16 +11,16 @@
 //     row i, for every stored k < i in ascending order, l_ik = a_ik / u_kk,
 //     then a_ij -= l_ik u_kj for every stored j > k of row k that row i
 //     also stores) runs sync-free: one warp per row, rows claimed chunk by
-//     chunk in the L claim order and in ascending order inside a chunk (a
-//     topological order), so a row only waits (bounded) on rows claimed
-//     before it.
+//     chunk in the L claim order of 32-row chunks and in ascending order
+//     inside a chunk (a topological order), so a row only waits (bounded) on
+//     rows claimed before it.  Row i waits for row k to be final before it
+//     reads u_kk and row k's upper part; the lanes then update row i's
+//     entries for row k's columns in parallel (each entry is hit at most
+//     once per k, and the k steps run in ascending order), so every entry
+//     sees exactly the oracle's sequence of roundings.  Products and
+//     differences are rounded separately, no fused multiply-add.
 //  4. k_ilu_store: factors rounded to the vector type, 1 / u_ii.
-//  5. tune_chunks: the substitutions' chunk size (32 or 8 rows), timed.  Row i waits for row
-// k to be final before it reads u_kk and row k's upper part; the lanes then
-// update row i's entries for row k's columns in parallel (each entry is hit
-// at most once per k, and the k steps run in ascending order), so every
-// entry sees exactly the oracle's sequence of roundings.  Products and
-// differences are rounded separately, no fused multiply-add.
+//  5. tune_chunks: the substitutions' chunk size and chunks per warp, timed.
 //
 // The factors are computed in double from the stored values and rounded
 // once to the vector type (double for GK_F64, float otherwise).
@@ -267,8 +267,6 @@ static unsigned resident_grid(K kernel, int64_t items) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * b));
 }
 
-// Levels of the L (up = false) or U chunk graph, the claim order sorted by
-// level into ord[0, nch), and the widest level in *maxw (host).
 // Levels of the L (up = false) or U graph of cs-row chunks, the claim order
 // sorted by level into ord (each level's run padded to a multiple of pad with
 // -1; at most pad * nch entries), its length (*nord), the widest padded
