@@ -55,6 +55,21 @@ def _peaks():
     return FALLBACK_HBM, "fallback"
 
 
+def job_throughput(local_ms, step_bytes, steps, world, device="cpu"):
+    """Whole-job GB/s of `world` replicas that each ran `steps` steps of
+    `step_bytes` algorithmic bytes: the job's time is the slowest rank's
+    (an all_reduce MAX over the default process group when world > 1).
+    Returns (job ms, GB/s)."""
+    total_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, step_bytes * steps * world / (total_ms / 1000.0) / 1e9
+
+
 def alg_bytes(m, sv, fmt):
     """Algorithmic bytes of one SpMV: unpadded matrix, x and y once."""
     b = m.nnz * (sv + 4) + m.n * sv + m.ncols * sv
@@ -687,15 +702,11 @@ def main():
     total_ms = t_start.elapsed_time(t_end)
     per_item_ms = [statistics.mean(evs[s_][k][0].elapsed_time(evs[s_][k][1])
                                    for s_ in range(args.steps)) for k in range(len(step_items))]
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     # the step counts every matrix at its CSR algorithmic bytes, whatever
     # format ran, so a format that moves more (COO's row indices) or less
     # (ELL's missing row pointer) does not change the yardstick
     step_bytes = sum(it["csr_bytes"] for it in step_items)
-    value = step_bytes * args.steps * world / (total_ms / 1000.0) / 1e9
+    total_ms, value = job_throughput(total_ms, step_bytes, args.steps, world, dev)
     peak, peak_kind = _peaks()
 
     # every format, for the record (not part of the timed step)
@@ -748,15 +759,18 @@ def main():
 
     e2e_step()
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     pool.shutdown()
+    _, e2e_gbs = job_throughput(e2e_s * 1000.0, step_bytes, args.steps, world, dev)
     h2d = sum(a.numel() * a.element_size() for a in hx)
     d2h = sum(b.numel() * b.element_size() for b in hy)
-    e2e = {"value": round(step_bytes * args.steps * world / e2e_s / 1e9, 1), "unit": "GB/s",
+    e2e = {"value": round(e2e_gbs, 1), "unit": "GB/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "how": "gk_apply with pinned host x and y (library-staged copies), one host thread "
                   "and CUDA stream per matrix, host wall clock"}
