@@ -303,3 +303,45 @@ def test_input_holding_the_unsolved_marker_is_a_plain_nan():
     want = oracle.ilu0_apply(m, oracle.ilu0(m), r2)
     assert np.array_equal(zt.cpu().numpy().view(np.uint64), want.view(np.uint64))
     A.close()
+
+
+def _power_law_with_diagonal(n, seed):
+    """Zipf(1.8) power-law rows (uniform random columns, up to 4096 long)
+    with a dominant diagonal merged into each row, columns ascending."""
+    m = W.power_law(n, seed=seed)
+    rows = np.repeat(np.arange(n), m.row_lengths())
+    keep = m.col_idx != rows
+    r, c, v = rows[keep], m.col_idx[keep], m.values[keep]
+    absum = np.bincount(r, weights=np.abs(v), minlength=n)
+    r = np.concatenate([r, np.arange(n)])
+    c = np.concatenate([c, np.arange(n)])
+    v = np.concatenate([v, absum + 1.0])
+    order = np.lexsort((c, r))
+    r, c, v = r[order], c[order], v[order]
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(r, minlength=n), out=rp[1:])
+    return W.CSR(n, n, rp, c, v)
+
+
+def test_power_law_hub_rows_bit_exact():
+    """Irregular dependencies: hub rows thousands of entries long, random
+    columns (shallow, wide dependency levels)."""
+    import torch
+    dev = torch_dev()
+    m = _power_law_with_diagonal(1 << 15, W.SEED_BASE + 7)
+    assert m.row_lengths().max() >= 1000
+    A = gk.Matrix.from_csr(m, "f64")
+    lu = oracle.ilu0(m)
+    assert np.array_equal(A.ilu_factors().view(np.uint64), lu.view(np.uint64))
+    r = W.uniform_vector(m.n, 21)
+    rt = torch.from_numpy(r).to(dev)
+    zt = torch.empty_like(rt)
+    A.precond_apply(rt, zt, "ilu")
+    torch.cuda.synchronize()
+    want = oracle.ilu0_apply(m, lu, r)
+    assert np.array_equal(zt.cpu().numpy().view(np.uint64), want.view(np.uint64))
+    xt = torch.zeros_like(rt)
+    info = A.solve(rt, xt, method="bicgstab", precond="ilu", tol=1e-10, max_iters=500)
+    assert info["return"] == gk.GK_OK, info
+    assert oracle.true_rel_residual(m, r, xt.cpu().numpy()) <= 1e-10
+    A.close()
