@@ -26,7 +26,8 @@
  *
  * Every floating-point operation is IEEE double with no contraction
  * (compile with -ffp-contract=off) so that results are identical on x86
- * and Arm hosts.
+ * and Arm hosts; the explicit fma() calls of ILU(0) are correctly rounded
+ * fused multiply-adds on both.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -430,7 +431,8 @@ void or_block_jacobi_apply(int32_t n, int32_t bs, const double* binv, const doub
  * the ILU(0) algorithm): for each row i in order, for each stored k < i in
  * ascending order, a_ik /= a_kk and then a_ij -= a_ik * a_kj for every
  * stored j > k of row k that is also stored in row i.  Entries outside the
- * pattern are dropped.  lu[] (nnz) receives L's strictly lower part (unit
+ * pattern are dropped.  Each update a - l * u is one fused multiply-add
+ * (C99 fma: the exact value rounded once).  lu[] (nnz) receives L's strictly lower part (unit
  * diagonal implied) and U (diagonal and above) in A's CSR order.
  * Rows need their columns strictly ascending (no duplicates): otherwise
  * OR_ERR_INVALID.  A row without a stored diagonal, or a zero pivot u_ii,
@@ -459,7 +461,7 @@ int or_ilu0(int32_t n, const int32_t* rp, const int32_t* ci, const double* va, d
                 const int32_t j = ci[q];
                 for (int32_t t = p + 1; t < rp[i + 1]; ++t)
                     if (ci[t] == j) {
-                        lu[t] = lu[t] - lu[p] * lu[q];
+                        lu[t] = fma(-lu[p], lu[q], lu[t]);
                         break;
                     }
             }
@@ -474,8 +476,9 @@ int or_ilu0(int32_t n, const int32_t* rp, const int32_t* ci, const double* va, d
  * subtracted in ascending column order; back substitution in descending
  * row order, z_i = (y_i - sum_{j>i} u_ij z_j) * (1 / u_ii) with the terms
  * subtracted in descending column order (each unknown is used in the order
- * the substitution produced it).  The paper does not fix the arithmetic of
- * the substitution; this reading scales by the pivot's reciprocal, rounded
+ * the substitution produced it), each subtraction of a product one fused
+ * multiply-add (fma).  The paper does not fix the arithmetic of the
+ * substitution; this reading scales by the pivot's reciprocal, rounded
  * once, as a preconditioner that stores inverted pivots does. */
 void or_ilu0_apply(int32_t n, const int32_t* rp, const int32_t* ci, const double* lu,
                    const double* r, double* z)
@@ -483,13 +486,13 @@ void or_ilu0_apply(int32_t n, const int32_t* rp, const int32_t* ci, const double
     double* y = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     for (int32_t i = 0; i < n; ++i) {
         double s = r[i];
-        for (int32_t p = rp[i]; p < rp[i + 1] && ci[p] < i; ++p) s = s - lu[p] * y[ci[p]];
+        for (int32_t p = rp[i]; p < rp[i + 1] && ci[p] < i; ++p) s = fma(-lu[p], y[ci[p]], s);
         y[i] = s;
     }
     for (int32_t i = n - 1; i >= 0; --i) {
         const int32_t d = diag_pos(rp, ci, i);
         double s = y[i];
-        for (int32_t p = rp[i + 1] - 1; p > d; --p) s = s - lu[p] * z[ci[p]];
+        for (int32_t p = rp[i + 1] - 1; p > d; --p) s = fma(-lu[p], z[ci[p]], s);
         const double rd = 1.0 / lu[d];
         z[i] = s * rd;
     }
