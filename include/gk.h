@@ -75,9 +75,9 @@ typedef enum { GK_CG = 0, GK_BICGSTAB = 1, GK_GMRES = 2, GK_CGS = 3 } gk_method;
  * consecutive rows (max_block_size > 1; each block inverted by Gauss-Jordan
  * with partial pivoting, a singular block is GK_ERR_ZERO_DIAG), and
  * ILU(0), the Ilu preconditioner of Listing 1: incomplete LU without
- * fill-in (A's pattern; the IKJ form, products and differences rounded
- * separately) applied as z = U^-1 (L^-1 r) by exact forward and backward
- * substitution.  ILU(0) needs every row's columns strictly ascending (what
+ * fill-in (A's pattern; the IKJ form, each update one fused
+ * multiply-add) applied as z = U^-1 (L^-1 r) by exact forward and backward
+ * substitution (the pivots applied as reciprocals rounded once).  ILU(0) needs every row's columns strictly ascending (what
  * gk_matrix_create_coo and the conversions produce; otherwise
  * GK_ERR_INVALID) and a stored diagonal with nonzero pivots (otherwise
  * GK_ERR_ZERO_DIAG).  For a symmetric matrix its U equals D L^T in exact

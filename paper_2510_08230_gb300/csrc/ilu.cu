@@ -17,8 +17,8 @@
 //     reads u_kk and row k's upper part; the lanes then update row i's
 //     entries for row k's columns in parallel (each entry is hit at most
 //     once per k, and the k steps run in ascending order), so every entry
-//     sees exactly the oracle's sequence of roundings.  Products and
-//     differences are rounded separately, no fused multiply-add.
+//     sees exactly the oracle's sequence of roundings.  Each update
+//     a_ij - l_ik u_kj is one fused multiply-add.
 //  4. k_ilu_store: factors rounded to the vector type, 1 / u_ii.
 //  5. tune_chunks: the substitutions' chunk size and chunks per warp, timed.
 //
@@ -215,7 +215,7 @@ k_ilu_factor(int32_t n, int32_t nch, int32_t cs, const int32_t* __restrict__ rp,
                     else hi = mid;
                 }
                 if (lo < p1 && ci[lo] == j)
-                    fac[lo] = __dsub_rn(__ldcg(fac + lo), __dmul_rn(l, __ldcg(fac + q)));
+                    fac[lo] = __fma_rn(-l, __ldcg(fac + q), __ldcg(fac + lo));
             }
             if (lane == 0) fac[pk] = l;
             __threadfence_block();

@@ -46,11 +46,10 @@
 //    runs out records an error flag, later waits of the launch give up at
 //    once, and the kernel finishes with wrong values instead of hanging.
 //    The solver engine turns the flag into GK_ERR_TIMEOUT.
-// Products and differences are rounded separately (no fused multiply-add)
-// and U's pivots are applied as stored reciprocals (1 / u_ii rounded once,
-// a multiplication instead of a division on the in-chunk chain), so that
-// FP64 results equal the plain substitution with those reciprocals bit
-// for bit.
+// Every subtraction of a product is one fused multiply-add, and U's pivots
+// are applied as stored reciprocals (1 / u_ii rounded once, a
+// multiplication instead of a division on the in-chunk chain), so that FP64
+// results equal the plain substitution with that arithmetic bit for bit.
 #pragma once
 
 #include "gk_internal.cuh"
@@ -174,12 +173,12 @@ __device__ __forceinline__ T wait_value(const T* p, T v, unsigned* err, unsigned
     }
 }
 
-// a - l * y with the product rounded before the subtraction
+// a - l * y as one fused multiply-add (rounded once)
 __device__ __forceinline__ double sub_mul(double a, double l, double y) {
-    return __dsub_rn(a, __dmul_rn(l, y));
+    return __fma_rn(-l, y, a);
 }
 __device__ __forceinline__ float sub_mul(float a, float l, float y) {
-    return __fsub_rn(a, __fmul_rn(l, y));
+    return __fmaf_rn(-l, y, a);
 }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
