@@ -345,3 +345,26 @@ def test_power_law_hub_rows_bit_exact():
     assert info["return"] == gk.GK_OK, info
     assert oracle.true_rel_residual(m, r, xt.cpu().numpy()) <= 1e-10
     A.close()
+
+
+@pytest.mark.parametrize("low", ["bf16", "f16"])
+def test_low_precision_storage_equals_fp32_of_the_rounded_values(low):
+    """A BF16- or FP16-stored handle factors its stored values in double and
+    rounds the factors to float, exactly as an FP32 handle holding the same
+    (exactly representable) values: factors and applications bit-identical."""
+    import torch
+    dev = torch_dev()
+    m = W.convection_diffusion_2d(50, 1.5)
+    L = _matrix(m, low)
+    F = gk.Matrix.from_csr(W.CSR(m.n, m.ncols, m.row_ptr, m.col_idx,
+                                 rounded_values(m, low).astype(np.float32)), "f32")
+    assert np.array_equal(L.ilu_factors().view(np.uint32), F.ilu_factors().view(np.uint32))
+    r = torch.from_numpy(W.uniform_vector(m.n, 8)).to(dev, torch.float32)
+    z1 = torch.empty_like(r)
+    z2 = torch.empty_like(r)
+    L.precond_apply(r, z1, "ilu")
+    F.precond_apply(r, z2, "ilu")
+    torch.cuda.synchronize()
+    assert torch.equal(z1, z2)
+    L.close()
+    F.close()
