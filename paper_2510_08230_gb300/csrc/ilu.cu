@@ -267,20 +267,15 @@ static unsigned resident_grid(K kernel, int64_t items) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * b));
 }
 
-// Levels of the L (up = false) or U graph of cs-row chunks, the claim order
-// sorted by level into ord (each level's run padded to a multiple of pad with
-// -1; at most pad * nch entries), its length (*nord), the widest padded
-// level (*maxw) and the number of levels (*nlev).
-static gk_status chunk_order(gk_matrix A, int32_t n, int32_t cs, int32_t pad, bool up,
-                             int32_t* ord, unsigned* maxw, unsigned* nlev, unsigned* nord,
-                             cudaStream_t s) {
+// Dependency levels of the L (up = false) or U graph of cs-row chunks into
+// lev (nch entries); *nlev = the number of levels.
+static gk_status chunk_levels(gk_matrix A, int32_t n, int32_t cs, bool up, DevBuf& lev,
+                              unsigned* nlev, cudaStream_t s) {
     const int32_t nch = (n + cs - 1) / cs;
-    DevBuf lev, cnt, misc;
+    DevBuf misc;
     GK_TRY(lev.ensure(sizeof(unsigned) * (size_t)nch));
-    GK_TRY(cnt.ensure(sizeof(unsigned) * ((size_t)nch + 2)));
     GK_TRY(misc.ensure(64));
     GK_CUDA(cudaMemsetAsync(lev.ptr, 0, sizeof(unsigned) * (size_t)nch, s));
-    GK_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(unsigned) * ((size_t)nch + 2), s));
     GK_CUDA(cudaMemsetAsync(misc.ptr, 0, 64, s));
     unsigned* mp = (unsigned*)misc.ptr;
     if (up)
@@ -289,23 +284,50 @@ static gk_status chunk_order(gk_matrix A, int32_t n, int32_t cs, int32_t pad, bo
     else
         k_chunk_levels<false><<<resident_grid(k_chunk_levels<false>, nch), 256, 0, s>>>(
             n, nch, cs, A->ilu_rp, A->ilu_ci, A->ilu_dpos, (unsigned*)lev.ptr, mp);
+    GK_CUDA(cudaGetLastError());
+    unsigned h[4] = {0, 0, 0, 0};
+    GK_CUDA(cudaMemcpyAsync(h, mp, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    if (h[1]) return GK_ERR_TIMEOUT;
+    *nlev = h[3];
+    return GK_OK;
+}
+
+// The claim order of nch chunks with levels lev: sorted by level into ord,
+// each level's run padded to a multiple of pad with -1 (at most pad * nch
+// entries); *nord = its length, *maxw = the widest padded level.
+static gk_status level_order(int32_t nch, int32_t pad, const DevBuf& lev, int32_t* ord,
+                             unsigned* maxw, unsigned* nord, cudaStream_t s) {
+    DevBuf cnt, misc;
+    GK_TRY(cnt.ensure(sizeof(unsigned) * ((size_t)nch + 2)));
+    GK_TRY(misc.ensure(64));
+    GK_CUDA(cudaMemsetAsync(cnt.ptr, 0, sizeof(unsigned) * ((size_t)nch + 2), s));
+    GK_CUDA(cudaMemsetAsync(misc.ptr, 0, 64, s));
+    unsigned* mp = (unsigned*)misc.ptr;
     const unsigned g = ew_grid(nch);
     k_level_hist<<<g, 256, 0, s>>>(nch, (const unsigned*)lev.ptr, (unsigned*)cnt.ptr);
     k_level_scan<<<1, 1024, 0, s>>>(nch + 2, pad, (unsigned*)cnt.ptr, mp + 2, mp + 4);
-    if (ord) {
-        GK_CUDA(cudaMemsetAsync(ord, 0xFF, sizeof(int32_t) * (size_t)pad * nch, s));
-        k_level_scatter<<<g, 256, 0, s>>>(nch, (const unsigned*)lev.ptr, (unsigned*)cnt.ptr, ord);
-    }
+    GK_CUDA(cudaMemsetAsync(ord, 0xFF, sizeof(int32_t) * (size_t)pad * nch, s));
+    k_level_scatter<<<g, 256, 0, s>>>(nch, (const unsigned*)lev.ptr, (unsigned*)cnt.ptr, ord);
     GK_CUDA(cudaGetLastError());
     unsigned h[5] = {0, 0, 0, 0, 0};
     GK_CUDA(cudaMemcpyAsync(h, mp, sizeof(h), cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaStreamSynchronize(s));
-    if (h[1]) return GK_ERR_TIMEOUT;
     *maxw = h[2];
-    *nlev = h[3];
     *nord = h[4];
     return GK_OK;
 }
+
+// Chunk levels of both triangles for the two chunk sizes (32 and 8 rows),
+// computed once per matrix and shared by the factorisation order and every
+// substitution candidate.
+struct IluLevels {
+    DevBuf l32, u32, l8, u8;
+    unsigned nl32 = 0, nu32 = 0, nl8 = 0, nu8 = 0;
+    const DevBuf& get(int cs, bool up) const {
+        return cs == 32 ? (up ? u32 : l32) : (up ? u8 : l8);
+    }
+};
 
 template <typename T>
 IluDev<T> ilu_view(gk_matrix A) {
@@ -340,15 +362,15 @@ template IluDev<float> ilu_view<float>(gk_matrix);
 // four 8-row chunks a warp; the 2D 5-point Laplacian 1024^2 17.4 ms, 10.4
 // with one 8-row chunk a warp, 12.5 with four).  Each candidate gets its
 // claim orders, grid caps and one timed application (after a warm-up one)
-// of z = M^-1 d with d = 1/u_ii; the fastest is kept.  GK_ILU_CHUNK (8, 16
-// or 32, one chunk a warp) forces a size.  Results never depend on the
+// of z = M^-1 d with d = 1/u_ii; the fastest is kept.  GK_ILU_CHUNK (8 or
+// 32, one chunk a warp) forces a size.  Results never depend on the
 // choice, only the time does.
 template <typename T>
-static gk_status tune_chunks(gk_matrix A, int32_t n, cudaStream_t s) {
+static gk_status tune_chunks(gk_matrix A, int32_t n, const IluLevels& lv, cudaStream_t s) {
     int forced = 0;
     if (const char* e = getenv("GK_ILU_CHUNK")) {
         const int v = atoi(e);
-        if (v == 8 || v == 16 || v == 32) forced = v;
+        if (v == 8 || v == 32) forced = v;
     }
     int64_t mult = 2;
     if (const char* e = getenv("GK_ILU_WARPS")) mult = std::max(1, atoi(e));
@@ -367,11 +389,11 @@ static gk_status tune_chunks(gk_matrix A, int32_t n, cudaStream_t s) {
         const int32_t cs = forced ? forced : all_cs[k], cpw = forced ? 1 : all_cpw[k];
         const int32_t nch = (n + cs - 1) / cs;
         const size_t cap = (size_t)cpw * nch;  // claim-order entries at most, per direction
-        unsigned wl = 0, wu = 0, ll = 0, lu_ = 0, nl = 0, nu = 0;
+        unsigned wl = 0, wu = 0, nl = 0, nu = 0;
         st = ordb[k].ensure(2 * sizeof(int32_t) * cap);
         int32_t* ob = (int32_t*)ordb[k].ptr;
-        if (st == GK_OK) st = chunk_order(A, n, cs, cpw, false, ob, &wl, &ll, &nl, s);
-        if (st == GK_OK) st = chunk_order(A, n, cs, cpw, true, ob + nl, &wu, &lu_, &nu, s);
+        if (st == GK_OK) st = level_order(nch, cpw, lv.get(cs, false), ob, &wl, &nl, s);
+        if (st == GK_OK) st = level_order(nch, cpw, lv.get(cs, true), ob + nl, &wu, &nu, s);
         if (st != GK_OK) break;
         nord[k][0] = (int32_t)nl;
         nord[k][1] = (int32_t)nu;
@@ -472,9 +494,14 @@ static gk_status ilu_build(gk_matrix A, gk_matrix C, cudaStream_t s) {
         if (h[3] & 2u) return GK_ERR_ZERO_DIAG;
         // the factorisation claims rows chunk by chunk in the L level order
         // of 32-row chunks
+        IluLevels lv;
+        GK_TRY(chunk_levels(A, n, 32, false, lv.l32, &lv.nl32, s));
+        GK_TRY(chunk_levels(A, n, 32, true, lv.u32, &lv.nu32, s));
+        GK_TRY(chunk_levels(A, n, 8, false, lv.l8, &lv.nl8, s));
+        GK_TRY(chunk_levels(A, n, 8, true, lv.u8, &lv.nu8, s));
         const int32_t cs = 32, nch = (n + cs - 1) / cs;
-        unsigned wl = 0, ll = 0, nl = 0;
-        GK_TRY(chunk_order(A, n, cs, 1, false, A->ilu_ord, &wl, &ll, &nl, s));
+        unsigned wl = 0, nl = 0;
+        GK_TRY(level_order(nch, 1, lv.l32, A->ilu_ord, &wl, &nl, s));
         k_ilu_factor<<<resident_grid(k_ilu_factor,
                                      std::min<int64_t>(n, 2 * (int64_t)cs * wl + 256)),
                        256, 0, s>>>(n, nch, cs, A->ilu_rp, A->ilu_ci, A->ilu_dpos, A->ilu_ord,
@@ -493,7 +520,8 @@ static gk_status ilu_build(gk_matrix A, gk_matrix C, cudaStream_t s) {
                                                             A->ilu_dpos, (float*)A->ilu_lu,
                                                             (float*)A->ilu_rdiag);
         GK_CUDA(cudaGetLastError());
-        GK_TRY(A->dtype == GK_F64 ? tune_chunks<double>(A, n, s) : tune_chunks<float>(A, n, s));
+        GK_TRY(A->dtype == GK_F64 ? tune_chunks<double>(A, n, lv, s)
+                                  : tune_chunks<float>(A, n, lv, s));
     }
     GK_CUDA(cudaStreamSynchronize(s));
     return GK_OK;
