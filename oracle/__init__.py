@@ -100,6 +100,8 @@ def _declare(L):
     L.or_ilu0.restype = ctypes.c_int
     L.or_ilu0_apply.argtypes = [i32, _i32p, _i32p, _f64p, _f64p, _f64p]
     L.or_ilu0_apply.restype = None
+    L.or_trsv.argtypes = [i32, _i32p, _i32p, _f64p, ctypes.c_int, ctypes.c_int, _f64p, _f64p]
+    L.or_trsv.restype = ctypes.c_int
     for name in ("or_cg", "or_bicgstab", "or_gmres", "or_cgs"):
         f = getattr(L, name)
         f.argtypes = [i32, _i32p, _i32p, _f64p, _f64p, _f64p, ctypes.POINTER(Opts),
@@ -262,6 +264,21 @@ def ilu0_apply(m, lu, r):
     lib().or_ilu0_apply(m.n, _i32(m.row_ptr), _i32(m.col_idx),
                         _f64(lu) if np.asarray(lu).size else np.zeros(1), _f64(r), z)
     return z[:m.n]
+
+
+def trsv(m, b, upper=False, unit=False):
+    """x with T x = b for the lower (or upper) triangle of m including its
+    diagonal (unit: diagonal taken as 1).  Raises ValueError for unsorted
+    columns or a missing diagonal, ZeroDivisionError for a zero diagonal."""
+    x = np.zeros(max(m.n, 1))
+    st = lib().or_trsv(m.n, _i32(m.row_ptr), _i32(m.col_idx),
+                       _f64(m.values) if m.nnz else np.zeros(1), int(upper), int(unit),
+                       _f64(b) if m.n else np.zeros(1), x)
+    if st == ERR_INVALID:
+        raise ValueError("triangular solve needs ascending columns and a stored diagonal")
+    if st != OK:
+        raise ZeroDivisionError("zero diagonal")
+    return x[:m.n]
 
 
 def solve(m, b, x0=None, method=CG, precond=0, tol=1e-10, max_iters=1000,

@@ -499,6 +499,43 @@ void or_ilu0_apply(int32_t n, const int32_t* rp, const int32_t* ci, const double
     free(y);
 }
 
+/* Sparse triangular solve with A's own lower (upper = 0) or upper triangle
+ * (the triangular solvers pyGinkgo binds beside ILU and IC, Section 5):
+ * T x = b by forward (lower) or back (upper) substitution, entries of the
+ * other triangle ignored.  Row i's terms are subtracted in the order the
+ * substitution produced the unknowns (lower: ascending columns, upper:
+ * descending), each as one fused multiply-add, then scaled by the rounded
+ * reciprocal 1 / a_ii (unit = 0) or taken as is (unit = 1: unit diagonal,
+ * the stored diagonal ignored), the same arithmetic as or_ilu0_apply.
+ * Every row must store its diagonal and have strictly ascending columns
+ * (else OR_ERR_INVALID); unit = 0 with a zero diagonal is OR_ERR_ZERO_DIAG. */
+int or_trsv(int32_t n, const int32_t* rp, const int32_t* ci, const double* va, int upper,
+            int unit, const double* b, double* x)
+{
+    for (int32_t i = 0; i < n; ++i) {
+        for (int32_t p = rp[i] + 1; p < rp[i + 1]; ++p)
+            if (ci[p] <= ci[p - 1]) return OR_ERR_INVALID;
+        const int32_t d = diag_pos(rp, ci, i);
+        if (d < 0) return OR_ERR_INVALID;
+        if (!unit && va[d] == 0.0) return OR_ERR_ZERO_DIAG;
+    }
+    for (int32_t t = 0; t < n; ++t) {
+        const int32_t i = upper ? n - 1 - t : t;
+        const int32_t d = diag_pos(rp, ci, i);
+        double s = b[i];
+        if (!upper)
+            for (int32_t p = rp[i]; p < d; ++p) s = fma(-va[p], x[ci[p]], s);
+        else
+            for (int32_t p = rp[i + 1] - 1; p > d; --p) s = fma(-va[p], x[ci[p]], s);
+        if (!unit) {
+            const double rd = 1.0 / va[d];
+            s = s * rd;
+        }
+        x[i] = s;
+    }
+    return OR_OK;
+}
+
 /* ------------------------------------------------------------------ */
 /* Solvers                                                             */
 /* ------------------------------------------------------------------ */

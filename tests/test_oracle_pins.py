@@ -756,3 +756,60 @@ def test_ilu_solvers_on_convection_diffusion(method):
     assert info["status"] == oracle.OK, info
     assert oracle.true_rel_residual(m, b, x) <= 1e-10
     assert info["iters"] < i0["iters"], (i0["iters"], info["iters"])
+
+
+# ----------------------------------------------------------------- triangular solves
+
+@pytest.mark.parametrize("upper", [False, True])
+@pytest.mark.parametrize("unit", [False, True])
+def test_trsv_matches_lapack_triangular_solve(upper, unit):
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    m = W.convection_diffusion_2d(13, 2.0)
+    D = m.to_dense()
+    T = np.triu(D) if upper else np.tril(D)
+    if unit:
+        np.fill_diagonal(T, 1.0)
+    b = W.uniform_vector(m.n, 31)
+    want = scipy_linalg.solve_triangular(T, b, lower=not upper, unit_diagonal=unit)
+    got = oracle.trsv(m, b, upper=upper, unit=unit)
+    assert np.allclose(got, want, rtol=1e-13, atol=1e-14)
+    # residual relative to |T| |x| + |b| (a unit triangle with -3 below the
+    # diagonal grows x like 3^n)
+    assert np.all(np.abs(T @ got - b) <= 1e-13 * (np.abs(T) @ np.abs(got) + np.abs(b)))
+
+
+def test_trsv_closed_form_bidiagonal():
+    # lower bidiagonal with 1 on the diagonal and -1 below: x_i = b_0 + ... + b_i
+    n = 50
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        if i > 0:
+            rows.append(i); cols.append(i - 1); vals.append(-1.0)
+        rows.append(i); cols.append(i); vals.append(1.0)
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=rp[1:])
+    m = _csr(n, n, rp, cols, vals)
+    b = np.arange(1.0, n + 1)
+    assert np.array_equal(oracle.trsv(m, b), np.cumsum(b))
+    # the same matrix's upper triangle is the identity
+    assert np.array_equal(oracle.trsv(m, b, upper=True), b)
+
+
+def test_trsv_on_ilu_factors_is_ilu_apply():
+    # L y = r with unit diagonal, then U z = y: the two substitutions of ILU(0)
+    m = W.laplacian_2d(9, 7)
+    lu = oracle.ilu0(m)
+    F = W.CSR(m.n, m.ncols, m.row_ptr, m.col_idx, lu)
+    r = W.uniform_vector(m.n, 4)
+    z = oracle.trsv(F, oracle.trsv(F, r, upper=False, unit=True), upper=True)
+    assert np.array_equal(z, oracle.ilu0_apply(m, lu, r))
+
+
+def test_trsv_errors():
+    with pytest.raises(ValueError):  # missing diagonal
+        oracle.trsv(_csr(2, 2, [0, 1, 2], [1, 0], [1.0, 1.0]), np.ones(2))
+    with pytest.raises(ZeroDivisionError):
+        oracle.trsv(_csr(2, 2, [0, 1, 2], [0, 1], [0.0, 1.0]), np.ones(2))
+    # a zero diagonal is fine with a unit diagonal
+    x = oracle.trsv(_csr(2, 2, [0, 1, 3], [0, 0, 1], [0.0, 2.0, 0.0]), np.ones(2), unit=True)
+    assert np.array_equal(x, [1.0, -1.0])
