@@ -307,6 +307,24 @@ gk_status gk_precond_apply(gk_matrix A, gk_precond kind, int32_t block_size,
  * hold L (unit diagonal implied), the rest U.  Blocking. */
 gk_status gk_ilu_factors(gk_matrix A, void* lu, void* stream);
 
+/* Sparse triangular solve T x = b with the lower (upper = 0) or upper
+ * (upper = 1) triangle of the square matrix A, diagonal included; entries
+ * of the other triangle are ignored (the triangular solvers pyGinkgo binds
+ * beside ILU and IC, Section 5).  unit_diagonal = 1 takes the diagonal as
+ * 1 (the stored values are then ignored, zeros allowed).  Every row must
+ * store its diagonal and have strictly ascending columns (GK_ERR_INVALID
+ * otherwise); a zero diagonal value without unit_diagonal is
+ * GK_ERR_ZERO_DIAG.  Arithmetic: row i's terms subtracted in the order the
+ * substitution produced the unknowns (lower: ascending columns; upper:
+ * descending), each as one fused multiply-add, then scaled by 1 / a_ii
+ * rounded once.  b, x: distinct device vectors of n entries in the vector
+ * type.  The pattern analysis (dependency levels, the claim order, the
+ * timed chunk shape) is built on first use and kept with A; the solve is
+ * the sync-free substitution kernel of ILU(0).  Blocks until x is written;
+ * GK_ERR_TIMEOUT if a bounded wait ran out. */
+gk_status gk_triangular_solve(gk_matrix A, int upper, int unit_diagonal, const void* b,
+                              void* x, void* stream);
+
 /* ---------------------------------------------------------------------
  * SpMV without device allocation
  * ------------------------------------------------------------------- */

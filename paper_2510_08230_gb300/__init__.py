@@ -39,7 +39,7 @@ EXPORTED = [
     "gk_matrix_create_csr", "gk_matrix_create_coo", "gk_matrix_convert",
     "gk_matrix_describe", "gk_matrix_export", "gk_matrix_destroy", "gk_apply",
     "gk_apply_adv", "gk_solve", "gk_solve_batched", "gk_status_string", "gk_version",
-    "gk_spmv_csr_f64_noalloc", "gk_precond_apply", "gk_ilu_factors",
+    "gk_spmv_csr_f64_noalloc", "gk_precond_apply", "gk_ilu_factors", "gk_triangular_solve",
 ]
 PRECONDS = {"none": GK_PRECOND_NONE, "jacobi": GK_PRECOND_JACOBI,
             "block_jacobi": GK_PRECOND_BLOCK_JACOBI, "ilu": GK_PRECOND_ILU}
@@ -110,6 +110,7 @@ def lib():
         L.gk_spmv_csr_f64_noalloc.argtypes = [i32, i32, i64, vp, vp, vp, f64, vp, f64, vp, vp]
         L.gk_precond_apply.argtypes = [vp, ctypes.c_int, i32, vp, vp, vp]
         L.gk_ilu_factors.argtypes = [vp, vp, vp]
+        L.gk_triangular_solve.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
         L.gk_status_string.argtypes = [ctypes.c_int]
         L.gk_status_string.restype = ctypes.c_char_p
         L.gk_version.argtypes = []
@@ -387,6 +388,13 @@ class Matrix:
     def precond_apply(self, r, z, kind="ilu", block_size=0, stream=None):
         """z = M^-1 r for the preconditioner `kind` (device vectors)."""
         _check(gk_precond_apply(self.handle, kind, block_size, r, z, stream), "gk_precond_apply")
+
+    def triangular_solve(self, b, x, upper=False, unit_diagonal=False, stream=None):
+        """x with T x = b, T the lower (or upper) triangle of this matrix
+        including its diagonal (unit_diagonal: taken as 1); device vectors."""
+        _check(lib().gk_triangular_solve(self.handle, int(bool(upper)), int(bool(unit_diagonal)),
+                                         _ptr(b), _ptr(x), _stream(stream)),
+               "gk_triangular_solve")
 
     def ilu_factors(self):
         """ILU(0) factors in the CSR order of the matrix (host array of the

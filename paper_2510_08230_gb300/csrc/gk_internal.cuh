@@ -171,6 +171,40 @@ struct CsrPlan {
 
 struct SolverCache;  // solve.cu
 
+// Two triangular factors sharing one CSR pattern: the ILU(0) factors, or a
+// matrix's own lower and upper triangles (gk_triangular_solve), with what
+// the substitution kernels need.  Built on first use and owned by the
+// handle (ilu.cu).
+struct TriStore {
+    int state = 0;                  // 1 built, < 0 the gk_status of a failed build
+    int zero_diag = 0;              // some diagonal value is zero
+    int32_t* rp = nullptr;          // row_ptr / col copies of the pattern
+    int32_t* ci = nullptr;
+    int32_t* dpos = nullptr;        // position of each row's diagonal
+    void* lu = nullptr;             // values in CSR order (vector type)
+    void* rdiag = nullptr;          // 1 / diagonal (vector type)
+    int32_t* ord = nullptr;         // chunks in claim (level) order: L, then U
+    int32_t nord[2] = {0, 0};       // claim-order lengths (L at ord, U after it)
+    int32_t warps[2] = {0, 0};      // warps per substitution launch (L, U)
+    int32_t cs = 32;                // rows per substitution chunk
+    int32_t cpw = 1;                // substitution chunks per warp
+    void* sync = nullptr;           // claim, exit and error words of both directions
+    DevBuf w;                       // scratch of one application
+    void release() {
+        dfree(rp);
+        dfree(ci);
+        dfree(dpos);
+        dfree(lu);
+        dfree(rdiag);
+        dfree(ord);
+        dfree(sync);
+        rp = ci = dpos = ord = nullptr;
+        lu = rdiag = sync = nullptr;
+        w.release();
+    }
+    ~TriStore() { release(); }
+};
+
 // result of one solve (either engine)
 struct SolveOut {
     gk_status status = GK_OK;
@@ -213,20 +247,10 @@ struct gk_matrix_s {
     int dinv_state = 0;           // 0 not built, 1 ok, -1 zero diagonal
     void* binv = nullptr;         // block-Jacobi inverses (vector type, column-major blocks)
     int32_t binv_bs = 0;          // their block size (0 none, -bs singular)
-    // ILU(0) factors in the vector type, built on first use
-    int ilu_state = 0;            // 0 not built, 1 built, < 0 the gk_status of a failed build
-    int32_t* ilu_rp = nullptr;    // CSR pattern of the factors (row_ptr, col)
-    int32_t* ilu_ci = nullptr;
-    int32_t* ilu_dpos = nullptr;  // position of each row's diagonal
-    void* ilu_lu = nullptr;       // factor values in CSR order
-    void* ilu_rdiag = nullptr;    // 1 / u_ii in the vector type
-    int32_t* ilu_ord = nullptr;   // chunks of 32 rows in claim (level) order: L, then U
-    int32_t ilu_warps[2] = {0, 0};  // warps per substitution launch (L, U)
-    int32_t ilu_cs = 32;            // rows per substitution chunk
-    int32_t ilu_cpw = 1;            // substitution chunks per warp
-    int32_t ilu_nord[2] = {0, 0};   // claim-order lengths (L at ilu_ord, U after it)
-    void* ilu_sync = nullptr;     // substitution claim counters, epochs and chunk flags
-    gk::DevBuf ilu_w;             // scratch of gk_precond_apply
+    // ILU(0) factors, and A's own triangles for gk_triangular_solve, built on
+    // first use (ilu.cu)
+    gk::TriStore* ilu = nullptr;
+    gk::TriStore* tri = nullptr;
     gk_matrix_s* lowp[3] = {nullptr, nullptr, nullptr};  // same layout, other dtype
     gk_matrix_s* solve_fmt = nullptr;  // SpMV layout picked for solves (null: not tuned)
     int solve_fmt_tuned = 0;

@@ -1,5 +1,7 @@
-// ilu.cu - ILU(0) factorisation on the device and the preconditioner
-// entry points (gk_precond_apply, gk_ilu_factors).
+// ilu.cu - ILU(0) factorisation on the device, the preconditioner entry
+// points (gk_precond_apply, gk_ilu_factors) and sparse triangular solves
+// with a matrix's own triangles (gk_triangular_solve), which reuse the same
+// setup (without the factorisation) and substitution kernels.
 //
 // Setup, once per matrix:
 //  1. k_ilu_prep: strictly ascending columns, diagonal positions.
@@ -230,31 +232,24 @@ k_ilu_factor(int32_t n, int32_t nch, int32_t cs, const int32_t* __restrict__ rp,
 
 // factors rounded to the vector type; the pivots' reciprocals 1 / u_ii
 // computed in double and rounded once
+// (*zero set when a diagonal value is 0)
 template <typename T>
 __global__ void k_ilu_store(int32_t n, int64_t nnz, const double* __restrict__ fac,
                             const int32_t* __restrict__ dpos, T* __restrict__ lu,
-                            T* __restrict__ rdiag) {
+                            T* __restrict__ rdiag, unsigned* zero) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
          k += (int64_t)gridDim.x * blockDim.x)
         lu[k] = cvt<T>(fac[k]);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        rdiag[i] = cvt<T>(__ddiv_rn(1.0, fac[dpos[i]]));
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = fac[dpos[i]];
+        if (d == 0.0) atomicOr(zero, 1u);
+        rdiag[i] = cvt<T>(__ddiv_rn(1.0, d));
+    }
 }
 
 static size_t ilu_sync_bytes() { return 2 * sizeof(TrsvSync); }
 
-static void ilu_release(gk_matrix A) {
-    dfree(A->ilu_rp);
-    dfree(A->ilu_ci);
-    dfree(A->ilu_dpos);
-    dfree(A->ilu_lu);
-    dfree(A->ilu_sync);
-    dfree(A->ilu_ord);
-    dfree(A->ilu_rdiag);
-    A->ilu_rp = A->ilu_ci = A->ilu_dpos = A->ilu_ord = nullptr;
-    A->ilu_lu = A->ilu_sync = A->ilu_rdiag = nullptr;
-}
 
 // Grid of `kernel` (256 threads) when each of `items` needs one warp, at
 // most the resident blocks.
@@ -269,7 +264,7 @@ static unsigned resident_grid(K kernel, int64_t items) {
 
 // Dependency levels of the L (up = false) or U graph of cs-row chunks into
 // lev (nch entries); *nlev = the number of levels.
-static gk_status chunk_levels(gk_matrix A, int32_t n, int32_t cs, bool up, DevBuf& lev,
+static gk_status chunk_levels(const TriStore* S, int32_t n, int32_t cs, bool up, DevBuf& lev,
                               unsigned* nlev, cudaStream_t s) {
     const int32_t nch = (n + cs - 1) / cs;
     DevBuf misc;
@@ -280,10 +275,10 @@ static gk_status chunk_levels(gk_matrix A, int32_t n, int32_t cs, bool up, DevBu
     unsigned* mp = (unsigned*)misc.ptr;
     if (up)
         k_chunk_levels<true><<<resident_grid(k_chunk_levels<true>, nch), 256, 0, s>>>(
-            n, nch, cs, A->ilu_rp, A->ilu_ci, A->ilu_dpos, (unsigned*)lev.ptr, mp);
+            n, nch, cs, S->rp, S->ci, S->dpos, (unsigned*)lev.ptr, mp);
     else
         k_chunk_levels<false><<<resident_grid(k_chunk_levels<false>, nch), 256, 0, s>>>(
-            n, nch, cs, A->ilu_rp, A->ilu_ci, A->ilu_dpos, (unsigned*)lev.ptr, mp);
+            n, nch, cs, S->rp, S->ci, S->dpos, (unsigned*)lev.ptr, mp);
     GK_CUDA(cudaGetLastError());
     unsigned h[4] = {0, 0, 0, 0};
     GK_CUDA(cudaMemcpyAsync(h, mp, sizeof(h), cudaMemcpyDeviceToHost, s));
@@ -330,26 +325,31 @@ struct IluLevels {
 };
 
 template <typename T>
-IluDev<T> ilu_view(gk_matrix A) {
+static IluDev<T> tri_view(const TriStore* S, int32_t n) {
     IluDev<T> f;
-    f.n = A->n;
-    f.cs = A->ilu_cs;
-    f.cpw = A->ilu_cpw;
-    f.nch = (A->n + f.cs - 1) / f.cs;
-    f.rp = A->ilu_rp;
-    f.ci = A->ilu_ci;
-    f.dpos = A->ilu_dpos;
-    f.lu = (const T*)A->ilu_lu;
-    f.rdiag = (const T*)A->ilu_rdiag;
-    f.ord_l = A->ilu_ord;
-    f.ord_u = A->ilu_ord + A->ilu_nord[0];
-    f.nord[0] = A->ilu_nord[0];
-    f.nord[1] = A->ilu_nord[1];
-    f.warps[0] = A->ilu_warps[0];
-    f.warps[1] = A->ilu_warps[1];
-    f.sy = (TrsvSync*)A->ilu_sync;
+    f.n = n;
+    f.cs = S->cs;
+    f.cpw = S->cpw;
+    f.nch = (n + f.cs - 1) / f.cs;
+    f.rp = S->rp;
+    f.ci = S->ci;
+    f.dpos = S->dpos;
+    f.lu = (const T*)S->lu;
+    f.rdiag = (const T*)S->rdiag;
+    f.ord_l = S->ord;
+    f.ord_u = S->ord + S->nord[0];
+    f.nord[0] = S->nord[0];
+    f.nord[1] = S->nord[1];
+    f.warps[0] = S->warps[0];
+    f.warps[1] = S->warps[1];
+    f.sy = (TrsvSync*)S->sync;
     if (const char* e = getenv("GK_ILU_PAUSE")) f.pause_max = (unsigned)std::max(32, atoi(e));
     return f;
+}
+
+template <typename T>
+IluDev<T> ilu_view(gk_matrix A) {
+    return tri_view<T>(A->ilu, A->n);
 }
 template IluDev<double> ilu_view<double>(gk_matrix);
 template IluDev<float> ilu_view<float>(gk_matrix);
@@ -366,7 +366,7 @@ template IluDev<float> ilu_view<float>(gk_matrix);
 // 32, one chunk a warp) forces a size.  Results never depend on the
 // choice, only the time does.
 template <typename T>
-static gk_status tune_chunks(gk_matrix A, int32_t n, const IluLevels& lv, cudaStream_t s) {
+static gk_status tune_chunks(TriStore* S, int32_t n, const IluLevels& lv, cudaStream_t s) {
     int forced = 0;
     if (const char* e = getenv("GK_ILU_CHUNK")) {
         const int v = atoi(e);
@@ -401,7 +401,7 @@ static gk_status tune_chunks(gk_matrix A, int32_t n, const IluLevels& lv, cudaSt
         warps[k][0] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, mult * (int64_t)wl / cpw), nl / cpw);
         warps[k][1] = (int32_t)std::min<int64_t>(std::max<int64_t>(64, mult * (int64_t)wu / cpw), nu / cpw);
         if (ncand == 1) break;
-        IluDev<T> f = ilu_view<T>(A);
+        IluDev<T> f = tri_view<T>(S, n);
         f.cs = cs;
         f.cpw = cpw;
         f.nch = nch;
@@ -412,7 +412,7 @@ static gk_status tune_chunks(gk_matrix A, int32_t n, const IluLevels& lv, cudaSt
         f.warps[0] = warps[k][0];
         f.warps[1] = warps[k][1];
         T* w = (T*)tmp.ptr;
-        const IluSrc<T> src{(const T*)A->ilu_rdiag};
+        const IluSrc<T> src{(const T*)S->rdiag};
         float ms = 0.f;
         st = ilu_apply<T>(f, src, w, IluOutStore<T>{w + n}, IluSkipNever{}, IluNoErr{}, s);
         if (st == GK_OK && cudaEventRecord(e0, s) != cudaSuccess) st = GK_ERR_CUDA;
@@ -431,42 +431,48 @@ static gk_status tune_chunks(gk_matrix A, int32_t n, const IluLevels& lv, cudaSt
     cudaEventDestroy(e1);
     if (st != GK_OK) return st;
     TrsvSync h[2];
-    GK_CUDA(cudaMemcpyAsync(h, A->ilu_sync, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaMemcpyAsync(h, S->sync, sizeof(h), cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaStreamSynchronize(s));
     if (h[0].err | h[1].err) return GK_ERR_TIMEOUT;
     const int32_t cs = forced ? forced : all_cs[pick], cpw = forced ? 1 : all_cpw[pick];
-    GK_CUDA(cudaMemcpyAsync(A->ilu_ord, ordb[pick].ptr,
+    GK_CUDA(cudaMemcpyAsync(S->ord, ordb[pick].ptr,
                             sizeof(int32_t) * ((size_t)nord[pick][0] + nord[pick][1]),
                             cudaMemcpyDeviceToDevice, s));
     GK_CUDA(cudaStreamSynchronize(s));
-    A->ilu_cs = cs;
-    A->ilu_cpw = cpw;
-    A->ilu_nord[0] = nord[pick][0];
-    A->ilu_nord[1] = nord[pick][1];
-    A->ilu_warps[0] = std::max(1, warps[pick][0]);
-    A->ilu_warps[1] = std::max(1, warps[pick][1]);
+    S->cs = cs;
+    S->cpw = cpw;
+    S->nord[0] = nord[pick][0];
+    S->nord[1] = nord[pick][1];
+    S->warps[0] = std::max(1, warps[pick][0]);
+    S->warps[1] = std::max(1, warps[pick][1]);
     return GK_OK;
 }
 
-static gk_status ilu_build(gk_matrix A, gk_matrix C, cudaStream_t s) {
+// Builds S for the CSR matrix C with values rounded to the vector type of
+// vdt.  factorize: the ILU(0) factors (a missing diagonal or zero pivot is
+// GK_ERR_ZERO_DIAG); otherwise C's own values, for triangular solves (a
+// missing diagonal is GK_ERR_INVALID, a zero one is recorded in
+// S->zero_diag).
+static gk_status tri_build(TriStore* S, gk_dtype vdt, gk_matrix C, bool factorize,
+                           cudaStream_t s) {
     const int32_t n = C->n;
     const int64_t nnz = C->nnz;
-    const size_t vb = vector_bytes(A->dtype);
-    GK_CUDA(dmalloc_t(&A->ilu_rp, (size_t)n + 1));
-    GK_CUDA(dmalloc_t(&A->ilu_ci, (size_t)std::max<int64_t>(nnz, 1)));
-    GK_CUDA(dmalloc_t(&A->ilu_dpos, (size_t)std::max(n, 1)));
-    GK_CUDA(dmalloc(&A->ilu_lu, vb * (size_t)std::max<int64_t>(nnz, 1)));
-    GK_CUDA(dmalloc(&A->ilu_rdiag, vb * (size_t)std::max(n, 1)));
-    GK_CUDA(dmalloc(&A->ilu_sync, ilu_sync_bytes()));
+    const size_t vb = vector_bytes(vdt);
+    GK_CUDA(dmalloc_t(&S->rp, (size_t)n + 1));
+    GK_CUDA(dmalloc_t(&S->ci, (size_t)std::max<int64_t>(nnz, 1)));
+    GK_CUDA(dmalloc_t(&S->dpos, (size_t)std::max(n, 1)));
+    GK_CUDA(dmalloc(&S->lu, vb * (size_t)std::max<int64_t>(nnz, 1)));
+    GK_CUDA(dmalloc(&S->rdiag, vb * (size_t)std::max(n, 1)));
+    GK_CUDA(dmalloc(&S->sync, ilu_sync_bytes()));
     // claim orders: at most 4 entries per 8-row chunk and direction
-    GK_CUDA(dmalloc_t(&A->ilu_ord, 2 * 4 * (size_t)std::max((n + 7) / 8, 1)));
-    GK_CUDA(cudaMemcpyAsync(A->ilu_rp, C->row_ptr, sizeof(int32_t) * ((size_t)n + 1),
+    GK_CUDA(dmalloc_t(&S->ord, 2 * 4 * (size_t)std::max((n + 7) / 8, 1)));
+    GK_CUDA(cudaMemcpyAsync(S->rp, C->row_ptr, sizeof(int32_t) * ((size_t)n + 1),
                             cudaMemcpyDeviceToDevice, s));
     if (nnz > 0)
-        GK_CUDA(cudaMemcpyAsync(A->ilu_ci, C->col, sizeof(int32_t) * (size_t)nnz,
+        GK_CUDA(cudaMemcpyAsync(S->ci, C->col, sizeof(int32_t) * (size_t)nnz,
                                 cudaMemcpyDeviceToDevice, s));
     // claim counters, exit counters and error flags start at 0
-    GK_CUDA(cudaMemsetAsync(A->ilu_sync, 0, ilu_sync_bytes(), s));
+    GK_CUDA(cudaMemsetAsync(S->sync, 0, ilu_sync_bytes(), s));
 
     DevBuf fac, done, misc;
     GK_TRY(fac.ensure(sizeof(double) * (size_t)std::max<int64_t>(nnz, 1)));
@@ -480,8 +486,8 @@ static gk_status ilu_build(gk_matrix A, gk_matrix C, cudaStream_t s) {
         const unsigned g = ew_grid(n);
         auto prep = [&](auto vt) {
             using V = decltype(vt);
-            k_ilu_prep<V><<<g, 256, 0, s>>>(n, A->ilu_rp, A->ilu_ci, (const V*)C->val,
-                                           (double*)fac.ptr, A->ilu_dpos, mp + 3);
+            k_ilu_prep<V><<<g, 256, 0, s>>>(n, S->rp, S->ci, (const V*)C->val,
+                                           (double*)fac.ptr, S->dpos, mp + 3);
         };
         if (C->dtype == GK_F64) prep(double());
         else if (C->dtype == GK_F32) prep(float());
@@ -491,64 +497,76 @@ static gk_status ilu_build(gk_matrix A, gk_matrix C, cudaStream_t s) {
         GK_CUDA(cudaMemcpyAsync(h, mp, sizeof(h), cudaMemcpyDeviceToHost, s));
         GK_CUDA(cudaStreamSynchronize(s));
         if (h[3] & 1u) return GK_ERR_INVALID;
-        if (h[3] & 2u) return GK_ERR_ZERO_DIAG;
-        // the factorisation claims rows chunk by chunk in the L level order
-        // of 32-row chunks
+        if (h[3] & 2u) return factorize ? GK_ERR_ZERO_DIAG : GK_ERR_INVALID;
+        // chunk levels for both sizes and directions, once
         IluLevels lv;
-        GK_TRY(chunk_levels(A, n, 32, false, lv.l32, &lv.nl32, s));
-        GK_TRY(chunk_levels(A, n, 32, true, lv.u32, &lv.nu32, s));
-        GK_TRY(chunk_levels(A, n, 8, false, lv.l8, &lv.nl8, s));
-        GK_TRY(chunk_levels(A, n, 8, true, lv.u8, &lv.nu8, s));
-        const int32_t cs = 32, nch = (n + cs - 1) / cs;
-        unsigned wl = 0, nl = 0;
-        GK_TRY(level_order(nch, 1, lv.l32, A->ilu_ord, &wl, &nl, s));
-        k_ilu_factor<<<resident_grid(k_ilu_factor,
-                                     std::min<int64_t>(n, 2 * (int64_t)cs * wl + 256)),
-                       256, 0, s>>>(n, nch, cs, A->ilu_rp, A->ilu_ci, A->ilu_dpos, A->ilu_ord,
-                                    (double*)fac.ptr, (unsigned*)done.ptr, mp);
+        GK_TRY(chunk_levels(S, n, 32, false, lv.l32, &lv.nl32, s));
+        GK_TRY(chunk_levels(S, n, 32, true, lv.u32, &lv.nu32, s));
+        GK_TRY(chunk_levels(S, n, 8, false, lv.l8, &lv.nl8, s));
+        GK_TRY(chunk_levels(S, n, 8, true, lv.u8, &lv.nu8, s));
+        if (factorize) {
+            // rows claimed chunk by chunk in the L level order of 32-row chunks
+            const int32_t cs = 32, nch = (n + cs - 1) / cs;
+            unsigned wl = 0, nl = 0;
+            GK_TRY(level_order(nch, 1, lv.l32, S->ord, &wl, &nl, s));
+            k_ilu_factor<<<resident_grid(k_ilu_factor,
+                                         std::min<int64_t>(n, 2 * (int64_t)cs * wl + 256)),
+                           256, 0, s>>>(n, nch, cs, S->rp, S->ci, S->dpos, S->ord,
+                                        (double*)fac.ptr, (unsigned*)done.ptr, mp);
+            GK_CUDA(cudaGetLastError());
+            GK_CUDA(cudaMemcpyAsync(h, mp, sizeof(h), cudaMemcpyDeviceToHost, s));
+            GK_CUDA(cudaStreamSynchronize(s));
+            if (h[1]) return GK_ERR_TIMEOUT;
+            if (h[2]) return GK_ERR_ZERO_DIAG;
+        }
+        GK_CUDA(cudaMemsetAsync(mp + 2, 0, sizeof(unsigned), s));
+        if (vdt == GK_F64)
+            k_ilu_store<double><<<ew_grid(nnz), 256, 0, s>>>(n, nnz, (const double*)fac.ptr,
+                                                             S->dpos, (double*)S->lu,
+                                                             (double*)S->rdiag, mp + 2);
+        else
+            k_ilu_store<float><<<ew_grid(nnz), 256, 0, s>>>(n, nnz, (const double*)fac.ptr,
+                                                            S->dpos, (float*)S->lu,
+                                                            (float*)S->rdiag, mp + 2);
         GK_CUDA(cudaGetLastError());
         GK_CUDA(cudaMemcpyAsync(h, mp, sizeof(h), cudaMemcpyDeviceToHost, s));
         GK_CUDA(cudaStreamSynchronize(s));
-        if (h[1]) return GK_ERR_TIMEOUT;
-        if (h[2]) return GK_ERR_ZERO_DIAG;
-        if (A->dtype == GK_F64)
-            k_ilu_store<double><<<ew_grid(nnz), 256, 0, s>>>(n, nnz, (const double*)fac.ptr,
-                                                             A->ilu_dpos, (double*)A->ilu_lu,
-                                                             (double*)A->ilu_rdiag);
-        else
-            k_ilu_store<float><<<ew_grid(nnz), 256, 0, s>>>(n, nnz, (const double*)fac.ptr,
-                                                            A->ilu_dpos, (float*)A->ilu_lu,
-                                                            (float*)A->ilu_rdiag);
-        GK_CUDA(cudaGetLastError());
-        GK_TRY(A->dtype == GK_F64 ? tune_chunks<double>(A, n, lv, s)
-                                  : tune_chunks<float>(A, n, lv, s));
+        S->zero_diag = h[2] != 0;
+        GK_TRY(vdt == GK_F64 ? tune_chunks<double>(S, n, lv, s) : tune_chunks<float>(S, n, lv, s));
     }
     GK_CUDA(cudaStreamSynchronize(s));
     return GK_OK;
 }
 
-gk_status ensure_ilu(gk_matrix A, cudaStream_t s) {
-    if (A->ilu_state == 1) return GK_OK;
-    if (A->ilu_state < 0) return (gk_status)A->ilu_state;
+// The TriStore *slot of A (ILU factors or raw triangles), built on first use.
+static gk_status ensure_store(gk_matrix A, TriStore** slot, bool factorize, cudaStream_t s) {
+    if (*slot && (*slot)->state == 1) return GK_OK;
+    if (*slot && (*slot)->state < 0) return (gk_status)(*slot)->state;
     if (A->n != A->ncols) return GK_ERR_INVALID;
+    if (!*slot) {
+        *slot = new (std::nothrow) TriStore();
+        if (!*slot) return GK_ERR_OOM;
+    }
+    TriStore* S = *slot;
     gk_matrix C = A, tmp = nullptr;
     if (A->fmt != GK_CSR) {
         GK_TRY(gk_matrix_convert(A, GK_CSR, A->dtype, 0, 0, s, &tmp));
         C = tmp;
     }
-    const gk_status st = ilu_build(A, C, s);
+    const gk_status st = tri_build(S, A->dtype, C, factorize, s);
     if (tmp) gk_matrix_destroy(tmp);
     if (st != GK_OK) {
         cudaStreamSynchronize(s);
-        ilu_release(A);
+        S->release();
         // a malformed or singular pattern stays so; other failures may be retried
-        if (st == GK_ERR_INVALID || st == GK_ERR_ZERO_DIAG) A->ilu_state = (int)st;
+        if (st == GK_ERR_INVALID || st == GK_ERR_ZERO_DIAG) S->state = (int)st;
         return st;
     }
-    A->ilu_state = 1;
+    S->state = 1;
     return GK_OK;
 }
 
+gk_status ensure_ilu(gk_matrix A, cudaStream_t s) { return ensure_store(A, &A->ilu, true, s); }
 
 template <typename T>
 __global__ void EW_BOUNDS k_scale_by(int32_t n, const T* __restrict__ d, const T* __restrict__ r,
@@ -581,11 +599,30 @@ static gk_status precond_apply_t(gk_matrix A, int kind, int32_t bs, const T* r, 
     }
     GK_TRY(ensure_ilu(A, s));
     if (n == 0) return GK_OK;
-    GK_TRY(A->ilu_w.ensure(sizeof(T) * (size_t)n));
+    GK_TRY(A->ilu->w.ensure(sizeof(T) * (size_t)n));
     const IluDev<T> f = ilu_view<T>(A);
     GK_TRY(ilu_clear_err(f, s));
-    GK_TRY(ilu_apply<T>(f, IluSrc<T>{r}, (T*)A->ilu_w.ptr, IluOutStore<T>{z}, IluSkipNever{},
+    GK_TRY(ilu_apply<T>(f, IluSrc<T>{r}, (T*)A->ilu->w.ptr, IluOutStore<T>{z}, IluSkipNever{},
                         IluNoErr{}, s));
+    TrsvSync h[2];
+    GK_CUDA(cudaMemcpyAsync(h, f.sy, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    if (h[0].err | h[1].err) return GK_ERR_TIMEOUT;
+    return GK_OK;
+}
+
+// T x = b with A's lower (upper = 0) or upper triangle; unit: unit diagonal.
+template <typename T>
+static gk_status tri_solve_t(gk_matrix A, int upper, int unit, const T* b, T* x,
+                             cudaStream_t s) {
+    GK_TRY(ensure_store(A, &A->tri, false, s));
+    if (!unit && A->tri->zero_diag) return GK_ERR_ZERO_DIAG;
+    if (A->n == 0) return GK_OK;
+    IluDev<T> f = tri_view<T>(A->tri, A->n);
+    f.ldiag = (!upper && !unit) ? 1 : 0;
+    f.udiag = unit ? 0 : 1;
+    GK_TRY(ilu_clear_err(f, s));
+    GK_TRY(tri_apply<T>(f, upper != 0, b, x, s));
     TrsvSync h[2];
     GK_CUDA(cudaMemcpyAsync(h, f.sy, sizeof(h), cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaStreamSynchronize(s));
@@ -596,6 +633,21 @@ static gk_status precond_apply_t(gk_matrix A, int kind, int32_t bs, const T* r, 
 }  // namespace gk
 
 using namespace gk;
+
+extern "C" gk_status gk_triangular_solve(gk_matrix A, int upper, int unit_diagonal, const void* b,
+                                         void* x, void* stream) {
+    if (!A || ((!b || !x) && A->n > 0)) return GK_ERR_INVALID;
+    if (A->n != A->ncols) return GK_ERR_INVALID;
+    if (A->n > 0 && b == x) return GK_ERR_INVALID;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != A->device) return GK_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(A->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (A->dtype == GK_F64)
+        return tri_solve_t<double>(A, upper, unit_diagonal, (const double*)b, (double*)x, s);
+    return tri_solve_t<float>(A, upper, unit_diagonal, (const float*)b, (float*)x, s);
+}
 
 extern "C" gk_status gk_precond_apply(gk_matrix A, gk_precond kind, int32_t block_size,
                                       const void* r, void* z, void* stream) {
@@ -624,7 +676,7 @@ extern "C" gk_status gk_ilu_factors(gk_matrix A, void* lu, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     GK_TRY(ensure_ilu(A, s));
     if (A->nnz > 0)
-        GK_CUDA(cudaMemcpyAsync(lu, A->ilu_lu, vector_bytes(A->dtype) * (size_t)A->nnz,
+        GK_CUDA(cudaMemcpyAsync(lu, A->ilu->lu, vector_bytes(A->dtype) * (size_t)A->nnz,
                                 cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaStreamSynchronize(s));
     return GK_OK;

@@ -82,6 +82,8 @@ struct IluDev {
     const int32_t* ord_u = nullptr;  // and U; nord entries each, multiples of 32 / cs
     int32_t nord[2] = {0, 0};
     TrsvSync* sy = nullptr;         // [2]
+    int32_t ldiag = 0;              // L scaled by rdiag (0: unit diagonal)
+    int32_t udiag = 1;              // U scaled by rdiag (0: unit diagonal)
     unsigned pause_max = 64;        // longest pause between polls (ns)
     int32_t warps[2] = {0, 0};      // host: warps per substitution launch
 };
@@ -299,7 +301,7 @@ k_ilu_trsv(IluDev<T> f, Src src, Out out, Skip sk, Err on_err) {
             }
             const int base = grp * cs;  // the group's first lane
             T mine = T(0);
-            if (!UP) {
+            if (!UP && !f.ldiag) {
                 // lane t's value is final at step t; later lanes subtract it
                 int32_t col = pin < pend ? f.ci[pin] : INT32_MAX;
                 T lv = pin < pend ? f.lu[pin] : T(0);
@@ -313,8 +315,25 @@ k_ilu_trsv(IluDev<T> f, Src src, Out out, Skip sk, Err on_err) {
                         lv = pin < pend ? f.lu[pin] : T(0);
                     }
                 }
-            } else {
+            } else if (!UP) {
+                // as above, each value scaled by its reciprocal diagonal
                 const T rd = has ? f.rdiag[i] : T(1);
+                int32_t col = pin < pend ? f.ci[pin] : INT32_MAX;
+                T lv = pin < pend ? f.lu[pin] : T(0);
+                for (int t = 0; t < cs; ++t) {
+                    T v = T(0);
+                    if (gl == t) v = mul_rn(acc, rd);
+                    const T yt = __shfl_sync(FULL, v, base + t);
+                    if (gl == t) mine = yt;
+                    if (col == c0 + t) {
+                        acc = sub_mul(acc, lv, yt);
+                        ++pin;
+                        col = pin < pend ? f.ci[pin] : INT32_MAX;
+                        lv = pin < pend ? f.lu[pin] : T(0);
+                    }
+                }
+            } else {
+                const T rd = has && f.udiag ? f.rdiag[i] : T(1);
                 int32_t col = pend > pin ? f.ci[pend - 1] : INT32_MIN;
                 T uv = pend > pin ? f.lu[pend - 1] : T(0);
                 for (int t = cs - 1; t >= 0; --t) {
@@ -378,6 +397,28 @@ static gk_status ilu_apply(const IluDev<T>& f, Src src, T* w, Out out, Skip sk, 
     km<<<mg, 256, 0, s>>>(f.n, w, out, sk);
     kl<<<ilu_grid(kl, f.warps[0]), 256, 0, s>>>(f, src, IluOutStore<T>{w}, sk, IluNoErr{});
     ku<<<ilu_grid(ku, f.warps[1]), 256, 0, s>>>(f, IluSrc<T>{w}, out, sk, on_err);
+    GK_CUDA(cudaGetLastError());
+    return GK_OK;
+}
+
+// One substitution alone (gk_triangular_solve): mark x unsolved, then the L
+// (up = false) or U launch from src into x.
+template <typename T>
+static gk_status tri_apply(const IluDev<T>& f, bool up, const T* src, T* x, cudaStream_t s) {
+    if (f.n == 0) return GK_OK;
+    auto km = k_ilu_mark<T, IluOutStore<T>, IluSkipNever>;
+    const unsigned mg = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(((int64_t)f.n + 1023) / 1024, (int64_t)num_sms() * 8));
+    km<<<mg, 256, 0, s>>>(f.n, x, IluOutStore<T>{x}, IluSkipNever{});
+    if (!up) {
+        auto kl = k_ilu_trsv<T, false, IluSrc<T>, IluOutStore<T>, IluSkipNever, IluNoErr>;
+        kl<<<ilu_grid(kl, f.warps[0]), 256, 0, s>>>(f, IluSrc<T>{src}, IluOutStore<T>{x},
+                                                     IluSkipNever{}, IluNoErr{});
+    } else {
+        auto ku = k_ilu_trsv<T, true, IluSrc<T>, IluOutStore<T>, IluSkipNever, IluNoErr>;
+        ku<<<ilu_grid(ku, f.warps[1]), 256, 0, s>>>(f, IluSrc<T>{src}, IluOutStore<T>{x},
+                                                     IluSkipNever{}, IluNoErr{});
+    }
     GK_CUDA(cudaGetLastError());
     return GK_OK;
 }

@@ -505,19 +505,9 @@ static void free_arrays(gk_matrix A) {
     dfree(A->coo_row);
     dfree(A->empty_rows);
     A->coo_row = A->empty_rows = nullptr;
-    dfree(A->ilu_rp);
-    dfree(A->ilu_ci);
-    dfree(A->ilu_dpos);
-    dfree(A->ilu_lu);
-    dfree(A->ilu_sync);
-    dfree(A->ilu_ord);
-    dfree(A->ilu_rdiag);
-    A->ilu_ord = nullptr;
-    A->ilu_rdiag = nullptr;
-    A->ilu_rp = A->ilu_ci = A->ilu_dpos = nullptr;
-    A->ilu_lu = A->ilu_sync = nullptr;
-    A->ilu_state = 0;
-    A->ilu_w.release();
+    delete A->ilu;
+    delete A->tri;
+    A->ilu = A->tri = nullptr;
     A->row_ptr = A->col = nullptr;
     A->val = nullptr;
     A->slice_len = nullptr;
