@@ -62,6 +62,19 @@ def matrix_bytes(m, refined):
     return b
 
 
+def ilu_bytes(m, refined):
+    """Device bytes an ILU(0) solve adds to a cached matrix: the factors'
+    pattern, values, diagonal data and claim orders (per value type: twice
+    once a refined solve factors the FP32 copy too) and two more solver
+    vectors."""
+    b = 4 * (m.n + 1) + 12 * m.nnz + 20 * m.n
+    return b * (2 if refined else 1) + 2 * 8 * m.n
+
+
+# preconditioners the batched engine runs (others go to gk_solve alone)
+BATCHED_PRECONDS = (None, False, True, 0, 1, "none", "jacobi")
+
+
 def request_bytes(req, small_n):
     """Device bytes held only while a request runs: b and x, plus the
     batched engine's per-system workspace (4 FP64 vectors)."""
@@ -124,7 +137,7 @@ class SolveServer:
                 return
             if key == keep:
                 continue
-            mat, nb, users, _ = self.cache[key]
+            mat, nb, users = self.cache[key][:3]
             if users == 0:
                 self.used -= nb
                 del self.cache[key]
@@ -135,14 +148,17 @@ class SolveServer:
         while self.queue:
             req = self.queue[0]
             refined = req.precision == "ir32"
+            ilu = req.precond == "ilu"
             need = request_bytes(req, self.small_n)
             entry = self.cache.get(req.key)
             if entry is None:
-                mb = matrix_bytes(req.m, refined)
-            elif refined and not entry[3]:  # a cached matrix gains its FP32 copy
-                mb = matrix_bytes(req.m, True) - matrix_bytes(req.m, False)
+                mb = matrix_bytes(req.m, refined) + (ilu_bytes(req.m, refined) if ilu else 0)
             else:
                 mb = 0
+                if refined and not entry[3]:  # a cached matrix gains its FP32 copy
+                    mb += matrix_bytes(req.m, True) - matrix_bytes(req.m, False)
+                if ilu and not entry[4]:  # ... or its ILU(0) factors
+                    mb += ilu_bytes(req.m, refined or entry[3])
             if self.used + need + mb > self.budget:
                 self._evict(need + mb, keep=req.key)
                 if self.used + need + mb > self.budget:
@@ -151,15 +167,15 @@ class SolveServer:
             req.need = need
             self.used += need + mb
             if entry is None:
-                self.cache[req.key] = [None, mb, 1, refined]
+                self.cache[req.key] = [None, mb, 1, refined, ilu]
             else:
                 entry[2] += 1
                 self.cache.move_to_end(req.key)
-                if mb:
-                    entry[1] += mb
-                    entry[3] = True
+                entry[1] += mb
+                entry[3] = entry[3] or refined
+                entry[4] = entry[4] or ilu
             small = req.m.n <= self.small_n and req.precision == "f64" and \
-                req.method in ("cg", "bicgstab")
+                req.method in ("cg", "bicgstab") and req.precond in BATCHED_PRECONDS
             req.batched = small
             (self.pending_small if small else self.pending_single).append(req)
 

@@ -142,3 +142,26 @@ def test_refined_and_large_requests_run_alone(fake_server):
     assert all(r.event.wait(30) for r in reqs)
     srv.close()
     assert not reqs[0].batched and not reqs[1].batched
+
+
+def test_ilu_and_block_jacobi_requests_run_alone_and_count_their_factors(fake_server):
+    """The batched engine runs no ILU(0) or block-Jacobi: small requests with
+    them go to gk_solve alone, and an ILU(0) request charges the factors to
+    the cached matrix once."""
+    sv, _ = fake_server
+    m = W.laplacian_2d(12)
+    reqs = [sv.SolveRequest(0, 0, m, np.ones(m.n), 1e-8, "f64", precond="ilu"),
+            sv.SolveRequest(1, 1, m, np.ones(m.n), 1e-8, "f64", precond="block_jacobi"),
+            sv.SolveRequest(2, 2, m, np.ones(m.n), 1e-8, "f64", precond="jacobi"),
+            sv.SolveRequest(3, 0, m, np.ones(m.n), 1e-8, "f64", precond="ilu")]
+    srv = sv.SolveServer(budget_bytes=1e9, workers=2)
+    for r in reqs:
+        srv.submit(r)
+    assert all(r.event.wait(30) for r in reqs)
+    cached = dict(srv.cache)
+    srv.close()
+    assert not reqs[0].batched and not reqs[1].batched and not reqs[3].batched
+    assert reqs[2].batched
+    want = sv.matrix_bytes(m, False) + sv.ilu_bytes(m, False)
+    assert cached[0][1] == want and cached[0][4]  # charged once for both ILU requests
+    assert cached[2][1] == sv.matrix_bytes(m, False) and not cached[2][4]
