@@ -27,6 +27,7 @@ constexpr int CL_MAX_BLOCKS = 16;
 struct ClusterArgs {
     int32_t n;
     int32_t rpb;  // rows per block
+    uint32_t rpb_inv;  // rpb > 1: floor(2^32 / rpb) + 1 (owner = umulhi(col, rpb_inv)); 0: rpb = 1
     const int32_t* rp;
     const int32_t* ci;
     const void* va;
@@ -79,7 +80,7 @@ __device__ __forceinline__ T cluster_row_dot(cgx::cluster_group& cl, const Clust
     const int32_t e = A.rp[i + 1];
     for (int32_t k = A.rp[i]; k < e; ++k) {
         const int32_t c = A.ci[k];
-        const unsigned owner = (unsigned)(c / A.rpb);
+        const unsigned owner = A.rpb_inv ? __umulhi((unsigned)c, A.rpb_inv) : (unsigned)c;  // c / rpb
         const int32_t loc = c - (int32_t)owner * A.rpb;
         const T gv = owner == my_rank ? g_s[loc] : cl.map_shared_rank(g_s, owner)[loc];
         s = fmadd(cvt<T>(va[k]), gv, s);
@@ -288,7 +289,10 @@ gk_status solve_cluster(gk_matrix A, const void* b, void* x, const gk_solve_opts
     static thread_local SolveOut* hout = nullptr;
     GK_TRY(outbuf.ensure(sizeof(SolveOut)));
     if (!hout) GK_CUDA(cudaMallocHost(&hout, sizeof(SolveOut)));
-    ClusterArgs args{A->n, rpb, A->row_ptr, A->col, A->val, b, x, o->tol, o->max_iters,
+    // col < n <= 16384 and rpb <= 1024, so col * rpb < 2^32 and the
+    // multiply-high quotient is exact
+    const uint32_t rpb_inv = rpb > 1 ? (uint32_t)((1ull << 32) / (uint64_t)rpb + 1) : 0u;
+    ClusterArgs args{A->n, rpb, rpb_inv, A->row_ptr, A->col, A->val, b, x, o->tol, o->max_iters,
                      o->precond == GK_PRECOND_JACOBI, (SolveOut*)outbuf.ptr};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
