@@ -42,10 +42,18 @@ struct ClusterArgs {
 // Sum of NA per-block partials over the cluster, identical in all threads:
 // block sum (warp 0), cluster barrier, then warp 0 loads the C block
 // partials (lane r reads block r) and adds them with a fixed shuffle tree;
-// every block evaluates the same tree over the same values.
-template <int NA>
+// every block evaluates the same tree over the same values.  fin(tot) runs
+// on thread 0 alone before the block barrier that publishes the totals:
+// the scalar work on them (divisions, square roots, decisions), which on
+// this part's narrow FP64 pipe costs microseconds if every thread repeats
+// it, writes its results to shared memory for the block.
+struct NoFin {
+    __device__ __forceinline__ void operator()(const double*) const {}
+};
+
+template <int NA, class Fin = NoFin>
 __device__ __forceinline__ void cluster_allsum(cgx::cluster_group& cl, double (&v)[NA],
-                                               double (*red)[4], int& tog) {
+                                               double (*red)[4], int& tog, Fin fin = Fin()) {
     __shared__ double tot[4];
     block_sum<NA>(v);
     if (threadIdx.x == 0)
@@ -65,6 +73,7 @@ __device__ __forceinline__ void cluster_allsum(cgx::cluster_group& cl, double (&
             p = warp_sum(p);
             if (lane == 0) tot[a] = p;
         }
+        if (threadIdx.x == 0) fin(tot);
     }
     __syncthreads();
 #pragma unroll
@@ -94,6 +103,10 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
     const unsigned rank = cl.block_rank();
     __shared__ T g_s[CL_RMAX * CL_THREADS];  // owned part of the gathered vector
     __shared__ double red[2][4];
+    // scalars of the iteration, computed by thread 0 (see cluster_allsum):
+    // 0 rho, 1 alpha, 2 beta, 3 status (0 go on, 1 NaN, 2 breakdown,
+    // 3 recurrence residual passed)
+    __shared__ double sc[4];
     int tog = 0;
     const V* va = (const V*)A.va;
     const T* b = (const T*)A.b;
@@ -172,8 +185,8 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
                 a[0] = fma((double)r[k], (double)z, a[0]);
             }
         }
-        cluster_allsum<1>(cl, a, red, tog);  // its barrier publishes p
-        rho = a[0];
+        cluster_allsum<1>(cl, a, red, tog, [&](const double* t) { sc[0] = t[0]; });
+        rho = a[0];  // its barrier published p and sc[0] = rho
     };
     int32_t it = 0;
     double rho = 0.0;
@@ -200,10 +213,13 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
                 pq[0] = fma((double)g_s[li], (double)q[k], pq[0]);
             }
         }
-        cluster_allsum<1>(cl, pq, red, tog);
-        if (!isfinite(pq[0])) { o.status = GK_ERR_NAN; break; }
-        if (pq[0] <= 0.0) { o.status = GK_BREAKDOWN; break; }
-        const T ta = (T)(rho / pq[0]);
+        cluster_allsum<1>(cl, pq, red, tog, [&](const double* t) {
+            sc[3] = !isfinite(t[0]) ? 1.0 : t[0] <= 0.0 ? 2.0 : 0.0;
+            sc[1] = sc[0] / t[0];
+        });
+        if (sc[3] == 1.0) { o.status = GK_ERR_NAN; break; }
+        if (sc[3] == 2.0) { o.status = GK_BREAKDOWN; break; }
+        const T ta = (T)sc[1];
         double a2[2] = {0.0, 0.0};
 #pragma unroll
         for (int k = 0; k < CL_RMAX; ++k) {
@@ -216,12 +232,22 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
                 a2[1] = fma((double)r[k], (double)r[k], a2[1]);
             }
         }
-        cluster_allsum<2>(cl, a2, red, tog);
+        cluster_allsum<2>(cl, a2, red, tog, [&](const double* t) {
+            const double rn = sqrt(t[1]);
+            o.rec = rn / bn;  // thread 0 reports
+            if (!isfinite(rn) || !isfinite(t[0])) {
+                sc[3] = 1.0;
+            } else if (rn <= thr) {
+                sc[3] = 3.0;
+            } else {
+                sc[3] = 0.0;
+                sc[2] = t[0] / sc[0];
+                sc[0] = t[0];
+            }
+        });
         ++it;
-        const double rn = sqrt(a2[1]);
-        o.rec = rn / bn;
-        if (!isfinite(rn) || !isfinite(a2[0])) { o.status = GK_ERR_NAN; break; }
-        if (rn <= thr) {
+        if (sc[3] == 1.0) { o.status = GK_ERR_NAN; break; }
+        if (sc[3] == 3.0) {
             // publish x, recompute the true residual, replace r on failure
 #pragma unroll
             for (int k = 0; k < CL_RMAX; ++k) {
@@ -236,8 +262,7 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
             init_dir(rho);
             continue;
         }
-        const T tb = (T)(a2[0] / rho);
-        rho = a2[0];
+        const T tb = (T)sc[2];
 #pragma unroll
         for (int k = 0; k < CL_RMAX; ++k) {
             const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;

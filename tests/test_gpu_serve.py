@@ -71,4 +71,6 @@ def test_budget_is_respected(pool):
         assert r.event.wait(300)
     srv.close()
     assert peak[0] <= biggest * 1.5
-    assert all(r.info["status"] == 0 for r in reqs)
+    bad = [(r.rid, r.m.n, r.method, r.precision, r.precond, r.tol, r.info)
+           for r in reqs if r.info["status"] != 0]
+    assert not bad, bad
