@@ -1060,7 +1060,7 @@ static __device__ bool multidot_finish(int32_t ncol, double* partials, unsigned*
 // rows, the chunk's packs of a thread (MD_ROWS / 256 / N of them) updated
 // together so their loads of each column are in flight at once.  Returns
 // the thread's sum of squares of the new w when want_norm.
-template <typename T>
+template <typename T, int CU = 1>
 __device__ __forceinline__ T subtract_chunk(const T* __restrict__ V, int64_t ldv, T* __restrict__ wc,
                                             int64_t r0, int32_t rows, int32_t kk, const T* s_nh,
                                             bool vec, T* s_w) {
@@ -1073,7 +1073,36 @@ __device__ __forceinline__ T subtract_chunk(const T* __restrict__ V, int64_t ldv
         const int p = threadIdx.x + q * MD_THREADS;
         if (p < np) W[q] = pld(wc, p, rows, vec);
     }
-    for (int j = 0; j <= kk; ++j) {
+    // CU > 1: CU columns' loads issued before their FMAs (more bytes in
+    // flight); every element still takes its FMAs in column order
+    int j = 0;
+    if constexpr (CU > 1) {
+        for (; j + CU <= kk + 1; j += CU) {
+            Pack<T> Vj[CU][PP];
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                const T* col = V + (int64_t)(j + u) * ldv + r0;
+#pragma unroll
+                for (int q = 0; q < PP; ++q) {
+                    const int p = threadIdx.x + q * MD_THREADS;
+                    if (p < np) Vj[u][q] = pld(col, p, rows, vec);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < CU; ++u) {
+                const T hj = s_nh[j + u];
+#pragma unroll
+                for (int q = 0; q < PP; ++q) {
+                    const int p = threadIdx.x + q * MD_THREADS;
+                    if (p < np) {
+#pragma unroll
+                        for (int c = 0; c < N; ++c) W[q].v[c] = fmadd(hj, Vj[u][q].v[c], W[q].v[c]);
+                    }
+                }
+            }
+        }
+    }
+    for (; j <= kk; ++j) {
         const T* col = V + (int64_t)j * ldv + r0;
         const T hj = s_nh[j];
 #pragma unroll
@@ -1229,7 +1258,9 @@ k_gm_orth(int32_t n, int64_t ldv, const T* __restrict__ V, T* __restrict__ w, KS
     T a[1] = {T(0)};
     for (int64_t r0 = beg; r0 < end; r0 += MD_ROWS) {
         const int32_t rows = (int32_t)min((int64_t)MD_ROWS, end - r0);
-        a[0] += subtract_chunk(V, ldv, w + r0, r0, rows, kk, s_nh, vec, (T*)nullptr);
+        // 4-byte types are bound by the loads in flight, FP64 by its FMA pipe
+        a[0] += subtract_chunk<T, sizeof(T) == 4 ? 4 : 1>(V, ldv, w + r0, r0, rows, kk, s_nh, vec,
+                                                          (T*)nullptr);
     }
     finish_ew<1>(a, partials, ticket, GmGivensFin{st});
 }
