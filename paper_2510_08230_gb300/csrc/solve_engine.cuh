@@ -485,6 +485,49 @@ __global__ void EW_BOUNDS k_cg_update(int32_t n, T* __restrict__ x, T* __restric
             }
         }
     }
+    if constexpr (sizeof(T) == 8) {
+        // FP64: the next pack's loads are issued before this pack's FMAs, so
+        // that the narrow FP64 pipe works while the loads are in flight
+        // (the same packs in the same order, so the same sums)
+        if (vec && j < np) {
+            Pack<T> P = pld(p, j, n, true), Q = pld(q, j, n, true);
+            Pack<T> X = pld(x, j, n, true), R = pld(r, j, n, true);
+            Pack<T> Z = dinv ? pld(dinv, j, n, true) : Pack<T>{};
+            for (;;) {
+                const int64_t jn = j + G;
+                const bool more = jn < np;
+                Pack<T> Pn{}, Qn{}, Xn{}, Rn{}, Zn{};
+                if (more) {
+                    Pn = pld(p, jn, n, true);
+                    Qn = pld(q, jn, n, true);
+                    Xn = pld(x, jn, n, true);
+                    Rn = pld(r, jn, n, true);
+                    if (dinv) Zn = pld(dinv, jn, n, true);
+                }
+#pragma unroll
+                for (int c = 0; c < N; ++c) {  // as cg_update_pack
+                    X.v[c] = fmadd(alpha, P.v[c], X.v[c]);
+                    R.v[c] = fmadd(-alpha, Q.v[c], R.v[c]);
+                    if (dinv) {
+                        Z.v[c] = Z.v[c] * R.v[c];
+                        a[0] = fmadd(R.v[c], Z.v[c], a[0]);
+                    }
+                    a[1] = fmadd(R.v[c], R.v[c], a[1]);
+                }
+                pst(x, j, n, true, X);
+                pst(r, j, n, true, R);
+                if (dinv) pst(z, j, n, true, Z);
+                if (!more) break;
+                P = Pn;
+                Q = Qn;
+                X = Xn;
+                R = Rn;
+                Z = Zn;
+                j = jn;
+            }
+            j = np;
+        }
+    }
     for (; j < np; j += G) cg_update_pack(j, n, vec, alpha, x, r, z, p, q, dinv, a);
     finish_ew<2>(a, partials, ticket, CgUpdFin{st, pkind});
 }
