@@ -217,9 +217,15 @@ typedef struct {
     int32_t mixed;        /* 0: plain; 1: FP32 inner solves in FP64 iterative
                              refinement; 2: BF16-stored FP32 inner solves;
                              3: FP16-stored FP32 inner solves */
-    double inner_tol;     /* refinement: inner reduction (0 = 1e-5); an inner
-                             solve confirms its true residual but gives up
-                             after two residual replacements */
+    double inner_tol;     /* refinement: inner reduction (0 = 1e-2 with BF16- or
+                             FP16-stored values and for GMRES, else 1e-5); an
+                             inner solve confirms its true residual but gives up
+                             after two residual replacements.  A correction that
+                             does not reduce the FP64 true residual, or whose
+                             inner solve broke down or met a NaN, is undone and
+                             the solve finishes in FP64 from the last accepted
+                             iterate (counted as one restart; its iterations
+                             count in iters, within max_iters) */
     int32_t max_outer;    /* refinement: outer cap (0 = 50) */
     const double* batch_tols; /* gk_solve_batched only: per-system tolerances
                              (host array of `count`), NULL = tol for all */

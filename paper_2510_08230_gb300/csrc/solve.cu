@@ -273,10 +273,11 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
     // the inner solver keeps its own vectors)
     const size_t s64 = ((size_t)n * 8 + 255) & ~(size_t)255;
     const size_t s32 = ((size_t)n * 4 + 255) & ~(size_t)255;
-    GK_TRY(C->vecs.ensure(s64 + 2 * s32 + 256));
+    GK_TRY(C->vecs.ensure(2 * s64 + 2 * s32 + 256));
     double* r64 = (double*)C->vecs.ptr;
     float* r32 = (float*)((char*)C->vecs.ptr + s64);
     float* d32 = (float*)((char*)C->vecs.ptr + s64 + s32);
+    double* xb = (double*)((char*)C->vecs.ptr + s64 + 2 * s32);  // the best iterate so far
     const size_t pcount = (size_t)num_sms() * 8 * 4;
     GK_TRY(C->partials.ensure(pcount * sizeof(double)));
     double* part = (double*)C->partials.ptr;
@@ -299,11 +300,25 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
         return GK_OK;
     }
     const int max_outer = o->max_outer > 0 ? o->max_outer : 50;
-    const double inner_tol = o->inner_tol > 0 ? o->inner_tol : 1e-5;  // see the header
+    // default inner reduction (see the header): 1e-2 where the inner system is
+    // itself accurate to about that (BF16 / FP16 values) or where the inner
+    // method restarts anyway (GMRES(m)); else 1e-5
+    const double inner_tol = o->inner_tol > 0 ? o->inner_tol
+                             : (o->mixed >= 2 || o->method == GK_GMRES) ? 1e-2 : 1e-5;
     const int m = o->method == GK_GMRES ? (o->krylov_dim ? o->krylov_dim : 30) : 0;
     int32_t total_inner = 0, restarts = 0;
     double tn = 0.0, last_rec = 0.0;
     gk_status status = GK_NOT_CONVERGED;
+    // Safeguard: the iterate with the smallest true residual is kept.  A
+    // step whose true residual exceeds 4x that smallest one (an inner solve
+    // in low precision that wandered on an ill-conditioned system), is not
+    // finite, or whose inner solve broke down or met a NaN, ends the
+    // refinement: x returns to the best iterate and the solve finishes in
+    // FP64 from there.  Smaller rises are let through: refinement with a
+    // loose inner tolerance is not monotone and recovers from them.
+    constexpr double GROWTH = 4.0;
+    bool finish64 = false;
+    double best_tn = INFINITY;
     int k = 0;
     for (;; ++k) {
         // r = b - A x in FP64 (and its norm)
@@ -315,6 +330,12 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
         GK_TRY((launch_spmv_rows<double, double>(A64, x, er, s)));
         GK_TRY(read_hdr(C, s));
         tn = C->hst->tnorm;
+        if (k > 0 && !(tn <= GROWTH * best_tn)) {
+            GK_CUDA(cudaMemcpyAsync(x, xb, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            tn = best_tn;
+            finish64 = true;
+            break;
+        }
         if (!std::isfinite(tn)) {
             status = GK_ERR_NAN;
             break;
@@ -343,12 +364,36 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
         total_inner += io.iters;
         restarts += io.restarts;
         last_rec = io.rec;
-        if (io.status == GK_BREAKDOWN || io.status == GK_ERR_NAN || io.status < GK_ERR_NAN) {
+        if (tn < best_tn) {  // x (not yet corrected) is the best iterate
+            GK_CUDA(cudaMemcpyAsync(xb, x, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            best_tn = tn;
+        }
+        if (io.status == GK_BREAKDOWN || io.status == GK_ERR_NAN) {
+            if (tn > best_tn) {
+                GK_CUDA(cudaMemcpyAsync(x, xb, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                tn = best_tn;
+            }
+            finish64 = true;
+            break;
+        }
+        if (io.status < GK_ERR_NAN) {
             status = io.status;
             break;
         }
         k_cast_add<float><<<ewg(k_cast_add<float>, n), 256, 0, s>>>(n, x, d32);
         GK_CUDA(cudaGetLastError());
+    }
+    if (finish64) {
+        gk_solve_opts o64 = *o;
+        o64.mixed = 0;
+        o64.max_iters = std::max(0, o->max_iters - total_inner);
+        SolveOut fo;
+        GK_TRY((solve_plain<double, double>(A, b, x, &o64, s, &fo)));
+        status = fo.status;
+        total_inner += fo.iters;
+        restarts += fo.restarts + 1;
+        last_rec = fo.rec;
+        tn = fo.tru * bnorm;
     }
     out->status = status;
     out->iters = total_inner;

@@ -249,6 +249,36 @@ def test_mixed_precision_refinement(mixed, method):
     assert np.linalg.norm(x - xo) <= kappa * 2e-10 * np.linalg.norm(xo)
 
 
+@pytest.mark.parametrize("mixed", [1, 2])
+def test_refinement_recovers_from_a_wandering_inner_solve(mixed):
+    """On the 2D 5-point Laplacian 1024^2 (condition number ~4e5) FP32
+    BiCGSTAB inner solves wander and hand back corrections that raise the
+    residual; refinement undoes such a correction and finishes in FP64, so
+    the solve still reaches the FP64 tolerance (FP64 BiCGSTAB converges)."""
+    m = W.laplacian_2d(1024)
+    b = W.uniform_vector(m.n, W.SEED_BASE + 3)
+    x, info = _gpu_solve(m, b, "bicgstab", 1, 1e-10, max_iters=40000, dtype="mixed", mixed=mixed)
+    assert info["return"] == gk.GK_OK, info
+    assert info["restarts"] >= 1  # the FP64 finish counts as one
+    assert oracle.true_rel_residual(m, b, x) <= 1e-10
+
+
+def test_refinement_default_inner_tolerance_by_method_and_storage():
+    """The default inner reduction: 1e-5 for FP32 CG, 1e-2 for GMRES and for
+    BF16-stored values (fewer inner iterations, more outer steps); every
+    variant reaches the FP64 tolerance."""
+    m, b = CASES["diff3d_12"]()
+    for method, mixed in (("cg", 1), ("gmres", 1), ("cg", 2)):
+        x, info = _gpu_solve(m, b, method, 1, 1e-10, dtype="mixed", mixed=mixed)
+        assert info["return"] == gk.GK_OK, (method, mixed, info)
+        assert oracle.true_rel_residual(m, b, x) <= 1e-10
+        x5, info5 = _gpu_solve(m, b, method, 1, 1e-10, dtype="mixed", mixed=mixed, inner_tol=1e-5)
+        x2, info2 = _gpu_solve(m, b, method, 1, 1e-10, dtype="mixed", mixed=mixed, inner_tol=1e-2)
+        want = info2 if (mixed == 2 or method == "gmres") else info5
+        assert (info["iters"], info["outer_iters"]) == (want["iters"], want["outer_iters"])
+        assert np.array_equal(x, x2 if want is info2 else x5)
+
+
 def test_config3_full_size_jacobi_cg_and_refinement():
     """128^3 log-normal diffusion: Jacobi-CG in FP64 and FP32-refined CG both
     reach a true residual of 1e-10 (oracle SpMV on the GPU's x)."""
