@@ -221,11 +221,13 @@ typedef struct {
                              FP16-stored values and for GMRES, else 1e-5); an
                              inner solve confirms its true residual but gives up
                              after two residual replacements.  A correction that
-                             does not reduce the FP64 true residual, or whose
-                             inner solve broke down or met a NaN, is undone and
-                             the solve finishes in FP64 from the last accepted
-                             iterate (counted as one restart; its iterations
-                             count in iters, within max_iters) */
+                             raises the FP64 true residual above 4x the best
+                             so far, or whose inner solve broke down or met a
+                             NaN, and three outer steps that together gain less
+                             than 2x, end the refinement: the solve finishes in
+                             FP64 from the best iterate (counted as one
+                             restart; its iterations count in iters, within
+                             max_iters) */
     int32_t max_outer;    /* refinement: outer cap (0 = 50) */
     const double* batch_tols; /* gk_solve_batched only: per-system tolerances
                              (host array of `count`), NULL = tol for all */

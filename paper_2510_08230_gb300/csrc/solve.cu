@@ -315,10 +315,15 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
     // finite, or whose inner solve broke down or met a NaN, ends the
     // refinement: x returns to the best iterate and the solve finishes in
     // FP64 from there.  Smaller rises are let through: refinement with a
-    // loose inner tolerance is not monotone and recovers from them.
+    // loose inner tolerance is not monotone and recovers from them.  So does
+    // stagnation: three outer steps that together cut the smallest residual
+    // by less than 2x (inner solves that stop early on a system the low
+    // precision cannot resolve).
     constexpr double GROWTH = 4.0;
+    constexpr int STAG_STEPS = 3;
     bool finish64 = false;
     double best_tn = INFINITY;
+    std::vector<double> best_hist;  // best_tn before each outer step
     int k = 0;
     for (;; ++k) {
         // r = b - A x in FP64 (and its norm)
@@ -336,6 +341,15 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
             finish64 = true;
             break;
         }
+        if (k >= STAG_STEPS && tn > thr &&
+            std::min(tn, best_tn) > 0.5 * best_hist[(size_t)(k - STAG_STEPS)]) {
+            if (tn > best_tn) {
+                GK_CUDA(cudaMemcpyAsync(x, xb, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                tn = best_tn;
+            }
+            finish64 = true;
+            break;
+        }
         if (!std::isfinite(tn)) {
             status = GK_ERR_NAN;
             break;
@@ -345,6 +359,7 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
             break;
         }
         if (k >= max_outer || total_inner >= o->max_iters) break;
+        best_hist.push_back(std::min(tn, best_tn));
         k_cast_to<float><<<ewg(k_cast_to<float>, n), 256, 0, s>>>(n, r64, r32);
         k_zero<float><<<ewg(k_zero<float>, n), 256, 0, s>>>(n, d32);
         GK_CUDA(cudaGetLastError());

@@ -263,6 +263,20 @@ def test_refinement_recovers_from_a_wandering_inner_solve(mixed):
     assert oracle.true_rel_residual(m, b, x) <= 1e-10
 
 
+def test_refinement_hands_a_stagnating_solve_to_fp64():
+    """Block-Jacobi(8) GMRES(30) on the 2D Laplacian 512^2: FP32 inner GMRES
+    solves stop early and the refinement gains ~15 % per outer step; after
+    three such steps the solve finishes in FP64 (which converges) instead of
+    running into the outer cap."""
+    m = W.laplacian_2d(512)
+    b = W.uniform_vector(m.n, W.SEED_BASE + 3)
+    x, info = _gpu_solve(m, b, "gmres", 2, 1e-10, max_iters=20000, dtype="mixed", mixed=1,
+                         block_size=8)
+    assert info["return"] == gk.GK_OK, info
+    assert info["outer_iters"] < 50
+    assert oracle.true_rel_residual(m, b, x) <= 1e-10
+
+
 def test_refinement_default_inner_tolerance_by_method_and_storage():
     """The default inner reduction: 1e-5 for FP32 CG, 1e-2 for GMRES and for
     BF16-stored values (fewer inner iterations, more outer steps); every
