@@ -192,7 +192,7 @@ def cpu_baseline(lap, seconds=12.0):
         _, threads = oracle.spmv_omp(lap, x, 0, y=y, arrays=(rp, ci, va))
         reps += 1
         el = time.perf_counter() - t0
-        if el >= seconds or reps >= 200:
+        if el >= seconds or reps >= 5000:
             break
     gbs = alg_bytes(lap, 8, "csr") * reps / el / 1e9
     return {"value": round(gbs, 2), "unit": "GB/s", "cores": int(threads), "kind": "oracle",
