@@ -527,7 +527,10 @@ def profile_case(name, dtype):
                steps) on the 128^3 diffusion problem (solver kernels: SpMV
                epilogues, fused updates, multi-dots)
       ilu      ILU(0) of the 2D 5-point Laplacian 512^2 and three
-               applications (the substitution kernels k_ilu_trsv)"""
+               applications (the substitution kernels k_ilu_trsv)
+      ilu_banded
+               the same on a banded SPD matrix (n = 2^15, half-bandwidth
+               48: every row depends on the one before it)"""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -535,15 +538,15 @@ def profile_case(name, dtype):
     from paper_2510_08230_gb300 import workloads as W
     dev = torch.device("cuda:0")
     vt = torch.float64 if dtype == "f64" else torch.float32
-    if name == "ilu":
-        m = W.laplacian_2d(512)
+    if name in ("ilu", "ilu_banded"):
+        m = W.laplacian_2d(512) if name == "ilu" else W.banded_spd(1 << 15, 48, 3)
         A = gk.Matrix.from_csr(m, dtype)
         r = torch.from_numpy(W.uniform_vector(m.n, W.SEED_BASE + 3)).to(dev, vt)
         z = torch.empty_like(r)
         for _ in range(3):
             A.precond_apply(r, z, "ilu")
         torch.cuda.synchronize()
-        print("profile case ilu", dtype, m.n, m.nnz)
+        print("profile case", name, dtype, m.n, m.nnz)
         A.close()
         return 0
     if name in ("cg", "bicgstab", "gmres"):
@@ -627,7 +630,7 @@ def main():
     ap.add_argument("--no-solvers", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--profile-case", choices=["merge", "coo", "rowtile", "ell", "sellp", "cg",
-                                               "bicgstab", "gmres", "ilu"],
+                                               "bicgstab", "gmres", "ilu", "ilu_banded"],
                     help="run one small case for an ncu capture and exit")
     ap.add_argument("--profile-dtype", default="f64", choices=["f64", "f32"])
     args = ap.parse_args()
