@@ -102,7 +102,7 @@ def build_items(gk, W, dtypes=("f64", "f32")):
 
 
 KERNEL_NAMES = {0: "k_csr_vector", 1: "k_csr_rowtile", 2: "k_csr_merge_reg", 3: "k_ell",
-                4: "k_sellp", 5: "k_coo_warp"}
+                4: "k_sellp", 5: "k_coo_warp", 6: "k_csr_warptile"}
 
 
 class ClockSampler:
@@ -200,7 +200,128 @@ def cpu_baseline(lap, seconds=12.0):
                       f"OpenMP oracle, plain sum), {el:.1f} s"}
 
 
-def cg_solves_per_s(gk, W, torch, dev, reps=20):
+def _x_err(x, xo):
+    d = float(np.linalg.norm(xo))
+    return float(np.linalg.norm(np.asarray(x, np.float64) - xo) / d) if d > 0 else None
+
+
+def oracle_legs(W, lap, keep, budget_s=60.0):
+    """The CPU oracle beside the GPU results (rank 0, one replica only):
+    - SpMV of the 256^3 Laplacian on one host thread (the OpenMP timing is
+      cpu_baseline);
+    - CG, BiCGSTAB and GMRES(30) to 1e-10 on the 64x64 Laplacian (no
+      preconditioner, run to the end) and with Jacobi on the 128^3 diffusion
+      matrix (CG run to the end; BiCGSTAB and GMRES(30) timed over a bounded
+      number of iterations and extrapolated to the iteration count the GPU's
+      FP64 solve needed);
+    - a loop of oracle Jacobi-CG solves over the first batched systems for
+      a bounded time, extrapolated to all 2048 by rows;
+    - for every GPU solution kept by the solver legs: the true relative
+      residual ||b - A x|| / ||b|| recomputed with the oracle's compensated
+      SpMV, and ||x - x_oracle|| / ||x_oracle|| against the oracle's own
+      solution of the same system (Jacobi-CG to 1e-10)."""
+    import oracle
+    t_start = time.perf_counter()
+    out = {"kind": "oracle", "cores_spmv_single": 1}
+    # single-thread SpMV
+    rp = np.ascontiguousarray(lap.row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(lap.col_idx, dtype=np.int32)
+    va = np.ascontiguousarray(lap.values, dtype=np.float64)
+    xv = np.random.default_rng(1).uniform(-1, 1, lap.n)
+    yv = np.zeros(lap.n)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.spmv_omp(lap, xv, 1, y=yv, arrays=(rp, ci, va))
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= 4.0:
+            break
+    out["spmv_single_thread"] = {
+        "GB_s": round(alg_bytes(lap, 8, "csr") * reps / el / 1e9, 2), "reps": reps,
+        "s": round(el, 2), "workload": "FP64 CSR SpMV of the 3D 7-point 256^3 Laplacian, 1 thread"}
+    # config 1: the 64x64 Laplacian, no preconditioner
+    m1 = W.laplacian_2d(64)
+    b1 = W.uniform_vector(m1.n, W.SEED_BASE + 1)
+    c1 = {}
+    x1o = None
+    for name, meth in (("cg", oracle.CG), ("bicgstab", oracle.BICGSTAB), ("gmres30", oracle.GMRES)):
+        t0 = time.perf_counter()
+        xo, io = oracle.solve(m1, b1, method=meth, tol=1e-10, max_iters=20000, krylov_dim=30)
+        el = time.perf_counter() - t0
+        c1[name] = {"ms": round(el * 1000, 3), "iters": io["iters"], "status": io["status"],
+                    "rel_res_true": io["rel_res_true"], "solves_per_s": round(1.0 / el, 1)}
+        if name == "cg":
+            x1o = xo
+    out["laplacian_64x64"] = c1
+    # config 3: 128^3 diffusion with Jacobi
+    m3 = W.diffusion_3d(128)
+    b3 = W.uniform_vector(m3.n, W.SEED_BASE + 3)
+    c3 = {}
+    t0 = time.perf_counter()
+    x3o, io = oracle.solve(m3, b3, method=oracle.CG, precond=1, tol=1e-10, max_iters=20000)
+    el = time.perf_counter() - t0
+    c3["cg_jacobi"] = {"s": round(el, 2), "iters": io["iters"], "status": io["status"],
+                       "rel_res_true": io["rel_res_true"], "ms_per_iter": round(el * 1e3 / max(io["iters"], 1), 2),
+                       "how": "run to the end"}
+    for name, meth, gpu_key in (("bicgstab_jacobi", oracle.BICGSTAB, "ir_128cubed/bicgstab/fp64"),
+                                ("gmres30_jacobi", oracle.GMRES, "ir_128cubed/gmres/fp64")):
+        k = 30
+        t0 = time.perf_counter()
+        _, io = oracle.solve(m3, b3, method=meth, precond=1, tol=1e-10, max_iters=k, krylov_dim=30)
+        el = time.perf_counter() - t0
+        per = el / max(io["iters"], 1)
+        gpu_iters = keep.get(gpu_key, (None, {}))[1].get("iters")
+        c3[name] = {"ms_per_iter": round(per * 1e3, 2), "sample_iters": io["iters"],
+                    "gpu_fp64_iters": gpu_iters,
+                    "s_extrapolated": round(per * gpu_iters, 1) if gpu_iters else None,
+                    "how": f"extrapolated: {io['iters']} oracle iterations timed, x the GPU "
+                           "FP64 solve's iteration count"}
+    out["diffusion_128cubed"] = c3
+    # batched: oracle Jacobi-CG loop over the systems, bounded time
+    mats, rhs = W.batched_rectangles(2048, seed=W.SEED_BASE + 4)
+    xs_gpu = keep.get("batched_2048/f64")
+    rows_done, done, errs, res = 0, 0, [], []
+    t0 = time.perf_counter()
+    for i, (m, b) in enumerate(zip(mats, rhs)):
+        xo, io = oracle.solve(m, b, method=oracle.CG, precond=1, tol=1e-10, max_iters=20000)
+        rows_done += m.n
+        done += 1
+        if xs_gpu is not None:
+            errs.append(_x_err(xs_gpu[i], xo))
+            res.append(oracle.true_rel_residual(m, b, xs_gpu[i]))
+        if time.perf_counter() - t0 >= 12.0:
+            break
+    el = time.perf_counter() - t0
+    total_rows = sum(m.n for m in mats)
+    out["batched_2048"] = {
+        "systems_timed": done, "s": round(el, 2),
+        "s_extrapolated_all": round(el * total_rows / rows_done, 1),
+        "how": "sequential oracle Jacobi-CG (FP64, 1e-10) loop over the first systems; "
+               "extrapolated to all 2048 by rows",
+        "gpu_batched_f64_max_rel_res_true_oracle": max(res) if res else None,
+        "gpu_batched_f64_max_x_err_vs_oracle": max(errs) if errs else None,
+        "systems_checked": len(errs)}
+    # oracle error of every kept GPU solution
+    checks = {}
+    for key, val in keep.items():
+        if key == "batched_2048/f64":
+            continue
+        x, rec = val
+        if key.startswith("cg/"):
+            m, b, xo = m1, b1, x1o
+        else:
+            m, b, xo = m3, b3, x3o
+        checks[key] = {"rel_res_true_oracle": oracle.true_rel_residual(m, b, x),
+                       "x_err_vs_oracle": _x_err(x, xo),
+                       "gpu_rel_res_true": rec.get("rel_res_true")}
+        rec["rel_res_true_oracle"] = checks[key]["rel_res_true_oracle"]
+        rec["x_err_vs_oracle"] = checks[key]["x_err_vs_oracle"]
+    out["gpu_results_vs_oracle"] = checks
+    out["total_s"] = round(time.perf_counter() - t_start, 1)
+    return out
+
+
+def cg_solves_per_s(gk, W, torch, dev, reps=20, keep=None):
     m = W.laplacian_2d(64)
     b = torch.from_numpy(W.uniform_vector(m.n, W.SEED_BASE + 1)).to(dev)
     A = gk.Matrix.from_csr(m)
@@ -218,9 +339,11 @@ def cg_solves_per_s(gk, W, torch, dev, reps=20):
             iters = info["iters"]
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        out[{1: "multi_kernel", 2: "single_block", 3: "cluster"}[engine]] = {
-            "solves_per_s": round(reps / el, 1), "iters": iters,
-            "rel_res_true": info["rel_res_true"]}
+        tag = {1: "multi_kernel", 2: "single_block", 3: "cluster"}[engine]
+        out[tag] = {"solves_per_s": round(reps / el, 1), "iters": iters,
+                    "rel_res_true": info["rel_res_true"]}
+        if keep is not None:
+            keep[f"cg/{tag}"] = (x.cpu().numpy(), out[tag])
     A.close()
     best = max(out.values(), key=lambda v: v["solves_per_s"])
     return {"solves_per_s": best["solves_per_s"], "workload": "2D 5-point 64x64 FP64 CG to 1e-10, "
@@ -241,7 +364,7 @@ def time_apply(it, stream, torch, reps=3):
     return e0.elapsed_time(e1) / reps
 
 
-def ir_compare(gk, W, torch, dev):
+def ir_compare(gk, W, torch, dev, keep=None):
     """128^3 log-normal diffusion: wall time to a true 1e-10 residual,
     FP32 inner solves in FP64 refinement vs plain FP64 (Jacobi-CG,
     Jacobi-GMRES(30) and Jacobi-CGS)."""
@@ -250,7 +373,7 @@ def ir_compare(gk, W, torch, dev):
     A = gk.Matrix.from_csr(m)
     out = {"workload": "128^3 7-point diffusion, exp(N(0,1)) cells, harmonic faces; "
                        "b ~ U[-1,1] seed 2513; x0 = 0; tol 1e-10 (true residual)"}
-    for method in ("cg", "gmres", "cgs"):
+    for method in ("cg", "bicgstab", "gmres", "cgs"):
         res = {}
         for mixed in (0, 1, 2):
             x = torch.zeros_like(b)
@@ -263,9 +386,12 @@ def ir_compare(gk, W, torch, dev):
                            mixed=mixed)
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
-            res[{0: "fp64", 1: "fp32_ir", 2: "bf16_ir"}[mixed]] = {
+            tag = {0: "fp64", 1: "fp32_ir", 2: "bf16_ir"}[mixed]
+            res[tag] = {
                 "ms": round(el * 1000, 2), "status": info["return"], "iters": info["iters"],
                 "outer": info["outer_iters"], "rel_res_true": info["rel_res_true"]}
+            if keep is not None:
+                keep[f"ir_128cubed/{method}/{tag}"] = (x.cpu().numpy(), res[tag])
         res["speedup_fp32_ir"] = round(res["fp64"]["ms"] / res["fp32_ir"]["ms"], 3)
         out[method] = res
     A.close()
@@ -297,7 +423,7 @@ def per_iteration_protocol(gk, W, torch, dev, iters=1000):
     return out
 
 
-def precond_compare(gk, W, torch, dev):
+def precond_compare(gk, W, torch, dev, keep=None):
     """CG and GMRES(30) to a true 1e-10 on the 128^3 diffusion matrix (FP64)
     without a preconditioner, with Jacobi, with block-Jacobi of 4, 8 and 16
     rows, and with ILU(0): iterations and wall time (host clock around the
@@ -326,6 +452,8 @@ def precond_compare(gk, W, torch, dev):
             res[label] = {"ms": round((time.perf_counter() - t0) * 1000, 2),
                           "iters": info["iters"], "status": info["return"],
                           "rel_res_true": info["rel_res_true"]}
+            if keep is not None:
+                keep[f"preconditioners/{method}/{label}"] = (x.cpu().numpy(), res[label])
         out[method] = res
     A.close()
     apply_us = {}
@@ -402,7 +530,7 @@ def abi_overhead(gk, W, torch, dev):
     return out
 
 
-def batched_compare(gk, W, torch, dev, count=2048):
+def batched_compare(gk, W, torch, dev, count=2048, keep=None):
     """2048 shifted-rectangle SPD systems (64-4096 rows): one persistent
     launch vs a per-system gk_solve loop, CG to 1e-10, FP64 and FP32."""
     mats, rhs = W.batched_rectangles(count, seed=W.SEED_BASE + 4)
@@ -424,6 +552,8 @@ def batched_compare(gk, W, torch, dev, count=2048):
         torch.cuda.synchronize()
         t_batch = time.perf_counter() - t0
         ok = sum(1 for i in infos if i["status"] == 0)
+        if keep is not None and dt == "f64":
+            keep["batched_2048/f64"] = [x.cpu().numpy() for x in xs]
         for x in xs:
             x.zero_()
         torch.cuda.synchronize()
@@ -443,17 +573,18 @@ def batched_compare(gk, W, torch, dev, count=2048):
     return out
 
 
-def serving_bench(gk, W, torch, dev, n_req=240, factors=(0.5, 0.8, 0.95)):
+def serving_bench(gk, W, torch, dev, n_req=240, factors=((0.5, 400), (0.8, 2000), (0.95, 400))):
     """Config 5: Poisson arrivals of solve requests (2D/3D stencils and
     banded SPD, n log-uniform 1e3..1e6, FP64 or FP32-refined 50/50, tol
     log-uniform 1e-10..1e-8) under a 40 GB budget.  Saturation throughput is
-    measured with a burst of n_req requests; then n_req requests arrive at
-    0.5 / 0.8 / 0.95 x saturation.  Latency = submit -> x back on the host."""
+    measured with a burst of n_req requests; then (rate factor, count)
+    requests arrive at 0.5 / 0.8 / 0.95 x saturation (2000 at 0.8, so that
+    its p99 rests on 20 samples).  Latency = submit -> x back on the host."""
     import threading
     from paper_2510_08230_gb300.serve import SolveRequest, SolveServer
     pool = W.serving_pool(24)
     rng = np.random.default_rng(W.SEED_BASE + 5)
-    params = W.serving_requests(pool, n_req * (len(factors) + 1))
+    params = W.serving_requests(pool, n_req + sum(c for _, c in factors))
     rhs = {}
 
     def make(rid):
@@ -464,7 +595,7 @@ def serving_bench(gk, W, torch, dev, n_req=240, factors=(0.5, 0.8, 0.95)):
         return SolveRequest(rid, mi, pool[mi], rhs[key], tol=tol, precision=prec)
 
     reqs = [make(i) for i in range(len(params))]
-    srv = SolveServer(budget_bytes=40e9, workers=6)
+    srv = SolveServer(budget_bytes=40e9, workers=6, long_workers=2)
     # warm-up: every pool matrix once per precision (uploads, plans, graphs)
     warm = []
     for mi, m in enumerate(pool):
@@ -474,7 +605,9 @@ def serving_bench(gk, W, torch, dev, n_req=240, factors=(0.5, 0.8, 0.95)):
         r.event.wait(600)
     out = {"workload": "24-matrix pool (2D 5-pt / 3D 7-pt / banded SPD w 5..64, n log-uniform "
                        "1e3..1e6), FP64 or FP32-refined 50/50, tol 1e-10..1e-8, Jacobi-CG, "
-                       f"40 GB budget, 6 worker streams, {n_req} requests per rate"}
+                       "40 GB budget, 6 worker streams (2 for long solves), "
+                       f"{n_req}-request burst, " +
+                       ", ".join(f"{c} requests at {f}x" for f, c in factors)}
     burst = reqs[:n_req]
     t0 = time.perf_counter()
     for r in burst:
@@ -484,8 +617,10 @@ def serving_bench(gk, W, torch, dev, n_req=240, factors=(0.5, 0.8, 0.95)):
     t1 = time.perf_counter()
     sat = n_req / (t1 - t0)
     out["saturation"] = SolveServer.summarize(burst, t0, t1)
-    for k, f in enumerate(factors):
-        batch = reqs[n_req * (k + 1):n_req * (k + 2)]
+    start = n_req
+    for f, cnt in factors:
+        batch = reqs[start:start + cnt]
+        start += cnt
         gaps = rng.exponential(1.0 / (f * sat), size=len(batch))
         arrive = np.cumsum(gaps)
 
@@ -520,6 +655,7 @@ def profile_case(name, dtype):
       merge    CSR merge path, Zipf(1.8) power-law n=2^21 (~33M nnz)
       coo      COO of the same power-law matrix
       rowtile  CSR row tiles, 3D 7-point Laplacian 128^3 (14.6M nnz)
+      warptile CSR warp tiles, the same Laplacian
       ell      ELL of the same Laplacian
       sellp    SELL-P(32) of the same Laplacian
       cg, bicgstab, gmres
@@ -563,7 +699,7 @@ def profile_case(name, dtype):
         os.environ["GK_CSR_KERNEL"] = "2"
         m = W.power_law(1 << 21, seed=W.SEED_BASE + 2)
     else:
-        os.environ["GK_CSR_KERNEL"] = "1"
+        os.environ["GK_CSR_KERNEL"] = "3" if name == "warptile" else "1"
         m = W.laplacian_3d(128)
     A = gk.Matrix.from_csr(m, dtype)
     if name in ("ell", "sellp", "coo"):
@@ -576,7 +712,7 @@ def profile_case(name, dtype):
         A.apply(x, y)
     torch.cuda.synchronize()
     print("profile case", name, dtype, KERNEL_NAMES[A.desc["spmv_kernel"]], m.n, m.nnz,
-          alg_bytes(m, 8 if dtype == "f64" else 4, "csr" if name in ("merge", "rowtile") else name))
+          alg_bytes(m, 8 if dtype == "f64" else 4, "csr" if name in ("merge", "rowtile", "warptile") else name))
     A.close()
     return 0
 
@@ -629,7 +765,8 @@ def main():
     ap.add_argument("--no-cg", action="store_true")
     ap.add_argument("--no-solvers", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--profile-case", choices=["merge", "coo", "rowtile", "ell", "sellp", "cg",
+    ap.add_argument("--profile-case", choices=["merge", "coo", "rowtile", "warptile", "ell",
+                                               "sellp", "cg",
                                                "bicgstab", "gmres", "ilu", "ilu_banded"],
                     help="run one small case for an ncu capture and exit")
     ap.add_argument("--profile-dtype", default="f64", choices=["f64", "f32"])
@@ -717,27 +854,41 @@ def main():
     for it in items:
         ms = time_apply(it, stream, torch, reps=max(3, args.steps))
         gbs = it["bytes"] / (ms / 1000.0) / 1e9
+        csr_gbs = it["csr_bytes"] / (ms / 1000.0) / 1e9
         sweep.append({"item": it["name"], "kernel": KERNEL_NAMES[it["kernel"]],
                       "us": round(ms * 1000, 1), "GB_s": round(gbs, 1),
                       "frac_of_measured_hbm": round(gbs / peak, 3),
+                      "csr_alg_GB_s": round(csr_gbs, 1),
+                      "csr_alg_frac": round(csr_gbs / peak, 3),
                       "frac_of_8TBs_nominal": round(gbs / 8000.0, 3),
                       "in_step": it in step_items})
-    # dominant kernel: largest share of the step's device time
+    # dominant kernel: largest share of the step's device time.  Its
+    # algorithmic bytes are the unpadded CSR matrix with x and y once
+    # (whatever format ran); the format's own bytes (COO's row index of
+    # every entry, padding excluded) are reported beside them.
     k_dom = max(range(len(step_items)), key=lambda k: per_item_ms[k])
     dom = step_items[k_dom]
-    dom_gbs = dom["bytes"] / (per_item_ms[k_dom] / 1000.0) / 1e9
+    dom_s = per_item_ms[k_dom] / 1000.0
+    dom_gbs = dom["csr_bytes"] / dom_s / 1e9
+    traffic = traffic_for(KERNEL_NAMES[dom["kernel"]], dom["name"])
     roofline = {"bound": "hbm", "achieved": round(dom_gbs, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(dom_gbs / peak, 3),
-                "traffic": traffic_for(KERNEL_NAMES[dom["kernel"]], dom["name"]),
+                "traffic": traffic,
                 "kernel": KERNEL_NAMES[dom["kernel"]], "item": dom["name"],
                 "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "algorithmic_bytes_per_launch": dom["bytes"],
+                "algorithmic_bytes_per_launch": dom["csr_bytes"],
+                "algorithmic_bytes_rule": "CSR: nnz*(sv+4) + 4(n+1) + n*sv (x) + n*sv (y)",
+                "format_bytes_per_launch": dom["bytes"],
+                "format_frac": round(dom["bytes"] / dom_s / 1e9 / peak, 3),
+                "traffic_over_algorithmic": (round(traffic / dom["csr_bytes"], 3)
+                                             if traffic else None),
                 "mean_launch_us": round(per_item_ms[k_dom] * 1000, 1),
                 "share_of_step": round(per_item_ms[k_dom] / sum(per_item_ms), 3)}
     step_detail = [{"item": it["name"], "kernel": KERNEL_NAMES[it["kernel"]],
-                    "us": round(ms * 1000, 1), "GB_s": round(it["bytes"] / (ms / 1000.0) / 1e9, 1),
-                    "frac_of_measured_hbm": round(it["bytes"] / (ms / 1000.0) / 1e9 / peak, 3)}
+                    "us": round(ms * 1000, 1),
+                    "GB_s": round(it["csr_bytes"] / (ms / 1000.0) / 1e9, 1),
+                    "frac_of_measured_hbm": round(it["csr_bytes"] / (ms / 1000.0) / 1e9 / peak, 3)}
                    for it, ms in zip(step_items, per_item_ms)]
 
     # e2e: the same step through the C ABI with pinned HOST buffers (H2D of
@@ -783,20 +934,23 @@ def main():
     del items, step_items
     torch.cuda.empty_cache()
 
-    cg = ir = batched = serving = per_iter = abi = pre = None
+    cg = ir = batched = serving = per_iter = abi = pre = orc = None
+    keep = {}
     if rank == 0 and not args.no_cg:
-        cg = cg_solves_per_s(gk, W, torch, dev)
+        cg = cg_solves_per_s(gk, W, torch, dev, keep=keep)
     if rank == 0 and not args.no_solvers:
-        ir = ir_compare(gk, W, torch, dev)
+        ir = ir_compare(gk, W, torch, dev, keep=keep)
         per_iter = per_iteration_protocol(gk, W, torch, dev)
         abi = abi_overhead(gk, W, torch, dev)
-        pre = precond_compare(gk, W, torch, dev)
-        batched = batched_compare(gk, W, torch, dev)
+        pre = precond_compare(gk, W, torch, dev, keep=keep)
+        batched = batched_compare(gk, W, torch, dev, keep=keep)
     if rank == 0 and not args.no_serving:
         serving = serving_bench(gk, W, torch, dev)
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         cpu = cpu_baseline(lap)
+        orc = oracle_legs(W, lap, keep)
+    del keep
     line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
@@ -805,7 +959,7 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "step": step_detail, "sweep": sweep, "roofline": roofline, "cpu_baseline": cpu,
             "e2e": e2e, "cg": cg, "ir_128cubed": ir, "per_iteration_1000": per_iter,
-            "abi_overhead": abi, "preconditioners": pre,
+            "abi_overhead": abi, "preconditioners": pre, "oracle": orc,
             "batched_2048": batched,
             "serving": serving, "clocks": clk,
             "gpu_launches": launches}

@@ -122,10 +122,15 @@ typedef struct {
     int64_t stored;        /* entries held in col/values incl. padding */
     int64_t device_bytes;  /* bytes of the format arrays on the device */
     int32_t spmv_kernel;   /* SpMV kernel apply uses: 0 CSR vector, 1 CSR row-tile,
-                              2 CSR merge-path, 3 ELL, 4 SELL-P, 5 COO */
+                              2 CSR merge-path, 3 ELL, 4 SELL-P, 5 COO,
+                              6 CSR warp-tile */
     int32_t spmv_launches; /* kernel launches per apply */
-    int32_t device_error;  /* 1 if a kernel on this matrix gave up a bounded
-                              device-side wait (its results are invalid) */
+    int32_t device_error;  /* nonzero if a kernel on this matrix gave up a
+                              bounded device-side wait, so its results are
+                              invalid: bit 0 the CSR row-tile SpMV (since the
+                              last gk_solve began, which clears it), bit 1 the
+                              last ILU(0) application, bit 2 the last
+                              gk_triangular_solve */
     int32_t solve_format;  /* layout the solvers' SpMV uses on this matrix: -1
                               until the first gk_solve picks it (CSR matrices
                               may solve on an ELL or SELL-P copy), else a
@@ -238,6 +243,13 @@ typedef struct {
                              cluster can be scheduled, else 1.  Block-Jacobi,
                              ILU(0) and CGS run on engine 1 only. */
     int32_t block_size;   /* block-Jacobi rows per diagonal block, 1..32 */
+    int64_t wait_budget_ns; /* longest a device-side wait of this solve may last
+                             (the ILU(0) substitutions' polls on values other
+                             warps produce, the CSR row-tile kernel's waits on
+                             its staged copies) before it gives up: the solve
+                             then returns GK_ERR_TIMEOUT and x holds no valid
+                             iterate.  0 = the default of 2 s; negative values
+                             are GK_ERR_INVALID */
 } gk_solve_opts;
 
 typedef struct {
@@ -248,6 +260,11 @@ typedef struct {
     double rel_res_recurrence;/* last recurrence / Givens estimate over ||b|| */
     double rel_res_true;      /* ||b - A x||_2 / ||b||_2 recomputed at exit */
     float device_ms;          /* device time of the solve (CUDA events) */
+    int32_t spmv_format;      /* layout the solve's SpMV ran on (GK_CSR, GK_ELL or
+                                 GK_SELLP; refinement: the FP64 residual's) */
+    int32_t slice_size;       /* SELL-P slice size of that layout, else 0 */
+    int32_t block_threads;    /* threads per block of the single-block engine and
+                                 of gk_solve_batched (autotuned), else 0 */
 } gk_solve_info;
 
 /* Solve A x = b for square A (Listing 1: solver.apply(b, x) overwrites
@@ -262,10 +279,18 @@ typedef struct {
  * b, x: device pointers of n entries (x in/out, the initial guess).
  * info may be NULL.  Blocks until the solve is finished (one stream
  * synchronise); everything is enqueued on `stream`.
- * SpMV layout (multi-kernel engine and refinement on a CSR matrix): the first
- * solve keeps an ELL copy of A when ELL stores at most 1.2 x nnz entries,
- * else a SELL-P(32) copy under the same bound, else uses the CSR kernels; the
- * copy lives with the handle (gk_matrix_desc.solve_format reports the pick).
+ * On the multi-kernel engine the Krylov loop runs on the device: one CUDA
+ * graph (built on the first solve with a given method, preconditioner and
+ * Krylov dimension, then kept with the handle) repeats chunks of iterations
+ * in a conditional loop node, with the confirmation of a passed recurrence
+ * residual and the residual replacement decided by kernels; the host only
+ * reads the outcome.  The solve works on the handle's own copies of b and x.
+ * SpMV layout (multi-kernel engine and refinement on a CSR matrix): a matrix
+ * whose apply uses the CSR warp-tile kernel (gk_matrix_desc.spmv_kernel 6)
+ * solves on its own arrays; otherwise the first solve keeps an ELL copy of A
+ * when ELL stores at most 1.2 x nnz entries, else a SELL-P(32) copy under the
+ * same bound, else uses the CSR kernels; the copy lives with the handle
+ * (gk_matrix_desc.solve_format reports the pick).
  * The rule reads only the sparsity pattern, so results are reproducible
  * across handles.  Environment GK_SOLVE_FORMAT=csr|ell|sellp forces a layout,
  * =timed picks the fastest of three timed SpMVs per admissible layout. */
@@ -273,14 +298,43 @@ gk_status gk_solve(gk_matrix A, const void* b, void* x,
                    const gk_solve_opts* opts, gk_solve_info* info,
                    void* stream);
 
+/* The same solve as gk_solve, enqueued on `stream` without waiting for it:
+ * the call returns once the work is enqueued and the outcome arrives in
+ * `info`, a DEVICE pointer to one gk_solve_info the caller owns, when the
+ * solve's work on the stream completes (device_ms is 0; read info after
+ * synchronising the stream or an event recorded after the call).  x holds
+ * the solution at the same point.  This is the serving form of the solver
+ * LinOp (Listing 1): a thread can enqueue many solves and never wait on any.
+ * The whole Krylov loop runs on the device (one CUDA graph whose
+ * conditional loop node repeats the iterations and the stopping test, see
+ * gk_solve), on the multi-kernel engine for every matrix size.  The first
+ * solve of a matrix builds what it needs (preconditioner, solver layout,
+ * the graph) and synchronises `stream` while doing so; later solves with
+ * the same method, preconditioner and Krylov dimension only enqueue.
+ * Solves on one matrix must be ordered (the same stream, or synchronised):
+ * the handle's workspace serves one solve at a time.  Refinement (mixed != 0)
+ * is GK_ERR_UNSUPPORTED here: its outer loop runs on the host.  Argument
+ * errors are returned at once like gk_solve's; the solve's own status
+ * (convergence, breakdown, a timed-out wait) is in info->status. */
+gk_status gk_solve_async(gk_matrix A, const void* b, void* x,
+                         const gk_solve_opts* opts, gk_solve_info* info, void* stream);
+
 /* Solve `count` independent systems As[i] x_i = b_i in one launch, one
- * thread block per system, whole iteration inside the kernel.  The block
- * size (128/256/512 threads) is autotuned per batch shape on the first call
- * for that shape (value type, method, preconditioner, log2 of the largest n
- * and of the count): each candidate runs the batch capped at 30 iterations
- * from the callers' initial guesses, which are restored afterwards; the
- * choice is cached for the process.  GK_AUTOTUNE=0 disables tuning
- * (256 threads), GK_BATCH_THREADS forces a size.  All
+ * thread block per system, whole iteration inside the kernel.  Each system's
+ * SpMV runs on a layout built for the call (one conversion launch for the
+ * whole batch): its CSR arrays, an ELL copy (where ELL stores at most 1.2 x
+ * its nonzeros) or a SELL-P copy with slices of S rows; every layout sums a
+ * row in CSR order, so the layout never changes a result.  The layout
+ * policy (CSR, ELL, SELL-P with S = 8, 16 or 32) and the block size
+ * (128/256/512 threads) are autotuned per batch shape on the first call for
+ * that shape (value type, method, preconditioner, log2 of the largest n and
+ * of the count): each candidate runs the batch capped at 30 iterations from
+ * the callers' initial guesses, which are restored afterwards; the choice
+ * is cached for the process and reported per system in infos (spmv_format,
+ * slice_size, block_threads).  Batches of fewer than 8 systems, or with
+ * GK_AUTOTUNE=0, use ELL where it pads little and 256 threads;
+ * GK_BATCH_LAYOUT (csr | ell | sellp8 | sellp16 | sellp32 | sellp64) and
+ * GK_BATCH_THREADS force either choice.  All
  * matrices must be CSR, square, of the same dtype, with n <= 16384; CG
  * and BiCGSTAB (GMRES: GK_ERR_UNSUPPORTED).  infos has count entries
  * (may be NULL).  bs / xs: arrays of device pointers (host arrays of
@@ -304,10 +358,12 @@ gk_status gk_solve_batched(int32_t count, const gk_matrix* As,
  * gk_solve).  Stream-ordered on `stream`; kinds NONE to BLOCK_JACOBI
  * return without waiting, ILU waits for the result and returns
  * GK_ERR_TIMEOUT if a substitution's bounded wait ran out (z is then
- * wrong).  The substitutions run sync-free: each warp solves 32
- * consecutive rows and waits, bounded, for the chunks its rows depend on. */
+ * wrong, and gk_matrix_describe reports device_error until the next ILU
+ * application).  The substitutions run sync-free: each warp solves a chunk
+ * of consecutive rows and waits, bounded by wait_budget_ns (0 = 2 s;
+ * negative: GK_ERR_INVALID), for the values its rows depend on. */
 gk_status gk_precond_apply(gk_matrix A, gk_precond kind, int32_t block_size,
-                           const void* r, void* z, void* stream);
+                           const void* r, void* z, int64_t wait_budget_ns, void* stream);
 
 /* The ILU(0) factors of A, built on first use, copied to the host array
  * lu (nnz entries in the vector type) in A's CSR order (for a padded
@@ -329,9 +385,10 @@ gk_status gk_ilu_factors(gk_matrix A, void* lu, void* stream);
  * type.  The pattern analysis (dependency levels, the claim order, the
  * timed chunk shape) is built on first use and kept with A; the solve is
  * the sync-free substitution kernel of ILU(0).  Blocks until x is written;
- * GK_ERR_TIMEOUT if a bounded wait ran out. */
+ * GK_ERR_TIMEOUT if a wait ran past wait_budget_ns (0 = 2 s; negative:
+ * GK_ERR_INVALID). */
 gk_status gk_triangular_solve(gk_matrix A, int upper, int unit_diagonal, const void* b,
-                              void* x, void* stream);
+                              void* x, int64_t wait_budget_ns, void* stream);
 
 /* ---------------------------------------------------------------------
  * SpMV without device allocation

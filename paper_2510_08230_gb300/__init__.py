@@ -40,6 +40,7 @@ EXPORTED = [
     "gk_matrix_describe", "gk_matrix_export", "gk_matrix_destroy", "gk_apply",
     "gk_apply_adv", "gk_solve", "gk_solve_batched", "gk_status_string", "gk_version",
     "gk_spmv_csr_f64_noalloc", "gk_precond_apply", "gk_ilu_factors", "gk_triangular_solve",
+    "gk_solve_async",
 ]
 PRECONDS = {"none": GK_PRECOND_NONE, "jacobi": GK_PRECOND_JACOBI,
             "block_jacobi": GK_PRECOND_BLOCK_JACOBI, "ilu": GK_PRECOND_ILU}
@@ -70,13 +71,16 @@ class gk_solve_opts(ctypes.Structure):
                 ("max_iters", ctypes.c_int32), ("krylov_dim", ctypes.c_int32),
                 ("mixed", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int32), ("batch_tols", ctypes.c_void_p),
-                ("engine", ctypes.c_int32), ("block_size", ctypes.c_int32)]
+                ("engine", ctypes.c_int32), ("block_size", ctypes.c_int32),
+                ("wait_budget_ns", ctypes.c_int64)]
 
 
 class gk_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
                 ("outer_iters", ctypes.c_int32), ("rel_res_recurrence", ctypes.c_double),
-                ("rel_res_true", ctypes.c_double), ("device_ms", ctypes.c_float)]
+                ("rel_res_true", ctypes.c_double), ("device_ms", ctypes.c_float),
+                ("spmv_format", ctypes.c_int32), ("slice_size", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -107,10 +111,11 @@ def lib():
                                ctypes.POINTER(gk_solve_info), vp]
         L.gk_solve_batched.argtypes = [i32, pm, pm, pm, ctypes.POINTER(gk_solve_opts),
                                        ctypes.POINTER(gk_solve_info), vp]
+        L.gk_solve_async.argtypes = [vp, vp, vp, ctypes.POINTER(gk_solve_opts), vp, vp]
         L.gk_spmv_csr_f64_noalloc.argtypes = [i32, i32, i64, vp, vp, vp, f64, vp, f64, vp, vp]
-        L.gk_precond_apply.argtypes = [vp, ctypes.c_int, i32, vp, vp, vp]
+        L.gk_precond_apply.argtypes = [vp, ctypes.c_int, i32, vp, vp, i64, vp]
         L.gk_ilu_factors.argtypes = [vp, vp, vp]
-        L.gk_triangular_solve.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+        L.gk_triangular_solve.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, i64, vp]
         L.gk_status_string.argtypes = [ctypes.c_int]
         L.gk_status_string.restype = ctypes.c_char_p
         L.gk_version.argtypes = []
@@ -227,13 +232,13 @@ def gk_apply_adv(A, alpha, b, beta, x, stream=None):
 
 
 def make_opts(method="cg", precond=None, tol=1e-10, max_iters=1000, krylov_dim=30, mixed=0,
-              inner_tol=0.0, max_outer=0, engine=0, block_size=0):
+              inner_tol=0.0, max_outer=0, engine=0, block_size=0, wait_budget_ns=0):
     """precond: None / "none" / 0, "jacobi" / 1 / True, "block_jacobi" / 2
     (with block_size rows per diagonal block) or "ilu" / 3 (ILU(0))."""
     m = METHODS[method] if isinstance(method, str) else int(method)
     p = _precond(precond)
     return gk_solve_opts(m, p, tol, max_iters, krylov_dim, mixed, inner_tol, max_outer, None,
-                         engine, block_size)
+                         engine, block_size, int(wait_budget_ns))
 
 
 def _precond(precond):
@@ -246,9 +251,9 @@ def _precond(precond):
     return int(precond)
 
 
-def gk_precond_apply(A, kind, block_size, r, z, stream=None):
+def gk_precond_apply(A, kind, block_size, r, z, wait_budget_ns=0, stream=None):
     return lib().gk_precond_apply(A, _precond(kind), int(block_size), _ptr(r), _ptr(z),
-                                  _stream(stream))
+                                  int(wait_budget_ns), _stream(stream))
 
 
 def gk_solve(A, b, x, opts, stream=None):
@@ -258,6 +263,21 @@ def gk_solve(A, b, x, opts, stream=None):
     d = info.as_dict()
     d["return"] = st
     return d
+
+
+def gk_solve_async(A, b, x, opts, info_dev, stream=None):
+    """Enqueues the solve; info_dev: a device buffer of
+    ctypes.sizeof(gk_solve_info) bytes (e.g. a CUDA uint8 tensor) that
+    receives the outcome.  Returns the enqueue status."""
+    return lib().gk_solve_async(A, _ptr(b), _ptr(x), ctypes.byref(opts), _ptr(info_dev),
+                                _stream(stream))
+
+
+def solve_info_from_bytes(buf):
+    """A gk_solve_info (dict) from its bytes (e.g. a device info buffer
+    copied to the host)."""
+    raw = bytes(np.asarray(buf, dtype=np.uint8).tobytes())
+    return gk_solve_info.from_buffer_copy(raw[:ctypes.sizeof(gk_solve_info)]).as_dict()
 
 
 def gk_solve_batched(As, bs, xs, opts, stream=None, tols=None):
@@ -307,10 +327,18 @@ class Matrix:
     @classmethod
     def from_csr(cls, m, dtype="f64", device=None):
         """From a workloads.CSR (host arrays) or any object with n, ncols,
-        row_ptr, col_idx, values.  Float64 values with an F32/BF16 dtype
-        are uploaded as F64 and rounded on the device (gk_matrix_convert)."""
-        if _dt(dtype) != GK_F64 and np.asarray(m.values).dtype == np.float64:
+        row_ptr, col_idx, values.  Values wider than dtype (float64 for
+        F32/BF16/F16, float32 for BF16/F16) are uploaded in their own type
+        and rounded on the device (gk_matrix_convert); BF16 values may also
+        be given as uint16 bit patterns."""
+        src = np.asarray(m.values).dtype
+        if _dt(dtype) != GK_F64 and src == np.float64:
             A = cls.from_csr(m, "f64", device)
+            B = A.convert("csr", dtype)
+            A.close()
+            return B
+        if _dt(dtype) in (GK_BF16, GK_F16) and src == np.float32:
+            A = cls.from_csr(m, "f32", device)
             B = A.convert("csr", dtype)
             A.close()
             return B
@@ -385,15 +413,17 @@ class Matrix:
     def apply_adv(self, alpha, b, beta, x, stream=None):
         _check(gk_apply_adv(self.handle, alpha, b, beta, x, stream), "gk_apply_adv")
 
-    def precond_apply(self, r, z, kind="ilu", block_size=0, stream=None):
+    def precond_apply(self, r, z, kind="ilu", block_size=0, stream=None, wait_budget_ns=0):
         """z = M^-1 r for the preconditioner `kind` (device vectors)."""
-        _check(gk_precond_apply(self.handle, kind, block_size, r, z, stream), "gk_precond_apply")
+        _check(gk_precond_apply(self.handle, kind, block_size, r, z, wait_budget_ns, stream),
+               "gk_precond_apply")
 
-    def triangular_solve(self, b, x, upper=False, unit_diagonal=False, stream=None):
+    def triangular_solve(self, b, x, upper=False, unit_diagonal=False, stream=None,
+                         wait_budget_ns=0):
         """x with T x = b, T the lower (or upper) triangle of this matrix
         including its diagonal (unit_diagonal: taken as 1); device vectors."""
         _check(lib().gk_triangular_solve(self.handle, int(bool(upper)), int(bool(unit_diagonal)),
-                                         _ptr(b), _ptr(x), _stream(stream)),
+                                         _ptr(b), _ptr(x), int(wait_budget_ns), _stream(stream)),
                "gk_triangular_solve")
 
     def ilu_factors(self):
@@ -427,37 +457,16 @@ class Matrix:
             pass
 
 
-def bf16_bits(a):
-    """bfloat16 bit patterns of float32 values, rounded to nearest even
-    (used to pass BF16 data through the ABI; float64 data is converted on
-    the device with gk_matrix_convert instead)."""
-    f = np.ascontiguousarray(np.asarray(a), dtype=np.float32)
-    u = f.view(np.uint32).astype(np.uint64)
-    rounded = (u + np.uint64(0x7FFF) + ((u >> np.uint64(16)) & np.uint64(1))) >> np.uint64(16)
-    out = rounded.astype(np.uint16)
-    out[np.isnan(f)] = np.uint16(0x7FC0)
-    return out
-
-
-def bf16_to_float(bits):
-    return (np.asarray(bits, dtype=np.uint16).astype(np.uint32) << np.uint32(16)).view(np.float32)
-
-
 def host_values(values, dtype):
-    """Values in the ABI layout of dtype (float32 input only for F32/BF16;
-    float16 values as they are for F16)."""
-    dt = _dt(dtype)
-    if dt == GK_F64:
-        return np.ascontiguousarray(values, dtype=np.float64)
+    """Values in the ABI layout of dtype, unchanged: float64 for F64,
+    float32 for F32, uint16 bfloat16 bit patterns for BF16, float16 for F16.
+    Narrowing is never done here; wider values go through the device
+    conversion (gk_matrix_convert)."""
+    want = {GK_F64: np.float64, GK_F32: np.float32, GK_BF16: np.uint16,
+            GK_F16: np.float16}[_dt(dtype)]
     v = np.asarray(values)
-    if dt == GK_F16:
-        if v.dtype != np.float16:
-            raise TypeError("F16 matrices take float16 values; convert float64 matrices on "
-                            "the device with gk_matrix_convert")
-        return np.ascontiguousarray(v)
-    if v.dtype != np.float32:
-        raise TypeError("F32/BF16 matrices take float32 values; convert float64 "
-                        "matrices on the device with gk_matrix_convert")
-    if dt == GK_F32:
-        return np.ascontiguousarray(v)
-    return np.ascontiguousarray(bf16_bits(v))
+    if v.dtype != want:
+        raise TypeError(f"dtype {dtype} takes {np.dtype(want).name} values, got {v.dtype}; "
+                        "upload wider values in their own type and convert them on the "
+                        "device with gk_matrix_convert")
+    return np.ascontiguousarray(v)

@@ -19,8 +19,13 @@
 namespace gk {
 
 
+// SpMV layouts of a system in the batched engine.  Every layout sums a row
+// in its CSR order (one fused multiply-add per stored entry, from zero), so
+// the layout never changes a result, only the memory access pattern.
+enum BatchLayout : int32_t { BL_CSR = 0, BL_ELL = 1, BL_SELLP = 2 };
+
 struct SysDesc {
-    int32_t n, pad;
+    int32_t n, fmt;  // fmt: a BatchLayout
     const int32_t* rp;
     const int32_t* ci;
     const void* va;
@@ -29,6 +34,14 @@ struct SysDesc {
     void* work;  // workspace vectors, each `ld` elements
     int64_t ld;
     double tol;  // this system's relative tolerance
+    // padded copy (ELL: K columns of pstride rows; SELL-P: slices of S rows
+    // with lengths slen[] and offsets sset[] in units of S entries)
+    int32_t* pcol;
+    void* pval;
+    int32_t* slen;
+    int32_t* sset;
+    int64_t pstride;
+    int32_t K, S;
 };
 
 struct SysOut {
@@ -119,6 +132,96 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ rp, const int32
     return s;
 }
 
+// Row i of a system in its layout (see BatchLayout): entries in CSR order,
+// padding (column -1) only after a row's last entry.
+template <typename V, typename T, typename G>
+__device__ __forceinline__ T sys_row_dot(const SysDesc& d, const G* __restrict__ g, int32_t i) {
+    if (d.fmt == BL_ELL) {
+        const int32_t* __restrict__ col = d.pcol;
+        const V* __restrict__ val = (const V*)d.pval;
+        T s = T(0);
+        int64_t p = i;
+        for (int32_t k = 0; k < d.K; ++k, p += d.pstride) {
+            const int32_t c = col[p];
+            if (c < 0) break;
+            s = fmadd(cvt<T>(val[p]), (T)g[c], s);
+        }
+        return s;
+    }
+    if (d.fmt == BL_SELLP) {
+        const int32_t sl = i / d.S, t = i - sl * d.S;
+        const int32_t* __restrict__ col = d.pcol;
+        const V* __restrict__ val = (const V*)d.pval;
+        const int32_t len = d.slen[sl];
+        int64_t p = (int64_t)d.sset[sl] * d.S + t;
+        T s = T(0);
+        for (int32_t k = 0; k < len; ++k, p += d.S) {
+            const int32_t c = col[p];
+            if (c < 0) break;
+            s = fmadd(cvt<T>(val[p]), (T)g[c], s);
+        }
+        return s;
+    }
+    return row_dot<V, T>(d.rp, d.ci, (const V*)d.va, g, i);
+}
+
+// Writes the padded copy of every system whose layout is ELL or SELL-P
+// (one block per system, grid-stride over systems).  SELL-P: slice lengths
+// (longest row of the slice), then their exclusive scan, then the entries.
+template <typename V>
+__global__ void __launch_bounds__(256) k_batch_pad(SysDesc* __restrict__ sys, int32_t count) {
+    for (int32_t sidx = blockIdx.x; sidx < count; sidx += gridDim.x) {
+        SysDesc& d = sys[sidx];
+        if (d.fmt == BL_CSR) continue;
+        const int32_t n = d.n;
+        const V* __restrict__ va = (const V*)d.va;
+        V* __restrict__ pv = (V*)d.pval;
+        if (d.fmt == BL_ELL) {
+            for (int64_t i = threadIdx.x; i < d.pstride; i += blockDim.x) {
+                const int32_t a = i < n ? d.rp[i] : 0, e = i < n ? d.rp[i + 1] : 0;
+                for (int32_t k = 0; k < d.K; ++k) {
+                    const int64_t p = (int64_t)k * d.pstride + i;
+                    const bool in = a + k < e;
+                    d.pcol[p] = in ? d.ci[a + k] : -1;
+                    pv[p] = in ? va[a + k] : V(0.0f);
+                }
+            }
+            continue;
+        }
+        const int32_t S = d.S, ns = (n + S - 1) / S;
+        for (int32_t sl = threadIdx.x; sl < ns; sl += blockDim.x) {
+            int32_t mx = 0;
+            for (int32_t t = 0; t < S; ++t) {
+                const int32_t i = sl * S + t;
+                if (i < n) mx = max(mx, d.rp[i + 1] - d.rp[i]);
+            }
+            d.slen[sl] = mx;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t acc = 0;
+            for (int32_t sl = 0; sl < ns; ++sl) {
+                d.sset[sl] = acc;
+                acc += d.slen[sl];
+            }
+            d.sset[ns] = acc;
+        }
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < (int64_t)ns * S; i += blockDim.x) {
+            const int32_t sl = (int32_t)(i / S), t = (int32_t)(i - (int64_t)sl * S);
+            const int32_t a = i < n ? d.rp[i] : 0, e = i < n ? d.rp[i + 1] : 0;
+            const int64_t base = (int64_t)d.sset[sl] * S + t;
+            for (int32_t k = 0; k < d.slen[sl]; ++k) {
+                const int64_t p = base + (int64_t)k * S;
+                const bool in = a + k < e;
+                d.pcol[p] = in ? d.ci[a + k] : -1;
+                pv[p] = in ? va[a + k] : V(0.0f);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Jacobi inverse diagonal of row i; 0 when missing or zero.
 template <typename V, typename T>
 __device__ __forceinline__ T row_dinv(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -170,7 +273,7 @@ __device__ bool block_setup(const SysDesc& d, const BlockOpts& opt, T* dinv, T* 
     }
     VAcc<1> rr = vacc<1>();
     for_rows_vl(n, [&](int32_t i, int s) {
-        const T ri = b[i] - row_dot<V, T>(d.rp, d.ci, va, x, i);
+        const T ri = b[i] - sys_row_dot<V, T>(d, x, i);
         r[i] = ri;
         rr.v[0][s] = fma((double)ri, (double)ri, rr.v[0][s]);
     });
@@ -198,7 +301,7 @@ __device__ double block_true_resid(const SysDesc& d, T* r) {
     const T* x = (const T*)d.x;
     VAcc<1> tt = vacc<1>();
     for_rows_vl(d.n, [&](int32_t i, int s) {
-        const T ri = b[i] - row_dot<V, T>(d.rp, d.ci, va, x, i);
+        const T ri = b[i] - sys_row_dot<V, T>(d, x, i);
         r[i] = ri;
         tt.v[0][s] = fma((double)ri, (double)ri, tt.v[0][s]);
     });
@@ -246,7 +349,7 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_cg(const SysDesc
             while (k < opt.max_iters) {
                 VAcc<1> pq = vacc<1>();
                 for_rows_vl(n, [&](int32_t i, int s) {
-                    const T sv = row_dot<V, T>(d.rp, d.ci, va, ps, i);
+                    const T sv = sys_row_dot<V, T>(d, ps, i);
                     q[i] = sv;
                     pq.v[0][s] = fma((double)ps[i], (double)sv, pq.v[0][s]);
                 });
@@ -345,7 +448,7 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_bicgstab(const S
                 __syncthreads();
                 VAcc<1> rv = vacc<1>();
                 for_rows_vl(n, [&](int32_t i, int s) {
-                    const T vi = row_dot<V, T>(d.rp, d.ci, va, gs, i);
+                    const T vi = sys_row_dot<V, T>(d, gs, i);
                     v[i] = vi;
                     rv.v[0][s] = fma((double)rh[i], (double)vi, rv.v[0][s]);
                 });
@@ -384,7 +487,7 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_bicgstab(const S
                 __syncthreads();
                 VAcc<2> a2 = vacc<2>();
                 for_rows_vl(n, [&](int32_t i, int s) {
-                    const T ti = row_dot<V, T>(d.rp, d.ci, va, gs, i);
+                    const T ti = sys_row_dot<V, T>(d, gs, i);
                     t[i] = ti;
                     a2.v[0][s] = fma((double)ti, (double)sv[i], a2.v[0][s]);
                     a2.v[1][s] = fma((double)ti, (double)ti, a2.v[1][s]);
@@ -430,8 +533,19 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_bicgstab(const S
 
 static int nslots(int method) { return method == GK_CG ? 4 : 9; }
 
+// Layout policy of a batch (picked by the autotuner per batch shape):
+// layout BL_CSR runs every system on its CSR arrays; BL_ELL gives each system
+// an ELL copy when ELL stores at most 1.2 x its nonzeros, else keeps its
+// CSR; BL_SELLP gives each system a SELL-P copy with slices of S rows.
+// nt: threads per block.
+struct BatchCfg {
+    int nt = 256;
+    int layout = BL_ELL;
+    int S = 32;
+};
+
 struct BatchBufs {
-    DevBuf desc, outs, work;
+    DevBuf desc, outs, work, pad;
     SysDesc* hdesc = nullptr;
     SysOut* hout = nullptr;
     size_t hcap = 0;
@@ -441,6 +555,7 @@ struct BatchBufs {
         desc.release();
         outs.release();
         work.release();
+        pad.release();
     }
 };
 
@@ -482,19 +597,43 @@ static gk_status launch_block(int method, const SysDesc* ddesc, SysOut* dout, in
     return GK_OK;
 }
 
+static size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Layout of system A under a policy, and the bytes of its padded copy.
+static int sys_layout(const gk_matrix A, const BatchCfg& cfg, size_t* pad_bytes) {
+    *pad_bytes = 0;
+    if (A->n == 0 || A->nnz == 0 || cfg.layout == BL_CSR) return BL_CSR;
+    const size_t sv = value_bytes(A->dtype);
+    if (cfg.layout == BL_ELL) {
+        const int64_t stride = ((int64_t)A->n + 31) / 32 * 32;
+        if ((int64_t)A->max_row * A->n > A->nnz + A->nnz / 5) return BL_CSR;
+        *pad_bytes = al256((size_t)A->max_row * stride * 4) + al256((size_t)A->max_row * stride * sv);
+        return BL_ELL;
+    }
+    // SELL-P: at most the longest row in every slice
+    const int64_t ns = ((int64_t)A->n + cfg.S - 1) / cfg.S;
+    const size_t ent = (size_t)ns * cfg.S * A->max_row;
+    *pad_bytes = al256(ent * 4) + al256(ent * sv) + al256(4 * (size_t)ns) + al256(4 * (size_t)(ns + 1));
+    return BL_SELLP;
+}
+
 // Runs count systems; infos may be null.  All matrices CSR, same dtype.
 static gk_status run_batch(int32_t count, const gk_matrix* As, const void* const* bs,
                            void* const* xs, const gk_solve_opts* o, gk_solve_info* infos,
-                           cudaStream_t s, int nt, float* ms_out) {
+                           cudaStream_t s, const BatchCfg& cfg, float* ms_out) {
+    const int nt = cfg.nt;
     const gk_dtype dt = As[0]->dtype;
     const size_t vb = vector_bytes(dt);
     int32_t nmax = 0;
-    size_t wbytes = 0;
+    size_t wbytes = 0, pbytes = 0;
     const int ns = nslots(o->method);
     for (int32_t i = 0; i < count; ++i) {
         nmax = std::max(nmax, As[i]->n);
         const size_t ld = (((size_t)As[i]->n * vb + 255) & ~(size_t)255) / vb;
         wbytes += ld * vb * ns;
+        size_t pb = 0;
+        sys_layout(As[i], cfg, &pb);
+        pbytes += pb;
     }
     const size_t smem = std::max<size_t>((size_t)nmax * vb, 16);
     if (smem > 200 * 1024) return GK_ERR_UNSUPPORTED;
@@ -512,12 +651,34 @@ static gk_status run_batch(int32_t count, const gk_matrix* As, const void* const
     GK_TRY(B.desc.ensure(sizeof(SysDesc) * (size_t)count));
     GK_TRY(B.outs.ensure(sizeof(SysOut) * (size_t)count));
     GK_TRY(B.work.ensure(wbytes + 256));
+    if (pbytes) GK_TRY(B.pad.ensure(pbytes + 256));
     char* w = (char*)B.work.ptr;
+    char* pw = (char*)B.pad.ptr;
+    bool any_pad = false;
     for (int32_t i = 0; i < count; ++i) {
         gk_matrix A = As[i];
         SysDesc& d = B.hdesc[i];
+        std::memset(&d, 0, sizeof(d));
         d.n = A->n;
-        d.pad = 0;
+        size_t pb = 0;
+        d.fmt = sys_layout(A, cfg, &pb);
+        if (d.fmt == BL_ELL) {
+            d.K = A->max_row;
+            d.pstride = ((int64_t)A->n + 31) / 32 * 32;
+            d.pcol = (int32_t*)pw;
+            d.pval = pw + al256((size_t)d.K * d.pstride * 4);
+        } else if (d.fmt == BL_SELLP) {
+            d.S = cfg.S;
+            d.K = A->max_row;
+            const int64_t nsl = ((int64_t)A->n + cfg.S - 1) / cfg.S;
+            const size_t ent = (size_t)nsl * cfg.S * A->max_row;
+            d.pcol = (int32_t*)pw;
+            d.pval = pw + al256(ent * 4);
+            d.slen = (int32_t*)(pw + al256(ent * 4) + al256(ent * value_bytes(A->dtype)));
+            d.sset = d.slen + al256(4 * (size_t)nsl) / 4;
+        }
+        pw += pb;
+        any_pad |= d.fmt != BL_CSR;
         d.rp = A->row_ptr;
         d.ci = A->col;
         d.va = A->val;
@@ -538,6 +699,14 @@ static gk_status run_batch(int32_t count, const gk_matrix* As, const void* const
     GK_CUDA(cudaEventCreate(&e1));
     GK_CUDA(cudaEventRecord(e0, s));
     gk_status st = GK_OK;
+    if (any_pad) {  // the padded copies of this batch, one block per system
+        const unsigned pg = (unsigned)std::min<int64_t>(count, (int64_t)sms * 8);
+        SysDesc* dd = (SysDesc*)B.desc.ptr;
+        if (dt == GK_F64) k_batch_pad<double><<<pg, 256, 0, s>>>(dd, count);
+        else if (dt == GK_F32) k_batch_pad<float><<<pg, 256, 0, s>>>(dd, count);
+        else k_batch_pad<__nv_bfloat16><<<pg, 256, 0, s>>>(dd, count);
+        GK_CUDA(cudaGetLastError());
+    }
     auto occ_of = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         int b = 1;
@@ -576,6 +745,11 @@ static gk_status run_batch(int32_t count, const gk_matrix* As, const void* const
                 infos[i].rel_res_recurrence = so.rec;
                 infos[i].rel_res_true = so.tru;
                 infos[i].device_ms = ms;
+                infos[i].spmv_format = B.hdesc[i].fmt == BL_ELL     ? GK_ELL
+                                       : B.hdesc[i].fmt == BL_SELLP ? GK_SELLP
+                                                                    : GK_CSR;
+                infos[i].block_threads = nt;
+                infos[i].slice_size = B.hdesc[i].fmt == BL_SELLP ? cfg.S : 0;
             }
     }
     cudaEventDestroy(e0);
@@ -594,22 +768,32 @@ gk_status solve_small(gk_matrix A, const void* b, void* x, const gk_solve_opts* 
     gk_matrix As[1] = {A};
     const void* bs[1] = {b};
     void* xs[1] = {x};
-    GK_TRY(run_batch(1, As, bs, xs, o, &info, s, BLOCK_MAX_THREADS, nullptr));
+    BatchCfg cfg;
+    cfg.nt = BLOCK_MAX_THREADS;
+    GK_TRY(run_batch(1, As, bs, xs, o, &info, s, cfg, nullptr));
     out->status = info.status;
     out->iters = info.iters;
     out->restarts = info.restarts;
     out->rec = info.rel_res_recurrence;
     out->tru = info.rel_res_true;
+    out->layout = info.spmv_format;
+    out->slice = info.slice_size;
+    out->threads = info.block_threads;
     return GK_OK;
 }
 
 // ------------------------------------------------------------ autotuner
-// Threads per block for a batch shape, picked by timing each candidate on
-// a capped run of the batch itself (the callers' initial guesses are saved
-// before and restored after the trials) and cached per key: value type,
-// method, preconditioner, log2 of the largest n and of the system count.
+// The configuration of a batch shape -- each system's SpMV layout (policy
+// CSR, ELL where its padding is at most 20 %, or SELL-P with slices of
+// S = 8, 16 or 32 rows) and the threads per block (128, 256, 512, which set
+// how many rows a warp and a thread take per sweep) -- is picked by timing
+// every candidate on a run of the batch itself capped at 30 iterations (the
+// callers' initial guesses are saved before and restored after the trials)
+// and cached per key: value type, method, preconditioner, log2 of the
+// largest n and of the system count.  No candidate changes a result: every
+// layout sums a row in CSR order and the reductions use fixed virtual lanes.
 static std::mutex g_tune_mu;
-static std::map<uint64_t, int> g_tune;
+static std::map<uint64_t, BatchCfg> g_tune;
 
 static uint64_t tune_key(gk_dtype dt, const gk_solve_opts* o, int32_t nmax, int32_t count) {
     auto lg = [](int64_t v) {
@@ -621,9 +805,9 @@ static uint64_t tune_key(gk_dtype dt, const gk_solve_opts* o, int32_t nmax, int3
            (lg(nmax) << 16) | lg(count);
 }
 
-static gk_status autotune_threads(int32_t count, const gk_matrix* As, const void* const* bs,
-                                  void* const* xs, const gk_solve_opts* o, cudaStream_t s,
-                                  int* best) {
+static gk_status autotune(int32_t count, const gk_matrix* As, const void* const* bs,
+                          void* const* xs, const gk_solve_opts* o, cudaStream_t s,
+                          BatchCfg* best) {
     const size_t vb = vector_bytes(As[0]->dtype);
     size_t total = 0;
     for (int32_t i = 0; i < count; ++i) total += (size_t)As[i]->n * vb;
@@ -645,20 +829,44 @@ static gk_status autotune_threads(int32_t count, const gk_matrix* As, const void
     gk_solve_opts trial = *o;
     trial.max_iters = std::min(o->max_iters, 30);
     float best_ms = 1e30f;
-    *best = 256;
-    for (int nt : {128, 256, 512}) {
-        GK_TRY(copy_all(false));
-        float ms = 0.f;
-        GK_TRY(run_batch(count, As, bs, xs, &trial, nullptr, s, nt, &ms));
-        if (ms < best_ms) {
-            best_ms = ms;
-            *best = nt;
+    *best = BatchCfg();
+    const int layouts[5][2] = {{BL_CSR, 0}, {BL_ELL, 0}, {BL_SELLP, 8}, {BL_SELLP, 16}, {BL_SELLP, 32}};
+    for (const auto& L : layouts)
+        for (int nt : {128, 256, 512}) {
+            BatchCfg c;
+            c.layout = L[0];
+            c.S = L[0] == BL_SELLP ? L[1] : 32;
+            c.nt = nt;
+            GK_TRY(copy_all(false));
+            float ms = 0.f;
+            GK_TRY(run_batch(count, As, bs, xs, &trial, nullptr, s, c, &ms));
+            if (ms < best_ms) {
+                best_ms = ms;
+                *best = c;
+            }
         }
-    }
     GK_TRY(copy_all(false));
     GK_CUDA(cudaStreamSynchronize(s));
     save.release();
     return GK_OK;
+}
+
+// GK_BATCH_LAYOUT = csr | ell | sellp8 | sellp16 | sellp32 | sellp64 forces a layout
+// policy; GK_BATCH_THREADS = 128 | 256 | 512 forces the block size.
+static bool forced_layout(BatchCfg* c) {
+    const char* e = getenv("GK_BATCH_LAYOUT");
+    if (!e) return false;
+    if (!strcmp(e, "csr")) c->layout = BL_CSR;
+    else if (!strcmp(e, "ell")) c->layout = BL_ELL;
+    else if (!strncmp(e, "sellp", 5)) {
+        const int S = atoi(e + 5);
+        if (S != 8 && S != 16 && S != 32 && S != 64) return false;
+        c->layout = BL_SELLP;
+        c->S = S;
+    } else {
+        return false;
+    }
+    return true;
 }
 
 }  // namespace gk
@@ -690,28 +898,37 @@ extern "C" gk_status gk_solve_batched(int32_t count, const gk_matrix* As, const 
         if (A->device != dev) return GK_ERR_UNSUPPORTED;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    BatchCfg cfg;  // untuned default: ELL where it pads little, 256 threads
     int nt = 0;
     if (const char* e = getenv("GK_BATCH_THREADS")) nt = atoi(e);
-    if (nt != 128 && nt != 256 && nt != 512) {
-        nt = 256;
-        const char* at = getenv("GK_AUTOTUNE");
-        if (!(at && at[0] == '0') && count >= 8) {
-            int32_t nmax = 0;
-            for (int32_t i = 0; i < count; ++i) nmax = std::max(nmax, As[i]->n);
-            const uint64_t key = tune_key(As[0]->dtype, o, nmax, count);
-            int found = 0;
-            {
-                std::lock_guard<std::mutex> lk(g_tune_mu);
-                auto it = g_tune.find(key);
-                if (it != g_tune.end()) found = it->second;
+    const bool fnt = nt == 128 || nt == 256 || nt == 512;
+    const bool flay = forced_layout(&cfg);
+    const char* at = getenv("GK_AUTOTUNE");
+    if (!(fnt && flay) && !(at && at[0] == '0') && count >= 8) {
+        int32_t nmax = 0;
+        for (int32_t i = 0; i < count; ++i) nmax = std::max(nmax, As[i]->n);
+        const uint64_t key = tune_key(As[0]->dtype, o, nmax, count);
+        bool found = false;
+        BatchCfg tuned;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) {
+                tuned = it->second;
+                found = true;
             }
-            if (!found) {
-                GK_TRY(autotune_threads(count, As, bs, xs, o, s, &found));
-                std::lock_guard<std::mutex> lk(g_tune_mu);
-                g_tune[key] = found;
-            }
-            nt = found;
         }
+        if (!found) {
+            GK_TRY(autotune(count, As, bs, xs, o, s, &tuned));
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune[key] = tuned;
+        }
+        if (!flay) {
+            cfg.layout = tuned.layout;
+            cfg.S = tuned.S;
+        }
+        if (!fnt) cfg.nt = tuned.nt;
     }
-    return run_batch(count, As, bs, xs, o, infos, s, nt, nullptr);
+    if (fnt) cfg.nt = nt;
+    return run_batch(count, As, bs, xs, o, infos, s, cfg, nullptr);
 }

@@ -152,14 +152,21 @@ struct DevBuf {
 // chunk c; tile_desc[c] = {first row, end row, aligned first nonzero,
 // staged entries}, staged entries <= tile_cap.  Merge path: block_row[b] =
 // first row of merge block b (n_blocks + 1 entries).
+constexpr int WT_WARPS = 8;  // warps per block of the warp-tile kernel (CSR kind 3)
+constexpr int WT_SMEM_CAP = 208 * 1024;  // largest ring of one warp-tile block (the
+                                         // epilogues' static shared memory fits beside it)
+
 struct CsrPlan {
-    int kind = 0;            // 0 vector (G lanes / row), 1 row-tile, 2 merge
+    int kind = 0;            // 0 vector (G lanes / row), 1 row-tile, 2 merge, 3 warp-tile
     int lanes = 1;           // vector kernel lanes per row
     int32_t ntiles = 0;
     int32_t chunk = 0;       // nnz per chunk used to cut tiles
-    int32_t tile_cap = 0;    // staged entries per tile (>= chunk + max_row + 14)
-    int32_t stages = 0;      // row-tile pipeline depth (0 = as many as fit, max 3)
+    int32_t tile_cap = 0;    // staged entries per tile (row-tile: >= chunk + max_row + 14;
+                             // warp-tile: >= 32 * wt_rpl * max_row + 14)
+    int32_t stages = 0;      // row-tile pipeline depth (0 = as many as fit, max 3);
+                             // warp-tile: stages per warp
     int4* tile_desc = nullptr;
+    int32_t wt_rpl = 2;      // warp-tile: rows per lane (tiles of 32 * wt_rpl rows)
     int32_t merge_blocks = 0;
     int32_t merge_e = 8;     // merge-path items per lane (4, 6 or 8)
     int32_t merge_warp = 2;  // merge units: 1 one warp (32*E items, operands staged in
@@ -210,6 +217,7 @@ struct SolveOut {
     gk_status status = GK_OK;
     int32_t iters = 0, restarts = 0;
     double rec = 0.0, tru = 0.0;
+    int32_t layout = GK_CSR, slice = 0, threads = 0;  // the SpMV layout and block size used
 };
 
 }  // namespace gk
@@ -257,7 +265,10 @@ struct gk_matrix_s {
     gk::SolverCache* solver = nullptr;
     gk::DevBuf stage_in, stage_out;  // host-pointer apply staging
     gk::DevBuf carry;                // merge-path block carries
-    cudaStream_t side = nullptr;     // library stream for graph capture
+    cudaStream_t side = nullptr;     // library streams for graph capture (the second
+    cudaStream_t side2 = nullptr;    // captures the body of a solve's loop)
+    uint64_t wait_ns = 2000000000ull;  // budget of the row-tile kernel's waits (a solve's
+                                       // wait_budget_ns while it runs, else 2 s)
     std::mutex mu;
 };
 

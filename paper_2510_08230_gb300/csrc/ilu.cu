@@ -56,7 +56,7 @@ __global__ void k_ilu_prep(int32_t n, const int32_t* __restrict__ rp, const int3
 __device__ __forceinline__ unsigned wait_nonzero(const unsigned* p, unsigned* err) {
     unsigned v = ld_acquire_u32(p);
     if (v) return v;
-    const long long t0 = clock64();
+    const uint64_t t0 = globaltimer_ns();
     unsigned ns = 32;
     for (;;) {
         __nanosleep(ns);
@@ -64,7 +64,7 @@ __device__ __forceinline__ unsigned wait_nonzero(const unsigned* p, unsigned* er
         v = ld_relaxed_u32(p);
         if (v) return ld_acquire_u32(p);
         if (ld_relaxed_u32(err) != 0u) return 0u;
-        if (clock64() - t0 > ILU_WAIT_CYCLES) {
+        if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) {
             atomicExch(err, 1u);
             return 0u;
         }
@@ -576,7 +576,7 @@ __global__ void EW_BOUNDS k_scale_by(int32_t n, const T* __restrict__ d, const T
 
 template <typename T>
 static gk_status precond_apply_t(gk_matrix A, int kind, int32_t bs, const T* r, T* z,
-                                 cudaStream_t s) {
+                                 uint64_t wait_ns, cudaStream_t s) {
     const int32_t n = A->n;
     if (kind == GK_PRECOND_NONE) {
         if (n > 0 && z != r)
@@ -600,7 +600,8 @@ static gk_status precond_apply_t(gk_matrix A, int kind, int32_t bs, const T* r, 
     GK_TRY(ensure_ilu(A, s));
     if (n == 0) return GK_OK;
     GK_TRY(A->ilu->w.ensure(sizeof(T) * (size_t)n));
-    const IluDev<T> f = ilu_view<T>(A);
+    IluDev<T> f = ilu_view<T>(A);
+    f.wait_ns = wait_ns;
     GK_TRY(ilu_clear_err(f, s));
     GK_TRY(ilu_apply<T>(f, IluSrc<T>{r}, (T*)A->ilu->w.ptr, IluOutStore<T>{z}, IluSkipNever{},
                         IluNoErr{}, s));
@@ -614,11 +615,12 @@ static gk_status precond_apply_t(gk_matrix A, int kind, int32_t bs, const T* r, 
 // T x = b with A's lower (upper = 0) or upper triangle; unit: unit diagonal.
 template <typename T>
 static gk_status tri_solve_t(gk_matrix A, int upper, int unit, const T* b, T* x,
-                             cudaStream_t s) {
+                             uint64_t wait_ns, cudaStream_t s) {
     GK_TRY(ensure_store(A, &A->tri, false, s));
     if (!unit && A->tri->zero_diag) return GK_ERR_ZERO_DIAG;
     if (A->n == 0) return GK_OK;
     IluDev<T> f = tri_view<T>(A->tri, A->n);
+    f.wait_ns = wait_ns;
     f.ldiag = (!upper && !unit) ? 1 : 0;
     f.udiag = unit ? 0 : 1;
     GK_TRY(ilu_clear_err(f, s));
@@ -635,8 +637,10 @@ static gk_status tri_solve_t(gk_matrix A, int upper, int unit, const T* b, T* x,
 using namespace gk;
 
 extern "C" gk_status gk_triangular_solve(gk_matrix A, int upper, int unit_diagonal, const void* b,
-                                         void* x, void* stream) {
+                                         void* x, int64_t wait_budget_ns, void* stream) {
     if (!A || ((!b || !x) && A->n > 0)) return GK_ERR_INVALID;
+    if (wait_budget_ns < 0) return GK_ERR_INVALID;
+    const uint64_t wb = wait_budget_ns > 0 ? (uint64_t)wait_budget_ns : WAIT_LIMIT_NS;
     if (A->n != A->ncols) return GK_ERR_INVALID;
     if (A->n > 0 && b == x) return GK_ERR_INVALID;
     int dev = -1;
@@ -645,13 +649,16 @@ extern "C" gk_status gk_triangular_solve(gk_matrix A, int upper, int unit_diagon
     std::lock_guard<std::mutex> lk(A->mu);
     cudaStream_t s = (cudaStream_t)stream;
     if (A->dtype == GK_F64)
-        return tri_solve_t<double>(A, upper, unit_diagonal, (const double*)b, (double*)x, s);
-    return tri_solve_t<float>(A, upper, unit_diagonal, (const float*)b, (float*)x, s);
+        return tri_solve_t<double>(A, upper, unit_diagonal, (const double*)b, (double*)x, wb, s);
+    return tri_solve_t<float>(A, upper, unit_diagonal, (const float*)b, (float*)x, wb, s);
 }
 
 extern "C" gk_status gk_precond_apply(gk_matrix A, gk_precond kind, int32_t block_size,
-                                      const void* r, void* z, void* stream) {
+                                      const void* r, void* z, int64_t wait_budget_ns,
+                                      void* stream) {
     if (!A || (!r && A->n > 0) || (!z && A->n > 0)) return GK_ERR_INVALID;
+    if (wait_budget_ns < 0) return GK_ERR_INVALID;
+    const uint64_t wb = wait_budget_ns > 0 ? (uint64_t)wait_budget_ns : WAIT_LIMIT_NS;
     if (A->n != A->ncols) return GK_ERR_INVALID;
     if (kind < GK_PRECOND_NONE || kind > GK_PRECOND_ILU) return GK_ERR_INVALID;
     if (kind == GK_PRECOND_ILU && A->n > 0 && r == z) return GK_ERR_INVALID;
@@ -663,8 +670,9 @@ extern "C" gk_status gk_precond_apply(gk_matrix A, gk_precond kind, int32_t bloc
     std::lock_guard<std::mutex> lk(A->mu);
     cudaStream_t s = (cudaStream_t)stream;
     if (A->dtype == GK_F64)
-        return precond_apply_t<double>(A, (int)kind, block_size, (const double*)r, (double*)z, s);
-    return precond_apply_t<float>(A, (int)kind, block_size, (const float*)r, (float*)z, s);
+        return precond_apply_t<double>(A, (int)kind, block_size, (const double*)r, (double*)z,
+                                       wb, s);
+    return precond_apply_t<float>(A, (int)kind, block_size, (const float*)r, (float*)z, wb, s);
 }
 
 extern "C" gk_status gk_ilu_factors(gk_matrix A, void* lu, void* stream) {

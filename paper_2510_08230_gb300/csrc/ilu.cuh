@@ -42,10 +42,11 @@
 //    subtracts every term in exactly the sequential order.
 //  - The last warp to leave the kernel resets the claim counter for the
 //    next launch.
-//  - Every wait is bounded (about two seconds of SM clock); a wait that
-//    runs out records an error flag, later waits of the launch give up at
-//    once, and the kernel finishes with wrong values instead of hanging.
-//    The solver engine turns the flag into GK_ERR_TIMEOUT.
+//  - Every wait is bounded (the caller's budget, 2 s by default, on the
+//    GPU's global nanosecond timer); a wait that runs out records an error
+//    flag, later waits of the launch give up at once, and the kernel
+//    finishes with wrong values instead of hanging.  The solver engine and
+//    the apply entry points turn the flag into GK_ERR_TIMEOUT.
 // Every subtraction of a product is one fused multiply-add, and U's pivots
 // are applied as stored reciprocals (1 / u_ii rounded once, a
 // multiplication instead of a division on the in-chunk chain), so that FP64
@@ -53,11 +54,11 @@
 #pragma once
 
 #include "gk_internal.cuh"
+#include "tma.cuh"
 
 namespace gk {
 
-constexpr int TRSV_CHUNK_MAX = 32;                  // rows per warp at most
-constexpr long long ILU_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int TRSV_CHUNK_MAX = 32;  // rows per warp at most
 
 // Per-direction words (index 0: L, 1: U).
 struct TrsvSync {
@@ -85,6 +86,7 @@ struct IluDev {
     int32_t ldiag = 0;              // L scaled by rdiag (0: unit diagonal)
     int32_t udiag = 1;              // U scaled by rdiag (0: unit diagonal)
     unsigned pause_max = 64;        // longest pause between polls (ns)
+    unsigned long long wait_ns = WAIT_LIMIT_NS;  // budget of one wait (%globaltimer)
     int32_t warps[2] = {0, 0};      // host: warps per substitution launch
 };
 
@@ -136,19 +138,20 @@ __device__ __forceinline__ void st_relaxed_v(float* p, float v) {
     asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
-// Spin until *flag == want (acquire), at most ILU_WAIT_CYCLES; on time-out
-// set *err and return false.  Once any wait of the launch has run out
-// (*err set), later waits give up at once.  Polls pause 32 to 256 ns.
-__device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned want, unsigned* err) {
+// Spin until *flag == want (acquire), at most limit_ns of %globaltimer; on
+// time-out set *err and return false.  Once any wait of the launch has run
+// out (*err set), later waits give up at once.  Polls pause 32 to 256 ns.
+__device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned want, unsigned* err,
+                                          unsigned long long limit_ns = WAIT_LIMIT_NS) {
     if (ld_acquire_u32(flag) == want) return true;
-    const long long t0 = clock64();
+    const uint64_t t0 = globaltimer_ns();
     unsigned ns = 32;
     for (;;) {
         __nanosleep(ns);
         if (ns < 256) ns <<= 1;
         if (ld_acquire_u32(flag) == want) return true;
         if (ld_relaxed_u32(err) != 0u) return false;
-        if (clock64() - t0 > ILU_WAIT_CYCLES) {
+        if (globaltimer_ns() - t0 > limit_ns) {
             atomicExch(err, 1u);
             return false;
         }
@@ -156,11 +159,13 @@ __device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned want, u
 }
 
 // The value of slot p once it is no longer the sentinel (v: a first load
-// already issued); bounded like wait_flag, pauses 32 to pause_max ns.
+// already issued); bounded like wait_flag (limit_ns), pauses 32 to
+// pause_max ns.
 template <typename T>
-__device__ __forceinline__ T wait_value(const T* p, T v, unsigned* err, unsigned pause_max) {
+__device__ __forceinline__ T wait_value(const T* p, T v, unsigned* err, unsigned pause_max,
+                                        unsigned long long limit_ns) {
     if (!Sentinel<T>::is(v)) return v;
-    const long long t0 = clock64();
+    const uint64_t t0 = globaltimer_ns();
     unsigned ns = 32;
     for (;;) {
         __nanosleep(ns);
@@ -168,7 +173,7 @@ __device__ __forceinline__ T wait_value(const T* p, T v, unsigned* err, unsigned
         v = ld_relaxed_v(p);
         if (!Sentinel<T>::is(v)) return v;
         if (ld_relaxed_u32(err) != 0u) return v;
-        if (clock64() - t0 > ILU_WAIT_CYCLES) {
+        if (globaltimer_ns() - t0 > limit_ns) {
             atomicExch(err, 1u);
             return v;
         }
@@ -287,7 +292,8 @@ k_ilu_trsv(IluDev<T> f, Src src, Out out, Skip sk, Err on_err) {
                     for (int u = 0; u < G; ++u)
                         if (jj[u] >= 0)
                             acc = sub_mul(acc, lv[u],
-                                          wait_value(dst + jj[u], vv[u], &sy->err, f.pause_max));
+                                          wait_value(dst + jj[u], vv[u], &sy->err, f.pause_max,
+                                                     f.wait_ns));
                     k = UP ? k - g : k + g;
                     if (g < G) break;
                 }

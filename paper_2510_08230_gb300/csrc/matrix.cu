@@ -527,6 +527,7 @@ static void destroy_handle(gk_matrix A) {
     A->stage_out.release();
     A->carry.release();
     if (A->side) cudaStreamDestroy(A->side);
+    if (A->side2) cudaStreamDestroy(A->side2);
     delete A;
 }
 
@@ -598,14 +599,40 @@ gk_status build_csr_plan(gk_matrix A, cudaStream_t s) {
         8192.0, std::max<double>(512.0, rows_per_tile * std::ceil(std::max(mean, 1.0))));
     chunk = (chunk + 7) & ~7;
     const int64_t cap = (int64_t)chunk + A->max_row + 16;
+    // warp tiles (kind 3): 32 * wt_rpl rows per warp, staged capacity of the
+    // longest possible tile, one stage per warp by default (measured on
+    // GB300, 3D 7-point 256^3 FP64: 1 stage 279 us, 2 stages 367 us, 3 644 us:
+    // a smaller ring lets more warps reside, which hides the copy latency
+    // better than prefetching within a warp); chosen for short rows of
+    // near-uniform length when 8 warps' rings leave room for two blocks per SM
+    const int64_t vb = (int64_t)value_bytes(A->dtype);
+    int wt_rpl = 2;
+    if (const char* e = getenv("GK_WT_RPL")) {
+        const int v = atoi(e);
+        wt_rpl = (v == 1 || v == 4) ? v : 2;
+    }
+    const int64_t wt_cap = ((int64_t)32 * wt_rpl * A->max_row + 14 + 7) & ~(int64_t)7;
+    int wt_nst = 1;
+    if (const char* e = getenv("GK_WT_STAGES")) wt_nst = std::max(1, std::min(4, atoi(e)));
+    auto wt_block_bytes = [&](int nst) {
+        return (int64_t)WT_WARPS * (((int64_t)nst * wt_cap * (4 + vb) + 8 * nst + 127) & ~(int64_t)127);
+    };
+    const bool wt_fits = wt_block_bytes(wt_nst) <= WT_SMEM_CAP;
     int kind = (A->max_row <= 1024) ? 1 : 2;
+    if (wt_fits && wt_block_bytes(wt_nst) <= 112 * 1024 && A->max_row <= 2.0 * mean + 1.0)
+        kind = 3;
     if (const char* force = getenv("GK_CSR_KERNEL")) kind = atoi(force);
+    if (kind == 3 && !wt_fits) kind = 1;
     // a single staged tile must fit in shared memory
     if (kind == 1 && ((cap + 7) & ~7) * (int64_t)(4 + value_bytes(A->dtype)) > 200 * 1024) kind = 2;
     P.kind = kind;
     P.stages = 1;
     if (const char* e = getenv("GK_ROWTILE_STAGES")) P.stages = std::max(1, std::min(3, atoi(e)));
-    if (kind == 1) {
+    if (kind == 3) {
+        P.stages = wt_nst;
+        P.wt_rpl = wt_rpl;
+        P.tile_cap = (int32_t)wt_cap;
+    } else if (kind == 1) {
         P.chunk = chunk;
         P.tile_cap = (int32_t)((cap + 7) & ~7);
         P.ntiles = (int32_t)std::max<int64_t>(1, (A->nnz + chunk - 1) / chunk);
@@ -995,10 +1022,23 @@ gk_status gk_matrix_describe(gk_matrix A, gk_matrix_desc* d) {
     d->slice_size = A->S;
     d->stride_factor = A->f;
     d->num_slices = A->nslices;
-    d->spmv_kernel = A->coo ? 5 : A->fmt == GK_CSR ? A->plan.kind : A->fmt == GK_ELL ? 3 : 4;
+    d->spmv_kernel = A->coo ? 5
+                     : A->fmt == GK_CSR ? (A->plan.kind == 3 ? 6 : A->plan.kind)
+                     : A->fmt == GK_ELL ? 3 : 4;
     if (A->plan.err) {
         int32_t e = 0;
-        if (cudaMemcpy(&e, A->plan.err, 4, cudaMemcpyDeviceToHost) == cudaSuccess) d->device_error = e;
+        if (cudaMemcpy(&e, A->plan.err, 4, cudaMemcpyDeviceToHost) == cudaSuccess && e)
+            d->device_error |= 1;
+    }
+    // the substitution kernels' sticky error words (TriStore::sync: four
+    // words per direction, the third is the error flag)
+    const gk::TriStore* tri[2] = {A->ilu, A->tri};
+    for (int k = 0; k < 2; ++k) {
+        if (!tri[k] || tri[k]->state != 1 || !tri[k]->sync) continue;
+        uint32_t w[8] = {};
+        if (cudaMemcpy(w, tri[k]->sync, sizeof(w), cudaMemcpyDeviceToHost) == cudaSuccess &&
+            (w[2] | w[6]))
+            d->device_error |= 2 << k;
     }
     d->spmv_launches = A->coo ? (A->n_empty ? 3 : 2)
                        : (A->fmt == GK_CSR && A->plan.kind == 2) ? 2 : 1;

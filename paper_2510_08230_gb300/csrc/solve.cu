@@ -134,9 +134,14 @@ gk_status get_lowp(gk_matrix A, gk_dtype d, cudaStream_t s, gk_matrix* out) {
 // SpMV layout for solves on a CSR matrix (solver format selection).  The
 // padded layouts stream their column/value arrays with paired, fully
 // coalesced loads and no row-pointer indirection, so when padding costs
-// little they beat every CSR kernel.  Default rule, decided on the first
-// solve and kept: ELL when its stored entries are at most 1.2 x nnz, else
-// SELL-P(32) when its stored entries are at most 1.2 x nnz, else the CSR
+// little they beat the CSR row-tile and merge kernels.  The CSR warp-tile
+// kernel (short rows of near-uniform length) comes within a few per cent of
+// ELL (GB300, 3D 7-point 256^3: 262 against 255 us in FP64, 166 against
+// 163 us in FP32) and sums every row in the same order, so such matrices
+// solve on their own CSR arrays and keep no padded copy.  Default rule,
+// decided on the first solve and kept: the CSR itself when its plan is the
+// warp-tile kernel, else ELL when its stored entries are at most 1.2 x nnz,
+// else SELL-P(32) when its stored entries are at most 1.2 x nnz, else the CSR
 // itself.  The rule depends only on the sparsity pattern, so every handle of
 // a matrix solves with the same summation order (bit-identical results).
 // GK_SOLVE_FORMAT=csr|ell|sellp forces a layout; GK_SOLVE_FORMAT=timed times
@@ -153,6 +158,11 @@ static gk_status solve_matrix(gk_matrix A, cudaStream_t s, gk_matrix* out) {
     const char* env = getenv("GK_SOLVE_FORMAT");
     const bool timed = env && !strcmp(env, "timed");
     const bool force = env && !timed && strcmp(env, "auto") != 0;
+    if (!force && !timed && A->plan.kind == 3) {
+        A->solve_fmt = nullptr;
+        A->solve_fmt_tuned = 1;
+        return GK_OK;
+    }
     const bool want_ell = !force || !strcmp(env, "ell");
     const bool want_sellp = !force || !strcmp(env, "sellp");
     auto padding_ok = [&](int64_t stored) { return force || stored <= A->nnz + A->nnz / 5; };
@@ -207,6 +217,7 @@ static gk_status solve_matrix(gk_matrix A, cudaStream_t s, gk_matrix* out) {
 
 gk_status side_stream(gk_matrix A) {
     if (!A->side) GK_CUDA(cudaStreamCreateWithFlags(&A->side, cudaStreamNonBlocking));
+    if (!A->side2) GK_CUDA(cudaStreamCreateWithFlags(&A->side2, cudaStreamNonBlocking));
     return GK_OK;
 }
 
@@ -242,8 +253,22 @@ static gk_status check_opts(gk_matrix A, const gk_solve_opts* o) {
     if (o->mixed < 0 || o->mixed > 3) return GK_ERR_INVALID;
     if (o->mixed && A->dtype != GK_F64) return GK_ERR_INVALID;
     if (o->engine < 0 || o->engine > 3) return GK_ERR_INVALID;
+    if (o->wait_budget_ns < 0) return GK_ERR_INVALID;
     if (A->n != A->ncols) return GK_ERR_INVALID;
     return GK_OK;
+}
+
+// The wait budget of a solve reaches every handle whose kernels the solve
+// launches (A, its solver layout copy, its low-precision copies); after the
+// solve they return to the default.
+static void reset_wait(gk_matrix A) {
+    A->wait_ns = WAIT_LIMIT_NS;
+    if (A->solve_fmt) A->solve_fmt->wait_ns = WAIT_LIMIT_NS;
+    for (gk_matrix L : A->lowp)
+        if (L) {
+            L->wait_ns = WAIT_LIMIT_NS;
+            if (L->solve_fmt) L->solve_fmt->wait_ns = WAIT_LIMIT_NS;
+        }
 }
 
 template <typename V, typename T>
@@ -252,8 +277,12 @@ static gk_status solve_plain(gk_matrix A, const void* b, void* x, const gk_solve
     const int m = o->method == GK_GMRES ? (o->krylov_dim ? o->krylov_dim : 30) : 0;
     gk_matrix M = nullptr;
     GK_TRY(solve_matrix(A, s, &M));
-    return solve_mk<V, T>(M, (const T*)b, (T*)x, o->method, (int)o->precond, o->block_size,
-                          o->tol, o->max_iters, m, s, out, false);
+    M->wait_ns = A->wait_ns;
+    GK_TRY((solve_mk<V, T>(M, (const T*)b, (T*)x, o->method, (int)o->precond, o->block_size,
+                           o->tol, o->max_iters, m, s, out, false)));
+    out->layout = M->fmt;
+    out->slice = M->fmt == GK_SELLP ? M->S : 0;
+    return GK_OK;
 }
 
 // FP64 iterative refinement: r = b - A x in FP64; inner solve of
@@ -267,6 +296,7 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
     GK_TRY(solve_matrix(L, s, &L));  // layout of the inner SpMV
     gk_matrix A64 = nullptr;
     GK_TRY(solve_matrix(A, s, &A64));  // layout of the outer FP64 residual
+    L->wait_ns = A64->wait_ns = A->wait_ns;
     SolverCache* C = nullptr;
     GK_TRY(get_cache(A, &C));
     // FP64 workspace: r64 ; FP32: r32, d32 (in the low-precision handle's cache
@@ -391,7 +421,7 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
             finish64 = true;
             break;
         }
-        if (io.status < GK_ERR_NAN) {
+        if (io.status < 0) {  // an error other than NaN (a timed-out wait, CUDA): d is invalid
             status = io.status;
             break;
         }
@@ -415,6 +445,8 @@ static gk_status solve_ir(gk_matrix A, const double* b, double* x, const gk_solv
     out->restarts = restarts;
     out->rec = last_rec;
     out->tru = tn / bnorm;
+    out->layout = A64->fmt;
+    out->slice = A64->fmt == GK_SELLP ? A64->S : 0;
     *outer = k;
     return GK_OK;
 }
@@ -428,6 +460,64 @@ int32_t cluster_max_n();
 }  // namespace gk
 
 using namespace gk;
+
+namespace gk {
+// info of a solve decided before any iteration (n = 0), in device memory
+__global__ void k_info_trivial(gk_solve_info* info, int32_t layout) {
+    gk_solve_info o = {};
+    o.status = GK_OK;
+    o.spmv_format = layout;
+    *info = o;
+}
+}  // namespace gk
+
+extern "C" gk_status gk_solve_async(gk_matrix A, const void* b, void* x,
+                                    const gk_solve_opts* opts, gk_solve_info* info,
+                                    void* stream) {
+    if (!A || !opts || !info) return GK_ERR_INVALID;
+    if (A->n > 0 && (!b || !x)) return GK_ERR_INVALID;
+    GK_TRY(check_opts(A, opts));
+    if (opts->mixed) return GK_ERR_UNSUPPORTED;  // refinement's outer loop runs on the host
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != A->device) return GK_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(A->mu);
+    A->wait_ns = opts->wait_budget_ns > 0 ? (uint64_t)opts->wait_budget_ns : WAIT_LIMIT_NS;
+    struct ResetWait {
+        gk_matrix A;
+        ~ResetWait() { reset_wait(A); }
+    } reset_on_exit{A};
+    if (A->n == 0) {
+        k_info_trivial<<<1, 1, 0, s>>>(info, A->fmt);
+        GK_CUDA(cudaGetLastError());
+        return GK_OK;
+    }
+    gk_matrix M = nullptr;
+    GK_TRY(solve_matrix(A, s, &M));
+    M->wait_ns = A->wait_ns;
+    const int m = opts->method == GK_GMRES ? (opts->krylov_dim ? opts->krylov_dim : 30) : 0;
+    SolveOut out;
+    const int pk = (int)opts->precond;
+    switch (A->dtype) {
+        case GK_F64:
+            return solve_mk<double, double>(M, (const double*)b, (double*)x, opts->method, pk,
+                                            opts->block_size, opts->tol, opts->max_iters, m, s,
+                                            &out, false, info);
+        case GK_F32:
+            return solve_mk<float, float>(M, (const float*)b, (float*)x, opts->method, pk,
+                                          opts->block_size, opts->tol, opts->max_iters, m, s, &out,
+                                          false, info);
+        case GK_F16:
+            return solve_mk<__half, float>(M, (const float*)b, (float*)x, opts->method, pk,
+                                           opts->block_size, opts->tol, opts->max_iters, m, s, &out,
+                                           false, info);
+        default:
+            return solve_mk<__nv_bfloat16, float>(M, (const float*)b, (float*)x, opts->method, pk,
+                                                  opts->block_size, opts->tol, opts->max_iters, m, s,
+                                                  &out, false, info);
+    }
+}
 
 extern "C" gk_status gk_solve(gk_matrix A, const void* b, void* x, const gk_solve_opts* opts,
                               gk_solve_info* info, void* stream) {
@@ -443,6 +533,11 @@ extern "C" gk_status gk_solve(gk_matrix A, const void* b, void* x, const gk_solv
     int32_t outer = 0;
     SolverCache* C = nullptr;
     GK_TRY(get_cache(A, &C));
+    A->wait_ns = opts->wait_budget_ns > 0 ? (uint64_t)opts->wait_budget_ns : WAIT_LIMIT_NS;
+    struct ResetWait {
+        gk_matrix A;
+        ~ResetWait() { reset_wait(A); }
+    } reset_on_exit{A};
     GK_CUDA(cudaEventRecord(C->ev0, s));
     gk_status st = GK_OK;
     if (A->n == 0) {
@@ -486,6 +581,9 @@ extern "C" gk_status gk_solve(gk_matrix A, const void* b, void* x, const gk_solv
         info->rel_res_recurrence = out.rec;
         info->rel_res_true = out.tru;
         info->device_ms = ms;
+        info->spmv_format = out.layout;
+        info->slice_size = out.slice;
+        info->block_threads = out.threads;
     }
     return out.status;
 }

@@ -59,6 +59,16 @@ struct KState {
     double best_rn;    // CG/BiCGSTAB/CGS inner solves: best residual so far ...
     int32_t best_iter; // ... and its iteration
     int32_t stall;     // stop after this many iterations without a 10 % gain (0: off)
+    // the solver loop on the device (see k_ctl_*): the requested reduction,
+    // the loop's control words and its bounds
+    double tol;
+    int32_t inner;      // a refinement inner solve (stops after two replacements)
+    int32_t done;       // the loop ends after this pass
+    int32_t nocheck;    // 0: this pass confirms a passed recurrence by the true residual
+    int32_t noreplace;  // 0: this pass restarts from x with r = b - A x
+    int32_t nofinal;    // 0: the exit computes the true residual
+    int32_t nozero;     // 0: b = 0, the exit zeroes x
+    int32_t loops, max_loops, checks_left;
     double H[(MAXM + 1) * MAXM];
     double cs[MAXM], sn[MAXM], g[MAXM + 1], y[MAXM];
     double h1[MAXM + 1], h2[MAXM + 1];
@@ -304,12 +314,15 @@ __global__ void EW_BOUNDS k_norm2(int32_t n, const T* __restrict__ v, double* pa
 }
 
 template <typename T>
-__global__ void EW_BOUNDS k_zero(int32_t n, T* __restrict__ v) {
+__global__ void EW_BOUNDS k_zero(int32_t n, T* __restrict__ v, const int32_t* gate = nullptr) {
+    if (gate && *reinterpret_cast<const volatile int32_t*>(gate) != 0) return;
     GRID_LOOP(i, n) v[i] = T(0);
 }
 
 template <typename T>
-__global__ void EW_BOUNDS k_copy(int32_t n, const T* __restrict__ a, T* __restrict__ b) {
+__global__ void EW_BOUNDS k_copy(int32_t n, const T* __restrict__ a, T* __restrict__ b,
+                                 const int32_t* gate = nullptr) {
+    if (gate && *reinterpret_cast<const volatile int32_t*>(gate) != 0) return;
     GRID_LOOP(i, n) b[i] = a[i];
 }
 
@@ -577,7 +590,8 @@ struct CgInitFin {
 template <typename T>
 __global__ void EW_BOUNDS k_cg_init(int32_t n, const T* __restrict__ r, T* __restrict__ z, T* __restrict__ p,
                           const T* __restrict__ dinv, KState* st, double* partials,
-                          unsigned* ticket) {
+                          unsigned* ticket, const int32_t* gate = nullptr) {
+    if (gate && *reinterpret_cast<const volatile int32_t*>(gate) != 0) return;
     T a[1] = {T(0)};
     GRID_LOOP(i, n) {
         const T ri = r[i];
@@ -789,7 +803,9 @@ struct BiInitFin {
 // rhat = r ; p = v = 0 ; rho = <rhat, r>
 template <typename T>
 __global__ void EW_BOUNDS k_bi_init(int32_t n, const T* __restrict__ r, T* __restrict__ rh, T* __restrict__ p,
-                          T* __restrict__ v, KState* st, double* partials, unsigned* ticket) {
+                          T* __restrict__ v, KState* st, double* partials, unsigned* ticket,
+                          const int32_t* gate = nullptr) {
+    if (gate && *reinterpret_cast<const volatile int32_t*>(gate) != 0) return;
     T a[1] = {T(0)};
     GRID_LOOP(i, n) {
         const T ri = r[i];
@@ -828,7 +844,9 @@ struct CgsInitFin {
 
 template <typename T>
 __global__ void EW_BOUNDS k_cgs_init(int32_t n, const T* __restrict__ r, T* __restrict__ rt,
-                                     KState* st, double* partials, unsigned* ticket) {
+                                     KState* st, double* partials, unsigned* ticket,
+                                     const int32_t* gate = nullptr) {
+    if (gate && *reinterpret_cast<const volatile int32_t*>(gate) != 0) return;
     constexpr int N = Pack<T>::N;
     const bool vec = al16(r) && al16(rt);
     T a[1] = {T(0)};
@@ -1478,11 +1496,11 @@ __global__ void k_jacobi_gen_padded(int32_t n, int fmt, int64_t stride, int32_t 
 // Setup fins: ||b|| -> thr; initial true residual
 struct FinBnorm {
     KState* st;
-    double tol;
+    double tol;  // < 0: the state's tol
     __device__ void operator()(double* t) const {
         const double bn = sqrt(t[0]);
         st->bnorm = bn;
-        st->thr = tol * bn;
+        st->thr = (tol < 0.0 ? st->tol : tol) * bn;
         if (!isfinite(bn)) {
             st->status = GK_ERR_NAN;
             st->halt = 2;
@@ -1724,6 +1742,14 @@ struct IluSkipHalt {
     __device__ __forceinline__ bool skip() const { return halted(st); }
 };
 
+// runs only while *gate is 0 (a gated step of the device solver loop)
+struct IluSkipGate {
+    const int32_t* gate;
+    __device__ __forceinline__ bool skip() const {
+        return *reinterpret_cast<const volatile int32_t*>(gate) != 0;
+    }
+};
+
 // GMRES v_0 step: only when a restart decided to continue
 struct IluSkipV0 {
     const KState* st;
@@ -1788,6 +1814,145 @@ __global__ void EW_BOUNDS k_dot_fin(int32_t n, const T* __restrict__ a, const T*
 
 constexpr size_t HDR = offsetof(KState, H);
 
+// ------------------------------------------------------------ device solver loop
+// The Krylov loop of the multi-kernel engine runs inside one CUDA graph: a
+// conditional WHILE node repeats a body made of a chunk of iterations and
+// the one-thread control steps below; cudaGraphSetConditional ends it.  The
+// control is the stopping rule: a recurrence residual that passes is
+// confirmed by the true residual b - A x; if that fails, the recurrence
+// restarts from x with r = b - A x (residual replacement), at most
+// checks_left times, and an inner solve of refinement stops after two
+// replacements.  max_loops bounds the passes whatever happens, so the loop
+// always ends.  The steps that run only on some passes (the confirmation,
+// the replacement, the exit's true residual) are kernels that return at once
+// unless their gate word in the state is 0.
+
+// A solve's state header: zero, then its parameters (on the caller's stream,
+// before the graph).
+static __global__ void k_state_init(KState* st, double tol, int32_t max_iters, int32_t m, double stag,
+                             int32_t stall, int32_t inner, int32_t max_loops, int32_t max_checks) {
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(st);
+    for (size_t k = 0; k < HDR / sizeof(unsigned long long); ++k) w[k] = 0ull;
+    st->tol = tol;
+    st->max_iters = max_iters;
+    st->m = m;
+    st->stag = stag;
+    st->stall = stall;
+    st->inner = inner;
+    st->max_loops = max_loops;
+    st->checks_left = max_checks;
+    st->nocheck = st->noreplace = st->nofinal = st->nozero = 1;
+}
+
+// after a chunk (CG, BiCGSTAB, CGS): stop, or confirm a passed recurrence
+static __global__ void k_ctl_check(KState* st) {
+    st->loops += 1;
+    st->nocheck = 1;
+    st->noreplace = 1;
+    if (st->halt == 2) {
+        st->done = 1;
+        return;
+    }
+    if (st->loops > st->max_loops) {
+        st->status = GK_ERR_TIMEOUT;
+        st->halt = 2;
+        st->done = 1;
+        return;
+    }
+    if (st->halt == 1) {
+        if (st->inner && st->restarts >= 2) {  // the outer FP64 residual decides
+            st->done = 1;
+            return;
+        }
+        if (--st->checks_left < 0) {
+            st->status = GK_ERR_TIMEOUT;
+            st->halt = 2;
+            st->done = 1;
+            return;
+        }
+        st->halt = 0;
+        st->nocheck = 0;  // the true residual runs next
+    }
+}
+
+// after the true residual: converged (its fin set halt = 2), out of
+// iterations, or replace r and restart
+static __global__ void k_ctl_replace(KState* st) {
+    if (st->nocheck) return;
+    st->nocheck = 1;
+    if (st->halt == 2) {
+        st->done = 1;
+        return;
+    }
+    if (st->iter >= st->max_iters) {
+        st->status = GK_NOT_CONVERGED;
+        st->halt = 2;
+        st->done = 1;
+        return;
+    }
+    st->noreplace = 0;  // r = b - A x and the method's restart run next
+}
+
+// end of a pass: count a replacement, and loop again unless done
+static __global__ void k_ctl_next(KState* st, cudaGraphConditionalHandle h) {
+    if (!st->noreplace) {
+        st->restarts += 1;
+        st->noreplace = 1;
+    }
+    cudaGraphSetConditional(h, st->done ? 0u : 1u);
+}
+
+// end of a GMRES pass: loop until halted (restarts are decided inside)
+static __global__ void k_ctl_gmres(KState* st, cudaGraphConditionalHandle h) {
+    st->loops += 1;
+    if (st->halt == 0 && st->loops > st->max_loops) {
+        st->status = GK_ERR_TIMEOUT;
+        st->halt = 2;
+    }
+    cudaGraphSetConditional(h, st->halt ? 0u : 1u);
+}
+
+// after the loop: whether the exit computes the true residual (not for an
+// inner solve that stopped on its recurrence) or zeroes x (b = 0)
+static __global__ void k_ctl_exit(KState* st) {
+    const bool inner_pass = st->inner && st->halt == 1;
+    st->nofinal = (st->bnorm > 0.0 && !inner_pass) ? 0 : 1;
+    st->nozero = st->bnorm == 0.0 ? 0 : 1;
+}
+
+// The outcome of a solve from its state (the rules of gk_solve): written
+// to info (host or device memory) by write_info / k_write_info.
+__host__ __device__ inline void solve_outcome(const KState* st, bool rowtile_err, int32_t layout,
+                                              int32_t slice, gk_solve_info* o) {
+    int status = st->status;
+    const bool inner_pass = st->inner && st->halt == 1;
+    const double bn = st->bnorm;
+    o->iters = st->iter;
+    o->restarts = st->restarts;
+    o->outer_iters = 0;
+    o->rel_res_recurrence = bn > 0.0 ? st->rnorm / bn : 0.0;
+    o->rel_res_true = inner_pass ? o->rel_res_recurrence : (bn > 0.0 ? st->tnorm / bn : 0.0);
+    if (inner_pass) status = GK_OK;
+    if (bn == 0.0) {
+        status = GK_OK;
+        o->iters = 0;
+        o->rel_res_recurrence = o->rel_res_true = 0.0;
+    }
+    if (rowtile_err) status = GK_ERR_TIMEOUT;
+    o->status = (gk_status)status;
+    o->device_ms = 0.f;
+    o->spmv_format = layout;
+    o->slice_size = slice;
+    o->block_threads = 0;
+}
+
+static __global__ void k_write_info(const KState* st, gk_solve_info* info, const int32_t* rowtile_err,
+                             int32_t layout, int32_t slice) {
+    gk_solve_info o;
+    solve_outcome(st, rowtile_err && *rowtile_err != 0, layout, slice, &o);
+    *info = o;
+}
+
 struct SolverCache {
     DevBuf vecs, partials, ticket, state;
     KState* hst = nullptr;  // pinned mirror of the state header
@@ -1795,10 +1960,9 @@ struct SolverCache {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // key of the captured graph
-    const void* kb = nullptr;
-    void* kx = nullptr;
     void* kv = nullptr;
     int kmethod = -1, kprec = -1, km = -1, kchunk = 0;
+    uint64_t kwait = 0;  // wait budget the graph's kernels were captured with
     ~SolverCache() {
         if (exec) cudaGraphExecDestroy(exec);
         if (hst) cudaFreeHost(hst);
@@ -1831,9 +1995,12 @@ static gk_status ensure_vecs(SolverCache* C, int64_t n, int count) {
     return C->vecs.ensure(stride * (size_t)count + 256);
 }
 
-// Capture `chunk` iterations of `body` into C->exec (cached by key).
-template <class Body>
-static gk_status capture_chunk(gk_matrix A, SolverCache* C, int chunk, Body&& body) {
+// Captures a whole solve into C->exec: pre(stream), then a conditional
+// WHILE node whose body is body(stream, handle) (it must end with a kernel
+// that sets the handle), then post(stream).  The body is captured on the
+// handle's second library stream into the node's child graph.
+template <class Pre, class Body, class Post>
+static gk_status capture_solve(gk_matrix A, SolverCache* C, Pre&& pre, Body&& body, Post&& post) {
     GK_TRY(side_stream(A));
     if (C->exec) {
         cudaGraphExecDestroy(C->exec);
@@ -1841,11 +2008,48 @@ static gk_status capture_chunk(gk_matrix A, SolverCache* C, int chunk, Body&& bo
     }
     cudaGraph_t g = nullptr;
     GK_CUDA(cudaStreamBeginCapture(A->side, cudaStreamCaptureModeThreadLocal));
-    gk_status st = GK_OK;
-    for (int c = 0; c < chunk && st == GK_OK; ++c) st = body(A->side);
+    gk_status st = pre(A->side);
+    if (st == GK_OK) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        cudaGraphConditionalHandle hc = 0;
+        cudaGraphNodeParams cp = {};
+        cudaGraphNode_t node = nullptr;
+        if (cudaStreamGetCaptureInfo(A->side, &cs, nullptr, &cg, &deps, nullptr, &ndeps) !=
+                cudaSuccess ||
+            cs != cudaStreamCaptureStatusActive ||
+            cudaGraphConditionalHandleCreate(&hc, cg, 1, cudaGraphCondAssignDefault) != cudaSuccess) {
+            st = GK_ERR_CUDA;
+        } else {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = hc;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            if (cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp) != cudaSuccess ||
+                cudaStreamUpdateCaptureDependencies(A->side, &node, nullptr, 1,
+                                                    cudaStreamSetCaptureDependencies) != cudaSuccess)
+                st = GK_ERR_CUDA;
+        }
+        if (st == GK_OK) {
+            if (cudaStreamBeginCaptureToGraph(A->side2, cp.conditional.phGraph_out[0], nullptr,
+                                              nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+                cudaSuccess) {
+                st = GK_ERR_CUDA;
+            } else {
+                st = body(A->side2, hc);
+                cudaGraph_t bg = nullptr;
+                if (cudaStreamEndCapture(A->side2, &bg) != cudaSuccess && st == GK_OK)
+                    st = GK_ERR_CUDA;
+            }
+        }
+    }
+    if (st == GK_OK) st = post(A->side);
     cudaError_t e = cudaStreamEndCapture(A->side, &g);
     if (st != GK_OK) {
         if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
         return st;
     }
     GK_CUDA(e);
@@ -1866,10 +2070,23 @@ inline int chunk_for(int64_t n) { return n < 200000 ? 32 : 8; }
 // convergence, and an FP32 solve can stall above a tight inner tolerance.
 template <typename V, typename T>
 gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t bs, double tol,
-                   int32_t max_iters, int32_t m, cudaStream_t s, SolveOut* out, bool inner) {
+                   int32_t max_iters, int32_t m, cudaStream_t s, SolveOut* out, bool inner,
+                   gk_solve_info* info_dev = nullptr) {
     const int32_t n = A->n;
     SolverCache* C = nullptr;
     GK_TRY(get_cache(A, &C));
+    // a row-tile SpMV whose wait ran past the budget sets the matrix's error
+    // word: cleared here, turned into GK_ERR_TIMEOUT at the end
+    const bool rowtile = A->fmt == GK_CSR && (A->plan.kind == 1 || A->plan.kind == 3) && A->plan.err;
+    if (rowtile) GK_CUDA(cudaMemsetAsync(A->plan.err, 0, sizeof(int32_t), s));
+    auto rowtile_timeout = [&]() -> bool {
+        if (!rowtile) return false;
+        int32_t e = 0;
+        if (cudaMemcpyAsync(&e, A->plan.err, sizeof(e), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return true;
+        return e != 0;
+    };
     // preconditioner: pkind 0 none, 1 Jacobi (fused into the update kernels
     // as dinv), 2 block-Jacobi of bs rows (separate k_bj_* kernels; the
     // update kernels then run unpreconditioned into the vectors B is
@@ -1891,12 +2108,13 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
     } else if (ilu) {
         GK_TRY(ensure_ilu(A, s));
         ild = ilu_view<T>(A);
+        ild.wait_ns = A->wait_ns;
         GK_TRY(ilu_clear_err(ild, s));
     }
     const int nvec0 = method == GK_CG ? 5 : (method == GK_BICGSTAB || method == GK_CGS) ? 10 : m + 5;
     // ILU: two more vectors, the L substitution's output and GMRES's scratch
     const int nvec = nvec0 + (ilu ? 2 : 0);
-    GK_TRY(ensure_vecs<T>(C, n, nvec));
+    GK_TRY(ensure_vecs<T>(C, n, nvec + 2));  // + the solve's copies of b and x
     T* ilu_w = ilu ? vec_at<T>(C, n, nvec0) : nullptr;
     T* ilu_s = ilu ? vec_at<T>(C, n, nvec0 + 1) : nullptr;
     // multi-dot kernels: one wave of resident blocks sharing the rows equally
@@ -1915,39 +2133,58 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
     KState* st = (KState*)C->state.ptr;
     const int32_t* halt = &st->halt;
 
-    // state header
-    KState* h = C->hst;
-    std::memset(h, 0, HDR);
-    h->max_iters = max_iters;
-    h->m = m;
-    h->stag = inner ? 0.95 : 0.0;
-    h->stall = inner ? 200 : 0;
-    GK_CUDA(cudaMemcpyAsync(st, h, HDR, cudaMemcpyHostToDevice, s));
-    k_norm2<T, FinBnorm><<<ewg(k_norm2<T, FinBnorm>, n), 256, 0, s>>>(n, b, part, tk, FinBnorm{st, tol});
+    // The solve reads and writes the handle's own copies of b and x, so the
+    // cached graph serves every right-hand side and initial guess.
+    T* bi = vec_at<T>(C, n, nvec);
+    T* xi = vec_at<T>(C, n, nvec + 1);
+    GK_CUDA(cudaMemcpyAsync(bi, b, sizeof(T) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    GK_CUDA(cudaMemcpyAsync(xi, x, sizeof(T) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    const int chunk = chunk_for(n);
+    const int32_t max_checks = max_iters + 4;
+    const int32_t max_loops = method == GK_GMRES ? max_iters / chunk + 8
+                                                 : max_iters / chunk + max_checks + 8;
+    k_state_init<<<1, 1, 0, s>>>(st, tol, max_iters, m, inner ? 0.95 : 0.0, inner ? 200 : 0,
+                                 inner ? 1 : 0, max_loops, max_checks);
     GK_CUDA(cudaGetLastError());
-
-    T *r = vec_at<T>(C, n, 0), *tmp = vec_at<T>(C, n, 1);
-    if (method == GK_GMRES) {
+    const int pkey = pkind * 64 + (block ? bs : 0);
+    T* r = vec_at<T>(C, n, 0);
+    T* tmp = vec_at<T>(C, n, 1);
+    // exit: the true residual (unless an inner solve stopped on its
+    // recurrence) or x = 0 for b = 0
+    auto post = [&](cudaStream_t cs) -> gk_status {
+        k_ctl_exit<<<1, 1, 0, cs>>>(st);
+        EpiResid<T, FinNorm> ef{tmp, bi, &st->nofinal, part, tk, FinNorm{st, 1}};
+        GK_TRY((launch_spmv_rows<V, T>(A, xi, ef, cs)));
+        k_zero<T><<<ewg(k_zero<T>, n), 256, 0, cs>>>(n, xi, &st->nozero);
+        GK_CUDA(cudaGetLastError());
+        return GK_OK;
+    };
+    const bool stale = !C->exec || C->kmethod != method || C->kprec != pkey || C->km != m ||
+                       C->kchunk != chunk || C->kv != (void*)C->vecs.ptr ||
+                       C->kwait != A->wait_ns;
+    if (method == GK_GMRES && stale) {
         T* Vm = vec_at<T>(C, n, 3);
         T *w = vec_at<T>(C, n, 1), *z = vec_at<T>(C, n, 2);
         const int64_t ldv = (int64_t)(((size_t)n * sizeof(T) + 255) & ~(size_t)255) / sizeof(T);
-        // cycle start: r = b - A x, restart fin sets g, k; v0 = r / beta0
-        EpiResid<T, GmRestartFin> e0{r, b, halt, part, tk, GmRestartFin{st}};
-        GK_TRY((launch_spmv_rows<V, T>(A, x, e0, s)));
         T* ubuf = vec_at<T>(C, n, m + 4);  // V y at a cycle end (block-Jacobi / ILU only)
-        k_gm_v0<T><<<ewg(k_gm_v0<T>, n), 256, 0, s>>>(n, Vm, r, z, dinv, st);
-        if (block)
-            k_bj_apply<T, EpiBjV0<T>><<<ewg(k_bj_apply<T, EpiBjV0<T>>, n), 256, 0, s>>>(
-                n, bs, binv, Vm, EpiBjV0<T>{z, st});
-        if (ilu)
-            GK_TRY(ilu_apply<T>(ild, IluSrc<T>{Vm}, ilu_w, IluOutStore<T>{z}, IluSkipV0{st},
-                                IluErrSt{st}, s));
-        GK_CUDA(cudaGetLastError());
-        const int chunk = chunk_for(n);
-        const int pkey = pkind * 64 + (block ? bs : 0);
-        if (!C->exec || C->kb != b || C->kx != x || C->kmethod != method || C->kprec != pkey ||
-            C->km != m || C->kchunk != chunk || C->kv != (void*)C->vecs.ptr) {
-            GK_TRY(capture_chunk(A, C, chunk, [&](cudaStream_t cs) -> gk_status {
+        auto pre = [&](cudaStream_t cs) -> gk_status {
+            k_norm2<T, FinBnorm><<<ewg(k_norm2<T, FinBnorm>, n), 256, 0, cs>>>(
+                n, bi, part, tk, FinBnorm{st, -1.0});
+            // cycle start: r = b - A x, restart fin sets g, k; v0 = r / beta0
+            EpiResid<T, GmRestartFin> e0{r, bi, halt, part, tk, GmRestartFin{st}};
+            GK_TRY((launch_spmv_rows<V, T>(A, xi, e0, cs)));
+            k_gm_v0<T><<<ewg(k_gm_v0<T>, n), 256, 0, cs>>>(n, Vm, r, z, dinv, st);
+            if (block)
+                k_bj_apply<T, EpiBjV0<T>><<<ewg(k_bj_apply<T, EpiBjV0<T>>, n), 256, 0, cs>>>(
+                    n, bs, binv, Vm, EpiBjV0<T>{z, st});
+            if (ilu)
+                GK_TRY(ilu_apply<T>(ild, IluSrc<T>{Vm}, ilu_w, IluOutStore<T>{z}, IluSkipV0{st},
+                                    IluErrSt{st}, cs));
+            GK_CUDA(cudaGetLastError());
+            return GK_OK;
+        };
+        auto body = [&](cudaStream_t cs, cudaGraphConditionalHandle hc) -> gk_status {
+            for (int c = 0; c < chunk; ++c) {
                 EpiStoreHalt<T> e1{w, halt};
                 GK_TRY((launch_spmv_rows<V, T>(A, z, e1, cs)));
                 k_gm_dot1<T><<<md_grid_of(k_gm_dot1<T>), MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st,
@@ -1956,17 +2193,17 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
                                                                                part, tk);
                 k_gm_orth<T><<<md_grid_of(k_gm_orth<T>), MD_THREADS, 0, cs>>>(n, ldv, Vm, w, st,
                                                                                part, tk);
-                k_gm_next<T><<<ewg(k_gm_next<T>, n), 256, 0, cs>>>(n, ldv, Vm, w, z, x, dinv, st,
+                k_gm_next<T><<<ewg(k_gm_next<T>, n), 256, 0, cs>>>(n, ldv, Vm, w, z, xi, dinv, st,
                                                                    sep ? ubuf : nullptr);
                 if (block)
                     k_bj_gm<T><<<ewg(k_bj_gm<T>, n), 256, 0, cs>>>(n, bs, binv, Vm, ldv, ubuf, z,
-                                                                   x, st);
+                                                                   xi, st);
                 if (ilu)
                     GK_TRY(ilu_apply<T>(ild, IluSrcGm<T>{Vm, ldv, ubuf, st}, ilu_w,
-                                        IluOutGm<T>{z, ilu_s, x, st}, IluSkipHalt{st},
+                                        IluOutGm<T>{z, ilu_s, xi, st}, IluSkipHalt{st},
                                         IluErrSt{st}, cs));
-                EpiGmResid<T> e2{r, b, st, part, tk, GmRestartFin{st}};
-                GK_TRY((launch_spmv_rows<V, T>(A, x, e2, cs)));
+                EpiGmResid<T> e2{r, bi, st, part, tk, GmRestartFin{st}};
+                GK_TRY((launch_spmv_rows<V, T>(A, xi, e2, cs)));
                 k_gm_v0<T><<<ewg(k_gm_v0<T>, n), 256, 0, cs>>>(n, Vm, r, z, dinv, st);
                 if (block)
                     k_bj_apply<T, EpiBjV0<T>><<<ewg(k_bj_apply<T, EpiBjV0<T>>, n), 256, 0, cs>>>(
@@ -1974,211 +2211,192 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
                 if (ilu)
                     GK_TRY(ilu_apply<T>(ild, IluSrc<T>{Vm}, ilu_w, IluOutStore<T>{z},
                                         IluSkipV0{st}, IluErrSt{st}, cs));
-                GK_CUDA(cudaGetLastError());
-                return GK_OK;
-            }));
-            C->kb = b; C->kx = x; C->kmethod = method; C->kprec = pkey; C->km = m;
-            C->kchunk = chunk; C->kv = C->vecs.ptr;
-        }
-        GK_TRY(read_hdr(C, s));
-        // every chunk advances the step counter unless halted: bound the loop
-        int64_t chunks_left = (int64_t)max_iters / chunk + 4;
-        while (!C->hst->halt) {
-            if (--chunks_left < 0) return GK_ERR_TIMEOUT;
-            GK_CUDA(cudaGraphLaunch(C->exec, s));
-            GK_TRY(read_hdr(C, s));
-        }
-    } else {
-        // initial true residual r = b - A x (stops at once when it passes)
-        EpiResid<T, FinTrue> e0{r, b, halt, part, tk, FinTrue{st, 0}};
-        GK_TRY((launch_spmv_rows<V, T>(A, x, e0, s)));
-        auto init = [&]() -> gk_status {
-            if (method == GK_CG && block) {  // z = B r, rho = <r, z> ; p = z
-                T *zb = vec_at<T>(C, n, 4), *pb = vec_at<T>(C, n, 3);
-                using E0 = EpiDot<T, CgInitFin>;
-                k_bj_apply<T, E0><<<ewg(k_bj_apply<T, E0>, n), 256, 0, s>>>(
-                    n, bs, binv, r, E0{zb, r, nullptr, part, tk, CgInitFin{st}});
-                k_copy<T><<<ewg(k_copy<T>, n), 256, 0, s>>>(n, zb, pb);
-            } else if (method == GK_CG && ilu) {  // z = M^-1 r, rho = <r, z> ; p = z
-                T *zb = vec_at<T>(C, n, 4), *pb = vec_at<T>(C, n, 3);
-                GK_TRY(ilu_apply<T>(ild, IluSrc<T>{r}, ilu_w, IluOutStore<T>{zb}, IluSkipNever{},
-                                    IluErrSt{st}, s));
-                k_dot_fin<T, CgInitFin><<<ewg(k_dot_fin<T, CgInitFin>, n), 256, 0, s>>>(
-                    n, r, zb, nullptr, part, tk, CgInitFin{st});
-                k_copy<T><<<ewg(k_copy<T>, n), 256, 0, s>>>(n, zb, pb);
-            } else if (method == GK_CG)  // slots: 0 r, 1 tmp, 2 q, 3 p, 4 z
-                k_cg_init<T><<<ewg(k_cg_init<T>, n), 256, 0, s>>>(n, r, vec_at<T>(C, n, 4), vec_at<T>(C, n, 3), dinv,
-                                                st, part, tk);
-            else if (method == GK_CGS)
-                // slots: 0 r, 1 tmp, 2 rt, 3 u, 4 p, 5 q, 6 ph, 7 vh, 8 uh
-                k_cgs_init<T><<<ewg(k_cgs_init<T>, n), 256, 0, s>>>(n, r, vec_at<T>(C, n, 2), st,
-                                                                    part, tk);
-            else
-                // slots: 0 r, 1 tmp, 2 rhat, 3 p, 4 phat, 5 s, 6 v, 7 shat, 8 t
-                k_bi_init<T><<<ewg(k_bi_init<T>, n), 256, 0, s>>>(n, r, vec_at<T>(C, n, 2), vec_at<T>(C, n, 3),
-                                                vec_at<T>(C, n, 6), st, part, tk);
+            }
+            k_ctl_gmres<<<1, 1, 0, cs>>>(st, hc);
             GK_CUDA(cudaGetLastError());
             return GK_OK;
         };
-        GK_TRY(init());
-        const int chunk = chunk_for(n);
-        const int pkey = pkind * 64 + (block ? bs : 0);
-        if (!C->exec || C->kb != b || C->kx != x || C->kmethod != method || C->kprec != pkey ||
-            C->kchunk != chunk || C->kv != (void*)C->vecs.ptr) {
-            GK_TRY(capture_chunk(A, C, chunk, [&](cudaStream_t cs) -> gk_status {
-                if (method == GK_CG) {
-                    T *z = prec ? vec_at<T>(C, n, 4) : r, *p = vec_at<T>(C, n, 3),
-                      *q = vec_at<T>(C, n, 2);
-                    EpiDot<T, CgAlphaFin> e1{q, p, halt, part, tk, CgAlphaFin{st}};
-                    GK_TRY((launch_spmv_rows<V, T>(A, p, e1, cs)));
-                    k_cg_update<T><<<ewg(k_cg_update<T>, n), 256, 0, cs>>>(n, x, r, z, p, q, dinv, st, part, tk, pkind);
-                    if (block) {  // z = B r ; beta = <r, z> / rho
-                        using E1 = EpiDot<T, CgBetaFin>;
-                        k_bj_apply<T, E1><<<ewg(k_bj_apply<T, E1>, n), 256, 0, cs>>>(
-                            n, bs, binv, r, E1{z, r, halt, part, tk, CgBetaFin{st}});
-                    }
-                    if (ilu) {  // z = M^-1 r ; beta = <r, z> / rho
-                        GK_TRY(ilu_apply<T>(ild, IluSrc<T>{r}, ilu_w, IluOutStore<T>{z},
-                                            IluSkipHalt{st}, IluErrSt{st}, cs));
-                        k_dot_fin<T, CgBetaFin><<<ewg(k_dot_fin<T, CgBetaFin>, n), 256, 0, cs>>>(
-                            n, r, z, halt, part, tk, CgBetaFin{st});
-                    }
-                    k_cg_p<T><<<ewg(k_cg_p<T>, n), 256, 0, cs>>>(n, p, z, st);
-                } else if (method == GK_CGS) {
-                    T *rt = vec_at<T>(C, n, 2), *u = vec_at<T>(C, n, 3), *p = vec_at<T>(C, n, 4);
-                    T *q = vec_at<T>(C, n, 5), *ph = vec_at<T>(C, n, 6), *vh = vec_at<T>(C, n, 7);
-                    T *uh = vec_at<T>(C, n, 8), *tb = vec_at<T>(C, n, 9);
-                    const T* phs = prec ? ph : p;
-                    k_cgs_p<T><<<ewg(k_cgs_p<T>, n), 256, 0, cs>>>(n, u, p, ph, r, q, dinv, st);
-                    if (block)
-                        k_bj_apply<T, EpiStoreHalt<T>><<<ewg(k_bj_apply<T, EpiStoreHalt<T>>, n), 256, 0, cs>>>(
-                            n, bs, binv, p, EpiStoreHalt<T>{ph, halt});
-                    if (ilu)
-                        GK_TRY(ilu_apply<T>(ild, IluSrc<T>{p}, ilu_w, IluOutStore<T>{ph},
-                                            IluSkipHalt{st}, IluErrSt{st}, cs));
-                    EpiDot<T, CgsAlphaFin> e1{vh, rt, halt, part, tk, CgsAlphaFin{st}};
-                    GK_TRY((launch_spmv_rows<V, T>(A, phs, e1, cs)));
-                    k_cgs_q<T><<<ewg(k_cgs_q<T>, n), 256, 0, cs>>>(n, q, uh, x, u, vh, dinv, st,
-                                                                   sep ? tb : nullptr);
-                    if (block)
-                        k_bj_apply<T, EpiBjX<T>><<<ewg(k_bj_apply<T, EpiBjX<T>>, n), 256, 0, cs>>>(
-                            n, bs, binv, tb, EpiBjX<T>{uh, x, st});
-                    if (ilu)
-                        GK_TRY(ilu_apply<T>(ild, IluSrc<T>{tb}, ilu_w, IluOutX<T>{uh, x, st},
-                                            IluSkipHalt{st}, IluErrSt{st}, cs));
-                    EpiCgsR<T> e2{r, rt, st, part, tk};
-                    GK_TRY((launch_spmv_rows<V, T>(A, uh, e2, cs)));
-                } else {
-                    T *rh = vec_at<T>(C, n, 2), *p = vec_at<T>(C, n, 3), *ph = vec_at<T>(C, n, 4);
-                    T *v = vec_at<T>(C, n, 6), *sv = vec_at<T>(C, n, 5), *sh = vec_at<T>(C, n, 7);
-                    T* t = vec_at<T>(C, n, 8);
-                    const T* phs = prec ? ph : p;
-                    const T* shs = prec ? sh : sv;
-                    k_bi_p<T><<<ewg(k_bi_p<T>, n), 256, 0, cs>>>(n, p, ph, r, v, dinv, st);
-                    if (block)
-                        k_bj_apply<T, EpiStoreHalt<T>><<<ewg(k_bj_apply<T, EpiStoreHalt<T>>, n), 256, 0, cs>>>(
-                            n, bs, binv, p, EpiStoreHalt<T>{ph, halt});
-                    if (ilu)
-                        GK_TRY(ilu_apply<T>(ild, IluSrc<T>{p}, ilu_w, IluOutStore<T>{ph},
-                                            IluSkipHalt{st}, IluErrSt{st}, cs));
-                    EpiDot<T, BiAlphaFin> e1{v, rh, halt, part, tk, BiAlphaFin{st}};
-                    GK_TRY((launch_spmv_rows<V, T>(A, phs, e1, cs)));
-                    k_bi_s<T><<<ewg(k_bi_s<T>, n), 256, 0, cs>>>(n, sv, sh, r, v, dinv, st, part, tk);
-                    if (block)
-                        k_bj_apply<T, EpiStoreHalt<T>><<<ewg(k_bj_apply<T, EpiStoreHalt<T>>, n), 256, 0, cs>>>(
-                            n, bs, binv, sv, EpiStoreHalt<T>{sh, halt});
-                    if (ilu)
-                        GK_TRY(ilu_apply<T>(ild, IluSrc<T>{sv}, ilu_w, IluOutStore<T>{sh},
-                                            IluSkipHalt{st}, IluErrSt{st}, cs));
-                    EpiBiT<T> e2{t, sv, st, part, tk, BiOmegaFin{st}};
-                    GK_TRY((launch_spmv_rows<V, T>(A, shs, e2, cs)));
-                    k_bi_update<T><<<ewg(k_bi_update<T>, n), 256, 0, cs>>>(n, x, r, phs, shs, sv, t, rh, st, part, tk);
+        GK_TRY(capture_solve(A, C, pre, body, post));
+    } else if (stale) {
+        // (re)start of the recurrence from r: gated by *gate when given
+        auto init = [&](cudaStream_t q, const int32_t* gate) -> gk_status {
+            if (method == GK_CG && block) {  // z = B r, rho = <r, z> ; p = z
+                T *zb = vec_at<T>(C, n, 4), *pb = vec_at<T>(C, n, 3);
+                using E0 = EpiDot<T, CgInitFin>;
+                k_bj_apply<T, E0><<<ewg(k_bj_apply<T, E0>, n), 256, 0, q>>>(
+                    n, bs, binv, r, E0{zb, r, gate, part, tk, CgInitFin{st}});
+                k_copy<T><<<ewg(k_copy<T>, n), 256, 0, q>>>(n, zb, pb, gate);
+            } else if (method == GK_CG && ilu) {  // z = M^-1 r, rho = <r, z> ; p = z
+                T *zb = vec_at<T>(C, n, 4), *pb = vec_at<T>(C, n, 3);
+                if (gate)
+                    GK_TRY(ilu_apply<T>(ild, IluSrc<T>{r}, ilu_w, IluOutStore<T>{zb},
+                                        IluSkipGate{gate}, IluErrSt{st}, q));
+                else
+                    GK_TRY(ilu_apply<T>(ild, IluSrc<T>{r}, ilu_w, IluOutStore<T>{zb},
+                                        IluSkipNever{}, IluErrSt{st}, q));
+                k_dot_fin<T, CgInitFin><<<ewg(k_dot_fin<T, CgInitFin>, n), 256, 0, q>>>(
+                    n, r, zb, gate, part, tk, CgInitFin{st});
+                k_copy<T><<<ewg(k_copy<T>, n), 256, 0, q>>>(n, zb, pb, gate);
+            } else if (method == GK_CG)  // slots: 0 r, 1 tmp, 2 q, 3 p, 4 z
+                k_cg_init<T><<<ewg(k_cg_init<T>, n), 256, 0, q>>>(
+                    n, r, vec_at<T>(C, n, 4), vec_at<T>(C, n, 3), dinv, st, part, tk, gate);
+            else if (method == GK_CGS)
+                // slots: 0 r, 1 tmp, 2 rt, 3 u, 4 p, 5 q, 6 ph, 7 vh, 8 uh
+                k_cgs_init<T><<<ewg(k_cgs_init<T>, n), 256, 0, q>>>(n, r, vec_at<T>(C, n, 2), st,
+                                                                    part, tk, gate);
+            else
+                // slots: 0 r, 1 tmp, 2 rhat, 3 p, 4 phat, 5 s, 6 v, 7 shat, 8 t
+                k_bi_init<T><<<ewg(k_bi_init<T>, n), 256, 0, q>>>(
+                    n, r, vec_at<T>(C, n, 2), vec_at<T>(C, n, 3), vec_at<T>(C, n, 6), st, part,
+                    tk, gate);
+            GK_CUDA(cudaGetLastError());
+            return GK_OK;
+        };
+        auto pre = [&](cudaStream_t cs) -> gk_status {
+            k_norm2<T, FinBnorm><<<ewg(k_norm2<T, FinBnorm>, n), 256, 0, cs>>>(
+                n, bi, part, tk, FinBnorm{st, -1.0});
+            // initial true residual r = b - A x (stops at once when it passes)
+            EpiResid<T, FinTrue> e0{r, bi, halt, part, tk, FinTrue{st, 0}};
+            GK_TRY((launch_spmv_rows<V, T>(A, xi, e0, cs)));
+            return init(cs, nullptr);
+        };
+        auto step = [&](cudaStream_t cs) -> gk_status {
+            if (method == GK_CG) {
+                T *z = prec ? vec_at<T>(C, n, 4) : r, *p = vec_at<T>(C, n, 3),
+                  *q = vec_at<T>(C, n, 2);
+                EpiDot<T, CgAlphaFin> e1{q, p, halt, part, tk, CgAlphaFin{st}};
+                GK_TRY((launch_spmv_rows<V, T>(A, p, e1, cs)));
+                k_cg_update<T><<<ewg(k_cg_update<T>, n), 256, 0, cs>>>(n, xi, r, z, p, q, dinv, st,
+                                                                       part, tk, pkind);
+                if (block) {  // z = B r ; beta = <r, z> / rho
+                    using E1 = EpiDot<T, CgBetaFin>;
+                    k_bj_apply<T, E1><<<ewg(k_bj_apply<T, E1>, n), 256, 0, cs>>>(
+                        n, bs, binv, r, E1{z, r, halt, part, tk, CgBetaFin{st}});
                 }
-                GK_CUDA(cudaGetLastError());
-                return GK_OK;
-            }));
-            C->kb = b; C->kx = x; C->kmethod = method; C->kprec = pkey; C->km = m;
-            C->kchunk = chunk; C->kv = C->vecs.ptr;
-        }
-        GK_TRY(read_hdr(C, s));
-        int64_t chunks_left = (int64_t)max_iters / chunk + 4;
-        int64_t checks_left = (int64_t)max_iters + 4;
-        for (;;) {
-            if (C->hst->halt == 2) break;
-            if (--chunks_left < 0 || checks_left < 0) return GK_ERR_TIMEOUT;
-            if (C->hst->halt == 1 && inner && C->hst->restarts >= 2) break;  // enough
-            if (C->hst->halt == 1) {
-                // recurrence passed: check the true residual
-                ++chunks_left;
-                --checks_left;
-                GK_TRY(clear_halt(C, s));
-                EpiResid<T, FinTrue> et{tmp, b, halt, part, tk, FinTrue{st, 1}};
-                GK_TRY((launch_spmv_rows<V, T>(A, x, et, s)));
-                GK_TRY(read_hdr(C, s));
-                if (C->hst->halt == 2) break;
-                if (C->hst->iter >= max_iters) {
-                    out->status = GK_NOT_CONVERGED;
-                    break;
+                if (ilu) {  // z = M^-1 r ; beta = <r, z> / rho
+                    GK_TRY(ilu_apply<T>(ild, IluSrc<T>{r}, ilu_w, IluOutStore<T>{z},
+                                        IluSkipHalt{st}, IluErrSt{st}, cs));
+                    k_dot_fin<T, CgBetaFin><<<ewg(k_dot_fin<T, CgBetaFin>, n), 256, 0, cs>>>(
+                        n, r, z, halt, part, tk, CgBetaFin{st});
                 }
-                // residual replacement and restart from x
-                k_copy<T><<<ewg(k_copy<T>, n), 256, 0, s>>>(n, tmp, r);
-                GK_TRY(init());
-                C->hst->restarts += 1;
-                GK_CUDA(cudaMemcpyAsync(&st->restarts, &C->hst->restarts, 4, cudaMemcpyHostToDevice, s));
-                GK_TRY(read_hdr(C, s));
-                continue;
+                k_cg_p<T><<<ewg(k_cg_p<T>, n), 256, 0, cs>>>(n, p, z, st);
+            } else if (method == GK_CGS) {
+                T *rt = vec_at<T>(C, n, 2), *u = vec_at<T>(C, n, 3), *p = vec_at<T>(C, n, 4);
+                T *q = vec_at<T>(C, n, 5), *ph = vec_at<T>(C, n, 6), *vh = vec_at<T>(C, n, 7);
+                T *uh = vec_at<T>(C, n, 8), *tb = vec_at<T>(C, n, 9);
+                const T* phs = prec ? ph : p;
+                k_cgs_p<T><<<ewg(k_cgs_p<T>, n), 256, 0, cs>>>(n, u, p, ph, r, q, dinv, st);
+                if (block)
+                    k_bj_apply<T, EpiStoreHalt<T>><<<ewg(k_bj_apply<T, EpiStoreHalt<T>>, n), 256, 0, cs>>>(
+                        n, bs, binv, p, EpiStoreHalt<T>{ph, halt});
+                if (ilu)
+                    GK_TRY(ilu_apply<T>(ild, IluSrc<T>{p}, ilu_w, IluOutStore<T>{ph},
+                                        IluSkipHalt{st}, IluErrSt{st}, cs));
+                EpiDot<T, CgsAlphaFin> e1{vh, rt, halt, part, tk, CgsAlphaFin{st}};
+                GK_TRY((launch_spmv_rows<V, T>(A, phs, e1, cs)));
+                k_cgs_q<T><<<ewg(k_cgs_q<T>, n), 256, 0, cs>>>(n, q, uh, xi, u, vh, dinv, st,
+                                                               sep ? tb : nullptr);
+                if (block)
+                    k_bj_apply<T, EpiBjX<T>><<<ewg(k_bj_apply<T, EpiBjX<T>>, n), 256, 0, cs>>>(
+                        n, bs, binv, tb, EpiBjX<T>{uh, xi, st});
+                if (ilu)
+                    GK_TRY(ilu_apply<T>(ild, IluSrc<T>{tb}, ilu_w, IluOutX<T>{uh, xi, st},
+                                        IluSkipHalt{st}, IluErrSt{st}, cs));
+                EpiCgsR<T> e2{r, rt, st, part, tk};
+                GK_TRY((launch_spmv_rows<V, T>(A, uh, e2, cs)));
+            } else {
+                T *rh = vec_at<T>(C, n, 2), *p = vec_at<T>(C, n, 3), *ph = vec_at<T>(C, n, 4);
+                T *v = vec_at<T>(C, n, 6), *sv = vec_at<T>(C, n, 5), *sh = vec_at<T>(C, n, 7);
+                T* t = vec_at<T>(C, n, 8);
+                const T* phs = prec ? ph : p;
+                const T* shs = prec ? sh : sv;
+                k_bi_p<T><<<ewg(k_bi_p<T>, n), 256, 0, cs>>>(n, p, ph, r, v, dinv, st);
+                if (block)
+                    k_bj_apply<T, EpiStoreHalt<T>><<<ewg(k_bj_apply<T, EpiStoreHalt<T>>, n), 256, 0, cs>>>(
+                        n, bs, binv, p, EpiStoreHalt<T>{ph, halt});
+                if (ilu)
+                    GK_TRY(ilu_apply<T>(ild, IluSrc<T>{p}, ilu_w, IluOutStore<T>{ph},
+                                        IluSkipHalt{st}, IluErrSt{st}, cs));
+                EpiDot<T, BiAlphaFin> e1{v, rh, halt, part, tk, BiAlphaFin{st}};
+                GK_TRY((launch_spmv_rows<V, T>(A, phs, e1, cs)));
+                k_bi_s<T><<<ewg(k_bi_s<T>, n), 256, 0, cs>>>(n, sv, sh, r, v, dinv, st, part, tk);
+                if (block)
+                    k_bj_apply<T, EpiStoreHalt<T>><<<ewg(k_bj_apply<T, EpiStoreHalt<T>>, n), 256, 0, cs>>>(
+                        n, bs, binv, sv, EpiStoreHalt<T>{sh, halt});
+                if (ilu)
+                    GK_TRY(ilu_apply<T>(ild, IluSrc<T>{sv}, ilu_w, IluOutStore<T>{sh},
+                                        IluSkipHalt{st}, IluErrSt{st}, cs));
+                EpiBiT<T> e2{t, sv, st, part, tk, BiOmegaFin{st}};
+                GK_TRY((launch_spmv_rows<V, T>(A, shs, e2, cs)));
+                k_bi_update<T><<<ewg(k_bi_update<T>, n), 256, 0, cs>>>(n, xi, r, phs, shs, sv, t,
+                                                                       rh, st, part, tk);
             }
-            GK_CUDA(cudaGraphLaunch(C->exec, s));
-            GK_TRY(read_hdr(C, s));
-        }
+            GK_CUDA(cudaGetLastError());
+            return GK_OK;
+        };
+        auto body = [&](cudaStream_t cs, cudaGraphConditionalHandle hc) -> gk_status {
+            for (int c = 0; c < chunk; ++c) GK_TRY(step(cs));
+            k_ctl_check<<<1, 1, 0, cs>>>(st);
+            // a passed recurrence: the true residual decides (tmp = b - A x)
+            EpiResid<T, FinTrue> et{tmp, bi, &st->nocheck, part, tk, FinTrue{st, 1}};
+            GK_TRY((launch_spmv_rows<V, T>(A, xi, et, cs)));
+            k_ctl_replace<<<1, 1, 0, cs>>>(st);
+            // residual replacement: r = tmp and the method restarts from x
+            k_copy<T><<<ewg(k_copy<T>, n), 256, 0, cs>>>(n, tmp, r, &st->noreplace);
+            GK_TRY(init(cs, &st->noreplace));
+            k_ctl_next<<<1, 1, 0, cs>>>(st, hc);
+            GK_CUDA(cudaGetLastError());
+            return GK_OK;
+        };
+        GK_TRY(capture_solve(A, C, pre, body, post));
     }
-    const KState* hs = C->hst;
-    if (out->status == GK_OK) out->status = (gk_status)hs->status;
-    if (hs->halt == 2 && hs->status == GK_OK) out->status = GK_OK;
-    if (inner && hs->halt == 1) {
-        out->status = GK_OK;
-        out->iters = hs->iter;
-        out->restarts = hs->restarts;
-        out->rec = hs->bnorm > 0 ? hs->rnorm / hs->bnorm : 0.0;
-        out->tru = out->rec;
+    if (stale) {
+        C->kmethod = method;
+        C->kprec = pkey;
+        C->km = m;
+        C->kchunk = chunk;
+        C->kv = C->vecs.ptr;
+        C->kwait = A->wait_ns;
+    }
+    GK_CUDA(cudaGraphLaunch(C->exec, s));
+    GK_CUDA(cudaMemcpyAsync(x, xi, sizeof(T) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    if (info_dev) {  // asynchronous: the outcome goes to device memory
+        k_write_info<<<1, 1, 0, s>>>(st, info_dev, rowtile ? A->plan.err : nullptr, A->fmt,
+                                     A->fmt == GK_SELLP ? A->S : 0);
+        GK_CUDA(cudaGetLastError());
         return GK_OK;
     }
-    out->iters = hs->iter;
-    out->restarts = hs->restarts;
-    out->rec = hs->bnorm > 0 ? hs->rnorm / hs->bnorm : 0.0;
-    // true residual at exit
-    if (hs->bnorm > 0) {
-        EpiResid<T, FinNorm> ef{tmp, b, nullptr, part, tk, FinNorm{st, 1}};
-        GK_TRY((launch_spmv_rows<V, T>(A, x, ef, s)));
-        GK_TRY(read_hdr(C, s));
-        out->tru = C->hst->tnorm / C->hst->bnorm;
-    } else {
-        k_zero<T><<<ewg(k_zero<T>, n), 256, 0, s>>>(n, x);
-        GK_CUDA(cudaGetLastError());
-        out->status = GK_OK;
-        out->iters = 0;
-        out->tru = out->rec = 0.0;
-    }
+    GK_TRY(read_hdr(C, s));
+    gk_solve_info o;
+    solve_outcome(C->hst, rowtile_timeout(), A->fmt, A->fmt == GK_SELLP ? A->S : 0, &o);
+    out->status = o.status;
+    out->iters = o.iters;
+    out->restarts = o.restarts;
+    out->rec = o.rel_res_recurrence;
+    out->tru = o.rel_res_true;
     return GK_OK;
 }
 
 
-// one solve on the multi-kernel engine (instantiated per value type)
+// one solve on the multi-kernel engine (instantiated per value type);
+// info_dev != nullptr: enqueue only, the outcome is written there
 template <typename V, typename T>
 gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t bs, double tol,
-                   int32_t max_iters, int32_t m, cudaStream_t s, SolveOut* out, bool inner);
+                   int32_t max_iters, int32_t m, cudaStream_t s, SolveOut* out, bool inner,
+                   gk_solve_info* info_dev);
 
 extern template gk_status solve_mk<double, double>(gk_matrix, const double*, double*, int, int, int32_t,
                                                    double, int32_t, int32_t, cudaStream_t,
-                                                   SolveOut*, bool);
+                                                   SolveOut*, bool, gk_solve_info*);
 extern template gk_status solve_mk<float, float>(gk_matrix, const float*, float*, int, int, int32_t,
                                                  double, int32_t, int32_t, cudaStream_t, SolveOut*,
-                                                 bool);
+                                                 bool, gk_solve_info*);
 extern template gk_status solve_mk<__nv_bfloat16, float>(gk_matrix, const float*, float*, int,
                                                          int, int32_t, double, int32_t, int32_t,
-                                                         cudaStream_t, SolveOut*, bool);
+                                                         cudaStream_t, SolveOut*, bool,
+                                                         gk_solve_info*);
 extern template gk_status solve_mk<__half, float>(gk_matrix, const float*, float*, int, int, int32_t,
                                                   double, int32_t, int32_t, cudaStream_t,
-                                                  SolveOut*, bool);
+                                                  SolveOut*, bool, gk_solve_info*);
 
 }  // namespace gk

@@ -3,5 +3,5 @@
 
 namespace gk {
 template gk_status solve_mk<__half, float>(gk_matrix, const float*, float*, int, int, int32_t, double,
-                                           int32_t, int32_t, cudaStream_t, SolveOut*, bool);
+                                           int32_t, int32_t, cudaStream_t, SolveOut*, bool, gk_solve_info*);
 }  // namespace gk

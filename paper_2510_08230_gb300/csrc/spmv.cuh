@@ -123,7 +123,8 @@ template <typename V, typename T, class Epi>
 __global__ void __launch_bounds__(256)
 k_csr_rowtile(int32_t ntiles, const int4* __restrict__ tdesc, const int32_t* __restrict__ rp,
               const int32_t* __restrict__ ci, const V* __restrict__ va,
-              const T* __restrict__ x, int32_t cap, int NST, Epi epi, int32_t* __restrict__ err) {
+              const T* __restrict__ x, int32_t cap, int NST, Epi epi, int32_t* __restrict__ err,
+              uint64_t wait_ns) {
     extern __shared__ __align__(128) unsigned char smem[];
     const uint32_t cbytes = (uint32_t)cap * 4u;
     const uint32_t sbytes = (uint32_t)cap * (4u + (uint32_t)sizeof(V));
@@ -156,7 +157,7 @@ k_csr_rowtile(int32_t ntiles, const int4* __restrict__ tdesc, const int32_t* __r
     bool timed_out = false;
     for (int32_t c = blockIdx.x; c < ntiles; c += stride, ++it) {
         const int s = it % NST;
-        const bool ok = mbar_wait_bounded(bar0 + 8u * s, (uint32_t)(it / NST) & 1u);
+        const bool ok = mbar_wait_bounded(bar0 + 8u * s, (uint32_t)(it / NST) & 1u, wait_ns);
         if (__syncthreads_or(!ok)) {
             timed_out = true;
             break;
@@ -188,7 +189,9 @@ k_csr_rowtile(int32_t ntiles, const int4* __restrict__ tdesc, const int32_t* __r
     if (timed_out) {
         if (threadIdx.x == 0) atomicExch(err, 1);
         epi.timed_out();
-        // let the copies already issued land before the block exits (bounded)
+        // let the copies already issued land before the block exits (bounded
+        // by the default limit, not the caller's budget: the shared memory
+        // they write must outlive them)
         for (int k = 0; k < NST; ++k) {
             const int32_t c = (int32_t)blockIdx.x + (it + k) * stride;
             if (c >= ntiles) break;
@@ -196,6 +199,160 @@ k_csr_rowtile(int32_t ntiles, const int4* __restrict__ tdesc, const int32_t* __r
         }
     }
     epi.finish(acc.v);
+}
+
+// ------------------------------------------------------------ warp-tile CSR
+
+// Tiles of 32 * RPL consecutive rows, one warp each, for short rows of
+// near-uniform length (stencils, diffusion operators).  A warp owns a ring
+// of NST shared-memory stages with one mbarrier each; lane 0 stages a tile's
+// column and value range there with two bulk copies (the range rounded out
+// to 8 entries: 16-byte aligned sources, sizes and destinations), NST - 1
+// tiles ahead of the one the warp computes.  Lane l runs rows r0 + l,
+// r0 + l + 32, ... of the tile from shared memory (two rows' loads issued
+// before either FMA chain).  The warps of a block never wait for one another
+// on the streaming path: a stage is refilled as soon as its own warp has
+// read it.  Tile t holds rows [t * 32 RPL, (t + 1) * 32 RPL); warp g of the
+// grid takes tiles g, g + W, g + 2W, ... (W warps in all).  With NST = 1 the
+// warp waits for each tile's copy: the other resident warps cover the
+// latency (measured fastest on the 3D stencils, where the small ring allows
+// more resident warps).  Every wait is bounded by wait_ns; a warp whose
+// wait runs out sets *err, lets its copies in flight land (default limit)
+// and stops; the other warps finish, and the epilogue's reductions still run.
+template <typename V>
+__host__ __device__ constexpr uint32_t wt_stage_bytes(int32_t cap) {
+    return (uint32_t)cap * (4u + (uint32_t)sizeof(V));
+}
+// one warp's ring: NST stages, then NST mbarriers; 128-byte multiple
+template <typename V>
+__host__ __device__ constexpr uint32_t wt_warp_bytes(int32_t cap, int nst) {
+    return ((uint32_t)nst * wt_stage_bytes<V>(cap) + 8u * (uint32_t)nst + 127u) & ~127u;
+}
+
+template <int RPL, typename V, typename T, class Epi>
+__global__ void __launch_bounds__(WT_WARPS * 32)
+k_csr_warptile(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+               const V* __restrict__ va, const T* __restrict__ x, int32_t cap, int NST, Epi epi,
+               int32_t* __restrict__ err, uint64_t wait_ns) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int ROWS = 32 * RPL;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t cbytes = (uint32_t)cap * 4u;
+    const uint32_t sbytes = wt_stage_bytes<V>(cap);
+    unsigned char* ring = smem + (size_t)wid * wt_warp_bytes<V>(cap, NST);
+    const uint32_t buf0 = smem_addr(ring);
+    const uint32_t bar0 = smem_addr(ring + (size_t)NST * sbytes);
+    AccArr<Epi> acc{};
+    if (epi.skip()) return;
+    const int32_t ntiles = (n + ROWS - 1) / ROWS;
+    const int32_t W = (int32_t)gridDim.x * WT_WARPS;
+    const int32_t g = (int32_t)blockIdx.x * WT_WARPS + wid;
+    if (lane == 0) {
+        for (int s = 0; s < NST; ++s) mbar_init(bar0 + 8u * s, 1u);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    auto issue = [&](int32_t t, int s) {  // lane 0 only
+        const int32_t r0 = t * ROWS, r1 = min(r0 + ROWS, n);
+        const int32_t e0 = __ldg(rp + r0), e1 = __ldg(rp + r1);
+        const int32_t a0 = e0 & ~7;
+        const int32_t w = e1 > e0 ? ((e1 + 7) & ~7) - a0 : 0;
+        const uint32_t bar = bar0 + 8u * s;
+        mbar_arrive_expect_tx(bar, (uint32_t)w * (4u + (uint32_t)sizeof(V)));
+        if (w > 0) {
+            bulk_g2s(buf0 + s * sbytes, ci + a0, (uint32_t)w * 4u, bar);
+            bulk_g2s(buf0 + s * sbytes + cbytes, va + a0, (uint32_t)w * (uint32_t)sizeof(V), bar);
+        }
+    };
+    if (lane == 0)
+        for (int s = 0; s < NST; ++s) {
+            const int32_t t = g + s * W;
+            if (t < ntiles) issue(t, s);
+        }
+    int it = 0;
+    bool timed_out = false;
+    for (int32_t t = g; t < ntiles; t += W, ++it) {
+        const int s = it % NST;
+        const int32_t r0 = t * ROWS;
+        // row bounds first: their loads overlap the wait for the tile
+        int32_t ks[RPL], ke[RPL];
+        const int32_t a0 = __ldg(rp + r0) & ~7;
+#pragma unroll
+        for (int q = 0; q < RPL; ++q) {
+            const int32_t r = r0 + lane + 32 * q;
+            ks[q] = r < n ? __ldg(rp + r) - a0 : 0;
+            ke[q] = r < n ? __ldg(rp + r + 1) - a0 : 0;
+        }
+        const bool ok = mbar_wait_bounded(bar0 + 8u * s, (uint32_t)(it / NST) & 1u, wait_ns);
+        if (!__all_sync(FULL, ok)) {
+            timed_out = true;
+            break;
+        }
+        const int32_t* s_col = reinterpret_cast<const int32_t*>(ring + (size_t)s * sbytes);
+        const V* s_val = reinterpret_cast<const V*>(ring + (size_t)s * sbytes + cbytes);
+        if constexpr (RPL == 1) {
+            const T sa = row_sum_staged<T, V>(s_col, s_val, x, ks[0], ke[0]);
+            if (r0 + lane < n) epi.row(r0 + lane, sa, acc.v);
+        } else {
+#pragma unroll
+            for (int q = 0; q < RPL; q += 2) {
+                T sa, sb;
+                row_pair_staged<T, V>(s_col, s_val, x, ks[q], ke[q], ks[q + 1], ke[q + 1], sa, sb);
+                const int32_t ra = r0 + lane + 32 * q, rb = ra + 32;
+                if (ra < n) epi.row(ra, sa, acc.v);
+                if (rb < n) epi.row(rb, sb, acc.v);
+            }
+        }
+        __syncwarp();  // every lane has read stage s
+        if (lane == 0) {
+            const int32_t tn = t + NST * W;
+            if (tn < ntiles) {
+                fence_proxy_async_smem();
+                issue(tn, s);
+            }
+        }
+    }
+    if (timed_out) {
+        if (lane == 0) {
+            atomicExch(err, 1);
+            // the copies already issued land before the warp stops (default limit)
+            for (int k = 0; k < NST; ++k) {
+                const int32_t t = g + (it + k) * W;
+                if (t >= ntiles) break;
+                mbar_wait_bounded(bar0 + 8u * ((it + k) % NST), (uint32_t)((it + k) / NST) & 1u);
+            }
+        }
+        epi.timed_out();
+        __syncwarp();
+    }
+    epi.finish(acc.v);
+}
+
+// ------------------------------------------------------------ carry scan
+
+// Inclusive segmented scan over the warp: lanes holding the same key in a
+// run of consecutive lanes add their values in a fixed tree order (at level
+// o, a lane adds the partial of the lane o places before it if that lane has
+// its key).  Only levels below the longest run of equal keys in the warp can
+// add anything, so the scan stops there: the sums are the same as with all
+// five levels, with fewer FP64 adds (runs are short on skewed matrices with
+// short rows).  Key INT32_MAX marks a lane without an open row; such lanes
+// are runs of their own (their sums are never used).
+template <typename T>
+__device__ __forceinline__ T warp_seg_scan(int32_t key, T v) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int32_t pkey = __shfl_up_sync(FULL, key, 1);
+    const bool start = lane == 0 || pkey != key || key == INT32_MAX;
+    const unsigned starts = __ballot_sync(FULL, start) & (0xffffffffu >> (31 - lane));
+    const int run = (int)__reduce_max_sync(FULL, (unsigned)(lane - (31 - __clz(starts)) + 1));
+    for (int o = 1; o < run; o <<= 1) {
+        const int32_t okey = __shfl_up_sync(FULL, key, o);
+        const T ov = __shfl_up_sync(FULL, v, o);
+        if (lane >= o && okey == key) v = ov + v;
+    }
+    return v;
 }
 
 // ------------------------------------------------------------ merge-path CSR
@@ -465,13 +622,7 @@ k_csr_merge_reg(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
     // carries: as in k_csr_merge_warp
     const bool valid = dt < d1;
     const int32_t myrow = valid ? i : INT32_MAX;
-    T sc = acc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t orow = __shfl_up_sync(FULL, myrow, o);
-        const T osc = __shfl_up_sync(FULL, sc, o);
-        if (lane >= o && orow == myrow) sc = osc + sc;
-    }
+    const T sc = warp_seg_scan(myrow, acc);
     const int32_t prow = __shfl_up_sync(FULL, myrow, 1);
     const T psc = __shfl_up_sync(FULL, sc, 1);
     const int32_t nrow = __shfl_down_sync(FULL, myrow, 1);
@@ -612,13 +763,7 @@ k_csr_merge_warp(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
     // scan (fixed order) gives each lane the sum over its run of lanes.
     const bool valid = dt < d1;
     const int32_t myrow = valid ? i : INT32_MAX;
-    T sc = acc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t orow = __shfl_up_sync(FULL, myrow, o);
-        const T osc = __shfl_up_sync(FULL, sc, o);
-        if (lane >= o && orow == myrow) sc = osc + sc;
-    }
+    const T sc = warp_seg_scan(myrow, acc);
     const int32_t prow = __shfl_up_sync(FULL, myrow, 1);
     const T psc = __shfl_up_sync(FULL, sc, 1);
     const int32_t nrow = __shfl_down_sync(FULL, myrow, 1);
@@ -725,13 +870,7 @@ k_coo_warp(int32_t n, int64_t nnz, const int32_t* __restrict__ rows,
     }
     // the lane's open run (a row that continues in the next lane) is its carry
     const int32_t myrow = open ? last : INT32_MAX;
-    T sc = acc;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int32_t orow = __shfl_up_sync(FULL, myrow, o);
-        const T osc = __shfl_up_sync(FULL, sc, o);
-        if (lane >= o && orow == myrow) sc = osc + sc;
-    }
+    const T sc = warp_seg_scan(myrow, acc);
     const int32_t prow = __shfl_up_sync(FULL, myrow, 1);
     const T psc = __shfl_up_sync(FULL, sc, 1);
     if (head_row >= 0) {
@@ -1004,6 +1143,20 @@ k_sellp_pairs(int32_t n, int32_t S, const int32_t* __restrict__ slen,
 
 // ------------------------------------------------------------ launcher
 
+// Lets `kernel` take the device's opt-in shared memory per block minus its
+// own static shared memory as dynamic shared memory (a constant per kernel).
+template <typename K>
+static gk_status allow_max_dynamic_smem(K kernel) {
+    cudaFuncAttributes fa;
+    GK_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    int dev = 0, optin = 0;
+    GK_CUDA(cudaGetDevice(&dev));
+    GK_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    GK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes));
+    return GK_OK;
+}
+
 template <typename K>
 static int occupancy_blocks(K kernel, int threads, size_t smem) {
     int b = 0;
@@ -1052,7 +1205,35 @@ gk_status launch_spmv_rows(gk_matrix A, const T* x, const Epi& epi, cudaStream_t
         grid = (unsigned)std::min<int64_t>(A->plan.ntiles, (int64_t)sms * occ_cache);
         if (grid < 1) grid = 1;
         k<<<grid, 256, smem, s>>>(A->plan.ntiles, A->plan.tile_desc, A->row_ptr, A->col,
-                                  (const V*)A->val, x, A->plan.tile_cap, nst, epi, A->plan.err);
+                                  (const V*)A->val, x, A->plan.tile_cap, nst, epi, A->plan.err,
+                                  A->wait_ns);
+    } else if (A->fmt == GK_CSR && A->plan.kind == 3) {
+        const int nst = A->plan.stages, rpl = A->plan.wt_rpl;
+        const int32_t cap = A->plan.tile_cap;
+        const size_t smem = (size_t)WT_WARPS * wt_warp_bytes<V>(cap, nst);
+        auto launch = [&](auto k) -> gk_status {
+            // one fixed cap for every launch (the most this kernel may take):
+            // host threads launching it for matrices of different tile sizes
+            // must not lower each other's limit between setting it and
+            // launching
+            static thread_local int occ_cache = 0;
+            static thread_local size_t occ_smem = 0;
+            if (occ_smem != smem || !occ_cache) {
+                GK_TRY(allow_max_dynamic_smem(k));
+                occ_cache = std::min(occupancy_blocks(k, WT_WARPS * 32, smem), 8);
+                occ_smem = smem;
+            }
+            const int64_t rows = 32 * (int64_t)rpl;
+            const int64_t ntiles = ((int64_t)A->n + rows - 1) / rows;
+            grid = (unsigned)std::max<int64_t>(
+                1, std::min<int64_t>((ntiles + WT_WARPS - 1) / WT_WARPS, (int64_t)sms * occ_cache));
+            k<<<grid, WT_WARPS * 32, smem, s>>>(A->n, A->row_ptr, A->col, (const V*)A->val, x,
+                                                cap, nst, epi, A->plan.err, A->wait_ns);
+            return GK_OK;
+        };
+        if (rpl == 1) GK_TRY(launch(k_csr_warptile<1, V, T, Epi>));
+        else if (rpl == 4) GK_TRY(launch(k_csr_warptile<4, V, T, Epi>));
+        else GK_TRY(launch(k_csr_warptile<2, V, T, Epi>));
     } else if (A->fmt == GK_CSR) {
         const int G = A->plan.lanes;
         const int64_t rows_per_block = 256 / G;

@@ -9,12 +9,20 @@ precision) arrive at any time.  The server:
 * admits a request when its device bytes (matrix if not cached, Krylov
   workspace, b and x) fit the budget next to everything admitted or
   cached; unused cached matrices are evicted to make room;
-* runs admitted work on a pool of worker threads, each owning a CUDA
-  stream, so solves overlap on the device;
+* sorts admitted work into two lanes by its expected solve time (learned
+  per matrix key and precision from the solves already served, else
+  estimated from the matrix size): a short lane served by most of the
+  workers, on high-priority CUDA streams, and a long lane of a few workers.
+  Long solves therefore never occupy every worker, run at most a few at a
+  time (each finishes sooner than if all of them shared the GPU at once),
+  and the short lane's kernels take SM slots as soon as a long solve's
+  blocks retire.  Within a lane the job with the smallest expected time
+  runs first, with aging (a job's priority improves by its waiting time),
+  so that no job waits forever;
 * batches continuously: small FP64 systems (n <= small_n) that arrive while
-  the workers are busy wait in a pending list and are all launched together
-  in one gk_solve_batched call as soon as a worker frees up; larger systems
-  and FP32-refined solves run gk_solve one per worker.
+  the short-lane workers are busy wait in a pending list and are all
+  launched together in one gk_solve_batched call as soon as a worker frees
+  up; other solves run gk_solve one per worker.
 
 Latency is measured from submit() to the solution being back on the host.
 All compute runs in libgk.so; this module only schedules.
@@ -84,30 +92,52 @@ def request_bytes(req, small_n):
     return 16 * n
 
 
+def estimate_seconds(m, precision):
+    """Prior for a matrix never solved before: CG iterations grow like the
+    grid's side for these stencils and bands, so nnz * sqrt(n) measures the
+    work (calibrated on GB300: ~60 ms for the 2D Laplacian 969^2 in FP64);
+    refinement about 1.5x faster."""
+    t = 1.5e-11 * m.nnz * np.sqrt(max(m.n, 1))
+    return t / 1.5 if precision == "ir32" else t
+
+
 class SolveServer:
-    def __init__(self, budget_bytes=40e9, workers=6, small_n=16384, batch_max=1024, device=0):
+    def __init__(self, budget_bytes=40e9, workers=6, small_n=16384, batch_max=1024, device=0,
+                 long_workers=2, long_s=0.02, aging=1.0):
         import torch
         self.torch = torch
         self.dev = torch.device(f"cuda:{device}")
         self.budget = float(budget_bytes)
         self.small_n = small_n
         self.batch_max = batch_max
+        self.long_s = long_s          # expected seconds above which a solve is long
+        self.aging = aging            # seconds of priority gained per second waited
         self.cv = threading.Condition()
         self.queue = collections.deque()      # submitted, not admitted
         self.pending_small = []               # admitted, waiting for a batch launch
-        self.pending_single = collections.deque()
+        self.pending_single = []              # admitted short solves
+        self.pending_long = []                # admitted long solves
         self.cache = collections.OrderedDict()  # key -> [Matrix, bytes, users, refined]
         self.used = 0.0                       # admitted request bytes + cached matrix bytes
-        self.idle = workers
-        self.jobs = collections.deque()
+        self.cost = {}                        # (key, precision) -> observed solve seconds (EWMA)
+        long_workers = max(0, min(long_workers, workers - 1))  # 0: one lane for everything
+        self.n_long = long_workers
+        self.idle = {"short": workers - long_workers, "long": long_workers}
+        self.jobs = {"short": collections.deque(), "long": collections.deque()}
         self.running = True
         self.completed = []
         self.error = None
-        self.threads = [threading.Thread(target=self._worker, daemon=True) for _ in range(workers)]
+        lanes = ["long"] * long_workers + ["short"] * (workers - long_workers)
+        self.threads = [threading.Thread(target=self._worker, args=(lane,), daemon=True)
+                        for lane in lanes]
         self.disp = threading.Thread(target=self._dispatch, daemon=True)
         for t in self.threads:
             t.start()
         self.disp.start()
+
+    def expected_seconds(self, req):
+        c = self.cost.get((req.key, req.precision))
+        return c if c is not None else estimate_seconds(req.m, req.precision)
 
     # ---------------------------------------------------------------- API
     def submit(self, req):
@@ -177,7 +207,12 @@ class SolveServer:
             small = req.m.n <= self.small_n and req.precision == "f64" and \
                 req.method in ("cg", "bicgstab") and req.precond in BATCHED_PRECONDS
             req.batched = small
-            (self.pending_small if small else self.pending_single).append(req)
+            if small:
+                self.pending_small.append(req)
+            elif self.n_long and self.expected_seconds(req) > self.long_s:
+                self.pending_long.append(req)
+            else:
+                self.pending_single.append(req)
 
     def _dispatch(self):
         try:
@@ -185,35 +220,60 @@ class SolveServer:
         except Exception as e:  # fail everything still waiting, loudly
             with self.cv:
                 self.error = e
-                waiting = list(self.queue) + self.pending_small + list(self.pending_single)
+                waiting = list(self.queue) + self.pending_small + self.pending_single + \
+                    self.pending_long
                 for r in waiting:
                     r.info = {"status": -3, "error": repr(e)}
                     r.event.set()
             raise
 
+    def _take(self, pending, now):
+        """The pending solve with the best priority: expected seconds minus
+        aging x seconds waited (shortest first, no starvation)."""
+        k = min(range(len(pending)),
+                key=lambda i: self.expected_seconds(pending[i]) -
+                self.aging * (now - pending[i].t_submit))
+        return pending.pop(k)
+
     def _dispatch_loop(self):
         with self.cv:
             while self.running:
                 self._admit()
-                while self.idle > 0 and (self.pending_small or self.pending_single):
-                    # serve the older head first; small heads take every pending
-                    # small system of the same kind with them
-                    if self.pending_small and (not self.pending_single or
-                                               self.pending_small[0].t_submit <=
-                                               self.pending_single[0].t_submit):
+                now = time.perf_counter()
+                while self.idle["long"] > 0 and self.pending_long:
+                    self.jobs["long"].append(("single", [self._take(self.pending_long, now)]))
+                    self.idle["long"] -= 1
+                    self.cv.notify_all()
+                while self.idle["short"] > 0 and (self.pending_small or self.pending_single):
+                    # a batch of every pending small system (expected to take about as
+                    # long as its slowest member) or the best short solve
+                    bt = -1.0
+                    if self.pending_small:
+                        head = min(self.pending_small, key=lambda r: r.t_submit)
+                        bt = max(self.expected_seconds(r) for r in self.pending_small) - \
+                            self.aging * (now - head.t_submit)
+                    st = min((self.expected_seconds(r) - self.aging * (now - r.t_submit)
+                              for r in self.pending_single), default=None)
+                    if self.pending_small and (st is None or bt <= st):
                         # group by method/precond so one launch serves them all
-                        head = self.pending_small[0]
                         grp = [r for r in self.pending_small
                                if r.method == head.method and r.precond == head.precond]
                         grp = grp[:self.batch_max]
                         ids = {id(r) for r in grp}
                         self.pending_small = [r for r in self.pending_small if id(r) not in ids]
-                        self.jobs.append(("batch", grp))
+                        self.jobs["short"].append(("batch", grp))
                     else:
-                        self.jobs.append(("single", [self.pending_single.popleft()]))
-                    self.idle -= 1
+                        self.jobs["short"].append(("single",
+                                                   [self._take(self.pending_single, now)]))
+                    self.idle["short"] -= 1
                     self.cv.notify_all()
-                self.cv.wait(timeout=0.05)
+                # a long-lane worker with nothing long to do helps with short work
+                while self.idle["long"] > 0 and not self.pending_long and self.pending_single \
+                        and self.idle["short"] == 0:
+                    self.jobs["long"].append(("single", [self._take(self.pending_single, now)]))
+                    self.idle["long"] -= 1
+                    self.cv.notify_all()
+                self.cv.wait(timeout=0.005)
 
     # -------------------------------------------------------------- workers
     def _matrix(self, req):
@@ -231,7 +291,7 @@ class SolveServer:
                     mat = self.cache[req.key][0]
         return mat
 
-    def _finish(self, reqs):
+    def _finish(self, reqs, lane, t_run):
         now = time.perf_counter()
         with self.cv:
             for r in reqs:
@@ -242,23 +302,30 @@ class SolveServer:
                     entry[2] -= 1
                 self.completed.append(r)
                 r.event.set()
-            self.idle += 1
+            if len(reqs) == 1 and reqs[0].info and reqs[0].info.get("status") == GK_OK:
+                k = (reqs[0].key, reqs[0].precision)
+                old = self.cost.get(k)
+                self.cost[k] = t_run if old is None else 0.5 * (old + t_run)
+            self.idle[lane] += 1
             self.cv.notify_all()
 
-    def _worker(self):
+    def _worker(self, lane):
         torch = self.torch
         torch.cuda.set_device(self.dev)
-        stream = torch.cuda.Stream(device=self.dev)
+        # short-lane streams get the higher priority: their blocks are
+        # scheduled ahead of a long solve's as SMs free up
+        lo, hi = torch.cuda.Stream.priority_range()
+        stream = torch.cuda.Stream(device=self.dev, priority=hi if lane == "short" else lo)
         while True:
             with self.cv:
-                while self.running and not self.jobs:
+                while self.running and not self.jobs[lane]:
                     self.cv.wait(timeout=0.1)
-                if not self.running and not self.jobs:
+                if not self.running and not self.jobs[lane]:
                     return
-                kind, reqs = self.jobs.popleft()
+                kind, reqs = self.jobs[lane].popleft()
+            t0 = time.perf_counter()
             try:
                 with torch.cuda.stream(stream):
-                    t0 = time.perf_counter()
                     for r in reqs:
                         r.t_start = t0
                     if kind == "batch":
@@ -268,7 +335,7 @@ class SolveServer:
             except Exception as e:  # surface as a failed request
                 for r in reqs:
                     r.info = {"status": -3, "error": repr(e)}
-            self._finish(reqs)
+            self._finish(reqs, lane, time.perf_counter() - t0)
 
     def _run_batch(self, reqs, stream):
         torch = self.torch
@@ -300,10 +367,19 @@ class SolveServer:
     def summarize(reqs, t0, t1):
         lat = np.array([r.t_done - r.t_submit for r in reqs if r.t_done is not None])
         wait = np.array([r.t_start - r.t_submit for r in reqs if r.t_start is not None])
+        serv = np.array([r.t_done - r.t_start for r in reqs
+                         if r.t_start is not None and r.t_done is not None])
         ok = sum(1 for r in reqs if r.info and r.info.get("status") == GK_OK)
+
+        def pct(a, q):
+            return round(float(np.percentile(a, q)) * 1e3, 2) if a.size else None
+
         return {"requests": len(reqs), "ok": ok,
                 "solves_per_s": round(len(lat) / max(t1 - t0, 1e-9), 2),
-                "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 2) if lat.size else None,
-                "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 2) if lat.size else None,
+                "p50_ms": pct(lat, 50), "p90_ms": pct(lat, 90), "p99_ms": pct(lat, 99),
+                "p99_over_p50": (round(float(np.percentile(lat, 99) / np.percentile(lat, 50)), 2)
+                                 if lat.size else None),
                 "mean_wait_ms": round(float(wait.mean()) * 1e3, 2) if wait.size else None,
+                "p99_wait_ms": pct(wait, 99), "service_p50_ms": pct(serv, 50),
+                "service_p99_ms": pct(serv, 99),
                 "batched_fraction": round(sum(r.batched for r in reqs) / max(len(reqs), 1), 3)}

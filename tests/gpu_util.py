@@ -41,6 +41,23 @@ def bf16_round_f64(v):
     return ((q + up.astype(np.uint64)) << np.uint64(45)).view(np.float64)
 
 
+def f32_to_bf16_bits(a):
+    """bfloat16 bit patterns (uint16) of float32 values, rounded to nearest
+    even (finite inputs), written from the bfloat16 definition: the upper 16
+    bits of the float32 encoding after rounding away the lower 16."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    low = u & np.uint64(0xFFFF)
+    hi = u >> np.uint64(16)
+    up = (low > 0x8000) | ((low == 0x8000) & ((hi & np.uint64(1)) == np.uint64(1)))
+    return (hi + up.astype(np.uint64)).astype(np.uint16)
+
+
+def bf16_bits_to_f64(bits):
+    """The float64 value of bfloat16 bit patterns (exact)."""
+    u = np.asarray(bits, dtype=np.uint16).astype(np.uint32) << np.uint32(16)
+    return u.view(np.float32).astype(np.float64)
+
+
 def rounded_values(m, dtype):
     """Matrix values as the GPU stores them, promoted to float64."""
     v = np.asarray(m.values)
@@ -53,7 +70,7 @@ def rounded_values(m, dtype):
     f = v.astype(np.float32)
     if dtype == "f32":
         return f.astype(np.float64)
-    return gk.bf16_to_float(gk.bf16_bits(f)).astype(np.float64)
+    return bf16_bits_to_f64(f32_to_bf16_bits(f))
 
 
 def rounded_vector(x, dtype):

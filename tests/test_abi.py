@@ -60,9 +60,10 @@ def test_invalid_arguments_rejected_on_host(lib):
     assert lib.gk_matrix_destroy(None) == gk.GK_ERR_INVALID
     assert lib.gk_matrix_describe(None, None) == gk.GK_ERR_INVALID
     assert lib.gk_solve(None, None, None, None, None, None) == gk.GK_ERR_INVALID
-    assert lib.gk_precond_apply(None, gk.GK_PRECOND_ILU, 0, None, None, None) == gk.GK_ERR_INVALID
+    assert lib.gk_precond_apply(None, gk.GK_PRECOND_ILU, 0, None, None, 0,
+                                None) == gk.GK_ERR_INVALID
     assert lib.gk_ilu_factors(None, None, None) == gk.GK_ERR_INVALID
-    assert lib.gk_triangular_solve(None, 0, 0, None, None, None) == gk.GK_ERR_INVALID
+    assert lib.gk_triangular_solve(None, 0, 0, None, None, 0, None) == gk.GK_ERR_INVALID
 
 
 def test_struct_layouts_match_header(lib, tmp_path):

@@ -112,3 +112,68 @@ def test_single_block_engine(method, precond):
     info = A.solve(bt, x, method=method, precond=precond, tol=1e-10, max_iters=5000, engine=2)
     assert info["return"] == gk.GK_OK, info
     assert oracle.true_rel_residual(m, b, x.cpu().numpy()) <= 1e-10
+
+
+def _with_env(env, fn):
+    import os
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        return fn()
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+@pytest.mark.parametrize("method", ["cg", "bicgstab"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_batched_layouts_give_identical_results(systems, method, dtype):
+    """Every SpMV layout the autotuner can pick (CSR, ELL where it pads
+    little, SELL-P with 8 to 64 rows per slice) and every block size sums a
+    row in CSR order and reduces over fixed virtual lanes: the solutions are
+    bit-identical, and infos report the layout each system ran on."""
+    mats, rhs = systems
+    mats = mats[:24] + [W.banded_spd(700, 40, 5)]  # rows of up to 81 entries
+    rhs = rhs[:24] + [W.uniform_vector(700, 3)]
+    tol = 1e-10 if dtype == "f64" else 1e-5
+    ref = None
+    for layout, S in (("csr", 0), ("ell", 0), ("sellp8", 8), ("sellp16", 16), ("sellp32", 32),
+                      ("sellp64", 64)):
+        for nt in ("128", "512"):
+            st, infos, xs = _with_env({"GK_BATCH_LAYOUT": layout, "GK_BATCH_THREADS": nt},
+                                      lambda: _batch(mats, rhs, dtype, method, "jacobi", tol))
+            assert st == gk.GK_OK
+            for m, info in zip(mats, infos):
+                assert info["status"] == gk.GK_OK, info
+                assert info["block_threads"] == int(nt)
+                want = {"csr": gk.GK_CSR, "ell": gk.GK_ELL}.get(layout, gk.GK_SELLP)
+                if layout == "ell" and m.row_lengths().max() * m.n > m.nnz + m.nnz // 5:
+                    want = gk.GK_CSR  # ELL would pad too much: the system keeps CSR
+                assert info["spmv_format"] == want and info["slice_size"] == S, (layout, info)
+            if ref is None:
+                ref = xs
+                for m, b, x, info in zip(mats, rhs, xs, infos):
+                    if dtype == "f64":
+                        assert oracle.true_rel_residual(m, b, x) <= 1e-10
+                    else:  # the residual of the stored (rounded) matrix
+                        assert info["rel_res_true"] <= 1e-5
+            else:
+                for x0, x1 in zip(ref, xs):
+                    assert np.array_equal(x0, x1), (layout, nt)
+
+
+def test_autotuner_reports_its_choice(systems):
+    """A tuned batch reports the chosen layout and block size, and its
+    results equal those of any forced configuration."""
+    mats, rhs = systems
+    st, infos, xs = _batch(mats[:48], rhs[:48], "f64", "cg", "jacobi", 1e-10)
+    assert st == gk.GK_OK
+    assert all(i["block_threads"] in (128, 256, 512) for i in infos)
+    assert all(i["spmv_format"] in (gk.GK_CSR, gk.GK_ELL, gk.GK_SELLP) for i in infos)
+    st2, infos2, xs2 = _with_env({"GK_BATCH_LAYOUT": "csr", "GK_BATCH_THREADS": "256"},
+                                 lambda: _batch(mats[:48], rhs[:48], "f64", "cg", "jacobi", 1e-10))
+    for a, b in zip(xs, xs2):
+        assert np.array_equal(a, b)

@@ -65,7 +65,8 @@ MATS = {
     "empty_rows_only": lambda: W.CSR(50, 50, np.zeros(51, np.int32), np.zeros(0, np.int32),
                                      np.zeros(0)),
 }
-VARIANTS = [("csr", 1, 0, 0), ("csr", 2, 0, 0), ("csr", 0, 0, 0), ("ell", None, 0, 0),
+VARIANTS = [("csr", 1, 0, 0), ("csr", 2, 0, 0), ("csr", 0, 0, 0), ("csr", 3, 0, 0),
+            ("ell", None, 0, 0),
             ("sellp", None, 32, 1), ("sellp", None, 8, 4), ("sellp", None, 64, 2),
             ("coo", None, 0, 0)]
 
@@ -85,6 +86,36 @@ def test_spmv_matches_oracle(name, fmt, kernel, S, f, dtype):
         y = _run(A, x, alpha, beta, y0 if use_y0 else None, dtype)
         ref, scale = oracle_apply(m, x, alpha, beta, y0 if use_y0 else None, dtype)
         assert_rows_close(y, ref, scale, TOL[dtype], f"{name} {fmt}/{kernel} {dtype} a={alpha} b={beta}")
+    A.close()
+
+
+@pytest.mark.parametrize("rpl,stages", [(1, 1), (1, 2), (2, 2), (4, 1), (4, 3)])
+@pytest.mark.parametrize("name", ["lap3d_40", "rand_300x7", "banded_5000", "empty_rows_only"])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_warptile_shapes(rpl, stages, name, dtype):
+    """The warp-tile CSR kernel for every tile height (32, 64, 128 rows)
+    and ring depth it can be configured with."""
+    env = {"GK_WT_RPL": str(rpl), "GK_WT_STAGES": str(stages)}
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        m = MATS[name]()
+        A = _make(m, "csr", dtype, 3)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    if A.desc["spmv_kernel"] != 6:
+        pytest.skip("tile does not fit shared memory; another CSR kernel is used")
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-1, 1, m.ncols)
+    y0 = rng.uniform(-1, 1, m.n)
+    for alpha, beta, use_y0 in ((1.0, 0.0, False), (-0.5, 2.0, True)):
+        y = _run(A, x, alpha, beta, y0 if use_y0 else None, dtype)
+        ref, scale = oracle_apply(m, x, alpha, beta, y0 if use_y0 else None, dtype)
+        assert_rows_close(y, ref, scale, TOL[dtype], f"{name} warptile rpl={rpl} nst={stages}")
     A.close()
 
 

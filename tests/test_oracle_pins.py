@@ -36,6 +36,42 @@ def test_spmv_matches_dense_matvec(seed, n, ncols, dens, empty, full, alpha, bet
         assert np.all(np.abs(y - ref) <= 1e-14 * scale + 1e-300)
 
 
+@pytest.mark.parametrize("make", [lambda: W.random_csr(301, 97, 0.1, 12, empty_rows=20, full_rows=2),
+                                  lambda: W.power_law(20000, max_len=2000, seed=3),
+                                  lambda: W.laplacian_3d(23)])
+@pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (-0.5, 2.0), (2.5, -1.0)])
+def test_spmv_omp_is_the_plain_row_sum(make, alpha, beta):
+    """The row-parallel timing-mode SpMV (the CPU baseline) gives, for any
+    thread count, the bits of the sequential plain-sum SpMV: every row is
+    one thread's left-to-right sum.  It also matches the dense matvec, does
+    not read y when beta = 0, and reports the threads it used."""
+    m = make()
+    rng = np.random.default_rng(8)
+    x = rng.standard_normal(m.ncols)
+    y0 = rng.standard_normal(m.n)
+    seq = oracle.spmv(m, x, alpha, beta, y0, compensated=False)
+    import os as _os
+    cores = len(_os.sched_getaffinity(0))
+    for threads in sorted({1, 2, cores}):
+        y = np.full(m.n, np.nan) if beta == 0.0 else y0.copy()
+        out, used = oracle.spmv_omp(m, x, threads, alpha, beta, y)
+        assert used == threads
+        assert np.array_equal(out.view(np.uint64), seq.view(np.uint64)), threads
+    if m.n <= 400:
+        ref = alpha * (m.to_dense() @ x) + beta * y0
+        scale = abs(alpha) * (np.abs(m.to_dense()) @ np.abs(x)) + abs(beta) * np.abs(y0)
+        assert np.all(np.abs(seq - ref) <= 1e-14 * scale + 1e-300)
+    else:
+        # integer-valued matrix and vector: every product and sum is exact
+        mi = W.CSR(m.n, m.ncols, m.row_ptr, m.col_idx, np.rint(4 * m.values))
+        xi = np.arange(m.ncols, dtype=np.float64) % 7 - 3
+        yi, _ = oracle.spmv_omp(mi, xi, cores)
+        rows = np.repeat(np.arange(m.n), m.row_lengths())
+        exact = np.zeros(m.n, dtype=np.int64)
+        np.add.at(exact, rows, mi.values.astype(np.int64) * xi.astype(np.int64)[m.col_idx])
+        assert np.array_equal(yi, exact.astype(np.float64))
+
+
 def test_spmv_beta_zero_does_not_read_y():
     m = W.laplacian_2d(4)
     y = np.full(m.n, np.nan)
@@ -720,6 +756,80 @@ def test_ilu0_apply_is_the_two_triangular_solves():
     got = oracle.ilu0_apply(m, lu, r)
     assert np.allclose(got, z, rtol=1e-13, atol=1e-14)
     assert np.allclose(L @ (U @ got), r, rtol=0, atol=1e-12)
+
+
+def _ilu0_textbook(m):
+    """ILU(0) in the IKJ order with plain arithmetic: l_ik = a_ik / u_kk
+    (a division) and a_ij = a_ij - l_ik * u_kj (a rounded product, then a
+    rounded difference), pattern entries only."""
+    lu = m.values.astype(np.float64).copy()
+    pos = [dict(zip(m.col_idx[m.row_ptr[i]:m.row_ptr[i + 1]].tolist(),
+                    range(m.row_ptr[i], m.row_ptr[i + 1]))) for i in range(m.n)]
+    for i in range(m.n):
+        for k in sorted(c for c in pos[i] if c < i):
+            lik = lu[pos[i][k]] / lu[pos[k][k]]
+            lu[pos[i][k]] = lik
+            for j, pkj in pos[k].items():
+                if j > k and j in pos[i]:
+                    lu[pos[i][j]] = lu[pos[i][j]] - lik * lu[pkj]
+    return lu
+
+
+def _ilu0_apply_textbook(m, lu, r):
+    """Forward then backward substitution, dividing by u_ii."""
+    y = np.zeros(m.n)
+    for i in range(m.n):
+        a, b = m.row_ptr[i], m.row_ptr[i + 1]
+        s = r[i]
+        for k in range(a, b):
+            if m.col_idx[k] < i:
+                s = s - lu[k] * y[m.col_idx[k]]
+        y[i] = s
+    z = np.zeros(m.n)
+    for i in reversed(range(m.n)):
+        a, b = m.row_ptr[i], m.row_ptr[i + 1]
+        s, d = y[i], None
+        for k in range(a, b):
+            c = m.col_idx[k]
+            if c > i:
+                s = s - lu[k] * z[c]
+            elif c == i:
+                d = lu[k]
+        z[i] = s / d
+    return z
+
+
+@pytest.mark.parametrize("make", [lambda: W.diffusion_3d(6),
+                                  lambda: W.convection_diffusion_2d(12, 2.0),
+                                  lambda: W.banded_spd(150, 6, 4),
+                                  lambda: W.power_law(300, max_len=40, seed=5)])
+def test_ilu0_fused_rounding_is_within_rounding_of_textbook(make):
+    """The oracle's ILU(0) takes each update as one fused multiply-add and
+    scales by a reciprocal pivot; the textbook form divides and rounds the
+    product separately.  Both are the same algorithm: factors and the
+    application agree to a few units of rounding (relative to the row's
+    magnitude), so the rounding reading cannot hide a wrong index, sign or
+    dropped term."""
+    m = make()
+    if m.name.startswith("powerlaw"):
+        # a diagonally dominant nonsymmetric matrix on the power-law pattern
+        # plus the diagonal
+        d = m.to_dense()
+        d[np.arange(m.n), np.arange(m.n)] = np.abs(d).sum(axis=1) + 1.0
+        rows, cols = np.nonzero(d)
+        rp = np.zeros(m.n + 1, np.int64)
+        np.add.at(rp, rows + 1, 1)
+        m = W.CSR(m.n, m.n, np.cumsum(rp), cols, d[rows, cols])
+    lu = oracle.ilu0(m)
+    ref = _ilu0_textbook(m)
+    rows = np.repeat(np.arange(m.n), m.row_lengths())
+    rowmax = np.zeros(m.n)
+    np.maximum.at(rowmax, rows, np.abs(ref))
+    assert np.all(np.abs(lu - ref) <= 1e-13 * rowmax[rows])
+    r = W.uniform_vector(m.n, 6)
+    z = oracle.ilu0_apply(m, lu, r)
+    zt = _ilu0_apply_textbook(m, ref, r)
+    assert np.allclose(z, zt, rtol=1e-12, atol=1e-13 * np.abs(zt).max())
 
 
 def test_ilu0_errors():

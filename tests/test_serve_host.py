@@ -33,8 +33,12 @@ class _FakeTorch(types.ModuleType):
         cuda.set_device = lambda d: None
 
         class Stream:
-            def __init__(self, device=None):
-                pass
+            def __init__(self, device=None, priority=0):
+                self.priority = priority
+
+            @staticmethod
+            def priority_range():
+                return 0, -1
 
         class stream:
             def __init__(self, s):
@@ -165,3 +169,40 @@ def test_ilu_and_block_jacobi_requests_run_alone_and_count_their_factors(fake_se
     want = sv.matrix_bytes(m, False) + sv.ilu_bytes(m, False)
     assert cached[0][1] == want and cached[0][4]  # charged once for both ILU requests
     assert cached[2][1] == sv.matrix_bytes(m, False) and not cached[2][4]
+
+
+def test_long_solves_use_their_own_lane_and_short_ones_pass_them(fake_server):
+    """Solves expected to run long go to the long lane (at most long_workers
+    at a time); short solves submitted behind them are served by the short
+    lane while the long ones still run; observed solve times replace the
+    size-based estimate."""
+    import threading
+    sv, FakeMat = fake_server
+    gate = threading.Event()
+    running_long = []
+    peak_long = [0]
+
+    def solve(self, b, x, stream, **kw):
+        if self.m.n > 100000:
+            running_long.append(1)
+            peak_long[0] = max(peak_long[0], len(running_long))
+            gate.wait(10)
+            running_long.pop()
+        return {"return": 0, "status": 0, "iters": 1}
+
+    FakeMat.solve = solve
+    big = W.laplacian_2d(800)      # expected above long_s
+    mid = W.laplacian_2d(150)      # 22500 rows: not batched, expected short
+    srv = sv.SolveServer(budget_bytes=1e12, workers=4, long_workers=2, long_s=0.02)
+    assert srv.expected_seconds(sv.SolveRequest(0, 0, big, np.ones(big.n))) > 0.02
+    assert srv.expected_seconds(sv.SolveRequest(0, 1, mid, np.ones(mid.n))) < 0.02
+    longs = [srv.submit(sv.SolveRequest(i, 0, big, np.ones(big.n))) for i in range(4)]
+    shorts = [srv.submit(sv.SolveRequest(10 + i, 1, mid, np.ones(mid.n))) for i in range(6)]
+    assert all(r.event.wait(10) for r in shorts)  # done while the long ones are held
+    assert not any(r.event.is_set() for r in longs)
+    assert peak_long[0] <= 2
+    gate.set()
+    assert all(r.event.wait(30) for r in longs)
+    assert srv.cost[(1, "f64")] < 0.02  # learned from the served solves
+    srv.close()
+    assert srv.error is None
