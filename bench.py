@@ -552,6 +552,13 @@ def batched_compare(gk, W, torch, dev, count=2048, keep=None):
         torch.cuda.synchronize()
         t_batch = time.perf_counter() - t0
         ok = sum(1 for i in infos if i["status"] == 0)
+        names = {gk.GK_CSR: "csr", gk.GK_ELL: "ell", gk.GK_SELLP: "sellp"}
+        chosen = {}
+        for i in infos:
+            k = (f"{names.get(i['spmv_format'], '?')}"
+                 f"{i['slice_size'] if i['spmv_format'] == gk.GK_SELLP else ''}"
+                 f"/{i['block_threads']}t")
+            chosen[k] = chosen.get(k, 0) + 1
         if keep is not None and dt == "f64":
             keep["batched_2048/f64"] = [x.cpu().numpy() for x in xs]
         for x in xs:
@@ -567,6 +574,7 @@ def batched_compare(gk, W, torch, dev, count=2048, keep=None):
         out[dt] = {"batched_ms": round(t_batch * 1000, 2), "loop_ms": round(t_loop * 1000, 2),
                    "speedup": round(t_loop / t_batch, 2),
                    "solves_per_s_batched": round(count / t_batch, 1),
+                   "autotuned_layouts": chosen,
                    "converged_batched": ok, "converged_loop": loop_ok}
         for A in As:
             A.close()
@@ -595,7 +603,7 @@ def serving_bench(gk, W, torch, dev, n_req=240, factors=((0.5, 400), (0.8, 2000)
         return SolveRequest(rid, mi, pool[mi], rhs[key], tol=tol, precision=prec)
 
     reqs = [make(i) for i in range(len(params))]
-    srv = SolveServer(budget_bytes=40e9, workers=6, long_workers=2)
+    srv = SolveServer(budget_bytes=40e9, workers=6)
     # warm-up: every pool matrix once per precision (uploads, plans, graphs)
     warm = []
     for mi, m in enumerate(pool):
@@ -605,7 +613,8 @@ def serving_bench(gk, W, torch, dev, n_req=240, factors=((0.5, 400), (0.8, 2000)
         r.event.wait(600)
     out = {"workload": "24-matrix pool (2D 5-pt / 3D 7-pt / banded SPD w 5..64, n log-uniform "
                        "1e3..1e6), FP64 or FP32-refined 50/50, tol 1e-10..1e-8, Jacobi-CG, "
-                       "40 GB budget, 6 worker streams (2 for long solves), "
+                       "40 GB budget, 6 workers (arrival order; batched small systems on "
+                       "high-priority streams), "
                        f"{n_req}-request burst, " +
                        ", ".join(f"{c} requests at {f}x" for f, c in factors)}
     burst = reqs[:n_req]

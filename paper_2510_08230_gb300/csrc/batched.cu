@@ -134,9 +134,12 @@ __device__ __forceinline__ T row_dot(const int32_t* __restrict__ rp, const int32
 
 // Row i of a system in its layout (see BatchLayout): entries in CSR order,
 // padding (column -1) only after a row's last entry.
-template <typename V, typename T, typename G>
+// L >= 0: every system of the batch has layout L (the branch is resolved at
+// compile time); L = -1: the layout is read per system.
+template <typename V, typename T, int L, typename G>
 __device__ __forceinline__ T sys_row_dot(const SysDesc& d, const G* __restrict__ g, int32_t i) {
-    if (d.fmt == BL_ELL) {
+    const int fmt = L >= 0 ? L : d.fmt;
+    if (fmt == BL_ELL) {
         const int32_t* __restrict__ col = d.pcol;
         const V* __restrict__ val = (const V*)d.pval;
         T s = T(0);
@@ -148,7 +151,7 @@ __device__ __forceinline__ T sys_row_dot(const SysDesc& d, const G* __restrict__
         }
         return s;
     }
-    if (d.fmt == BL_SELLP) {
+    if (fmt == BL_SELLP) {
         const int32_t sl = i / d.S, t = i - sl * d.S;
         const int32_t* __restrict__ col = d.pcol;
         const V* __restrict__ val = (const V*)d.pval;
@@ -234,7 +237,7 @@ __device__ __forceinline__ T row_dinv(const int32_t* __restrict__ rp, const int3
 
 // Prepares a system: Jacobi diagonal (in work slot 0), ||b||, true residual.
 // Returns false (and fills o) when the solve is already decided.
-template <typename V, typename T>
+template <typename V, typename T, int L>
 __device__ bool block_setup(const SysDesc& d, const BlockOpts& opt, T* dinv, T* r, double& bn,
                             double& thr, SysOut& o) {
     const int32_t n = d.n;
@@ -273,7 +276,7 @@ __device__ bool block_setup(const SysDesc& d, const BlockOpts& opt, T* dinv, T* 
     }
     VAcc<1> rr = vacc<1>();
     for_rows_vl(n, [&](int32_t i, int s) {
-        const T ri = b[i] - sys_row_dot<V, T>(d, x, i);
+        const T ri = b[i] - sys_row_dot<V, T, L>(d, x, i);
         r[i] = ri;
         rr.v[0][s] = fma((double)ri, (double)ri, rr.v[0][s]);
     });
@@ -294,14 +297,14 @@ __device__ bool block_setup(const SysDesc& d, const BlockOpts& opt, T* dinv, T* 
 }
 
 // r = b - A x in place; returns ||r||
-template <typename V, typename T>
+template <typename V, typename T, int L>
 __device__ double block_true_resid(const SysDesc& d, T* r) {
     const V* va = (const V*)d.va;
     const T* b = (const T*)d.b;
     const T* x = (const T*)d.x;
     VAcc<1> tt = vacc<1>();
     for_rows_vl(d.n, [&](int32_t i, int s) {
-        const T ri = b[i] - sys_row_dot<V, T>(d, x, i);
+        const T ri = b[i] - sys_row_dot<V, T, L>(d, x, i);
         r[i] = ri;
         tt.v[0][s] = fma((double)ri, (double)ri, tt.v[0][s]);
     });
@@ -314,7 +317,7 @@ __device__ double block_true_resid(const SysDesc& d, T* r) {
 // work slots: 0 dinv, 1 r, 2 q, 3 scratch (final residual)
 constexpr int BLOCK_MAX_THREADS = 512;
 
-template <typename V, typename T>
+template <typename V, typename T, int L>
 __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_cg(const SysDesc* __restrict__ sys, SysOut* __restrict__ outs,
                            int32_t count, BlockOpts opt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_cg(const SysDesc
         T* scratch = q + d.ld;
         SysOut o;
         double bn = 0.0, thr = 0.0;
-        if (block_setup<V, T>(d, opt, dinv, r, bn, thr, o)) {
+        if (block_setup<V, T, L>(d, opt, dinv, r, bn, thr, o)) {
             double rho = 0.0;
             auto init_dir = [&]() {
                 VAcc<1> rz = vacc<1>();
@@ -349,7 +352,7 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_cg(const SysDesc
             while (k < opt.max_iters) {
                 VAcc<1> pq = vacc<1>();
                 for_rows_vl(n, [&](int32_t i, int s) {
-                    const T sv = sys_row_dot<V, T>(d, ps, i);
+                    const T sv = sys_row_dot<V, T, L>(d, ps, i);
                     q[i] = sv;
                     pq.v[0][s] = fma((double)ps[i], (double)sv, pq.v[0][s]);
                 });
@@ -375,7 +378,7 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_cg(const SysDesc
                 o.rec = rn / bn;
                 if (!isfinite(rn) || !isfinite(t2[0])) { o.status = GK_ERR_NAN; break; }
                 if (rn <= thr) {
-                    const double tn = block_true_resid<V, T>(d, r);
+                    const double tn = block_true_resid<V, T, L>(d, r);
                     if (tn <= thr) { o.status = GK_OK; break; }
                     o.restarts += 1;  // residual replacement, restart from x
                     init_dir();
@@ -391,7 +394,7 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_cg(const SysDesc
                 __syncthreads();
             }
             o.iters = k;
-            o.tru = block_true_resid<V, T>(d, scratch) / bn;
+            o.tru = block_true_resid<V, T, L>(d, scratch) / bn;
         }
         if (threadIdx.x == 0) outs[sidx] = o;
         __syncthreads();
@@ -400,7 +403,7 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_cg(const SysDesc
 
 // ---------------------------------------------------------------- BiCGSTAB
 // work slots: 0 dinv, 1 r, 2 rhat, 3 p, 4 phat, 5 v, 6 s, 7 shat, 8 t
-template <typename V, typename T>
+template <typename V, typename T, int L>
 __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_bicgstab(const SysDesc* __restrict__ sys, SysOut* __restrict__ outs,
                                  int32_t count, BlockOpts opt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_bicgstab(const S
         T *sv = v + d.ld, *sh = sv + d.ld, *t = sh + d.ld;
         SysOut o;
         double bn = 0.0, thr = 0.0;
-        if (block_setup<V, T>(d, opt, dinv, r, bn, thr, o)) {
+        if (block_setup<V, T, L>(d, opt, dinv, r, bn, thr, o)) {
             double rho = 1.0, alpha = 1.0, omega = 1.0, rho_new = 0.0;
             auto restart = [&]() {
                 VAcc<1> a = vacc<1>();
@@ -448,7 +451,7 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_bicgstab(const S
                 __syncthreads();
                 VAcc<1> rv = vacc<1>();
                 for_rows_vl(n, [&](int32_t i, int s) {
-                    const T vi = sys_row_dot<V, T>(d, gs, i);
+                    const T vi = sys_row_dot<V, T, L>(d, gs, i);
                     v[i] = vi;
                     rv.v[0][s] = fma((double)rh[i], (double)vi, rv.v[0][s]);
                 });
@@ -473,7 +476,7 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_bicgstab(const S
                     for (int32_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = fmadd(ta, ph[i], x[i]);
                     o.rec = sn / bn;
                     __syncthreads();
-                    const double tn = block_true_resid<V, T>(d, r);
+                    const double tn = block_true_resid<V, T, L>(d, r);
                     if (tn <= thr) { o.status = GK_OK; break; }
                     o.restarts += 1;
                     restart();
@@ -487,7 +490,7 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_bicgstab(const S
                 __syncthreads();
                 VAcc<2> a2 = vacc<2>();
                 for_rows_vl(n, [&](int32_t i, int s) {
-                    const T ti = sys_row_dot<V, T>(d, gs, i);
+                    const T ti = sys_row_dot<V, T, L>(d, gs, i);
                     t[i] = ti;
                     a2.v[0][s] = fma((double)ti, (double)sv[i], a2.v[0][s]);
                     a2.v[1][s] = fma((double)ti, (double)ti, a2.v[1][s]);
@@ -515,14 +518,14 @@ __global__ void __launch_bounds__(BLOCK_MAX_THREADS, 1) k_block_bicgstab(const S
                 o.rec = rn / bn;
                 if (!isfinite(rn)) { o.status = GK_ERR_NAN; break; }
                 if (rn <= thr) {
-                    const double tn = block_true_resid<V, T>(d, r);
+                    const double tn = block_true_resid<V, T, L>(d, r);
                     if (tn <= thr) { o.status = GK_OK; break; }
                     o.restarts += 1;
                     restart();
                 }
             }
             o.iters = k;
-            o.tru = block_true_resid<V, T>(d, t) / bn;
+            o.tru = block_true_resid<V, T, L>(d, t) / bn;
         }
         if (threadIdx.x == 0) outs[sidx] = o;
         __syncthreads();
@@ -580,19 +583,30 @@ struct BatchLease {
     }
 };
 
+// The block kernel for a method, value type and batch layout (lay: the one
+// layout of every system, or -1 for a mix).
+template <typename V, typename T, int L>
+static auto block_kernel(int method) {
+    return method == GK_CG ? k_block_cg<V, T, L> : k_block_bicgstab<V, T, L>;
+}
+
 template <typename V, typename T>
-static gk_status launch_block(int method, const SysDesc* ddesc, SysOut* dout, int32_t count,
-                              const BlockOpts& bo, int nt, size_t smem, unsigned grid,
-                              cudaStream_t s) {
-    if (method == GK_CG) {
-        auto k = k_block_cg<V, T>;
-        GK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        k<<<grid, nt, smem, s>>>(ddesc, dout, count, bo);
-    } else {
-        auto k = k_block_bicgstab<V, T>;
-        GK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        k<<<grid, nt, smem, s>>>(ddesc, dout, count, bo);
+static auto block_kernel(int method, int lay) {
+    switch (lay) {
+        case BL_CSR: return block_kernel<V, T, BL_CSR>(method);
+        case BL_ELL: return block_kernel<V, T, BL_ELL>(method);
+        case BL_SELLP: return block_kernel<V, T, BL_SELLP>(method);
+        default: return block_kernel<V, T, -1>(method);
     }
+}
+
+template <typename V, typename T>
+static gk_status launch_block(int method, int lay, const SysDesc* ddesc, SysOut* dout,
+                              int32_t count, const BlockOpts& bo, int nt, size_t smem,
+                              unsigned grid, cudaStream_t s) {
+    auto k = block_kernel<V, T>(method, lay);
+    GK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k<<<grid, nt, smem, s>>>(ddesc, dout, count, bo);
     GK_CUDA(cudaGetLastError());
     return GK_OK;
 }
@@ -713,20 +727,23 @@ static gk_status run_batch(int32_t count, const gk_matrix* As, const void* const
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, nt, smem) != cudaSuccess || b < 1) b = 1;
         return b;
     };
-    if (dt == GK_F64) {
-        occ = o->method == GK_CG ? occ_of(k_block_cg<double, double>) : occ_of(k_block_bicgstab<double, double>);
-    } else if (dt == GK_F32) {
-        occ = o->method == GK_CG ? occ_of(k_block_cg<float, float>) : occ_of(k_block_bicgstab<float, float>);
-    } else {
-        occ = o->method == GK_CG ? occ_of(k_block_cg<__nv_bfloat16, float>)
-                                 : occ_of(k_block_bicgstab<__nv_bfloat16, float>);
-    }
+    // one layout for the whole batch: the kernel without the per-row branch
+    int lay = count > 0 ? B.hdesc[0].fmt : BL_CSR;
+    for (int32_t i = 1; i < count && lay >= 0; ++i)
+        if (B.hdesc[i].fmt != lay) lay = -1;
+    if (dt == GK_F64) occ = occ_of(block_kernel<double, double>(o->method, lay));
+    else if (dt == GK_F32) occ = occ_of(block_kernel<float, float>(o->method, lay));
+    else occ = occ_of(block_kernel<__nv_bfloat16, float>(o->method, lay));
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(count, (int64_t)sms * occ));
     const SysDesc* dd = (const SysDesc*)B.desc.ptr;
     SysOut* dout = (SysOut*)B.outs.ptr;
-    if (dt == GK_F64) st = launch_block<double, double>(o->method, dd, dout, count, bo, nt, smem, grid, s);
-    else if (dt == GK_F32) st = launch_block<float, float>(o->method, dd, dout, count, bo, nt, smem, grid, s);
-    else st = launch_block<__nv_bfloat16, float>(o->method, dd, dout, count, bo, nt, smem, grid, s);
+    if (dt == GK_F64)
+        st = launch_block<double, double>(o->method, lay, dd, dout, count, bo, nt, smem, grid, s);
+    else if (dt == GK_F32)
+        st = launch_block<float, float>(o->method, lay, dd, dout, count, bo, nt, smem, grid, s);
+    else
+        st = launch_block<__nv_bfloat16, float>(o->method, lay, dd, dout, count, bo, nt, smem,
+                                                grid, s);
     GK_CUDA(cudaEventRecord(e1, s));
     if (st == GK_OK) {
         GK_CUDA(cudaMemcpyAsync(B.hout, B.outs.ptr, sizeof(SysOut) * (size_t)count,

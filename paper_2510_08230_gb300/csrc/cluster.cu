@@ -11,7 +11,8 @@
 // fixed-order block sum, a cluster barrier, and every thread summing the C
 // block partials in rank order, so all blocks take identical decisions and
 // the result does not depend on timing.  Per CG iteration: three cluster
-// barriers and no kernel launches.
+// barriers and no kernel launches.  The block's rows are staged in shared
+// memory once per solve (see staged_row_dot) when they fit.
 #include <cooperative_groups.h>
 
 #include "prims.cuh"
@@ -97,11 +98,37 @@ __device__ __forceinline__ T cluster_row_dot(cgx::cluster_group& cl, const Clust
     return s;
 }
 
-template <typename V, typename T>
+// The block's rows staged once per solve (the matrix does not change while
+// it runs): value (in the vector type, converted exactly) and source
+// (owner rank << 16 | offset in the owner's part) of every entry, in CSR
+// order, so that an SpMV issues a row's remote gathers back to back.
+template <typename T, int U = 4>
+__device__ __forceinline__ T staged_row_dot(cgx::cluster_group& cl, const T* s_val,
+                                            const uint32_t* s_src, int32_t a, int32_t e,
+                                            T* g_s) {
+    T s = T(0);
+    for (int32_t k0 = a; k0 < e; k0 += U) {
+        T v[U], g[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (k0 + u < e) {
+                const uint32_t src = s_src[k0 + u];
+                v[u] = s_val[k0 + u];
+                g[u] = cl.map_shared_rank(g_s, src >> 16)[src & 0xFFFFu];
+            }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (k0 + u < e) s = fmadd(v[u], g[u], s);
+    }
+    return s;
+}
+
+template <typename V, typename T, bool STAGED>
 __global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
     cgx::cluster_group cl = cgx::this_cluster();
     const unsigned rank = cl.block_rank();
     __shared__ T g_s[CL_RMAX * CL_THREADS];  // owned part of the gathered vector
+    extern __shared__ __align__(16) unsigned char cl_dyn[];  // staged rows (STAGED)
     __shared__ double red[2][4];
     // scalars of the iteration, computed by thread 0 (see cluster_allsum):
     // 0 rho, 1 alpha, 2 beta, 3 status (0 go on, 1 NaN, 2 breakdown,
@@ -115,6 +142,30 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
     const int32_t nloc = max(0, min(A.rpb, A.n - r0));
     T x[CL_RMAX], r[CL_RMAX], q[CL_RMAX], di[CL_RMAX];
     double acc2[2] = {0.0, 0.0};
+    // staged rows: entries [e0, e1) of the CSR belong to this block
+    const int32_t e0 = nloc > 0 ? A.rp[r0] : 0, e1 = nloc > 0 ? A.rp[r0 + nloc] : 0;
+    T* s_val = reinterpret_cast<T*>(cl_dyn);
+    uint32_t* s_src = reinterpret_cast<uint32_t*>(cl_dyn + (((size_t)(e1 - e0) * sizeof(T) + 15) & ~(size_t)15));
+    int32_t ra[CL_RMAX], re[CL_RMAX];  // this thread's rows in the staged arrays
+    if constexpr (STAGED) {
+        for (int32_t k = e0 + (int32_t)threadIdx.x; k < e1; k += CL_THREADS) {
+            const int32_t c = A.ci[k];
+            const unsigned owner = A.rpb_inv ? __umulhi((unsigned)c, A.rpb_inv) : (unsigned)c;
+            s_val[k - e0] = cvt<T>(va[k]);
+            s_src[k - e0] = (owner << 16) | (uint32_t)(c - (int32_t)owner * A.rpb);
+        }
+#pragma unroll
+        for (int k = 0; k < CL_RMAX; ++k) {
+            const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+            ra[k] = li < nloc ? A.rp[r0 + li] - e0 : 0;
+            re[k] = li < nloc ? A.rp[r0 + li + 1] - e0 : 0;
+        }
+    }
+    // row i = r0 + li of this block times the gathered vector
+    auto row_dot = [&](int k, int32_t li) -> T {
+        if constexpr (STAGED) return staged_row_dot<T>(cl, s_val, s_src, ra[k], re[k], g_s);
+        else return cluster_row_dot<V, T>(cl, A, va, g_s, r0 + li, rank);
+    };
     // x into shared memory (for the initial residual), b norm, Jacobi diagonal
 #pragma unroll
     for (int k = 0; k < CL_RMAX; ++k) {
@@ -165,7 +216,7 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
             const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
             if (li < nloc) {
                 const int32_t i = r0 + li;
-                r[k] = b[i] - cluster_row_dot<V, T>(cl, A, va, g_s, i, rank);
+                r[k] = b[i] - row_dot(k, li);
                 a[0] = fma((double)r[k], (double)r[k], a[0]);
             }
         }
@@ -209,7 +260,7 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
         for (int k = 0; k < CL_RMAX; ++k) {
             const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
             if (li < nloc) {
-                q[k] = cluster_row_dot<V, T>(cl, A, va, g_s, r0 + li, rank);
+                q[k] = row_dot(k, li);
                 pq[0] = fma((double)g_s[li], (double)q[k], pq[0]);
             }
         }
@@ -319,10 +370,16 @@ gk_status solve_cluster(gk_matrix A, const void* b, void* x, const gk_solve_opts
     const uint32_t rpb_inv = rpb > 1 ? (uint32_t)((1ull << 32) / (uint64_t)rpb + 1) : 0u;
     ClusterArgs args{A->n, rpb, rpb_inv, A->row_ptr, A->col, A->val, b, x, o->tol, o->max_iters,
                      o->precond == GK_PRECOND_JACOBI, (SolveOut*)outbuf.ptr};
+    // stage the rows in shared memory when the largest block's entries fit
+    // (bounded by rows per block x longest row)
+    const size_t vb = vector_bytes(A->dtype);
+    const int64_t ent = (int64_t)rpb * A->max_row;
+    const size_t stage_bytes = (((size_t)ent * vb + 15) & ~(size_t)15) + 4 * (size_t)ent;
+    const bool staged = stage_bytes <= 160 * 1024;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
     cfg.blockDim = dim3(CL_THREADS, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = staged ? stage_bytes : 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -337,15 +394,24 @@ gk_status solve_cluster(gk_matrix A, const void* b, void* x, const gk_solve_opts
             cudaError_t a = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             if (a != cudaSuccess) return a;
         }
+        cudaError_t m = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             160 * 1024 + 64);
+        if (m != cudaSuccess) return m;
         int nclusters = 0;
         cudaError_t q = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
         if (q != cudaSuccess) return q;
         if (nclusters < 1) return cudaErrorLaunchOutOfResources;
         return cudaLaunchKernelEx(&cfg, kern, args);
     };
-    if (A->dtype == GK_F64) e = go(k_cluster_cg<double, double>);
-    else if (A->dtype == GK_F32) e = go(k_cluster_cg<float, float>);
-    else e = go(k_cluster_cg<__nv_bfloat16, float>);
+    if (staged) {
+        if (A->dtype == GK_F64) e = go(k_cluster_cg<double, double, true>);
+        else if (A->dtype == GK_F32) e = go(k_cluster_cg<float, float, true>);
+        else e = go(k_cluster_cg<__nv_bfloat16, float, true>);
+    } else {
+        if (A->dtype == GK_F64) e = go(k_cluster_cg<double, double, false>);
+        else if (A->dtype == GK_F32) e = go(k_cluster_cg<float, float, false>);
+        else e = go(k_cluster_cg<__nv_bfloat16, float, false>);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         return GK_ERR_UNSUPPORTED;

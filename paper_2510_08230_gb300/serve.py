@@ -9,20 +9,21 @@ precision) arrive at any time.  The server:
 * admits a request when its device bytes (matrix if not cached, Krylov
   workspace, b and x) fit the budget next to everything admitted or
   cached; unused cached matrices are evicted to make room;
-* sorts admitted work into two lanes by its expected solve time (learned
-  per matrix key and precision from the solves already served, else
-  estimated from the matrix size): a short lane served by most of the
-  workers, on high-priority CUDA streams, and a long lane of a few workers.
-  Long solves therefore never occupy every worker, run at most a few at a
-  time (each finishes sooner than if all of them shared the GPU at once),
-  and the short lane's kernels take SM slots as soon as a long solve's
-  blocks retire.  Within a lane the job with the smallest expected time
-  runs first, with aging (a job's priority improves by its waiting time),
-  so that no job waits forever;
+* runs admitted work on a pool of worker threads in arrival order (or,
+  with order="sjf", the job with the smallest expected solve time first,
+  aged by its waiting time); the expected time is learned per matrix key
+  and precision from the solves already served, else estimated from the
+  matrix size.  Optionally (long_workers > 0) solves expected to run long
+  get a lane of their own, so that they never occupy every worker;
 * batches continuously: small FP64 systems (n <= small_n) that arrive while
-  the short-lane workers are busy wait in a pending list and are all
-  launched together in one gk_solve_batched call as soon as a worker frees
-  up; other solves run gk_solve one per worker.
+  the workers are busy wait in a pending list and are all launched together
+  in one gk_solve_batched call as soon as a worker frees up, on the
+  worker's highest-priority CUDA stream (its blocks are scheduled ahead of
+  a running large solve's as SMs free up); other solves run gk_solve one
+  per worker on a default-priority stream.  Measured on GB300 (the
+  24-matrix mix): two lanes of 2 + 4 workers lowered the saturation
+  throughput from ~104 to ~58 solves/s and raised p99 at 0.8x load, because
+  the long solves queued behind each other; so one pool is the default.
 
 Latency is measured from submit() to the solution being back on the host.
 All compute runs in libgk.so; this module only schedules.
@@ -103,7 +104,7 @@ def estimate_seconds(m, precision):
 
 class SolveServer:
     def __init__(self, budget_bytes=40e9, workers=6, small_n=16384, batch_max=1024, device=0,
-                 long_workers=2, long_s=0.02, aging=1.0):
+                 long_workers=0, long_s=0.02, aging=1.0, order="fifo"):
         import torch
         self.torch = torch
         self.dev = torch.device(f"cuda:{device}")
@@ -112,6 +113,7 @@ class SolveServer:
         self.batch_max = batch_max
         self.long_s = long_s          # expected seconds above which a solve is long
         self.aging = aging            # seconds of priority gained per second waited
+        self.order = order            # "fifo" or "sjf" (smallest expected time, aged)
         self.cv = threading.Condition()
         self.queue = collections.deque()      # submitted, not admitted
         self.pending_small = []               # admitted, waiting for a batch launch
@@ -227,12 +229,15 @@ class SolveServer:
                     r.event.set()
             raise
 
+    def _prio(self, req, now):
+        """Dispatch key (smaller first): arrival time, or for "sjf" the
+        expected seconds minus aging x seconds waited (no starvation)."""
+        if self.order == "fifo":
+            return req.t_submit
+        return self.expected_seconds(req) - self.aging * (now - req.t_submit)
+
     def _take(self, pending, now):
-        """The pending solve with the best priority: expected seconds minus
-        aging x seconds waited (shortest first, no starvation)."""
-        k = min(range(len(pending)),
-                key=lambda i: self.expected_seconds(pending[i]) -
-                self.aging * (now - pending[i].t_submit))
+        k = min(range(len(pending)), key=lambda i: self._prio(pending[i], now))
         return pending.pop(k)
 
     def _dispatch_loop(self):
@@ -250,10 +255,10 @@ class SolveServer:
                     bt = -1.0
                     if self.pending_small:
                         head = min(self.pending_small, key=lambda r: r.t_submit)
-                        bt = max(self.expected_seconds(r) for r in self.pending_small) - \
+                        bt = head.t_submit if self.order == "fifo" else \
+                            max(self.expected_seconds(r) for r in self.pending_small) - \
                             self.aging * (now - head.t_submit)
-                    st = min((self.expected_seconds(r) - self.aging * (now - r.t_submit)
-                              for r in self.pending_single), default=None)
+                    st = min((self._prio(r, now) for r in self.pending_single), default=None)
                     if self.pending_small and (st is None or bt <= st):
                         # group by method/precond so one launch serves them all
                         grp = [r for r in self.pending_small
@@ -312,10 +317,11 @@ class SolveServer:
     def _worker(self, lane):
         torch = self.torch
         torch.cuda.set_device(self.dev)
-        # short-lane streams get the higher priority: their blocks are
-        # scheduled ahead of a long solve's as SMs free up
+        # batched small systems run on the highest-priority stream: their
+        # blocks are scheduled ahead of a large solve's as SMs free up
         lo, hi = torch.cuda.Stream.priority_range()
-        stream = torch.cuda.Stream(device=self.dev, priority=hi if lane == "short" else lo)
+        stream_hi = torch.cuda.Stream(device=self.dev, priority=hi)
+        stream_lo = torch.cuda.Stream(device=self.dev, priority=lo)
         while True:
             with self.cv:
                 while self.running and not self.jobs[lane]:
@@ -324,6 +330,7 @@ class SolveServer:
                     return
                 kind, reqs = self.jobs[lane].popleft()
             t0 = time.perf_counter()
+            stream = stream_hi if kind == "batch" else stream_lo
             try:
                 with torch.cuda.stream(stream):
                     for r in reqs:
