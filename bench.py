@@ -581,7 +581,8 @@ def batched_compare(gk, W, torch, dev, count=2048, keep=None):
     return out
 
 
-def serving_bench(gk, W, torch, dev, n_req=240, factors=((0.5, 400), (0.8, 2000), (0.95, 400))):
+def serving_bench(gk, W, torch, dev, n_req=240, factors=((0.5, 400), (0.8, 2000), (0.95, 400)),
+                  server_kw=None):
     """Config 5: Poisson arrivals of solve requests (2D/3D stencils and
     banded SPD, n log-uniform 1e3..1e6, FP64 or FP32-refined 50/50, tol
     log-uniform 1e-10..1e-8) under a 40 GB budget.  Saturation throughput is
@@ -603,7 +604,7 @@ def serving_bench(gk, W, torch, dev, n_req=240, factors=((0.5, 400), (0.8, 2000)
         return SolveRequest(rid, mi, pool[mi], rhs[key], tol=tol, precision=prec)
 
     reqs = [make(i) for i in range(len(params))]
-    srv = SolveServer(budget_bytes=40e9, workers=6)
+    srv = SolveServer(budget_bytes=40e9, **(server_kw or dict(workers=6)))
     # warm-up: every pool matrix once per precision (uploads, plans, graphs)
     warm = []
     for mi, m in enumerate(pool):

@@ -104,7 +104,7 @@ def estimate_seconds(m, precision):
 
 class SolveServer:
     def __init__(self, budget_bytes=40e9, workers=6, small_n=16384, batch_max=1024, device=0,
-                 long_workers=0, long_s=0.02, aging=1.0, order="fifo"):
+                 long_workers=0, long_s=0.02, aging=1.0, order="fifo", long_priority="low"):
         import torch
         self.torch = torch
         self.dev = torch.device(f"cuda:{device}")
@@ -114,6 +114,7 @@ class SolveServer:
         self.long_s = long_s          # expected seconds above which a solve is long
         self.aging = aging            # seconds of priority gained per second waited
         self.order = order            # "fifo" or "sjf" (smallest expected time, aged)
+        self.long_priority = long_priority  # stream priority of the long lane: "low" or "high"
         self.cv = threading.Condition()
         self.queue = collections.deque()      # submitted, not admitted
         self.pending_small = []               # admitted, waiting for a batch launch
@@ -322,6 +323,8 @@ class SolveServer:
         lo, hi = torch.cuda.Stream.priority_range()
         stream_hi = torch.cuda.Stream(device=self.dev, priority=hi)
         stream_lo = torch.cuda.Stream(device=self.dev, priority=lo)
+        if lane == "long" and self.long_priority == "high":
+            stream_lo = stream_hi  # long solves ahead of everything else
         while True:
             with self.cv:
                 while self.running and not self.jobs[lane]:

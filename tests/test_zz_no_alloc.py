@@ -77,3 +77,27 @@ def test_noalloc_rejects_sizes_over_the_limit():
     assert st == gk.GK_ERR_INVALID
     assert gk.gk_spmv_csr_f64_noalloc(-1, 1, 0, None, None, None, 1.0, None, 0.0, None) == \
         gk.GK_ERR_INVALID
+
+
+def test_noalloc_near_limit_256cubed():
+    """The 3D 7-point Laplacian 256^3: n + nnz = 133,824,512, just under the
+    134,217,728 limit (65,346 of the 65,536 merge blocks the scratch holds).
+    With x_i = i mod 7 every product and partial sum is an exact integer, so
+    the output must equal A x exactly, for two calls in a row."""
+    import oracle
+    import torch
+    m = W.laplacian_3d(256)
+    assert m.n + m.nnz <= 134217728
+    rp, ci, va = _device_csr(m)
+    x = (np.arange(m.n) % 7).astype(np.float64)
+    exact, _ = oracle.spmv_omp(m, x)  # plain sums of exact integers: exact
+    xt = torch.from_numpy(x).cuda()
+    y = torch.full((m.n,), float("nan"), dtype=torch.float64, device="cuda")
+    assert gk.gk_spmv_csr_f64_noalloc(m.n, m.ncols, m.nnz, rp, ci, va, 1.0, xt, 0.0, y) == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(y.cpu().numpy(), exact)
+    y0 = (np.arange(m.n) % 5).astype(np.float64)
+    y = torch.from_numpy(y0).cuda()
+    assert gk.gk_spmv_csr_f64_noalloc(m.n, m.ncols, m.nnz, rp, ci, va, -2.0, xt, 0.5, y) == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(y.cpu().numpy(), -2.0 * exact + 0.5 * y0)
