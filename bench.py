@@ -671,7 +671,8 @@ def profile_case(name, dtype):
       cg, bicgstab, gmres
                24 Jacobi-preconditioned iterations (GMRES(30): Arnoldi
                steps) on the 128^3 diffusion problem (solver kernels: SpMV
-               epilogues, fused updates, multi-dots)
+               epilogues, fused updates, multi-dots), the solve graph
+               unrolled (GK_SOLVE_UNROLLED=3) so that ncu sees its kernels
       ilu      ILU(0) of the 2D 5-point Laplacian 512^2 and three
                applications (the substitution kernels k_ilu_trsv)
       ilu_banded
@@ -696,6 +697,9 @@ def profile_case(name, dtype):
         A.close()
         return 0
     if name in ("cg", "bicgstab", "gmres"):
+        # the solve graph without its conditional loop node (profilers do not
+        # see into such graphs): 3 unrolled passes of 8 iterations
+        os.environ["GK_SOLVE_UNROLLED"] = "3"
         m = W.diffusion_3d(128)
         A = gk.Matrix.from_csr(m, dtype)
         b = torch.from_numpy(W.uniform_vector(m.n, W.SEED_BASE + 3)).to(dev, vt)

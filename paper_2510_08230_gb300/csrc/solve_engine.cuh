@@ -1893,23 +1893,24 @@ static __global__ void k_ctl_replace(KState* st) {
     st->noreplace = 0;  // r = b - A x and the method's restart run next
 }
 
-// end of a pass: count a replacement, and loop again unless done
-static __global__ void k_ctl_next(KState* st, cudaGraphConditionalHandle h) {
+// end of a pass: count a replacement, and loop again unless done (cond = 0:
+// an unrolled graph without the loop node, see capture_solve)
+static __global__ void k_ctl_next(KState* st, cudaGraphConditionalHandle h, int cond) {
     if (!st->noreplace) {
         st->restarts += 1;
         st->noreplace = 1;
     }
-    cudaGraphSetConditional(h, st->done ? 0u : 1u);
+    if (cond) cudaGraphSetConditional(h, st->done ? 0u : 1u);
 }
 
 // end of a GMRES pass: loop until halted (restarts are decided inside)
-static __global__ void k_ctl_gmres(KState* st, cudaGraphConditionalHandle h) {
+static __global__ void k_ctl_gmres(KState* st, cudaGraphConditionalHandle h, int cond) {
     st->loops += 1;
     if (st->halt == 0 && st->loops > st->max_loops) {
         st->status = GK_ERR_TIMEOUT;
         st->halt = 2;
     }
-    cudaGraphSetConditional(h, st->halt ? 0u : 1u);
+    if (cond) cudaGraphSetConditional(h, st->halt ? 0u : 1u);
 }
 
 // after the loop: whether the exit computes the true residual (not for an
@@ -1996,9 +1997,13 @@ static gk_status ensure_vecs(SolverCache* C, int64_t n, int count) {
 }
 
 // Captures a whole solve into C->exec: pre(stream), then a conditional
-// WHILE node whose body is body(stream, handle) (it must end with a kernel
-// that sets the handle), then post(stream).  The body is captured on the
-// handle's second library stream into the node's child graph.
+// WHILE node whose body is body(stream, handle, 1) (it must end with a
+// kernel that sets the handle), then post(stream).  The body is captured on
+// the handle's second library stream into the node's child graph.
+// GK_SOLVE_UNROLLED=k (k > 0) instead repeats body(stream, 0, 0) k times
+// with no loop node: the solve runs at most k passes, and every kernel of
+// it can be profiled (profilers do not see into graphs with conditional
+// nodes); for measurement only.
 template <class Pre, class Body, class Post>
 static gk_status capture_solve(gk_matrix A, SolverCache* C, Pre&& pre, Body&& body, Post&& post) {
     GK_TRY(side_stream(A));
@@ -2006,10 +2011,13 @@ static gk_status capture_solve(gk_matrix A, SolverCache* C, Pre&& pre, Body&& bo
         cudaGraphExecDestroy(C->exec);
         C->exec = nullptr;
     }
+    int unrolled = 0;
+    if (const char* e = getenv("GK_SOLVE_UNROLLED")) unrolled = std::max(0, atoi(e));
     cudaGraph_t g = nullptr;
     GK_CUDA(cudaStreamBeginCapture(A->side, cudaStreamCaptureModeThreadLocal));
     gk_status st = pre(A->side);
-    if (st == GK_OK) {
+    for (int k = 0; k < unrolled && st == GK_OK; ++k) st = body(A->side, 0, 0);
+    if (st == GK_OK && !unrolled) {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         cudaGraph_t cg = nullptr;
         const cudaGraphNode_t* deps = nullptr;
@@ -2038,7 +2046,7 @@ static gk_status capture_solve(gk_matrix A, SolverCache* C, Pre&& pre, Body&& bo
                 cudaSuccess) {
                 st = GK_ERR_CUDA;
             } else {
-                st = body(A->side2, hc);
+                st = body(A->side2, hc, 1);
                 cudaGraph_t bg = nullptr;
                 if (cudaStreamEndCapture(A->side2, &bg) != cudaSuccess && st == GK_OK)
                     st = GK_ERR_CUDA;
@@ -2183,7 +2191,7 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
             GK_CUDA(cudaGetLastError());
             return GK_OK;
         };
-        auto body = [&](cudaStream_t cs, cudaGraphConditionalHandle hc) -> gk_status {
+        auto body = [&](cudaStream_t cs, cudaGraphConditionalHandle hc, int cond) -> gk_status {
             for (int c = 0; c < chunk; ++c) {
                 EpiStoreHalt<T> e1{w, halt};
                 GK_TRY((launch_spmv_rows<V, T>(A, z, e1, cs)));
@@ -2212,7 +2220,7 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
                     GK_TRY(ilu_apply<T>(ild, IluSrc<T>{Vm}, ilu_w, IluOutStore<T>{z},
                                         IluSkipV0{st}, IluErrSt{st}, cs));
             }
-            k_ctl_gmres<<<1, 1, 0, cs>>>(st, hc);
+            k_ctl_gmres<<<1, 1, 0, cs>>>(st, hc, cond);
             GK_CUDA(cudaGetLastError());
             return GK_OK;
         };
@@ -2334,7 +2342,7 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
             GK_CUDA(cudaGetLastError());
             return GK_OK;
         };
-        auto body = [&](cudaStream_t cs, cudaGraphConditionalHandle hc) -> gk_status {
+        auto body = [&](cudaStream_t cs, cudaGraphConditionalHandle hc, int cond) -> gk_status {
             for (int c = 0; c < chunk; ++c) GK_TRY(step(cs));
             k_ctl_check<<<1, 1, 0, cs>>>(st);
             // a passed recurrence: the true residual decides (tmp = b - A x)
@@ -2344,7 +2352,7 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
             // residual replacement: r = tmp and the method restarts from x
             k_copy<T><<<ewg(k_copy<T>, n), 256, 0, cs>>>(n, tmp, r, &st->noreplace);
             GK_TRY(init(cs, &st->noreplace));
-            k_ctl_next<<<1, 1, 0, cs>>>(st, hc);
+            k_ctl_next<<<1, 1, 0, cs>>>(st, hc, cond);
             GK_CUDA(cudaGetLastError());
             return GK_OK;
         };

@@ -130,3 +130,28 @@ def test_async_not_converged_and_errors():
     assert gk.gk_solve_async(A.handle, bt, x, gk.make_opts(method="cg"),
                              None) == gk.GK_ERR_INVALID
     A.close()
+
+
+def test_unrolled_profiling_graph_gives_the_same_solve(monkeypatch):
+    """GK_SOLVE_UNROLLED=k builds the solve graph without its loop node (the
+    body repeated k times, so that a profiler can see every kernel): for a
+    solve that needs exactly those passes it gives the bits of the looped
+    graph."""
+    import torch
+    dev = torch_dev()
+    m = W.laplacian_2d(48)  # 2304 rows: passes of 32 iterations
+    b = torch.from_numpy(W.uniform_vector(m.n, 4)).to(dev)
+    out = []
+    for unrolled in (None, "2"):
+        if unrolled:
+            monkeypatch.setenv("GK_SOLVE_UNROLLED", unrolled)
+        else:
+            monkeypatch.delenv("GK_SOLVE_UNROLLED", raising=False)
+        A = gk.Matrix.from_csr(m)  # a fresh handle: the graph is built for this solve
+        x = torch.zeros_like(b)
+        info = A.solve(b, x, method="cg", precond="jacobi", tol=1e-14, max_iters=64, engine=1)
+        out.append((x.cpu().numpy(), info))
+        A.close()
+    (x0, i0), (x1, i1) = out
+    assert i0["return"] == i1["return"] == gk.GK_NOT_CONVERGED and i0["iters"] == i1["iters"] == 64
+    assert np.array_equal(x0, x1)
