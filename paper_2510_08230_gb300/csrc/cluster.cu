@@ -1,19 +1,23 @@
 // cluster.cu - cluster engine: one thread-block cluster (up to 16 blocks,
 // one per SM) runs a whole CG solve of one small system.
 //
-// Same algorithm, stopping rule and residual replacement as the other CG
-// engines (Hestenes-Stiefel, optional Jacobi; stopping per Listing 2; true
-// residual confirms convergence).  Block r of the cluster owns rows
-// [r*rpb, (r+1)*rpb); each thread keeps up to RMAX of those rows' x, r, q
-// and inverse diagonal in registers.  The vector SpMV gathers from (p, or x
-// for the true residual) lives in the owners' shared memory and is read
-// across the cluster through distributed shared memory.  A reduction is a
-// fixed-order block sum, a cluster barrier, and every thread summing the C
-// block partials in rank order, so all blocks take identical decisions and
-// the result does not depend on timing.  Per CG iteration: three cluster
-// barriers and no kernel launches.  The block's rows are staged in shared
-// memory once per solve (see staged_row_dot) when they fit.
+// CG (optional Jacobi) with the stopping rule and residual replacement of
+// the other CG engines (stopping per Listing 2; the true residual confirms
+// convergence).  Block r of the cluster owns rows [r*rpb, (r+1)*rpb); each
+// thread keeps up to RMAX of those rows' iterates and inverse diagonal in
+// registers.  The vector the SpMV gathers from (the direction or u = M^-1 r,
+// or x for the true residual) lives in the owners' shared memory and is
+// read across the cluster through distributed shared memory.  A reduction
+// is a fixed-order block sum, a cluster barrier, and every thread summing
+// the C block partials in rank order, so all blocks take identical
+// decisions and the result does not depend on timing.  Per CG iteration:
+// two cluster barriers with the single-reduction (Chronopoulos-Gear)
+// recurrence, the default, or three with Hestenes-Stiefel; no kernel
+// launches.  The block's rows are staged in shared memory once per solve
+// (see staged_row_dot) when they fit.
 #include <cooperative_groups.h>
+#include <cstring>
+#include <type_traits>
 
 #include "prims.cuh"
 
@@ -40,14 +44,18 @@ struct ClusterArgs {
     SolveOut* out;
 };
 
-// Sum of NA per-block partials over the cluster, identical in all threads:
-// block sum (warp 0), cluster barrier, then warp 0 loads the C block
-// partials (lane r reads block r) and adds them with a fixed shuffle tree;
-// every block evaluates the same tree over the same values.  fin(tot) runs
-// on thread 0 alone before the block barrier that publishes the totals:
-// the scalar work on them (divisions, square roots, decisions), which on
-// this part's narrow FP64 pipe costs microseconds if every thread repeats
-// it, writes its results to shared memory for the block.
+// Sum of NA <= 3 per-thread values over the cluster, identical in all
+// threads.  On this part the FP64 pipe is narrow and a dependent FP64
+// operation has a long latency, so the tree is shallow and issues few
+// FP64 instructions: the threads store their values, warp a (one per SM
+// sub-partition) sums value a - 8 per lane added pairwise, then a 5-level
+// shuffle tree - and stores the block partial; one cluster barrier; warp a
+// loads the C block partials of value a (lane l from block l) and a
+// 4-level shuffle tree (C <= 16) finishes.  Every block evaluates the same
+// tree over the same values, so all take identical decisions.  fin(tot)
+// runs on thread 0 alone before the block barrier that publishes the
+// totals: the scalar work on them (divisions, decisions) writes its
+// results to shared memory for the block.
 struct NoFin {
     __device__ __forceinline__ void operator()(const double*) const {}
 };
@@ -55,27 +63,31 @@ struct NoFin {
 template <int NA, class Fin = NoFin>
 __device__ __forceinline__ void cluster_allsum(cgx::cluster_group& cl, double (&v)[NA],
                                                double (*red)[4], int& tog, Fin fin = Fin()) {
+    static_assert(NA >= 1 && NA <= 3 && CL_THREADS == 256, "one warp per value, 8 per lane");
+    __shared__ double sh[NA][CL_THREADS];
     __shared__ double tot[4];
-    block_sum<NA>(v);
-    if (threadIdx.x == 0)
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
 #pragma unroll
-        for (int a = 0; a < NA; ++a) red[tog][a] = v[a];
-    cl.sync();
-    if (threadIdx.x < 32) {
-        const unsigned C = cl.num_blocks();
-        const unsigned lane = threadIdx.x;
+    for (int a = 0; a < NA; ++a) sh[a][threadIdx.x] = v[a];
+    __syncthreads();
+    if (warp < (unsigned)NA) {
+        const double* w = sh[warp];
+        double t = ((w[lane] + w[lane + 32]) + (w[lane + 64] + w[lane + 96])) +
+                   ((w[lane + 128] + w[lane + 160]) + (w[lane + 192] + w[lane + 224]));
 #pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            double p = 0.0;
-            if (lane < C) {
-                double(*rr)[4] = cl.map_shared_rank(red, lane);
-                p = rr[tog][a];
-            }
-            p = warp_sum(p);
-            if (lane == 0) tot[a] = p;
-        }
-        if (threadIdx.x == 0) fin(tot);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) red[tog][warp] = t;
     }
+    cl.sync();
+    if (warp < (unsigned)NA) {
+        double t = 0.0;
+        if (lane < cl.num_blocks()) t = cl.map_shared_rank(red, lane)[tog][warp];
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) tot[warp] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) fin(tot);
     __syncthreads();
 #pragma unroll
     for (int a = 0; a < NA; ++a) v[a] = tot[a];
@@ -123,17 +135,24 @@ __device__ __forceinline__ T staged_row_dot(cgx::cluster_group& cl, const T* s_v
     return s;
 }
 
-template <typename V, typename T, bool STAGED>
-__global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
+// SR = false: Hestenes-Stiefel CG, three cluster barriers per iteration
+// (publish p; reduce <p, Ap>; reduce <r, z>, ||r||^2).  SR = true: the
+// same iterates computed with one reduction per iteration (the
+// Chronopoulos-Gear recurrence: s = A p carried by its own update, so
+// <r, u>, <A u, u> and ||r||^2 are reduced together after the SpMV of
+// u = M^-1 r), two cluster barriers per iteration (publish u; reduce).
+template <typename V, typename T, bool STAGED, bool SR>
+__global__ void __launch_bounds__(CL_THREADS, 1) k_cluster_cg(ClusterArgs A) {
     cgx::cluster_group cl = cgx::this_cluster();
     const unsigned rank = cl.block_rank();
     __shared__ T g_s[CL_RMAX * CL_THREADS];  // owned part of the gathered vector
     extern __shared__ __align__(16) unsigned char cl_dyn[];  // staged rows (STAGED)
     __shared__ double red[2][4];
     // scalars of the iteration, computed by thread 0 (see cluster_allsum):
-    // 0 rho, 1 alpha, 2 beta, 3 status (0 go on, 1 NaN, 2 breakdown,
-    // 3 recurrence residual passed)
-    __shared__ double sc[4];
+    // 0 rho (SR: gamma = <r, u>), 1 alpha, 2 beta, 3 status (0 go on,
+    // 1 NaN, 2 breakdown, 3 recurrence residual passed), 4 (SR) kappa =
+    // gamma * alpha of the previous iteration
+    __shared__ double sc[5];
     int tog = 0;
     const V* va = (const V*)A.va;
     const T* b = (const T*)A.b;
@@ -141,6 +160,7 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
     const int32_t r0 = (int32_t)rank * A.rpb;
     const int32_t nloc = max(0, min(A.rpb, A.n - r0));
     T x[CL_RMAX], r[CL_RMAX], q[CL_RMAX], di[CL_RMAX];
+    T p[SR ? CL_RMAX : 1], w[SR ? CL_RMAX : 1];  // SR: p in registers (g_s holds u), q = s
     double acc2[2] = {0.0, 0.0};
     // staged rows: entries [e0, e1) of the CSR belong to this block
     const int32_t e0 = nloc > 0 ? A.rp[r0] : 0, e1 = nloc > 0 ? A.rp[r0 + nloc] : 0;
@@ -192,6 +212,10 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
     o.status = GK_NOT_CONVERGED;
     const double bn = sqrt(acc2[0]);
     const double thr = A.tol * bn;
+    // the iterations test ||r||^2 <= thr^2 (no square root on the critical
+    // path); rec2 keeps the last ||r||^2 for the report
+    const double thr2 = thr * thr;
+    double rec2 = -1.0;
     bool run = true;
     if (acc2[1] != 0.0) {
         o.status = GK_ERR_ZERO_DIAG;
@@ -253,6 +277,105 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
             run = false;
         }
     }
+    if constexpr (SR) {
+        // u = M^-1 r into shared memory, w = A u, p = s = 0; alpha =
+        // gamma / delta with gamma = <r, u>, delta = <w, u>, beta = 0
+        auto sr_start = [&]() {
+            cl.sync();  // every block is done gathering from g_s
+#pragma unroll
+            for (int k = 0; k < CL_RMAX; ++k) {
+                const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+                p[k] = q[k] = T(0);
+                if (li < nloc) g_s[li] = A.prec ? di[k] * r[k] : r[k];
+            }
+            cl.sync();  // u published
+            double a[2] = {0.0, 0.0};
+#pragma unroll
+            for (int k = 0; k < CL_RMAX; ++k) {
+                const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+                if (li < nloc) {
+                    w[k] = row_dot(k, li);
+                    const T u = g_s[li];
+                    a[0] = fma((double)r[k], (double)u, a[0]);
+                    a[1] = fma((double)w[k], (double)u, a[1]);
+                }
+            }
+            cluster_allsum<2>(cl, a, red, tog, [&](const double* t) {
+                sc[3] = !isfinite(t[0]) || !isfinite(t[1]) ? 1.0 : t[1] <= 0.0 ? 2.0 : 0.0;
+                sc[0] = t[0];
+                sc[1] = t[0] / t[1];
+                sc[2] = 0.0;
+                sc[4] = t[0] * sc[1];
+            });
+        };
+        if (run) sr_start();
+        while (run && it < A.max_iters) {
+            if (sc[3] == 1.0) { o.status = GK_ERR_NAN; break; }
+            if (sc[3] == 2.0) { o.status = GK_BREAKDOWN; break; }
+            const T ta = (T)sc[1], tb = (T)sc[2];
+            double a[3] = {0.0, 0.0, 0.0};  // <r, u>, <w, u>, ||r||^2
+            // every block finished its gathers of u before the reduction
+            // barrier that produced alpha and beta: u may be overwritten
+#pragma unroll
+            for (int k = 0; k < CL_RMAX; ++k) {
+                const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+                if (li < nloc) {
+                    p[k] = fmadd(tb, p[k], g_s[li]);
+                    q[k] = fmadd(tb, q[k], w[k]);  // s = A p
+                    x[k] = fmadd(ta, p[k], x[k]);
+                    r[k] = fmadd(-ta, q[k], r[k]);
+                    const T u = A.prec ? di[k] * r[k] : r[k];
+                    g_s[li] = u;
+                    a[0] = fma((double)r[k], (double)u, a[0]);
+                    a[2] = fma((double)r[k], (double)r[k], a[2]);
+                }
+            }
+            cl.sync();  // u published
+#pragma unroll
+            for (int k = 0; k < CL_RMAX; ++k) {
+                const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+                if (li < nloc) {
+                    w[k] = row_dot(k, li);
+                    a[1] = fma((double)w[k], (double)g_s[li], a[1]);
+                }
+            }
+            // beta = gamma' / gamma; alpha = gamma' / (delta - beta gamma' /
+            // alpha_old) = gamma' kappa / (delta kappa - gamma'^2) with
+            // kappa = gamma alpha_old (two independent divisions)
+            cluster_allsum<3>(cl, a, red, tog, [&](const double* t) {
+                rec2 = t[2];  // thread 0 reports sqrt(rec2) / ||b||
+                if (!isfinite(t[2]) || !isfinite(t[0]) || !isfinite(t[1])) {
+                    sc[3] = 1.0;
+                } else if (t[2] <= thr2) {
+                    sc[3] = 3.0;
+                } else {
+                    const double kap = sc[4];
+                    const double den = t[1] * kap - t[0] * t[0];
+                    sc[2] = t[0] / sc[0];
+                    sc[1] = t[0] * kap / den;
+                    sc[3] = den > 0.0 && isfinite(sc[1]) ? 0.0 : 2.0;
+                    sc[0] = t[0];
+                    sc[4] = t[0] * sc[1];
+                }
+            });
+            ++it;
+            if (sc[3] == 3.0) {
+                // publish x, recompute the true residual, restart on failure
+#pragma unroll
+                for (int k = 0; k < CL_RMAX; ++k) {
+                    const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
+                    if (li < nloc) g_s[li] = x[k];
+                }
+                cl.sync();
+                double tn = 0.0;
+                true_resid(tn);
+                if (tn <= thr) { o.status = GK_OK; break; }
+                o.restarts += 1;
+                sr_start();
+            }
+        }
+        run = false;  // the Hestenes-Stiefel loop below does not run
+    }
     if (run) init_dir(rho);
     while (run && it < A.max_iters) {
         double pq[1] = {0.0};
@@ -284,11 +407,10 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
             }
         }
         cluster_allsum<2>(cl, a2, red, tog, [&](const double* t) {
-            const double rn = sqrt(t[1]);
-            o.rec = rn / bn;  // thread 0 reports
-            if (!isfinite(rn) || !isfinite(t[0])) {
+            rec2 = t[1];  // thread 0 reports sqrt(rec2) / ||b||
+            if (!isfinite(t[1]) || !isfinite(t[0])) {
                 sc[3] = 1.0;
-            } else if (rn <= thr) {
+            } else if (t[1] <= thr2) {
                 sc[3] = 3.0;
             } else {
                 sc[3] = 0.0;
@@ -325,6 +447,7 @@ __global__ void __launch_bounds__(CL_THREADS) k_cluster_cg(ClusterArgs A) {
         cl.sync();
     }
     o.iters = it;
+    if (rec2 >= 0.0) o.rec = sqrt(rec2) / bn;
     // write x back and recompute the true residual for the report
     if (o.status != GK_ERR_ZERO_DIAG && bn > 0.0) {
         cl.sync();
@@ -388,6 +511,10 @@ gk_status solve_cluster(gk_matrix A, const void* b, void* x, const gk_solve_opts
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    // one reduction per iteration (Chronopoulos-Gear) unless
+    // GK_CLUSTER_RECURRENCE=hs asks for the Hestenes-Stiefel recurrence
+    bool sr = true;
+    if (const char* e = getenv("GK_CLUSTER_RECURRENCE")) sr = strcmp(e, "hs") != 0;
     cudaError_t e;
     auto go = [&](auto kern) -> cudaError_t {
         if (C > 8) {
@@ -403,15 +530,16 @@ gk_status solve_cluster(gk_matrix A, const void* b, void* x, const gk_solve_opts
         if (nclusters < 1) return cudaErrorLaunchOutOfResources;
         return cudaLaunchKernelEx(&cfg, kern, args);
     };
-    if (staged) {
-        if (A->dtype == GK_F64) e = go(k_cluster_cg<double, double, true>);
-        else if (A->dtype == GK_F32) e = go(k_cluster_cg<float, float, true>);
-        else e = go(k_cluster_cg<__nv_bfloat16, float, true>);
-    } else {
-        if (A->dtype == GK_F64) e = go(k_cluster_cg<double, double, false>);
-        else if (A->dtype == GK_F32) e = go(k_cluster_cg<float, float, false>);
-        else e = go(k_cluster_cg<__nv_bfloat16, float, false>);
-    }
+    auto pick = [&](auto st, auto srt) -> cudaError_t {
+        constexpr bool S = decltype(st)::value, R = decltype(srt)::value;
+        if (A->dtype == GK_F64) return go(k_cluster_cg<double, double, S, R>);
+        if (A->dtype == GK_F32) return go(k_cluster_cg<float, float, S, R>);
+        return go(k_cluster_cg<__nv_bfloat16, float, S, R>);
+    };
+    using yes = std::true_type;
+    using no = std::false_type;
+    if (staged) e = sr ? pick(yes{}, yes{}) : pick(yes{}, no{});
+    else e = sr ? pick(no{}, yes{}) : pick(no{}, no{});
     if (e != cudaSuccess) {
         cudaGetLastError();
         return GK_ERR_UNSUPPORTED;

@@ -289,10 +289,11 @@ static gk_status chunk_levels(const TriStore* S, int32_t n, int32_t cs, bool up,
 }
 
 // The claim order of nch chunks with levels lev: sorted by level into ord,
-// each level's run padded to a multiple of pad with -1 (at most pad * nch
-// entries); *nord = its length, *maxw = the widest padded level.
+// each level's run padded to a multiple of pad with -1 (at most
+// nch + (pad - 1) * levels entries; ord holds cap entries, at least that);
+// *nord = its length, *maxw = the widest padded level.
 static gk_status level_order(int32_t nch, int32_t pad, const DevBuf& lev, int32_t* ord,
-                             unsigned* maxw, unsigned* nord, cudaStream_t s) {
+                             size_t cap, unsigned* maxw, unsigned* nord, cudaStream_t s) {
     DevBuf cnt, misc;
     GK_TRY(cnt.ensure(sizeof(unsigned) * ((size_t)nch + 2)));
     GK_TRY(misc.ensure(64));
@@ -302,7 +303,7 @@ static gk_status level_order(int32_t nch, int32_t pad, const DevBuf& lev, int32_
     const unsigned g = ew_grid(nch);
     k_level_hist<<<g, 256, 0, s>>>(nch, (const unsigned*)lev.ptr, (unsigned*)cnt.ptr);
     k_level_scan<<<1, 1024, 0, s>>>(nch + 2, pad, (unsigned*)cnt.ptr, mp + 2, mp + 4);
-    GK_CUDA(cudaMemsetAsync(ord, 0xFF, sizeof(int32_t) * (size_t)pad * nch, s));
+    GK_CUDA(cudaMemsetAsync(ord, 0xFF, sizeof(int32_t) * std::min(cap, (size_t)pad * nch), s));
     k_level_scatter<<<g, 256, 0, s>>>(nch, (const unsigned*)lev.ptr, (unsigned*)cnt.ptr, ord);
     GK_CUDA(cudaGetLastError());
     unsigned h[5] = {0, 0, 0, 0, 0};
@@ -317,12 +318,18 @@ static gk_status level_order(int32_t nch, int32_t pad, const DevBuf& lev, int32_
 // computed once per matrix and shared by the factorisation order and every
 // substitution candidate.
 struct IluLevels {
-    DevBuf l32, u32, l8, u8;
-    unsigned nl32 = 0, nu32 = 0, nl8 = 0, nu8 = 0;
+    DevBuf l32, u32, l8, u8, l1, u1;
+    unsigned nl32 = 0, nu32 = 0, nl8 = 0, nu8 = 0, nl1 = 0, nu1 = 0;
     const DevBuf& get(int cs, bool up) const {
-        return cs == 32 ? (up ? u32 : l32) : (up ? u8 : l8);
+        return cs == 32 ? (up ? u32 : l32) : cs == 8 ? (up ? u8 : l8) : (up ? u1 : l1);
+    }
+    unsigned levels(int cs, bool up) const {
+        return cs == 32 ? (up ? nu32 : nl32) : cs == 8 ? (up ? nu8 : nl8) : (up ? nu1 : nl1);
     }
 };
+
+// claim-order entries S->ord holds (both directions)
+static size_t ord_capacity(int32_t n) { return 2 * 4 * (size_t)std::max((n + 7) / 8, 1); }
 
 template <typename T>
 static IluDev<T> tri_view(const TriStore* S, int32_t n) {
@@ -357,27 +364,33 @@ template IluDev<float> ilu_view<float>(gk_matrix);
 // Rows per substitution chunk and chunks per warp, timed per matrix:
 // 32-row chunks need the fewest dependency levels, 8-row chunks the
 // shortest chain inside a chunk; four 8-row chunks to a warp need 4x fewer
-// warps but move in step.  Which wins depends on the pattern (measured on
-// GB300, FP64: the 128^3 diffusion matrix 3.05 ms with 32 rows, 3.26 with
-// four 8-row chunks a warp; the 2D 5-point Laplacian 1024^2 17.4 ms, 10.4
-// with one 8-row chunk a warp, 12.5 with four).  Each candidate gets its
-// claim orders, grid caps and one timed application (after a warm-up one)
-// of z = M^-1 d with d = 1/u_ii; the fastest is kept.  GK_ILU_CHUNK (8 or
-// 32, one chunk a warp) forces a size.  Results never depend on the
-// choice, only the time does.
+// warps but move in step.  Single-row chunks, 32 to a warp (rows of one
+// dependency level, so a warp's rows never wait on each other), remove the
+// chain inside a chunk altogether: a level costs one hand-off; they are a
+// candidate when the row levels are wide enough (the padded claim order at
+// most twice n).  Which wins depends on the pattern (measured on GB300,
+// FP64: the 128^3 diffusion matrix 3.05 ms with 32 rows, 3.26 with four
+// 8-row chunks a warp; the 2D 5-point Laplacian 1024^2 17.4 ms, 10.4 with
+// one 8-row chunk a warp, 12.5 with four).  Each candidate gets its claim
+// orders, grid caps and one timed application (after a warm-up one) of
+// z = M^-1 d with d = 1/u_ii; the fastest is kept.  GK_ILU_CHUNK (8 or 32,
+// one chunk a warp; 1: single rows, 32 a warp) forces a shape.  Results
+// never depend on the choice, only the time does.
 template <typename T>
 static gk_status tune_chunks(TriStore* S, int32_t n, const IluLevels& lv, cudaStream_t s) {
     int forced = 0;
     if (const char* e = getenv("GK_ILU_CHUNK")) {
         const int v = atoi(e);
-        if (v == 8 || v == 32) forced = v;
+        if (v == 1 || v == 8 || v == 32) forced = v;
     }
     int64_t mult = 2;
     if (const char* e = getenv("GK_ILU_WARPS")) mult = std::max(1, atoi(e));
-    const int all_cs[3] = {32, 8, 8}, all_cpw[3] = {1, 1, 4};
-    const int ncand = forced ? 1 : 3;
-    DevBuf ordb[3], tmp;
-    int32_t warps[3][2] = {}, nord[3][2] = {};
+    const int all_cs[4] = {32, 8, 8, 1}, all_cpw[4] = {1, 1, 4, 32};
+    // single-row chunks only when their padded claim orders stay within 2n
+    const bool rows_ok = (size_t)n + 31 * (size_t)std::max(lv.nl1, lv.nu1) <= 2 * (size_t)n;
+    const int ncand = forced ? 1 : rows_ok ? 4 : 3;
+    DevBuf ordb[4], tmp;
+    int32_t warps[4][2] = {}, nord[4][2] = {};
     GK_TRY(tmp.ensure(2 * sizeof(T) * (size_t)n));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     GK_CUDA(cudaEventCreate(&e0));
@@ -386,14 +399,20 @@ static gk_status tune_chunks(TriStore* S, int32_t n, const IluLevels& lv, cudaSt
     float best = 0.f;
     int pick = 0;
     for (int k = 0; k < ncand && st == GK_OK; ++k) {
-        const int32_t cs = forced ? forced : all_cs[k], cpw = forced ? 1 : all_cpw[k];
+        const int32_t cs = forced ? forced : all_cs[k];
+        const int32_t cpw = forced ? (forced == 1 ? 32 : 1) : all_cpw[k];
         const int32_t nch = (n + cs - 1) / cs;
-        const size_t cap = (size_t)cpw * nch;  // claim-order entries at most, per direction
+        // claim-order entries at most, per direction: every level padded
+        const size_t cap = std::min((size_t)cpw * nch,
+                                    (size_t)nch + (size_t)(cpw - 1) *
+                                                      std::max(lv.levels(cs, false),
+                                                               lv.levels(cs, true)));
         unsigned wl = 0, wu = 0, nl = 0, nu = 0;
         st = ordb[k].ensure(2 * sizeof(int32_t) * cap);
         int32_t* ob = (int32_t*)ordb[k].ptr;
-        if (st == GK_OK) st = level_order(nch, cpw, lv.get(cs, false), ob, &wl, &nl, s);
-        if (st == GK_OK) st = level_order(nch, cpw, lv.get(cs, true), ob + nl, &wu, &nu, s);
+        if (st == GK_OK) st = level_order(nch, cpw, lv.get(cs, false), ob, cap, &wl, &nl, s);
+        if (st == GK_OK)
+            st = level_order(nch, cpw, lv.get(cs, true), ob + nl, cap, &wu, &nu, s);
         if (st != GK_OK) break;
         nord[k][0] = (int32_t)nl;
         nord[k][1] = (int32_t)nu;
@@ -434,7 +453,14 @@ static gk_status tune_chunks(TriStore* S, int32_t n, const IluLevels& lv, cudaSt
     GK_CUDA(cudaMemcpyAsync(h, S->sync, sizeof(h), cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaStreamSynchronize(s));
     if (h[0].err | h[1].err) return GK_ERR_TIMEOUT;
-    const int32_t cs = forced ? forced : all_cs[pick], cpw = forced ? 1 : all_cpw[pick];
+    const int32_t cs = forced ? forced : all_cs[pick];
+    const int32_t cpw = forced ? (forced == 1 ? 32 : 1) : all_cpw[pick];
+    const size_t need = (size_t)nord[pick][0] + nord[pick][1];
+    if (need > ord_capacity(n)) {  // single-row chunks: a longer claim order
+        dfree(S->ord);
+        S->ord = nullptr;
+        GK_CUDA(dmalloc_t(&S->ord, need));
+    }
     GK_CUDA(cudaMemcpyAsync(S->ord, ordb[pick].ptr,
                             sizeof(int32_t) * ((size_t)nord[pick][0] + nord[pick][1]),
                             cudaMemcpyDeviceToDevice, s));
@@ -464,8 +490,9 @@ static gk_status tri_build(TriStore* S, gk_dtype vdt, gk_matrix C, bool factoriz
     GK_CUDA(dmalloc(&S->lu, vb * (size_t)std::max<int64_t>(nnz, 1)));
     GK_CUDA(dmalloc(&S->rdiag, vb * (size_t)std::max(n, 1)));
     GK_CUDA(dmalloc(&S->sync, ilu_sync_bytes()));
-    // claim orders: at most 4 entries per 8-row chunk and direction
-    GK_CUDA(dmalloc_t(&S->ord, 2 * 4 * (size_t)std::max((n + 7) / 8, 1)));
+    // claim orders: at most 4 entries per 8-row chunk and direction (single-
+    // row chunks, when picked, reallocate it)
+    GK_CUDA(dmalloc_t(&S->ord, ord_capacity(n)));
     GK_CUDA(cudaMemcpyAsync(S->rp, C->row_ptr, sizeof(int32_t) * ((size_t)n + 1),
                             cudaMemcpyDeviceToDevice, s));
     if (nnz > 0)
@@ -504,11 +531,13 @@ static gk_status tri_build(TriStore* S, gk_dtype vdt, gk_matrix C, bool factoriz
         GK_TRY(chunk_levels(S, n, 32, true, lv.u32, &lv.nu32, s));
         GK_TRY(chunk_levels(S, n, 8, false, lv.l8, &lv.nl8, s));
         GK_TRY(chunk_levels(S, n, 8, true, lv.u8, &lv.nu8, s));
+        GK_TRY(chunk_levels(S, n, 1, false, lv.l1, &lv.nl1, s));
+        GK_TRY(chunk_levels(S, n, 1, true, lv.u1, &lv.nu1, s));
         if (factorize) {
             // rows claimed chunk by chunk in the L level order of 32-row chunks
             const int32_t cs = 32, nch = (n + cs - 1) / cs;
             unsigned wl = 0, nl = 0;
-            GK_TRY(level_order(nch, 1, lv.l32, S->ord, &wl, &nl, s));
+            GK_TRY(level_order(nch, 1, lv.l32, S->ord, (size_t)nch, &wl, &nl, s));
             k_ilu_factor<<<resident_grid(k_ilu_factor,
                                          std::min<int64_t>(n, 2 * (int64_t)cs * wl + 256)),
                            256, 0, s>>>(n, nch, cs, S->rp, S->ci, S->dpos, S->ord,

@@ -368,3 +368,31 @@ def test_low_precision_storage_equals_fp32_of_the_rounded_values(low):
     assert torch.equal(z1, z2)
     L.close()
     F.close()
+
+
+@pytest.mark.parametrize("chunk", ["1", "8", "32"])
+@pytest.mark.parametrize("case", ["lap2d_37x29", "convdiff_45", "diff3d_12", "random_700",
+                                  "lap1d_33", "one_row", "power_law"])
+def test_every_substitution_shape_bit_exact(monkeypatch, chunk, case):
+    """Each shape the setup can time for the substitutions (single rows,
+    32 of one dependency level to a warp; 8- or 32-row chunks, one to a
+    warp) gives the oracle's substitution bit for bit, repeated applies
+    included: the shape changes only who computes a row, never its order of
+    subtractions."""
+    import torch
+    monkeypatch.setenv("GK_ILU_CHUNK", chunk)
+    dev = torch_dev()
+    m = (_power_law_with_diagonal(1 << 12, W.SEED_BASE + 8) if case == "power_law"
+         else CASES[case]())
+    A = gk.Matrix.from_csr(m, "f64")
+    lu = oracle.ilu0(m)
+    rng = np.random.default_rng(31)
+    for rep in range(2):
+        r = rng.uniform(-1, 1, m.n)
+        rt = torch.from_numpy(r).to(dev)
+        zt = torch.full_like(rt, float("nan"))
+        A.precond_apply(rt, zt, "ilu")
+        torch.cuda.synchronize()
+        want = oracle.ilu0_apply(m, lu, r)
+        assert np.array_equal(zt.cpu().numpy().view(np.uint64), want.view(np.uint64)), rep
+    A.close()
