@@ -487,7 +487,10 @@ gk_status solve_cluster(gk_matrix A, const void* b, void* x, const gk_solve_opts
     static thread_local DevBuf outbuf;
     static thread_local SolveOut* hout = nullptr;
     GK_TRY(outbuf.ensure(sizeof(SolveOut)));
-    if (!hout) GK_CUDA(cudaMallocHost(&hout, sizeof(SolveOut)));
+    if (!hout) {
+        GateShared gate;
+        GK_CUDA(cudaMallocHost(&hout, sizeof(SolveOut)));
+    }
     // col < n <= 16384 and rpb <= 1024, so col * rpb < 2^32 and the
     // multiply-high quotient is exact
     const uint32_t rpb_inv = rpb > 1 ? (uint32_t)((1ull << 32) / (uint64_t)rpb + 1) : 0u;

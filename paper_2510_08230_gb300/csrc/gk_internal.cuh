@@ -280,4 +280,21 @@ void free_solver_cache(gk_matrix A);
 gk_status spmv_dispatch(gk_matrix A, double alpha, const void* b, double beta,
                         void* x, cudaStream_t s);
 int num_sms();
+// CUDA graph capture excludes the library's device-wide driver calls in
+// other host threads.  On GB300 with driver 580, cuStreamEndCapture crashed
+// when another thread freed device memory or synchronised the device while
+// the capture was open (serving workers uploading, evicting and building
+// solve graphs at once), even with captures serialised.  So a capture holds
+// the gate exclusively (GateCapture: one capture at a time), and every
+// allocation, free and device synchronisation holds it shared (GateShared;
+// re-entrant within a thread, and a no-op inside the thread's own capture).
+struct GateShared {
+    GateShared();
+    ~GateShared();
+    bool held;
+};
+struct GateCapture {
+    GateCapture();
+    ~GateCapture();
+};
 }  // namespace gk

@@ -12,6 +12,8 @@
 #include <cstring>
 #include <vector>
 
+#include <shared_mutex>
+
 #include "prims.cuh"
 
 namespace gk {
@@ -23,16 +25,43 @@ void set_error(const char* where, cudaError_t e) {
 }
 const char* last_error() { return g_last_error.c_str(); }
 
+static std::shared_mutex g_gate;
+static thread_local int g_gate_depth = 0;   // shared holds of this thread
+static thread_local bool g_in_capture = false;
+
+GateShared::GateShared() : held(false) {
+    if (g_in_capture) return;
+    if (g_gate_depth++ == 0) {
+        g_gate.lock_shared();
+        held = true;
+    }
+}
+GateShared::~GateShared() {
+    if (g_in_capture) return;
+    if (--g_gate_depth == 0 && held) g_gate.unlock_shared();
+}
+GateCapture::GateCapture() {
+    g_gate.lock();
+    g_in_capture = true;
+}
+GateCapture::~GateCapture() {
+    g_in_capture = false;
+    g_gate.unlock();
+}
+
 cudaError_t dmalloc(void** p, size_t bytes) {
+    GateShared gate;
     *p = nullptr;
     return cudaMalloc(p, bytes + 64);
 }
 void dfree(void* p) {
+    GateShared gate;
     if (p) cudaFree(p);
 }
 
 gk_status DevBuf::ensure(size_t want) {
     if (want <= bytes && ptr) return GK_OK;
+    GateShared gate;
     if (ptr) {
         cudaFree(ptr);
         ptr = nullptr;
@@ -44,6 +73,7 @@ gk_status DevBuf::ensure(size_t want) {
     return GK_OK;
 }
 void DevBuf::release() {
+    GateShared gate;
     if (ptr) cudaFree(ptr);
     ptr = nullptr;
     bytes = 0;
@@ -1063,6 +1093,7 @@ gk_status gk_matrix_describe(gk_matrix A, gk_matrix_desc* d) {
 
 gk_status gk_matrix_export(gk_matrix A, int32_t* idx_a, int64_t* sets, int32_t* col, void* values) {
     if (!A) return GK_ERR_INVALID;
+    GateShared gate;
     GK_CUDA(cudaDeviceSynchronize());
     const size_t vb = value_bytes(A->dtype);
     if (A->coo) {
@@ -1088,6 +1119,7 @@ gk_status gk_matrix_export(gk_matrix A, int32_t* idx_a, int64_t* sets, int32_t* 
 
 gk_status gk_matrix_destroy(gk_matrix A) {
     if (!A) return GK_ERR_INVALID;
+    GateShared gate;  // streams, graphs, events and memory go: no capture meanwhile
     cudaDeviceSynchronize();
     destroy_handle(A);
     return GK_OK;

@@ -7,12 +7,14 @@
 namespace gk {
 
 void free_solver_cache(gk_matrix A) {
+    GateShared gate;
     delete A->solver;
     A->solver = nullptr;
 }
 
 gk_status get_cache(gk_matrix A, SolverCache** out) {
     if (!A->solver) {
+        GateShared gate;
         SolverCache* C = new (std::nothrow) SolverCache();
         if (!C) return GK_ERR_OOM;
         A->solver = C;

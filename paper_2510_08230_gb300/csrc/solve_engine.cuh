@@ -2006,6 +2006,7 @@ static gk_status ensure_vecs(SolverCache* C, int64_t n, int count) {
 // nodes); for measurement only.
 template <class Pre, class Body, class Post>
 static gk_status capture_solve(gk_matrix A, SolverCache* C, Pre&& pre, Body&& body, Post&& post) {
+    GateCapture gate;  // one capture at a time, no device-wide call meanwhile
     GK_TRY(side_stream(A));
     if (C->exec) {
         cudaGraphExecDestroy(C->exec);
