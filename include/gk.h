@@ -284,10 +284,13 @@ typedef struct {
  * Krylov dimension, then kept with the handle) repeats chunks of iterations
  * in a conditional loop node, with the confirmation of a passed recurrence
  * residual and the residual replacement decided by kernels; the host only
- * reads the outcome.  The solve works on the handle's own copies of b and x.
+ * reads the outcome (GK_SOLVE_LOOP=host launches one graph per pass from
+ * the host instead, two in flight; same results).  The solve works on the
+ * handle's own copies of b and x.
  * SpMV layout (multi-kernel engine and refinement on a CSR matrix): a matrix
- * whose apply uses the CSR warp-tile kernel (gk_matrix_desc.spmv_kernel 6)
- * solves on its own arrays; otherwise the first solve keeps an ELL copy of A
+ * of at least 2^24 entries whose apply uses the CSR warp-tile kernel
+ * (gk_matrix_desc.spmv_kernel 6) solves on its own arrays; otherwise the
+ * first solve keeps an ELL copy of A
  * when ELL stores at most 1.2 x nnz entries, else a SELL-P(32) copy under the
  * same bound, else uses the CSR kernels; the copy lives with the handle
  * (gk_matrix_desc.solve_format reports the pick).

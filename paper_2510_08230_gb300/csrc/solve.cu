@@ -138,11 +138,16 @@ gk_status get_lowp(gk_matrix A, gk_dtype d, cudaStream_t s, gk_matrix* out) {
 // coalesced loads and no row-pointer indirection, so when padding costs
 // little they beat the CSR row-tile and merge kernels.  The CSR warp-tile
 // kernel (short rows of near-uniform length) comes within a few per cent of
-// ELL (GB300, 3D 7-point 256^3: 262 against 255 us in FP64, 166 against
-// 163 us in FP32) and sums every row in the same order, so such matrices
-// solve on their own CSR arrays and keep no padded copy.  Default rule,
-// decided on the first solve and kept: the CSR itself when its plan is the
-// warp-tile kernel, else ELL when its stored entries are at most 1.2 x nnz,
+// ELL on large matrices (GB300, 3D 7-point 256^3: 262 against 255 us in
+// FP64, 166 against 163 us in FP32), so those solve on their own CSR arrays
+// and keep no padded copy, which would cost gigabytes.  On smaller ones the
+// warp-tile launch's ramp (a full wave of blocks staging tiles into shared
+// memory) costs more than ELL's padding, and its shared memory keeps
+// concurrent solves from overlapping: six mid-size serving solves (n 70K to
+// 430K) took 225 ms one after another and 131 ms at once on the CSR, 193 and
+// 97 ms with the ELL copy.  Default rule, decided on the first solve and
+// kept: the CSR itself when its plan is the warp-tile kernel and it holds at
+// least SOLVE_CSR_MIN_NNZ entries, else ELL when its stored entries are at most 1.2 x nnz,
 // else SELL-P(32) when its stored entries are at most 1.2 x nnz, else the CSR
 // itself.  The rule depends only on the sparsity pattern, so every handle of
 // a matrix solves with the same summation order (bit-identical results).
@@ -150,6 +155,8 @@ gk_status get_lowp(gk_matrix A, gk_dtype d, cudaStream_t s, gk_matrix* out) {
 // three SpMVs of each admissible layout and keeps the fastest.  The copy holds
 // the same values bit for bit, so the choice changes the order of the row
 // sums, not the matrix.
+constexpr int64_t SOLVE_CSR_MIN_NNZ = int64_t(1) << 24;
+
 static gk_status solve_matrix(gk_matrix A, cudaStream_t s, gk_matrix* out) {
     *out = A;
     if (A->fmt != GK_CSR || A->n == 0) return GK_OK;
@@ -160,7 +167,7 @@ static gk_status solve_matrix(gk_matrix A, cudaStream_t s, gk_matrix* out) {
     const char* env = getenv("GK_SOLVE_FORMAT");
     const bool timed = env && !strcmp(env, "timed");
     const bool force = env && !timed && strcmp(env, "auto") != 0;
-    if (!force && !timed && A->plan.kind == 3) {
+    if (!force && !timed && A->plan.kind == 3 && A->nnz >= SOLVE_CSR_MIN_NNZ) {
         A->solve_fmt = nullptr;
         A->solve_fmt_tuned = 1;
         return GK_OK;

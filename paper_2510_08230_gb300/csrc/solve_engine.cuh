@@ -1959,13 +1959,23 @@ struct SolverCache {
     KState* hst = nullptr;  // pinned mirror of the state header
     int32_t* hzero = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // host-driven loop: the passes and the exit as graphs of their own, and
+    // two pinned header slots with their events (pass k writes slot k % 2)
+    cudaGraphExec_t exec_body = nullptr, exec_post = nullptr;
+    KState* hring = nullptr;
+    cudaEvent_t evr[2] = {nullptr, nullptr};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // key of the captured graph
     void* kv = nullptr;
-    int kmethod = -1, kprec = -1, km = -1, kchunk = 0;
+    int kmethod = -1, kprec = -1, km = -1, kchunk = 0, khost = -1;
     uint64_t kwait = 0;  // wait budget the graph's kernels were captured with
     ~SolverCache() {
         if (exec) cudaGraphExecDestroy(exec);
+        if (exec_body) cudaGraphExecDestroy(exec_body);
+        if (exec_post) cudaGraphExecDestroy(exec_post);
+        if (hring) cudaFreeHost(hring);
+        for (cudaEvent_t e : evr)
+            if (e) cudaEventDestroy(e);
         if (hst) cudaFreeHost(hst);
         if (hzero) cudaFreeHost(hzero);
         if (ev0) cudaEventDestroy(ev0);
@@ -2004,13 +2014,44 @@ static gk_status ensure_vecs(SolverCache* C, int64_t n, int count) {
 // with no loop node: the solve runs at most k passes, and every kernel of
 // it can be profiled (profilers do not see into graphs with conditional
 // nodes); for measurement only.
+// host_loop: three graphs instead -- C->exec = pre, C->exec_body = one
+// pass, body(stream, 0, 0), and C->exec_post = post -- which run_host_loop
+// launches, the passes from the host.
+template <class F>
+static gk_status capture_one(cudaStream_t cs, F&& f, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    GK_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    gk_status st = f(cs);
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (st != GK_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st != GK_OK ? st : GK_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    GK_CUDA(e);
+    return GK_OK;
+}
+
 template <class Pre, class Body, class Post>
-static gk_status capture_solve(gk_matrix A, SolverCache* C, Pre&& pre, Body&& body, Post&& post) {
+static gk_status capture_solve(gk_matrix A, SolverCache* C, Pre&& pre, Body&& body, Post&& post,
+                               bool host_loop) {
     GateCapture gate;  // one capture at a time, no device-wide call meanwhile
     GK_TRY(side_stream(A));
-    if (C->exec) {
-        cudaGraphExecDestroy(C->exec);
-        C->exec = nullptr;
+    for (cudaGraphExec_t* x : {&C->exec, &C->exec_body, &C->exec_post})
+        if (*x) {
+            cudaGraphExecDestroy(*x);
+            *x = nullptr;
+        }
+    if (host_loop) {
+        if (!C->hring) GK_CUDA(cudaMallocHost(&C->hring, 2 * HDR));
+        for (cudaEvent_t& e : C->evr)
+            if (!e) GK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        GK_TRY(capture_one(A->side, pre, &C->exec));
+        GK_TRY(capture_one(A->side, [&](cudaStream_t cs) { return body(cs, 0, 0); },
+                           &C->exec_body));
+        return capture_one(A->side, post, &C->exec_post);
     }
     int unrolled = 0;
     if (const char* e = getenv("GK_SOLVE_UNROLLED")) unrolled = std::max(0, atoi(e));
@@ -2069,6 +2110,44 @@ static gk_status capture_solve(gk_matrix A, SolverCache* C, Pre&& pre, Body&& bo
 }
 
 inline int chunk_for(int64_t n) { return n < 200000 ? 32 : 8; }
+
+// Where the Krylov loop runs: on the device (one graph with a conditional
+// WHILE node, the default) or, with GK_SOLVE_LOOP=host, from the host:
+// one graph per pass, launched while the previous pass runs.
+inline bool solve_loop_on_host() {
+    const char* e = getenv("GK_SOLVE_LOOP");
+    return e && strcmp(e, "host") == 0;
+}
+
+// A captured host-driven solve: pre, then passes until the state says the
+// loop is over (done; GMRES: halt) with two passes in flight, then post.
+// Each pass copies the state header into its pinned slot (pass k: slot
+// k % 2) and records that slot's event.  The pass issued after the last one
+// needed finds the solve halted and every kernel of it returns at once, so
+// the result is the device loop's, bit for bit.
+static gk_status run_host_loop(SolverCache* C, cudaStream_t s, bool gmres, int32_t max_loops) {
+    GK_CUDA(cudaGraphLaunch(C->exec, s));
+    char* ring = reinterpret_cast<char*>(C->hring);
+    auto issue = [&](int k) -> gk_status {
+        GK_CUDA(cudaGraphLaunch(C->exec_body, s));
+        GK_CUDA(cudaMemcpyAsync(ring + (size_t)(k & 1) * HDR, C->state.ptr, HDR,
+                                cudaMemcpyDeviceToHost, s));
+        GK_CUDA(cudaEventRecord(C->evr[k & 1], s));
+        return GK_OK;
+    };
+    int issued = 0;
+    GK_TRY(issue(issued++));
+    GK_TRY(issue(issued++));
+    for (int k = 0;; ++k) {
+        GK_CUDA(cudaEventSynchronize(C->evr[k & 1]));
+        const KState* h = reinterpret_cast<const KState*>(ring + (size_t)(k & 1) * HDR);
+        const bool over = gmres ? h->halt != 0 : h->done != 0;
+        if (over || k > max_loops + 2) break;  // the device bounds the passes too
+        GK_TRY(issue(issued++));
+    }
+    GK_CUDA(cudaGraphLaunch(C->exec_post, s));
+    return GK_OK;
+}
 
 
 // Runs one Krylov solve on the multi-kernel engine.  b, x: device vectors
@@ -2168,9 +2247,10 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
         GK_CUDA(cudaGetLastError());
         return GK_OK;
     };
+    const bool host_loop = !info_dev && solve_loop_on_host();
     const bool stale = !C->exec || C->kmethod != method || C->kprec != pkey || C->km != m ||
                        C->kchunk != chunk || C->kv != (void*)C->vecs.ptr ||
-                       C->kwait != A->wait_ns;
+                       C->kwait != A->wait_ns || C->khost != (int)host_loop;
     if (method == GK_GMRES && stale) {
         T* Vm = vec_at<T>(C, n, 3);
         T *w = vec_at<T>(C, n, 1), *z = vec_at<T>(C, n, 2);
@@ -2225,7 +2305,7 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
             GK_CUDA(cudaGetLastError());
             return GK_OK;
         };
-        GK_TRY(capture_solve(A, C, pre, body, post));
+        GK_TRY(capture_solve(A, C, pre, body, post, host_loop));
     } else if (stale) {
         // (re)start of the recurrence from r: gated by *gate when given
         auto init = [&](cudaStream_t q, const int32_t* gate) -> gk_status {
@@ -2357,7 +2437,7 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
             GK_CUDA(cudaGetLastError());
             return GK_OK;
         };
-        GK_TRY(capture_solve(A, C, pre, body, post));
+        GK_TRY(capture_solve(A, C, pre, body, post, host_loop));
     }
     if (stale) {
         C->kmethod = method;
@@ -2366,8 +2446,12 @@ gk_status solve_mk(gk_matrix A, const T* b, T* x, int method, int pkind, int32_t
         C->kchunk = chunk;
         C->kv = C->vecs.ptr;
         C->kwait = A->wait_ns;
+        C->khost = (int)host_loop;
     }
-    GK_CUDA(cudaGraphLaunch(C->exec, s));
+    if (host_loop)
+        GK_TRY(run_host_loop(C, s, method == GK_GMRES, max_loops));
+    else
+        GK_CUDA(cudaGraphLaunch(C->exec, s));
     GK_CUDA(cudaMemcpyAsync(x, xi, sizeof(T) * (size_t)n, cudaMemcpyDeviceToDevice, s));
     if (info_dev) {  // asynchronous: the outcome goes to device memory
         k_write_info<<<1, 1, 0, s>>>(st, info_dev, rowtile ? A->plan.err : nullptr, A->fmt,

@@ -17,13 +17,14 @@ precision) arrive at any time.  The server:
   get a lane of their own, so that they never occupy every worker;
 * batches continuously: small FP64 systems (n <= small_n) that arrive while
   the workers are busy wait in a pending list and are all launched together
-  in one gk_solve_batched call as soon as a worker frees up, on the
-  worker's highest-priority CUDA stream (its blocks are scheduled ahead of
-  a running large solve's as SMs free up); other solves run gk_solve one
-  per worker on a default-priority stream.  Measured on GB300 (the
-  24-matrix mix): two lanes of 2 + 4 workers lowered the saturation
-  throughput from ~104 to ~58 solves/s and raised p99 at 0.8x load, because
-  the long solves queued behind each other; so one pool is the default.
+  in one gk_solve_batched call as soon as a worker frees up; other solves
+  run gk_solve one per worker.  Measured on GB300 (the 24-matrix mix): two
+  lanes of 2 + 4 workers lowered the saturation throughput and raised p99
+  at 0.8x load, because the long solves queued behind each other, so one
+  pool is the default.  Batches on the highest-priority CUDA stream
+  (batch_priority="high") starved the large solves (the slowest request's
+  service time 3.2 s against 0.55 s, 73 against 92 solves/s at
+  saturation), so every launch uses the same priority by default.
 
 Latency is measured from submit() to the solution being back on the host.
 All compute runs in libgk.so; this module only schedules.
@@ -104,7 +105,8 @@ def estimate_seconds(m, precision):
 
 class SolveServer:
     def __init__(self, budget_bytes=40e9, workers=6, small_n=16384, batch_max=1024, device=0,
-                 long_workers=0, long_s=0.02, aging=1.0, order="fifo", long_priority="low"):
+                 long_workers=0, long_s=0.02, aging=1.0, order="fifo", long_priority="low",
+                 batch_priority="low"):
         import torch
         self.torch = torch
         self.dev = torch.device(f"cuda:{device}")
@@ -115,6 +117,7 @@ class SolveServer:
         self.aging = aging            # seconds of priority gained per second waited
         self.order = order            # "fifo" or "sjf" (smallest expected time, aged)
         self.long_priority = long_priority  # stream priority of the long lane: "low" or "high"
+        self.batch_priority = batch_priority  # stream priority of batched launches: "high" or "low"
         self.cv = threading.Condition()
         self.queue = collections.deque()      # submitted, not admitted
         self.pending_small = []               # admitted, waiting for a batch launch
@@ -318,13 +321,15 @@ class SolveServer:
     def _worker(self, lane):
         torch = self.torch
         torch.cuda.set_device(self.dev)
-        # batched small systems run on the highest-priority stream: their
-        # blocks are scheduled ahead of a large solve's as SMs free up
+        # batch_priority="high": batched small systems on the highest-priority
+        # stream, their blocks scheduled ahead of a large solve's
         lo, hi = torch.cuda.Stream.priority_range()
         stream_hi = torch.cuda.Stream(device=self.dev, priority=hi)
         stream_lo = torch.cuda.Stream(device=self.dev, priority=lo)
         if lane == "long" and self.long_priority == "high":
             stream_lo = stream_hi  # long solves ahead of everything else
+        if self.batch_priority != "high":
+            stream_hi = stream_lo  # batches at the priority of single solves
         while True:
             with self.cv:
                 while self.running and not self.jobs[lane]:

@@ -155,3 +155,31 @@ def test_unrolled_profiling_graph_gives_the_same_solve(monkeypatch):
     (x0, i0), (x1, i1) = out
     assert i0["return"] == i1["return"] == gk.GK_NOT_CONVERGED and i0["iters"] == i1["iters"] == 64
     assert np.array_equal(x0, x1)
+
+
+@pytest.mark.parametrize("method,precond", [("cg", "jacobi"), ("bicgstab", "jacobi"),
+                                            ("gmres", "jacobi"), ("cgs", None), ("cg", "ilu")])
+def test_host_driven_loop_equals_device_loop(monkeypatch, method, precond):
+    """GK_SOLVE_LOOP=host runs the same passes from the host (one graph per
+    pass, two in flight): the same bits, iterations and outcome as the
+    loop inside one graph, including a solve that converges mid-pass and
+    FP32 refinement (whose inner solves run the loop too)."""
+    import torch
+    m = W.diffusion_3d(20)
+    b = torch.from_numpy(W.uniform_vector(m.n, 8)).to(torch_dev())
+    out = {}
+    for mode in ("device", "host"):
+        monkeypatch.setenv("GK_SOLVE_LOOP", mode)
+        A = gk.Matrix.from_csr(m)
+        for mixed in (0, 1):
+            x = torch.zeros_like(b)
+            info = A.solve(b, x, method=method, precond=precond, tol=1e-10, max_iters=5000,
+                           engine=1, mixed=mixed)
+            out[mode, mixed] = (x.cpu().numpy(), info)
+        A.close()
+    for mixed in (0, 1):
+        (xd, idv), (xh, ih) = out["device", mixed], out["host", mixed]
+        assert idv["return"] == ih["return"] == gk.GK_OK, (idv, ih)
+        assert np.array_equal(xd, xh), mixed
+        assert (idv["iters"], idv["restarts"], idv["outer_iters"]) == \
+            (ih["iters"], ih["restarts"], ih["outer_iters"])

@@ -342,17 +342,28 @@ def _solve_format(m, **kw):
 
 def test_solve_format_selection(monkeypatch):
     """Solves on a CSR handle whose plan is the warp-tile kernel (short rows
-    of near-uniform length) run on the CSR itself; other CSR handles use ELL
-    when its padding is <= 20 %, else SELL-P(32) when its padding is <= 20 %,
-    else the CSR kernels.  The choice reads only the pattern, so a matrix
-    always solves the same way (bit-reproducible); every choice meets the
-    tolerance.  (The row sums of the layouts agree, but the fused dot
-    products add per-thread partials in a layout-specific order, so the
-    iterates of different layouts differ in rounding.)"""
+    of near-uniform length) and which holds at least 2^24 entries run on the
+    CSR itself; other CSR handles use ELL when its padding is <= 20 %, else
+    SELL-P(32) when its padding is <= 20 %, else the CSR kernels.  The choice
+    reads only the pattern, so a matrix always solves the same way
+    (bit-reproducible); every choice meets the tolerance.  (The row sums of
+    the layouts agree, but the fused dot products add per-thread partials in
+    a layout-specific order, so the iterates of different layouts differ in
+    rounding.)"""
+    import torch
     monkeypatch.delenv("GK_SOLVE_FORMAT", raising=False)
+    big = W.laplacian_3d(140)  # 19.1M entries, warp-tile plan
+    assert big.nnz >= 1 << 24
+    Ab = gk.Matrix.from_csr(big, "f64")
+    bb = torch.ones(big.n, dtype=torch.float64, device=torch_dev())
+    xb = torch.zeros_like(bb)
+    Ab.solve(bb, xb, method="cg", precond="jacobi", tol=1e-10, max_iters=2, engine=1)
+    assert Ab.describe()["solve_format"] == gk.GK_CSR
+    Ab.close()
+    del big, bb, xb
     m, b = CASES["lap2d_64"]()
-    fmt, x, info = _solve_format(m)
-    assert fmt == gk.GK_CSR and info["return"] == gk.GK_OK
+    fmt, x, info = _solve_format(m)  # warp-tile plan, but small: the ELL copy
+    assert fmt == gk.GK_ELL and info["return"] == gk.GK_OK
     assert oracle.true_rel_residual(m, W.uniform_vector(m.n, 11), x) <= 1e-10
     fmt_again, x_again, _ = _solve_format(m)
     assert fmt_again == fmt and np.array_equal(x, x_again)
