@@ -614,8 +614,8 @@ def serving_bench(gk, W, torch, dev, n_req=240, factors=((0.5, 400), (0.8, 2000)
         r.event.wait(600)
     out = {"workload": "24-matrix pool (2D 5-pt / 3D 7-pt / banded SPD w 5..64, n log-uniform "
                        "1e3..1e6), FP64 or FP32-refined 50/50, tol 1e-10..1e-8, Jacobi-CG, "
-                       "40 GB budget, 6 workers (arrival order; batched small systems on "
-                       "high-priority streams), "
+                       "40 GB budget, 6 workers (arrival order; small FP64 systems batched; "
+                       "one stream priority), "
                        f"{n_req}-request burst, " +
                        ", ".join(f"{c} requests at {f}x" for f, c in factors)}
     burst = reqs[:n_req]
