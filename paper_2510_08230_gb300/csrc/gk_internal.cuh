@@ -196,8 +196,17 @@ struct TriStore {
     int32_t cs = 32;                // rows per substitution chunk
     int32_t cpw = 1;                // substitution chunks per warp
     void* sync = nullptr;           // claim, exit and error words of both directions
+    // level-synchronous substitution (lvl = 1: picked): rows of L then U in
+    // level order (2n), each triangle's level starts (nlev + 1 each)
+    int32_t lvl = 0;
+    int32_t* lrows = nullptr;
+    int32_t* lstart = nullptr;
+    int32_t nlev[2] = {0, 0};
     DevBuf w;                       // scratch of one application
     void release() {
+        dfree(lrows);
+        dfree(lstart);
+        lrows = lstart = nullptr;
         dfree(rp);
         dfree(ci);
         dfree(dpos);

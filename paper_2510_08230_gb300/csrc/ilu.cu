@@ -283,6 +283,7 @@ static gk_status chunk_levels(const TriStore* S, int32_t n, int32_t cs, bool up,
     unsigned h[4] = {0, 0, 0, 0};
     GK_CUDA(cudaMemcpyAsync(h, mp, sizeof(h), cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaStreamSynchronize(s));
+    misc.release();
     if (h[1]) return GK_ERR_TIMEOUT;
     *nlev = h[3];
     return GK_OK;
@@ -309,6 +310,8 @@ static gk_status level_order(int32_t nch, int32_t pad, const DevBuf& lev, int32_
     unsigned h[5] = {0, 0, 0, 0, 0};
     GK_CUDA(cudaMemcpyAsync(h, mp, sizeof(h), cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaStreamSynchronize(s));
+    cnt.release();
+    misc.release();
     *maxw = h[2];
     *nord = h[4];
     return GK_OK;
@@ -326,7 +329,45 @@ struct IluLevels {
     unsigned levels(int cs, bool up) const {
         return cs == 32 ? (up ? nu32 : nl32) : cs == 8 ? (up ? nu8 : nl8) : (up ? nu1 : nl1);
     }
+    ~IluLevels() {
+        for (DevBuf* b : {&l32, &u32, &l8, &u8, &l1, &u1}) b->release();
+    }
 };
+
+// Level-synchronous mode: the rows of each triangle in level order (the
+// counting sort of their row levels, no padding) and the first position of
+// every level.  Levels are numbered 1..nlev (every level holds a row);
+// level l starts at start[l - 1], and start[nlev] = n.
+__global__ void k_level_starts(int32_t n, const int32_t* __restrict__ rows,
+                               const unsigned* __restrict__ lev, int32_t* __restrict__ start,
+                               int32_t nlev) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned l = lev[rows[idx]];
+        if (idx == 0 || lev[rows[idx - 1]] != l) start[l - 1] = (int32_t)idx;
+        if (idx == n - 1) start[nlev] = n;
+    }
+}
+
+static gk_status build_row_levels(TriStore* S, int32_t n, const IluLevels& lv, cudaStream_t s) {
+    if (S->lrows) return GK_OK;
+    const size_t nl = lv.nl1, nu = lv.nu1;
+    GK_CUDA(dmalloc_t(&S->lrows, 2 * (size_t)std::max(n, 1)));
+    GK_CUDA(dmalloc_t(&S->lstart, nl + nu + 2));
+    unsigned mw = 0, no = 0;
+    GK_TRY(level_order(n, 1, lv.l1, S->lrows, (size_t)n, &mw, &no, s));
+    if (no != (unsigned)n) return GK_ERR_CUDA;
+    GK_TRY(level_order(n, 1, lv.u1, S->lrows + n, (size_t)n, &mw, &no, s));
+    if (no != (unsigned)n) return GK_ERR_CUDA;
+    const unsigned g = ew_grid(n);
+    k_level_starts<<<g, 256, 0, s>>>(n, S->lrows, (const unsigned*)lv.l1.ptr, S->lstart, (int32_t)nl);
+    k_level_starts<<<g, 256, 0, s>>>(n, S->lrows + n, (const unsigned*)lv.u1.ptr, S->lstart + nl + 1,
+                                     (int32_t)nu);
+    GK_CUDA(cudaGetLastError());
+    S->nlev[0] = (int32_t)nl;
+    S->nlev[1] = (int32_t)nu;
+    return GK_OK;
+}
 
 // claim-order entries S->ord holds (both directions)
 static size_t ord_capacity(int32_t n) { return 2 * 4 * (size_t)std::max((n + 7) / 8, 1); }
@@ -351,6 +392,13 @@ static IluDev<T> tri_view(const TriStore* S, int32_t n) {
     f.warps[1] = S->warps[1];
     f.sy = (TrsvSync*)S->sync;
     if (const char* e = getenv("GK_ILU_PAUSE")) f.pause_max = (unsigned)std::max(32, atoi(e));
+    f.lvl = S->lvl;
+    f.lrows[0] = S->lrows;
+    f.lrows[1] = S->lrows ? S->lrows + n : nullptr;
+    f.lstart[0] = S->lstart;
+    f.lstart[1] = S->lstart ? S->lstart + S->nlev[0] + 1 : nullptr;
+    f.nlev[0] = S->nlev[0];
+    f.nlev[1] = S->nlev[1];
     return f;
 }
 
@@ -374,14 +422,17 @@ template IluDev<float> ilu_view<float>(gk_matrix);
 // one 8-row chunk a warp, 12.5 with four).  Each candidate gets its claim
 // orders, grid caps and one timed application (after a warm-up one) of
 // z = M^-1 d with d = 1/u_ii; the fastest is kept.  GK_ILU_CHUNK (8 or 32,
-// one chunk a warp; 1: single rows, 32 a warp) forces a shape.  Results
-// never depend on the choice, only the time does.
+// one chunk a warp; 1: single rows, 32 a warp; lvl: the level-synchronous
+// cluster kernel) forces a shape.  Results never depend on the choice,
+// only the time does.
 template <typename T>
 static gk_status tune_chunks(TriStore* S, int32_t n, const IluLevels& lv, cudaStream_t s) {
     int forced = 0;
+    bool forced_lvl = false;
     if (const char* e = getenv("GK_ILU_CHUNK")) {
         const int v = atoi(e);
         if (v == 1 || v == 8 || v == 32) forced = v;
+        if (!strcmp(e, "lvl")) forced_lvl = true, forced = 32;  // the chunk state stays valid
     }
     int64_t mult = 2;
     if (const char* e = getenv("GK_ILU_WARPS")) mult = std::max(1, atoi(e));
@@ -446,9 +497,42 @@ static gk_status tune_chunks(TriStore* S, int32_t n, const IluLevels& lv, cudaSt
             pick = k;
         }
     }
+    // the level-synchronous mode (one cluster, a barrier per row level):
+    // only when forced -- it measured slower than the chunked kernel on
+    // every matrix tried (GB300, FP64: 128^3 diffusion 4.70 against 2.81 ms
+    // per application, 2D Laplacian 1024^2 13.2 against 9.5 ms, power-law
+    // n = 2^21 with a dominant diagonal 76 against 12 ms): a level costs
+    // ~6 us, the L2 round trips of its row data and unknowns plus the
+    // barrier's release of its stores
+    bool lvl = false;
+    if (st == GK_OK && forced_lvl) {
+        gk_status ls = build_row_levels(S, n, lv, s);
+        float ms = 0.f;
+        if (ls == GK_OK) {
+            IluDev<T> f = tri_view<T>(S, n);
+            f.lvl = 1;
+            T* w = (T*)tmp.ptr;
+            const IluSrc<T> src{(const T*)S->rdiag};
+            ls = ilu_apply<T>(f, src, w, IluOutStore<T>{w + n}, IluSkipNever{}, IluNoErr{}, s);
+            if (ls == GK_OK && cudaEventRecord(e0, s) != cudaSuccess) ls = GK_ERR_CUDA;
+            if (ls == GK_OK)
+                ls = ilu_apply<T>(f, src, w, IluOutStore<T>{w + n}, IluSkipNever{}, IluNoErr{}, s);
+            if (ls == GK_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                                cudaEventSynchronize(e1) != cudaSuccess ||
+                                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                ls = GK_ERR_CUDA;
+        }
+        if (ls != GK_OK) {
+            cudaGetLastError();  // a cluster that cannot be scheduled: keep the chunks
+            if (forced_lvl) st = ls;
+        } else {
+            lvl = forced_lvl || ms < best;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != GK_OK) return st;
+    S->lvl = lvl ? 1 : 0;
     TrsvSync h[2];
     GK_CUDA(cudaMemcpyAsync(h, S->sync, sizeof(h), cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaStreamSynchronize(s));

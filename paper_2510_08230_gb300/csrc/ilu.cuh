@@ -88,6 +88,12 @@ struct IluDev {
     unsigned pause_max = 64;        // longest pause between polls (ns)
     unsigned long long wait_ns = WAIT_LIMIT_NS;  // budget of one wait (%globaltimer)
     int32_t warps[2] = {0, 0};      // host: warps per substitution launch
+    // level-synchronous mode (lvl != 0, see k_ilu_trsv_cluster): the rows of
+    // each triangle sorted by dependency level, and where each level starts
+    int32_t lvl = 0;
+    const int32_t* lrows[2] = {nullptr, nullptr};   // n rows each (L, U)
+    const int32_t* lstart[2] = {nullptr, nullptr};  // nlev + 1 offsets each
+    int32_t nlev[2] = {0, 0};
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -378,6 +384,129 @@ struct IluNoErr {
     __device__ __forceinline__ void operator()(unsigned) const {}
 };
 
+// ------------------------------------------------ level-synchronous mode
+// One thread-block cluster (CLT_BLOCKS blocks of CLT_THREADS) solves a whole
+// triangle level by level: the rows of a level are spread over the
+// cluster's threads, and a cluster barrier (release/acquire at cluster
+// scope) ends the level, so a level's values are visible to the next one
+// without polling.  Each row subtracts its terms in the substitution order
+// with fused multiply-adds, exactly as the chunked kernel, so the result is
+// the same bit for bit.  While a level's barrier completes, each thread
+// loads the next level's row data (rows, pivots, the first CLT_TPR terms'
+// columns and factors, the input values), which depend on nothing solved;
+// only the loads of solved values wait for the barrier.  The unknowns are
+// read at GPU scope from L2 (ld.relaxed.gpu): another block of the cluster
+// wrote them.  No thread ever waits on another except at the barrier.
+constexpr int CLT_BLOCKS = 8;    // a portable cluster size
+constexpr int CLT_THREADS = 512;
+constexpr int CLT_RPT = 4;       // rows of a level a thread prefetches
+constexpr int CLT_TPR = 4;       // terms of a row prefetched
+
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+    asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
+template <typename T>
+struct CltRow {
+    int32_t i;       // row (-1: none)
+    int32_t k, ke;   // its terms [k, ke) in substitution order (L ascending, U: k > ke, descending)
+    int32_t c[CLT_TPR];
+    T v[CLT_TPR];
+    T in, rd;
+};
+
+template <typename T, bool UP>
+__device__ __forceinline__ void clt_load(const IluDev<T>& f, const T* __restrict__ in, int32_t i,
+                                         CltRow<T>& R) {
+    R.i = i;
+    if (i < 0) return;
+    const int32_t d = f.dpos[i];
+    if (!UP) {
+        R.k = f.rp[i];
+        R.ke = d;
+    } else {
+        R.k = f.rp[i + 1] - 1;
+        R.ke = d;
+    }
+#pragma unroll
+    for (int t = 0; t < CLT_TPR; ++t) {
+        const int32_t kk = UP ? R.k - t : R.k + t;
+        const bool ok = UP ? kk > R.ke : kk < R.ke;
+        R.c[t] = ok ? f.ci[kk] : -1;
+        R.v[t] = ok ? f.lu[kk] : T(0);
+    }
+    R.in = in[i];
+    R.rd = (UP ? f.udiag : f.ldiag) ? f.rdiag[i] : T(1);
+}
+
+template <typename T, bool UP>
+__device__ __forceinline__ T clt_solve(const IluDev<T>& f, const CltRow<T>& R, const T* dst) {
+    T acc = mul_rn(R.in, T(1));  // quiets a signalling NaN, else exact
+    T z[CLT_TPR];
+#pragma unroll
+    for (int t = 0; t < CLT_TPR; ++t) z[t] = R.c[t] >= 0 ? ld_relaxed_v(dst + R.c[t]) : T(0);
+#pragma unroll
+    for (int t = 0; t < CLT_TPR; ++t)
+        if (R.c[t] >= 0) acc = sub_mul(acc, R.v[t], z[t]);
+    // terms past the prefetched ones, in the same order
+    if (UP) {
+        for (int32_t kk = R.k - CLT_TPR; kk > R.ke; --kk)
+            acc = sub_mul(acc, f.lu[kk], ld_relaxed_v(dst + f.ci[kk]));
+        return mul_rn(acc, R.rd);
+    }
+    for (int32_t kk = R.k + CLT_TPR; kk < R.ke; ++kk)
+        acc = sub_mul(acc, f.lu[kk], ld_relaxed_v(dst + f.ci[kk]));
+    return f.ldiag ? mul_rn(acc, R.rd) : acc;
+}
+
+template <typename T, bool UP, class Src, class Out, class Skip>
+__global__ void __launch_bounds__(CLT_THREADS, 1)
+k_ilu_trsv_cluster(IluDev<T> f, Src src, Out out, Skip sk) {
+    if (sk.skip()) return;  // read before the launch's first barrier: every block agrees
+    const unsigned nblk = gridDim.x;  // one cluster: the grid
+    const int32_t nthr = (int32_t)(nblk * CLT_THREADS);
+    const int32_t tid = (int32_t)(blockIdx.x * CLT_THREADS + threadIdx.x);
+    const int32_t* rows = f.lrows[UP ? 1 : 0];
+    const int32_t* start = f.lstart[UP ? 1 : 0];
+    const int32_t nlev = f.nlev[UP ? 1 : 0];
+    const T* in = src.ptr();
+    T* dst = out.dst();
+    CltRow<T> R[CLT_RPT];
+    auto prefetch = [&](int32_t L) {
+        const int32_t b = L < nlev ? start[L] : 0, e = L < nlev ? start[L + 1] : 0;
+#pragma unroll
+        for (int r = 0; r < CLT_RPT; ++r) {
+            const int32_t idx = b + tid + r * nthr;
+            clt_load<T, UP>(f, in, idx < e ? rows[idx] : -1, R[r]);
+        }
+    };
+    prefetch(0);
+    for (int32_t L = 0; L < nlev; ++L) {
+#pragma unroll
+        for (int r = 0; r < CLT_RPT; ++r)
+            if (R[r].i >= 0) {
+                const T v = clt_solve<T, UP>(f, R[r], dst);
+                dst[R[r].i] = v;
+                out.extra(R[r].i, v);
+            }
+        // rows of a level wider than CLT_RPT x the cluster's threads
+        const int32_t b = start[L], e = start[L + 1];
+        for (int32_t idx = b + tid + CLT_RPT * nthr; idx < e; idx += nthr) {
+            CltRow<T> X;
+            clt_load<T, UP>(f, in, rows[idx], X);
+            const T v = clt_solve<T, UP>(f, X, dst);
+            dst[X.i] = v;
+            out.extra(X.i, v);
+        }
+        cluster_arrive_release();
+        prefetch(L + 1);  // independent of the values being published
+        cluster_wait_acquire();
+    }
+}
+
 // Blocks of 256 threads for a substitution: `warps` warps (a few times the
 // widest level), at most the resident ones.
 template <typename K>
@@ -389,12 +518,35 @@ static unsigned ilu_grid(K kernel, int32_t warps) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * b));
 }
 
+// One level-synchronous substitution: a single cluster of CLT_BLOCKS blocks.
+template <typename T, bool UP, class Src, class Out, class Skip>
+static gk_status launch_clt(const IluDev<T>& f, Src src, Out out, Skip sk, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CLT_BLOCKS, 1, 1);
+    cfg.blockDim = dim3(CLT_THREADS, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CLT_BLOCKS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    GK_CUDA(cudaLaunchKernelEx(&cfg, k_ilu_trsv_cluster<T, UP, Src, Out, Skip>, f, src, out, sk));
+    return GK_OK;
+}
+
 // z = U^-1 L^-1 src: mark both outputs unsolved, L into w, then U from w
-// with the caller's output.
+// with the caller's output (level-synchronous mode: two cluster launches,
+// nothing to mark, no waits that could run out).
 template <typename T, class Src, class Out, class Skip, class Err>
 static gk_status ilu_apply(const IluDev<T>& f, Src src, T* w, Out out, Skip sk, Err on_err,
                            cudaStream_t s) {
     if (f.n == 0) return GK_OK;
+    if (f.lvl) {
+        GK_TRY((launch_clt<T, false>(f, src, IluOutStore<T>{w}, sk, s)));
+        return launch_clt<T, true>(f, IluSrc<T>{w}, out, sk, s);
+    }
     auto km = k_ilu_mark<T, Out, Skip>;
     auto kl = k_ilu_trsv<T, false, Src, IluOutStore<T>, Skip, IluNoErr>;
     auto ku = k_ilu_trsv<T, true, IluSrc<T>, Out, Skip, Err>;
@@ -412,6 +564,11 @@ static gk_status ilu_apply(const IluDev<T>& f, Src src, T* w, Out out, Skip sk, 
 template <typename T>
 static gk_status tri_apply(const IluDev<T>& f, bool up, const T* src, T* x, cudaStream_t s) {
     if (f.n == 0) return GK_OK;
+    if (f.lvl) {
+        if (up)
+            return launch_clt<T, true>(f, IluSrc<T>{src}, IluOutStore<T>{x}, IluSkipNever{}, s);
+        return launch_clt<T, false>(f, IluSrc<T>{src}, IluOutStore<T>{x}, IluSkipNever{}, s);
+    }
     auto km = k_ilu_mark<T, IluOutStore<T>, IluSkipNever>;
     const unsigned mg = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>(((int64_t)f.n + 1023) / 1024, (int64_t)num_sms() * 8));

@@ -370,15 +370,16 @@ def test_low_precision_storage_equals_fp32_of_the_rounded_values(low):
     F.close()
 
 
-@pytest.mark.parametrize("chunk", ["1", "8", "32"])
+@pytest.mark.parametrize("chunk", ["1", "8", "32", "lvl"])
 @pytest.mark.parametrize("case", ["lap2d_37x29", "convdiff_45", "diff3d_12", "random_700",
                                   "lap1d_33", "one_row", "power_law"])
 def test_every_substitution_shape_bit_exact(monkeypatch, chunk, case):
     """Each shape the setup can time for the substitutions (single rows,
     32 of one dependency level to a warp; 8- or 32-row chunks, one to a
-    warp) gives the oracle's substitution bit for bit, repeated applies
-    included: the shape changes only who computes a row, never its order of
-    subtractions."""
+    warp; "lvl": one thread-block cluster, level by level with a cluster
+    barrier between levels) gives the oracle's substitution bit for bit,
+    repeated applies included: the shape changes only who computes a row,
+    never its order of subtractions."""
     import torch
     monkeypatch.setenv("GK_ILU_CHUNK", chunk)
     dev = torch_dev()

@@ -41,7 +41,13 @@ def _solve(A, b, upper, unit, dtype):
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("upper", [False, True])
 @pytest.mark.parametrize("unit", [False, True])
-def test_fp64_bit_exact(case, upper, unit):
+@pytest.mark.parametrize("mode", ["tuned", "lvl"])
+def test_fp64_bit_exact(monkeypatch, case, upper, unit, mode):
+    """mode "lvl": the level-synchronous cluster substitution forced."""
+    if mode == "lvl":
+        monkeypatch.setenv("GK_ILU_CHUNK", "lvl")
+    else:
+        monkeypatch.delenv("GK_ILU_CHUNK", raising=False)
     m = CASES[case]()
     A = gk.Matrix.from_csr(m, "f64")
     rng = np.random.default_rng(5)
