@@ -67,6 +67,16 @@ def test_noalloc_allocates_nothing_after_setup():
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
     assert free1 == free0
+    # a call captured in global mode: any allocation (or other call that may
+    # synchronise the device) inside it would fail the capture
+    g = torch.cuda.CUDAGraph()
+    y2 = torch.full_like(y, float("nan"))
+    with torch.cuda.graph(g, capture_error_mode="global"):
+        st = gk.gk_spmv_csr_f64_noalloc(m.n, m.ncols, m.nnz, rp, ci, va, 1.0, xt, 0.0, y2)
+    assert st == 0
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y2, y)
 
 
 def test_noalloc_rejects_sizes_over_the_limit():
