@@ -581,7 +581,7 @@ def batched_compare(gk, W, torch, dev, count=2048, keep=None):
     return out
 
 
-def serving_bench(gk, W, torch, dev, n_req=480, factors=((0.5, 400), (0.8, 2000), (0.95, 400)),
+def serving_bench(gk, W, torch, dev, n_req=240, factors=((0.5, 400), (0.8, 2000), (0.95, 400)),
                   server_kw=None):
     """Config 5: Poisson arrivals of solve requests (2D/3D stencils and
     banded SPD, n log-uniform 1e3..1e6, FP64 or FP32-refined 50/50, tol
