@@ -334,7 +334,7 @@ gk_status gk_solve_async(gk_matrix A, const void* b, void* x,
  * of the count): each candidate runs the batch capped at 30 iterations from
  * the callers' initial guesses, which are restored afterwards; the choice
  * is cached for the process and reported per system in infos (spmv_format,
- * slice_size, block_threads).  Batches of fewer than 8 systems, or with
+ * slice_size, block_threads).  Batches of fewer than 64 systems, or with
  * GK_AUTOTUNE=0, use CSR and 256 threads;
  * GK_BATCH_LAYOUT (csr | ell | sellp8 | sellp16 | sellp32 | sellp64) and
  * GK_BATCH_THREADS force either choice.  All

@@ -540,11 +540,13 @@ static int nslots(int method) { return method == GK_CG ? 4 : 9; }
 // layout BL_CSR runs every system on its CSR arrays; BL_ELL gives each system
 // an ELL copy when ELL stores at most 1.2 x its nonzeros, else keeps its
 // CSR; BL_SELLP gives each system a SELL-P copy with slices of S rows.
-// nt: threads per block.  The untuned default (batches of fewer than 8
-// systems) is CSR with 256 threads: on lone serving-size systems (n 1,575 to
+// nt: threads per block.  The untuned default (batches of fewer than
+// TUNE_MIN_COUNT systems) is CSR with 256 threads: on lone serving-size systems (n 1,575 to
 // 13,689; stencils and banded SPD) CSR took 0.31-0.65x the time of ELL or
 // SELL-P(32) in the one-block kernel (e.g. 2D Laplacian n = 13,456: 33.8 ms
 // against 56.8 ms with ELL).
+constexpr int32_t TUNE_MIN_COUNT = 64;  // smallest batch the autotuner times
+
 struct BatchCfg {
     int nt = 256;
     int layout = BL_CSR;
@@ -926,7 +928,11 @@ extern "C" gk_status gk_solve_batched(int32_t count, const gk_matrix* As, const 
     const bool fnt = nt == 128 || nt == 256 || nt == 512;
     const bool flay = forced_layout(&cfg);
     const char* at = getenv("GK_AUTOTUNE");
-    if (!(fnt && flay) && !(at && at[0] == '0') && count >= 8) {
+    // batches of fewer than TUNE_MIN_COUNT systems run the untuned default:
+    // their trial runs cost more than a better layout saves (the serving
+    // loop's varying small batches, each a new shape, lost ~20 % of their
+    // throughput to them: 81 against 100 solves/s at saturation)
+    if (!(fnt && flay) && !(at && at[0] == '0') && count >= TUNE_MIN_COUNT) {
         int32_t nmax = 0;
         for (int32_t i = 0; i < count; ++i) nmax = std::max(nmax, As[i]->n);
         const uint64_t key = tune_key(As[0]->dtype, o, nmax, count);
