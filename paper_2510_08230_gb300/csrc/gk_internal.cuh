@@ -202,11 +202,21 @@ struct TriStore {
     int32_t* lrows = nullptr;
     int32_t* lstart = nullptr;
     int32_t nlev[2] = {0, 0};
+    // window mode (win = 1: picked): one record per level-ordered row of L
+    // then U (WinRec of the vector type), the deepest dependency in levels
+    // of each triangle, and the level-ordered input scratch (n values)
+    int32_t win = 0;
+    int32_t wdist[2] = {1, 1};
+    void* wrec = nullptr;
+    void* wperm = nullptr;
     DevBuf w;                       // scratch of one application
     void release() {
         dfree(lrows);
         dfree(lstart);
+        dfree(wrec);
+        dfree(wperm);
         lrows = lstart = nullptr;
+        wrec = wperm = nullptr;
         dfree(rp);
         dfree(ci);
         dfree(dpos);

@@ -349,6 +349,125 @@ __global__ void k_level_starts(int32_t n, const int32_t* __restrict__ rows,
     }
 }
 
+// ---------------------------------------------------- window-mode records
+__global__ void k_scatter_pos(int32_t n, const int32_t* __restrict__ rows, int32_t* __restrict__ pos) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x)
+        pos[rows[idx]] = (int32_t)idx;
+}
+
+// most terms of a row and deepest dependency (in levels) of one triangle
+template <bool UP>
+__global__ void k_win_check(int32_t n, const unsigned* __restrict__ lev,
+                            const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const int32_t* __restrict__ dpos, unsigned* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t d = dpos[i];
+        const int32_t k0 = UP ? d + 1 : rp[i], k1 = UP ? rp[i + 1] : d;
+        unsigned md = 0;
+        for (int32_t k = k0; k < k1; ++k) md = max(md, lev[i] - lev[ci[k]]);
+        atomicMax(out, (unsigned)(k1 - k0));
+        atomicMax(out + 1, md);
+    }
+}
+
+// record of level-ordered row idx: its terms in substitution order, each
+// with the block that owns its source row in the source's level, how many
+// levels back that is, and the source's index in the block's share
+template <typename T, bool UP>
+__global__ void k_win_rec(int32_t n, const int32_t* __restrict__ rows,
+                          const unsigned* __restrict__ lev, const int32_t* __restrict__ pos,
+                          const int32_t* __restrict__ start, const int32_t* __restrict__ rp,
+                          const int32_t* __restrict__ ci, const int32_t* __restrict__ dpos,
+                          const T* __restrict__ lu, const T* __restrict__ rdiag,
+                          WinRec<T>* __restrict__ rec) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = rows[idx];
+        const int32_t d = dpos[i];
+        WinRec<T> R;
+        R.i = i;
+        R.nt = 0;
+        R.rd = rdiag[i];
+        for (int t = 0; t < WIN_MAXT; ++t) {
+            R.co[t] = 0;
+            R.v[t] = T(0);
+        }
+        // L: ascending from the row start; U: descending from the row end
+        const int32_t nt = UP ? rp[i + 1] - 1 - d : d - rp[i];
+        for (int32_t t = 0; t < nt && t < WIN_MAXT; ++t) {
+            const int32_t k = UP ? rp[i + 1] - 1 - t : rp[i] + t;
+            const int32_t j = ci[k];
+            const int32_t lj = (int32_t)lev[j] - 1;  // levels are 1-based
+            const int32_t s0 = start[lj], len = start[lj + 1] - s0;
+            const int32_t per = (len + WIN_BLOCKS - 1) / WIN_BLOCKS;
+            const int32_t q = pos[j] - s0, r = q / per;
+            R.co[t] = (r << 20) | ((int32_t)(lev[i] - lev[j]) << 16) | (q - r * per);
+            R.v[t] = lu[k];
+        }
+        R.nt = nt;
+        rec[idx] = R;
+    }
+}
+
+// Builds the window-mode data when the matrix qualifies (at most WIN_MAXT
+// terms a row and dependencies at most WIN_MAXD levels back in each
+// triangle, at most WIN_CAP rows of a level per block); *ok = false
+// otherwise.  Needs the row levels (build_row_levels).
+template <typename T>
+static gk_status build_win(TriStore* S, int32_t n, const IluLevels& lv, cudaStream_t s, bool* ok) {
+    *ok = false;
+    if (n == 0) return GK_OK;
+    const unsigned* lev[2] = {(const unsigned*)lv.l1.ptr, (const unsigned*)lv.u1.ptr};
+    // shares per block: from the level starts
+    for (int u = 0; u < 2; ++u) {
+        std::vector<int32_t> h((size_t)S->nlev[u] + 1);
+        const int32_t* st = S->lstart + (u ? S->nlev[0] + 1 : 0);
+        GK_CUDA(cudaMemcpyAsync(h.data(), st, sizeof(int32_t) * h.size(), cudaMemcpyDeviceToHost, s));
+        GK_CUDA(cudaStreamSynchronize(s));
+        for (int32_t L = 0; L < S->nlev[u]; ++L)
+            if ((h[L + 1] - h[L] + WIN_BLOCKS - 1) / WIN_BLOCKS > WIN_CAP) return GK_OK;
+    }
+    DevBuf chk;
+    GK_TRY(chk.ensure(16));
+    GK_CUDA(cudaMemsetAsync(chk.ptr, 0, 16, s));
+    unsigned* cp = (unsigned*)chk.ptr;
+    const unsigned g = ew_grid(n);
+    k_win_check<false><<<g, 256, 0, s>>>(n, lev[0], S->rp, S->ci, S->dpos, cp);
+    k_win_check<true><<<g, 256, 0, s>>>(n, lev[1], S->rp, S->ci, S->dpos, cp + 2);
+    GK_CUDA(cudaGetLastError());
+    unsigned h[4];
+    GK_CUDA(cudaMemcpyAsync(h, cp, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GK_CUDA(cudaStreamSynchronize(s));
+    chk.release();
+    if (h[0] > WIN_MAXT || h[2] > WIN_MAXT || h[1] > WIN_MAXD || h[3] > WIN_MAXD) return GK_OK;
+    if (!S->wrec) GK_CUDA(dmalloc(&S->wrec, 2 * sizeof(WinRec<T>) * (size_t)n));
+    if (!S->wperm) GK_CUDA(dmalloc(&S->wperm, sizeof(T) * (size_t)n));
+    DevBuf pos;
+    GK_TRY(pos.ensure(sizeof(int32_t) * (size_t)n));
+    int32_t* pp = (int32_t*)pos.ptr;
+    WinRec<T>* rec = static_cast<WinRec<T>*>(S->wrec);
+    for (int u = 0; u < 2; ++u) {
+        const int32_t* rows = S->lrows + (u ? n : 0);
+        const int32_t* st = S->lstart + (u ? S->nlev[0] + 1 : 0);
+        k_scatter_pos<<<g, 256, 0, s>>>(n, rows, pp);
+        if (u)
+            k_win_rec<T, true><<<g, 256, 0, s>>>(n, rows, lev[1], pp, st, S->rp, S->ci, S->dpos,
+                                                (const T*)S->lu, (const T*)S->rdiag, rec + n);
+        else
+            k_win_rec<T, false><<<g, 256, 0, s>>>(n, rows, lev[0], pp, st, S->rp, S->ci, S->dpos,
+                                                 (const T*)S->lu, (const T*)S->rdiag, rec);
+    }
+    GK_CUDA(cudaGetLastError());
+    GK_CUDA(cudaStreamSynchronize(s));
+    pos.release();
+    S->wdist[0] = (int32_t)std::max(1u, h[1]);
+    S->wdist[1] = (int32_t)std::max(1u, h[3]);
+    *ok = true;
+    return GK_OK;
+}
+
 static gk_status build_row_levels(TriStore* S, int32_t n, const IluLevels& lv, cudaStream_t s) {
     if (S->lrows) return GK_OK;
     const size_t nl = lv.nl1, nu = lv.nu1;
@@ -399,6 +518,12 @@ static IluDev<T> tri_view(const TriStore* S, int32_t n) {
     f.lstart[1] = S->lstart ? S->lstart + S->nlev[0] + 1 : nullptr;
     f.nlev[0] = S->nlev[0];
     f.nlev[1] = S->nlev[1];
+    f.win = S->win;
+    f.wdist[0] = S->wdist[0];
+    f.wdist[1] = S->wdist[1];
+    f.wrec[0] = S->wrec;
+    f.wrec[1] = S->wrec ? static_cast<const char*>(S->wrec) + sizeof(WinRec<T>) * (size_t)n : nullptr;
+    f.wperm = static_cast<T*>(S->wperm);
     return f;
 }
 
@@ -428,11 +553,13 @@ template IluDev<float> ilu_view<float>(gk_matrix);
 template <typename T>
 static gk_status tune_chunks(TriStore* S, int32_t n, const IluLevels& lv, cudaStream_t s) {
     int forced = 0;
-    bool forced_lvl = false;
+    bool forced_lvl = false, forced_win = false;
     if (const char* e = getenv("GK_ILU_CHUNK")) {
         const int v = atoi(e);
         if (v == 1 || v == 8 || v == 32) forced = v;
-        if (!strcmp(e, "lvl")) forced_lvl = true, forced = 32;  // the chunk state stays valid
+        // the chunk state stays valid under a forced level-synchronous mode
+        if (!strcmp(e, "lvl")) forced_lvl = true, forced = 32;
+        if (!strcmp(e, "win")) forced_win = true, forced = 32;
     }
     int64_t mult = 2;
     if (const char* e = getenv("GK_ILU_WARPS")) mult = std::max(1, atoi(e));
@@ -529,10 +656,45 @@ static gk_status tune_chunks(TriStore* S, int32_t n, const IluLevels& lv, cudaSt
             lvl = forced_lvl || ms < best;
         }
     }
+    // the window mode (stencil-like matrices, see k_ilu_trsv_win): timed
+    // against the chunks when the matrix qualifies
+    bool win = false;
+    if (st == GK_OK && !lvl && (forced_win || !forced)) {
+        bool ok = false;
+        gk_status ws = build_row_levels(S, n, lv, s);
+        if (ws == GK_OK) ws = build_win<T>(S, n, lv, s, &ok);
+        float ms = 0.f;
+        if (ws == GK_OK && ok) {
+            IluDev<T> f = tri_view<T>(S, n);
+            f.win = 1;
+            T* w = (T*)tmp.ptr;
+            const IluSrc<T> src{(const T*)S->rdiag};
+            ws = ilu_apply<T>(f, src, w, IluOutStore<T>{w + n}, IluSkipNever{}, IluNoErr{}, s);
+            if (ws == GK_OK && cudaEventRecord(e0, s) != cudaSuccess) ws = GK_ERR_CUDA;
+            if (ws == GK_OK)
+                ws = ilu_apply<T>(f, src, w, IluOutStore<T>{w + n}, IluSkipNever{}, IluNoErr{}, s);
+            if (ws == GK_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                                cudaEventSynchronize(e1) != cudaSuccess ||
+                                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                ws = GK_ERR_CUDA;
+        }
+        if (ws != GK_OK) {
+            cudaGetLastError();  // a cluster that cannot be scheduled: keep the chunks
+            if (forced_win) st = ws;
+        } else if (ok) {
+            win = forced_win || ms < best;
+        }
+        if (!win) {  // not picked: its records go
+            dfree(S->wrec);
+            dfree(S->wperm);
+            S->wrec = S->wperm = nullptr;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != GK_OK) return st;
     S->lvl = lvl ? 1 : 0;
+    S->win = win ? 1 : 0;
     TrsvSync h[2];
     GK_CUDA(cudaMemcpyAsync(h, S->sync, sizeof(h), cudaMemcpyDeviceToHost, s));
     GK_CUDA(cudaStreamSynchronize(s));

@@ -53,6 +53,8 @@
 // results equal the plain substitution with that arithmetic bit for bit.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "gk_internal.cuh"
 #include "tma.cuh"
 
@@ -94,6 +96,12 @@ struct IluDev {
     const int32_t* lrows[2] = {nullptr, nullptr};   // n rows each (L, U)
     const int32_t* lstart[2] = {nullptr, nullptr};  // nlev + 1 offsets each
     int32_t nlev[2] = {0, 0};
+    // window mode (win != 0, see k_ilu_trsv_win): per triangle one record
+    // per level-ordered row, and a scratch vector for the level-ordered input
+    int32_t win = 0;
+    int32_t wdist[2] = {1, 1};           // deepest dependency, in levels
+    const void* wrec[2] = {nullptr, nullptr};  // WinRec<T>[n] each
+    T* wperm = nullptr;                  // n
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -518,6 +526,185 @@ static unsigned ilu_grid(K kernel, int32_t warps) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)num_sms() * b));
 }
 
+// ------------------------------------------------------------ window mode
+// Level-synchronous like k_ilu_trsv_cluster, for matrices whose rows
+// depend only on the previous WIN_MAXD levels (stencils in their natural
+// order: one level back) with at most WIN_MAXT terms a row per triangle.
+// Each of the cluster's blocks owns a contiguous share of every level's
+// rows, and keeps the values of its rows of the last D + 1 levels in a
+// shared-memory ring; a row reads the values it needs through distributed
+// shared memory, so a level's hand-off is a cluster barrier over shared
+// memory, without L2 round trips.  Everything a row needs besides those
+// values -- its record (the terms' cluster coordinates and factors in
+// substitution order, the pivot) and its input, permuted into level order
+// by k_perm_gather before the launch -- is one coalesced load, issued for
+// the next level between the barrier's arrive and wait.  The values go to
+// the output vector after the arrive, so the barrier's release waits on
+// shared-memory stores only.  The order of subtractions of every row is the
+// substitution order, so the result is bit-identical to the other modes.
+constexpr int WIN_BLOCKS = 8;     // portable cluster size
+constexpr int WIN_THREADS = 512;
+constexpr int WIN_MAXT = 4;       // terms of a row (per triangle)
+constexpr int WIN_MAXD = 2;       // deepest dependency, in levels
+constexpr int WIN_CAP = 1536;     // rows of a level per block
+constexpr int WIN_RPT = 3;        // rows per thread held across the barrier
+
+template <typename T>
+struct alignas(16) WinRec {
+    int32_t i, nt;           // row, terms
+    int32_t co[WIN_MAXT];    // term sources: rank << 20 | levels back << 16 | index in the block
+    T v[WIN_MAXT];           // factors, in substitution order
+    T rd;                    // reciprocal pivot
+};
+
+__device__ __forceinline__ void win_slice(const int32_t* start, int32_t L, unsigned rank,
+                                          int32_t& a, int32_t& b) {
+    const int32_t s0 = start[L], len = start[L + 1] - s0;
+    const int32_t per = (len + WIN_BLOCKS - 1) / WIN_BLOCKS;
+    a = s0 + min(len, (int32_t)rank * per);
+    b = s0 + min(len, (int32_t)(rank + 1) * per);
+}
+
+// the values a row needs, read from the owners' rings
+template <typename T>
+__device__ __forceinline__ void win_gather(const WinRec<T>& R, int32_t L, int nslot, T* ring,
+                                           T (&z)[WIN_MAXT]) {
+    namespace cgw = cooperative_groups;
+    cgw::cluster_group cl = cgw::this_cluster();
+#pragma unroll
+    for (int t = 0; t < WIN_MAXT; ++t) {
+        z[t] = T(0);
+        if (t < R.nt) {
+            const int32_t co = R.co[t];
+            const int slot = (L - ((co >> 16) & 15)) % nslot;
+            const T* src = cl.map_shared_rank(ring, (unsigned)(co >> 20));
+            z[t] = src[slot * WIN_CAP + (co & 0xFFFF)];
+        }
+    }
+}
+
+template <typename T, bool UP>
+__device__ __forceinline__ T win_finish(const IluDev<T>& f, const WinRec<T>& R, T in,
+                                        const T (&z)[WIN_MAXT]) {
+    T acc = mul_rn(in, T(1));  // quiets a signalling NaN, else exact
+#pragma unroll
+    for (int t = 0; t < WIN_MAXT; ++t)
+        if (t < R.nt) acc = sub_mul(acc, R.v[t], z[t]);
+    if (UP) return mul_rn(acc, f.udiag ? R.rd : T(1));
+    return f.ldiag ? mul_rn(acc, R.rd) : acc;
+}
+
+template <typename T, bool UP>
+__device__ __forceinline__ T win_solve(const IluDev<T>& f, const WinRec<T>& R, T in, int32_t L,
+                                       int nslot, T* ring) {
+    T z[WIN_MAXT];
+    win_gather<T>(R, L, nslot, ring, z);
+    return win_finish<T, UP>(f, R, in, z);
+}
+
+template <typename T, bool UP, class Out, class Skip>
+__global__ void __launch_bounds__(WIN_THREADS, 1)
+k_ilu_trsv_win(IluDev<T> f, Out out, Skip sk) {
+    if (sk.skip()) return;  // read before the first barrier: every block agrees
+    __shared__ T ring[(WIN_MAXD + 1) * WIN_CAP];
+    const unsigned rank = blockIdx.x;  // one cluster: the grid
+    const int nslot = f.wdist[UP ? 1 : 0] + 1;
+    const WinRec<T>* rec = static_cast<const WinRec<T>*>(f.wrec[UP ? 1 : 0]);
+    const int32_t* start = f.lstart[UP ? 1 : 0];
+    const int32_t nlev = f.nlev[UP ? 1 : 0];
+    const T* inp = f.wperm;
+    T* dst = out.dst();
+    WinRec<T> R[WIN_RPT];
+    T in[WIN_RPT];
+    int32_t a = 0, b = 0;
+    auto prefetch = [&](int32_t L) {
+        int32_t pa = 0, pb = 0;
+        if (L < nlev) win_slice(start, L, rank, pa, pb);
+#pragma unroll
+        for (int r = 0; r < WIN_RPT; ++r) {
+            const int32_t idx = pa + (int32_t)threadIdx.x + r * WIN_THREADS;
+            R[r].nt = -1;
+            if (idx < pb) {
+                R[r] = rec[idx];
+                in[r] = inp[idx];
+            }
+        }
+    };
+    prefetch(0);
+    for (int32_t L = 0; L < nlev; ++L) {
+        win_slice(start, L, rank, a, b);
+        T* mine = ring + (L % nslot) * WIN_CAP;
+        // every row's reads first, then the arithmetic, then the stores: the
+        // compiler cannot tell the rings' slots apart, so a store between
+        // two rows would order the next row's reads after it
+        T zz[WIN_RPT][WIN_MAXT], zv[WIN_RPT];
+#pragma unroll
+        for (int r = 0; r < WIN_RPT; ++r)
+            if (R[r].nt >= 0) win_gather<T>(R[r], L, nslot, ring, zz[r]);
+#pragma unroll
+        for (int r = 0; r < WIN_RPT; ++r)
+            if (R[r].nt >= 0) zv[r] = win_finish<T, UP>(f, R[r], in[r], zz[r]);
+#pragma unroll
+        for (int r = 0; r < WIN_RPT; ++r)
+            if (R[r].nt >= 0) mine[threadIdx.x + r * WIN_THREADS] = zv[r];
+        // rows past WIN_RPT x WIN_THREADS of this block's share
+        for (int32_t idx = a + (int32_t)threadIdx.x + WIN_RPT * WIN_THREADS; idx < b;
+             idx += WIN_THREADS) {
+            const WinRec<T> X = rec[idx];
+            const T v = win_solve<T, UP>(f, X, inp[idx], L, nslot, ring);
+            mine[idx - a] = v;
+            dst[X.i] = v;
+            out.extra(X.i, v);
+        }
+        cluster_arrive_release();
+#pragma unroll
+        for (int r = 0; r < WIN_RPT; ++r)
+            if (R[r].nt >= 0) {
+                dst[R[r].i] = zv[r];
+                out.extra(R[r].i, zv[r]);
+            }
+        prefetch(L + 1);
+        cluster_wait_acquire();
+    }
+}
+
+// out[idx] = src[rows[idx]]: an input in level order
+template <typename T, class Src, class Skip>
+__global__ void __launch_bounds__(256)
+k_perm_gather(int32_t n, const int32_t* __restrict__ rows, Src src, T* __restrict__ out, Skip sk) {
+    if (sk.skip()) return;
+    const T* in = src.ptr();
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x)
+        out[idx] = in[rows[idx]];
+}
+
+template <typename T, bool UP, class Out, class Skip>
+static gk_status launch_win(const IluDev<T>& f, Out out, Skip sk, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(WIN_BLOCKS, 1, 1);
+    cfg.blockDim = dim3(WIN_THREADS, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = WIN_BLOCKS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    GK_CUDA(cudaLaunchKernelEx(&cfg, k_ilu_trsv_win<T, UP, Out, Skip>, f, out, sk));
+    return GK_OK;
+}
+
+template <typename T, class Src, class Skip>
+static gk_status perm_gather(const IluDev<T>& f, bool up, Src src, Skip sk, cudaStream_t s) {
+    const unsigned g = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(((int64_t)f.n + 1023) / 1024, (int64_t)num_sms() * 8));
+    k_perm_gather<T, Src, Skip><<<g, 256, 0, s>>>(f.n, f.lrows[up ? 1 : 0], src, f.wperm, sk);
+    GK_CUDA(cudaGetLastError());
+    return GK_OK;
+}
+
 // One level-synchronous substitution: a single cluster of CLT_BLOCKS blocks.
 template <typename T, bool UP, class Src, class Out, class Skip>
 static gk_status launch_clt(const IluDev<T>& f, Src src, Out out, Skip sk, cudaStream_t s) {
@@ -543,6 +730,12 @@ template <typename T, class Src, class Out, class Skip, class Err>
 static gk_status ilu_apply(const IluDev<T>& f, Src src, T* w, Out out, Skip sk, Err on_err,
                            cudaStream_t s) {
     if (f.n == 0) return GK_OK;
+    if (f.win) {
+        GK_TRY((perm_gather<T>(f, false, src, sk, s)));
+        GK_TRY((launch_win<T, false>(f, IluOutStore<T>{w}, sk, s)));
+        GK_TRY((perm_gather<T>(f, true, IluSrc<T>{w}, sk, s)));
+        return launch_win<T, true>(f, out, sk, s);
+    }
     if (f.lvl) {
         GK_TRY((launch_clt<T, false>(f, src, IluOutStore<T>{w}, sk, s)));
         return launch_clt<T, true>(f, IluSrc<T>{w}, out, sk, s);
@@ -564,6 +757,11 @@ static gk_status ilu_apply(const IluDev<T>& f, Src src, T* w, Out out, Skip sk, 
 template <typename T>
 static gk_status tri_apply(const IluDev<T>& f, bool up, const T* src, T* x, cudaStream_t s) {
     if (f.n == 0) return GK_OK;
+    if (f.win) {
+        GK_TRY((perm_gather<T>(f, up, IluSrc<T>{src}, IluSkipNever{}, s)));
+        if (up) return launch_win<T, true>(f, IluOutStore<T>{x}, IluSkipNever{}, s);
+        return launch_win<T, false>(f, IluOutStore<T>{x}, IluSkipNever{}, s);
+    }
     if (f.lvl) {
         if (up)
             return launch_clt<T, true>(f, IluSrc<T>{src}, IluOutStore<T>{x}, IluSkipNever{}, s);

@@ -370,14 +370,16 @@ def test_low_precision_storage_equals_fp32_of_the_rounded_values(low):
     F.close()
 
 
-@pytest.mark.parametrize("chunk", ["1", "8", "32", "lvl"])
+@pytest.mark.parametrize("chunk", ["1", "8", "32", "lvl", "win"])
 @pytest.mark.parametrize("case", ["lap2d_37x29", "convdiff_45", "diff3d_12", "random_700",
                                   "lap1d_33", "one_row", "power_law"])
 def test_every_substitution_shape_bit_exact(monkeypatch, chunk, case):
     """Each shape the setup can time for the substitutions (single rows,
     32 of one dependency level to a warp; 8- or 32-row chunks, one to a
     warp; "lvl": one thread-block cluster, level by level with a cluster
-    barrier between levels) gives the oracle's substitution bit for bit,
+    barrier between levels; "win": the same with the recent levels' values
+    in distributed shared memory, where the matrix qualifies -- the others
+    fall back to the timed shapes) gives the oracle's substitution bit for bit,
     repeated applies included: the shape changes only who computes a row,
     never its order of subtractions."""
     import torch
@@ -396,4 +398,29 @@ def test_every_substitution_shape_bit_exact(monkeypatch, chunk, case):
         torch.cuda.synchronize()
         want = oracle.ilu0_apply(m, lu, r)
         assert np.array_equal(zt.cpu().numpy().view(np.uint64), want.view(np.uint64)), rep
+    A.close()
+
+
+def test_window_mode_on_a_stencil_bit_exact(monkeypatch):
+    """The 3D diffusion stencil qualifies for the shared-memory window mode
+    (3 terms a row per triangle, dependencies one level back); forced, it
+    must give the oracle's ILU(0) application and ILU-preconditioned GMRES
+    must converge as with the other shapes."""
+    import torch
+    monkeypatch.setenv("GK_ILU_CHUNK", "win")
+    m = W.diffusion_3d(40, seed=6)  # 64,000 rows, 118 levels per triangle
+    A = gk.Matrix.from_csr(m, "f64")
+    lu = oracle.ilu0(m)
+    r = W.uniform_vector(m.n, 23)
+    rt = torch.from_numpy(r).to(torch_dev())
+    zt = torch.full_like(rt, float("nan"))
+    for _ in range(2):
+        A.precond_apply(rt, zt, "ilu")
+        torch.cuda.synchronize()
+        want = oracle.ilu0_apply(m, lu, r)
+        assert np.array_equal(zt.cpu().numpy().view(np.uint64), want.view(np.uint64))
+    xt = torch.zeros_like(rt)
+    info = A.solve(rt, xt, method="gmres", precond="ilu", tol=1e-10, max_iters=2000)
+    assert info["return"] == gk.GK_OK, info
+    assert oracle.true_rel_residual(m, r, xt.cpu().numpy()) <= 1e-10
     A.close()

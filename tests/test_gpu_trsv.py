@@ -41,11 +41,12 @@ def _solve(A, b, upper, unit, dtype):
 @pytest.mark.parametrize("case", list(CASES))
 @pytest.mark.parametrize("upper", [False, True])
 @pytest.mark.parametrize("unit", [False, True])
-@pytest.mark.parametrize("mode", ["tuned", "lvl"])
+@pytest.mark.parametrize("mode", ["tuned", "lvl", "win"])
 def test_fp64_bit_exact(monkeypatch, case, upper, unit, mode):
-    """mode "lvl": the level-synchronous cluster substitution forced."""
-    if mode == "lvl":
-        monkeypatch.setenv("GK_ILU_CHUNK", "lvl")
+    """mode "lvl": the level-synchronous cluster substitution forced; "win":
+    its shared-memory window variant, where the matrix qualifies."""
+    if mode in ("lvl", "win"):
+        monkeypatch.setenv("GK_ILU_CHUNK", mode)
     else:
         monkeypatch.delenv("GK_ILU_CHUNK", raising=False)
     m = CASES[case]()
