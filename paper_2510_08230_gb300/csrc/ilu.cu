@@ -387,11 +387,9 @@ __global__ void k_win_rec(int32_t n, const int32_t* __restrict__ rows,
         const int32_t i = rows[idx];
         const int32_t d = dpos[i];
         WinRec<T> R;
-        R.i = i;
-        R.nt = 0;
         R.rd = rdiag[i];
         for (int t = 0; t < WIN_MAXT; ++t) {
-            R.co[t] = 0;
+            R.co[t] = -1;
             R.v[t] = T(0);
         }
         // L: ascending from the row start; U: descending from the row end
@@ -403,10 +401,10 @@ __global__ void k_win_rec(int32_t n, const int32_t* __restrict__ rows,
             const int32_t s0 = start[lj], len = start[lj + 1] - s0;
             const int32_t per = (len + WIN_BLOCKS - 1) / WIN_BLOCKS;
             const int32_t q = pos[j] - s0, r = q / per;
-            R.co[t] = (r << 20) | ((int32_t)(lev[i] - lev[j]) << 16) | (q - r * per);
+            R.co[t] = (int16_t)((r << (WIN_IDX_BITS + 1)) |
+                                ((int32_t)(lev[i] - lev[j] - 1) << WIN_IDX_BITS) | (q - r * per));
             R.v[t] = lu[k];
         }
-        R.nt = nt;
         rec[idx] = R;
     }
 }
@@ -419,6 +417,26 @@ template <typename T>
 static gk_status build_win(TriStore* S, int32_t n, const IluLevels& lv, cudaStream_t s, bool* ok) {
     *ok = false;
     if (n == 0) return GK_OK;
+    {  // the cluster must fit: WIN_BLOCKS blocks with their shared memory
+        auto k = k_ilu_trsv_win<T, false, IluOutStore<T>, IluSkipNever, IluNoErr>;
+        GK_TRY(win_attributes<T>(k));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(WIN_BLOCKS, 1, 1);
+        cfg.blockDim = dim3(WIN_THREADS, 1, 1);
+        cfg.dynamicSmemBytes = WinSmem<T>::bytes;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = WIN_BLOCKS;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, k, &cfg) != cudaSuccess || nc < 1) {
+            (void)cudaGetLastError();
+            return GK_OK;
+        }
+    }
     const unsigned* lev[2] = {(const unsigned*)lv.l1.ptr, (const unsigned*)lv.u1.ptr};
     // shares per block: from the level starts
     for (int u = 0; u < 2; ++u) {
@@ -443,7 +461,8 @@ static gk_status build_win(TriStore* S, int32_t n, const IluLevels& lv, cudaStre
     chk.release();
     if (h[0] > WIN_MAXT || h[2] > WIN_MAXT || h[1] > WIN_MAXD || h[3] > WIN_MAXD) return GK_OK;
     if (!S->wrec) GK_CUDA(dmalloc(&S->wrec, 2 * sizeof(WinRec<T>) * (size_t)n));
-    if (!S->wperm) GK_CUDA(dmalloc(&S->wperm, sizeof(T) * (size_t)n));
+    // the kernel's input copies are widened to 16-byte boundaries
+    if (!S->wperm) GK_CUDA(dmalloc(&S->wperm, sizeof(T) * ((size_t)n + WinSmem<T>::AL)));
     DevBuf pos;
     GK_TRY(pos.ensure(sizeof(int32_t) * (size_t)n));
     int32_t* pp = (int32_t*)pos.ptr;

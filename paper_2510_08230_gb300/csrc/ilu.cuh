@@ -53,6 +53,7 @@
 // results equal the plain substitution with that arithmetic bit for bit.
 #pragma once
 
+#include <atomic>
 #include <cooperative_groups.h>
 
 #include "gk_internal.cuh"
@@ -417,6 +418,20 @@ __device__ __forceinline__ void cluster_wait_acquire() {
     asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
 }
 
+// Arrive on the cluster barrier releasing this block's shared-memory writes
+// only (a restricted release fence, then a relaxed arrive; the wait side
+// acquires).  For the window mode: blocks exchange values through their
+// shared-memory rings alone, and the output vector's stores are read by no
+// block of the same launch, so they need not be performed before the
+// barrier completes.  A read of another block's ring is ordered before that
+// block's later overwrite of the slot by the barrier and by its value being
+// used before this block's arrive.
+__device__ __forceinline__ void cluster_arrive_release_smem() {
+    asm volatile(
+        "fence.release.sync_restrict::shared::cta.cluster;\n\t"
+        "barrier.cluster.arrive.relaxed;" ::: "memory");
+}
+
 template <typename T>
 struct CltRow {
     int32_t i;       // row (-1: none)
@@ -534,28 +549,82 @@ static unsigned ilu_grid(K kernel, int32_t warps) {
 // rows, and keeps the values of its rows of the last D + 1 levels in a
 // shared-memory ring; a row reads the values it needs through distributed
 // shared memory, so a level's hand-off is a cluster barrier over shared
-// memory, without L2 round trips.  Everything a row needs besides those
-// values -- its record (the terms' cluster coordinates and factors in
-// substitution order, the pivot) and its input, permuted into level order
-// by k_perm_gather before the launch -- is one coalesced load, issued for
-// the next level between the barrier's arrive and wait.  The values go to
-// the output vector after the arrive, so the barrier's release waits on
-// shared-memory stores only.  The order of subtractions of every row is the
-// substitution order, so the result is bit-identical to the other modes.
-constexpr int WIN_BLOCKS = 8;     // portable cluster size
-constexpr int WIN_THREADS = 512;
+// memory, without L2 round trips.  Everything else a row needs -- its
+// record (the terms' cluster coordinates and factors in substitution
+// order, the pivot) and its input, permuted into level order by
+// k_perm_gather before the launch -- depends on nothing solved: thread 0
+// of a block copies the block's share of a level's records and inputs into
+// shared memory with the bulk-copy unit a level ahead, and the threads move
+// the next level's into registers while a barrier completes, so no level
+// waits on a global load.  The values go to the output vector after the
+// arrive, and the arrive releases shared-memory writes only, so the barrier
+// never waits for global stores.  The order of subtractions of every row
+// is the substitution order, so the result is bit-identical to the other
+// modes.
+constexpr int WIN_BLOCKS = 16;    // a cluster over the portable 8 blocks
+constexpr int WIN_THREADS = 256;
 constexpr int WIN_MAXT = 4;       // terms of a row (per triangle)
 constexpr int WIN_MAXD = 2;       // deepest dependency, in levels
-constexpr int WIN_CAP = 1536;     // rows of a level per block
-constexpr int WIN_RPT = 3;        // rows per thread held across the barrier
+constexpr int WIN_RPT = 3;        // rows of a level per thread
+constexpr int WIN_CAP = WIN_RPT * WIN_THREADS;  // rows of a level per block
+// a term's coordinates in the 15 bits of WinRec::co: the index in the
+// owner's share, then one bit for the levels back, then the owner's rank
+constexpr int WIN_IDX_BITS = WIN_BLOCKS <= 8 ? 11 : 10;
+static_assert(WIN_BLOCKS <= (1 << (14 - WIN_IDX_BITS)) && WIN_MAXD <= 2 &&
+                  WIN_CAP <= (1 << WIN_IDX_BITS),
+              "a term's coordinates must fit the 15 bits of WinRec::co");
 
+// One level-ordered row of a triangle.  co[t]: the block that owns the
+// source row in the source's level (the top bits), how many levels back
+// that level is, less one (bit WIN_IDX_BITS), and the source's index in
+// that block's share (the low WIN_IDX_BITS bits); -1 past the row's terms,
+// whose factors are 0.
 template <typename T>
 struct alignas(16) WinRec {
-    int32_t i, nt;           // row, terms
-    int32_t co[WIN_MAXT];    // term sources: rank << 20 | levels back << 16 | index in the block
-    T v[WIN_MAXT];           // factors, in substitution order
-    T rd;                    // reciprocal pivot
+    T v[WIN_MAXT];          // factors, in substitution order
+    T rd;                   // reciprocal pivot
+    int16_t co[WIN_MAXT];
 };
+static_assert(sizeof(WinRec<double>) == 48 && sizeof(WinRec<float>) == 32,
+              "records are whole 16-byte chunks");
+
+// dynamic shared memory of k_ilu_trsv_win: two mbarriers, the ring of
+// values, two buffers of a level's records as they lie in global memory
+// (with 48-byte records a warp's 16-byte reads of them meet no bank
+// conflict), then two of inputs (their copy is widened to 16-byte
+// boundaries at both ends, so a buffer holds up to 32 bytes more)
+template <typename T>
+struct WinSmem {
+    static constexpr int NC = (int)(sizeof(WinRec<T>) / 16);
+    static constexpr int AL = (int)(16 / sizeof(T));  // inputs a 16-byte chunk
+    static constexpr int INCAP = WIN_CAP + 2 * AL;
+    static constexpr size_t bars = 16;
+    static constexpr size_t ring = (size_t)(WIN_MAXD + 1) * WIN_CAP * sizeof(T);
+    static constexpr size_t recs = (size_t)2 * WIN_CAP * NC * 16;
+    static constexpr size_t ins = (size_t)2 * INCAP * sizeof(T);
+    static constexpr size_t bytes = bars + ring + recs + ins;
+};
+static_assert(WinSmem<double>::bytes <= 227 * 1024, "one block per SM");
+
+// The window mode's wait for a copy: polls the barrier without the
+// suspension of mbarrier.try_wait, so a budget shorter than a copy runs out
+__device__ __forceinline__ bool win_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    auto done = [&]() {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        return ok != 0;
+    };
+    const uint64_t t0 = globaltimer_ns();
+    while (!done())
+        if (globaltimer_ns() - t0 >= limit_ns) return false;
+    return true;
+}
 
 __device__ __forceinline__ void win_slice(const int32_t* start, int32_t L, unsigned rank,
                                           int32_t& a, int32_t& b) {
@@ -565,110 +634,198 @@ __device__ __forceinline__ void win_slice(const int32_t* start, int32_t L, unsig
     b = s0 + min(len, (int32_t)(rank + 1) * per);
 }
 
-// the values a row needs, read from the owners' rings
+// address of the same shared-memory location in block `rank` of the cluster
+__device__ __forceinline__ uint32_t dsmem_map(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void dsmem_ld(double& v, uint32_t addr) {
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr) : "memory");
+}
+__device__ __forceinline__ void dsmem_ld(float& v, uint32_t addr) {
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+}
+
+// the values a row needs, read from the owners' rings: ring1 / ring2 are
+// the shared-memory addresses of the slots of the levels one and two back
 template <typename T>
-__device__ __forceinline__ void win_gather(const WinRec<T>& R, int32_t L, int nslot, T* ring,
+__device__ __forceinline__ void win_gather(const WinRec<T>& R, uint32_t ring1, uint32_t ring2,
                                            T (&z)[WIN_MAXT]) {
-    namespace cgw = cooperative_groups;
-    cgw::cluster_group cl = cgw::this_cluster();
 #pragma unroll
     for (int t = 0; t < WIN_MAXT; ++t) {
         z[t] = T(0);
-        if (t < R.nt) {
-            const int32_t co = R.co[t];
-            const int slot = (L - ((co >> 16) & 15)) % nslot;
-            const T* src = cl.map_shared_rank(ring, (unsigned)(co >> 20));
-            z[t] = src[slot * WIN_CAP + (co & 0xFFFF)];
+        const int32_t co = R.co[t];
+        if (co >= 0) {
+            const uint32_t a = ((co >> WIN_IDX_BITS) & 1 ? ring2 : ring1) +
+                               (uint32_t)(co & ((1 << WIN_IDX_BITS) - 1)) * sizeof(T);
+            dsmem_ld(z[t], dsmem_map(a, (uint32_t)(co >> (WIN_IDX_BITS + 1))));
         }
     }
 }
 
+// in: already multiplied by 1 by k_perm_gather (which quiets a signalling
+// NaN, as the other modes do first; exact otherwise)
 template <typename T, bool UP>
 __device__ __forceinline__ T win_finish(const IluDev<T>& f, const WinRec<T>& R, T in,
                                         const T (&z)[WIN_MAXT]) {
-    T acc = mul_rn(in, T(1));  // quiets a signalling NaN, else exact
+    T acc = in;
 #pragma unroll
     for (int t = 0; t < WIN_MAXT; ++t)
-        if (t < R.nt) acc = sub_mul(acc, R.v[t], z[t]);
+        if (R.co[t] >= 0) acc = sub_mul(acc, R.v[t], z[t]);
     if (UP) return mul_rn(acc, f.udiag ? R.rd : T(1));
     return f.ldiag ? mul_rn(acc, R.rd) : acc;
 }
 
-template <typename T, bool UP>
-__device__ __forceinline__ T win_solve(const IluDev<T>& f, const WinRec<T>& R, T in, int32_t L,
-                                       int nslot, T* ring) {
-    T z[WIN_MAXT];
-    win_gather<T>(R, L, nslot, ring, z);
-    return win_finish<T, UP>(f, R, in, z);
-}
-
-template <typename T, bool UP, class Out, class Skip>
+template <typename T, bool UP, class Out, class Skip, class Err>
 __global__ void __launch_bounds__(WIN_THREADS, 1)
-k_ilu_trsv_win(IluDev<T> f, Out out, Skip sk) {
+k_ilu_trsv_win(IluDev<T> f, Out out, Skip sk, Err on_err) {
     if (sk.skip()) return;  // read before the first barrier: every block agrees
-    __shared__ T ring[(WIN_MAXD + 1) * WIN_CAP];
+    using SM = WinSmem<T>;
+    extern __shared__ __align__(16) unsigned char wsm[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wsm);
+    T* ring = reinterpret_cast<T*>(wsm + SM::bars);
+    WinRec<T>* rbuf = reinterpret_cast<WinRec<T>*>(wsm + SM::bars + SM::ring);
+    T* ibuf = reinterpret_cast<T*>(wsm + SM::bars + SM::ring + SM::recs);
     const unsigned rank = blockIdx.x;  // one cluster: the grid
+    const int tid = (int)threadIdx.x;
     const int nslot = f.wdist[UP ? 1 : 0] + 1;
     const WinRec<T>* rec = static_cast<const WinRec<T>*>(f.wrec[UP ? 1 : 0]);
     const int32_t* start = f.lstart[UP ? 1 : 0];
+    const int32_t* rows = f.lrows[UP ? 1 : 0];
     const int32_t nlev = f.nlev[UP ? 1 : 0];
     const T* inp = f.wperm;
     T* dst = out.dst();
-    WinRec<T> R[WIN_RPT];
-    T in[WIN_RPT];
-    int32_t a = 0, b = 0;
-    auto prefetch = [&](int32_t L) {
-        int32_t pa = 0, pb = 0;
-        if (L < nlev) win_slice(start, L, rank, pa, pb);
-#pragma unroll
-        for (int r = 0; r < WIN_RPT; ++r) {
-            const int32_t idx = pa + (int32_t)threadIdx.x + r * WIN_THREADS;
-            R[r].nt = -1;
-            if (idx < pb) {
-                R[r] = rec[idx];
-                in[r] = inp[idx];
-            }
+    unsigned* err = &f.sy[UP ? 1 : 0].err;
+    // thread 0 copies the block's share of level L's records and inputs into
+    // buffer L & 1 with the bulk-copy unit; the buffer's mbarrier completes
+    // a phase when the bytes have landed
+    auto stage = [&](int32_t L) {
+        int32_t a, b;
+        win_slice(start, L, rank, a, b);
+        const int buf = L & 1;
+        const uint32_t bar = smem_addr(bars + buf);
+        const int32_t a0 = a & ~(SM::AL - 1), b0 = (b + SM::AL - 1) & ~(SM::AL - 1);
+        const uint32_t rb = (uint32_t)(b - a) * (uint32_t)sizeof(WinRec<T>);
+        const uint32_t ib = (uint32_t)(b0 - a0) * (uint32_t)sizeof(T);
+        mbar_arrive_expect_tx(bar, b > a ? rb + ib : 0u);
+        if (b > a) {
+            bulk_g2s(smem_addr(rbuf + (size_t)buf * WIN_CAP), rec + a, rb, bar);
+            bulk_g2s(smem_addr(ibuf + (size_t)buf * SM::INCAP), inp + a0, ib, bar);
         }
     };
-    prefetch(0);
-    for (int32_t L = 0; L < nlev; ++L) {
+    WinRec<T> R[WIN_RPT];
+    T in[WIN_RPT];
+    int32_t ii[WIN_RPT];
+    bool has[WIN_RPT];
+    // level L's rows from its buffer into registers once its copy landed
+    // (their row numbers from the level order, needed only after the
+    // level's arrive); false if the wait ran out
+    auto take = [&](int32_t L) -> bool {
+        int32_t a, b;
         win_slice(start, L, rank, a, b);
+        const int buf = L & 1;
+        const bool ok = win_wait(smem_addr(bars + buf), (uint32_t)(L >> 1) & 1u, f.wait_ns);
+        const WinRec<T>* sr = rbuf + (size_t)buf * WIN_CAP;
+        const T* si = ibuf + (size_t)buf * SM::INCAP + (a & (SM::AL - 1));
+#pragma unroll
+        for (int r = 0; r < WIN_RPT; ++r) {
+            const int32_t q = tid + r * WIN_THREADS;
+            has[r] = ok && a + q < b;
+            if (has[r]) {
+                R[r] = sr[q];
+                in[r] = si[q];
+                ii[r] = rows[a + q];
+            }
+        }
+        return ok;
+    };
+    if (tid == 0) {
+        mbar_init(smem_addr(bars), 1);
+        mbar_init(smem_addr(bars + 1), 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    bool live = true;             // every copy issued so far was waited for
+    int32_t pend = 0, npend = 0;  // else levels [pend, pend + npend) may be in flight
+    if (tid == 0) {
+        if (nlev > 0) stage(0);
+        if (nlev > 1) stage(1);
+    }
+    if (nlev > 0) {
+        live = __syncthreads_and(take(0)) != 0;
+        if (!live) npend = min(nlev, 2);
+    }
+    const uint32_t ring0 = smem_addr(ring);
+    constexpr uint32_t SLOT = WIN_CAP * sizeof(T);
+    for (int32_t L = 0; L < nlev; ++L) {
         T* mine = ring + (L % nslot) * WIN_CAP;
+        const uint32_t ring1 = ring0 + (uint32_t)((L + 2 * nslot - 1) % nslot) * SLOT;
+        const uint32_t ring2 = ring0 + (uint32_t)((L + 2 * nslot - 2) % nslot) * SLOT;
         // every row's reads first, then the arithmetic, then the stores: the
         // compiler cannot tell the rings' slots apart, so a store between
         // two rows would order the next row's reads after it
         T zz[WIN_RPT][WIN_MAXT], zv[WIN_RPT];
 #pragma unroll
         for (int r = 0; r < WIN_RPT; ++r)
-            if (R[r].nt >= 0) win_gather<T>(R[r], L, nslot, ring, zz[r]);
+            if (has[r]) win_gather<T>(R[r], ring1, ring2, zz[r]);
 #pragma unroll
         for (int r = 0; r < WIN_RPT; ++r)
-            if (R[r].nt >= 0) zv[r] = win_finish<T, UP>(f, R[r], in[r], zz[r]);
+            if (has[r]) zv[r] = win_finish<T, UP>(f, R[r], in[r], zz[r]);
 #pragma unroll
         for (int r = 0; r < WIN_RPT; ++r)
-            if (R[r].nt >= 0) mine[threadIdx.x + r * WIN_THREADS] = zv[r];
-        // rows past WIN_RPT x WIN_THREADS of this block's share
-        for (int32_t idx = a + (int32_t)threadIdx.x + WIN_RPT * WIN_THREADS; idx < b;
-             idx += WIN_THREADS) {
-            const WinRec<T> X = rec[idx];
-            const T v = win_solve<T, UP>(f, X, inp[idx], L, nslot, ring);
-            mine[idx - a] = v;
-            dst[X.i] = v;
-            out.extra(X.i, v);
-        }
-        cluster_arrive_release();
+            if (has[r]) mine[tid + r * WIN_THREADS] = zv[r];
+        cluster_arrive_release_smem();
 #pragma unroll
         for (int r = 0; r < WIN_RPT; ++r)
-            if (R[r].nt >= 0) {
-                dst[R[r].i] = zv[r];
-                out.extra(R[r].i, zv[r]);
+            if (has[r]) {
+                dst[ii[r]] = zv[r];
+                out.extra(ii[r], zv[r]);
             }
-        prefetch(L + 1);
+        if (L + 1 < nlev) {
+            // level L + 1's copy was issued a level ahead; the block barrier
+            // also tells that every thread has taken level L's rows out of
+            // the buffer that level L + 2 is copied into
+            bool ok = live && take(L + 1);
+            ok = __syncthreads_and(ok) != 0;
+            if (live && !ok) {
+                pend = L + 1;
+                npend = 1;
+            }
+            live = ok;
+            if (!live)
+#pragma unroll
+                for (int r = 0; r < WIN_RPT; ++r) has[r] = false;
+            if (tid == 0 && live && L + 2 < nlev) {
+                fence_proxy_async_smem();
+                stage(L + 2);
+            }
+        }
         cluster_wait_acquire();
+    }
+    if (npend > 0) {
+        // a wait ran out: report it, and keep the shared memory until the
+        // copies in flight have landed (with the default limit, not the
+        // caller's budget: the block must outlive the copies into it)
+        if (tid == 0) {
+            atomicExch(err, 1u);
+            for (int32_t L = pend; L < pend + npend; ++L)
+                mbar_wait_bounded(smem_addr(bars + (L & 1)), (uint32_t)(L >> 1) & 1u);
+        }
+        __syncthreads();
+    }
+    if (UP) {
+        // the U launch hands both directions' error flags to on_err, after
+        // a barrier that orders every block's report before the read
+        cluster_arrive_release();
+        cluster_wait_acquire();
+        if (rank == 0 && tid == 0)
+            on_err(ld_acquire_u32(&f.sy[0].err) | ld_acquire_u32(&f.sy[1].err));
     }
 }
 
-// out[idx] = src[rows[idx]]: an input in level order
+// out[idx] = src[rows[idx]] * 1: an input in level order, a signalling NaN
+// quieted as the substitutions of the other modes do first
 template <typename T, class Src, class Skip>
 __global__ void __launch_bounds__(256)
 k_perm_gather(int32_t n, const int32_t* __restrict__ rows, Src src, T* __restrict__ out, Skip sk) {
@@ -676,14 +833,33 @@ k_perm_gather(int32_t n, const int32_t* __restrict__ rows, Src src, T* __restric
     const T* in = src.ptr();
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x)
-        out[idx] = in[rows[idx]];
+        out[idx] = mul_rn(in[rows[idx]], T(1));
 }
 
-template <typename T, bool UP, class Out, class Skip>
-static gk_status launch_win(const IluDev<T>& f, Out out, Skip sk, cudaStream_t s) {
+template <typename T, class K>
+static gk_status win_attributes(K k) {
+    if (WIN_BLOCKS > 8)
+        GK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    GK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)WinSmem<T>::bytes));
+    return GK_OK;
+}
+
+template <typename T, bool UP, class Out, class Skip, class Err>
+static gk_status launch_win(const IluDev<T>& f, Out out, Skip sk, Err on_err, cudaStream_t s) {
+    auto k = k_ilu_trsv_win<T, UP, Out, Skip, Err>;
+    // more than the default 48 KB of dynamic shared memory, and a cluster
+    // over 8 blocks where WIN_BLOCKS asks for one (attributes of the
+    // function, not stream operations: set once, before the first launch)
+    static std::atomic<bool> attr{false};
+    if (!attr.load(std::memory_order_acquire)) {
+        GK_TRY(win_attributes<T>(k));
+        attr.store(true, std::memory_order_release);
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(WIN_BLOCKS, 1, 1);
     cfg.blockDim = dim3(WIN_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = WinSmem<T>::bytes;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -692,7 +868,7 @@ static gk_status launch_win(const IluDev<T>& f, Out out, Skip sk, cudaStream_t s
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    GK_CUDA(cudaLaunchKernelEx(&cfg, k_ilu_trsv_win<T, UP, Out, Skip>, f, out, sk));
+    GK_CUDA(cudaLaunchKernelEx(&cfg, k, f, out, sk, on_err));
     return GK_OK;
 }
 
@@ -732,9 +908,9 @@ static gk_status ilu_apply(const IluDev<T>& f, Src src, T* w, Out out, Skip sk, 
     if (f.n == 0) return GK_OK;
     if (f.win) {
         GK_TRY((perm_gather<T>(f, false, src, sk, s)));
-        GK_TRY((launch_win<T, false>(f, IluOutStore<T>{w}, sk, s)));
+        GK_TRY((launch_win<T, false>(f, IluOutStore<T>{w}, sk, IluNoErr{}, s)));
         GK_TRY((perm_gather<T>(f, true, IluSrc<T>{w}, sk, s)));
-        return launch_win<T, true>(f, out, sk, s);
+        return launch_win<T, true>(f, out, sk, on_err, s);
     }
     if (f.lvl) {
         GK_TRY((launch_clt<T, false>(f, src, IluOutStore<T>{w}, sk, s)));
@@ -759,8 +935,8 @@ static gk_status tri_apply(const IluDev<T>& f, bool up, const T* src, T* x, cuda
     if (f.n == 0) return GK_OK;
     if (f.win) {
         GK_TRY((perm_gather<T>(f, up, IluSrc<T>{src}, IluSkipNever{}, s)));
-        if (up) return launch_win<T, true>(f, IluOutStore<T>{x}, IluSkipNever{}, s);
-        return launch_win<T, false>(f, IluOutStore<T>{x}, IluSkipNever{}, s);
+        if (up) return launch_win<T, true>(f, IluOutStore<T>{x}, IluSkipNever{}, IluNoErr{}, s);
+        return launch_win<T, false>(f, IluOutStore<T>{x}, IluSkipNever{}, IluNoErr{}, s);
     }
     if (f.lvl) {
         if (up)

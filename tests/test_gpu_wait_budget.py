@@ -108,6 +108,39 @@ def test_ilu_solve_times_out_then_recovers(banded, method, mixed):
     assert oracle.true_rel_residual(m, b, xt.cpu().numpy()) <= 1e-10
 
 
+def test_window_mode_times_out_then_recovers(monkeypatch):
+    """The window mode's substitutions wait only for their own bulk copies
+    of the rows' records: with a budget shorter than one copy (the first
+    level's is waited for right after it is issued) the apply returns
+    GK_ERR_TIMEOUT, the blocks still wait for their copies in flight before
+    they exit, and the next apply with the default budget is exact."""
+    import torch
+    monkeypatch.setenv("GK_ILU_CHUNK", "win")
+    m = W.laplacian_3d(24)
+    A = gk.Matrix.from_csr(m, "f64")
+    r = W.uniform_vector(m.n, 8)
+    rt, zt = _dev(r), _dev(np.zeros(m.n))
+    want = oracle.ilu0_apply(m, oracle.ilu0(m), r)
+    A.precond_apply(rt, zt, "ilu")
+    torch.cuda.synchronize()
+    assert np.array_equal(zt.cpu().numpy(), want)
+    st = gk.gk_precond_apply(A.handle, "ilu", 0, rt, zt, 1)
+    assert st == gk.GK_ERR_TIMEOUT
+    zt.zero_()
+    A.precond_apply(rt, zt, "ilu")
+    torch.cuda.synchronize()
+    assert np.array_equal(zt.cpu().numpy(), want)
+    b = W.uniform_vector(m.n, 9)
+    bt, xt = _dev(b), _dev(np.zeros(m.n))
+    info = A.solve(bt, xt, method="cg", precond="ilu", tol=1e-10, max_iters=500, wait_budget_ns=1)
+    assert info["return"] == gk.GK_ERR_TIMEOUT, info
+    xt.zero_()
+    info = A.solve(bt, xt, method="cg", precond="ilu", tol=1e-10, max_iters=500)
+    assert info["return"] == gk.GK_OK, info
+    assert oracle.true_rel_residual(m, b, xt.cpu().numpy()) <= 1e-10
+    A.close()
+
+
 def test_negative_budget_is_invalid(banded):
     m, A = banded
     rt, zt = _dev(np.ones(m.n)), _dev(np.zeros(m.n))
