@@ -401,6 +401,40 @@ def test_every_substitution_shape_bit_exact(monkeypatch, chunk, case):
     A.close()
 
 
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("case", ["lap2d_37x29", "diff3d_12", "lap1d_33", "one_row"])
+def test_shapes_agree_bit_for_bit_with_signalling_nan_inputs(monkeypatch, dtype, case):
+    """Every substitution shape gives the same bits as the 32-row chunks, in
+    FP32 as in FP64, for an input holding signalling NaNs: each shape
+    multiplies its inputs by 1 before the first subtraction (the window mode
+    in its level-order gather), so a NaN comes out the same in every row
+    that depends on it, and the other rows are untouched."""
+    import torch
+    dev = torch_dev()
+    m = CASES[case]()
+    vt = torch.float64 if dtype == "f64" else torch.float32
+    ut = np.uint64 if dtype == "f64" else np.uint32
+    snan = ut(0x7FF0000000000005) if dtype == "f64" else ut(0x7F800005)
+    r = W.uniform_vector(m.n, 17).astype(np.float64 if dtype == "f64" else np.float32)
+    bad = sorted({m.n // 2, m.n - 1})
+    r.view(ut)[bad] = snan
+    outs = {}
+    for chunk in ["32", "8", "1", "lvl", "win"]:
+        monkeypatch.setenv("GK_ILU_CHUNK", chunk)
+        A = gk.Matrix.from_csr(m, dtype)
+        rt = torch.from_numpy(r).to(dev)
+        zt = torch.zeros(m.n, dtype=vt, device=dev)
+        A.precond_apply(rt, zt, "ilu")
+        torch.cuda.synchronize()
+        outs[chunk] = zt.cpu().numpy().view(ut).copy()
+        A.close()
+    z = outs["32"].view(r.dtype)
+    assert np.isnan(z[bad]).all()
+    assert not np.any(outs["32"] == snan)
+    for chunk, o in outs.items():
+        assert np.array_equal(o, outs["32"]), chunk
+
+
 def test_window_mode_on_a_stencil_bit_exact(monkeypatch):
     """The 3D diffusion stencil qualifies for the shared-memory window mode
     (3 terms a row per triangle, dependencies one level back); forced, it
