@@ -56,6 +56,23 @@ struct ClusterArgs {
 // runs on thread 0 alone before the block barrier that publishes the
 // totals: the scalar work on them (divisions, decisions) writes its
 // results to shared memory for the block.
+// The cluster barrier of this kernel.  Blocks exchange data through
+// shared memory only (the gathered vector g_s, the reduction partials red);
+// global memory is read at the start and written by each block for its
+// own rows at the end.  So the arrive releases this block's shared-memory
+// writes only (a restricted release fence, then a relaxed arrive; the wait
+// acquires), which keeps the barrier from waiting on the memory system.  A
+// remote read of another block's shared memory is ordered before that
+// block's later overwrite by the barrier between them and by the read's
+// value being stored to this block's shared memory before this block
+// arrives.
+__device__ __forceinline__ void cluster_sync_smem() {
+    asm volatile(
+        "fence.release.sync_restrict::shared::cta.cluster;\n\t"
+        "barrier.cluster.arrive.relaxed;\n\t"
+        "barrier.cluster.wait.acquire;" ::: "memory");
+}
+
 struct NoFin {
     __device__ __forceinline__ void operator()(const double*) const {}
 };
@@ -78,7 +95,7 @@ __device__ __forceinline__ void cluster_allsum(cgx::cluster_group& cl, double (&
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0) red[tog][warp] = t;
     }
-    cl.sync();
+    cluster_sync_smem();
     if (warp < (unsigned)NA) {
         double t = 0.0;
         if (lane < cl.num_blocks()) t = cl.map_shared_rank(red, lane)[tog][warp];
@@ -250,7 +267,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_cluster_cg(ClusterArgs A) {
     // p = z = M^-1 r into shared memory; rho = <r, z>
     auto init_dir = [&](double& rho) {
         double a[1] = {0.0};
-        cl.sync();  // every block is done gathering from g_s
+        cluster_sync_smem();  // every block is done gathering from g_s
 #pragma unroll
         for (int k = 0; k < CL_RMAX; ++k) {
             const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
@@ -281,14 +298,14 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_cluster_cg(ClusterArgs A) {
         // u = M^-1 r into shared memory, w = A u, p = s = 0; alpha =
         // gamma / delta with gamma = <r, u>, delta = <w, u>, beta = 0
         auto sr_start = [&]() {
-            cl.sync();  // every block is done gathering from g_s
+            cluster_sync_smem();  // every block is done gathering from g_s
 #pragma unroll
             for (int k = 0; k < CL_RMAX; ++k) {
                 const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
                 p[k] = q[k] = T(0);
                 if (li < nloc) g_s[li] = A.prec ? di[k] * r[k] : r[k];
             }
-            cl.sync();  // u published
+            cluster_sync_smem();  // u published
             double a[2] = {0.0, 0.0};
 #pragma unroll
             for (int k = 0; k < CL_RMAX; ++k) {
@@ -330,7 +347,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_cluster_cg(ClusterArgs A) {
                     a[2] = fma((double)r[k], (double)r[k], a[2]);
                 }
             }
-            cl.sync();  // u published
+            cluster_sync_smem();  // u published
 #pragma unroll
             for (int k = 0; k < CL_RMAX; ++k) {
                 const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
@@ -366,7 +383,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_cluster_cg(ClusterArgs A) {
                     const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
                     if (li < nloc) g_s[li] = x[k];
                 }
-                cl.sync();
+                cluster_sync_smem();
                 double tn = 0.0;
                 true_resid(tn);
                 if (tn <= thr) { o.status = GK_OK; break; }
@@ -427,7 +444,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_cluster_cg(ClusterArgs A) {
                 const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
                 if (li < nloc) g_s[li] = x[k];
             }
-            cl.sync();
+            cluster_sync_smem();
             double tn = 0.0;
             true_resid(tn);
             if (tn <= thr) { o.status = GK_OK; break; }
@@ -444,13 +461,13 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_cluster_cg(ClusterArgs A) {
                 g_s[li] = fmadd(tb, g_s[li], z);
             }
         }
-        cl.sync();
+        cluster_sync_smem();
     }
     o.iters = it;
     if (rec2 >= 0.0) o.rec = sqrt(rec2) / bn;
     // write x back and recompute the true residual for the report
     if (o.status != GK_ERR_ZERO_DIAG && bn > 0.0) {
-        cl.sync();
+        cluster_sync_smem();
 #pragma unroll
         for (int k = 0; k < CL_RMAX; ++k) {
             const int32_t li = (int32_t)threadIdx.x + k * CL_THREADS;
@@ -459,7 +476,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_cluster_cg(ClusterArgs A) {
                 g_s[li] = x[k];
             }
         }
-        cl.sync();
+        cluster_sync_smem();
         double tn = 0.0;
         true_resid(tn);
         o.tru = tn / bn;
