@@ -245,8 +245,9 @@ typedef struct {
     int32_t block_size;   /* block-Jacobi rows per diagonal block, 1..32 */
     int64_t wait_budget_ns; /* longest a device-side wait of this solve may last
                              (the ILU(0) substitutions' polls on values other
-                             warps produce, the CSR row-tile kernel's waits on
-                             its staged copies) before it gives up: the solve
+                             warps produce, or the window mode's waits on its
+                             copies of row records; the CSR row-tile kernel's
+                             waits on its staged copies) before it gives up: the solve
                              then returns GK_ERR_TIMEOUT and x holds no valid
                              iterate.  0 = the default of 2 s; negative values
                              are GK_ERR_INVALID */
@@ -364,7 +365,13 @@ gk_status gk_solve_batched(int32_t count, const gk_matrix* As,
  * wrong, and gk_matrix_describe reports device_error until the next ILU
  * application).  The substitutions run sync-free: each warp solves a chunk
  * of consecutive rows and waits, bounded by wait_budget_ns (0 = 2 s;
- * negative: GK_ERR_INVALID), for the values its rows depend on. */
+ * negative: GK_ERR_INVALID), for the values its rows depend on.  On
+ * stencil-like matrices (at most 4 terms a row per triangle, dependencies
+ * at most 2 levels back, levels of at most 12,288 rows) setup may pick the
+ * window mode instead, when it is faster: one cluster of 16 blocks solves
+ * a triangle level by level through distributed shared memory, and its
+ * only waits, for its own copies of the next level's row records, take the
+ * same budget.  Every mode gives the same bits. */
 gk_status gk_precond_apply(gk_matrix A, gk_precond kind, int32_t block_size,
                            const void* r, void* z, int64_t wait_budget_ns, void* stream);
 
